@@ -1,0 +1,232 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+library routines (numpy.linalg.cholesky), a textbook row-oriented Cholesky in pure
+Python, graph elimination by brute force, closed forms (1D Laplacian), the paper's
+Fig. 1 level sets (Sec. 3) and exact invariants."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_09288_gb300 import inputs
+
+
+def dense_L(f):
+    L = np.zeros((f.n, f.n))
+    for j in range(f.n):
+        L[f.li[f.lp[j]:f.lp[j + 1]], j] = f.lx[f.lp[j]:f.lp[j + 1]]
+    return L
+
+
+def seeded_perm(n, seed):
+    return np.argsort(inputs.uniform(seed, 9, n), kind="stable").astype(np.int32)
+
+
+def textbook_cholesky(a):
+    """Row-by-row (Cholesky-Banachiewicz) dense factorization, pure Python loops."""
+    n = len(a)
+    L = [[0.0] * n for _ in range(n)]
+    for i in range(n):
+        for j in range(i + 1):
+            s = sum(L[i][k] * L[j][k] for k in range(j))
+            if i == j:
+                L[i][j] = math.sqrt(a[i][i] - s)
+            else:
+                L[i][j] = (a[i][j] - s) / L[j][j]
+    return np.array(L)
+
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (2, 2), (7, 3), (40, 4), (120, 5)])
+def test_dense_vs_numpy(n, seed):
+    A = inputs.random_spd_dense(n, seed)
+    for perm in (np.arange(n, dtype=np.int32), seeded_perm(n, seed)):
+        f = oracle.cholesky(A, perm)
+        Ad = A.to_dense()[np.ix_(perm, perm)]
+        ref = np.linalg.cholesky(Ad)
+        err = np.linalg.norm(dense_L(f) - ref) / np.linalg.norm(ref)
+        assert err <= 1e-14, err
+        assert f.nnz_l == n * (n + 1) // 2
+
+
+@pytest.mark.parametrize("n", [3, 9, 12])
+def test_dense_vs_textbook_loops(n):
+    A = inputs.random_spd_dense(n, 11 + n)
+    f = oracle.cholesky(A)
+    ref = textbook_cholesky(A.to_dense().tolist())
+    assert np.linalg.norm(dense_L(f) - ref) <= 1e-14 * np.linalg.norm(ref)
+
+
+def test_lap1d_closed_form():
+    n = 60
+    f = oracle.cholesky(inputs.laplacian_1d(n))
+    L = dense_L(f)
+    j = np.arange(n)
+    diag = np.sqrt((j + 2.0) / (j + 1.0))
+    sub = -np.sqrt((j[:-1] + 1.0) / (j[:-1] + 2.0))
+    assert np.max(np.abs(np.diag(L) - diag) / diag) <= 1e-15
+    assert np.max(np.abs(np.diag(L, -1) - sub) / np.abs(sub)) <= 1e-15
+    assert f.nnz_l == 2 * n - 1
+    assert list(f.parent) == list(range(1, n)) + [-1]
+    start, sp, lv = f.supernodes(10 ** 6)
+    # only the last two columns have nested structure (c = 2, 1): supernodes
+    # {0}, {1}, ..., {n-3}, {n-2, n-1}, forming one chain
+    assert list(start) == list(range(n - 1)) + [n]
+    assert list(sp) == list(range(1, n - 1)) + [-1]
+    assert list(lv) == list(range(n - 1))
+
+
+def graph_elimination_pattern(adj, n):
+    """Fill pattern by eliminating vertices in order: the later neighbours of vertex k
+    become a clique (brute force on a dense boolean matrix)."""
+    M = np.array(adj, dtype=bool)
+    for k in range(n):
+        nb = [i for i in range(k + 1, n) if M[i, k]]
+        for a in nb:
+            for b in nb:
+                M[a, b] = True
+    return np.tril(M | np.eye(n, dtype=bool))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_symbolic_vs_graph_elimination(seed):
+    n = 30
+    u = inputs.uniform(100 + seed, 7, n * n).reshape(n, n)
+    adj = (u > 0.85) | (u.T > 0.85)
+    a = np.where(adj, 0.1 * np.sign(u + u.T), 0.0)
+    a = a + a.T
+    a[np.arange(n), np.arange(n)] = np.abs(a).sum(1) + 1.0
+    A = inputs.from_dense(a)
+    perm = seeded_perm(n, seed)
+    f = oracle.cholesky(A, perm)
+    pat = graph_elimination_pattern((a != 0)[np.ix_(perm, perm)], n)
+    got = np.zeros((n, n), bool)
+    for j in range(n):
+        got[f.li[f.lp[j]:f.lp[j + 1]], j] = True
+    assert (got == pat).all()
+    # elimination tree: parent(j) = first off-diagonal row of column j
+    for j in range(n):
+        rows = np.nonzero(pat[j + 1:, j])[0]
+        assert f.parent[j] == (rows[0] + j + 1 if rows.size else -1)
+    assert (f.colcount == pat.sum(0)).all()
+    # numeric L has no entry outside the symbolic pattern
+    Lref = np.linalg.cholesky(a[np.ix_(perm, perm)])
+    assert np.all(np.abs(Lref[~pat]) < 1e-300)
+
+
+def test_fig1_level_sets():
+    """Sec. 3, Fig. 1: supernodes 1,2 -> 4; 3 -> 5; 4,5 -> 6.  The best parallel
+    schedule is {1,2,3}, then {4,5}, then {6}."""
+    n = 6
+    a = np.eye(n) * 4.0
+    for i, j in [(3, 0), (3, 1), (4, 2), (5, 3), (5, 4)]:
+        a[i, j] = a[j, i] = -1.0
+    f = oracle.cholesky(inputs.from_dense(a))
+    assert list(f.parent) == [3, 3, 4, 5, 5, -1]
+    start, sp, lv = f.supernodes(64)
+    assert list(start) == [0, 1, 2, 3, 4, 5, 6]
+    sets = [sorted(int(s) + 1 for s in np.nonzero(lv == l)[0]) for l in range(lv.max() + 1)]
+    assert sets == [[1, 2, 3], [4, 5], [6]]
+
+
+def test_dense_supernode_and_width_cap():
+    n = 30
+    f = oracle.cholesky(inputs.random_spd_dense(n, 3))
+    start, sp, lv = f.supernodes(10 ** 6)
+    assert list(start) == [0, n]
+    start, sp, lv = f.supernodes(8)
+    assert list(start) == [0, 8, 16, 24, 30]
+    assert list(sp) == [1, 2, 3, -1]
+    assert list(lv) == [0, 1, 2, 3]
+
+
+@pytest.mark.parametrize("name", ["lap2d_12", "lap3d_5", "st27x3_3", "dense"])
+def test_flop_model_counts(name):
+    if name == "dense":
+        A, perm = inputs.random_spd_dense(25, 8), None
+    else:
+        A, perm = inputs.workload(name)
+    f = oracle.cholesky(A, perm)
+    assert f.flops_counted == f.flops  # every counted op equals sum_j c_j^2
+    assert f.flops == float(np.sum(f.colcount.astype(np.int64) ** 2))
+
+
+@pytest.mark.parametrize("name", ["lap2d_32", "st27x3_5", "diff3d7_8"])
+def test_llt_invariant(name):
+    A, perm = inputs.workload(name)
+    f = oracle.cholesky(A, perm)
+    e = oracle.llt_error(A.n, f.bp, f.bi, f.bx, f.lp, f.li, f.lx)
+    assert e <= 1e-13, e
+
+
+def test_diagonal_and_block_diagonal():
+    d = 1.0 + np.arange(10.0)
+    f = oracle.cholesky(inputs.from_dense(np.diag(d)))
+    assert np.array_equal(f.lx, np.sqrt(d))
+    b1 = inputs.random_spd_dense(6, 1).to_dense()
+    b2 = inputs.random_spd_dense(9, 2).to_dense()
+    a = np.zeros((15, 15))
+    a[:6, :6], a[6:, 6:] = b1, b2
+    L = dense_L(oracle.cholesky(inputs.from_dense(a)))
+    assert np.allclose(L[:6, :6], np.linalg.cholesky(b1), rtol=1e-14, atol=1e-14)
+    assert np.allclose(L[6:, 6:], np.linalg.cholesky(b2), rtol=1e-14, atol=1e-14)
+    assert np.all(L[6:, :6] == 0.0)
+
+
+def test_not_spd_detected():
+    d = 1.0 + np.arange(10.0)
+    d[7] = -1.0
+    with pytest.raises(oracle.NotSPD) as e:
+        oracle.cholesky(inputs.from_dense(np.diag(d)))
+    assert e.value.col == 7
+    a = inputs.laplacian_2d_5pt(6)
+    vals = a.vals.copy()
+    vals[a.colptr[20]] = -4.0
+    bad = inputs.SpdMatrix(a.n, a.colptr, a.rowind, vals)
+    with pytest.raises(oracle.NotSPD):
+        oracle.cholesky(bad)
+
+
+def test_permute_matches_dense_indexing():
+    A = inputs.laplacian_3d_7pt(4)
+    perm = seeded_perm(A.n, 3)
+    bp, bi, bx = oracle.permute(A.n, A.colptr, A.rowind, A.vals, perm)
+    B = inputs.SpdMatrix(A.n, bp, bi, bx).to_dense()
+    assert np.array_equal(B, A.to_dense()[np.ix_(perm, perm)])
+    with pytest.raises(ValueError):
+        oracle.permute(A.n, A.colptr, A.rowind, A.vals, np.zeros(A.n, np.int32))
+
+
+def test_solve_1d_and_residual():
+    n = 200
+    A = inputs.laplacian_1d(n)
+    f = oracle.cholesky(A)
+    xt = inputs.uniform(1, 5, n)
+    b = A.to_dense() @ xt
+    x = f.solve(b)[:, 0]
+    kappa = (2.0 / (1 - math.cos(math.pi / (n + 1))))  # lambda_max / lambda_min bound
+    assert np.max(np.abs(x - xt)) <= 10 * kappa * 2.2e-16 * np.max(np.abs(xt))
+    assert oracle.residual(n, A.colptr, A.rowind, A.vals, b, x) <= 1e-15
+
+
+def test_solve_multi_rhs_permuted():
+    A, perm = inputs.workload("st27x3_4")
+    f = oracle.cholesky(A, perm)
+    X_true = inputs.rhs_block(4, A.n, 3)
+    Bm = A.to_scipy_full() @ X_true
+    X = f.solve(Bm)
+    assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, Bm, X) <= 1e-15
+    np.testing.assert_allclose(X, np.linalg.solve(A.to_dense(), Bm), rtol=1e-11, atol=1e-13)
+
+
+def test_residual_and_spmv_definitions():
+    d = np.array([1.0, 2.0, 4.0])
+    A = inputs.from_dense(np.diag(d))
+    x = np.array([1.0, -1.0, 0.5])
+    assert np.array_equal(oracle.spmv(3, A.colptr, A.rowind, A.vals, x), d * x)
+    b = d * x
+    b[1] += 0.25  # ||r||_inf = 0.25, ||A||_inf = 4, ||x||_inf = 1
+    assert oracle.residual(3, A.colptr, A.rowind, A.vals, b, x) == 0.25 / 4.0
+    A2 = inputs.laplacian_2d_5pt(5)
+    x2 = inputs.uniform(3, 5, 25)
+    assert np.allclose(oracle.spmv(25, A2.colptr, A2.rowind, A2.vals, x2), A2.to_dense() @ x2,
+                       rtol=0, atol=1e-14)
