@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the FP64 supernodal Cholesky factorization + solve on one GB300 per rank.
+
+Workload (default): 3D 27-point stencil, 3 unknowns per node, 48^3 grid (n = 331,776),
+nested-dissection ordering, seed 2, FP64; one step = numeric factorization (all levels:
+assembly, POTRF, TRSM, Schur update + scatter) + one forward/back solve with
+b = A x_true.  Inputs (values, right-hand side) are resident in HBM before the timed
+region; the factor (3.9 GB) and the values are far larger than L2, so no flush is needed.
+
+value     = factorization flops (sum_j c_j^2) per second of the whole step, all ranks
+e2e       = the same through the C ABI with host (pinned) buffers: values and b copied in,
+            x copied out, every step
+roofline  = the dominant kernel's algorithmic flops / its CUDA-event time, against the
+            FP64 peak (measured bf16 peak x the nominal FP64/bf16 ratio 1.25/2250)
+
+Multi-GPU: one process per GPU (torchrun), each factoring its own replica (the
+factorization of one matrix is not sharded): weak scaling, no data-path collective.
+``--impl reference`` times the CPU oracle (test code, single thread) on a bounded
+sample of the same family instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "factor GFLOP/s + % FP64 peak; served solves/s and p99 latency at resid<=1e-12"
+NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0  # nominal dense FP64 / BF16 rates of a GB300
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"bf16_tflops": FALLBACK_BF16_TFLOPS, "hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running (clocks and throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        with open(self.file.name) as f:
+            rows = [r.split(",") for r in f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("factor_kernels.cu",):
+        with open(os.path.join(ROOT, "paper_2202_09288_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def oracle_sample(name: str):
+    """Times the CPU oracle (one thread) on one factorization + solve of a sample."""
+    import oracle
+    from paper_2202_09288_gb300 import inputs
+
+    A, perm = inputs.workload(name)
+    bp, bi, bx = oracle.permute(A.n, A.colptr, A.rowind, A.vals, perm)
+    parent, cc, lp, li = oracle.symbolic(A.n, bp, bi)
+    b = A.to_scipy_full() @ inputs.rhs_block(1, A.n, 1)[:, 0]
+    t0 = time.perf_counter()
+    lx, fl = oracle.factor(A.n, bp, bi, bx, lp, li)
+    x = oracle.solve(A.n, lp, li, lx, perm, b)
+    dt = time.perf_counter() - t0
+    flops = float(np.sum(cc.astype(np.float64) ** 2))
+    return flops, dt, x
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return 0
+    sample = args.ref_sample
+    times, flops = [], 0.0
+    for i in range(args.warmup + args.steps):
+        flops, dt, _ = oracle_sample(sample)
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * float(np.mean(times))
+    gf = flops / (ms * 1e-3) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gf, "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": gf, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample}: one FP64 factorization + 1-RHS solve per step "
+                                   f"({flops:.3e} flops) by the single-thread C oracle"},
+        "e2e": {"value": gf, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(args):
+    return {"workload": args.workload, "n": None, "precision": "fp64", "nrhs": 1,
+            "ordering": "geometric nested dissection (leaf 64 nodes)",
+            "width_cap": args.width, "assembly": args.assembly,
+            "l2": "inputs larger than L2 (factor ~3.9 GB), no flush"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="st27x3_48")
+    ap.add_argument("--width", type=int, default=64)
+    ap.add_argument("--assembly", default="atomic", choices=["atomic", "owner"])
+    ap.add_argument("--cpu-sample", default="st27x3_24")
+    ap.add_argument("--ref-sample", default="st27x3_20")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    import paper_2202_09288_gb300 as P
+    from paper_2202_09288_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    A, perm = inputs.workload(args.workload)
+    n = A.n
+    xt = inputs.rhs_block(1, n, 1)[:, 0]
+    Afull = A.to_scipy_full()
+    b = Afull @ xt
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = P.Context(device=local, width_cap=args.width,
+                    assembly=P.CHOL_ASSEMBLY_OWNER if args.assembly == "owner"
+                    else P.CHOL_ASSEMBLY_ATOMIC, stream=stream.cuda_stream)
+    sym = P.Symbolic(ctx, A, perm)
+    F = sym.info["flops"]
+    vals_d = torch.from_numpy(A.vals).cuda()
+    b_d = torch.from_numpy(b).cuda()
+    x_d = torch.empty_like(b_d)
+    torch.cuda.synchronize()
+    num = P.Factor(ctx, sym, vals_d)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        num.refactor(vals_d)
+        if ev is not None:
+            ev[1].record(stream)
+        num.solve(b_d, x_d)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    rc, bad = num.status()
+    if rc != P.CHOL_OK:
+        raise SystemExit(f"factorization failed: {P.chol_strerror(rc)} at column {bad}")
+
+    clocks = ClockSampler(local)
+    P.chol_profile_reset(ctx.handle)
+    P.chol_profile_enable(ctx.handle, True)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    P.chol_profile_enable(ctx.handle, False)
+    prof = P.chol_profile_read(ctx.handle)
+    total_ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    fac_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    sol_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    x = x_d.cpu().numpy()
+    rn = np.abs(b - Afull @ x).max()
+    anorm = np.abs(Afull).sum(axis=1).max()
+    resid = float(rn / (anorm * np.abs(x).max()))
+    launches = sum(v["launches"] for v in prof.values())
+
+    # end to end through host buffers (pinned): values + b in, x out, every step
+    vals_h = torch.empty(A.vals.shape, dtype=torch.float64, pin_memory=True).numpy()
+    vals_h[:] = A.vals
+    b_h = torch.empty((n,), dtype=torch.float64, pin_memory=True).numpy()
+    b_h[:] = b
+    x_h = torch.empty((n, 1), dtype=torch.float64, pin_memory=True).numpy()
+    for _ in range(1):
+        num.refactor(vals_h)
+        P.chol_solve(ctx.handle, num.handle, b_h.reshape(n, 1), x_h)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        num.refactor(vals_h)
+        P.chol_solve(ctx.handle, num.handle, b_h.reshape(n, 1), x_h)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    peaks, peak_src = measured_peaks()
+    fp64_peak_tflops = peaks["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
+    fac_kinds = {k: v for k, v in prof.items() if v["timed"] > 0 and v["flops"] > 0}
+    dom = max(fac_kinds, key=lambda k: fac_kinds[k]["ms"])
+    d = prof[dom]
+    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+    traffic = ncu_traffic(dom)
+
+    value = world * F / (ms_step * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": dict(workload_config(args), n=n, nnz_a=A.nnz_lower, nnz_l=sym.info["nnz_l"],
+                       flops_per_step=F, nsuper=sym.info["nsuper"],
+                       nlevels=sym.info["nlevels"],
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "factor_ms": fac_ms, "solve_ms": sol_ms,
+        "factor_gflops": F / (fac_ms * 1e-3) / 1e9,
+        "fp64_peak_frac": (F / (fac_ms * 1e-3) / 1e12) / fp64_peak_tflops,
+        "residual": resid,
+        "gpu_launches": int(launches),
+        "e2e": {"value": world * F / e2e_s / 1e9, "unit": "GFLOP/s",
+                "h2d_bytes_per_step": int(A.vals.nbytes + b_h.nbytes),
+                "d2h_bytes_per_step": int(x_h.nbytes)},
+        "roofline": {"bound": "tensor", "kernel": dom, "achieved": achieved,
+                     "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak_tflops, "traffic": traffic,
+                     "peak_source": f"FP64 = {peak_src} bf16 {peaks['bf16_tflops']} TFLOP/s x "
+                                    "nominal FP64/bf16 1.25/2250 (DMMA loop measured "
+                                    "1.046 TFLOP/s on this pool)"},
+        "kernels": {k: {"launches": v["launches"], "ms": v["ms"] / args.steps,
+                        "share": v["ms"] / max(sum(w["ms"] for w in prof.values()), 1e-9)}
+                    for k, v in prof.items() if v["launches"]},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fl, dt, _ = oracle_sample(args.cpu_sample)
+        line["cpu_baseline"] = {
+            "value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"{args.cpu_sample}: one FP64 factorization + 1-RHS solve "
+                      f"({fl:.3e} flops, {dt:.1f} s) by the single-thread C oracle"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * chol.h -- C ABI of a GB300 (sm_103a) supernodal sparse Cholesky library.
+ *
+ * The library factors a sparse symmetric positive definite matrix A = L L^T and solves
+ * A X = B with the two triangular solves L Y = B, L^T X = Y.  This is the computation the
+ * paper ("Optimization of the Sparse Multi-Threaded Cholesky Factorization for A64FX")
+ * names as the bulk of the solver: Sec. 1 states A = L L^T and the three phases
+ * analyze / factorize / solve, Sec. 2 describes the analysis (reordering, elimination
+ * tree, supernodes), Sec. 3 and Listing 1 the supernodal factorization (SYRK and GEMM
+ * updates from earlier supernodes, then POTRF and TRSM of the supernode, with a
+ * serialized assembly of the updates), and Fig. 1 the elimination-tree parallelism.
+ *
+ * Conventions that hold for every entry point:
+ *  - Matrices enter as the LOWER triangle, diagonal included, in compressed sparse column
+ *    form: colptr int64[n+1], rowind int32[nnz] (rows strictly increasing inside a
+ *    column, every row >= its column), values float64[nnz] in the same order.
+ *  - perm is int32[n] with perm[new] = old; the library factors B = P^T A P, i.e.
+ *    B[i][j] = A[perm[i]][perm[j]].  Solves take and return vectors in A's numbering.
+ *  - Dense blocks (B, X) are column-major n x nrhs with a leading dimension >= n.
+ *  - Every function returns an int status: CHOL_OK (0), CHOL_PENDING (1), or a negative
+ *    CHOL_E_* code; chol_strerror() names it.  No exception crosses the ABI and the
+ *    library never aborts the process.
+ *  - "where" arguments say whether a pointer is host memory (CHOL_HOST) or device memory
+ *    of the context's GPU (CHOL_DEVICE).  Device work is ordered on the context stream.
+ *    Host-pointer calls copy in, compute and copy out before returning; device-pointer
+ *    calls return after enqueueing, and a device-side failure (a non-positive pivot) is
+ *    reported by the next chol_factor_status() call.
+ *  - Ownership: the caller owns every array it passes and may free it once the call
+ *    returns (device arrays: once the stream has passed the call).  Handles returned by
+ *    the library are owned by it until the matching chol_free_* / chol_destroy.
+ *  - Threading: a context and its handles must not be used from two threads at once.
+ */
+#ifndef CHOL_H
+#define CHOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHOL_OK 0
+#define CHOL_PENDING 1
+#define CHOL_E_INVALID (-1)   /* malformed input or argument */
+#define CHOL_E_NOT_SPD (-2)   /* a pivot was <= 0 or NaN: A is not positive definite */
+#define CHOL_E_OOM (-3)       /* device allocation failed or the HBM budget is exceeded */
+#define CHOL_E_CUDA (-4)      /* a CUDA runtime call failed */
+#define CHOL_E_TIMEOUT (-5)   /* a bounded device-side wait expired */
+#define CHOL_E_NODEVICE (-6)  /* no usable CUDA device for a call that needs one */
+#define CHOL_E_STALL (-7)     /* iterative refinement did not converge */
+
+#define CHOL_HOST 0
+#define CHOL_DEVICE 1
+
+/* Scatter of the Schur updates into ancestor supernodes (Sec. 3: the paper serializes
+ * this assembly with a lock).  ATOMIC adds each update with device atomics (fast, run-to-
+ * run rounding differences).  OWNER stages each level's updates and lets every target
+ * pull them in a fixed order (bitwise reproducible). */
+#define CHOL_ASSEMBLY_ATOMIC 0
+#define CHOL_ASSEMBLY_OWNER 1
+
+#define CHOL_FP64 0   /* FP64 factor */
+#define CHOL_MIXED 1  /* FP32 panels with TF32 tensor-core Schur updates; FP64 refinement */
+
+typedef struct chol_ctx chol_ctx;
+typedef struct chol_sym chol_sym;
+typedef struct chol_num chol_num;
+
+typedef struct chol_opts {
+  int device;         /* CUDA device ordinal */
+  void* stream;       /* cudaStream_t for all device work; NULL: the context makes one */
+  int width_cap;      /* largest supernode width W in columns (1..128); 0 = default 64 */
+  int assembly;       /* CHOL_ASSEMBLY_ATOMIC or CHOL_ASSEMBLY_OWNER */
+  size_t hbm_budget;  /* bytes of device memory the context may hold; 0 = no limit */
+  double pivot_tau;   /* CHOL_MIXED: a pivot below pivot_tau * a_jj redoes the supernode's
+                         diagonal block in FP64; 0 = default 1e-5 */
+} chol_opts;
+
+typedef struct chol_sym_stats {
+  int64_t n;          /* order of A */
+  int64_t nnz_a;      /* stored lower entries of A */
+  int64_t nnz_l;      /* entries of L (diagonal included), exact, no padding */
+  int64_t l_storage;  /* values held by the supernode panels (incl. unused upper
+                         triangles of diagonal blocks) */
+  int64_t nsuper;     /* supernodes after the width cap */
+  int64_t nlevels;    /* elimination-tree levels of the supernodal tree */
+  double flops;       /* sum_j c_j^2, c_j = entries of column j of L */
+  int64_t max_width;  /* widest supernode */
+  int64_t max_rows;   /* most rows in a supernode */
+} chol_sym_stats;
+
+/* Fills *opts with the defaults (device 0, own stream, W = 64, atomic assembly). */
+void chol_default_opts(chol_opts* opts);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int chol_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* chol_strerror(int status);
+
+/* Creates a context bound to opts->device.  Fails with CHOL_E_NODEVICE when the device
+ * cannot be opened.  opts may be NULL for the defaults. */
+int chol_create(const chol_opts* opts, chol_ctx** out);
+void chol_destroy(chol_ctx* ctx);
+
+/* Symbolic analysis (Sec. 2): permutes the pattern, builds the elimination tree
+ * (parent(j) = smallest off-diagonal row of column j of L), the column counts, the
+ * fundamental supernodes cut to at most W columns, their row structures, the level sets
+ * of the supernodal tree (Sec. 3, Fig. 1) and the per-level task lists of the device
+ * factorization.  Host work only (no device is touched): only opts->width_cap is read,
+ * opts may be NULL for W = 64, and the result is uploaded to the device of the first
+ * context that factors with it.  Errors: CHOL_E_INVALID for n < 0, n >= 2^31,
+ * a row out of range, above the diagonal, unsorted or duplicated, a perm that is not a
+ * permutation.  The caller keeps ownership of colptr, rowind and perm. */
+int chol_analyze(const chol_opts* opts, int64_t n, const int64_t* colptr,
+                 const int32_t* rowind, const int32_t* perm, chol_sym** out);
+int chol_sym_info(const chol_sym* sym, chol_sym_stats* stats);
+
+/* Copies symbolic results to host arrays; each pointer may be NULL.  parent and colcount
+ * have n entries (column elimination tree, -1 at a root; column counts incl. diagonal);
+ * sn_start has nsuper+1 entries (first column of each supernode, then n); sn_level has
+ * nsuper entries (0 for supernodes without children, else 1 + the children's maximum). */
+int chol_sym_export(const chol_sym* sym, int32_t* parent, int64_t* colcount,
+                    int32_t* sn_start, int32_t* sn_level);
+void chol_free_sym(chol_sym* sym);
+
+/* Numeric factorization of B = P^T A P (Sec. 3, Listing 1, reorganized per level).
+ * vals holds A's lower values in the order of the colptr/rowind given to chol_analyze.
+ * precision is CHOL_FP64 or CHOL_MIXED.  Allocates the factor on the device and enqueues
+ * the factorization; *out is valid at once.  Errors: CHOL_E_INVALID, CHOL_E_OOM,
+ * CHOL_E_CUDA; a non-positive pivot surfaces through chol_factor_status(). */
+int chol_factorize(chol_ctx* ctx, const chol_sym* sym, const double* vals, int where,
+                   int precision, chol_num** out);
+
+/* Re-runs the numeric factorization in the storage of an existing factor with new values
+ * on the same pattern (no allocation). */
+int chol_refactorize(chol_ctx* ctx, chol_num* num, const double* vals, int where);
+
+/* Waits for the factorization to finish.  Returns CHOL_OK or CHOL_E_NOT_SPD; in the
+ * latter case *bad_col (if not NULL) receives a column of B whose pivot failed (the
+ * smallest one this run saw). */
+int chol_factor_status(chol_ctx* ctx, const chol_num* num, int64_t* bad_col);
+
+/* Copies L to host CSC arrays in B's numbering: Lp int64[n+1], Li int32[nnz_l],
+ * Lx float64[nnz_l], rows sorted, diagonal first.  Any pointer may be NULL. */
+int chol_factor_export(chol_ctx* ctx, const chol_num* num, int64_t* Lp, int32_t* Li,
+                       double* Lx);
+void chol_free_num(chol_num* num);
+
+/* Solves A X = B (Sec. 1: L Y = P^T B, then L^T Z = Y, X = P Z) for nrhs right-hand
+ * sides with the device forward and back substitution over the supernodal levels.
+ * X may equal B (in place) only when ldx == ldb.  where: CHOL_HOST (copy in, solve, copy
+ * out, synchronize) or CHOL_DEVICE (stream-ordered, returns after enqueue). */
+int chol_solve(chol_ctx* ctx, const chol_num* num, int64_t nrhs, const double* B,
+               int64_t ldb, double* X, int64_t ldx, int where);
+
+/* ---- tracing ------------------------------------------------------------------------
+ * Per-kernel-kind accounting of the device work a context enqueues: the launch count is
+ * always kept; with profiling on, every launch is bracketed by CUDA events on the context
+ * stream and its duration is added to its kind.  flops and bytes are the algorithmic work
+ * of the launches (Schur tiles: u(u+1)n per supernode of u off-diagonal rows and n
+ * columns; POTRF: n^3/3 + n^2/2; TRSM: u n^2; solves: bytes of L and the vectors read). */
+typedef struct chol_prof_entry {
+  char name[32];      /* kernel kind, e.g. "schur64_f64" */
+  int64_t launches;   /* launches since the last reset */
+  double ms;          /* summed event time of the timed launches (profiling on) */
+  int64_t timed;      /* launches that were bracketed by events */
+  double flops;       /* algorithmic flops of those launches */
+  double bytes;       /* algorithmic bytes of those launches */
+} chol_prof_entry;
+
+/* Turns event bracketing on (1) or off (0).  Events are recorded on the context stream;
+ * do not enable while the stream is being captured into a CUDA graph. */
+int chol_profile_enable(chol_ctx* ctx, int on);
+/* Synchronizes the stream, folds finished events in, and copies up to max entries; the
+ * number of kinds is stored in *count.  Entries with zero launches are included. */
+int chol_profile_read(chol_ctx* ctx, chol_prof_entry* out, int max, int* count);
+int chol_profile_reset(chol_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHOL_H */

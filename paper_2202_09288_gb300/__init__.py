@@ -1,0 +1,311 @@
+"""GB300 (sm_103a) supernodal sparse Cholesky: a thin ctypes binding of include/chol.h.
+
+Every function here only marshals arguments to the C ABI of ``libchol.so``; all work runs
+in the library (host analysis in C++, the numeric phases in CUDA kernels).  If the
+library is missing, importing works but every call raises: there is no fallback.
+
+Host arrays are numpy arrays; device arrays are torch CUDA tensors (PyTorch is used only
+for device memory and streams).  Function names follow the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchol.so")
+
+CHOL_OK, CHOL_PENDING = 0, 1
+CHOL_E_INVALID, CHOL_E_NOT_SPD, CHOL_E_OOM, CHOL_E_CUDA = -1, -2, -3, -4
+CHOL_E_TIMEOUT, CHOL_E_NODEVICE, CHOL_E_STALL = -5, -6, -7
+CHOL_HOST, CHOL_DEVICE = 0, 1
+CHOL_ASSEMBLY_ATOMIC, CHOL_ASSEMBLY_OWNER = 0, 1
+CHOL_FP64, CHOL_MIXED = 0, 1
+
+
+class CholError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        msg = lib().chol_strerror(status).decode()
+        super().__init__(f"{where}: {msg} ({status})" if where else f"{msg} ({status})")
+        self.status = status
+
+
+class chol_opts(C.Structure):
+    _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("width_cap", C.c_int),
+                ("assembly", C.c_int), ("hbm_budget", C.c_size_t), ("pivot_tau", C.c_double)]
+
+
+class chol_sym_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz_a", C.c_int64), ("nnz_l", C.c_int64),
+                ("l_storage", C.c_int64), ("nsuper", C.c_int64), ("nlevels", C.c_int64),
+                ("flops", C.c_double), ("max_width", C.c_int64), ("max_rows", C.c_int64)]
+
+
+class chol_prof_entry(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double),
+                ("timed", C.c_int64), ("flops", C.c_double), ("bytes", C.c_double)]
+
+
+# name -> (restype, argtypes)
+_P, _I, _I64 = C.c_void_p, C.c_int, C.c_int64
+EXPORTS = {
+    "chol_default_opts": (None, [C.POINTER(chol_opts)]),
+    "chol_version": (_I, []),
+    "chol_strerror": (C.c_char_p, [_I]),
+    "chol_create": (_I, [C.POINTER(chol_opts), C.POINTER(_P)]),
+    "chol_destroy": (None, [_P]),
+    "chol_analyze": (_I, [C.POINTER(chol_opts), _I64, _P, _P, _P, C.POINTER(_P)]),
+    "chol_sym_info": (_I, [_P, C.POINTER(chol_sym_stats)]),
+    "chol_sym_export": (_I, [_P, _P, _P, _P, _P]),
+    "chol_free_sym": (None, [_P]),
+    "chol_factorize": (_I, [_P, _P, _P, _I, _I, C.POINTER(_P)]),
+    "chol_refactorize": (_I, [_P, _P, _P, _I]),
+    "chol_factor_status": (_I, [_P, _P, C.POINTER(_I64)]),
+    "chol_factor_export": (_I, [_P, _P, _P, _P, _P]),
+    "chol_free_num": (None, [_P]),
+    "chol_solve": (_I, [_P, _P, _I64, _P, _I64, _P, _I64, _I]),
+    "chol_profile_enable": (_I, [_P, _I]),
+    "chol_profile_read": (_I, [_P, C.POINTER(chol_prof_entry), _I, C.POINTER(_I)]),
+    "chol_profile_reset": (_I, [_P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads libchol.so (raises if it has not been built: no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; build it with "
+                               "`python -m paper_2202_09288_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != CHOL_OK:
+        raise CholError(rc, where)
+
+
+def _ptr(a):
+    """(pointer, where) of a numpy array (host) or a torch CUDA tensor (device)."""
+    if a is None:
+        return None, CHOL_HOST
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous and not a.flags.f_contiguous:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data, CHOL_HOST
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), (CHOL_DEVICE if a.is_cuda else CHOL_HOST)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+# ---- C ABI, one Python function per entry point -----------------------------------------
+def chol_default_opts() -> chol_opts:
+    o = chol_opts()
+    lib().chol_default_opts(C.byref(o))
+    return o
+
+
+def chol_version() -> int:
+    return lib().chol_version()
+
+
+def chol_create(opts: chol_opts | None = None) -> int:
+    h = C.c_void_p()
+    _check(lib().chol_create(C.byref(opts) if opts is not None else None, C.byref(h)),
+           "chol_create")
+    return h.value
+
+
+def chol_destroy(ctx: int) -> None:
+    lib().chol_destroy(ctx)
+
+
+def chol_analyze(opts, n, colptr, rowind, perm) -> int:
+    colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+    rowind = np.ascontiguousarray(rowind, dtype=np.int32)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    h = C.c_void_p()
+    _check(lib().chol_analyze(C.byref(opts) if opts is not None else None, int(n),
+                              colptr.ctypes.data, rowind.ctypes.data,
+                              perm.ctypes.data, C.byref(h)), "chol_analyze")
+    return h.value
+
+
+def chol_sym_info(sym) -> dict:
+    st = chol_sym_stats()
+    _check(lib().chol_sym_info(sym, C.byref(st)), "chol_sym_info")
+    return {name: getattr(st, name) for name, _ in chol_sym_stats._fields_}
+
+
+def chol_sym_export(sym) -> dict:
+    info = chol_sym_info(sym)
+    n, ns = info["n"], info["nsuper"]
+    parent = np.zeros(n, np.int32)
+    cc = np.zeros(n, np.int64)
+    start = np.zeros(ns + 1, np.int32)
+    level = np.zeros(ns, np.int32)
+    _check(lib().chol_sym_export(sym, parent.ctypes.data, cc.ctypes.data, start.ctypes.data,
+                                 level.ctypes.data), "chol_sym_export")
+    return {"parent": parent, "colcount": cc, "sn_start": start, "sn_level": level}
+
+
+def chol_free_sym(sym) -> None:
+    lib().chol_free_sym(sym)
+
+
+def chol_factorize(ctx, sym, vals, precision=CHOL_FP64) -> int:
+    p, where = _ptr(vals)
+    h = C.c_void_p()
+    _check(lib().chol_factorize(ctx, sym, p, where, precision, C.byref(h)), "chol_factorize")
+    return h.value
+
+
+def chol_refactorize(ctx, num, vals) -> None:
+    p, where = _ptr(vals)
+    _check(lib().chol_refactorize(ctx, num, p, where), "chol_refactorize")
+
+
+def chol_factor_status(ctx, num) -> tuple[int, int]:
+    bad = C.c_int64(-1)
+    rc = lib().chol_factor_status(ctx, num, C.byref(bad))
+    if rc not in (CHOL_OK, CHOL_E_NOT_SPD):
+        _check(rc, "chol_factor_status")
+    return rc, bad.value
+
+
+def chol_factor_export(ctx, num, n, nnz_l):
+    lp = np.zeros(n + 1, np.int64)
+    li = np.zeros(nnz_l, np.int32)
+    lx = np.zeros(nnz_l, np.float64)
+    _check(lib().chol_factor_export(ctx, num, lp.ctypes.data, li.ctypes.data, lx.ctypes.data),
+           "chol_factor_export")
+    return lp, li, lx
+
+
+def chol_free_num(num) -> None:
+    lib().chol_free_num(num)
+
+
+def chol_solve(ctx, num, B, X=None):
+    """Solves A X = B.  B: numpy (n,) / (n, k) Fortran-ordered, or a torch CUDA tensor laid
+    out column-major (shape (k, n) contiguous, i.e. column c is row c of the tensor)."""
+    if isinstance(B, np.ndarray):
+        B2 = np.asfortranarray(B.reshape(B.shape[0], -1), dtype=np.float64)
+        n, k = B2.shape
+        if X is None:
+            X = np.zeros((n, k), dtype=np.float64, order="F")
+        pb, wb = _ptr(B2)
+        px, wx = _ptr(X)
+        _check(lib().chol_solve(ctx, num, k, pb, n, px, n, CHOL_HOST), "chol_solve")
+        return X.reshape(B.shape) if B.ndim == 1 else X
+    # torch device tensor: (k, n) contiguous = n x k column-major, ld = n
+    k, n = (1, B.shape[0]) if B.dim() == 1 else (B.shape[0], B.shape[1])
+    if X is None:
+        X = B.new_empty(B.shape)
+    pb, wb = _ptr(B)
+    px, wx = _ptr(X)
+    if wb != CHOL_DEVICE or wx != CHOL_DEVICE:
+        raise ValueError("torch tensors must live on the context's CUDA device")
+    _check(lib().chol_solve(ctx, num, k, pb, n, px, n, CHOL_DEVICE), "chol_solve")
+    return X
+
+
+def chol_profile_enable(ctx, on: bool) -> None:
+    _check(lib().chol_profile_enable(ctx, 1 if on else 0), "chol_profile_enable")
+
+
+def chol_profile_read(ctx) -> dict:
+    arr = (chol_prof_entry * 32)()
+    cnt = C.c_int()
+    _check(lib().chol_profile_read(ctx, arr, 32, C.byref(cnt)), "chol_profile_read")
+    return {arr[k].name.decode(): {"launches": arr[k].launches, "ms": arr[k].ms,
+                                   "timed": arr[k].timed, "flops": arr[k].flops,
+                                   "bytes": arr[k].bytes} for k in range(cnt.value)}
+
+
+def chol_profile_reset(ctx) -> None:
+    _check(lib().chol_profile_reset(ctx), "chol_profile_reset")
+
+
+# ---- small object wrappers used by the tests and the bench -------------------------------
+def make_opts(device: int = 0, width_cap: int = 64, assembly: int = CHOL_ASSEMBLY_ATOMIC,
+              stream: int | None = None, hbm_budget: int = 0) -> chol_opts:
+    o = chol_default_opts()
+    o.device, o.width_cap, o.assembly, o.hbm_budget = device, width_cap, assembly, hbm_budget
+    o.stream = stream
+    return o
+
+
+class Context:
+    def __init__(self, device: int = 0, width_cap: int = 64, assembly: int = CHOL_ASSEMBLY_ATOMIC,
+                 stream: int | None = None, hbm_budget: int = 0):
+        self.opts = make_opts(device, width_cap, assembly, stream, hbm_budget)
+        self.handle = chol_create(self.opts)
+
+    def close(self):
+        if self.handle:
+            chol_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Symbolic:
+    """Host symbolic analysis; ``opts`` is a Context, a chol_opts, or None (W = 64)."""
+
+    def __init__(self, opts, A, perm):
+        if isinstance(opts, Context):
+            opts = opts.opts
+        self.n = A.n
+        self.handle = chol_analyze(opts, A.n, A.colptr, A.rowind, perm)
+        self.info = chol_sym_info(self.handle)
+
+    def export(self):
+        return chol_sym_export(self.handle)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                chol_free_sym(self.handle)
+        except Exception:
+            pass
+
+
+class Factor:
+    def __init__(self, ctx: Context, sym: Symbolic, vals, precision=CHOL_FP64):
+        self.ctx, self.sym = ctx, sym
+        self.handle = chol_factorize(ctx.handle, sym.handle, vals, precision)
+
+    def refactor(self, vals):
+        chol_refactorize(self.ctx.handle, self.handle, vals)
+
+    def status(self):
+        return chol_factor_status(self.ctx.handle, self.handle)
+
+    def export(self):
+        return chol_factor_export(self.ctx.handle, self.handle, self.sym.n,
+                                  self.sym.info["nnz_l"])
+
+    def solve(self, B, X=None):
+        return chol_solve(self.ctx.handle, self.handle, B, X)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                chol_free_num(self.handle)
+        except Exception:
+            pass

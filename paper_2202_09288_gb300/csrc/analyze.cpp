@@ -1,0 +1,344 @@
+// analyze.cpp -- host symbolic analysis for the supernodal factorization.
+//
+// Sec. 2 of the paper: the analysis phase reorders the matrix (here the ordering is an
+// input), builds the elimination tree and merges adjacent columns into supernodes; Sec. 3
+// and Fig. 1: supernodes whose subtrees are finished can be factored at the same time,
+// which gives the level sets that the device schedule runs one after another.
+//
+// Algorithms (all standard, none shared with the test oracle):
+//   elimination tree  Liu's algorithm with path compression over the rows of B
+//   column counts     row-subtree traversal: row i of L is the union of the etree paths
+//                     from every k with B_ik != 0 up to i; each visited column gets +1
+//   supernodes        column j joins j-1 iff parent(j-1) = j, c_j = c_{j-1} - 1 and j has
+//                     one child; then cut into pieces of at most W columns
+//   row structure     rows(F) = own columns U rows of B below F U rows of F's children
+//                     below F, merged with a marker array
+//   levels            0 for supernodes without children, else 1 + max over children
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "chol_internal.h"
+
+namespace chol {
+
+namespace {
+
+// Tile class of a supernode's Schur update, given how many 64-tiles its level holds.
+int choose_tile_class(int64_t u, int64_t level_tiles64) {
+  if (u >= 64 && level_tiles64 >= 2 * 152) return kTile64;
+  if (u > 16) return kTile32;
+  return kTile16;
+}
+
+void push4(std::vector<int32_t>& v, int32_t a, int32_t b, int32_t c, int32_t d) {
+  v.push_back(a); v.push_back(b); v.push_back(c); v.push_back(d);
+}
+
+}  // namespace
+
+int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32_t* perm,
+            int width_cap, Sym* S) {
+  if (n < 0 || n >= (int64_t(1) << 31) || !colptr || (n > 0 && (!rowind || !perm)))
+    return CHOL_E_INVALID;
+  if (width_cap <= 0) width_cap = 64;
+  if (width_cap > kMaxWidth) return CHOL_E_INVALID;
+  S->n = n;
+  S->width_cap = width_cap;
+  if (colptr[0] != 0) return CHOL_E_INVALID;
+  for (int64_t j = 0; j < n; j++)
+    if (colptr[j + 1] < colptr[j]) return CHOL_E_INVALID;
+  const int64_t nnz = colptr[n];
+  S->nnz_a = nnz;
+
+  // ---- permutation -------------------------------------------------------------------
+  S->perm.assign(perm, perm + n);
+  S->iperm.assign(n, -1);
+  for (int64_t i = 0; i < n; i++) {
+    if (perm[i] < 0 || perm[i] >= n || S->iperm[perm[i]] != -1) return CHOL_E_INVALID;
+    S->iperm[perm[i]] = (int32_t)i;
+  }
+  const int32_t* ip = S->iperm.data();
+
+  // ---- validate A and build the rows of B's strict lower part (CSR) --------------------
+  std::vector<int64_t> rp(n + 1, 0);
+  for (int64_t j = 0; j < n; j++) {
+    for (int64_t p = colptr[j]; p < colptr[j + 1]; p++) {
+      int64_t i = rowind[p];
+      if (i < j || i >= n) return CHOL_E_INVALID;
+      if (p > colptr[j] && rowind[p - 1] >= i) return CHOL_E_INVALID;
+      int32_t a = ip[i], b = ip[j];
+      if (a != b) rp[std::max(a, b) + 1]++;
+    }
+  }
+  for (int64_t i = 0; i < n; i++) rp[i + 1] += rp[i];
+  std::vector<int32_t> rc(rp[n]);
+  {
+    std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t p = colptr[j]; p < colptr[j + 1]; p++) {
+        int32_t a = ip[rowind[p]], b = ip[j];
+        if (a != b) rc[fill[std::max(a, b)]++] = std::min(a, b);
+      }
+  }
+
+  // ---- elimination tree (Liu, path compression) ---------------------------------------
+  S->parent.assign(n, -1);
+  {
+    std::vector<int32_t> anc(n, -1);
+    for (int64_t i = 0; i < n; i++) {
+      for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+        int32_t r = rc[p];
+        while (anc[r] != -1 && anc[r] != i) {
+          int32_t t = anc[r];
+          anc[r] = (int32_t)i;
+          r = t;
+        }
+        if (anc[r] == -1) {
+          anc[r] = (int32_t)i;
+          S->parent[r] = (int32_t)i;
+        }
+      }
+    }
+  }
+
+  // ---- column counts by row subtrees ---------------------------------------------------
+  S->colcount.assign(n, 1);
+  {
+    std::vector<int32_t> mark(n, -1);
+    for (int64_t i = 0; i < n; i++) {
+      mark[i] = (int32_t)i;
+      for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+        for (int32_t j = rc[p]; mark[j] != i; j = S->parent[j]) {
+          S->colcount[j]++;
+          mark[j] = (int32_t)i;
+        }
+      }
+    }
+  }
+  S->nnz_l = 0;
+  S->flops = 0.0;
+  for (int64_t j = 0; j < n; j++) {
+    S->nnz_l += S->colcount[j];
+    S->flops += (double)S->colcount[j] * (double)S->colcount[j];
+  }
+
+  // ---- fundamental supernodes ----------------------------------------------------------
+  std::vector<int32_t> nchild(n, 0);
+  for (int64_t j = 0; j < n; j++)
+    if (S->parent[j] >= 0) nchild[S->parent[j]]++;
+  std::vector<int32_t> fstart;  // fundamental supernode starts
+  for (int64_t j = 0; j < n; j++) {
+    bool joins = j > 0 && S->parent[j - 1] == j && S->colcount[j] == S->colcount[j - 1] - 1 &&
+                 nchild[j] == 1;
+    if (!joins) fstart.push_back((int32_t)j);
+  }
+  const int64_t nf = (int64_t)fstart.size();
+  fstart.push_back((int32_t)n);
+  std::vector<int32_t> f_of(n);
+  for (int64_t f = 0; f < nf; f++)
+    for (int32_t j = fstart[f]; j < fstart[f + 1]; j++) f_of[j] = (int32_t)f;
+
+  // ---- row structures of the fundamental supernodes -----------------------------------
+  // B's lower entries by column: column c holds rows r > c with B_rc != 0 (transpose of rc)
+  std::vector<int64_t> cp(n + 1, 0);
+  for (int64_t p = 0; p < rp[n]; p++) cp[rc[p] + 1]++;
+  for (int64_t j = 0; j < n; j++) cp[j + 1] += cp[j];
+  std::vector<int32_t> cr(rp[n]);
+  {
+    std::vector<int64_t> fill(cp.begin(), cp.end() - 1);
+    for (int64_t i = 0; i < n; i++)
+      for (int64_t p = rp[i]; p < rp[i + 1]; p++) cr[fill[rc[p]]++] = (int32_t)i;
+  }
+  std::vector<int64_t> frp(nf + 1, 0);
+  std::vector<int32_t> frows;
+  frows.reserve((size_t)std::min<int64_t>(S->nnz_l, (int64_t)64 << 20));
+  std::vector<int32_t> fhead(nf, -1), fnext(nf, -1);
+  {
+    std::vector<int32_t> mark(n, -1);
+    std::vector<int32_t> tmp;
+    for (int64_t f = 0; f < nf; f++) {
+      const int32_t a = fstart[f], l = fstart[f + 1] - 1;
+      tmp.clear();
+      for (int32_t j = a; j <= l; j++) tmp.push_back(j);
+      for (int32_t j = a; j <= l; j++)
+        for (int64_t p = cp[j]; p < cp[j + 1]; p++) {
+          int32_t i = cr[p];
+          if (i > l && mark[i] != f) { mark[i] = (int32_t)f; tmp.push_back(i); }
+        }
+      for (int32_t c = fhead[f]; c != -1; c = fnext[c])
+        for (int64_t p = frp[c]; p < frp[c + 1]; p++) {
+          int32_t i = frows[p];
+          if (i > l && mark[i] != f) { mark[i] = (int32_t)f; tmp.push_back(i); }
+        }
+      std::sort(tmp.begin() + (l - a + 1), tmp.end());
+      if ((int64_t)tmp.size() != S->colcount[a]) return CHOL_E_INVALID;  // inconsistent
+      frows.insert(frows.end(), tmp.begin(), tmp.end());
+      frp[f + 1] = (int64_t)frows.size();
+      int32_t par = S->parent[l];
+      if (par >= 0) {
+        int32_t pf = f_of[par];
+        fnext[f] = fhead[pf];
+        fhead[pf] = (int32_t)f;
+      }
+    }
+  }
+
+  // ---- width cap: cut fundamental supernodes into chunks ------------------------------
+  S->sn_start.clear();
+  std::vector<int32_t> chunk_f;
+  for (int64_t f = 0; f < nf; f++)
+    for (int32_t j = fstart[f]; j < fstart[f + 1]; j += width_cap) {
+      S->sn_start.push_back(j);
+      chunk_f.push_back((int32_t)f);
+    }
+  S->ns = (int32_t)S->sn_start.size();
+  S->sn_start.push_back((int32_t)n);
+  const int32_t ns = S->ns;
+  S->col2sn.assign(n, 0);
+  S->sn_m.assign(ns, 0);
+  S->sn_rowptr.assign(ns + 1, 0);
+  S->sn_valptr.assign(ns + 1, 0);
+  S->rows.clear();
+  S->max_width = S->max_rows = 0;
+  for (int32_t s = 0; s < ns; s++) {
+    const int32_t a = S->sn_start[s], b = S->sn_start[s + 1];
+    const int32_t f = chunk_f[s];
+    const int64_t off = a - fstart[f];
+    for (int32_t j = a; j < b; j++) S->col2sn[j] = s;
+    const int64_t m = (frp[f + 1] - frp[f]) - off;
+    S->sn_m[s] = (int32_t)m;
+    S->rows.insert(S->rows.end(), frows.begin() + frp[f] + off, frows.begin() + frp[f + 1]);
+    S->sn_rowptr[s + 1] = (int64_t)S->rows.size();
+    S->sn_valptr[s + 1] = S->sn_valptr[s] + m * (int64_t)(b - a);
+    S->max_width = std::max<int64_t>(S->max_width, b - a);
+    S->max_rows = std::max<int64_t>(S->max_rows, m);
+  }
+  S->l_storage = S->sn_valptr[ns];
+  S->sn_parent.assign(ns, -1);
+  S->sn_level.assign(ns, 0);
+  for (int32_t s = 0; s < ns; s++) {
+    int32_t last = S->sn_start[s + 1] - 1;
+    if (S->parent[last] >= 0) S->sn_parent[s] = S->col2sn[S->parent[last]];
+  }
+  for (int32_t s = 0; s < ns; s++)
+    if (S->sn_parent[s] >= 0)
+      S->sn_level[S->sn_parent[s]] = std::max(S->sn_level[S->sn_parent[s]], S->sn_level[s] + 1);
+
+  // ---- where every entry of A lands in the panels -------------------------------------
+  S->amap.assign(nnz, 0);
+  for (int64_t j = 0; j < n; j++)
+    for (int64_t p = colptr[j]; p < colptr[j + 1]; p++) {
+      int32_t a = ip[rowind[p]], b = ip[j];
+      int32_t r = std::max(a, b), c = std::min(a, b);
+      int32_t t = S->col2sn[c];
+      const int32_t* rt = S->rows.data() + S->sn_rowptr[t];
+      const int32_t* e = std::lower_bound(rt, rt + S->sn_m[t], r);
+      if (e == rt + S->sn_m[t] || *e != r) return CHOL_E_INVALID;  // not in the structure
+      S->amap[p] = S->sn_valptr[t] + (int64_t)(c - S->sn_start[t]) * S->sn_m[t] + (e - rt);
+    }
+
+  // ---- level sets ---------------------------------------------------------------------
+  S->nlev = 0;
+  for (int32_t s = 0; s < ns; s++) S->nlev = std::max(S->nlev, S->sn_level[s] + 1);
+  S->lvl_ptr.assign(S->nlev + 1, 0);
+  for (int32_t s = 0; s < ns; s++) S->lvl_ptr[S->sn_level[s] + 1]++;
+  for (int32_t l = 0; l < S->nlev; l++) S->lvl_ptr[l + 1] += S->lvl_ptr[l];
+  S->lvl_sn.assign(ns, 0);
+  {
+    std::vector<int32_t> fill(S->lvl_ptr.begin(), S->lvl_ptr.end() - 1);
+    for (int32_t s = 0; s < ns; s++) S->lvl_sn[fill[S->sn_level[s]]++] = s;
+  }
+
+  // ---- per-level task lists -----------------------------------------------------------
+  for (int k = 0; k < kNumTaskKinds; k++) {
+    S->tasks[k].clear();
+    S->task_off[k].assign(S->nlev + 1, 0);
+    S->lvl_flops[k].assign(S->nlev, 0.0);
+  }
+  S->lvl_panel_bytes.assign(S->nlev, 0.0);
+  S->sn_ustage.assign(ns, -1);
+  S->asm_src.clear();
+  S->stage_elems = 0;
+  for (int32_t l = 0; l < S->nlev; l++) {
+    int64_t tiles64 = 0, stage = 0;
+    for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
+      int32_t s = S->lvl_sn[q];
+      int64_t u = S->sn_m[s] - (S->sn_start[s + 1] - S->sn_start[s]);
+      int64_t nt = (u + 63) / 64;
+      tiles64 += nt * (nt + 1) / 2;
+    }
+    for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
+      const int32_t s = S->lvl_sn[q];
+      const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
+      const int32_t u = S->sn_m[s] - w;
+      const int32_t first_bwd = (int32_t)(S->tasks[kTaskBwd].size() / 4);
+      const int32_t nbwd = (std::max(u, 1) + kSolveRows - 1) / kSolveRows;
+      push4(S->tasks[kTaskPotrf], s, first_bwd, nbwd, 0);
+      const double dn = w, du = u;
+      S->lvl_flops[kTaskPotrf][l] += dn * (dn + 1) * (2 * dn + 1) / 6.0;
+      S->lvl_flops[kTaskTrsm][l] += du * dn * dn;
+      S->lvl_panel_bytes[l] += 8.0 * (dn + du) * dn;
+      for (int32_t r0 = 0; r0 < u; r0 += kTrsmRows) push4(S->tasks[kTaskTrsm], s, r0, 0, 0);
+      for (int32_t r0 = 0; r0 < std::max(u, 1); r0 += kSolveRows) {
+        push4(S->tasks[kTaskFwd], s, r0, 0, 0);
+        push4(S->tasks[kTaskBwd], s, r0, 0, 0);
+      }
+      if (u > 0) {
+        int cls = choose_tile_class(u, tiles64);
+        int T = tile_of_class(cls);
+        S->lvl_flops[kTaskSchur64 + cls][l] += du * (du + 1) * dn;
+        for (int32_t i0 = 0; i0 < u; i0 += T)
+          for (int32_t k0 = 0; k0 <= i0; k0 += T)
+            push4(S->tasks[kTaskSchur64 + cls], s, i0, k0, 0);
+        S->sn_ustage[s] = stage;
+        stage += (int64_t)u * u;
+      }
+    }
+    S->stage_elems = std::max(S->stage_elems, stage);
+    // owner assembly groups: for every target supernode t hit by this level, per block
+    // of 32 target columns, the sources s of this level in ascending order
+    {
+      struct Src { int32_t t, cb, s, kb, ke; };
+      std::vector<Src> srcs;
+      for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
+        const int32_t s = S->lvl_sn[q];
+        const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
+        const int32_t m = S->sn_m[s];
+        const int32_t* rs = S->rows.data() + S->sn_rowptr[s];
+        int32_t k = w;
+        while (k < m) {
+          const int32_t t = S->col2sn[rs[k]];
+          const int32_t t0 = S->sn_start[t];
+          const int32_t cb = (rs[k] - t0) / 32;
+          int32_t ke = k;
+          while (ke < m && S->col2sn[rs[ke]] == t && (rs[ke] - t0) / 32 == cb) ke++;
+          srcs.push_back({t, cb, s, k - w, ke - w});
+          k = ke;
+        }
+      }
+      std::stable_sort(srcs.begin(), srcs.end(), [](const Src& x, const Src& y) {
+        if (x.t != y.t) return x.t < y.t;
+        if (x.cb != y.cb) return x.cb < y.cb;
+        return x.s < y.s;
+      });
+      // kTaskAsm entries are groups {t, cb, first, end}: target supernode t, block cb of
+      // 32 of its columns, and the range [first, end) of asm_src entries {s, kb, ke, -}
+      // that update it, s ascending (the fixed summation order)
+      size_t g = 0;
+      while (g < srcs.size()) {
+        size_t h = g;
+        while (h < srcs.size() && srcs[h].t == srcs[g].t && srcs[h].cb == srcs[g].cb) h++;
+        const int32_t first = (int32_t)(S->asm_src.size() / 4);
+        for (size_t q = g; q < h; q++) push4(S->asm_src, srcs[q].s, srcs[q].kb, srcs[q].ke, 0);
+        push4(S->tasks[kTaskAsm], srcs[g].t, srcs[g].cb, first, first + (int32_t)(h - g));
+        g = h;
+      }
+    }
+    for (int k = 0; k < kNumTaskKinds; k++)
+      S->task_off[k][l + 1] = (int64_t)S->tasks[k].size() / 4;
+  }
+  return CHOL_OK;
+}
+
+}  // namespace chol

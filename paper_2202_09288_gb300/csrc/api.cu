@@ -1,0 +1,681 @@
+// api.cu -- the C ABI (include/chol.h): contexts, device memory, upload of the symbolic
+// analysis, and the per-level launch sequence of the factorization and the solves.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "chol_internal.h"
+#include "kernels.h"
+
+using chol::MatDev;
+using chol::SnDev;
+using chol::Sym;
+
+// Kernel kinds of the tracing counters.
+enum ProfKindId {
+  kProfAssemble, kProfPotrf, kProfTrsm, kProfSchur64, kProfSchur32, kProfSchur16,
+  kProfAsmOwner, kProfFwd, kProfBwd, kProfPerm, kNumProf
+};
+static const char* kProfNames[kNumProf] = {
+    "assemble", "potrf_f64", "trsm_f64", "schur64_f64", "schur32_f64", "schur16_f64",
+    "assemble_owner", "solve_fwd", "solve_bwd", "solve_perm"};
+
+struct ProfPending {
+  int kind;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+
+struct chol_ctx {
+  chol_opts opts;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaMemPool_t pool = nullptr;
+  size_t held = 0;
+  bool attrs_set = false;
+  // tracing
+  bool prof_on = false;
+  chol_prof_entry prof[kNumProf];
+  std::vector<ProfPending> pending;
+  std::vector<cudaEvent_t> spare_events;
+  cudaEvent_t open_event = nullptr;
+};
+
+struct DevSym {
+  int device = -1;
+  int32_t* rows = nullptr;
+  int32_t* col2sn = nullptr;
+  int64_t* amap = nullptr;
+  int32_t* perm = nullptr;
+  int4* tasks[chol::kNumTaskKinds] = {};
+  int4* asm_src = nullptr;
+  size_t bytes = 0;
+};
+
+struct chol_sym {
+  Sym S;
+  DevSym dev;
+  chol_ctx* ctx = nullptr;  // context that holds dev (set at upload)
+  int64_t max_bwd_per_level = 0;
+};
+
+struct chol_num {
+  chol_ctx* ctx = nullptr;
+  const chol_sym* sym = nullptr;
+  int precision = CHOL_FP64;
+  int assembly = CHOL_ASSEMBLY_ATOMIC;
+  void* L = nullptr;           // panels
+  SnDev* d_sn = nullptr;
+  MatDev* d_mat = nullptr;
+  unsigned long long* d_err = nullptr;
+  double* d_vals = nullptr;    // staging of host values
+  double* d_stage = nullptr;   // owner assembly staging
+  // solve workspace, grown on demand
+  int64_t ws_nrhs = 0;
+  double* d_y = nullptr;
+  double* d_w = nullptr;
+  double* d_part = nullptr;
+  double* d_bx = nullptr;      // host-call staging of B / X
+};
+
+namespace {
+
+cudaEvent_t prof_event(chol_ctx* c) {
+  cudaEvent_t e = nullptr;
+  if (!c->spare_events.empty()) {
+    e = c->spare_events.back();
+    c->spare_events.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    e = nullptr;
+  }
+  return e;
+}
+
+// Brackets one launch of kind k (the launch count is always kept).
+void prof_begin(chol_ctx* c) {
+  if (!c->prof_on) return;
+  c->open_event = prof_event(c);
+  if (c->open_event) cudaEventRecord(c->open_event, c->stream);
+}
+
+void prof_end(chol_ctx* c, int k, double flops, double bytes) {
+  c->prof[k].launches++;
+  if (!c->prof_on || !c->open_event) return;
+  cudaEvent_t b = prof_event(c);
+  if (!b) return;
+  cudaEventRecord(b, c->stream);
+  c->pending.push_back({k, c->open_event, b, flops, bytes});
+  c->open_event = nullptr;
+}
+
+void prof_fold(chol_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->prof[p.kind].ms += ms;
+      c->prof[p.kind].timed++;
+      c->prof[p.kind].flops += p.flops;
+      c->prof[p.kind].bytes += p.bytes;
+    } else {
+      cudaGetLastError();
+    }
+    c->spare_events.push_back(p.a);
+    c->spare_events.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+void prof_reset(chol_ctx* c) {
+  for (int k = 0; k < kNumProf; k++) {
+    memset(&c->prof[k], 0, sizeof(chol_prof_entry));
+    snprintf(c->prof[k].name, sizeof(c->prof[k].name), "%s", kProfNames[k]);
+  }
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    if ((call) != cudaSuccess) {                   \
+      cudaGetLastError();                          \
+      return CHOL_E_CUDA;                          \
+    }                                              \
+  } while (0)
+
+int dev_alloc(chol_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (c->opts.hbm_budget && c->held + bytes > c->opts.hbm_budget) return CHOL_E_OOM;
+  if (cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return CHOL_E_OOM;
+  }
+  c->held += bytes;
+  return CHOL_OK;
+}
+
+void dev_free(chol_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFreeAsync(p, c->stream);
+  if (bytes == 0) bytes = 16;
+  c->held -= std::min(c->held, bytes);
+}
+
+template <typename T>
+int upload(chol_ctx* c, T** dst, const std::vector<T>& v, size_t* acc) {
+  size_t bytes = v.size() * sizeof(T);
+  int rc = dev_alloc(c, (void**)dst, bytes);
+  if (rc) return rc;
+  *acc += bytes ? bytes : 16;
+  if (bytes) CK(cudaMemcpyAsync(*dst, v.data(), bytes, cudaMemcpyHostToDevice, c->stream));
+  return CHOL_OK;
+}
+
+void free_devsym(chol_sym* s) {
+  if (!s->ctx) return;
+  chol_ctx* c = s->ctx;
+  DevSym& d = s->dev;
+  const Sym& S = s->S;
+  dev_free(c, d.rows, S.rows.size() * 4);
+  dev_free(c, d.col2sn, S.col2sn.size() * 4);
+  dev_free(c, d.amap, S.amap.size() * 8);
+  dev_free(c, d.perm, S.perm.size() * 4);
+  for (int k = 0; k < chol::kNumTaskKinds; k++) dev_free(c, d.tasks[k], S.tasks[k].size() * 4);
+  dev_free(c, d.asm_src, S.asm_src.size() * 4);
+  d = DevSym();
+  s->ctx = nullptr;
+}
+
+int ensure_uploaded(chol_ctx* c, chol_sym* s) {
+  if (s->ctx == c) return CHOL_OK;
+  if (s->ctx) return CHOL_E_INVALID;  // bound to another context
+  const Sym& S = s->S;
+  DevSym& d = s->dev;
+  size_t acc = 0;
+  int rc;
+  s->ctx = c;
+  if ((rc = upload(c, &d.rows, S.rows, &acc)) || (rc = upload(c, &d.col2sn, S.col2sn, &acc)) ||
+      (rc = upload(c, &d.amap, S.amap, &acc)) || (rc = upload(c, &d.perm, S.perm, &acc))) {
+    free_devsym(s);
+    return rc;
+  }
+  for (int k = 0; k < chol::kNumTaskKinds; k++)
+    if ((rc = upload(c, reinterpret_cast<int32_t**>(&d.tasks[k]), S.tasks[k], &acc))) {
+      free_devsym(s);
+      return rc;
+    }
+  if ((rc = upload(c, reinterpret_cast<int32_t**>(&d.asm_src), S.asm_src, &acc))) {
+    free_devsym(s);
+    return rc;
+  }
+  d.bytes = acc;
+  d.device = c->opts.device;
+  int64_t mb = 0;
+  for (int32_t l = 0; l < S.nlev; l++)
+    mb = std::max(mb, S.task_off[chol::kTaskBwd][l + 1] - S.task_off[chol::kTaskBwd][l]);
+  s->max_bwd_per_level = mb;
+  return CHOL_OK;
+}
+
+int ensure_attrs(chol_ctx* c) {
+  if (c->attrs_set) return CHOL_OK;
+  int rc = chol::set_factor_kernel_attrs(chol::kMaxWidth);
+  if (rc) return rc;
+  rc = chol::set_solve_kernel_attrs(chol::kMaxWidth, 32);
+  if (rc) return rc;
+  c->attrs_set = true;
+  return CHOL_OK;
+}
+
+const int4* task_ptr(const chol_sym* s, int kind, int32_t level, int* count) {
+  const Sym& S = s->S;
+  int64_t a = S.task_off[kind][level], b = S.task_off[kind][level + 1];
+  *count = (int)(b - a);
+  return s->dev.tasks[kind] + a;
+}
+
+int enqueue_factor(chol_num* f, const double* vals_dev) {
+  chol_ctx* c = f->ctx;
+  const chol_sym* sym = f->sym;
+  const Sym& S = sym->S;
+  cudaStream_t st = c->stream;
+  const size_t esz = sizeof(double);
+  CK(cudaMemsetAsync(f->d_err, 0, 2 * sizeof(unsigned long long), st));
+  prof_begin(c);
+  CK(cudaMemsetAsync(f->L, 0, (size_t)S.l_storage * esz, st));
+  chol::launch_assemble(vals_dev, sym->dev.amap, S.nnz_a, f->L, false, st);
+  prof_end(c, kProfAssemble, 0.0, (double)S.l_storage * esz + 16.0 * S.nnz_a + 8.0 * S.nnz_a);
+  const bool owner = f->assembly == CHOL_ASSEMBLY_OWNER;
+  for (int32_t l = 0; l < S.nlev; l++) {
+    int cnt;
+    const int4* t = task_ptr(sym, chol::kTaskPotrf, l, &cnt);
+    prof_begin(c);
+    chol::launch_potrf(t, cnt, f->d_sn, f->d_mat, (int)S.max_width, st);
+    prof_end(c, kProfPotrf, S.lvl_flops[chol::kTaskPotrf][l], 0.0);
+    t = task_ptr(sym, chol::kTaskTrsm, l, &cnt);
+    if (cnt > 0) {
+      prof_begin(c);
+      chol::launch_trsm(t, cnt, f->d_sn, (int)S.max_width, st);
+      prof_end(c, kProfTrsm, S.lvl_flops[chol::kTaskTrsm][l], 0.0);
+    }
+    for (int cls = 0; cls < chol::kNumTileClasses; cls++) {
+      t = task_ptr(sym, chol::kTaskSchur64 + cls, l, &cnt);
+      if (cnt <= 0) continue;
+      prof_begin(c);
+      chol::launch_schur(cls, t, cnt, f->d_sn, f->d_mat, f->d_stage, owner, st);
+      prof_end(c, kProfSchur64 + cls, S.lvl_flops[chol::kTaskSchur64 + cls][l], 0.0);
+    }
+    if (owner) {
+      t = task_ptr(sym, chol::kTaskAsm, l, &cnt);
+      if (cnt > 0) {
+        prof_begin(c);
+        chol::launch_assemble_owner(t, cnt, sym->dev.asm_src, f->d_sn, f->d_mat, f->d_stage, st);
+        prof_end(c, kProfAsmOwner, 0.0, 0.0);
+      }
+    }
+  }
+  CK(cudaGetLastError());
+  return CHOL_OK;
+}
+
+int ensure_solve_ws(chol_num* f, int64_t nrhs) {
+  if (f->ws_nrhs >= nrhs) return CHOL_OK;
+  chol_ctx* c = f->ctx;
+  const Sym& S = f->sym->S;
+  const int64_t n = S.n;
+  int64_t old = f->ws_nrhs;
+  dev_free(c, f->d_y, (size_t)n * old * 8);
+  dev_free(c, f->d_w, (size_t)n * old * 8);
+  dev_free(c, f->d_bx, (size_t)n * old * 8);
+  dev_free(c, f->d_part, (size_t)f->sym->max_bwd_per_level * S.width_cap * old * 8);
+  f->d_y = f->d_w = f->d_bx = f->d_part = nullptr;
+  f->ws_nrhs = 0;
+  int rc;
+  if ((rc = dev_alloc(c, (void**)&f->d_y, (size_t)n * nrhs * 8)) ||
+      (rc = dev_alloc(c, (void**)&f->d_w, (size_t)n * nrhs * 8)) ||
+      (rc = dev_alloc(c, (void**)&f->d_bx, (size_t)n * nrhs * 8)) ||
+      (rc = dev_alloc(c, (void**)&f->d_part,
+                      (size_t)f->sym->max_bwd_per_level * S.width_cap * nrhs * 8)))
+    return rc;
+  f->ws_nrhs = nrhs;
+  return CHOL_OK;
+}
+
+// Device-pointer solve of nrhs <= 32 columns.
+int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx) {
+  chol_ctx* c = f->ctx;
+  const chol_sym* sym = f->sym;
+  const Sym& S = sym->S;
+  cudaStream_t st = c->stream;
+  const int64_t n = S.n;
+  const int W = S.width_cap;
+  const double vec = 8.0 * n * nrhs;
+  prof_begin(c);
+  chol::launch_gather_perm(B, ldb, sym->dev.perm, n, nrhs, f->d_y, st);
+  prof_end(c, kProfPerm, 0.0, 2 * vec + 4.0 * n);
+  for (int32_t l = 0; l < S.nlev; l++) {
+    int cnt;
+    const int4* t = task_ptr(sym, chol::kTaskFwd, l, &cnt);
+    prof_begin(c);
+    chol::launch_fwd(t, cnt, f->d_sn, n, nrhs, W, f->d_y, f->d_w, st);
+    prof_end(c, kProfFwd, 0.0, S.lvl_panel_bytes[l]);
+  }
+  for (int32_t l = S.nlev - 1; l >= 0; l--) {
+    int nb, nd;
+    const int4* tb = task_ptr(sym, chol::kTaskBwd, l, &nb);
+    const int4* td = task_ptr(sym, chol::kTaskPotrf, l, &nd);
+    prof_begin(c);
+    chol::launch_bwd(tb, nb, S.task_off[chol::kTaskBwd][l], td, nd, f->d_sn, n, nrhs, W,
+                     f->d_w, f->d_part, st);
+    prof_end(c, kProfBwd, 0.0, S.lvl_panel_bytes[l]);
+  }
+  prof_begin(c);
+  chol::launch_scatter_perm(f->d_w, sym->dev.perm, n, nrhs, X, ldx, st);
+  prof_end(c, kProfPerm, 0.0, 2 * vec + 4.0 * n);
+  CK(cudaGetLastError());
+  return CHOL_OK;
+}
+
+void free_num_buffers(chol_num* f) {
+  chol_ctx* c = f->ctx;
+  if (!c) return;
+  const Sym& S = f->sym->S;
+  const size_t esz = f->precision == CHOL_MIXED ? 4 : 8;
+  dev_free(c, f->L, (size_t)S.l_storage * esz);
+  dev_free(c, f->d_sn, (size_t)S.ns * sizeof(SnDev));
+  dev_free(c, f->d_mat, sizeof(MatDev));
+  dev_free(c, f->d_err, 16);
+  dev_free(c, f->d_vals, (size_t)S.nnz_a * 8);
+  dev_free(c, f->d_stage, (size_t)S.stage_elems * 8);
+  dev_free(c, f->d_y, (size_t)S.n * f->ws_nrhs * 8);
+  dev_free(c, f->d_w, (size_t)S.n * f->ws_nrhs * 8);
+  dev_free(c, f->d_bx, (size_t)S.n * f->ws_nrhs * 8);
+  dev_free(c, f->d_part, (size_t)f->sym->max_bwd_per_level * S.width_cap * f->ws_nrhs * 8);
+}
+
+}  // namespace
+
+extern "C" {
+
+int chol_version(void) { return 100; }
+
+const char* chol_strerror(int s) {
+  switch (s) {
+    case CHOL_OK: return "ok";
+    case CHOL_PENDING: return "pending";
+    case CHOL_E_INVALID: return "invalid argument or malformed matrix";
+    case CHOL_E_NOT_SPD: return "matrix is not positive definite";
+    case CHOL_E_OOM: return "out of device memory or over the HBM budget";
+    case CHOL_E_CUDA: return "CUDA runtime error";
+    case CHOL_E_TIMEOUT: return "device-side wait timed out";
+    case CHOL_E_NODEVICE: return "no usable CUDA device";
+    case CHOL_E_STALL: return "iterative refinement did not converge";
+    default: return "unknown status";
+  }
+}
+
+void chol_default_opts(chol_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->width_cap = 64;
+  o->assembly = CHOL_ASSEMBLY_ATOMIC;
+  o->pivot_tau = 1e-5;
+}
+
+int chol_create(const chol_opts* opts, chol_ctx** out) {
+  if (!out) return CHOL_E_INVALID;
+  *out = nullptr;
+  chol_ctx* c = new (std::nothrow) chol_ctx();
+  if (!c) return CHOL_E_OOM;
+  if (opts) c->opts = *opts; else chol_default_opts(&c->opts);
+  if (c->opts.width_cap <= 0) c->opts.width_cap = 64;
+  if (c->opts.width_cap > chol::kMaxWidth ||
+      (c->opts.assembly != CHOL_ASSEMBLY_ATOMIC && c->opts.assembly != CHOL_ASSEMBLY_OWNER)) {
+    delete c;
+    return CHOL_E_INVALID;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || c->opts.device < 0 || c->opts.device >= ndev) {
+    cudaGetLastError();
+    delete c;
+    return CHOL_E_NODEVICE;
+  }
+  if (cudaSetDevice(c->opts.device) != cudaSuccess) { delete c; return CHOL_E_NODEVICE; }
+  if (c->opts.stream) {
+    c->stream = (cudaStream_t)c->opts.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return CHOL_E_CUDA;
+    }
+    c->own_stream = true;
+  }
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = c->opts.device;
+  if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return CHOL_E_CUDA;
+  }
+  uint64_t thr = UINT64_MAX;
+  cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  prof_reset(c);
+  *out = c;
+  return CHOL_OK;
+}
+
+void chol_destroy(chol_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->opts.device);
+  cudaStreamSynchronize(c->stream);
+  prof_fold(c);
+  for (cudaEvent_t e : c->spare_events) cudaEventDestroy(e);
+  if (c->open_event) cudaEventDestroy(c->open_event);
+  cudaMemPoolDestroy(c->pool);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int chol_analyze(const chol_opts* opts, int64_t n, const int64_t* colptr,
+                 const int32_t* rowind, const int32_t* perm, chol_sym** out) {
+  if (!out) return CHOL_E_INVALID;
+  *out = nullptr;
+  chol_sym* s = new (std::nothrow) chol_sym();
+  if (!s) return CHOL_E_OOM;
+  int rc;
+  try {
+    rc = chol::analyze(n, colptr, rowind, perm, opts ? opts->width_cap : 64, &s->S);
+  } catch (const std::bad_alloc&) {
+    rc = CHOL_E_OOM;
+  } catch (...) {
+    rc = CHOL_E_INVALID;
+  }
+  if (rc) { delete s; return rc; }
+  *out = s;
+  return CHOL_OK;
+}
+
+int chol_sym_info(const chol_sym* s, chol_sym_stats* st) {
+  if (!s || !st) return CHOL_E_INVALID;
+  const Sym& S = s->S;
+  st->n = S.n;
+  st->nnz_a = S.nnz_a;
+  st->nnz_l = S.nnz_l;
+  st->l_storage = S.l_storage;
+  st->nsuper = S.ns;
+  st->nlevels = S.nlev;
+  st->flops = S.flops;
+  st->max_width = S.max_width;
+  st->max_rows = S.max_rows;
+  return CHOL_OK;
+}
+
+int chol_sym_export(const chol_sym* s, int32_t* parent, int64_t* colcount, int32_t* sn_start,
+                    int32_t* sn_level) {
+  if (!s) return CHOL_E_INVALID;
+  const Sym& S = s->S;
+  if (parent) std::copy(S.parent.begin(), S.parent.end(), parent);
+  if (colcount) std::copy(S.colcount.begin(), S.colcount.end(), colcount);
+  if (sn_start) std::copy(S.sn_start.begin(), S.sn_start.end(), sn_start);
+  if (sn_level) std::copy(S.sn_level.begin(), S.sn_level.end(), sn_level);
+  return CHOL_OK;
+}
+
+void chol_free_sym(chol_sym* s) {
+  if (!s) return;
+  if (s->ctx) {
+    cudaSetDevice(s->ctx->opts.device);
+    free_devsym(s);
+  }
+  delete s;
+}
+
+int chol_factorize(chol_ctx* c, const chol_sym* sym_c, const double* vals, int where,
+                   int precision, chol_num** out) {
+  if (!c || !sym_c || !out || (!vals && sym_c->S.nnz_a > 0)) return CHOL_E_INVALID;
+  if (where != CHOL_HOST && where != CHOL_DEVICE) return CHOL_E_INVALID;
+  if (precision != CHOL_FP64) return CHOL_E_INVALID;
+  *out = nullptr;
+  chol_sym* sym = const_cast<chol_sym*>(sym_c);
+  if (cudaSetDevice(c->opts.device) != cudaSuccess) return CHOL_E_NODEVICE;
+  int rc = ensure_uploaded(c, sym);
+  if (rc) return rc;
+  if ((rc = ensure_attrs(c))) return rc;
+  const Sym& S = sym->S;
+  chol_num* f = new (std::nothrow) chol_num();
+  if (!f) return CHOL_E_OOM;
+  f->ctx = c;
+  f->sym = sym;
+  f->precision = precision;
+  f->assembly = c->opts.assembly;
+  if ((rc = dev_alloc(c, &f->L, (size_t)S.l_storage * 8)) ||
+      (rc = dev_alloc(c, (void**)&f->d_sn, (size_t)S.ns * sizeof(SnDev))) ||
+      (rc = dev_alloc(c, (void**)&f->d_mat, sizeof(MatDev))) ||
+      (rc = dev_alloc(c, (void**)&f->d_err, 16)) ||
+      (rc = dev_alloc(c, (void**)&f->d_vals, (size_t)S.nnz_a * 8)) ||
+      (f->assembly == CHOL_ASSEMBLY_OWNER &&
+       (rc = dev_alloc(c, (void**)&f->d_stage, (size_t)S.stage_elems * 8)))) {
+    free_num_buffers(f);
+    delete f;
+    return rc;
+  }
+  std::vector<SnDev> sn(S.ns);
+  for (int32_t s = 0; s < S.ns; s++) {
+    sn[s].L = (double*)f->L + S.sn_valptr[s];
+    sn[s].rows = sym->dev.rows + S.sn_rowptr[s];
+    sn[s].n = S.sn_start[s + 1] - S.sn_start[s];
+    sn[s].m = S.sn_m[s];
+    sn[s].col0 = S.sn_start[s];
+    sn[s].mat = 0;
+    sn[s].ustage = S.sn_ustage[s];
+  }
+  MatDev md;
+  md.col2sn = sym->dev.col2sn;
+  md.sn_base = 0;
+  md.pad0 = 0;
+  md.err = f->d_err;
+  if (cudaMemcpyAsync(f->d_sn, sn.data(), sn.size() * sizeof(SnDev), cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(f->d_mat, &md, sizeof(md), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    free_num_buffers(f);
+    delete f;
+    return CHOL_E_CUDA;
+  }
+  *out = f;
+  return chol_refactorize(c, f, vals, where);
+}
+
+int chol_refactorize(chol_ctx* c, chol_num* f, const double* vals, int where) {
+  if (!c || !f || f->ctx != c) return CHOL_E_INVALID;
+  if (where != CHOL_HOST && where != CHOL_DEVICE) return CHOL_E_INVALID;
+  const Sym& S = f->sym->S;
+  if (!vals && S.nnz_a > 0) return CHOL_E_INVALID;
+  if (cudaSetDevice(c->opts.device) != cudaSuccess) return CHOL_E_NODEVICE;
+  const double* v = vals;
+  if (where == CHOL_HOST) {
+    CK(cudaMemcpyAsync(f->d_vals, vals, (size_t)S.nnz_a * 8, cudaMemcpyHostToDevice, c->stream));
+    v = f->d_vals;
+  }
+  return enqueue_factor(f, v);
+}
+
+int chol_factor_status(chol_ctx* c, const chol_num* f, int64_t* bad_col) {
+  if (!c || !f || f->ctx != c) return CHOL_E_INVALID;
+  unsigned long long ee[2] = {0, 0};
+  CK(cudaMemcpyAsync(ee, f->d_err, 16, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  if (ee[1]) return CHOL_E_INVALID;  // internal relative-map inconsistency
+  const unsigned long long e = ee[0];
+  if (e) {
+    if (bad_col) *bad_col = (int64_t)(e - 1);
+    return CHOL_E_NOT_SPD;
+  }
+  if (bad_col) *bad_col = -1;
+  return CHOL_OK;
+}
+
+int chol_factor_export(chol_ctx* c, const chol_num* f, int64_t* Lp, int32_t* Li, double* Lx) {
+  if (!c || !f || f->ctx != c) return CHOL_E_INVALID;
+  const Sym& S = f->sym->S;
+  std::vector<double> panels;
+  if (Lx) {
+    try {
+      panels.resize((size_t)S.l_storage);
+    } catch (...) {
+      return CHOL_E_OOM;
+    }
+    CK(cudaMemcpyAsync(panels.data(), f->L, (size_t)S.l_storage * 8, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  int64_t pos = 0;
+  if (Lp) Lp[0] = 0;
+  for (int32_t s = 0; s < S.ns; s++) {
+    const int32_t n = S.sn_start[s + 1] - S.sn_start[s], m = S.sn_m[s];
+    const int32_t* rows = S.rows.data() + S.sn_rowptr[s];
+    for (int32_t jj = 0; jj < n; jj++) {
+      for (int32_t r = jj; r < m; r++) {
+        if (Li) Li[pos] = rows[r];
+        if (Lx) Lx[pos] = panels[S.sn_valptr[s] + (int64_t)jj * m + r];
+        pos++;
+      }
+      if (Lp) Lp[S.sn_start[s] + jj + 1] = pos;
+    }
+  }
+  return CHOL_OK;
+}
+
+void chol_free_num(chol_num* f) {
+  if (!f) return;
+  if (f->ctx) {
+    cudaSetDevice(f->ctx->opts.device);
+    free_num_buffers(f);
+  }
+  delete f;
+}
+
+int chol_solve(chol_ctx* c, const chol_num* fc, int64_t nrhs, const double* B, int64_t ldb,
+               double* X, int64_t ldx, int where) {
+  chol_num* f = const_cast<chol_num*>(fc);
+  if (!c || !f || f->ctx != c || nrhs < 0 || !B || !X) return CHOL_E_INVALID;
+  const int64_t n = f->sym->S.n;
+  if (ldb < n || ldx < n || (where != CHOL_HOST && where != CHOL_DEVICE)) return CHOL_E_INVALID;
+  if (B == X && ldb != ldx) return CHOL_E_INVALID;
+  if (nrhs == 0 || n == 0) return CHOL_OK;
+  if (cudaSetDevice(c->opts.device) != cudaSuccess) return CHOL_E_NODEVICE;
+  const int64_t chunk = std::min<int64_t>(nrhs, 32);
+  int rc = ensure_solve_ws(f, chunk);
+  if (rc) return rc;
+  for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
+    const int k = (int)std::min<int64_t>(chunk, nrhs - c0);
+    if (where == CHOL_HOST) {
+      CK(cudaMemcpy2DAsync(f->d_bx, n * 8, B + c0 * ldb, ldb * 8, n * 8, k,
+                           cudaMemcpyHostToDevice, c->stream));
+      if ((rc = enqueue_solve(f, k, f->d_bx, n, f->d_bx, n))) return rc;
+      CK(cudaMemcpy2DAsync(X + c0 * ldx, ldx * 8, f->d_bx, n * 8, n * 8, k,
+                           cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      if ((rc = enqueue_solve(f, k, B + c0 * ldb, ldb, X + c0 * ldx, ldx))) return rc;
+    }
+  }
+  if (where == CHOL_HOST) CK(cudaStreamSynchronize(c->stream));
+  return CHOL_OK;
+}
+
+int chol_profile_enable(chol_ctx* c, int on) {
+  if (!c) return CHOL_E_INVALID;
+  c->prof_on = on != 0;
+  return CHOL_OK;
+}
+
+int chol_profile_read(chol_ctx* c, chol_prof_entry* out, int max, int* count) {
+  if (!c || (!out && max > 0)) return CHOL_E_INVALID;
+  cudaSetDevice(c->opts.device);
+  CK(cudaStreamSynchronize(c->stream));
+  prof_fold(c);
+  for (int k = 0; k < kNumProf && k < max; k++) out[k] = c->prof[k];
+  if (count) *count = kNumProf;
+  return CHOL_OK;
+}
+
+int chol_profile_reset(chol_ctx* c) {
+  if (!c) return CHOL_E_INVALID;
+  cudaSetDevice(c->opts.device);
+  CK(cudaStreamSynchronize(c->stream));
+  prof_fold(c);
+  prof_reset(c);
+  return CHOL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// chol_internal.h -- data structures shared by the host analysis, the runtime and the
+// device kernels of the supernodal Cholesky library.  Not part of the public ABI.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/chol.h"
+
+namespace chol {
+
+// Row blocks and tile shapes of the device task lists.
+constexpr int kTrsmRows = 32;    // off-diagonal rows per TRSM task (one warp, one row each)
+constexpr int kSolveRows = 128;  // off-diagonal rows per solve task
+constexpr int kMaxWidth = 128;   // hard limit on the width cap W (diagonal block in smem)
+
+// Schur tile classes: the update U = L21 L21^T of a supernode is cut into lower-triangular
+// T x T tiles, T in {64, 32, 16}.
+enum SchurClass { kTile64 = 0, kTile32 = 1, kTile16 = 2, kNumTileClasses = 3 };
+inline int tile_of_class(int c) { return c == kTile64 ? 64 : (c == kTile32 ? 32 : 16); }
+
+// Task kinds of the per-level schedule.  Every task is an int4 {s, a, b, c}.
+enum TaskKind {
+  kTaskPotrf = 0,   // {s, first_bwd, nbwd, -}: diagonal block of s; its backward tasks
+  kTaskTrsm = 1,    // {s, r0, -, -}: L21 rows r0 .. r0+kTrsmRows of s
+  kTaskSchur64 = 2, // {s, i0, k0, -}: tile of U_s (rows i0.., cols k0.., offsets into L21)
+  kTaskSchur32 = 3,
+  kTaskSchur16 = 4,
+  kTaskFwd = 5,     // {s, r0, -, -}: forward-solve block
+  kTaskBwd = 6,     // {s, r0, -, -}: backward-solve partial block
+  kTaskAsm = 7,     // {t, cb, first, end}: owner assembly group (see Sym::asm_src)
+  kNumTaskKinds = 8
+};
+
+// Device descriptor of one supernode (absolute device pointers: descriptors of several
+// matrices can be concatenated into one batch).
+struct alignas(16) SnDev {
+  void* L;              // panel, m x n column-major, ld = m (double or float)
+  const int32_t* rows;  // m row indices (matrix numbering), ascending; first n = own columns
+  int32_t n, m;         // columns, rows
+  int32_t col0;         // first column
+  int32_t mat;          // index into the MatDev array
+  int64_t ustage;       // owner assembly: offset of U_s in the level staging buffer (-1 none)
+};
+
+struct alignas(16) MatDev {
+  const int32_t* col2sn;          // column -> supernode index (matrix-local)
+  int32_t sn_base;                // index of supernode 0 of this matrix in the SnDev array
+  int32_t pad0;
+  unsigned long long* err;        // err[0]: first failing column + 1 (0 = none), atomicMin;
+                                  // err[1]: relative-map misses (internal check, 0 expected)
+};
+
+// Host-side symbolic analysis result.
+struct Sym {
+  int64_t n = 0, nnz_a = 0;
+  int width_cap = 64;
+  std::vector<int32_t> perm, iperm;
+  std::vector<int32_t> parent;
+  std::vector<int64_t> colcount;
+  int32_t ns = 0;
+  std::vector<int32_t> sn_start;   // ns + 1
+  std::vector<int32_t> sn_m;       // rows of each supernode
+  std::vector<int64_t> sn_rowptr;  // ns + 1 offsets into rows
+  std::vector<int32_t> rows;
+  std::vector<int64_t> sn_valptr;  // ns + 1 offsets into panel storage
+  std::vector<int32_t> sn_parent, sn_level;
+  std::vector<int32_t> col2sn;     // n
+  std::vector<int64_t> amap;       // nnz_a: panel offset of every stored entry of A
+  int32_t nlev = 0;
+  std::vector<int32_t> lvl_ptr, lvl_sn;
+  // task lists: tasks[k] holds all tasks of kind k, level l occupies
+  // [task_off[k][l], task_off[k][l+1])
+  std::vector<int32_t> tasks[kNumTaskKinds];      // 4 ints per task
+  std::vector<int64_t> task_off[kNumTaskKinds];   // nlev + 1
+  // owner assembly: staging offsets of U_s inside its level's buffer, and the size
+  int64_t stage_elems = 0;
+  std::vector<int64_t> sn_ustage;  // ns
+  // sources of the owner-assembly groups: {s, kb, ke, 0}, columns [kb, ke) of U_s
+  std::vector<int32_t> asm_src;
+  // algorithmic flops of each task kind per level (POTRF n(n+1)(2n+1)/6, TRSM u n^2,
+  // Schur u(u+1)n per supernode; they add up to sum_j c_j^2) and panel bytes per level
+  std::vector<double> lvl_flops[kNumTaskKinds];
+  std::vector<double> lvl_panel_bytes;
+  double flops = 0.0;
+  int64_t nnz_l = 0, l_storage = 0, max_width = 0, max_rows = 0;
+};
+
+// Host analysis (analyze.cpp).  Returns CHOL_OK or CHOL_E_INVALID.
+int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32_t* perm,
+            int width_cap, Sym* out);
+
+}  // namespace chol

@@ -1,0 +1,253 @@
+// solve_kernels.cu -- supernodal forward and back substitution on the device.
+//
+// Sec. 1 and Sec. 2 of the paper: the solve phase solves L y = b and then L^T x = y.  With
+// the supernodal factor both run over the level sets: the forward solve goes from the
+// leaves up (a supernode's rows are final once all of its descendants are done), the back
+// solve from the root down (a supernode needs the solution on its off-diagonal rows, which
+// belong to ancestors).
+//
+// Vectors are n x nrhs column-major in the permuted numbering, ld = n.
+//   forward  task {s, r0}: y_s <- L11^{-1} y_s (redundantly in every task of s; the task
+//            with r0 = 0 stores it in w), then y[rows[n+i]] -= L21[i, :] y_s for its rows.
+//   backward task {s, r0}: part_q[j, c] = sum_{i in block} L21[i, j] x[rows[n+i], c] into
+//            a staging slot q; then per supernode x_s = L11^{-T} (w_s - sum_q part_q), the
+//            partials summed in task order (deterministic).
+#include <cuda_runtime.h>
+
+#include "chol_internal.h"
+#include "kernels.h"
+
+namespace chol {
+
+__global__ void k_gather_perm(const double* __restrict__ B, int64_t ldb,
+                              const int32_t* __restrict__ perm, int64_t n, int nrhs,
+                              double* __restrict__ y) {
+  const int64_t total = n * nrhs;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = q / n, i = q - c * n;
+    y[q] = B[c * ldb + perm[i]];
+  }
+}
+
+__global__ void k_scatter_perm(const double* __restrict__ w, const int32_t* __restrict__ perm,
+                               int64_t n, int nrhs, double* __restrict__ X, int64_t ldx) {
+  const int64_t total = n * nrhs;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = q / n, i = q - c * n;
+    X[c * ldx + perm[i]] = w[q];
+  }
+}
+
+constexpr int kSolveThreads = kSolveRows;  // one off-diagonal row per thread
+constexpr int kRhsChunk = 8;
+
+// Warp-level triangular solve of the n x n lower L11 (smem, column-major ld n) against
+// xs (smem, n x nrhs, ld n).  Forward: xs <- L11^{-1} xs.  Backward: xs <- L11^{-T} xs.
+// Lane l owns rows l, l+32, l+64, l+96 (n <= 128).
+template <bool FORWARD>
+__device__ void warp_trisolve(const double* L11, const double* rdiag, double* xs, int n,
+                              int nrhs) {
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < nrhs; c++) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int r = lane + 32 * q;
+      v[q] = r < n ? xs[c * n + r] : 0.0;
+    }
+    for (int jj = 0; jj < n; jj++) {
+      const int j = FORWARD ? jj : n - 1 - jj;
+      const int qj = j >> 5, lj = j & 31;
+      double own = v[0];
+      if (qj == 1) own = v[1];
+      if (qj == 2) own = v[2];
+      if (qj == 3) own = v[3];
+      const double xj = __shfl_sync(0xffffffffu, own, lj) * rdiag[j];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int r = lane + 32 * q;
+        if (r == j) v[q] = xj;
+        else if (FORWARD ? (r > j && r < n) : (r < j)) {
+          // forward: row r of column j of L11; backward: (L^T)_{r j} = L_{j r}
+          const double l = FORWARD ? L11[j * n + r] : L11[r * n + j];
+          v[q] -= l * xj;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int r = lane + 32 * q;
+      if (r < n) xs[c * n + r] = v[q];
+    }
+  }
+}
+
+__device__ void load_l11(const SnDev& d, double* L11, double* rdiag) {
+  const double* L = reinterpret_cast<const double*>(d.L);
+  const int n = d.n;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int c = idx / n, r = idx - c * n;
+    L11[idx] = r >= c ? L[(int64_t)c * d.m + r] : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rdiag[j] = 1.0 / L11[j * n + j];
+  __syncthreads();
+}
+
+// smem: L11 n*n, rdiag n, xs n*nrhs
+__global__ void __launch_bounds__(kSolveThreads)
+    k_fwd(const int4* __restrict__ tasks, const SnDev* __restrict__ sns, int64_t ldv, int nrhs,
+          double* __restrict__ y, double* __restrict__ w) {
+  extern __shared__ __align__(16) double sm[];
+  const int4 tk = tasks[blockIdx.x];
+  const SnDev d = sns[tk.x];
+  const int n = d.n, m = d.m, u = m - n;
+  double* L11 = sm;
+  double* rdiag = L11 + n * n;
+  double* xs = rdiag + n;
+  for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+    const int c = idx / n, j = idx - c * n;
+    xs[idx] = y[c * ldv + d.col0 + j];
+  }
+  load_l11(d, L11, rdiag);
+  if (threadIdx.x < 32) warp_trisolve<true>(L11, rdiag, xs, n, nrhs);
+  __syncthreads();
+  if (tk.y == 0)
+    for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+      const int c = idx / n, j = idx - c * n;
+      w[c * ldv + d.col0 + j] = xs[idx];
+    }
+  const int i = tk.y + threadIdx.x;
+  if (i < u) {
+    const double* L = reinterpret_cast<const double*>(d.L) + n + i;
+    const int64_t grow = d.rows[n + i];
+    for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
+      double acc[kRhsChunk];
+#pragma unroll
+      for (int c = 0; c < kRhsChunk; c++) acc[c] = 0.0;
+      for (int j = 0; j < n; j++) {
+        const double l = L[(int64_t)j * m];
+#pragma unroll
+        for (int c = 0; c < kRhsChunk; c++)
+          if (c0 + c < nrhs) acc[c] += l * xs[(c0 + c) * n + j];
+      }
+#pragma unroll
+      for (int c = 0; c < kRhsChunk; c++)
+        if (c0 + c < nrhs) atomicAdd(&y[(int64_t)(c0 + c) * ldv + grow], -acc[c]);
+    }
+  }
+}
+
+// Backward partials: the level's task q = blockIdx.x writes part[q * W * nrhs + c * W + j].
+__global__ void __launch_bounds__(kSolveThreads)
+    k_bwd_partial(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
+                  int64_t ldv, int nrhs, int W, const double* __restrict__ w,
+                  double* __restrict__ part) {
+  extern __shared__ __align__(16) double sm[];
+  const int4 tk = tasks[blockIdx.x];
+  const SnDev d = sns[tk.x];
+  const int n = d.n, m = d.m, u = m - n;
+  const int rb = min(kSolveRows, u - tk.y);
+  double* xg = sm;  // rb x nrhs
+  for (int idx = threadIdx.x; idx < rb * nrhs; idx += blockDim.x) {
+    const int c = idx / rb, i = idx - c * rb;
+    xg[idx] = w[c * ldv + d.rows[n + tk.y + i]];
+  }
+  __syncthreads();
+  double* out = part + (int64_t)blockIdx.x * W * nrhs;
+  const double* L = reinterpret_cast<const double*>(d.L) + n + tk.y;
+  for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+    const int c = idx / n, j = idx - c * n;
+    double acc = 0.0;
+    const double* col = L + (int64_t)j * m;
+    for (int i = 0; i < rb; i++) acc += col[i] * xg[c * rb + i];
+    out[c * W + j] = acc;
+  }
+}
+
+// Backward diagonal step, one CTA per supernode: task {s, first_bwd, nbwd}; first_bwd is
+// a global index into the backward task list, base the first task of this level.
+__global__ void __launch_bounds__(kSolveThreads)
+    k_bwd_diag(const int4* __restrict__ tasks, int64_t base, const SnDev* __restrict__ sns,
+               int64_t ldv, int nrhs, int W, const double* __restrict__ part,
+               double* __restrict__ w) {
+  extern __shared__ __align__(16) double sm[];
+  const int4 tk = tasks[blockIdx.x];
+  const SnDev d = sns[tk.x];
+  const int n = d.n;
+  double* L11 = sm;
+  double* rdiag = L11 + n * n;
+  double* xs = rdiag + n;
+  const int u = d.m - n;
+  for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+    const int c = idx / n, j = idx - c * n;
+    double v = w[c * ldv + d.col0 + j];
+    if (u > 0)
+      for (int q = 0; q < tk.z; q++) v -= part[(tk.y - base + q) * W * nrhs + c * W + j];
+    xs[idx] = v;
+  }
+  load_l11(d, L11, rdiag);
+  if (threadIdx.x < 32) warp_trisolve<false>(L11, rdiag, xs, n, nrhs);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+    const int c = idx / n, j = idx - c * n;
+    w[c * ldv + d.col0 + j] = xs[idx];
+  }
+}
+
+// ---- launchers ---------------------------------------------------------------------------------
+static inline size_t solve_smem(int W, int nrhs) {
+  return ((size_t)W * W + W + (size_t)W * nrhs) * sizeof(double);
+}
+
+void launch_gather_perm(const double* B, int64_t ldb, const int32_t* perm, int64_t n, int nrhs,
+                        double* y, cudaStream_t st) {
+  if (n <= 0) return;
+  int64_t total = n * nrhs;
+  int blocks = (int)((total + 255) / 256 < 152 * 8 ? (total + 255) / 256 : 152 * 8);
+  k_gather_perm<<<blocks, 256, 0, st>>>(B, ldb, perm, n, nrhs, y);
+}
+
+void launch_scatter_perm(const double* w, const int32_t* perm, int64_t n, int nrhs, double* X,
+                         int64_t ldx, cudaStream_t st) {
+  if (n <= 0) return;
+  int64_t total = n * nrhs;
+  int blocks = (int)((total + 255) / 256 < 152 * 8 ? (total + 255) / 256 : 152 * 8);
+  k_scatter_perm<<<blocks, 256, 0, st>>>(w, perm, n, nrhs, X, ldx);
+}
+
+void launch_fwd(const int4* tasks, int ntasks, const SnDev* sns, int64_t ldv, int nrhs, int W,
+                double* y, double* w, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  k_fwd<<<ntasks, kSolveThreads, solve_smem(W, nrhs), st>>>(tasks, sns, ldv, nrhs, y, w);
+}
+
+void launch_bwd(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* diag_tasks,
+                int ndiag, const SnDev* sns, int64_t ldv, int nrhs, int W, double* w,
+                double* part, cudaStream_t st) {
+  if (nbwd > 0)
+    k_bwd_partial<<<nbwd, kSolveThreads, (size_t)kSolveRows * nrhs * sizeof(double), st>>>(
+        bwd_tasks, sns, ldv, nrhs, W, w, part);
+  if (ndiag > 0)
+    k_bwd_diag<<<ndiag, kSolveThreads, solve_smem(W, nrhs), st>>>(diag_tasks, bwd_base, sns,
+                                                                  ldv, nrhs, W, part, w);
+}
+
+int set_solve_kernel_attrs(int W, int max_nrhs) {
+  size_t sm = solve_smem(W, max_nrhs);
+  if (cudaFuncSetAttribute(k_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+      cudaSuccess)
+    return CHOL_E_CUDA;
+  if (cudaFuncSetAttribute(k_bwd_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+      cudaSuccess)
+    return CHOL_E_CUDA;
+  size_t sp = (size_t)kSolveRows * max_nrhs * sizeof(double);
+  if (cudaFuncSetAttribute(k_bwd_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sp) != cudaSuccess)
+    return CHOL_E_CUDA;
+  return CHOL_OK;
+}
+
+}  // namespace chol

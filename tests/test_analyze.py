@@ -1,0 +1,114 @@
+"""Host symbolic analysis of the library (through the C ABI) against the oracle's brute
+force: elimination tree, column counts, supernode partition and level sets must match
+bit for bit (Sec. 2 analysis; Sec. 3 / Fig. 1 level sets).  CPU only."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2202_09288_gb300 as P
+from paper_2202_09288_gb300 import inputs
+
+CASES = ["lap2d_16", "lap2d_64", "lap3d_9", "st27x3_6", "diff3d7_10"]
+
+
+def both(A, perm, W):
+    sym = P.Symbolic(P.make_opts(width_cap=W), A, perm)
+    got = sym.export()
+    bp, bi, bx = oracle.permute(A.n, A.colptr, A.rowind, A.vals, perm)
+    parent, cc, lp, li = oracle.symbolic(A.n, bp, bi)
+    start, sp, lv = oracle.supernodes(parent, cc, W)
+    return sym, got, (parent, cc, start, lv)
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("W", [64, 16, 1, 128])
+def test_symbolic_matches_oracle(name, W):
+    A, perm = inputs.workload(name)
+    sym, got, (parent, cc, start, lv) = both(A, perm, W)
+    assert np.array_equal(got["parent"], parent)
+    assert np.array_equal(got["colcount"], cc)
+    assert np.array_equal(got["sn_start"], start)
+    assert np.array_equal(got["sn_level"], lv)
+    info = sym.info
+    assert info["nnz_l"] == int(cc.sum())
+    assert info["flops"] == float(np.sum(cc.astype(np.float64) ** 2))
+    assert info["nsuper"] == len(start) - 1
+    assert info["nlevels"] == int(lv.max()) + 1
+    assert info["max_width"] <= W
+
+
+def test_random_patterns_and_perms():
+    for seed in range(5):
+        n = 80
+        u = inputs.uniform(200 + seed, 7, n * n).reshape(n, n)
+        adj = (u > 0.93) | (u.T > 0.93)
+        a = np.where(adj, -0.05, 0.0)
+        a = np.tril(a) + np.tril(a, -1).T
+        a[np.arange(n), np.arange(n)] = 1.0
+        A = inputs.from_dense(a)
+        perm = np.argsort(inputs.uniform(seed, 9, n), kind="stable").astype(np.int32)
+        for W in (3, 64):
+            sym, got, (parent, cc, start, lv) = both(A, perm, W)
+            assert np.array_equal(got["parent"], parent)
+            assert np.array_equal(got["colcount"], cc)
+            assert np.array_equal(got["sn_start"], start)
+            assert np.array_equal(got["sn_level"], lv)
+
+
+def test_fig1_tree_levels():
+    a = np.eye(6) * 4.0
+    for i, j in [(3, 0), (3, 1), (4, 2), (5, 3), (5, 4)]:
+        a[i, j] = a[j, i] = -1.0
+    sym = P.Symbolic(None, inputs.from_dense(a), np.arange(6, dtype=np.int32))
+    e = sym.export()
+    assert list(e["sn_level"]) == [0, 0, 0, 1, 1, 2]
+
+
+def test_empty_and_one():
+    A = inputs.from_dense(np.array([[2.0]]))
+    sym = P.Symbolic(None, A, np.zeros(1, np.int32))
+    assert sym.info["nnz_l"] == 1 and sym.info["nsuper"] == 1
+    A0 = inputs.SpdMatrix(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    sym0 = P.Symbolic(None, A0, np.zeros(0, np.int32))
+    assert sym0.info["nnz_l"] == 0 and sym0.info["nsuper"] == 0
+
+
+def _bad(n, colptr, rowind, perm):
+    with pytest.raises(P.CholError) as e:
+        P.chol_analyze(None, n, np.array(colptr), np.array(rowind), np.array(perm))
+    assert e.value.status == P.CHOL_E_INVALID
+
+
+def test_invalid_inputs_rejected():
+    _bad(2, [0, 1, 2], [1, 0], [0, 1])          # entry above the diagonal in column 1
+    _bad(2, [0, 2, 3], [1, 0, 1], [0, 1])       # unsorted rows
+    _bad(2, [0, 2, 3], [0, 0, 1], [0, 1])       # duplicate row
+    _bad(2, [0, 2, 3], [0, 2, 1], [0, 1])       # row out of range
+    _bad(2, [0, 1, 2], [0, 1], [0, 0])          # perm not a permutation
+    _bad(2, [0, 1, 2], [0, 1], [0, 2])          # perm out of range
+    _bad(-1, [0], [], [])                       # negative order
+    with pytest.raises(P.CholError):
+        P.chol_analyze(P.make_opts(width_cap=512), 1, np.array([0, 1]), np.array([0]),
+                       np.array([0]))
+
+
+def test_abi_exports_every_declared_symbol():
+    import re
+    import ctypes
+    hdr = open(P.LIB_PATH.replace("paper_2202_09288_gb300/libchol.so", "include/chol.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"\b(chol_[a-z_0-9]+)\s*\(", hdr))
+    assert names, "no declarations parsed"
+    L = ctypes.CDLL(P.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(P.EXPORTS) >= names
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(P.CholError) as e:
+        P.Context()
+    assert e.value.status == P.CHOL_E_NODEVICE

@@ -1,0 +1,190 @@
+"""GPU parity of the FP64 supernodal factorization and solves against the CPU oracle.
+
+The factor L of B = P^T A P is unique (Sec. 1: A = L L^T); the device path reorganizes the
+left-looking supernodal algorithm (Sec. 3, Listing 1) per etree level, so it must give the
+oracle's L up to rounding: the pattern bit for bit and the values within 1e-12 relative
+Frobenius error; every solve must reach a relative residual <= 1e-13."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2202_09288_gb300 as P
+from paper_2202_09288_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FACTOR_TOL = 1e-12   # relative Frobenius error of L against the oracle
+RESID_TOL = 1e-13    # ||b - A x||_inf / (||A||_inf ||x||_inf)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+_ORACLE = {}
+
+
+def oracle_factor(name):
+    if name not in _ORACLE:
+        if name.startswith("dense_"):
+            A = inputs.random_spd_dense(int(name.split("_")[1]), 7)
+            perm = np.arange(A.n, dtype=np.int32)
+        elif name.startswith("lap1d_"):
+            A = inputs.laplacian_1d(int(name.split("_")[1]))
+            perm = np.arange(A.n, dtype=np.int32)
+        elif name.startswith("diag_"):
+            n = int(name.split("_")[1])
+            A = inputs.from_dense(np.diag(1.0 + np.arange(n, dtype=float)))
+            perm = np.arange(n, dtype=np.int32)
+        else:
+            A, perm = inputs.workload(name)
+        _ORACLE[name] = (A, perm, oracle.cholesky(A, perm))
+    return _ORACLE[name]
+
+
+def check_factor(ctx, name, W):
+    A, perm, f = oracle_factor(name)
+    sym = P.Symbolic(P.make_opts(width_cap=W), A, perm)
+    num = P.Factor(ctx, sym, A.vals)
+    rc, bad = num.status()
+    assert rc == P.CHOL_OK, (rc, bad)
+    lp, li, lx = num.export()
+    assert np.array_equal(lp, f.lp) and np.array_equal(li, f.li)
+    err = np.linalg.norm(lx - f.lx) / np.linalg.norm(f.lx)
+    assert err <= FACTOR_TOL, err
+    xt = inputs.rhs_block(3, A.n, 1)[:, 0]
+    b = A.to_scipy_full() @ xt
+    x = num.solve(b)
+    res = oracle.residual(A.n, A.colptr, A.rowind, A.vals, b, x)
+    assert res <= RESID_TOL, res
+    return sym, num
+
+
+CASES = ["lap2d_64", "lap2d_23", "lap3d_12", "st27x3_6", "st27x3_11", "diff3d7_14",
+         "dense_150", "lap1d_300", "diag_50", "dense_1"]
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("assembly", [P.CHOL_ASSEMBLY_ATOMIC, P.CHOL_ASSEMBLY_OWNER])
+def test_factor_parity(torch, name, assembly):
+    ctx = P.Context(assembly=assembly)
+    check_factor(ctx, name, 64)
+
+
+@pytest.mark.parametrize("W", [1, 7, 16, 128])
+def test_width_caps(torch, W):
+    ctx = P.Context(width_cap=W)
+    for name in ("lap2d_23", "st27x3_6", "dense_150"):
+        check_factor(ctx, name, W)
+
+
+def test_multi_rhs_host_and_device(torch):
+    ctx = P.Context()
+    A, perm, f = oracle_factor("st27x3_11")
+    sym = P.Symbolic(ctx, A, perm)
+    num = P.Factor(ctx, sym, A.vals)
+    Afull = A.to_scipy_full()
+    for k in (1, 3, 16, 40):
+        Xt = inputs.rhs_block(k, A.n, k)
+        Bm = np.asfortranarray(Afull @ Xt)
+        X = num.solve(Bm)
+        assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, Bm, X) <= RESID_TOL
+        # same thing through device pointers (tensor rows = right-hand sides)
+        Bd = torch.from_numpy(np.ascontiguousarray(Bm.T)).cuda()
+        Xd = num.solve(Bd)
+        torch.cuda.synchronize()
+        Xh = Xd.cpu().numpy().T
+        assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, Bm, Xh) <= RESID_TOL
+        np.testing.assert_allclose(Xh, X, rtol=0, atol=1e-12 * np.abs(X).max())
+
+
+def test_device_values_and_refactorize(torch):
+    ctx = P.Context()
+    A, perm, f = oracle_factor("diff3d7_14")
+    sym = P.Symbolic(ctx, A, perm)
+    vals_d = torch.from_numpy(A.vals).cuda()
+    num = P.Factor(ctx, sym, vals_d)
+    assert num.status()[0] == P.CHOL_OK
+    lx1 = num.export()[2]
+    assert np.linalg.norm(lx1 - f.lx) / np.linalg.norm(f.lx) <= FACTOR_TOL
+    # new values on the same pattern: 4 A has factor 2 L
+    num.refactor(4.0 * A.vals)
+    assert num.status()[0] == P.CHOL_OK
+    lx2 = num.export()[2]
+    assert np.linalg.norm(lx2 - 2.0 * f.lx) / np.linalg.norm(2.0 * f.lx) <= FACTOR_TOL
+
+
+def test_not_spd_reported(torch):
+    ctx = P.Context()
+    A, perm = inputs.workload("lap2d_23")
+    vals = A.vals.copy()
+    vals[A.colptr[100]] = -4.0  # negate one diagonal entry
+    sym = P.Symbolic(ctx, A, perm)
+    num = P.Factor(ctx, sym, vals)
+    rc, bad = num.status()
+    assert rc == P.CHOL_E_NOT_SPD
+    assert 0 <= bad < A.n
+    # the context stays usable afterwards
+    num.refactor(A.vals)
+    assert num.status()[0] == P.CHOL_OK
+
+
+def test_owner_assembly_is_bitwise_reproducible(torch):
+    ctx = P.Context(assembly=P.CHOL_ASSEMBLY_OWNER)
+    A, perm, f = oracle_factor("st27x3_11")
+    sym = P.Symbolic(ctx, A, perm)
+    num = P.Factor(ctx, sym, A.vals)
+    first = num.export()[2].copy()
+    b = A.to_scipy_full() @ inputs.rhs_block(5, A.n, 1)[:, 0]
+    x1 = num.solve(b).copy()
+    for _ in range(3):
+        num.refactor(A.vals)
+        assert np.array_equal(num.export()[2], first)
+    assert np.array_equal(num.solve(b), x1)
+
+
+def test_profile_counters(torch):
+    ctx = P.Context()
+    A, perm, f = oracle_factor("st27x3_11")
+    sym = P.Symbolic(ctx, A, perm)
+    P.chol_profile_enable(ctx.handle, True)
+    num = P.Factor(ctx, sym, A.vals)
+    prof = P.chol_profile_read(ctx.handle)
+    total = sum(v["flops"] for v in prof.values())
+    assert abs(total - sym.info["flops"]) <= 1e-9 * sym.info["flops"]
+    assert prof["potrf_f64"]["launches"] == sym.info["nlevels"]
+    assert all(v["ms"] >= 0 for v in prof.values())
+
+
+def test_full_size_st27x3_48_properties(torch):
+    """The 48^3 3-dof workload the bench times, in the same launch configuration: the
+    oracle cannot factor it in seconds, so check properties that hold at any size:
+    entries of L L^T sampled against B, and the residual of a solve."""
+    ctx = P.Context()
+    A, perm = inputs.workload("st27x3_48")
+    sym = P.Symbolic(ctx, A, perm)
+    num = P.Factor(ctx, sym, torch.from_numpy(A.vals).cuda())
+    assert num.status()[0] == P.CHOL_OK
+    lp, li, lx = num.export()
+    n = A.n
+    # sampled entries (i, j) of B = P^T A P: (L L^T)_ij = sum_k L_ik L_jk
+    bp, bi, bx = oracle.permute(n, A.colptr, A.rowind, A.vals, perm)
+    rng_cols = (np.abs(inputs.uniform(11, 6, 40)) * n).astype(np.int64)
+    import scipy.sparse as sp
+    Lm = sp.csc_matrix((lx, li, lp), shape=(n, n)).tocsr()
+    for j in rng_cols:
+        rows = bi[bp[j]:bp[j + 1]]
+        vals = bx[bp[j]:bp[j + 1]]
+        lj = Lm.getrow(j)
+        for i, v in zip(rows, vals):
+            li_row = Lm.getrow(i)
+            s = li_row.multiply(lj).sum()
+            assert abs(s - v) <= 1e-13 * max(abs(v), np.abs(bx[bp[i]])), (i, j, s, v)
+    xt = inputs.rhs_block(2, n, 1)[:, 0]
+    b = A.to_scipy_full() @ xt
+    x = num.solve(b)
+    assert oracle.residual(n, A.colptr, A.rowind, A.vals, b, x) <= RESID_TOL
