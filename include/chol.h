@@ -27,7 +27,10 @@
  *    reported by the next chol_factor_status() call.
  *  - Ownership: the caller owns every array it passes and may free it once the call
  *    returns (device arrays: once the stream has passed the call).  Handles returned by
- *    the library are owned by it until the matching chol_free_* / chol_destroy.
+ *    the library are owned by it until the matching chol_free_* / chol_destroy.  A factor
+ *    refers to the analysis it was made from: free factors before that analysis.
+ *    Destroying a context releases the device memory of every handle bound to it; those
+ *    handles must then only be passed to chol_free_*.
  *  - Threading: a context and its handles must not be used from two threads at once.
  */
 #ifndef CHOL_H

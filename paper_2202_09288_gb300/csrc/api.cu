@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <set>
+#include <unordered_map>
 #include <vector>
 
 #include "chol_internal.h"
@@ -43,6 +45,10 @@ struct chol_ctx {
   std::vector<ProfPending> pending;
   std::vector<cudaEvent_t> spare_events;
   cudaEvent_t open_event = nullptr;
+  // handles holding device memory of this context; chol_destroy detaches them
+  std::set<chol_sym*> syms;
+  std::set<chol_num*> nums;
+  std::unordered_map<void*, size_t> sizes;  // live allocations (budget accounting)
 };
 
 struct DevSym {
@@ -155,14 +161,18 @@ int dev_alloc(chol_ctx* c, void** p, size_t bytes) {
     return CHOL_E_OOM;
   }
   c->held += bytes;
+  c->sizes[*p] = bytes;
   return CHOL_OK;
 }
 
-void dev_free(chol_ctx* c, void* p, size_t bytes) {
+void dev_free(chol_ctx* c, void* p) {
   if (!p) return;
   cudaFreeAsync(p, c->stream);
-  if (bytes == 0) bytes = 16;
-  c->held -= std::min(c->held, bytes);
+  auto it = c->sizes.find(p);
+  if (it != c->sizes.end()) {
+    c->held -= std::min(c->held, it->second);
+    c->sizes.erase(it);
+  }
 }
 
 template <typename T>
@@ -179,14 +189,14 @@ void free_devsym(chol_sym* s) {
   if (!s->ctx) return;
   chol_ctx* c = s->ctx;
   DevSym& d = s->dev;
-  const Sym& S = s->S;
-  dev_free(c, d.rows, S.rows.size() * 4);
-  dev_free(c, d.col2sn, S.col2sn.size() * 4);
-  dev_free(c, d.amap, S.amap.size() * 8);
-  dev_free(c, d.perm, S.perm.size() * 4);
-  for (int k = 0; k < chol::kNumTaskKinds; k++) dev_free(c, d.tasks[k], S.tasks[k].size() * 4);
-  dev_free(c, d.asm_src, S.asm_src.size() * 4);
+  dev_free(c, d.rows);
+  dev_free(c, d.col2sn);
+  dev_free(c, d.amap);
+  dev_free(c, d.perm);
+  for (int k = 0; k < chol::kNumTaskKinds; k++) dev_free(c, d.tasks[k]);
+  dev_free(c, d.asm_src);
   d = DevSym();
+  c->syms.erase(s);
   s->ctx = nullptr;
 }
 
@@ -198,6 +208,7 @@ int ensure_uploaded(chol_ctx* c, chol_sym* s) {
   size_t acc = 0;
   int rc;
   s->ctx = c;
+  c->syms.insert(s);
   if ((rc = upload(c, &d.rows, S.rows, &acc)) || (rc = upload(c, &d.col2sn, S.col2sn, &acc)) ||
       (rc = upload(c, &d.amap, S.amap, &acc)) || (rc = upload(c, &d.perm, S.perm, &acc))) {
     free_devsym(s);
@@ -287,11 +298,10 @@ int ensure_solve_ws(chol_num* f, int64_t nrhs) {
   chol_ctx* c = f->ctx;
   const Sym& S = f->sym->S;
   const int64_t n = S.n;
-  int64_t old = f->ws_nrhs;
-  dev_free(c, f->d_y, (size_t)n * old * 8);
-  dev_free(c, f->d_w, (size_t)n * old * 8);
-  dev_free(c, f->d_bx, (size_t)n * old * 8);
-  dev_free(c, f->d_part, (size_t)f->sym->max_bwd_per_level * S.width_cap * old * 8);
+  dev_free(c, f->d_y);
+  dev_free(c, f->d_w);
+  dev_free(c, f->d_bx);
+  dev_free(c, f->d_part);
   f->d_y = f->d_w = f->d_bx = f->d_part = nullptr;
   f->ws_nrhs = 0;
   int rc;
@@ -343,18 +353,18 @@ int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X
 void free_num_buffers(chol_num* f) {
   chol_ctx* c = f->ctx;
   if (!c) return;
-  const Sym& S = f->sym->S;
-  const size_t esz = f->precision == CHOL_MIXED ? 4 : 8;
-  dev_free(c, f->L, (size_t)S.l_storage * esz);
-  dev_free(c, f->d_sn, (size_t)S.ns * sizeof(SnDev));
-  dev_free(c, f->d_mat, sizeof(MatDev));
-  dev_free(c, f->d_err, 16);
-  dev_free(c, f->d_vals, (size_t)S.nnz_a * 8);
-  dev_free(c, f->d_stage, (size_t)S.stage_elems * 8);
-  dev_free(c, f->d_y, (size_t)S.n * f->ws_nrhs * 8);
-  dev_free(c, f->d_w, (size_t)S.n * f->ws_nrhs * 8);
-  dev_free(c, f->d_bx, (size_t)S.n * f->ws_nrhs * 8);
-  dev_free(c, f->d_part, (size_t)f->sym->max_bwd_per_level * S.width_cap * f->ws_nrhs * 8);
+  dev_free(c, f->L);
+  dev_free(c, f->d_sn);
+  dev_free(c, f->d_mat);
+  dev_free(c, f->d_err);
+  dev_free(c, f->d_vals);
+  dev_free(c, f->d_stage);
+  dev_free(c, f->d_y);
+  dev_free(c, f->d_w);
+  dev_free(c, f->d_bx);
+  dev_free(c, f->d_part);
+  c->nums.erase(f);
+  f->ctx = nullptr;
 }
 
 }  // namespace
@@ -438,6 +448,11 @@ void chol_destroy(chol_ctx* c) {
   prof_fold(c);
   for (cudaEvent_t e : c->spare_events) cudaEventDestroy(e);
   if (c->open_event) cudaEventDestroy(c->open_event);
+  // detach handles that still hold device memory of this context (their later free_* or
+  // any other call sees no context and does nothing / returns CHOL_E_INVALID)
+  while (!c->nums.empty()) free_num_buffers(*c->nums.begin());
+  while (!c->syms.empty()) free_devsym(*c->syms.begin());
+  cudaStreamSynchronize(c->stream);
   cudaMemPoolDestroy(c->pool);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -512,6 +527,7 @@ int chol_factorize(chol_ctx* c, const chol_sym* sym_c, const double* vals, int w
   chol_num* f = new (std::nothrow) chol_num();
   if (!f) return CHOL_E_OOM;
   f->ctx = c;
+  c->nums.insert(f);
   f->sym = sym;
   f->precision = precision;
   f->assembly = c->opts.assembly;
