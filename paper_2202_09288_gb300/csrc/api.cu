@@ -255,7 +255,10 @@ int enqueue_factor(chol_num* f, const double* vals_dev) {
   const Sym& S = sym->S;
   cudaStream_t st = c->stream;
   const size_t esz = sizeof(double);
-  CK(cudaMemsetAsync(f->d_err, 0, 2 * sizeof(unsigned long long), st));
+  // err[0] = smallest failing column + 1, kept by atomicMin: starts at all ones (none);
+  // err[1] = relative-map misses: starts at 0
+  CK(cudaMemsetAsync(f->d_err, 0xff, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(f->d_err + 1, 0, sizeof(unsigned long long), st));
   prof_begin(c);
   CK(cudaMemsetAsync(f->L, 0, (size_t)S.l_storage * esz, st));
   chol::launch_assemble(vals_dev, sym->dev.amap, S.nnz_a, f->L, false, st);
@@ -593,7 +596,7 @@ int chol_factor_status(chol_ctx* c, const chol_num* f, int64_t* bad_col) {
   CK(cudaGetLastError());
   if (ee[1]) return CHOL_E_INVALID;  // internal relative-map inconsistency
   const unsigned long long e = ee[0];
-  if (e) {
+  if (e != ~0ull) {
     if (bad_col) *bad_col = (int64_t)(e - 1);
     return CHOL_E_NOT_SPD;
   }

@@ -48,7 +48,8 @@ struct alignas(16) MatDev {
   const int32_t* col2sn;          // column -> supernode index (matrix-local)
   int32_t sn_base;                // index of supernode 0 of this matrix in the SnDev array
   int32_t pad0;
-  unsigned long long* err;        // err[0]: first failing column + 1 (0 = none), atomicMin;
+  unsigned long long* err;        // err[0]: smallest failing column + 1 (all ones = none),
+                                  // kept by atomicMin;
                                   // err[1]: relative-map misses (internal check, 0 expected)
 };
 
