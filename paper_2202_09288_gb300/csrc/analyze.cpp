@@ -259,6 +259,11 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
   S->lvl_panel_bytes.assign(S->nlev, 0.0);
   S->sn_ustage.assign(ns, -1);
   S->asm_src.clear();
+  S->fg_lvl.assign(1, 0);
+  S->fg_ptr.assign(1, 0);
+  S->fg_row.clear();
+  S->fg_ent.clear();
+  S->max_fwd_per_level = 0;
   S->stage_elems = 0;
   for (int32_t l = 0; l < S->nlev; l++) {
     int64_t tiles64 = 0, stage = 0;
@@ -337,6 +342,33 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
     }
     for (int k = 0; k < kNumTaskKinds; k++)
       S->task_off[k][l + 1] = (int64_t)S->tasks[k].size() / 4;
+    // owner-ordered forward-solve gather lists of this level
+    {
+      const int64_t f0 = S->task_off[kTaskFwd][l], f1 = S->task_off[kTaskFwd][l + 1];
+      S->max_fwd_per_level = std::max(S->max_fwd_per_level, f1 - f0);
+      std::vector<std::pair<int32_t, int32_t>> ent;  // (target row, slot)
+      for (int64_t q = f0; q < f1; q++) {
+        const int32_t s = S->tasks[kTaskFwd][4 * q], r0 = S->tasks[kTaskFwd][4 * q + 1];
+        const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
+        const int32_t u = S->sn_m[s] - w;
+        const int32_t* rs = S->rows.data() + S->sn_rowptr[s] + w;
+        for (int32_t ii = 0; ii < kSolveRows && r0 + ii < u; ii++)
+          ent.push_back({rs[r0 + ii], (int32_t)((q - f0) * kSolveRows + ii)});
+      }
+      // slots grow with the task index, and tasks are ordered by source supernode
+      std::stable_sort(ent.begin(), ent.end(),
+                       [](const std::pair<int32_t, int32_t>& x,
+                          const std::pair<int32_t, int32_t>& y) { return x.first < y.first; });
+      size_t e = 0;
+      while (e < ent.size()) {
+        size_t g = e;
+        S->fg_row.push_back(ent[e].first);
+        while (g < ent.size() && ent[g].first == ent[e].first) S->fg_ent.push_back(ent[g++].second);
+        S->fg_ptr.push_back((int64_t)S->fg_ent.size());
+        e = g;
+      }
+      S->fg_lvl.push_back((int64_t)S->fg_row.size());
+    }
   }
   return CHOL_OK;
 }

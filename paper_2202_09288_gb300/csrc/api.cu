@@ -59,6 +59,9 @@ struct DevSym {
   int32_t* perm = nullptr;
   int4* tasks[chol::kNumTaskKinds] = {};
   int4* asm_src = nullptr;
+  int64_t* fg_ptr = nullptr;
+  int32_t* fg_row = nullptr;
+  int32_t* fg_ent = nullptr;
   size_t bytes = 0;
 };
 
@@ -86,6 +89,7 @@ struct chol_num {
   double* d_w = nullptr;
   double* d_part = nullptr;
   double* d_bx = nullptr;      // host-call staging of B / X
+  double* d_fstage = nullptr;  // owner-ordered forward-solve staging
 };
 
 namespace {
@@ -195,6 +199,9 @@ void free_devsym(chol_sym* s) {
   dev_free(c, d.perm);
   for (int k = 0; k < chol::kNumTaskKinds; k++) dev_free(c, d.tasks[k]);
   dev_free(c, d.asm_src);
+  dev_free(c, d.fg_ptr);
+  dev_free(c, d.fg_row);
+  dev_free(c, d.fg_ent);
   d = DevSym();
   c->syms.erase(s);
   s->ctx = nullptr;
@@ -219,7 +226,9 @@ int ensure_uploaded(chol_ctx* c, chol_sym* s) {
       free_devsym(s);
       return rc;
     }
-  if ((rc = upload(c, reinterpret_cast<int32_t**>(&d.asm_src), S.asm_src, &acc))) {
+  if ((rc = upload(c, reinterpret_cast<int32_t**>(&d.asm_src), S.asm_src, &acc)) ||
+      (rc = upload(c, &d.fg_ptr, S.fg_ptr, &acc)) || (rc = upload(c, &d.fg_row, S.fg_row, &acc)) ||
+      (rc = upload(c, &d.fg_ent, S.fg_ent, &acc))) {
     free_devsym(s);
     return rc;
   }
@@ -305,9 +314,14 @@ int ensure_solve_ws(chol_num* f, int64_t nrhs) {
   dev_free(c, f->d_w);
   dev_free(c, f->d_bx);
   dev_free(c, f->d_part);
-  f->d_y = f->d_w = f->d_bx = f->d_part = nullptr;
+  dev_free(c, f->d_fstage);
+  f->d_y = f->d_w = f->d_bx = f->d_part = f->d_fstage = nullptr;
   f->ws_nrhs = 0;
   int rc;
+  if (f->assembly == CHOL_ASSEMBLY_OWNER &&
+      (rc = dev_alloc(c, (void**)&f->d_fstage,
+                      (size_t)S.max_fwd_per_level * chol::kSolveRows * nrhs * 8)))
+    return rc;
   if ((rc = dev_alloc(c, (void**)&f->d_y, (size_t)n * nrhs * 8)) ||
       (rc = dev_alloc(c, (void**)&f->d_w, (size_t)n * nrhs * 8)) ||
       (rc = dev_alloc(c, (void**)&f->d_bx, (size_t)n * nrhs * 8)) ||
@@ -334,7 +348,11 @@ int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X
     int cnt;
     const int4* t = task_ptr(sym, chol::kTaskFwd, l, &cnt);
     prof_begin(c);
-    chol::launch_fwd(t, cnt, f->d_sn, n, nrhs, W, f->d_y, f->d_w, st);
+    chol::launch_fwd(t, cnt, f->d_sn, n, nrhs, W, f->d_y, f->d_w, f->d_fstage, st);
+    if (f->d_fstage)
+      chol::launch_fwd_gather(sym->dev.fg_row + S.fg_lvl[l], sym->dev.fg_ptr + S.fg_lvl[l],
+                              sym->dev.fg_ent, S.fg_lvl[l + 1] - S.fg_lvl[l], n, nrhs,
+                              f->d_fstage, f->d_y, st);
     prof_end(c, kProfFwd, 0.0, S.lvl_panel_bytes[l]);
   }
   for (int32_t l = S.nlev - 1; l >= 0; l--) {
@@ -366,6 +384,7 @@ void free_num_buffers(chol_num* f) {
   dev_free(c, f->d_w);
   dev_free(c, f->d_bx);
   dev_free(c, f->d_part);
+  dev_free(c, f->d_fstage);
   c->nums.erase(f);
   f->ctx = nullptr;
 }

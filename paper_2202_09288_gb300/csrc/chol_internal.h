@@ -80,6 +80,12 @@ struct Sym {
   std::vector<int64_t> sn_ustage;  // ns
   // sources of the owner-assembly groups: {s, kb, ke, 0}, columns [kb, ke) of U_s
   std::vector<int32_t> asm_src;
+  // owner-ordered forward solve: the rows updated by level l are fg_row[fg_lvl[l] ..
+  // fg_lvl[l+1]); row i sums the staged contributions fg_ent[fg_ptr[i] .. fg_ptr[i+1])
+  // (level-local slots q * kSolveRows + ii of forward task q), in ascending source order
+  std::vector<int64_t> fg_lvl, fg_ptr;
+  std::vector<int32_t> fg_row, fg_ent;
+  int64_t max_fwd_per_level = 0;
   // algorithmic flops of each task kind per level (POTRF n(n+1)(2n+1)/6, TRSM u n^2,
   // Schur u(u+1)n per supernode; they add up to sum_j c_j^2) and panel bytes per level
   std::vector<double> lvl_flops[kNumTaskKinds];

@@ -25,7 +25,10 @@ void launch_gather_perm(const double* B, int64_t ldb, const int32_t* perm, int64
 void launch_scatter_perm(const double* w, const int32_t* perm, int64_t n, int nrhs, double* X,
                          int64_t ldx, cudaStream_t st);
 void launch_fwd(const int4* tasks, int ntasks, const SnDev* sns, int64_t ldv, int nrhs, int W,
-                double* y, double* w, cudaStream_t st);
+                double* y, double* w, double* fstage, cudaStream_t st);
+void launch_fwd_gather(const int32_t* fg_row, const int64_t* fg_ptr, const int32_t* fg_ent,
+                       int64_t nrows, int64_t ldv, int nrhs, const double* fstage, double* y,
+                       cudaStream_t st);
 void launch_bwd(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* diag_tasks,
                 int ndiag, const SnDev* sns, int64_t ldv, int nrhs, int W, double* w,
                 double* part, cudaStream_t st);

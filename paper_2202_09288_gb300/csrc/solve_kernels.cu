@@ -8,11 +8,14 @@
 //
 // Vectors are n x nrhs column-major in the permuted numbering, ld = n.
 //   forward  task {s, r0}: y_s <- L11^{-1} y_s (redundantly in every task of s; the task
-//            with r0 = 0 stores it in w), then y[rows[n+i]] -= L21[i, :] y_s for its rows.
+//            with r0 = 0 stores it in w), then y[rows[n+i]] -= L21[i, :] y_s for its rows,
+//            by atomics, or (owner order) staged and summed per row in a fixed order.
 //   backward task {s, r0}: part_q[j, c] = sum_{i in block} L21[i, j] x[rows[n+i], c] into
 //            a staging slot q; then per supernode x_s = L11^{-T} (w_s - sum_q part_q), the
 //            partials summed in task order (deterministic).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "chol_internal.h"
 #include "kernels.h"
@@ -96,10 +99,12 @@ __device__ void load_l11(const SnDev& d, double* L11, double* rdiag) {
   __syncthreads();
 }
 
-// smem: L11 n*n, rdiag n, xs n*nrhs
+// smem: L11 n*n, rdiag n, xs n*nrhs.  STAGE: the off-diagonal products go to the level's
+// staging slots (q * kSolveRows + ii) * nrhs + c instead of atomics into y.
+template <bool STAGE>
 __global__ void __launch_bounds__(kSolveThreads)
     k_fwd(const int4* __restrict__ tasks, const SnDev* __restrict__ sns, int64_t ldv, int nrhs,
-          double* __restrict__ y, double* __restrict__ w) {
+          double* __restrict__ y, double* __restrict__ w, double* __restrict__ fstage) {
   extern __shared__ __align__(16) double sm[];
   const int4 tk = tasks[blockIdx.x];
   const SnDev d = sns[tk.x];
@@ -134,8 +139,29 @@ __global__ void __launch_bounds__(kSolveThreads)
           if (c0 + c < nrhs) acc[c] += l * xs[(c0 + c) * n + j];
       }
 #pragma unroll
-      for (int c = 0; c < kRhsChunk; c++)
-        if (c0 + c < nrhs) atomicAdd(&y[(int64_t)(c0 + c) * ldv + grow], -acc[c]);
+      for (int c = 0; c < kRhsChunk; c++) {
+        if (c0 + c >= nrhs) continue;
+        if (STAGE)
+          fstage[((int64_t)blockIdx.x * kSolveRows + threadIdx.x) * nrhs + c0 + c] = acc[c];
+        else
+          atomicAdd(&y[(int64_t)(c0 + c) * ldv + grow], -acc[c]);
+      }
+    }
+  }
+}
+
+// Owner-ordered forward update: row fg_row[i] of y subtracts its staged contributions in
+// the fixed order of fg_ent (ascending source supernode).
+__global__ void k_fwd_gather(const int32_t* __restrict__ fg_row, const int64_t* __restrict__ fg_ptr,
+                             const int32_t* __restrict__ fg_ent, int64_t nrows, int64_t ldv,
+                             int nrhs, const double* __restrict__ fstage, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = fg_row[i];
+    for (int c = 0; c < nrhs; c++) {
+      double s = 0.0;
+      for (int64_t e = fg_ptr[i]; e < fg_ptr[i + 1]; e++) s += fstage[(int64_t)fg_ent[e] * nrhs + c];
+      y[(int64_t)c * ldv + r] -= s;
     }
   }
 }
@@ -219,9 +245,22 @@ void launch_scatter_perm(const double* w, const int32_t* perm, int64_t n, int nr
 }
 
 void launch_fwd(const int4* tasks, int ntasks, const SnDev* sns, int64_t ldv, int nrhs, int W,
-                double* y, double* w, cudaStream_t st) {
+                double* y, double* w, double* fstage, cudaStream_t st) {
   if (ntasks <= 0) return;
-  k_fwd<<<ntasks, kSolveThreads, solve_smem(W, nrhs), st>>>(tasks, sns, ldv, nrhs, y, w);
+  if (fstage)
+    k_fwd<true><<<ntasks, kSolveThreads, solve_smem(W, nrhs), st>>>(tasks, sns, ldv, nrhs, y, w,
+                                                                    fstage);
+  else
+    k_fwd<false><<<ntasks, kSolveThreads, solve_smem(W, nrhs), st>>>(tasks, sns, ldv, nrhs, y,
+                                                                     w, nullptr);
+}
+
+void launch_fwd_gather(const int32_t* fg_row, const int64_t* fg_ptr, const int32_t* fg_ent,
+                       int64_t nrows, int64_t ldv, int nrhs, const double* fstage, double* y,
+                       cudaStream_t st) {
+  if (nrows <= 0) return;
+  int blocks = (int)std::min<int64_t>((nrows + 127) / 128, 152 * 8);
+  k_fwd_gather<<<blocks, 128, 0, st>>>(fg_row, fg_ptr, fg_ent, nrows, ldv, nrhs, fstage, y);
 }
 
 void launch_bwd(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* diag_tasks,
@@ -237,8 +276,10 @@ void launch_bwd(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* d
 
 int set_solve_kernel_attrs(int W, int max_nrhs) {
   size_t sm = solve_smem(W, max_nrhs);
-  if (cudaFuncSetAttribute(k_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(k_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+          cudaSuccess)
     return CHOL_E_CUDA;
   if (cudaFuncSetAttribute(k_bwd_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
       cudaSuccess)
