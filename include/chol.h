@@ -52,6 +52,8 @@ extern "C" {
 #define CHOL_E_TIMEOUT (-5)   /* a bounded device-side wait expired */
 #define CHOL_E_NODEVICE (-6)  /* no usable CUDA device for a call that needs one */
 #define CHOL_E_STALL (-7)     /* iterative refinement did not converge */
+#define CHOL_E_SCRATCH (-8)   /* chol_solve_noalloc: the solve needs more than the fixed
+                                 scratch area holds */
 
 #define CHOL_HOST 0
 #define CHOL_DEVICE 1
@@ -157,6 +159,24 @@ void chol_free_num(chol_num* num);
  * out, synchronize) or CHOL_DEVICE (stream-ordered, returns after enqueue). */
 int chol_solve(chol_ctx* ctx, const chol_num* num, int64_t nrhs, const double* B,
                int64_t ldb, double* X, int64_t ldx, int where);
+
+/* Device-pointer solve that allocates nothing (the paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they solve, e.g. code
+ * capturing a stream in global capture mode, where cudaMalloc is an error, or a runtime
+ * that owns all device memory).  Same arguments and result as chol_solve with
+ * where = CHOL_DEVICE: B and X are device pointers, the work is enqueued on the context
+ * stream and the call returns without waiting.  The workspace is one fixed array of
+ * chol_noalloc_scratch_bytes() (32 MiB) compiled into the library; every GPU that loads
+ * the library holds it until the process exits.  A solve of k = min(nrhs, 32) columns
+ * needs about 8 * (2 n k + per-level partial sums) bytes; larger requests fail with
+ * CHOL_E_SCRATCH before any work is enqueued.  The first call on a device looks up the
+ * array's device address (with that device current); make that first call before any
+ * stream capture.  All calls share the array and leave its contents behind (nothing in
+ * it needs clearing); calls whose device work overlaps (other streams or contexts on the
+ * same device) race on it and must be ordered by the caller. */
+int chol_solve_noalloc(chol_ctx* ctx, const chol_num* num, int64_t nrhs, const double* B,
+                       int64_t ldb, double* X, int64_t ldx);
+size_t chol_noalloc_scratch_bytes(void);
 
 /* ---- tracing ------------------------------------------------------------------------
  * Per-kernel-kind accounting of the device work a context enqueues: the launch count is

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libchol.so")
 
 CHOL_OK, CHOL_PENDING = 0, 1
 CHOL_E_INVALID, CHOL_E_NOT_SPD, CHOL_E_OOM, CHOL_E_CUDA = -1, -2, -3, -4
-CHOL_E_TIMEOUT, CHOL_E_NODEVICE, CHOL_E_STALL = -5, -6, -7
+CHOL_E_TIMEOUT, CHOL_E_NODEVICE, CHOL_E_STALL, CHOL_E_SCRATCH = -5, -6, -7, -8
 CHOL_HOST, CHOL_DEVICE = 0, 1
 CHOL_ASSEMBLY_ATOMIC, CHOL_ASSEMBLY_OWNER = 0, 1
 CHOL_FP64, CHOL_MIXED = 0, 1
@@ -66,6 +66,8 @@ EXPORTS = {
     "chol_factor_export": (_I, [_P, _P, _P, _P, _P]),
     "chol_free_num": (None, [_P]),
     "chol_solve": (_I, [_P, _P, _I64, _P, _I64, _P, _I64, _I]),
+    "chol_solve_noalloc": (_I, [_P, _P, _I64, _P, _I64, _P, _I64]),
+    "chol_noalloc_scratch_bytes": (C.c_size_t, []),
     "chol_profile_enable": (_I, [_P, _I]),
     "chol_profile_read": (_I, [_P, C.POINTER(chol_prof_entry), _I, C.POINTER(_I)]),
     "chol_profile_reset": (_I, [_P]),
@@ -218,6 +220,22 @@ def chol_solve(ctx, num, B, X=None):
         raise ValueError("torch tensors must live on the context's CUDA device")
     _check(lib().chol_solve(ctx, num, k, pb, n, px, n, CHOL_DEVICE), "chol_solve")
     return X
+
+
+def chol_solve_noalloc(ctx, num, B, X):
+    """Device-pointer solve without any device allocation (torch CUDA tensors laid out as
+    in chol_solve: shape (k, n) contiguous, or (n,) for one right-hand side)."""
+    k, n = (1, B.shape[0]) if B.dim() == 1 else (B.shape[0], B.shape[1])
+    pb, wb = _ptr(B)
+    px, wx = _ptr(X)
+    if wb != CHOL_DEVICE or wx != CHOL_DEVICE:
+        raise ValueError("chol_solve_noalloc takes device tensors")
+    _check(lib().chol_solve_noalloc(ctx, num, k, pb, n, px, n), "chol_solve_noalloc")
+    return X
+
+
+def chol_noalloc_scratch_bytes() -> int:
+    return lib().chol_noalloc_scratch_bytes()
 
 
 def chol_profile_enable(ctx, on: bool) -> None:

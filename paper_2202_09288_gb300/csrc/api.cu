@@ -10,6 +10,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "api_internal.h"
 #include "chol_internal.h"
 #include "kernels.h"
 
@@ -391,6 +392,72 @@ void free_num_buffers(chol_num* f) {
 
 }  // namespace
 
+namespace chol {
+
+// Workspace, in doubles, of a device-pointer solve of k <= 32 right-hand sides: y and w
+// (n k each), the backward partials (max tasks of a level x W x k) and, for owner
+// assembly, the forward staging (max tasks of a level x kSolveRows x k).
+size_t solve_scratch_doubles(const chol_num* f, int64_t k) {
+  const Sym& S = f->sym->S;
+  size_t d = 2 * (size_t)S.n * k + (size_t)f->sym->max_bwd_per_level * S.width_cap * k;
+  if (f->assembly == CHOL_ASSEMBLY_OWNER) d += (size_t)S.max_fwd_per_level * kSolveRows * k;
+  return d;
+}
+
+// The launch sequence of enqueue_solve on caller-provided workspace ws (at least
+// solve_scratch_doubles(f, k) doubles).  Creates no events and allocates nothing.
+int enqueue_solve_ws(chol_ctx* c, const chol_num* f, int k, const double* B, int64_t ldb,
+                     double* X, int64_t ldx, double* ws) {
+  const chol_sym* sym = f->sym;
+  const Sym& S = sym->S;
+  cudaStream_t st = c->stream;
+  const int64_t n = S.n;
+  const int W = S.width_cap;
+  double* y = ws;
+  double* w = y + (size_t)n * k;
+  double* part = w + (size_t)n * k;
+  double* fstage = nullptr;
+  if (f->assembly == CHOL_ASSEMBLY_OWNER)
+    fstage = part + (size_t)sym->max_bwd_per_level * W * k;
+  launch_gather_perm(B, ldb, sym->dev.perm, n, k, y, st);
+  c->prof[kProfPerm].launches++;
+  for (int32_t l = 0; l < S.nlev; l++) {
+    int cnt;
+    const int4* t = task_ptr(sym, kTaskFwd, l, &cnt);
+    launch_fwd(t, cnt, f->d_sn, n, k, W, y, w, fstage, st);
+    if (fstage)
+      launch_fwd_gather(sym->dev.fg_row + S.fg_lvl[l], sym->dev.fg_ptr + S.fg_lvl[l],
+                        sym->dev.fg_ent, S.fg_lvl[l + 1] - S.fg_lvl[l], n, k, fstage, y, st);
+    c->prof[kProfFwd].launches++;
+  }
+  for (int32_t l = S.nlev - 1; l >= 0; l--) {
+    int nb, nd;
+    const int4* tb = task_ptr(sym, kTaskBwd, l, &nb);
+    const int4* td = task_ptr(sym, kTaskPotrf, l, &nd);
+    launch_bwd(tb, nb, S.task_off[kTaskBwd][l], td, nd, f->d_sn, n, k, W, w, part, st);
+    c->prof[kProfBwd].launches++;
+  }
+  launch_scatter_perm(w, sym->dev.perm, n, k, X, ldx, st);
+  c->prof[kProfPerm].launches++;
+  if (cudaGetLastError() != cudaSuccess) return CHOL_E_CUDA;
+  return CHOL_OK;
+}
+
+// Checks the arguments of a device-pointer solve; on success *n_out holds the order.
+int check_solve_args(chol_ctx* c, const chol_num* f, int64_t nrhs, const double* B,
+                     int64_t ldb, const double* X, int64_t ldx, int64_t* n_out) {
+  if (!c || !f || f->ctx != c || nrhs < 0 || !B || !X) return CHOL_E_INVALID;
+  const int64_t n = f->sym->S.n;
+  if (ldb < n || ldx < n || (B == X && ldb != ldx)) return CHOL_E_INVALID;
+  *n_out = n;
+  return CHOL_OK;
+}
+
+cudaStream_t ctx_stream(const chol_ctx* c) { return c->stream; }
+int ctx_device(const chol_ctx* c) { return c->opts.device; }
+
+}  // namespace chol
+
 extern "C" {
 
 int chol_version(void) { return 100; }
@@ -406,6 +473,7 @@ const char* chol_strerror(int s) {
     case CHOL_E_TIMEOUT: return "device-side wait timed out";
     case CHOL_E_NODEVICE: return "no usable CUDA device";
     case CHOL_E_STALL: return "iterative refinement did not converge";
+    case CHOL_E_SCRATCH: return "request exceeds the fixed no-allocation scratch area";
     default: return "unknown status";
   }
 }
