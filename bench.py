@@ -105,9 +105,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def ncu_traffic(kernel: str, flops_per_launch: float):
+    """DRAM bytes per launch of `kernel`: the committed ncu capture's bytes per
+    algorithmic flop (a smaller case of the same kernel) times this launch size's flops,
+    provided the capture was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -116,7 +117,7 @@ def ncu_traffic(kernel: str):
     e = d.get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e["dram_bytes_per_flop"] * flops_per_launch
 
 
 def oracle_sample(name: str):
@@ -297,7 +298,7 @@ def main():
     dom = max(fac_kinds, key=lambda k: fac_kinds[k]["ms"])
     d = prof[dom]
     achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-    traffic = ncu_traffic(dom)
+    traffic = ncu_traffic(dom, d["flops"] / max(d["timed"], 1))
 
     value = world * F / (ms_step * 1e-3) / 1e9
     line = {
