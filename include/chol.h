@@ -131,9 +131,12 @@ int chol_sym_export(const chol_sym* sym, int32_t* parent, int64_t* colcount,
 void chol_free_sym(chol_sym* sym);
 
 /* Numeric factorization of B = P^T A P (Sec. 3, Listing 1, reorganized per level).
- * vals holds A's lower values in the order of the colptr/rowind given to chol_analyze.
- * precision is CHOL_FP64 or CHOL_MIXED.  Allocates the factor on the device and enqueues
- * the factorization; *out is valid at once.  Errors: CHOL_E_INVALID, CHOL_E_OOM,
+ * vals holds A's lower values in the order of the colptr/rowind given to chol_analyze
+ * (copied into the factor).  precision is CHOL_FP64, or CHOL_MIXED: FP32 panels of the
+ * equilibrated matrix S B S, S = diag(B)^{-1/2}, with a diagonal block refactored in FP64
+ * whenever one of its FP32 pivots falls below opts.pivot_tau; use chol_refine to reach
+ * FP64 accuracy with it.  Allocates the factor on the device and enqueues the
+ * factorization; *out is valid at once.  Errors: CHOL_E_INVALID, CHOL_E_OOM,
  * CHOL_E_CUDA; a non-positive pivot surfaces through chol_factor_status(). */
 int chol_factorize(chol_ctx* ctx, const chol_sym* sym, const double* vals, int where,
                    int precision, chol_num** out);
@@ -159,6 +162,29 @@ void chol_free_num(chol_num* num);
  * out, synchronize) or CHOL_DEVICE (stream-ordered, returns after enqueue). */
 int chol_solve(chol_ctx* ctx, const chol_num* num, int64_t nrhs, const double* B,
                int64_t ldb, double* X, int64_t ldx, int where);
+
+/* Result of chol_refine. */
+typedef struct chol_refine_info {
+  int iterations;       /* refinement steps taken, over all passes and column blocks */
+  int fell_back;        /* 1 if refinement with a CHOL_MIXED factor stalled and the FP64
+                           factor (made once, kept with the factor) was used */
+  double residual;      /* final max over columns of ||b - A x||_inf / (||A||_inf ||x||_inf) */
+  int64_t pivot_redos;  /* diagonal blocks of a CHOL_MIXED factor refactored in FP64 */
+} chol_refine_info;
+
+/* Solves A X = B to a relative residual <= tol by iterative refinement (FP64 residual
+ * r = b - A x with the original A, correction d from the factor, x += d).  With a
+ * CHOL_FP64 factor this polishes the direct solution; with a CHOL_MIXED factor (FP32
+ * panels of the equilibrated matrix diag(A)^{-1/2} A diag(A)^{-1/2}) it recovers FP64
+ * accuracy.  Refinement stops when the residual meets tol, or stalls when the largest
+ * residual norm fails to halve twice in a row or after maxit steps; a stalled CHOL_MIXED
+ * factor falls back once to an FP64 factor of the same values (kept until the values
+ * change) and refines again.  B and X must not alias.  where as in chol_solve; the call
+ * synchronizes with the stream (it reads residual norms every step).  Returns CHOL_OK,
+ * CHOL_E_STALL (X holds the last iterate, info->residual its residual), or an error. */
+int chol_refine(chol_ctx* ctx, chol_num* num, int64_t nrhs, const double* B, int64_t ldb,
+                double* X, int64_t ldx, int where, double tol, int maxit,
+                chol_refine_info* info);
 
 /* Device-pointer solve that allocates nothing (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they solve, e.g. code

@@ -43,6 +43,11 @@ class chol_sym_stats(C.Structure):
                 ("flops", C.c_double), ("max_width", C.c_int64), ("max_rows", C.c_int64)]
 
 
+class chol_refine_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("fell_back", C.c_int), ("residual", C.c_double),
+                ("pivot_redos", C.c_int64)]
+
+
 class chol_prof_entry(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double),
                 ("timed", C.c_int64), ("flops", C.c_double), ("bytes", C.c_double)]
@@ -66,6 +71,8 @@ EXPORTS = {
     "chol_factor_export": (_I, [_P, _P, _P, _P, _P]),
     "chol_free_num": (None, [_P]),
     "chol_solve": (_I, [_P, _P, _I64, _P, _I64, _P, _I64, _I]),
+    "chol_refine": (_I, [_P, _P, _I64, _P, _I64, _P, _I64, _I, C.c_double, _I,
+                         C.POINTER(chol_refine_info)]),
     "chol_solve_noalloc": (_I, [_P, _P, _I64, _P, _I64, _P, _I64]),
     "chol_noalloc_scratch_bytes": (C.c_size_t, []),
     "chol_profile_enable": (_I, [_P, _I]),
@@ -222,6 +229,30 @@ def chol_solve(ctx, num, B, X=None):
     return X
 
 
+def chol_refine(ctx, num, B, X=None, tol=1e-12, maxit=10, check=True):
+    """Iterative refinement to ||b - A x||_inf / (||A||_inf ||x||_inf) <= tol.  B: numpy
+    (n,) / (n, k) or a torch CUDA tensor of shape (k, n) / (n,) (as chol_solve).  Returns
+    (X, info dict); raises CholError on failure (CHOL_E_STALL only if check is True)."""
+    info = chol_refine_info()
+    if isinstance(B, np.ndarray):
+        B2 = np.asfortranarray(B.reshape(B.shape[0], -1), dtype=np.float64)
+        n, k = B2.shape
+        X2 = np.zeros((n, k), dtype=np.float64, order="F")
+        rc = lib().chol_refine(ctx, num, k, B2.ctypes.data, n, X2.ctypes.data, n, CHOL_HOST,
+                               tol, maxit, C.byref(info))
+        out = X2.reshape(B.shape) if B.ndim == 1 else X2
+    else:
+        k, n = (1, B.shape[0]) if B.dim() == 1 else (B.shape[0], B.shape[1])
+        out = B.new_empty(B.shape) if X is None else X
+        rc = lib().chol_refine(ctx, num, k, B.data_ptr(), n, out.data_ptr(), n, CHOL_DEVICE,
+                               tol, maxit, C.byref(info))
+    d = {"iterations": info.iterations, "fell_back": bool(info.fell_back),
+         "residual": info.residual, "pivot_redos": info.pivot_redos, "status": rc}
+    if rc != CHOL_OK and (check or rc != CHOL_E_STALL):
+        raise CholError(rc, "chol_refine")
+    return out, d
+
+
 def chol_solve_noalloc(ctx, num, B, X):
     """Device-pointer solve without any device allocation (torch CUDA tensors laid out as
     in chol_solve: shape (k, n) contiguous, or (n,) for one right-hand side)."""
@@ -320,6 +351,9 @@ class Factor:
 
     def solve(self, B, X=None):
         return chol_solve(self.ctx.handle, self.handle, B, X)
+
+    def refine(self, B, X=None, tol=1e-12, maxit=10, check=True):
+        return chol_refine(self.ctx.handle, self.handle, B, X, tol, maxit, check)
 
     def __del__(self):
         try:

@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libchol.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["analyze.cpp", "api.cu", "factor_kernels.cu", "solve_kernels.cu", "noalloc.cu"]
+SOURCES = ["analyze.cpp", "api.cu", "factor_kernels.cu", "solve_kernels.cu", "noalloc.cu",
+           "refine_kernels.cu"]
 
 
 def nvcc() -> str:

@@ -82,6 +82,36 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
       }
   }
 
+  // ---- A as given, and its full symmetric CSR for the residual --------------------------
+  S->a_colptr.assign(colptr, colptr + n + 1);
+  S->a_rowind.assign(rowind, rowind + nnz);
+  {
+    S->csr_ptr.assign(n + 1, 0);
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t p = colptr[j]; p < colptr[j + 1]; p++) {
+        S->csr_ptr[rowind[p] + 1]++;
+        if (rowind[p] != j) S->csr_ptr[j + 1]++;
+      }
+    for (int64_t i = 0; i < n; i++) S->csr_ptr[i + 1] += S->csr_ptr[i];
+    if (S->csr_ptr[n] >= (int64_t(1) << 31) || nnz >= (int64_t(1) << 31)) return CHOL_E_INVALID;
+    S->csr_col.assign(S->csr_ptr[n], 0);
+    S->csr_src.assign(S->csr_ptr[n], 0);
+    std::vector<int64_t> fill(S->csr_ptr.begin(), S->csr_ptr.end() - 1);
+    // visiting columns in order keeps every CSR row sorted by column
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t p = colptr[j]; p < colptr[j + 1]; p++) {
+        const int32_t i = rowind[p];
+        if (i != j) {
+          S->csr_col[fill[j]] = i;  // upper triangle: row j, column i > j (placed later)
+          S->csr_src[fill[j]] = (int32_t)p;
+          fill[j]++;
+        }
+        S->csr_col[fill[i]] = (int32_t)j;
+        S->csr_src[fill[i]] = (int32_t)p;
+        fill[i]++;
+      }
+  }
+
   // ---- elimination tree (Liu, path compression) ---------------------------------------
   S->parent.assign(n, -1);
   {

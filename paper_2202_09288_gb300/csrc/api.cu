@@ -1,8 +1,10 @@
 // api.cu -- the C ABI (include/chol.h): contexts, device memory, upload of the symbolic
-// analysis, and the per-level launch sequence of the factorization and the solves.
+// analysis, the per-level launch sequences of the factorization and the solves, and the
+// iterative-refinement driver.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -21,11 +23,14 @@ using chol::Sym;
 // Kernel kinds of the tracing counters.
 enum ProfKindId {
   kProfAssemble, kProfPotrf, kProfTrsm, kProfSchur64, kProfSchur32, kProfSchur16,
-  kProfAsmOwner, kProfFwd, kProfBwd, kProfPerm, kNumProf
+  kProfAsmOwner, kProfFwd, kProfBwd, kProfPerm, kProfScale, kProfPotrfF32, kProfTrsmF32,
+  kProfSchur64F32, kProfSchur32F32, kProfSchur16F32, kProfRefine, kNumProf
 };
 static const char* kProfNames[kNumProf] = {
-    "assemble", "potrf_f64", "trsm_f64", "schur64_f64", "schur32_f64", "schur16_f64",
-    "assemble_owner", "solve_fwd", "solve_bwd", "solve_perm"};
+    "assemble",    "potrf_f64",   "trsm_f64",    "schur64_f64",  "schur32_f64",
+    "schur16_f64", "assemble_owner", "solve_fwd", "solve_bwd",   "solve_perm",
+    "equilibrate", "potrf_f32",   "trsm_f32",    "schur64_f32",  "schur32_f32",
+    "schur16_f32", "refine"};
 
 struct ProfPending {
   int kind;
@@ -58,6 +63,12 @@ struct DevSym {
   int32_t* col2sn = nullptr;
   int64_t* amap = nullptr;
   int32_t* perm = nullptr;
+  int32_t* iperm = nullptr;
+  int64_t* a_colptr = nullptr;
+  int32_t* a_rowind = nullptr;
+  int64_t* csr_ptr = nullptr;
+  int32_t* csr_col = nullptr;
+  int32_t* csr_src = nullptr;
   int4* tasks[chol::kNumTaskKinds] = {};
   int4* asm_src = nullptr;
   int64_t* fg_ptr = nullptr;
@@ -78,12 +89,14 @@ struct chol_num {
   const chol_sym* sym = nullptr;
   int precision = CHOL_FP64;
   int assembly = CHOL_ASSEMBLY_ATOMIC;
-  void* L = nullptr;           // panels
+  void* L = nullptr;           // panels (double, or float for CHOL_MIXED)
   SnDev* d_sn = nullptr;
   MatDev* d_mat = nullptr;
-  unsigned long long* d_err = nullptr;
-  double* d_vals = nullptr;    // staging of host values
+  unsigned long long* d_err = nullptr;  // [0] failing column + 1, [1] map misses,
+                                        // [2] FP64 pivot redos
+  double* d_vals = nullptr;    // device copy of A's values (assembly and residual)
   double* d_stage = nullptr;   // owner assembly staging
+  double* d_scale = nullptr;   // CHOL_MIXED: equilibration a_jj^{-1/2}
   // solve workspace, grown on demand
   int64_t ws_nrhs = 0;
   double* d_y = nullptr;
@@ -91,9 +104,19 @@ struct chol_num {
   double* d_part = nullptr;
   double* d_bx = nullptr;      // host-call staging of B / X
   double* d_fstage = nullptr;  // owner-ordered forward-solve staging
+  // refinement workspace
+  int64_t rws_nrhs = 0;
+  double* d_rr = nullptr;      // residual
+  double* d_rd = nullptr;      // correction
+  double* d_rb = nullptr;      // host-call staging of B
+  unsigned long long* d_norm = nullptr;  // per-column max |r|, max |x|, and ||A||_inf
+  double anorm = -1.0;         // ||A||_inf of the current values (-1: not computed)
+  chol_num* fb = nullptr;      // FP64 factor made when refinement of a mixed one stalls
 };
 
 namespace {
+
+constexpr int kNormSlots = 2 * 32 + 1;
 
 cudaEvent_t prof_event(chol_ctx* c) {
   cudaEvent_t e = nullptr;
@@ -194,15 +217,10 @@ void free_devsym(chol_sym* s) {
   if (!s->ctx) return;
   chol_ctx* c = s->ctx;
   DevSym& d = s->dev;
-  dev_free(c, d.rows);
-  dev_free(c, d.col2sn);
-  dev_free(c, d.amap);
-  dev_free(c, d.perm);
+  void* ptrs[] = {d.rows, d.col2sn, d.amap, d.perm, d.iperm, d.a_colptr, d.a_rowind,
+                  d.csr_ptr, d.csr_col, d.csr_src, d.asm_src, d.fg_ptr, d.fg_row, d.fg_ent};
+  for (void* p : ptrs) dev_free(c, p);
   for (int k = 0; k < chol::kNumTaskKinds; k++) dev_free(c, d.tasks[k]);
-  dev_free(c, d.asm_src);
-  dev_free(c, d.fg_ptr);
-  dev_free(c, d.fg_row);
-  dev_free(c, d.fg_ent);
   d = DevSym();
   c->syms.erase(s);
   s->ctx = nullptr;
@@ -218,7 +236,16 @@ int ensure_uploaded(chol_ctx* c, chol_sym* s) {
   s->ctx = c;
   c->syms.insert(s);
   if ((rc = upload(c, &d.rows, S.rows, &acc)) || (rc = upload(c, &d.col2sn, S.col2sn, &acc)) ||
-      (rc = upload(c, &d.amap, S.amap, &acc)) || (rc = upload(c, &d.perm, S.perm, &acc))) {
+      (rc = upload(c, &d.amap, S.amap, &acc)) || (rc = upload(c, &d.perm, S.perm, &acc)) ||
+      (rc = upload(c, &d.iperm, S.iperm, &acc)) ||
+      (rc = upload(c, &d.a_colptr, S.a_colptr, &acc)) ||
+      (rc = upload(c, &d.a_rowind, S.a_rowind, &acc)) ||
+      (rc = upload(c, &d.csr_ptr, S.csr_ptr, &acc)) ||
+      (rc = upload(c, &d.csr_col, S.csr_col, &acc)) ||
+      (rc = upload(c, &d.csr_src, S.csr_src, &acc)) ||
+      (rc = upload(c, reinterpret_cast<int32_t**>(&d.asm_src), S.asm_src, &acc)) ||
+      (rc = upload(c, &d.fg_ptr, S.fg_ptr, &acc)) || (rc = upload(c, &d.fg_row, S.fg_row, &acc)) ||
+      (rc = upload(c, &d.fg_ent, S.fg_ent, &acc))) {
     free_devsym(s);
     return rc;
   }
@@ -227,12 +254,6 @@ int ensure_uploaded(chol_ctx* c, chol_sym* s) {
       free_devsym(s);
       return rc;
     }
-  if ((rc = upload(c, reinterpret_cast<int32_t**>(&d.asm_src), S.asm_src, &acc)) ||
-      (rc = upload(c, &d.fg_ptr, S.fg_ptr, &acc)) || (rc = upload(c, &d.fg_row, S.fg_row, &acc)) ||
-      (rc = upload(c, &d.fg_ent, S.fg_ent, &acc))) {
-    free_devsym(s);
-    return rc;
-  }
   d.bytes = acc;
   d.device = c->opts.device;
   int64_t mb = 0;
@@ -259,45 +280,60 @@ const int4* task_ptr(const chol_sym* s, int kind, int32_t level, int* count) {
   return s->dev.tasks[kind] + a;
 }
 
-int enqueue_factor(chol_num* f, const double* vals_dev) {
+// Enqueues the numeric factorization of the values in f->d_vals.
+int enqueue_factor(chol_num* f) {
   chol_ctx* c = f->ctx;
   const chol_sym* sym = f->sym;
   const Sym& S = sym->S;
   cudaStream_t st = c->stream;
-  const size_t esz = sizeof(double);
+  const bool f32 = f->precision == CHOL_MIXED;
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
   // err[0] = smallest failing column + 1, kept by atomicMin: starts at all ones (none);
-  // err[1] = relative-map misses: starts at 0
+  // err[1] = relative-map misses, err[2] = FP64 pivot redos: start at 0
   CK(cudaMemsetAsync(f->d_err, 0xff, sizeof(unsigned long long), st));
-  CK(cudaMemsetAsync(f->d_err + 1, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(f->d_err + 1, 0, 3 * sizeof(unsigned long long), st));
+  f->anorm = -1.0;
   prof_begin(c);
   CK(cudaMemsetAsync(f->L, 0, (size_t)S.l_storage * esz, st));
-  chol::launch_assemble(vals_dev, sym->dev.amap, S.nnz_a, f->L, false, st);
-  prof_end(c, kProfAssemble, 0.0, (double)S.l_storage * esz + 16.0 * S.nnz_a + 8.0 * S.nnz_a);
+  if (f32) {
+    chol::launch_diag_scale(sym->dev.a_colptr, sym->dev.a_rowind, f->d_vals, sym->dev.iperm,
+                            S.n, f->d_scale, f->d_err, st);
+    chol::launch_assemble_scaled(sym->dev.a_colptr, sym->dev.a_rowind, f->d_vals,
+                                 sym->dev.amap, f->d_scale, S.n, (float*)f->L, st);
+    prof_end(c, kProfScale, 0.0, (double)S.l_storage * esz + 24.0 * S.nnz_a);
+  } else {
+    chol::launch_assemble(f->d_vals, sym->dev.amap, S.nnz_a, f->L, false, st);
+    prof_end(c, kProfAssemble, 0.0, (double)S.l_storage * esz + 16.0 * S.nnz_a + 8.0 * S.nnz_a);
+  }
   const bool owner = f->assembly == CHOL_ASSEMBLY_OWNER;
+  const float tau = (float)(c->opts.pivot_tau > 0 ? c->opts.pivot_tau : 1e-5);
+  const int kp = f32 ? kProfPotrfF32 : kProfPotrf, kt = f32 ? kProfTrsmF32 : kProfTrsm;
+  const int ks = f32 ? kProfSchur64F32 : kProfSchur64;
   for (int32_t l = 0; l < S.nlev; l++) {
     int cnt;
     const int4* t = task_ptr(sym, chol::kTaskPotrf, l, &cnt);
     prof_begin(c);
-    chol::launch_potrf(t, cnt, f->d_sn, f->d_mat, (int)S.max_width, st);
-    prof_end(c, kProfPotrf, S.lvl_flops[chol::kTaskPotrf][l], 0.0);
+    chol::launch_potrf(t, cnt, f->d_sn, f->d_mat, (int)S.max_width, f32, tau, st);
+    prof_end(c, kp, S.lvl_flops[chol::kTaskPotrf][l], 0.0);
     t = task_ptr(sym, chol::kTaskTrsm, l, &cnt);
     if (cnt > 0) {
       prof_begin(c);
-      chol::launch_trsm(t, cnt, f->d_sn, (int)S.max_width, st);
-      prof_end(c, kProfTrsm, S.lvl_flops[chol::kTaskTrsm][l], 0.0);
+      chol::launch_trsm(t, cnt, f->d_sn, (int)S.max_width, f32, st);
+      prof_end(c, kt, S.lvl_flops[chol::kTaskTrsm][l], 0.0);
     }
     for (int cls = 0; cls < chol::kNumTileClasses; cls++) {
       t = task_ptr(sym, chol::kTaskSchur64 + cls, l, &cnt);
       if (cnt <= 0) continue;
       prof_begin(c);
-      chol::launch_schur(cls, t, cnt, f->d_sn, f->d_mat, f->d_stage, owner, st);
-      prof_end(c, kProfSchur64 + cls, S.lvl_flops[chol::kTaskSchur64 + cls][l], 0.0);
+      chol::launch_schur(cls, t, cnt, f->d_sn, f->d_mat, f->d_stage, owner, f32, st);
+      prof_end(c, ks + cls, S.lvl_flops[chol::kTaskSchur64 + cls][l], 0.0);
     }
     if (owner) {
       t = task_ptr(sym, chol::kTaskAsm, l, &cnt);
       if (cnt > 0) {
         prof_begin(c);
-        chol::launch_assemble_owner(t, cnt, sym->dev.asm_src, f->d_sn, f->d_mat, f->d_stage, st);
+        chol::launch_assemble_owner(t, cnt, sym->dev.asm_src, f->d_sn, f->d_mat, f->d_stage, f32,
+                                    st);
         prof_end(c, kProfAsmOwner, 0.0, 0.0);
       }
     }
@@ -341,20 +377,22 @@ int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X
   cudaStream_t st = c->stream;
   const int64_t n = S.n;
   const int W = S.width_cap;
+  const bool f32 = f->precision == CHOL_MIXED;
+  const double* scale = f32 ? f->d_scale : nullptr;
   const double vec = 8.0 * n * nrhs;
   prof_begin(c);
-  chol::launch_gather_perm(B, ldb, sym->dev.perm, n, nrhs, f->d_y, st);
+  chol::launch_gather_perm(B, ldb, sym->dev.perm, scale, n, nrhs, f->d_y, st);
   prof_end(c, kProfPerm, 0.0, 2 * vec + 4.0 * n);
   for (int32_t l = 0; l < S.nlev; l++) {
     int cnt;
     const int4* t = task_ptr(sym, chol::kTaskFwd, l, &cnt);
     prof_begin(c);
-    chol::launch_fwd(t, cnt, f->d_sn, n, nrhs, W, f->d_y, f->d_w, f->d_fstage, st);
+    chol::launch_fwd(t, cnt, f->d_sn, n, nrhs, W, f->d_y, f->d_w, f->d_fstage, f32, st);
     if (f->d_fstage)
       chol::launch_fwd_gather(sym->dev.fg_row + S.fg_lvl[l], sym->dev.fg_ptr + S.fg_lvl[l],
                               sym->dev.fg_ent, S.fg_lvl[l + 1] - S.fg_lvl[l], n, nrhs,
                               f->d_fstage, f->d_y, st);
-    prof_end(c, kProfFwd, 0.0, S.lvl_panel_bytes[l]);
+    prof_end(c, kProfFwd, 0.0, S.lvl_panel_bytes[l] * (f32 ? 0.5 : 1.0));
   }
   for (int32_t l = S.nlev - 1; l >= 0; l--) {
     int nb, nd;
@@ -362,11 +400,11 @@ int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X
     const int4* td = task_ptr(sym, chol::kTaskPotrf, l, &nd);
     prof_begin(c);
     chol::launch_bwd(tb, nb, S.task_off[chol::kTaskBwd][l], td, nd, f->d_sn, n, nrhs, W,
-                     f->d_w, f->d_part, st);
-    prof_end(c, kProfBwd, 0.0, S.lvl_panel_bytes[l]);
+                     f->d_w, f->d_part, f32, st);
+    prof_end(c, kProfBwd, 0.0, S.lvl_panel_bytes[l] * (f32 ? 0.5 : 1.0));
   }
   prof_begin(c);
-  chol::launch_scatter_perm(f->d_w, sym->dev.perm, n, nrhs, X, ldx, st);
+  chol::launch_scatter_perm(f->d_w, sym->dev.perm, scale, n, nrhs, X, ldx, st);
   prof_end(c, kProfPerm, 0.0, 2 * vec + 4.0 * n);
   CK(cudaGetLastError());
   return CHOL_OK;
@@ -375,19 +413,162 @@ int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X
 void free_num_buffers(chol_num* f) {
   chol_ctx* c = f->ctx;
   if (!c) return;
-  dev_free(c, f->L);
-  dev_free(c, f->d_sn);
-  dev_free(c, f->d_mat);
-  dev_free(c, f->d_err);
-  dev_free(c, f->d_vals);
-  dev_free(c, f->d_stage);
-  dev_free(c, f->d_y);
-  dev_free(c, f->d_w);
-  dev_free(c, f->d_bx);
-  dev_free(c, f->d_part);
-  dev_free(c, f->d_fstage);
+  void* ptrs[] = {f->L, f->d_sn, f->d_mat, f->d_err, f->d_vals, f->d_stage, f->d_scale,
+                  f->d_y, f->d_w, f->d_bx, f->d_part, f->d_fstage, f->d_rr, f->d_rd,
+                  f->d_rb, f->d_norm};
+  for (void* p : ptrs) dev_free(c, p);
   c->nums.erase(f);
   f->ctx = nullptr;
+}
+
+// Allocates a factor and enqueues its numeric factorization of vals.
+int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int precision,
+                int assembly, chol_num** out) {
+  const Sym& S = sym->S;
+  chol_num* f = new (std::nothrow) chol_num();
+  if (!f) return CHOL_E_OOM;
+  f->ctx = c;
+  c->nums.insert(f);
+  f->sym = sym;
+  f->precision = precision;
+  f->assembly = assembly;
+  const bool f32 = precision == CHOL_MIXED;
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  int rc;
+  if ((rc = dev_alloc(c, &f->L, (size_t)S.l_storage * esz)) ||
+      (rc = dev_alloc(c, (void**)&f->d_sn, (size_t)S.ns * sizeof(SnDev))) ||
+      (rc = dev_alloc(c, (void**)&f->d_mat, sizeof(MatDev))) ||
+      (rc = dev_alloc(c, (void**)&f->d_err, 4 * sizeof(unsigned long long))) ||
+      (rc = dev_alloc(c, (void**)&f->d_vals, (size_t)S.nnz_a * 8)) ||
+      (f32 && (rc = dev_alloc(c, (void**)&f->d_scale, (size_t)S.n * 8))) ||
+      (assembly == CHOL_ASSEMBLY_OWNER &&
+       (rc = dev_alloc(c, (void**)&f->d_stage, (size_t)S.stage_elems * 8)))) {
+    free_num_buffers(f);
+    delete f;
+    return rc;
+  }
+  std::vector<SnDev> sn(S.ns);
+  for (int32_t s = 0; s < S.ns; s++) {
+    sn[s].L = (char*)f->L + (size_t)S.sn_valptr[s] * esz;
+    sn[s].rows = sym->dev.rows + S.sn_rowptr[s];
+    sn[s].n = S.sn_start[s + 1] - S.sn_start[s];
+    sn[s].m = S.sn_m[s];
+    sn[s].col0 = S.sn_start[s];
+    sn[s].mat = 0;
+    sn[s].ustage = S.sn_ustage[s];
+  }
+  MatDev md;
+  md.col2sn = sym->dev.col2sn;
+  md.sn_base = 0;
+  md.pad0 = 0;
+  md.err = f->d_err;
+  if (cudaMemcpyAsync(f->d_sn, sn.data(), sn.size() * sizeof(SnDev), cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(f->d_mat, &md, sizeof(md), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    free_num_buffers(f);
+    delete f;
+    return CHOL_E_CUDA;
+  }
+  *out = f;
+  return chol_refactorize(c, f, vals, where);
+}
+
+int ensure_refine_ws(chol_num* f, int64_t k) {
+  if (f->rws_nrhs >= k) return CHOL_OK;
+  chol_ctx* c = f->ctx;
+  const int64_t n = f->sym->S.n;
+  dev_free(c, f->d_rr);
+  dev_free(c, f->d_rd);
+  dev_free(c, f->d_rb);
+  f->d_rr = f->d_rd = f->d_rb = nullptr;
+  f->rws_nrhs = 0;
+  int rc;
+  if (!f->d_norm && (rc = dev_alloc(c, (void**)&f->d_norm, kNormSlots * 8))) return rc;
+  if ((rc = dev_alloc(c, (void**)&f->d_rr, (size_t)n * k * 8)) ||
+      (rc = dev_alloc(c, (void**)&f->d_rd, (size_t)n * k * 8)) ||
+      (rc = dev_alloc(c, (void**)&f->d_rb, (size_t)n * k * 8)))
+    return rc;
+  f->rws_nrhs = k;
+  return CHOL_OK;
+}
+
+int compute_anorm(chol_num* f) {
+  if (f->anorm >= 0.0) return CHOL_OK;
+  chol_ctx* c = f->ctx;
+  const chol_sym* sym = f->sym;
+  unsigned long long* slot = f->d_norm + 2 * 32;
+  CK(cudaMemsetAsync(slot, 0, 8, c->stream));
+  prof_begin(c);
+  chol::launch_anorm(sym->dev.csr_ptr, sym->dev.csr_src, f->d_vals, sym->S.n, slot, c->stream);
+  prof_end(c, kProfRefine, 0.0, 0.0);
+  unsigned long long v = 0;
+  CK(cudaMemcpyAsync(&v, slot, 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  double a;
+  memcpy(&a, &v, 8);
+  f->anorm = a;
+  return CHOL_OK;
+}
+
+// Residual R = B - A X of k columns, and its relative size; *rmax = max_c ||r_c||_inf.
+int residual_norms(chol_num* f, int k, const double* B, int64_t ldb, const double* X,
+                   int64_t ldx, double* rel, double* rmax) {
+  chol_ctx* c = f->ctx;
+  const chol_sym* sym = f->sym;
+  const int64_t n = sym->S.n;
+  CK(cudaMemsetAsync(f->d_norm, 0, 2 * 32 * 8, c->stream));
+  prof_begin(c);
+  chol::launch_residual(sym->dev.csr_ptr, sym->dev.csr_col, sym->dev.csr_src, f->d_vals, n, k, X,
+                        ldx, B, ldb, f->d_rr, n, c->stream);
+  chol::launch_absmax(f->d_rr, n, n, k, f->d_norm, c->stream);
+  chol::launch_absmax(X, ldx, n, k, f->d_norm + 32, c->stream);
+  prof_end(c, kProfRefine, 2.0 * (double)sym->S.csr_ptr[n] * k,
+           (12.0 * (double)sym->S.csr_ptr[n] + 24.0 * n) * k);
+  unsigned long long h[64];
+  CK(cudaMemcpyAsync(h, f->d_norm, 64 * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  double worst = 0.0, rm = 0.0;
+  for (int j = 0; j < k; j++) {
+    double r, x;
+    memcpy(&r, &h[j], 8);
+    memcpy(&x, &h[32 + j], 8);
+    const double v = (f->anorm > 0 && x > 0) ? r / (f->anorm * x) : r;
+    worst = std::max(worst, v);
+    rm = std::max(rm, r);
+  }
+  *rel = worst;
+  *rmax = rm;
+  return CHOL_OK;
+}
+
+// Refinement of k <= 32 device columns with factor g (f holds A's values and workspace).
+// Returns CHOL_OK when the residual meets tol, CHOL_E_STALL when it stalls.
+int refine_pass(chol_num* f, chol_num* g, int k, const double* B, int64_t ldb, double* X,
+                int64_t ldx, double tol, int maxit, chol_refine_info* info) {
+  chol_ctx* c = f->ctx;
+  const int64_t n = f->sym->S.n;
+  int rc;
+  if ((rc = ensure_solve_ws(g, k))) return rc;
+  if ((rc = enqueue_solve(g, k, B, ldb, X, ldx))) return rc;
+  double prev = INFINITY, rel = 0, rmax = 0;
+  int stall = 0;
+  for (int it = 0;; it++) {
+    if ((rc = residual_norms(f, k, B, ldb, X, ldx, &rel, &rmax))) return rc;
+    info->residual = rel;
+    if (rel <= tol) return CHOL_OK;
+    if (it >= maxit) return CHOL_E_STALL;
+    stall = rmax > 0.5 * prev ? stall + 1 : 0;
+    if (stall >= 2) return CHOL_E_STALL;
+    prev = rmax;
+    if ((rc = enqueue_solve(g, k, f->d_rr, n, f->d_rd, n))) return rc;
+    prof_begin(c);
+    chol::launch_axpy(X, ldx, f->d_rd, n, n, k, c->stream);
+    prof_end(c, kProfRefine, (double)n * k, 24.0 * n * k);
+    info->iterations++;
+  }
 }
 
 }  // namespace
@@ -413,18 +594,20 @@ int enqueue_solve_ws(chol_ctx* c, const chol_num* f, int k, const double* B, int
   cudaStream_t st = c->stream;
   const int64_t n = S.n;
   const int W = S.width_cap;
+  const bool f32 = f->precision == CHOL_MIXED;
+  const double* scale = f32 ? f->d_scale : nullptr;
   double* y = ws;
   double* w = y + (size_t)n * k;
   double* part = w + (size_t)n * k;
   double* fstage = nullptr;
   if (f->assembly == CHOL_ASSEMBLY_OWNER)
     fstage = part + (size_t)sym->max_bwd_per_level * W * k;
-  launch_gather_perm(B, ldb, sym->dev.perm, n, k, y, st);
+  launch_gather_perm(B, ldb, sym->dev.perm, scale, n, k, y, st);
   c->prof[kProfPerm].launches++;
   for (int32_t l = 0; l < S.nlev; l++) {
     int cnt;
     const int4* t = task_ptr(sym, kTaskFwd, l, &cnt);
-    launch_fwd(t, cnt, f->d_sn, n, k, W, y, w, fstage, st);
+    launch_fwd(t, cnt, f->d_sn, n, k, W, y, w, fstage, f32, st);
     if (fstage)
       launch_fwd_gather(sym->dev.fg_row + S.fg_lvl[l], sym->dev.fg_ptr + S.fg_lvl[l],
                         sym->dev.fg_ent, S.fg_lvl[l + 1] - S.fg_lvl[l], n, k, fstage, y, st);
@@ -434,10 +617,10 @@ int enqueue_solve_ws(chol_ctx* c, const chol_num* f, int k, const double* B, int
     int nb, nd;
     const int4* tb = task_ptr(sym, kTaskBwd, l, &nb);
     const int4* td = task_ptr(sym, kTaskPotrf, l, &nd);
-    launch_bwd(tb, nb, S.task_off[kTaskBwd][l], td, nd, f->d_sn, n, k, W, w, part, st);
+    launch_bwd(tb, nb, S.task_off[kTaskBwd][l], td, nd, f->d_sn, n, k, W, w, part, f32, st);
     c->prof[kProfBwd].launches++;
   }
-  launch_scatter_perm(w, sym->dev.perm, n, k, X, ldx, st);
+  launch_scatter_perm(w, sym->dev.perm, scale, n, k, X, ldx, st);
   c->prof[kProfPerm].launches++;
   if (cudaGetLastError() != cudaSuccess) return CHOL_E_CUDA;
   return CHOL_OK;
@@ -606,59 +789,14 @@ int chol_factorize(chol_ctx* c, const chol_sym* sym_c, const double* vals, int w
                    int precision, chol_num** out) {
   if (!c || !sym_c || !out || (!vals && sym_c->S.nnz_a > 0)) return CHOL_E_INVALID;
   if (where != CHOL_HOST && where != CHOL_DEVICE) return CHOL_E_INVALID;
-  if (precision != CHOL_FP64) return CHOL_E_INVALID;
+  if (precision != CHOL_FP64 && precision != CHOL_MIXED) return CHOL_E_INVALID;
   *out = nullptr;
   chol_sym* sym = const_cast<chol_sym*>(sym_c);
   if (cudaSetDevice(c->opts.device) != cudaSuccess) return CHOL_E_NODEVICE;
   int rc = ensure_uploaded(c, sym);
   if (rc) return rc;
   if ((rc = ensure_attrs(c))) return rc;
-  const Sym& S = sym->S;
-  chol_num* f = new (std::nothrow) chol_num();
-  if (!f) return CHOL_E_OOM;
-  f->ctx = c;
-  c->nums.insert(f);
-  f->sym = sym;
-  f->precision = precision;
-  f->assembly = c->opts.assembly;
-  if ((rc = dev_alloc(c, &f->L, (size_t)S.l_storage * 8)) ||
-      (rc = dev_alloc(c, (void**)&f->d_sn, (size_t)S.ns * sizeof(SnDev))) ||
-      (rc = dev_alloc(c, (void**)&f->d_mat, sizeof(MatDev))) ||
-      (rc = dev_alloc(c, (void**)&f->d_err, 16)) ||
-      (rc = dev_alloc(c, (void**)&f->d_vals, (size_t)S.nnz_a * 8)) ||
-      (f->assembly == CHOL_ASSEMBLY_OWNER &&
-       (rc = dev_alloc(c, (void**)&f->d_stage, (size_t)S.stage_elems * 8)))) {
-    free_num_buffers(f);
-    delete f;
-    return rc;
-  }
-  std::vector<SnDev> sn(S.ns);
-  for (int32_t s = 0; s < S.ns; s++) {
-    sn[s].L = (double*)f->L + S.sn_valptr[s];
-    sn[s].rows = sym->dev.rows + S.sn_rowptr[s];
-    sn[s].n = S.sn_start[s + 1] - S.sn_start[s];
-    sn[s].m = S.sn_m[s];
-    sn[s].col0 = S.sn_start[s];
-    sn[s].mat = 0;
-    sn[s].ustage = S.sn_ustage[s];
-  }
-  MatDev md;
-  md.col2sn = sym->dev.col2sn;
-  md.sn_base = 0;
-  md.pad0 = 0;
-  md.err = f->d_err;
-  if (cudaMemcpyAsync(f->d_sn, sn.data(), sn.size() * sizeof(SnDev), cudaMemcpyHostToDevice,
-                      c->stream) != cudaSuccess ||
-      cudaMemcpyAsync(f->d_mat, &md, sizeof(md), cudaMemcpyHostToDevice, c->stream) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(c->stream) != cudaSuccess) {
-    cudaGetLastError();
-    free_num_buffers(f);
-    delete f;
-    return CHOL_E_CUDA;
-  }
-  *out = f;
-  return chol_refactorize(c, f, vals, where);
+  return make_factor(c, sym, vals, where, precision, c->opts.assembly, out);
 }
 
 int chol_refactorize(chol_ctx* c, chol_num* f, const double* vals, int where) {
@@ -667,18 +805,21 @@ int chol_refactorize(chol_ctx* c, chol_num* f, const double* vals, int where) {
   const Sym& S = f->sym->S;
   if (!vals && S.nnz_a > 0) return CHOL_E_INVALID;
   if (cudaSetDevice(c->opts.device) != cudaSuccess) return CHOL_E_NODEVICE;
-  const double* v = vals;
-  if (where == CHOL_HOST) {
-    CK(cudaMemcpyAsync(f->d_vals, vals, (size_t)S.nnz_a * 8, cudaMemcpyHostToDevice, c->stream));
-    v = f->d_vals;
+  if (S.nnz_a > 0)
+    CK(cudaMemcpyAsync(f->d_vals, vals, (size_t)S.nnz_a * 8,
+                       where == CHOL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       c->stream));
+  if (f->fb) {  // values changed: a fallback factor of the old values is stale
+    chol_free_num(f->fb);
+    f->fb = nullptr;
   }
-  return enqueue_factor(f, v);
+  return enqueue_factor(f);
 }
 
 int chol_factor_status(chol_ctx* c, const chol_num* f, int64_t* bad_col) {
   if (!c || !f || f->ctx != c) return CHOL_E_INVALID;
-  unsigned long long ee[2] = {0, 0};
-  CK(cudaMemcpyAsync(ee, f->d_err, 16, cudaMemcpyDeviceToHost, c->stream));
+  unsigned long long ee[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(ee, f->d_err, 24, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaGetLastError());
   if (ee[1]) return CHOL_E_INVALID;  // internal relative-map inconsistency
@@ -694,14 +835,18 @@ int chol_factor_status(chol_ctx* c, const chol_num* f, int64_t* bad_col) {
 int chol_factor_export(chol_ctx* c, const chol_num* f, int64_t* Lp, int32_t* Li, double* Lx) {
   if (!c || !f || f->ctx != c) return CHOL_E_INVALID;
   const Sym& S = f->sym->S;
+  const bool f32 = f->precision == CHOL_MIXED;
   std::vector<double> panels;
+  std::vector<float> panels32;
   if (Lx) {
     try {
-      panels.resize((size_t)S.l_storage);
+      if (f32) panels32.resize((size_t)S.l_storage);
+      else panels.resize((size_t)S.l_storage);
     } catch (...) {
       return CHOL_E_OOM;
     }
-    CK(cudaMemcpyAsync(panels.data(), f->L, (size_t)S.l_storage * 8, cudaMemcpyDeviceToHost,
+    void* dst = f32 ? (void*)panels32.data() : (void*)panels.data();
+    CK(cudaMemcpyAsync(dst, f->L, (size_t)S.l_storage * (f32 ? 4 : 8), cudaMemcpyDeviceToHost,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
@@ -713,7 +858,10 @@ int chol_factor_export(chol_ctx* c, const chol_num* f, int64_t* Lp, int32_t* Li,
     for (int32_t jj = 0; jj < n; jj++) {
       for (int32_t r = jj; r < m; r++) {
         if (Li) Li[pos] = rows[r];
-        if (Lx) Lx[pos] = panels[S.sn_valptr[s] + (int64_t)jj * m + r];
+        if (Lx) {
+          const int64_t q = S.sn_valptr[s] + (int64_t)jj * m + r;
+          Lx[pos] = f32 ? (double)panels32[q] : panels[q];
+        }
         pos++;
       }
       if (Lp) Lp[S.sn_start[s] + jj + 1] = pos;
@@ -724,6 +872,7 @@ int chol_factor_export(chol_ctx* c, const chol_num* f, int64_t* Lp, int32_t* Li,
 
 void chol_free_num(chol_num* f) {
   if (!f) return;
+  if (f->fb) chol_free_num(f->fb);
   if (f->ctx) {
     cudaSetDevice(f->ctx->opts.device);
     free_num_buffers(f);
@@ -756,6 +905,71 @@ int chol_solve(chol_ctx* c, const chol_num* fc, int64_t nrhs, const double* B, i
     }
   }
   if (where == CHOL_HOST) CK(cudaStreamSynchronize(c->stream));
+  return CHOL_OK;
+}
+
+int chol_refine(chol_ctx* c, chol_num* f, int64_t nrhs, const double* B, int64_t ldb,
+                double* X, int64_t ldx, int where, double tol, int maxit,
+                chol_refine_info* info) {
+  chol_refine_info local;
+  if (!info) info = &local;
+  memset(info, 0, sizeof(*info));
+  if (!c || !f || f->ctx != c || nrhs < 0 || !B || !X || B == X || tol < 0 || maxit < 0)
+    return CHOL_E_INVALID;
+  const int64_t n = f->sym->S.n;
+  if (ldb < n || ldx < n || (where != CHOL_HOST && where != CHOL_DEVICE)) return CHOL_E_INVALID;
+  if (nrhs == 0 || n == 0) return CHOL_OK;
+  if (cudaSetDevice(c->opts.device) != cudaSuccess) return CHOL_E_NODEVICE;
+  int rc = chol_factor_status(c, f, nullptr);
+  if (rc) return rc;
+  unsigned long long redo = 0;
+  CK(cudaMemcpy(&redo, f->d_err + 2, 8, cudaMemcpyDeviceToHost));
+  info->pivot_redos = (int64_t)redo;
+  const int64_t chunk = std::min<int64_t>(nrhs, 32);
+  if ((rc = ensure_refine_ws(f, chunk)) || (rc = ensure_solve_ws(f, chunk)) ||
+      (rc = compute_anorm(f)))
+    return rc;
+  double worst = 0.0;
+  for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
+    const int k = (int)std::min<int64_t>(chunk, nrhs - c0);
+    const double* Bd = B + c0 * ldb;
+    double* Xd = X + c0 * ldx;
+    int64_t lb = ldb, lx = ldx;
+    if (where == CHOL_HOST) {
+      CK(cudaMemcpy2DAsync(f->d_rb, n * 8, Bd, ldb * 8, n * 8, k, cudaMemcpyHostToDevice,
+                           c->stream));
+      Bd = f->d_rb;
+      Xd = f->d_bx;
+      lb = lx = n;
+    }
+    chol_refine_info part;
+    memset(&part, 0, sizeof(part));
+    rc = f->fb ? CHOL_E_STALL : refine_pass(f, f, k, Bd, lb, Xd, lx, tol, maxit, &part);
+    if (rc == CHOL_E_STALL && f->precision == CHOL_MIXED) {
+      // the mixed factor cannot deliver tol: factor A in FP64 once and refine with it
+      if (!f->fb) {
+        if ((rc = make_factor(c, const_cast<chol_sym*>(f->sym), f->d_vals, CHOL_DEVICE,
+                              CHOL_FP64, f->assembly, &f->fb)))
+          return rc;
+        if ((rc = chol_factor_status(c, f->fb, nullptr))) return rc;
+      }
+      info->fell_back = 1;
+      rc = refine_pass(f, f->fb, k, Bd, lb, Xd, lx, tol, maxit, &part);
+    }
+    info->iterations += part.iterations;
+    worst = std::max(worst, part.residual);
+    if (where == CHOL_HOST)
+      CK(cudaMemcpy2DAsync(X + c0 * ldx, ldx * 8, f->d_bx, n * 8, n * 8, k,
+                           cudaMemcpyDeviceToHost, c->stream));
+    if (rc && rc != CHOL_E_STALL) return rc;
+    if (rc == CHOL_E_STALL) {
+      info->residual = worst;
+      CK(cudaStreamSynchronize(c->stream));
+      return CHOL_E_STALL;
+    }
+  }
+  info->residual = worst;
+  CK(cudaStreamSynchronize(c->stream));
   return CHOL_OK;
 }
 

@@ -58,6 +58,12 @@ struct Sym {
   int64_t n = 0, nnz_a = 0;
   int width_cap = 64;
   std::vector<int32_t> perm, iperm;
+  std::vector<int64_t> a_colptr;   // A's lower CSC as given (original numbering)
+  std::vector<int32_t> a_rowind;
+  // full symmetric A in CSR form for the FP64 residual: row i holds columns csr_col[e]
+  // with values vals[csr_src[e]] for e in [csr_ptr[i], csr_ptr[i+1])
+  std::vector<int64_t> csr_ptr;
+  std::vector<int32_t> csr_col, csr_src;
   std::vector<int32_t> parent;
   std::vector<int64_t> colcount;
   int32_t ns = 0;

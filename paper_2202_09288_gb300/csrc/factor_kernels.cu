@@ -137,15 +137,75 @@ __global__ void __launch_bounds__(kTrsmRows) k_trsm(const int4* __restrict__ tas
   }
 }
 
-// ---- Schur update tiles ---------------------------------------------------------------------
-// Task {s, i0, k0}: the T x T tile of U_s = L21 L21^T at rows i0.., columns k0.. (offsets
-// into the off-diagonal rows of s), computed with FP64 m8n8k4 DMMA.  Then each entry
-// U(i, k), i >= k, is subtracted from the target panel t owning column rows[k]: column
-// rows[k] - col0(t), row position of rows[i] inside t's row list (the relative map,
-// found by binary search in t's sorted rows once per tile row and target).
+// Applies a finished T x T tile of U_s (in shared memory, Cs[kk * (TILE + 1) + ii], rows
+// i0 + ii and columns k0 + kk of the off-diagonal part of s): each entry U(i, k), i >= k,
+// is subtracted from the target panel t owning column rows[k] -- column rows[k] - col0(t),
+// row position of rows[i] inside t's row list (the relative map, found by binary search in
+// t's sorted rows once per tile row and target).
 //   OWNER == false: atomicAdd into the panel.
 //   OWNER == true : the tile is written to the level staging buffer (U_s column-major,
 //                   ld u) and k_assemble_owner applies it later in a fixed order.
+template <typename T, int TILE, int THREADS, bool OWNER>
+__device__ __forceinline__ void schur_tile_epilogue(const T* Cs, const SnDev& d, int i0, int k0,
+                                                    const SnDev* __restrict__ sns,
+                                                    const MatDev* __restrict__ mats,
+                                                    T* __restrict__ stage) {
+  __shared__ int run_start[TILE + 1];
+  __shared__ int run_t[TILE];
+  __shared__ int nruns;
+  __shared__ int relpos[TILE];
+  const int tid = threadIdx.x;
+  const int n = d.n, u = d.m - d.n;
+  const int32_t* rows = d.rows + n;  // off-diagonal rows of s
+  const int ilim = min(TILE, u - i0), klim = min(TILE, u - k0);
+  if (OWNER) {
+    T* U = stage + d.ustage;
+    for (int idx = tid; idx < klim * TILE; idx += THREADS) {
+      const int kk = idx / TILE, ii = idx - kk * TILE;
+      if (ii < ilim && i0 + ii >= k0 + kk)
+        U[(int64_t)(k0 + kk) * u + i0 + ii] = Cs[kk * (TILE + 1) + ii];
+    }
+    return;
+  }
+  const MatDev md = mats[d.mat];
+  // runs of tile columns with the same target supernode
+  if (tid == 0) {
+    int nr = 0, prev = -1;
+    for (int kk = 0; kk < klim; kk++) {
+      const int t = md.col2sn[rows[k0 + kk]];
+      if (t != prev) { run_start[nr] = kk; run_t[nr] = t; nr++; prev = t; }
+    }
+    run_start[nr] = klim;
+    nruns = nr;
+  }
+  __syncthreads();
+  for (int r = 0; r < nruns; r++) {
+    const SnDev td = sns[md.sn_base + run_t[r]];
+    const int kb = run_start[r], ke = run_start[r + 1];
+    // relative map of the tile rows inside the target's rows (rows >= the run's first
+    // column row are all present in the target, by the elimination-tree property)
+    for (int ii = tid; ii < ilim; ii += THREADS) {
+      const int gi = i0 + ii;
+      relpos[ii] = gi >= k0 + kb ? relative_row(md, td.rows, td.m, rows[gi]) : -1;
+    }
+    __syncthreads();
+    T* Lt = reinterpret_cast<T*>(td.L);
+    const int w = ke - kb;
+    for (int idx = tid; idx < w * TILE; idx += THREADS) {
+      const int kk = kb + idx / TILE, ii = idx % TILE;
+      if (ii < ilim && i0 + ii >= k0 + kk && relpos[ii] >= 0) {
+        const int c = rows[k0 + kk] - td.col0;
+        atomicAdd(&Lt[(int64_t)c * td.m + relpos[ii]], -Cs[kk * (TILE + 1) + ii]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- Schur update tiles ---------------------------------------------------------------------
+// Task {s, i0, k0}: the T x T tile of U_s = L21 L21^T at rows i0.., columns k0.. (offsets
+// into the off-diagonal rows of s), computed with FP64 m8n8k4 DMMA, then handed to
+// schur_tile_epilogue.
 template <int TILE>
 struct SchurCfg {
   static constexpr int WARPS_M = TILE == 64 ? 2 : 1;
@@ -171,10 +231,6 @@ __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
   constexpr int KC = Cfg::KC, LDS = Cfg::LDS, MB = Cfg::MB;
   __shared__ __align__(16) double sh[2 * KC * LDS > TILE * (TILE + 1) ? 2 * KC * LDS
                                                                       : TILE * (TILE + 1)];
-  __shared__ int run_start[TILE + 1];
-  __shared__ int run_t[TILE];
-  __shared__ int nruns;
-  __shared__ int relpos[TILE];
   double* As = sh;              // [KC][LDS]: As[kk][ii] = L21[i0 + ii][kc + kk]
   double* Bs = sh + KC * LDS;   // [KC][LDS]: Bs[kk][jj] = L21[k0 + jj][kc + kk]
 
@@ -235,49 +291,152 @@ __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
       }
   __syncthreads();
 
-  const int32_t* rows = d.rows + n;  // off-diagonal rows of s
-  const int ilim = min(TILE, u - i0), klim = min(TILE, u - k0);
-  if (OWNER) {
-    double* U = stage + d.ustage;
-    for (int idx = tid; idx < klim * TILE; idx += Cfg::THREADS) {
+  schur_tile_epilogue<double, TILE, Cfg::THREADS, OWNER>(Cs, d, i0, k0, sns, mats, stage);
+}
+
+// ---- FP32 Schur tiles (mixed precision) -------------------------------------------------------
+// The same task and epilogue as k_schur_f64 on FP32 panels: each of the (T/4)^2 threads
+// accumulates a 4 x 4 block of the tile in FP32 registers (rows ty + q T/4, columns
+// tx + p T/4) from K chunks staged in shared memory.
+template <int TILE>
+struct SchurF32Cfg {
+  static constexpr int S = TILE / 4;
+  static constexpr int THREADS = S * S;
+  static constexpr int KC = 32;
+  static constexpr int LDS = TILE + 4;
+};
+
+template <int TILE, bool OWNER>
+__global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
+    k_schur_f32(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
+                const MatDev* __restrict__ mats, float* __restrict__ stage) {
+  using Cfg = SchurF32Cfg<TILE>;
+  constexpr int KC = Cfg::KC, LDS = Cfg::LDS, S = Cfg::S;
+  __shared__ __align__(16) float sh[2 * KC * LDS > TILE * (TILE + 1) ? 2 * KC * LDS
+                                                                     : TILE * (TILE + 1)];
+  float* As = sh;
+  float* Bs = sh + KC * LDS;
+  const int4 tk = tasks[blockIdx.x];
+  const SnDev d = sns[tk.x];
+  const int n = d.n, m = d.m, u = m - n;
+  const int i0 = tk.y, k0 = tk.z;
+  const float* L = reinterpret_cast<const float*>(d.L);
+  const int tid = threadIdx.x, tx = tid % S, ty = tid / S;
+  float acc[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+#pragma unroll
+    for (int p = 0; p < 4; p++) acc[q][p] = 0.f;
+  for (int kc = 0; kc < n; kc += KC) {
+    const int kw = min(KC, n - kc);
+    for (int idx = tid; idx < KC * TILE; idx += Cfg::THREADS) {
       const int kk = idx / TILE, ii = idx - kk * TILE;
-      if (ii < ilim && i0 + ii >= k0 + kk)
-        U[(int64_t)(k0 + kk) * u + i0 + ii] = Cs[kk * (TILE + 1) + ii];
+      float va = 0.f, vb = 0.f;
+      if (kk < kw) {
+        const int64_t col = (int64_t)(kc + kk) * m + n;
+        if (i0 + ii < u) va = L[col + i0 + ii];
+        if (k0 + ii < u) vb = L[col + k0 + ii];
+      }
+      As[kk * LDS + ii] = va;
+      Bs[kk * LDS + ii] = vb;
     }
-    return;
+    __syncthreads();
+    for (int kk = 0; kk < kw; kk++) {
+      float a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) a[q] = As[kk * LDS + ty + q * S];
+#pragma unroll
+      for (int p = 0; p < 4; p++) b[p] = Bs[kk * LDS + tx + p * S];
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int p = 0; p < 4; p++) acc[q][p] = fmaf(a[q], b[p], acc[q][p]);
+    }
+    __syncthreads();
   }
-  const MatDev md = mats[d.mat];
-  // runs of tile columns with the same target supernode
-  if (tid == 0) {
-    int nr = 0, prev = -1;
-    for (int kk = 0; kk < klim; kk++) {
-      const int t = md.col2sn[rows[k0 + kk]];
-      if (t != prev) { run_start[nr] = kk; run_t[nr] = t; nr++; prev = t; }
-    }
-    run_start[nr] = klim;
-    nruns = nr;
+  float* Cs = sh;
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+#pragma unroll
+    for (int p = 0; p < 4; p++) Cs[(tx + p * S) * (TILE + 1) + ty + q * S] = acc[q][p];
+  __syncthreads();
+  schur_tile_epilogue<float, TILE, Cfg::THREADS, OWNER>(Cs, d, i0, k0, sns, mats, stage);
+}
+
+// ---- POTRF of the mixed-precision factor ---------------------------------------------------
+// FP32 panels of the equilibrated matrix (unit diagonal before updates).  The block is
+// factored in FP32; if any pivot falls below tau (tau times the original diagonal, which
+// is 1 after equilibration), the block is factored again in FP64 from an FP64 copy of
+// its values, and the FP64 result is rounded into the panel.  err[2] counts such redos.
+__global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ tasks,
+                                                     const SnDev* __restrict__ sns,
+                                                     const MatDev* __restrict__ mats,
+                                                     float tau) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int4 tk = tasks[blockIdx.x];
+  const SnDev d = sns[tk.x];
+  const int n = d.n, m = d.m;
+  float* L = reinterpret_cast<float*>(d.L);
+  double* D = reinterpret_cast<double*>(smem_raw);   // n x n FP64 copy
+  float* A = reinterpret_cast<float*>(D + n * n);    // n x n FP32 work block
+  __shared__ float fpiv_inv;
+  __shared__ double dpiv_inv;
+  __shared__ int redo;
+  if (threadIdx.x == 0) redo = 0;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    int c = idx / n, r = idx - c * n;
+    const float v = r >= c ? L[(int64_t)c * m + r] : 0.f;
+    A[idx] = v;
+    D[idx] = (double)v;
   }
   __syncthreads();
-  for (int r = 0; r < nruns; r++) {
-    const SnDev td = sns[md.sn_base + run_t[r]];
-    const int kb = run_start[r], ke = run_start[r + 1];
-    // relative map of the tile rows inside the target's rows (rows >= the run's first
-    // column row are all present in the target, by the elimination-tree property)
-    for (int ii = tid; ii < ilim; ii += Cfg::THREADS) {
-      const int gi = i0 + ii;
-      relpos[ii] = gi >= k0 + kb ? relative_row(md, td.rows, td.m, rows[gi]) : -1;
+  for (int j = 0; j < n; j++) {
+    if (threadIdx.x == 0) {
+      float p = A[j * n + j];
+      if (!(p >= tau)) { redo = 1; p = 1.f; }
+      const float s = sqrtf(p);
+      A[j * n + j] = s;
+      fpiv_inv = 1.f / s;
     }
     __syncthreads();
-    double* Lt = reinterpret_cast<double*>(td.L);
-    const int w = ke - kb;
-    for (int idx = tid; idx < w * TILE; idx += Cfg::THREADS) {
-      const int kk = kb + idx / TILE, ii = idx % TILE;
-      if (ii < ilim && i0 + ii >= k0 + kk && relpos[ii] >= 0) {
-        const int c = rows[k0 + kk] - td.col0;
-        atomicAdd(&Lt[(int64_t)c * td.m + relpos[ii]], -Cs[kk * (TILE + 1) + ii]);
+    if (redo) break;
+    const float inv = fpiv_inv;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] *= inv;
+    __syncthreads();
+    const int nt = n - j - 1;
+    for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
+      int c = idx / nt, r = idx - c * nt;
+      if (r >= c) A[(j + 1 + c) * n + j + 1 + r] -= A[j * n + j + 1 + r] * A[j * n + j + 1 + c];
+    }
+    __syncthreads();
+  }
+  if (redo) {
+    if (threadIdx.x == 0) atomicAdd(mats[d.mat].err + 2, 1ull);
+    for (int j = 0; j < n; j++) {
+      if (threadIdx.x == 0) {
+        double p = D[j * n + j];
+        if (!(p > 0.0)) { record_error(mats[d.mat], d.col0 + j); p = 1.0; }
+        const double s = sqrt(p);
+        D[j * n + j] = s;
+        dpiv_inv = 1.0 / s;
       }
+      __syncthreads();
+      const double inv = dpiv_inv;
+      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) D[j * n + i] *= inv;
+      __syncthreads();
+      const int nt = n - j - 1;
+      for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
+        int c = idx / nt, r = idx - c * nt;
+        if (r >= c) D[(j + 1 + c) * n + j + 1 + r] -= D[j * n + j + 1 + r] * D[j * n + j + 1 + c];
+      }
+      __syncthreads();
     }
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) A[idx] = (float)D[idx];
     __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    int c = idx / n, r = idx - c * n;
+    if (r >= c) L[(int64_t)c * m + r] = A[idx];
   }
 }
 
@@ -289,21 +448,22 @@ __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
 constexpr int kAsmThreads = 256;
 constexpr int kAsmRowChunk = 1024;
 
+template <typename T>
 __global__ void __launch_bounds__(kAsmThreads)
     k_assemble_owner(const int4* __restrict__ groups, const int4* __restrict__ srcs,
                      const SnDev* __restrict__ sns, const MatDev* __restrict__ mats,
-                     const double* __restrict__ stage) {
+                     const T* __restrict__ stage) {
   __shared__ int relpos[kAsmRowChunk];
   const int4 g = groups[blockIdx.x];
   const SnDev td = sns[g.x];
   const MatDev md = mats[td.mat];
-  double* Lt = reinterpret_cast<double*>(td.L);
+  T* Lt = reinterpret_cast<T*>(td.L);
   for (int q = g.z; q < g.w; q++) {
     const int4 sr = srcs[q];
     const SnDev sd = sns[sr.x];
     const int u = sd.m - sd.n;
     const int32_t* rows = sd.rows + sd.n;
-    const double* U = stage + sd.ustage;
+    const T* U = stage + sd.ustage;
     for (int ib = sr.y; ib < u; ib += kAsmRowChunk) {
       const int ilen = min(kAsmRowChunk, u - ib);
       __syncthreads();
@@ -332,52 +492,85 @@ void launch_assemble(const double* vals, const int64_t* amap, int64_t nnz, void*
   else k_assemble<double><<<blocks, 256, 0, st>>>(vals, amap, nnz, (double*)L);
 }
 
-void launch_potrf(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
-                  int max_width, cudaStream_t st) {
-  if (ntasks <= 0) return;
-  size_t sm = (size_t)max_width * max_width * sizeof(double);
-  k_potrf<double><<<ntasks, 128, sm, st>>>(tasks, sns, mats);
+static size_t potrf_smem(int w) { return (size_t)w * w * sizeof(double); }
+static size_t potrf_mixed_smem(int w) { return (size_t)w * w * (sizeof(double) + sizeof(float)); }
+static size_t trsm_smem(int w) {
+  return ((size_t)w * w + w + (size_t)w * kTrsmRows) * sizeof(double);
 }
 
-void launch_trsm(const int4* tasks, int ntasks, const SnDev* sns, int max_width,
+void launch_potrf(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
+                  int max_width, bool f32, float tau, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  if (f32)
+    k_potrf_mixed<<<ntasks, 128, potrf_mixed_smem(max_width), st>>>(tasks, sns, mats, tau);
+  else
+    k_potrf<double><<<ntasks, 128, potrf_smem(max_width), st>>>(tasks, sns, mats);
+}
+
+void launch_trsm(const int4* tasks, int ntasks, const SnDev* sns, int max_width, bool f32,
                  cudaStream_t st) {
   if (ntasks <= 0) return;
-  size_t sm = ((size_t)max_width * max_width + max_width + (size_t)max_width * kTrsmRows) *
-              sizeof(double);
-  k_trsm<double><<<ntasks, kTrsmRows, sm, st>>>(tasks, sns);
+  if (f32) k_trsm<float><<<ntasks, kTrsmRows, trsm_smem(max_width), st>>>(tasks, sns);
+  else k_trsm<double><<<ntasks, kTrsmRows, trsm_smem(max_width), st>>>(tasks, sns);
+}
+
+template <int T>
+static void schur_f64_t(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
+                        double* stage, bool owner, cudaStream_t st) {
+  if (owner)
+    k_schur_f64<T, true><<<ntasks, SchurCfg<T>::THREADS, 0, st>>>(tasks, sns, mats, stage);
+  else
+    k_schur_f64<T, false><<<ntasks, SchurCfg<T>::THREADS, 0, st>>>(tasks, sns, mats, stage);
+}
+
+template <int T>
+static void schur_f32_t(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
+                        float* stage, bool owner, cudaStream_t st) {
+  if (owner)
+    k_schur_f32<T, true><<<ntasks, SchurF32Cfg<T>::THREADS, 0, st>>>(tasks, sns, mats, stage);
+  else
+    k_schur_f32<T, false><<<ntasks, SchurF32Cfg<T>::THREADS, 0, st>>>(tasks, sns, mats, stage);
 }
 
 void launch_schur(int cls, const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
-                  double* stage, bool owner, cudaStream_t st) {
+                  void* stage, bool owner, bool f32, cudaStream_t st) {
   if (ntasks <= 0) return;
-#define CHOL_SCHUR(T)                                                                        \
-  if (owner)                                                                                 \
-    k_schur_f64<T, true><<<ntasks, SchurCfg<T>::THREADS, 0, st>>>(tasks, sns, mats, stage);  \
-  else                                                                                       \
-    k_schur_f64<T, false><<<ntasks, SchurCfg<T>::THREADS, 0, st>>>(tasks, sns, mats, stage);
-  if (cls == kTile64) { CHOL_SCHUR(64) }
-  else if (cls == kTile32) { CHOL_SCHUR(32) }
-  else { CHOL_SCHUR(16) }
-#undef CHOL_SCHUR
+  if (f32) {
+    float* s = static_cast<float*>(stage);
+    if (cls == kTile64) schur_f32_t<64>(tasks, ntasks, sns, mats, s, owner, st);
+    else if (cls == kTile32) schur_f32_t<32>(tasks, ntasks, sns, mats, s, owner, st);
+    else schur_f32_t<16>(tasks, ntasks, sns, mats, s, owner, st);
+  } else {
+    double* s = static_cast<double*>(stage);
+    if (cls == kTile64) schur_f64_t<64>(tasks, ntasks, sns, mats, s, owner, st);
+    else if (cls == kTile32) schur_f64_t<32>(tasks, ntasks, sns, mats, s, owner, st);
+    else schur_f64_t<16>(tasks, ntasks, sns, mats, s, owner, st);
+  }
 }
 
 void launch_assemble_owner(const int4* groups, int ngroups, const int4* srcs, const SnDev* sns,
-                           const MatDev* mats, const double* stage, cudaStream_t st) {
+                           const MatDev* mats, const void* stage, bool f32, cudaStream_t st) {
   if (ngroups <= 0) return;
-  k_assemble_owner<<<ngroups, kAsmThreads, 0, st>>>(groups, srcs, sns, mats, stage);
+  if (f32)
+    k_assemble_owner<float><<<ngroups, kAsmThreads, 0, st>>>(groups, srcs, sns, mats,
+                                                             static_cast<const float*>(stage));
+  else
+    k_assemble_owner<double><<<ngroups, kAsmThreads, 0, st>>>(groups, srcs, sns, mats,
+                                                              static_cast<const double*>(stage));
+}
+
+template <typename K>
+static bool set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+         cudaSuccess;
 }
 
 int set_factor_kernel_attrs(int max_width) {
-  size_t potrf = (size_t)max_width * max_width * sizeof(double);
-  size_t trsm = ((size_t)max_width * max_width + max_width + (size_t)max_width * kTrsmRows) *
-                sizeof(double);
-  if (cudaFuncSetAttribute(k_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)potrf) != cudaSuccess)
-    return CHOL_E_CUDA;
-  if (cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)trsm) != cudaSuccess)
-    return CHOL_E_CUDA;
-  return CHOL_OK;
+  bool ok = set_smem(k_potrf<double>, potrf_smem(max_width)) &&
+            set_smem(k_potrf_mixed, potrf_mixed_smem(max_width)) &&
+            set_smem(k_trsm<double>, trsm_smem(max_width)) &&
+            set_smem(k_trsm<float>, trsm_smem(max_width));
+  return ok ? CHOL_OK : CHOL_E_CUDA;
 }
 
 }  // namespace chol

@@ -6,7 +6,8 @@
 // solve from the root down (a supernode needs the solution on its off-diagonal rows, which
 // belong to ancestors).
 //
-// Vectors are n x nrhs column-major in the permuted numbering, ld = n.
+// Vectors are n x nrhs column-major in the permuted numbering, ld = n, always FP64; the
+// panels are FP64 or FP32 (mixed-precision factor), read and widened to FP64.
 //   forward  task {s, r0}: y_s <- L11^{-1} y_s (redundantly in every task of s; the task
 //            with r0 = 0 stores it in w), then y[rows[n+i]] -= L21[i, :] y_s for its rows,
 //            by atomics, or (owner order) staged and summed per row in a fixed order.
@@ -22,24 +23,29 @@
 
 namespace chol {
 
+// y[i, c] = B[perm[i], c] (* scale[perm[i]] when scale is given: the equilibrated system)
 __global__ void k_gather_perm(const double* __restrict__ B, int64_t ldb,
-                              const int32_t* __restrict__ perm, int64_t n, int nrhs,
-                              double* __restrict__ y) {
+                              const int32_t* __restrict__ perm, const double* __restrict__ scale,
+                              int64_t n, int nrhs, double* __restrict__ y) {
   const int64_t total = n * nrhs;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = q / n, i = q - c * n;
-    y[q] = B[c * ldb + perm[i]];
+    const int32_t o = perm[i];
+    y[q] = scale ? B[c * ldb + o] * scale[o] : B[c * ldb + o];
   }
 }
 
+// X[perm[i], c] = w[i, c] (* scale[perm[i]])
 __global__ void k_scatter_perm(const double* __restrict__ w, const int32_t* __restrict__ perm,
-                               int64_t n, int nrhs, double* __restrict__ X, int64_t ldx) {
+                               const double* __restrict__ scale, int64_t n, int nrhs,
+                               double* __restrict__ X, int64_t ldx) {
   const int64_t total = n * nrhs;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = q / n, i = q - c * n;
-    X[c * ldx + perm[i]] = w[q];
+    const int32_t o = perm[i];
+    X[c * ldx + o] = scale ? w[q] * scale[o] : w[q];
   }
 }
 
@@ -87,12 +93,13 @@ __device__ void warp_trisolve(const double* L11, const double* rdiag, double* xs
   }
 }
 
+template <typename P>
 __device__ void load_l11(const SnDev& d, double* L11, double* rdiag) {
-  const double* L = reinterpret_cast<const double*>(d.L);
+  const P* L = reinterpret_cast<const P*>(d.L);
   const int n = d.n;
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int c = idx / n, r = idx - c * n;
-    L11[idx] = r >= c ? L[(int64_t)c * d.m + r] : 0.0;
+    L11[idx] = r >= c ? (double)L[(int64_t)c * d.m + r] : 0.0;
   }
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += blockDim.x) rdiag[j] = 1.0 / L11[j * n + j];
@@ -101,7 +108,7 @@ __device__ void load_l11(const SnDev& d, double* L11, double* rdiag) {
 
 // smem: L11 n*n, rdiag n, xs n*nrhs.  STAGE: the off-diagonal products go to the level's
 // staging slots (q * kSolveRows + ii) * nrhs + c instead of atomics into y.
-template <bool STAGE>
+template <typename P, bool STAGE>
 __global__ void __launch_bounds__(kSolveThreads)
     k_fwd(const int4* __restrict__ tasks, const SnDev* __restrict__ sns, int64_t ldv, int nrhs,
           double* __restrict__ y, double* __restrict__ w, double* __restrict__ fstage) {
@@ -116,7 +123,7 @@ __global__ void __launch_bounds__(kSolveThreads)
     const int c = idx / n, j = idx - c * n;
     xs[idx] = y[c * ldv + d.col0 + j];
   }
-  load_l11(d, L11, rdiag);
+  load_l11<P>(d, L11, rdiag);
   if (threadIdx.x < 32) warp_trisolve<true>(L11, rdiag, xs, n, nrhs);
   __syncthreads();
   if (tk.y == 0)
@@ -126,14 +133,14 @@ __global__ void __launch_bounds__(kSolveThreads)
     }
   const int i = tk.y + threadIdx.x;
   if (i < u) {
-    const double* L = reinterpret_cast<const double*>(d.L) + n + i;
+    const P* L = reinterpret_cast<const P*>(d.L) + n + i;
     const int64_t grow = d.rows[n + i];
     for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
       double acc[kRhsChunk];
 #pragma unroll
       for (int c = 0; c < kRhsChunk; c++) acc[c] = 0.0;
       for (int j = 0; j < n; j++) {
-        const double l = L[(int64_t)j * m];
+        const double l = (double)L[(int64_t)j * m];
 #pragma unroll
         for (int c = 0; c < kRhsChunk; c++)
           if (c0 + c < nrhs) acc[c] += l * xs[(c0 + c) * n + j];
@@ -167,6 +174,7 @@ __global__ void k_fwd_gather(const int32_t* __restrict__ fg_row, const int64_t* 
 }
 
 // Backward partials: the level's task q = blockIdx.x writes part[q * W * nrhs + c * W + j].
+template <typename P>
 __global__ void __launch_bounds__(kSolveThreads)
     k_bwd_partial(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
                   int64_t ldv, int nrhs, int W, const double* __restrict__ w,
@@ -183,18 +191,19 @@ __global__ void __launch_bounds__(kSolveThreads)
   }
   __syncthreads();
   double* out = part + (int64_t)blockIdx.x * W * nrhs;
-  const double* L = reinterpret_cast<const double*>(d.L) + n + tk.y;
+  const P* L = reinterpret_cast<const P*>(d.L) + n + tk.y;
   for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
     const int c = idx / n, j = idx - c * n;
     double acc = 0.0;
-    const double* col = L + (int64_t)j * m;
-    for (int i = 0; i < rb; i++) acc += col[i] * xg[c * rb + i];
+    const P* col = L + (int64_t)j * m;
+    for (int i = 0; i < rb; i++) acc += (double)col[i] * xg[c * rb + i];
     out[c * W + j] = acc;
   }
 }
 
 // Backward diagonal step, one CTA per supernode: task {s, first_bwd, nbwd}; first_bwd is
 // a global index into the backward task list, base the first task of this level.
+template <typename P>
 __global__ void __launch_bounds__(kSolveThreads)
     k_bwd_diag(const int4* __restrict__ tasks, int64_t base, const SnDev* __restrict__ sns,
                int64_t ldv, int nrhs, int W, const double* __restrict__ part,
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(kSolveThreads)
       for (int q = 0; q < tk.z; q++) v -= part[(tk.y - base + q) * W * nrhs + c * W + j];
     xs[idx] = v;
   }
-  load_l11(d, L11, rdiag);
+  load_l11<P>(d, L11, rdiag);
   if (threadIdx.x < 32) warp_trisolve<false>(L11, rdiag, xs, n, nrhs);
   __syncthreads();
   for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
@@ -228,31 +237,37 @@ static inline size_t solve_smem(int W, int nrhs) {
   return ((size_t)W * W + W + (size_t)W * nrhs) * sizeof(double);
 }
 
-void launch_gather_perm(const double* B, int64_t ldb, const int32_t* perm, int64_t n, int nrhs,
-                        double* y, cudaStream_t st) {
-  if (n <= 0) return;
-  int64_t total = n * nrhs;
-  int blocks = (int)((total + 255) / 256 < 152 * 8 ? (total + 255) / 256 : 152 * 8);
-  k_gather_perm<<<blocks, 256, 0, st>>>(B, ldb, perm, n, nrhs, y);
+static inline int grid_for(int64_t total) {
+  return (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
 }
 
-void launch_scatter_perm(const double* w, const int32_t* perm, int64_t n, int nrhs, double* X,
-                         int64_t ldx, cudaStream_t st) {
+void launch_gather_perm(const double* B, int64_t ldb, const int32_t* perm, const double* scale,
+                        int64_t n, int nrhs, double* y, cudaStream_t st) {
   if (n <= 0) return;
-  int64_t total = n * nrhs;
-  int blocks = (int)((total + 255) / 256 < 152 * 8 ? (total + 255) / 256 : 152 * 8);
-  k_scatter_perm<<<blocks, 256, 0, st>>>(w, perm, n, nrhs, X, ldx);
+  k_gather_perm<<<grid_for(n * nrhs), 256, 0, st>>>(B, ldb, perm, scale, n, nrhs, y);
+}
+
+void launch_scatter_perm(const double* w, const int32_t* perm, const double* scale, int64_t n,
+                         int nrhs, double* X, int64_t ldx, cudaStream_t st) {
+  if (n <= 0) return;
+  k_scatter_perm<<<grid_for(n * nrhs), 256, 0, st>>>(w, perm, scale, n, nrhs, X, ldx);
+}
+
+template <typename P>
+static void fwd_t(const int4* tasks, int ntasks, const SnDev* sns, int64_t ldv, int nrhs, int W,
+                  double* y, double* w, double* fstage, cudaStream_t st) {
+  const size_t sm = solve_smem(W, nrhs);
+  if (fstage)
+    k_fwd<P, true><<<ntasks, kSolveThreads, sm, st>>>(tasks, sns, ldv, nrhs, y, w, fstage);
+  else
+    k_fwd<P, false><<<ntasks, kSolveThreads, sm, st>>>(tasks, sns, ldv, nrhs, y, w, nullptr);
 }
 
 void launch_fwd(const int4* tasks, int ntasks, const SnDev* sns, int64_t ldv, int nrhs, int W,
-                double* y, double* w, double* fstage, cudaStream_t st) {
+                double* y, double* w, double* fstage, bool f32, cudaStream_t st) {
   if (ntasks <= 0) return;
-  if (fstage)
-    k_fwd<true><<<ntasks, kSolveThreads, solve_smem(W, nrhs), st>>>(tasks, sns, ldv, nrhs, y, w,
-                                                                    fstage);
-  else
-    k_fwd<false><<<ntasks, kSolveThreads, solve_smem(W, nrhs), st>>>(tasks, sns, ldv, nrhs, y,
-                                                                     w, nullptr);
+  if (f32) fwd_t<float>(tasks, ntasks, sns, ldv, nrhs, W, y, w, fstage, st);
+  else fwd_t<double>(tasks, ntasks, sns, ldv, nrhs, W, y, w, fstage, st);
 }
 
 void launch_fwd_gather(const int32_t* fg_row, const int64_t* fg_ptr, const int32_t* fg_ent,
@@ -263,32 +278,39 @@ void launch_fwd_gather(const int32_t* fg_row, const int64_t* fg_ptr, const int32
   k_fwd_gather<<<blocks, 128, 0, st>>>(fg_row, fg_ptr, fg_ent, nrows, ldv, nrhs, fstage, y);
 }
 
-void launch_bwd(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* diag_tasks,
-                int ndiag, const SnDev* sns, int64_t ldv, int nrhs, int W, double* w,
-                double* part, cudaStream_t st) {
+template <typename P>
+static void bwd_t(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* diag_tasks,
+                  int ndiag, const SnDev* sns, int64_t ldv, int nrhs, int W, double* w,
+                  double* part, cudaStream_t st) {
   if (nbwd > 0)
-    k_bwd_partial<<<nbwd, kSolveThreads, (size_t)kSolveRows * nrhs * sizeof(double), st>>>(
+    k_bwd_partial<P><<<nbwd, kSolveThreads, (size_t)kSolveRows * nrhs * sizeof(double), st>>>(
         bwd_tasks, sns, ldv, nrhs, W, w, part);
   if (ndiag > 0)
-    k_bwd_diag<<<ndiag, kSolveThreads, solve_smem(W, nrhs), st>>>(diag_tasks, bwd_base, sns,
-                                                                  ldv, nrhs, W, part, w);
+    k_bwd_diag<P><<<ndiag, kSolveThreads, solve_smem(W, nrhs), st>>>(diag_tasks, bwd_base, sns,
+                                                                     ldv, nrhs, W, part, w);
+}
+
+void launch_bwd(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* diag_tasks,
+                int ndiag, const SnDev* sns, int64_t ldv, int nrhs, int W, double* w,
+                double* part, bool f32, cudaStream_t st) {
+  if (f32) bwd_t<float>(bwd_tasks, nbwd, bwd_base, diag_tasks, ndiag, sns, ldv, nrhs, W, w, part, st);
+  else bwd_t<double>(bwd_tasks, nbwd, bwd_base, diag_tasks, ndiag, sns, ldv, nrhs, W, w, part, st);
+}
+
+template <typename K>
+static bool set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+         cudaSuccess;
 }
 
 int set_solve_kernel_attrs(int W, int max_nrhs) {
-  size_t sm = solve_smem(W, max_nrhs);
-  if (cudaFuncSetAttribute(k_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-          cudaSuccess)
-    return CHOL_E_CUDA;
-  if (cudaFuncSetAttribute(k_bwd_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-      cudaSuccess)
-    return CHOL_E_CUDA;
-  size_t sp = (size_t)kSolveRows * max_nrhs * sizeof(double);
-  if (cudaFuncSetAttribute(k_bwd_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sp) != cudaSuccess)
-    return CHOL_E_CUDA;
-  return CHOL_OK;
+  const size_t sm = solve_smem(W, max_nrhs);
+  const size_t sp = (size_t)kSolveRows * max_nrhs * sizeof(double);
+  bool ok = set_smem(k_fwd<double, false>, sm) && set_smem(k_fwd<double, true>, sm) &&
+            set_smem(k_fwd<float, false>, sm) && set_smem(k_fwd<float, true>, sm) &&
+            set_smem(k_bwd_diag<double>, sm) && set_smem(k_bwd_diag<float>, sm) &&
+            set_smem(k_bwd_partial<double>, sp) && set_smem(k_bwd_partial<float>, sp);
+  return ok ? CHOL_OK : CHOL_E_CUDA;
 }
 
 }  // namespace chol
