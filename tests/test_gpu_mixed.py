@@ -98,7 +98,9 @@ def test_fallback_to_fp64_when_refinement_stalls(torch):
     assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, b, x) <= REFINE_TOL
     # the FP64 factor is kept: a second call goes straight to it
     x2, info2 = num.refine(b, tol=REFINE_TOL, maxit=0)
-    assert info2["fell_back"] and np.array_equal(x, x2)
+    assert info2["fell_back"]
+    # atomic assembly: equal up to the rounding of the forward-solve scatter order
+    np.testing.assert_allclose(x2, x, rtol=0, atol=1e-12 * np.abs(x).max())
 
 
 def test_small_pivot_redone_in_fp64(torch):
