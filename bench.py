@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "factor GFLOP/s + % FP64 peak; served solves/s and p99 latency at resid<=1e-12"
 NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0  # nominal dense FP64 / BF16 rates of a GB300
 FALLBACK_BF16_TFLOPS = 1900.0
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def measured_peaks():
@@ -165,7 +166,8 @@ def run_reference(args, rank: int, world: int):
 
 
 def workload_config(args):
-    return {"workload": args.workload, "n": None, "precision": "fp64", "nrhs": 1,
+    return {"workload": args.workload, "n": None, "precision": args.precision,
+            "nrhs": args.nrhs,
             "ordering": "geometric nested dissection (leaf 64 nodes)",
             "width_cap": args.width, "assembly": args.assembly,
             "l2": "inputs larger than L2 (factor ~3.9 GB), no flush"}
@@ -183,6 +185,10 @@ def main():
     ap.add_argument("--cpu-sample", default="st27x3_24")
     ap.add_argument("--ref-sample", default="st27x3_20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="mixed: FP32 factor + FP64 iterative refinement to --tol")
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--tol", type=float, default=1e-12)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -205,9 +211,12 @@ def main():
 
     A, perm = inputs.workload(args.workload)
     n = A.n
-    xt = inputs.rhs_block(1, n, 1)[:, 0]
+    nrhs = args.nrhs
+    Xt = inputs.rhs_block(1, n, nrhs)
     Afull = A.to_scipy_full()
-    b = Afull @ xt
+    b = np.asfortranarray(Afull @ Xt)
+    mixed = args.precision == "mixed"
+    prec = P.CHOL_MIXED if mixed else P.CHOL_FP64
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = P.Context(device=local, width_cap=args.width,
@@ -216,10 +225,11 @@ def main():
     sym = P.Symbolic(ctx, A, perm)
     F = sym.info["flops"]
     vals_d = torch.from_numpy(A.vals).cuda()
-    b_d = torch.from_numpy(b).cuda()
+    b_d = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()  # (k, n): column c = row c
     x_d = torch.empty_like(b_d)
     torch.cuda.synchronize()
-    num = P.Factor(ctx, sym, vals_d)
+    num = P.Factor(ctx, sym, vals_d, precision=prec)
+    refine_info = {}
 
     def step(ev=None):
         if ev is not None:
@@ -227,7 +237,11 @@ def main():
         num.refactor(vals_d)
         if ev is not None:
             ev[1].record(stream)
-        num.solve(b_d, x_d)
+        if mixed:
+            _, info = num.refine(b_d, x_d, tol=args.tol)
+            refine_info.update(info)
+        else:
+            num.solve(b_d, x_d)
         if ev is not None:
             ev[2].record(stream)
 
@@ -248,8 +262,8 @@ def main():
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for k in range(args.steps):
-        step(evs[k])
+    for it in range(args.steps):
+        step(evs[it])
     t_end.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -265,27 +279,36 @@ def main():
     ms_step = total_ms / args.steps
     fac_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     sol_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
-    x = x_d.cpu().numpy()
-    rn = np.abs(b - Afull @ x).max()
+    x = np.asfortranarray(x_d.cpu().numpy().T)
     anorm = np.abs(Afull).sum(axis=1).max()
-    resid = float(rn / (anorm * np.abs(x).max()))
+    resid = float(max(np.abs(b[:, c] - Afull @ x[:, c]).max() / (anorm * np.abs(x[:, c]).max())
+                      for c in range(nrhs)))
     launches = sum(v["launches"] for v in prof.values())
 
     # end to end through host buffers (pinned): values + b in, x out, every step
     vals_h = torch.empty(A.vals.shape, dtype=torch.float64, pin_memory=True).numpy()
     vals_h[:] = A.vals
-    b_h = torch.empty((n,), dtype=torch.float64, pin_memory=True).numpy()
+    b_h = torch.empty((nrhs, n), dtype=torch.float64, pin_memory=True).numpy().T
     b_h[:] = b
-    x_h = torch.empty((n, 1), dtype=torch.float64, pin_memory=True).numpy()
-    for _ in range(1):
+    x_h = torch.empty((nrhs, n), dtype=torch.float64, pin_memory=True).numpy().T
+
+    def host_step():
         num.refactor(vals_h)
-        P.chol_solve(ctx.handle, num.handle, b_h.reshape(n, 1), x_h)
+        if mixed:
+            info = P.chol_refine_info()
+            rc = P.lib().chol_refine(ctx.handle, num.handle, nrhs, b_h.ctypes.data, n,
+                                     x_h.ctypes.data, n, P.CHOL_HOST, args.tol, 10, info)
+            if rc:
+                raise P.CholError(rc, "chol_refine")
+        else:
+            P.chol_solve(ctx.handle, num.handle, b_h, x_h)
+
+    host_step()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        num.refactor(vals_h)
-        P.chol_solve(ctx.handle, num.handle, b_h.reshape(n, 1), x_h)
+        host_step()
     e2e_s = (time.perf_counter() - t0) / args.steps
     if dist:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
@@ -294,17 +317,26 @@ def main():
 
     peaks, peak_src = measured_peaks()
     fp64_peak_tflops = peaks["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
-    fac_kinds = {k: v for k, v in prof.items() if v["timed"] > 0 and v["flops"] > 0}
-    dom = max(fac_kinds, key=lambda k: fac_kinds[k]["ms"])
+    fac_kinds = {kk: v for kk, v in prof.items() if v["timed"] > 0 and v["flops"] > 0}
+    dom = max(fac_kinds, key=lambda kk: fac_kinds[kk]["ms"])
     d = prof[dom]
     achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
     traffic = ncu_traffic(dom, d["flops"] / max(d["timed"], 1))
+    if dom.endswith("_f64"):
+        roof = {"bound": "tensor", "peak": fp64_peak_tflops,
+                "peak_source": f"FP64 = {peak_src} bf16 {peaks['bf16_tflops']} TFLOP/s x "
+                               "nominal FP64/bf16 1.25/2250 (DMMA loop measured 1.046 "
+                               "TFLOP/s on this pool)"}
+    else:
+        roof = {"bound": "alu", "peak": FP32_SIMT_PEAK_TFLOPS,
+                "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 "
+                               "TFLOP/s nominal; 72.0 measured by an FFMA loop"}
 
     value = world * F / (ms_step * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
         "data": "synthetic",
         "config": dict(workload_config(args), n=n, nnz_a=A.nnz_lower, nnz_l=sym.info["nnz_l"],
                        flops_per_step=F, nsuper=sym.info["nsuper"],
@@ -318,17 +350,31 @@ def main():
         "e2e": {"value": world * F / e2e_s / 1e9, "unit": "GFLOP/s",
                 "h2d_bytes_per_step": int(A.vals.nbytes + b_h.nbytes),
                 "d2h_bytes_per_step": int(x_h.nbytes)},
-        "roofline": {"bound": "tensor", "kernel": dom, "achieved": achieved,
-                     "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak_tflops, "traffic": traffic,
-                     "peak_source": f"FP64 = {peak_src} bf16 {peaks['bf16_tflops']} TFLOP/s x "
-                                    "nominal FP64/bf16 1.25/2250 (DMMA loop measured "
-                                    "1.046 TFLOP/s on this pool)"},
+        "roofline": {"bound": roof["bound"], "kernel": dom, "achieved": achieved,
+                     "peak": roof["peak"], "unit": "TFLOP/s",
+                     "frac": achieved / roof["peak"], "traffic": traffic,
+                     "peak_source": roof["peak_source"]},
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"] / args.steps,
                         "share": v["ms"] / max(sum(w["ms"] for w in prof.values()), 1e-9)}
                     for k, v in prof.items() if v["launches"]},
         "clocks": clk,
     }
+    if mixed:
+        line["refine"] = refine_info
+        # the FP64 factor of the same matrix, timed once, for comparison
+        f64 = P.Factor(ctx, sym, vals_d, precision=P.CHOL_FP64)
+        f64.status()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        f64.refactor(vals_d)
+        e1.record(stream)
+        f64.solve(b_d, x_d)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        line["fp64_reference"] = {"factor_ms": e0.elapsed_time(e1),
+                                  "solve_ms": e1.elapsed_time(e2),
+                                  "factor_gflops": F / (e0.elapsed_time(e1) * 1e-3) / 1e9}
+        del f64
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fl, dt, _ = oracle_sample(args.cpu_sample)
         line["cpu_baseline"] = {
