@@ -204,6 +204,41 @@ int chol_solve_noalloc(chol_ctx* ctx, const chol_num* num, int64_t nrhs, const d
                        int64_t ldb, double* X, int64_t ldx);
 size_t chol_noalloc_scratch_bytes(void);
 
+/* ---- batching ----------------------------------------------------------------------
+ * A batch packs existing factors (same context, precision and assembly mode; any
+ * patterns) so that level l of the batch -- level l, counted from the leaves, of every
+ * member (Sec. 3, Fig. 1 applied across matrices) -- runs as one launch per kernel kind.
+ * Kernels are persistent: each launch covers its task list with at most one wave of
+ * CTAs.  With use_graph, the first chol_batch_factorize captures the whole launch
+ * sequence into a CUDA graph and later calls replay it.  Members stay usable on their own
+ * (chol_solve, chol_refine, chol_factor_status); free the batch before its members. */
+typedef struct chol_batch chol_batch;
+int chol_batch_create(chol_ctx* ctx, int count, chol_num* const* nums, chol_batch** out);
+/* Re-factors every member.  vals[i] (may be NULL, as may vals itself: keep member i's
+ * current values) are new values of member i on its pattern, host or device per where.
+ * Stream-ordered; check each member with chol_factor_status. */
+int chol_batch_factorize(chol_ctx* ctx, chol_batch* batch, const double* const* vals,
+                         int where, int use_graph);
+void chol_batch_free(chol_batch* batch);
+
+/* Schur tile sizes per supernode size class: 64x64 tiles for supernodes with at least
+ * min_rows_tile64 off-diagonal rows on levels holding at least min_level_tiles64 such
+ * tiles, else 32x32 from min_rows_tile32 rows, else 16x16.  Default {64, 17, 304}. */
+typedef struct chol_tile_policy {
+  int min_rows_tile64;
+  int min_rows_tile32;
+  int min_level_tiles64;
+} chol_tile_policy;
+int chol_sym_get_tile_policy(const chol_sym* sym, chol_tile_policy* policy);
+/* Rebuilds the Schur task lists of sym (and its device copy); factors made from sym use
+ * the new lists from their next factorization; existing batches keep their own copy. */
+int chol_sym_set_tile_policy(chol_sym* sym, const chol_tile_policy* policy);
+/* Autotuner: times refactorizations of num (reps each) under candidate tile policies by
+ * coordinate descent over the three thresholds, keeps the fastest in num's analysis,
+ * stores it in *best (and its time in *best_ms) and leaves num factored under it. */
+int chol_autotune(chol_ctx* ctx, chol_num* num, int reps, chol_tile_policy* best,
+                  double* best_ms);
+
 /* ---- tracing ------------------------------------------------------------------------
  * Per-kernel-kind accounting of the device work a context enqueues: the launch count is
  * always kept; with profiling on, every launch is bracketed by CUDA events on the context

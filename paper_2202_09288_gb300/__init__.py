@@ -48,6 +48,11 @@ class chol_refine_info(C.Structure):
                 ("pivot_redos", C.c_int64)]
 
 
+class chol_tile_policy(C.Structure):
+    _fields_ = [("min_rows_tile64", C.c_int), ("min_rows_tile32", C.c_int),
+                ("min_level_tiles64", C.c_int)]
+
+
 class chol_prof_entry(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double),
                 ("timed", C.c_int64), ("flops", C.c_double), ("bytes", C.c_double)]
@@ -75,6 +80,12 @@ EXPORTS = {
                          C.POINTER(chol_refine_info)]),
     "chol_solve_noalloc": (_I, [_P, _P, _I64, _P, _I64, _P, _I64]),
     "chol_noalloc_scratch_bytes": (C.c_size_t, []),
+    "chol_batch_create": (_I, [_P, _I, C.POINTER(_P), C.POINTER(_P)]),
+    "chol_batch_factorize": (_I, [_P, _P, C.POINTER(_P), _I, _I]),
+    "chol_batch_free": (None, [_P]),
+    "chol_sym_get_tile_policy": (_I, [_P, C.POINTER(chol_tile_policy)]),
+    "chol_sym_set_tile_policy": (_I, [_P, C.POINTER(chol_tile_policy)]),
+    "chol_autotune": (_I, [_P, _P, _I, C.POINTER(chol_tile_policy), C.POINTER(C.c_double)]),
     "chol_profile_enable": (_I, [_P, _I]),
     "chol_profile_read": (_I, [_P, C.POINTER(chol_prof_entry), _I, C.POINTER(_I)]),
     "chol_profile_reset": (_I, [_P]),
@@ -269,6 +280,51 @@ def chol_noalloc_scratch_bytes() -> int:
     return lib().chol_noalloc_scratch_bytes()
 
 
+def chol_batch_create(ctx, nums) -> int:
+    arr = (C.c_void_p * len(nums))(*nums)
+    h = C.c_void_p()
+    _check(lib().chol_batch_create(ctx, len(nums), arr, C.byref(h)), "chol_batch_create")
+    return h.value
+
+
+def chol_batch_factorize(ctx, batch, vals=None, use_graph=True) -> None:
+    """vals: None, or a list with one entry per member (None, a numpy array or a torch CUDA
+    tensor of that member's values; all entries host or all device)."""
+    arr, where = None, CHOL_HOST
+    if vals is not None:
+        ptrs = []
+        for v in vals:
+            p, w = _ptr(v)
+            ptrs.append(p)
+            if v is not None:
+                where = w
+        arr = (C.c_void_p * len(ptrs))(*ptrs)
+    _check(lib().chol_batch_factorize(ctx, batch, arr, where, 1 if use_graph else 0),
+           "chol_batch_factorize")
+
+
+def chol_batch_free(batch) -> None:
+    lib().chol_batch_free(batch)
+
+
+def chol_sym_get_tile_policy(sym) -> dict:
+    p = chol_tile_policy()
+    _check(lib().chol_sym_get_tile_policy(sym, C.byref(p)), "chol_sym_get_tile_policy")
+    return {f: getattr(p, f) for f, _ in chol_tile_policy._fields_}
+
+
+def chol_sym_set_tile_policy(sym, policy: dict) -> None:
+    p = chol_tile_policy(**policy)
+    _check(lib().chol_sym_set_tile_policy(sym, C.byref(p)), "chol_sym_set_tile_policy")
+
+
+def chol_autotune(ctx, num, reps=1) -> tuple[dict, float]:
+    p = chol_tile_policy()
+    ms = C.c_double()
+    _check(lib().chol_autotune(ctx, num, reps, C.byref(p), C.byref(ms)), "chol_autotune")
+    return {f: getattr(p, f) for f, _ in chol_tile_policy._fields_}, ms.value
+
+
 def chol_profile_enable(ctx, on: bool) -> None:
     _check(lib().chol_profile_enable(ctx, 1 if on else 0), "chol_profile_enable")
 
@@ -352,6 +408,9 @@ class Factor:
     def solve(self, B, X=None):
         return chol_solve(self.ctx.handle, self.handle, B, X)
 
+    def autotune(self, reps=1):
+        return chol_autotune(self.ctx.handle, self.handle, reps)
+
     def refine(self, B, X=None, tol=1e-12, maxit=10, check=True):
         return chol_refine(self.ctx.handle, self.handle, B, X, tol, maxit, check)
 
@@ -359,5 +418,27 @@ class Factor:
         try:
             if self.handle:
                 chol_free_num(self.handle)
+        except Exception:
+            pass
+
+
+class Batch:
+    """Batched factorization of several factors (same context, precision, assembly)."""
+
+    def __init__(self, ctx: Context, factors):
+        self.ctx, self.factors = ctx, list(factors)
+        self.handle = chol_batch_create(ctx.handle, [f.handle for f in self.factors])
+
+    def factorize(self, vals=None, use_graph=True):
+        chol_batch_factorize(self.ctx.handle, self.handle, vals, use_graph)
+
+    def close(self):
+        if self.handle:
+            chol_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

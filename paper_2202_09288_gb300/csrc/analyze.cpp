@@ -24,10 +24,11 @@ namespace chol {
 
 namespace {
 
-// Tile class of a supernode's Schur update, given how many 64-tiles its level holds.
-int choose_tile_class(int64_t u, int64_t level_tiles64) {
-  if (u >= 64 && level_tiles64 >= 2 * 152) return kTile64;
-  if (u > 16) return kTile32;
+// Tile class of a supernode's Schur update (u off-diagonal rows), given how many 64-tiles
+// its level holds.
+int choose_tile_class(const TilePolicy& p, int64_t u, int64_t level_tiles64) {
+  if (u >= p.min_rows_tile64 && level_tiles64 >= p.min_level_tiles64) return kTile64;
+  if (u >= p.min_rows_tile32) return kTile32;
   return kTile16;
 }
 
@@ -296,13 +297,7 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
   S->max_fwd_per_level = 0;
   S->stage_elems = 0;
   for (int32_t l = 0; l < S->nlev; l++) {
-    int64_t tiles64 = 0, stage = 0;
-    for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
-      int32_t s = S->lvl_sn[q];
-      int64_t u = S->sn_m[s] - (S->sn_start[s + 1] - S->sn_start[s]);
-      int64_t nt = (u + 63) / 64;
-      tiles64 += nt * (nt + 1) / 2;
-    }
+    int64_t stage = 0;
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
       const int32_t s = S->lvl_sn[q];
       const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
@@ -320,12 +315,6 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
         push4(S->tasks[kTaskBwd], s, r0, 0, 0);
       }
       if (u > 0) {
-        int cls = choose_tile_class(u, tiles64);
-        int T = tile_of_class(cls);
-        S->lvl_flops[kTaskSchur64 + cls][l] += du * (du + 1) * dn;
-        for (int32_t i0 = 0; i0 < u; i0 += T)
-          for (int32_t k0 = 0; k0 <= i0; k0 += T)
-            push4(S->tasks[kTaskSchur64 + cls], s, i0, k0, 0);
         S->sn_ustage[s] = stage;
         stage += (int64_t)u * u;
       }
@@ -400,7 +389,39 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
       S->fg_lvl.push_back((int64_t)S->fg_row.size());
     }
   }
+  build_schur_tasks(S, TilePolicy());
   return CHOL_OK;
+}
+
+void build_schur_tasks(Sym* S, const TilePolicy& policy) {
+  S->policy = policy;
+  for (int k = kTaskSchur64; k <= kTaskSchur16; k++) {
+    S->tasks[k].clear();
+    S->task_off[k].assign(S->nlev + 1, 0);
+    S->lvl_flops[k].assign(S->nlev, 0.0);
+  }
+  for (int32_t l = 0; l < S->nlev; l++) {
+    int64_t tiles64 = 0;
+    for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
+      const int32_t s = S->lvl_sn[q];
+      const int64_t u = S->sn_m[s] - (S->sn_start[s + 1] - S->sn_start[s]);
+      const int64_t nt = (u + 63) / 64;
+      tiles64 += nt * (nt + 1) / 2;
+    }
+    for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
+      const int32_t s = S->lvl_sn[q];
+      const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
+      const int32_t u = S->sn_m[s] - w;
+      if (u <= 0) continue;
+      const int cls = choose_tile_class(policy, u, tiles64);
+      const int T = tile_of_class(cls);
+      S->lvl_flops[kTaskSchur64 + cls][l] += (double)u * (u + 1.0) * w;
+      for (int32_t i0 = 0; i0 < u; i0 += T)
+        for (int32_t k0 = 0; k0 <= i0; k0 += T) push4(S->tasks[kTaskSchur64 + cls], s, i0, k0, 0);
+    }
+    for (int k = kTaskSchur64; k <= kTaskSchur16; k++)
+      S->task_off[k][l + 1] = (int64_t)S->tasks[k].size() / 4;
+  }
 }
 
 }  // namespace chol

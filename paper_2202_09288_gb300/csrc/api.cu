@@ -15,106 +15,12 @@
 #include "api_internal.h"
 #include "chol_internal.h"
 #include "kernels.h"
+#include "runtime.h"
 
-using chol::MatDev;
-using chol::SnDev;
-using chol::Sym;
+using namespace chol::rt;
 
-// Kernel kinds of the tracing counters.
-enum ProfKindId {
-  kProfAssemble, kProfPotrf, kProfTrsm, kProfSchur64, kProfSchur32, kProfSchur16,
-  kProfAsmOwner, kProfFwd, kProfBwd, kProfPerm, kProfScale, kProfPotrfF32, kProfTrsmF32,
-  kProfSchur64F32, kProfSchur32F32, kProfSchur16F32, kProfRefine, kNumProf
-};
-static const char* kProfNames[kNumProf] = {
-    "assemble",    "potrf_f64",   "trsm_f64",    "schur64_f64",  "schur32_f64",
-    "schur16_f64", "assemble_owner", "solve_fwd", "solve_bwd",   "solve_perm",
-    "equilibrate", "potrf_f32",   "trsm_f32",    "schur64_f32",  "schur32_f32",
-    "schur16_f32", "refine"};
-
-struct ProfPending {
-  int kind;
-  cudaEvent_t a, b;
-  double flops, bytes;
-};
-
-struct chol_ctx {
-  chol_opts opts;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  cudaMemPool_t pool = nullptr;
-  size_t held = 0;
-  bool attrs_set = false;
-  // tracing
-  bool prof_on = false;
-  chol_prof_entry prof[kNumProf];
-  std::vector<ProfPending> pending;
-  std::vector<cudaEvent_t> spare_events;
-  cudaEvent_t open_event = nullptr;
-  // handles holding device memory of this context; chol_destroy detaches them
-  std::set<chol_sym*> syms;
-  std::set<chol_num*> nums;
-  std::unordered_map<void*, size_t> sizes;  // live allocations (budget accounting)
-};
-
-struct DevSym {
-  int device = -1;
-  int32_t* rows = nullptr;
-  int32_t* col2sn = nullptr;
-  int64_t* amap = nullptr;
-  int32_t* perm = nullptr;
-  int32_t* iperm = nullptr;
-  int64_t* a_colptr = nullptr;
-  int32_t* a_rowind = nullptr;
-  int64_t* csr_ptr = nullptr;
-  int32_t* csr_col = nullptr;
-  int32_t* csr_src = nullptr;
-  int4* tasks[chol::kNumTaskKinds] = {};
-  int4* asm_src = nullptr;
-  int64_t* fg_ptr = nullptr;
-  int32_t* fg_row = nullptr;
-  int32_t* fg_ent = nullptr;
-  size_t bytes = 0;
-};
-
-struct chol_sym {
-  Sym S;
-  DevSym dev;
-  chol_ctx* ctx = nullptr;  // context that holds dev (set at upload)
-  int64_t max_bwd_per_level = 0;
-};
-
-struct chol_num {
-  chol_ctx* ctx = nullptr;
-  const chol_sym* sym = nullptr;
-  int precision = CHOL_FP64;
-  int assembly = CHOL_ASSEMBLY_ATOMIC;
-  void* L = nullptr;           // panels (double, or float for CHOL_MIXED)
-  SnDev* d_sn = nullptr;
-  MatDev* d_mat = nullptr;
-  unsigned long long* d_err = nullptr;  // [0] failing column + 1, [1] map misses,
-                                        // [2] FP64 pivot redos
-  double* d_vals = nullptr;    // device copy of A's values (assembly and residual)
-  double* d_stage = nullptr;   // owner assembly staging
-  double* d_scale = nullptr;   // CHOL_MIXED: equilibration a_jj^{-1/2}
-  // solve workspace, grown on demand
-  int64_t ws_nrhs = 0;
-  double* d_y = nullptr;
-  double* d_w = nullptr;
-  double* d_part = nullptr;
-  double* d_bx = nullptr;      // host-call staging of B / X
-  double* d_fstage = nullptr;  // owner-ordered forward-solve staging
-  // refinement workspace
-  int64_t rws_nrhs = 0;
-  double* d_rr = nullptr;      // residual
-  double* d_rd = nullptr;      // correction
-  double* d_rb = nullptr;      // host-call staging of B
-  unsigned long long* d_norm = nullptr;  // per-column max |r|, max |x|, and ||A||_inf
-  double anorm = -1.0;         // ||A||_inf of the current values (-1: not computed)
-  chol_num* fb = nullptr;      // FP64 factor made when refinement of a mixed one stalls
-};
-
-namespace {
+namespace chol {
+namespace rt {
 
 constexpr int kNormSlots = 2 * 32 + 1;
 
@@ -280,8 +186,9 @@ const int4* task_ptr(const chol_sym* s, int kind, int32_t level, int* count) {
   return s->dev.tasks[kind] + a;
 }
 
-// Enqueues the numeric factorization of the values in f->d_vals.
-int enqueue_factor(chol_num* f) {
+// Zeroes the panels and error words of f and assembles its values (f->d_vals) into them
+// (FP64), or equilibrates and assembles them (CHOL_MIXED).
+int enqueue_assembly(chol_num* f) {
   chol_ctx* c = f->ctx;
   const chol_sym* sym = f->sym;
   const Sym& S = sym->S;
@@ -305,41 +212,97 @@ int enqueue_factor(chol_num* f) {
     chol::launch_assemble(f->d_vals, sym->dev.amap, S.nnz_a, f->L, false, st);
     prof_end(c, kProfAssemble, 0.0, (double)S.l_storage * esz + 16.0 * S.nnz_a + 8.0 * S.nnz_a);
   }
-  const bool owner = f->assembly == CHOL_ASSEMBLY_OWNER;
+  return CHOL_OK;
+}
+
+// The task lists of one matrix, as a view for enqueue_levels.
+TaskView sym_view(const chol_sym* sym) {
+  const Sym& S = sym->S;
+  TaskView v;
+  for (int k = 0; k < chol::kNumTaskKinds; k++) {
+    v.d[k] = sym->dev.tasks[k];
+    v.off[k] = S.task_off[k].data();
+    v.flops[k] = S.lvl_flops[k].data();
+  }
+  v.asm_src = sym->dev.asm_src;
+  v.nlev = S.nlev;
+  v.max_width = (int)S.max_width;
+  return v;
+}
+
+// Per level: POTRF, TRSM, the Schur tile classes and (owner mode) the ordered assembly,
+// each one launch over the level's tasks of every matrix in the view.
+int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
+                   bool f32, bool owner) {
+  cudaStream_t st = c->stream;
   const float tau = (float)(c->opts.pivot_tau > 0 ? c->opts.pivot_tau : 1e-5);
   const int kp = f32 ? kProfPotrfF32 : kProfPotrf, kt = f32 ? kProfTrsmF32 : kProfTrsm;
   const int ks = f32 ? kProfSchur64F32 : kProfSchur64;
-  for (int32_t l = 0; l < S.nlev; l++) {
+  for (int32_t l = 0; l < v.nlev; l++) {
     int cnt;
-    const int4* t = task_ptr(sym, chol::kTaskPotrf, l, &cnt);
-    prof_begin(c);
-    chol::launch_potrf(t, cnt, f->d_sn, f->d_mat, (int)S.max_width, f32, tau, st);
-    prof_end(c, kp, S.lvl_flops[chol::kTaskPotrf][l], 0.0);
-    t = task_ptr(sym, chol::kTaskTrsm, l, &cnt);
+    const int4* t = v.level(chol::kTaskPotrf, l, &cnt);
     if (cnt > 0) {
       prof_begin(c);
-      chol::launch_trsm(t, cnt, f->d_sn, (int)S.max_width, f32, st);
-      prof_end(c, kt, S.lvl_flops[chol::kTaskTrsm][l], 0.0);
+      chol::launch_potrf(t, cnt, sns, mats, v.max_width, f32, tau, st);
+      prof_end(c, kp, v.flops[chol::kTaskPotrf][l], 0.0);
+    }
+    t = v.level(chol::kTaskTrsm, l, &cnt);
+    if (cnt > 0) {
+      prof_begin(c);
+      chol::launch_trsm(t, cnt, sns, v.max_width, f32, st);
+      prof_end(c, kt, v.flops[chol::kTaskTrsm][l], 0.0);
     }
     for (int cls = 0; cls < chol::kNumTileClasses; cls++) {
-      t = task_ptr(sym, chol::kTaskSchur64 + cls, l, &cnt);
+      t = v.level(chol::kTaskSchur64 + cls, l, &cnt);
       if (cnt <= 0) continue;
       prof_begin(c);
-      chol::launch_schur(cls, t, cnt, f->d_sn, f->d_mat, f->d_stage, owner, f32, st);
-      prof_end(c, ks + cls, S.lvl_flops[chol::kTaskSchur64 + cls][l], 0.0);
+      chol::launch_schur(cls, t, cnt, sns, mats, owner, f32, st);
+      prof_end(c, ks + cls, v.flops[chol::kTaskSchur64 + cls][l], 0.0);
     }
     if (owner) {
-      t = task_ptr(sym, chol::kTaskAsm, l, &cnt);
+      t = v.level(chol::kTaskAsm, l, &cnt);
       if (cnt > 0) {
         prof_begin(c);
-        chol::launch_assemble_owner(t, cnt, sym->dev.asm_src, f->d_sn, f->d_mat, f->d_stage, f32,
-                                    st);
+        chol::launch_assemble_owner(t, cnt, v.asm_src, sns, mats, f32, st);
         prof_end(c, kProfAsmOwner, 0.0, 0.0);
       }
     }
   }
   CK(cudaGetLastError());
   return CHOL_OK;
+}
+
+// Enqueues the numeric factorization of the values in f->d_vals.
+int enqueue_factor(chol_num* f) {
+  int rc = enqueue_assembly(f);
+  if (rc) return rc;
+  return enqueue_levels(f->ctx, sym_view(f->sym), f->d_sn, f->d_mat,
+                        f->precision == CHOL_MIXED, f->assembly == CHOL_ASSEMBLY_OWNER);
+}
+
+// Device descriptors of f's supernodes (matrix slot `mat`) and of f itself.
+void fill_descriptors(const chol_num* f, int mat, int32_t sn_base, std::vector<SnDev>* sn,
+                      MatDev* md) {
+  const chol_sym* sym = f->sym;
+  const Sym& S = sym->S;
+  const size_t esz = f->precision == CHOL_MIXED ? sizeof(float) : sizeof(double);
+  const size_t first = sn->size();
+  sn->resize(first + S.ns);
+  for (int32_t s = 0; s < S.ns; s++) {
+    SnDev& d = (*sn)[first + s];
+    d.L = (char*)f->L + (size_t)S.sn_valptr[s] * esz;
+    d.rows = sym->dev.rows + S.sn_rowptr[s];
+    d.n = S.sn_start[s + 1] - S.sn_start[s];
+    d.m = S.sn_m[s];
+    d.col0 = S.sn_start[s];
+    d.mat = mat;
+    d.ustage = S.sn_ustage[s];
+  }
+  md->col2sn = sym->dev.col2sn;
+  md->sn_base = sn_base;
+  md->pad0 = 0;
+  md->stage = f->d_stage;
+  md->err = f->d_err;
 }
 
 int ensure_solve_ws(chol_num* f, int64_t nrhs) {
@@ -447,21 +410,9 @@ int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int p
     delete f;
     return rc;
   }
-  std::vector<SnDev> sn(S.ns);
-  for (int32_t s = 0; s < S.ns; s++) {
-    sn[s].L = (char*)f->L + (size_t)S.sn_valptr[s] * esz;
-    sn[s].rows = sym->dev.rows + S.sn_rowptr[s];
-    sn[s].n = S.sn_start[s + 1] - S.sn_start[s];
-    sn[s].m = S.sn_m[s];
-    sn[s].col0 = S.sn_start[s];
-    sn[s].mat = 0;
-    sn[s].ustage = S.sn_ustage[s];
-  }
+  std::vector<SnDev> sn;
   MatDev md;
-  md.col2sn = sym->dev.col2sn;
-  md.sn_base = 0;
-  md.pad0 = 0;
-  md.err = f->d_err;
+  fill_descriptors(f, 0, 0, &sn, &md);
   if (cudaMemcpyAsync(f->d_sn, sn.data(), sn.size() * sizeof(SnDev), cudaMemcpyHostToDevice,
                       c->stream) != cudaSuccess ||
       cudaMemcpyAsync(f->d_mat, &md, sizeof(md), cudaMemcpyHostToDevice, c->stream) !=
@@ -571,7 +522,8 @@ int refine_pass(chol_num* f, chol_num* g, int k, const double* B, int64_t ldb, d
   }
 }
 
-}  // namespace
+}  // namespace rt
+}  // namespace chol
 
 namespace chol {
 
@@ -723,6 +675,7 @@ void chol_destroy(chol_ctx* c) {
   if (c->open_event) cudaEventDestroy(c->open_event);
   // detach handles that still hold device memory of this context (their later free_* or
   // any other call sees no context and does nothing / returns CHOL_E_INVALID)
+  detach_batches(c);
   while (!c->nums.empty()) free_num_buffers(*c->nums.begin());
   while (!c->syms.empty()) free_devsym(*c->syms.begin());
   cudaStreamSynchronize(c->stream);

@@ -48,13 +48,24 @@ struct alignas(16) MatDev {
   const int32_t* col2sn;          // column -> supernode index (matrix-local)
   int32_t sn_base;                // index of supernode 0 of this matrix in the SnDev array
   int32_t pad0;
+  void* stage;                    // owner assembly: the level staging buffer of this matrix
   unsigned long long* err;        // err[0]: smallest failing column + 1 (all ones = none),
                                   // kept by atomicMin;
                                   // err[1]: relative-map misses (internal check, 0 expected)
 };
 
+// Which Schur tile size a supernode gets (autotuned per matrix family): 64x64 tiles when it
+// has at least min_rows_tile64 off-diagonal rows and its level holds at least
+// min_level_tiles64 such tiles, else 32x32 from min_rows_tile32 rows, else 16x16.
+struct TilePolicy {
+  int min_rows_tile64 = 64;
+  int min_rows_tile32 = 17;
+  int min_level_tiles64 = 2 * 152;
+};
+
 // Host-side symbolic analysis result.
 struct Sym {
+  TilePolicy policy;
   int64_t n = 0, nnz_a = 0;
   int width_cap = 64;
   std::vector<int32_t> perm, iperm;
@@ -103,5 +114,7 @@ struct Sym {
 // Host analysis (analyze.cpp).  Returns CHOL_OK or CHOL_E_INVALID.
 int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32_t* perm,
             int width_cap, Sym* out);
+// (Re)builds the Schur tile task lists of every level under a tile policy.
+void build_schur_tasks(Sym* S, const TilePolicy& policy);
 
 }  // namespace chol

@@ -18,6 +18,7 @@
 
 #include "chol_internal.h"
 #include "kernels.h"
+#include "launch_util.h"
 
 namespace chol {
 
@@ -60,46 +61,49 @@ __global__ void k_assemble(const double* __restrict__ vals, const int64_t* __res
 // One CTA per supernode; the n x n lower block is factored in shared memory by the
 // unblocked right-looking column algorithm: pivot sqrt, column scale, rank-1 update.
 template <typename T>
-__global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks,
+__global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, int ntasks,
                                                const SnDev* __restrict__ sns,
                                                const MatDev* __restrict__ mats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
-  const int4 tk = tasks[blockIdx.x];
-  const SnDev d = sns[tk.x];
-  const int n = d.n, m = d.m;
-  T* L = reinterpret_cast<T*>(d.L);
-  __shared__ T piv_inv;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    int c = idx / n, r = idx - c * n;
-    A[idx] = r >= c ? L[(int64_t)c * m + r] : T(0);
-  }
-  __syncthreads();
-  for (int j = 0; j < n; j++) {
-    if (threadIdx.x == 0) {
-      T p = A[j * n + j];
-      if (!(p > T(0))) {
-        record_error(mats[d.mat], d.col0 + j);
-        p = T(1);
+  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+    const int4 tk = tasks[tq];
+    const SnDev d = sns[tk.x];
+    const int n = d.n, m = d.m;
+    T* L = reinterpret_cast<T*>(d.L);
+    __shared__ T piv_inv;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      int c = idx / n, r = idx - c * n;
+      A[idx] = r >= c ? L[(int64_t)c * m + r] : T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+      if (threadIdx.x == 0) {
+        T p = A[j * n + j];
+        if (!(p > T(0))) {
+          record_error(mats[d.mat], d.col0 + j);
+          p = T(1);
+        }
+        T s = sqrt(p);
+        A[j * n + j] = s;
+        piv_inv = T(1) / s;
       }
-      T s = sqrt(p);
-      A[j * n + j] = s;
-      piv_inv = T(1) / s;
+      __syncthreads();
+      const T inv = piv_inv;
+      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] *= inv;
+      __syncthreads();
+      const int nt = n - j - 1;
+      for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
+        int c = idx / nt, r = idx - c * nt;
+        if (r >= c) A[(j + 1 + c) * n + j + 1 + r] -= A[j * n + j + 1 + r] * A[j * n + j + 1 + c];
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      int c = idx / n, r = idx - c * n;
+      if (r >= c) L[(int64_t)c * m + r] = A[idx];
     }
     __syncthreads();
-    const T inv = piv_inv;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] *= inv;
-    __syncthreads();
-    const int nt = n - j - 1;
-    for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
-      int c = idx / nt, r = idx - c * nt;
-      if (r >= c) A[(j + 1 + c) * n + j + 1 + r] -= A[j * n + j + 1 + r] * A[j * n + j + 1 + c];
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    int c = idx / n, r = idx - c * n;
-    if (r >= c) L[(int64_t)c * m + r] = A[idx];
   }
 }
 
@@ -107,33 +111,36 @@ __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks,
 // Task {s, r0}: rows r0 .. r0+31 of L21 (panel rows n + r0 + t), one row per thread:
 // x_j = (a_j - sum_{k<j} x_k L_jk) / L_jj, i.e. L21 = A21 L11^{-T}.
 template <typename T>
-__global__ void __launch_bounds__(kTrsmRows) k_trsm(const int4* __restrict__ tasks,
+__global__ void __launch_bounds__(kTrsmRows) k_trsm(const int4* __restrict__ tasks, int ntasks,
                                                     const SnDev* __restrict__ sns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int4 tk = tasks[blockIdx.x];
-  const SnDev d = sns[tk.x];
-  const int n = d.n, m = d.m;
-  T* L = reinterpret_cast<T*>(d.L);
-  T* L11 = reinterpret_cast<T*>(smem_raw);  // n x n, column-major, ld n
-  T* rdiag = L11 + n * n;                   // n
-  T* X = rdiag + n;                         // n x 32: X[k * 32 + t]
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    int c = idx / n, r = idx - c * n;
-    L11[idx] = r >= c ? L[(int64_t)c * m + r] : T(0);
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) rdiag[j] = T(1) / L11[j * n + j];
-  __syncthreads();
-  const int t = threadIdx.x;
-  const int row = n + tk.y + t;
-  if (row < m) {
-    for (int j = 0; j < n; j++) {
-      T acc = L[(int64_t)j * m + row];
-      for (int k = 0; k < j; k++) acc -= X[k * kTrsmRows + t] * L11[k * n + j];
-      acc *= rdiag[j];
-      X[j * kTrsmRows + t] = acc;
-      L[(int64_t)j * m + row] = acc;
+  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+    const int4 tk = tasks[tq];
+    const SnDev d = sns[tk.x];
+    const int n = d.n, m = d.m;
+    T* L = reinterpret_cast<T*>(d.L);
+    T* L11 = reinterpret_cast<T*>(smem_raw);  // n x n, column-major, ld n
+    T* rdiag = L11 + n * n;                   // n
+    T* X = rdiag + n;                         // n x 32: X[k * 32 + t]
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      int c = idx / n, r = idx - c * n;
+      L11[idx] = r >= c ? L[(int64_t)c * m + r] : T(0);
     }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) rdiag[j] = T(1) / L11[j * n + j];
+    __syncthreads();
+    const int t = threadIdx.x;
+    const int row = n + tk.y + t;
+    if (row < m) {
+      for (int j = 0; j < n; j++) {
+        T acc = L[(int64_t)j * m + row];
+        for (int k = 0; k < j; k++) acc -= X[k * kTrsmRows + t] * L11[k * n + j];
+        acc *= rdiag[j];
+        X[j * kTrsmRows + t] = acc;
+        L[(int64_t)j * m + row] = acc;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -225,8 +232,8 @@ __device__ __forceinline__ void dmma_884(double (&c)[2], double a, double b) {
 
 template <int TILE, bool OWNER>
 __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
-    k_schur_f64(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
-                const MatDev* __restrict__ mats, double* __restrict__ stage) {
+    k_schur_f64(const int4* __restrict__ tasks, int ntasks, const SnDev* __restrict__ sns,
+                const MatDev* __restrict__ mats) {
   using Cfg = SchurCfg<TILE>;
   constexpr int KC = Cfg::KC, LDS = Cfg::LDS, MB = Cfg::MB;
   __shared__ __align__(16) double sh[2 * KC * LDS > TILE * (TILE + 1) ? 2 * KC * LDS
@@ -234,64 +241,68 @@ __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
   double* As = sh;              // [KC][LDS]: As[kk][ii] = L21[i0 + ii][kc + kk]
   double* Bs = sh + KC * LDS;   // [KC][LDS]: Bs[kk][jj] = L21[k0 + jj][kc + kk]
 
-  const int4 tk = tasks[blockIdx.x];
-  const SnDev d = sns[tk.x];
-  const int n = d.n, m = d.m, u = m - n;
-  const int i0 = tk.y, k0 = tk.z;
-  const double* L = reinterpret_cast<const double*>(d.L);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp / Cfg::WARPS_N, wn = warp % Cfg::WARPS_N;
+  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+    const int4 tk = tasks[tq];
+    const SnDev d = sns[tk.x];
+    const int n = d.n, m = d.m, u = m - n;
+    const int i0 = tk.y, k0 = tk.z;
+    const double* L = reinterpret_cast<const double*>(d.L);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp / Cfg::WARPS_N, wn = warp % Cfg::WARPS_N;
 
-  double acc[MB][MB][2];
-#pragma unroll
-  for (int a = 0; a < MB; a++)
-#pragma unroll
-    for (int b = 0; b < MB; b++) acc[a][b][0] = acc[a][b][1] = 0.0;
+    double acc[MB][MB][2];
+  #pragma unroll
+    for (int a = 0; a < MB; a++)
+  #pragma unroll
+      for (int b = 0; b < MB; b++) acc[a][b][0] = acc[a][b][1] = 0.0;
 
-  for (int kc = 0; kc < n; kc += KC) {
-    const int kw = min(KC, n - kc);
-    for (int idx = tid; idx < KC * TILE; idx += Cfg::THREADS) {
-      const int kk = idx / TILE, ii = idx - kk * TILE;
-      double va = 0.0, vb = 0.0;
-      if (kk < kw) {
-        const int64_t col = (int64_t)(kc + kk) * m + n;
-        if (i0 + ii < u) va = L[col + i0 + ii];
-        if (k0 + ii < u) vb = L[col + k0 + ii];
+    for (int kc = 0; kc < n; kc += KC) {
+      const int kw = min(KC, n - kc);
+      for (int idx = tid; idx < KC * TILE; idx += Cfg::THREADS) {
+        const int kk = idx / TILE, ii = idx - kk * TILE;
+        double va = 0.0, vb = 0.0;
+        if (kk < kw) {
+          const int64_t col = (int64_t)(kc + kk) * m + n;
+          if (i0 + ii < u) va = L[col + i0 + ii];
+          if (k0 + ii < u) vb = L[col + k0 + ii];
+        }
+        As[kk * LDS + ii] = va;
+        Bs[kk * LDS + ii] = vb;
       }
-      As[kk * LDS + ii] = va;
-      Bs[kk * LDS + ii] = vb;
+      __syncthreads();
+      const int ksteps = (kw + 3) >> 2;
+      for (int ks = 0; ks < ksteps; ks++) {
+        const int kr = ks * 4 + (lane & 3);
+        double af[MB], bf[MB];
+  #pragma unroll
+        for (int a = 0; a < MB; a++) af[a] = As[kr * LDS + wm * Cfg::WT + a * 8 + (lane >> 2)];
+  #pragma unroll
+        for (int b = 0; b < MB; b++) bf[b] = Bs[kr * LDS + wn * Cfg::WT + b * 8 + (lane >> 2)];
+  #pragma unroll
+        for (int a = 0; a < MB; a++)
+  #pragma unroll
+          for (int b = 0; b < MB; b++) dmma_884(acc[a][b], af[a], bf[b]);
+      }
+      __syncthreads();
     }
+    // accumulators -> shared tile Cs[kk][ii] (ld TILE + 1)
+    double* Cs = sh;
+  #pragma unroll
+    for (int a = 0; a < MB; a++)
+  #pragma unroll
+      for (int b = 0; b < MB; b++)
+  #pragma unroll
+        for (int e = 0; e < 2; e++) {
+          const int ii = wm * Cfg::WT + a * 8 + (lane >> 2);
+          const int kk = wn * Cfg::WT + b * 8 + (lane & 3) * 2 + e;
+          Cs[kk * (TILE + 1) + ii] = acc[a][b][e];
+        }
     __syncthreads();
-    const int ksteps = (kw + 3) >> 2;
-    for (int ks = 0; ks < ksteps; ks++) {
-      const int kr = ks * 4 + (lane & 3);
-      double af[MB], bf[MB];
-#pragma unroll
-      for (int a = 0; a < MB; a++) af[a] = As[kr * LDS + wm * Cfg::WT + a * 8 + (lane >> 2)];
-#pragma unroll
-      for (int b = 0; b < MB; b++) bf[b] = Bs[kr * LDS + wn * Cfg::WT + b * 8 + (lane >> 2)];
-#pragma unroll
-      for (int a = 0; a < MB; a++)
-#pragma unroll
-        for (int b = 0; b < MB; b++) dmma_884(acc[a][b], af[a], bf[b]);
-    }
+
+    schur_tile_epilogue<double, TILE, Cfg::THREADS, OWNER>(
+        Cs, d, i0, k0, sns, mats, static_cast<double*>(mats[d.mat].stage));
     __syncthreads();
   }
-  // accumulators -> shared tile Cs[kk][ii] (ld TILE + 1)
-  double* Cs = sh;
-#pragma unroll
-  for (int a = 0; a < MB; a++)
-#pragma unroll
-    for (int b = 0; b < MB; b++)
-#pragma unroll
-      for (int e = 0; e < 2; e++) {
-        const int ii = wm * Cfg::WT + a * 8 + (lane >> 2);
-        const int kk = wn * Cfg::WT + b * 8 + (lane & 3) * 2 + e;
-        Cs[kk * (TILE + 1) + ii] = acc[a][b][e];
-      }
-  __syncthreads();
-
-  schur_tile_epilogue<double, TILE, Cfg::THREADS, OWNER>(Cs, d, i0, k0, sns, mats, stage);
 }
 
 // ---- FP32 Schur tiles (mixed precision) -------------------------------------------------------
@@ -308,59 +319,63 @@ struct SchurF32Cfg {
 
 template <int TILE, bool OWNER>
 __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
-    k_schur_f32(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
-                const MatDev* __restrict__ mats, float* __restrict__ stage) {
+    k_schur_f32(const int4* __restrict__ tasks, int ntasks, const SnDev* __restrict__ sns,
+                const MatDev* __restrict__ mats) {
   using Cfg = SchurF32Cfg<TILE>;
   constexpr int KC = Cfg::KC, LDS = Cfg::LDS, S = Cfg::S;
   __shared__ __align__(16) float sh[2 * KC * LDS > TILE * (TILE + 1) ? 2 * KC * LDS
                                                                      : TILE * (TILE + 1)];
   float* As = sh;
   float* Bs = sh + KC * LDS;
-  const int4 tk = tasks[blockIdx.x];
-  const SnDev d = sns[tk.x];
-  const int n = d.n, m = d.m, u = m - n;
-  const int i0 = tk.y, k0 = tk.z;
-  const float* L = reinterpret_cast<const float*>(d.L);
-  const int tid = threadIdx.x, tx = tid % S, ty = tid / S;
-  float acc[4][4];
-#pragma unroll
-  for (int q = 0; q < 4; q++)
-#pragma unroll
-    for (int p = 0; p < 4; p++) acc[q][p] = 0.f;
-  for (int kc = 0; kc < n; kc += KC) {
-    const int kw = min(KC, n - kc);
-    for (int idx = tid; idx < KC * TILE; idx += Cfg::THREADS) {
-      const int kk = idx / TILE, ii = idx - kk * TILE;
-      float va = 0.f, vb = 0.f;
-      if (kk < kw) {
-        const int64_t col = (int64_t)(kc + kk) * m + n;
-        if (i0 + ii < u) va = L[col + i0 + ii];
-        if (k0 + ii < u) vb = L[col + k0 + ii];
+  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+    const int4 tk = tasks[tq];
+    const SnDev d = sns[tk.x];
+    const int n = d.n, m = d.m, u = m - n;
+    const int i0 = tk.y, k0 = tk.z;
+    const float* L = reinterpret_cast<const float*>(d.L);
+    const int tid = threadIdx.x, tx = tid % S, ty = tid / S;
+    float acc[4][4];
+  #pragma unroll
+    for (int q = 0; q < 4; q++)
+  #pragma unroll
+      for (int p = 0; p < 4; p++) acc[q][p] = 0.f;
+    for (int kc = 0; kc < n; kc += KC) {
+      const int kw = min(KC, n - kc);
+      for (int idx = tid; idx < KC * TILE; idx += Cfg::THREADS) {
+        const int kk = idx / TILE, ii = idx - kk * TILE;
+        float va = 0.f, vb = 0.f;
+        if (kk < kw) {
+          const int64_t col = (int64_t)(kc + kk) * m + n;
+          if (i0 + ii < u) va = L[col + i0 + ii];
+          if (k0 + ii < u) vb = L[col + k0 + ii];
+        }
+        As[kk * LDS + ii] = va;
+        Bs[kk * LDS + ii] = vb;
       }
-      As[kk * LDS + ii] = va;
-      Bs[kk * LDS + ii] = vb;
+      __syncthreads();
+      for (int kk = 0; kk < kw; kk++) {
+        float a[4], b[4];
+  #pragma unroll
+        for (int q = 0; q < 4; q++) a[q] = As[kk * LDS + ty + q * S];
+  #pragma unroll
+        for (int p = 0; p < 4; p++) b[p] = Bs[kk * LDS + tx + p * S];
+  #pragma unroll
+        for (int q = 0; q < 4; q++)
+  #pragma unroll
+          for (int p = 0; p < 4; p++) acc[q][p] = fmaf(a[q], b[p], acc[q][p]);
+      }
+      __syncthreads();
     }
+    float* Cs = sh;
+  #pragma unroll
+    for (int q = 0; q < 4; q++)
+  #pragma unroll
+      for (int p = 0; p < 4; p++) Cs[(tx + p * S) * (TILE + 1) + ty + q * S] = acc[q][p];
     __syncthreads();
-    for (int kk = 0; kk < kw; kk++) {
-      float a[4], b[4];
-#pragma unroll
-      for (int q = 0; q < 4; q++) a[q] = As[kk * LDS + ty + q * S];
-#pragma unroll
-      for (int p = 0; p < 4; p++) b[p] = Bs[kk * LDS + tx + p * S];
-#pragma unroll
-      for (int q = 0; q < 4; q++)
-#pragma unroll
-        for (int p = 0; p < 4; p++) acc[q][p] = fmaf(a[q], b[p], acc[q][p]);
-    }
+    schur_tile_epilogue<float, TILE, Cfg::THREADS, OWNER>(
+        Cs, d, i0, k0, sns, mats, static_cast<float*>(mats[d.mat].stage));
     __syncthreads();
   }
-  float* Cs = sh;
-#pragma unroll
-  for (int q = 0; q < 4; q++)
-#pragma unroll
-    for (int p = 0; p < 4; p++) Cs[(tx + p * S) * (TILE + 1) + ty + q * S] = acc[q][p];
-  __syncthreads();
-  schur_tile_epilogue<float, TILE, Cfg::THREADS, OWNER>(Cs, d, i0, k0, sns, mats, stage);
 }
 
 // ---- POTRF of the mixed-precision factor ---------------------------------------------------
@@ -368,75 +383,78 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
 // factored in FP32; if any pivot falls below tau (tau times the original diagonal, which
 // is 1 after equilibration), the block is factored again in FP64 from an FP64 copy of
 // its values, and the FP64 result is rounded into the panel.  err[2] counts such redos.
-__global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ tasks,
+__global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ tasks, int ntasks,
                                                      const SnDev* __restrict__ sns,
                                                      const MatDev* __restrict__ mats,
                                                      float tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int4 tk = tasks[blockIdx.x];
-  const SnDev d = sns[tk.x];
-  const int n = d.n, m = d.m;
-  float* L = reinterpret_cast<float*>(d.L);
-  double* D = reinterpret_cast<double*>(smem_raw);   // n x n FP64 copy
-  float* A = reinterpret_cast<float*>(D + n * n);    // n x n FP32 work block
-  __shared__ float fpiv_inv;
-  __shared__ double dpiv_inv;
-  __shared__ int redo;
-  if (threadIdx.x == 0) redo = 0;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    int c = idx / n, r = idx - c * n;
-    const float v = r >= c ? L[(int64_t)c * m + r] : 0.f;
-    A[idx] = v;
-    D[idx] = (double)v;
-  }
-  __syncthreads();
-  for (int j = 0; j < n; j++) {
-    if (threadIdx.x == 0) {
-      float p = A[j * n + j];
-      if (!(p >= tau)) { redo = 1; p = 1.f; }
-      const float s = sqrtf(p);
-      A[j * n + j] = s;
-      fpiv_inv = 1.f / s;
+  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+    const int4 tk = tasks[tq];
+    const SnDev d = sns[tk.x];
+    const int n = d.n, m = d.m;
+    float* L = reinterpret_cast<float*>(d.L);
+    double* D = reinterpret_cast<double*>(smem_raw);   // n x n FP64 copy
+    float* A = reinterpret_cast<float*>(D + n * n);    // n x n FP32 work block
+    __shared__ float fpiv_inv;
+    __shared__ double dpiv_inv;
+    __shared__ int redo;
+    if (threadIdx.x == 0) redo = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      int c = idx / n, r = idx - c * n;
+      const float v = r >= c ? L[(int64_t)c * m + r] : 0.f;
+      A[idx] = v;
+      D[idx] = (double)v;
     }
     __syncthreads();
-    if (redo) break;
-    const float inv = fpiv_inv;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] *= inv;
-    __syncthreads();
-    const int nt = n - j - 1;
-    for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
-      int c = idx / nt, r = idx - c * nt;
-      if (r >= c) A[(j + 1 + c) * n + j + 1 + r] -= A[j * n + j + 1 + r] * A[j * n + j + 1 + c];
-    }
-    __syncthreads();
-  }
-  if (redo) {
-    if (threadIdx.x == 0) atomicAdd(mats[d.mat].err + 2, 1ull);
     for (int j = 0; j < n; j++) {
       if (threadIdx.x == 0) {
-        double p = D[j * n + j];
-        if (!(p > 0.0)) { record_error(mats[d.mat], d.col0 + j); p = 1.0; }
-        const double s = sqrt(p);
-        D[j * n + j] = s;
-        dpiv_inv = 1.0 / s;
+        float p = A[j * n + j];
+        if (!(p >= tau)) { redo = 1; p = 1.f; }
+        const float s = sqrtf(p);
+        A[j * n + j] = s;
+        fpiv_inv = 1.f / s;
       }
       __syncthreads();
-      const double inv = dpiv_inv;
-      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) D[j * n + i] *= inv;
+      if (redo) break;
+      const float inv = fpiv_inv;
+      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] *= inv;
       __syncthreads();
       const int nt = n - j - 1;
       for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
         int c = idx / nt, r = idx - c * nt;
-        if (r >= c) D[(j + 1 + c) * n + j + 1 + r] -= D[j * n + j + 1 + r] * D[j * n + j + 1 + c];
+        if (r >= c) A[(j + 1 + c) * n + j + 1 + r] -= A[j * n + j + 1 + r] * A[j * n + j + 1 + c];
       }
       __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) A[idx] = (float)D[idx];
+    if (redo) {
+      if (threadIdx.x == 0) atomicAdd(mats[d.mat].err + 2, 1ull);
+      for (int j = 0; j < n; j++) {
+        if (threadIdx.x == 0) {
+          double p = D[j * n + j];
+          if (!(p > 0.0)) { record_error(mats[d.mat], d.col0 + j); p = 1.0; }
+          const double s = sqrt(p);
+          D[j * n + j] = s;
+          dpiv_inv = 1.0 / s;
+        }
+        __syncthreads();
+        const double inv = dpiv_inv;
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) D[j * n + i] *= inv;
+        __syncthreads();
+        const int nt = n - j - 1;
+        for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
+          int c = idx / nt, r = idx - c * nt;
+          if (r >= c) D[(j + 1 + c) * n + j + 1 + r] -= D[j * n + j + 1 + r] * D[j * n + j + 1 + c];
+        }
+        __syncthreads();
+      }
+      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) A[idx] = (float)D[idx];
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      int c = idx / n, r = idx - c * n;
+      if (r >= c) L[(int64_t)c * m + r] = A[idx];
+    }
     __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    int c = idx / n, r = idx - c * n;
-    if (r >= c) L[(int64_t)c * m + r] = A[idx];
   }
 }
 
@@ -450,36 +468,38 @@ constexpr int kAsmRowChunk = 1024;
 
 template <typename T>
 __global__ void __launch_bounds__(kAsmThreads)
-    k_assemble_owner(const int4* __restrict__ groups, const int4* __restrict__ srcs,
-                     const SnDev* __restrict__ sns, const MatDev* __restrict__ mats,
-                     const T* __restrict__ stage) {
+    k_assemble_owner(const int4* __restrict__ groups, int ntasks, const int4* __restrict__ srcs,
+                     const SnDev* __restrict__ sns, const MatDev* __restrict__ mats) {
   __shared__ int relpos[kAsmRowChunk];
-  const int4 g = groups[blockIdx.x];
-  const SnDev td = sns[g.x];
-  const MatDev md = mats[td.mat];
-  T* Lt = reinterpret_cast<T*>(td.L);
-  for (int q = g.z; q < g.w; q++) {
-    const int4 sr = srcs[q];
-    const SnDev sd = sns[sr.x];
-    const int u = sd.m - sd.n;
-    const int32_t* rows = sd.rows + sd.n;
-    const T* U = stage + sd.ustage;
-    for (int ib = sr.y; ib < u; ib += kAsmRowChunk) {
-      const int ilen = min(kAsmRowChunk, u - ib);
-      __syncthreads();
-      for (int ii = threadIdx.x; ii < ilen; ii += blockDim.x)
-        relpos[ii] = relative_row(md, td.rows, td.m, rows[ib + ii]);
-      __syncthreads();
-      const int kw = sr.z - sr.y;
-      for (int idx = threadIdx.x; idx < kw * ilen; idx += blockDim.x) {
-        const int kk = idx / ilen, ii = idx - kk * ilen;
-        const int k = sr.y + kk, i = ib + ii;
-        if (i >= k && relpos[ii] >= 0) {
-          const int c = rows[k] - td.col0;
-          Lt[(int64_t)c * td.m + relpos[ii]] -= U[(int64_t)k * u + i];
+  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+    const int4 g = groups[tq];
+    const SnDev td = sns[g.x];
+    const MatDev md = mats[td.mat];
+    T* Lt = reinterpret_cast<T*>(td.L);
+    for (int q = g.z; q < g.w; q++) {
+      const int4 sr = srcs[q];
+      const SnDev sd = sns[sr.x];
+      const int u = sd.m - sd.n;
+      const int32_t* rows = sd.rows + sd.n;
+      const T* U = static_cast<const T*>(md.stage) + sd.ustage;
+      for (int ib = sr.y; ib < u; ib += kAsmRowChunk) {
+        const int ilen = min(kAsmRowChunk, u - ib);
+        __syncthreads();
+        for (int ii = threadIdx.x; ii < ilen; ii += blockDim.x)
+          relpos[ii] = relative_row(md, td.rows, td.m, rows[ib + ii]);
+        __syncthreads();
+        const int kw = sr.z - sr.y;
+        for (int idx = threadIdx.x; idx < kw * ilen; idx += blockDim.x) {
+          const int kk = idx / ilen, ii = idx - kk * ilen;
+          const int k = sr.y + kk, i = ib + ii;
+          if (i >= k && relpos[ii] >= 0) {
+            const int c = rows[k] - td.col0;
+            Lt[(int64_t)c * td.m + relpos[ii]] -= U[(int64_t)k * u + i];
+          }
         }
       }
     }
+    __syncthreads();
   }
 }
 
@@ -501,62 +521,80 @@ static size_t trsm_smem(int w) {
 void launch_potrf(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
                   int max_width, bool f32, float tau, cudaStream_t st) {
   if (ntasks <= 0) return;
-  if (f32)
-    k_potrf_mixed<<<ntasks, 128, potrf_mixed_smem(max_width), st>>>(tasks, sns, mats, tau);
-  else
-    k_potrf<double><<<ntasks, 128, potrf_smem(max_width), st>>>(tasks, sns, mats);
+  if (f32) {
+    const size_t sm = potrf_mixed_smem(max_width);
+    k_potrf_mixed<<<persistent_grid(k_potrf_mixed, 128, sm, ntasks), 128, sm, st>>>(
+        tasks, ntasks, sns, mats, tau);
+  } else {
+    const size_t sm = potrf_smem(max_width);
+    k_potrf<double><<<persistent_grid(k_potrf<double>, 128, sm, ntasks), 128, sm, st>>>(
+        tasks, ntasks, sns, mats);
+  }
+}
+
+template <typename T>
+static void trsm_t(const int4* tasks, int ntasks, const SnDev* sns, int max_width, cudaStream_t st) {
+  const size_t sm = trsm_smem(max_width);
+  k_trsm<T><<<persistent_grid(k_trsm<T>, kTrsmRows, sm, ntasks), kTrsmRows, sm, st>>>(
+      tasks, ntasks, sns);
 }
 
 void launch_trsm(const int4* tasks, int ntasks, const SnDev* sns, int max_width, bool f32,
                  cudaStream_t st) {
   if (ntasks <= 0) return;
-  if (f32) k_trsm<float><<<ntasks, kTrsmRows, trsm_smem(max_width), st>>>(tasks, sns);
-  else k_trsm<double><<<ntasks, kTrsmRows, trsm_smem(max_width), st>>>(tasks, sns);
+  if (f32) trsm_t<float>(tasks, ntasks, sns, max_width, st);
+  else trsm_t<double>(tasks, ntasks, sns, max_width, st);
 }
 
-template <int T>
+template <int T, bool OWNER>
 static void schur_f64_t(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
-                        double* stage, bool owner, cudaStream_t st) {
-  if (owner)
-    k_schur_f64<T, true><<<ntasks, SchurCfg<T>::THREADS, 0, st>>>(tasks, sns, mats, stage);
-  else
-    k_schur_f64<T, false><<<ntasks, SchurCfg<T>::THREADS, 0, st>>>(tasks, sns, mats, stage);
+                        cudaStream_t st) {
+  constexpr int th = SchurCfg<T>::THREADS;
+  k_schur_f64<T, OWNER><<<persistent_grid(k_schur_f64<T, OWNER>, th, 0, ntasks), th, 0, st>>>(
+      tasks, ntasks, sns, mats);
 }
 
-template <int T>
+template <int T, bool OWNER>
 static void schur_f32_t(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
-                        float* stage, bool owner, cudaStream_t st) {
-  if (owner)
-    k_schur_f32<T, true><<<ntasks, SchurF32Cfg<T>::THREADS, 0, st>>>(tasks, sns, mats, stage);
-  else
-    k_schur_f32<T, false><<<ntasks, SchurF32Cfg<T>::THREADS, 0, st>>>(tasks, sns, mats, stage);
+                        cudaStream_t st) {
+  constexpr int th = SchurF32Cfg<T>::THREADS;
+  k_schur_f32<T, OWNER><<<persistent_grid(k_schur_f32<T, OWNER>, th, 0, ntasks), th, 0, st>>>(
+      tasks, ntasks, sns, mats);
 }
 
-void launch_schur(int cls, const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
-                  void* stage, bool owner, bool f32, cudaStream_t st) {
-  if (ntasks <= 0) return;
+template <bool OWNER>
+static void schur_cls(int cls, bool f32, const int4* tasks, int ntasks, const SnDev* sns,
+                      const MatDev* mats, cudaStream_t st) {
   if (f32) {
-    float* s = static_cast<float*>(stage);
-    if (cls == kTile64) schur_f32_t<64>(tasks, ntasks, sns, mats, s, owner, st);
-    else if (cls == kTile32) schur_f32_t<32>(tasks, ntasks, sns, mats, s, owner, st);
-    else schur_f32_t<16>(tasks, ntasks, sns, mats, s, owner, st);
+    if (cls == kTile64) schur_f32_t<64, OWNER>(tasks, ntasks, sns, mats, st);
+    else if (cls == kTile32) schur_f32_t<32, OWNER>(tasks, ntasks, sns, mats, st);
+    else schur_f32_t<16, OWNER>(tasks, ntasks, sns, mats, st);
   } else {
-    double* s = static_cast<double*>(stage);
-    if (cls == kTile64) schur_f64_t<64>(tasks, ntasks, sns, mats, s, owner, st);
-    else if (cls == kTile32) schur_f64_t<32>(tasks, ntasks, sns, mats, s, owner, st);
-    else schur_f64_t<16>(tasks, ntasks, sns, mats, s, owner, st);
+    if (cls == kTile64) schur_f64_t<64, OWNER>(tasks, ntasks, sns, mats, st);
+    else if (cls == kTile32) schur_f64_t<32, OWNER>(tasks, ntasks, sns, mats, st);
+    else schur_f64_t<16, OWNER>(tasks, ntasks, sns, mats, st);
   }
 }
 
+void launch_schur(int cls, const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
+                  bool owner, bool f32, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  if (owner) schur_cls<true>(cls, f32, tasks, ntasks, sns, mats, st);
+  else schur_cls<false>(cls, f32, tasks, ntasks, sns, mats, st);
+}
+
+template <typename T>
+static void asm_owner_t(const int4* groups, int ngroups, const int4* srcs, const SnDev* sns,
+                        const MatDev* mats, cudaStream_t st) {
+  k_assemble_owner<T><<<persistent_grid(k_assemble_owner<T>, kAsmThreads, 0, ngroups),
+                        kAsmThreads, 0, st>>>(groups, ngroups, srcs, sns, mats);
+}
+
 void launch_assemble_owner(const int4* groups, int ngroups, const int4* srcs, const SnDev* sns,
-                           const MatDev* mats, const void* stage, bool f32, cudaStream_t st) {
+                           const MatDev* mats, bool f32, cudaStream_t st) {
   if (ngroups <= 0) return;
-  if (f32)
-    k_assemble_owner<float><<<ngroups, kAsmThreads, 0, st>>>(groups, srcs, sns, mats,
-                                                             static_cast<const float*>(stage));
-  else
-    k_assemble_owner<double><<<ngroups, kAsmThreads, 0, st>>>(groups, srcs, sns, mats,
-                                                              static_cast<const double*>(stage));
+  if (f32) asm_owner_t<float>(groups, ngroups, srcs, sns, mats, st);
+  else asm_owner_t<double>(groups, ngroups, srcs, sns, mats, st);
 }
 
 template <typename K>

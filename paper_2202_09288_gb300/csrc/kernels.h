@@ -15,9 +15,9 @@ void launch_potrf(const int4* tasks, int ntasks, const SnDev* sns, const MatDev*
 void launch_trsm(const int4* tasks, int ntasks, const SnDev* sns, int max_width, bool f32,
                  cudaStream_t st);
 void launch_schur(int cls, const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
-                  void* stage, bool owner, bool f32, cudaStream_t st);
+                  bool owner, bool f32, cudaStream_t st);
 void launch_assemble_owner(const int4* groups, int ngroups, const int4* srcs, const SnDev* sns,
-                           const MatDev* mats, const void* stage, bool f32, cudaStream_t st);
+                           const MatDev* mats, bool f32, cudaStream_t st);
 int set_factor_kernel_attrs(int max_width);
 
 void launch_gather_perm(const double* B, int64_t ldb, const int32_t* perm, const double* scale,

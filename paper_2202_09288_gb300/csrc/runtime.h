@@ -1,0 +1,156 @@
+// runtime.h -- internal runtime state shared by the translation units of the library:
+// the handle structures behind the C ABI, device allocation, tracing and launch helpers.
+// Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <set>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/chol.h"
+#include "chol_internal.h"
+
+using chol::MatDev;
+using chol::SnDev;
+using chol::Sym;
+
+// Kernel kinds of the tracing counters.
+enum ProfKindId {
+  kProfAssemble, kProfPotrf, kProfTrsm, kProfSchur64, kProfSchur32, kProfSchur16,
+  kProfAsmOwner, kProfFwd, kProfBwd, kProfPerm, kProfScale, kProfPotrfF32, kProfTrsmF32,
+  kProfSchur64F32, kProfSchur32F32, kProfSchur16F32, kProfRefine, kProfGraph, kNumProf
+};
+inline const char* const kProfNames[kNumProf] = {
+    "assemble",    "potrf_f64",   "trsm_f64",    "schur64_f64",  "schur32_f64",
+    "schur16_f64", "assemble_owner", "solve_fwd", "solve_bwd",   "solve_perm",
+    "equilibrate", "potrf_f32",   "trsm_f32",    "schur64_f32",  "schur32_f32",
+    "schur16_f32", "refine",      "batch_graph"};
+
+struct ProfPending {
+  int kind;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+
+struct chol_ctx {
+  chol_opts opts;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaMemPool_t pool = nullptr;
+  size_t held = 0;
+  bool attrs_set = false;
+  // tracing
+  bool prof_on = false;
+  chol_prof_entry prof[kNumProf];
+  std::vector<ProfPending> pending;
+  std::vector<cudaEvent_t> spare_events;
+  cudaEvent_t open_event = nullptr;
+  // handles holding device memory of this context; chol_destroy detaches them
+  std::set<chol_sym*> syms;
+  std::set<chol_num*> nums;
+  std::set<chol_batch*> batches;
+  std::unordered_map<void*, size_t> sizes;  // live allocations (budget accounting)
+};
+
+struct DevSym {
+  int device = -1;
+  int32_t* rows = nullptr;
+  int32_t* col2sn = nullptr;
+  int64_t* amap = nullptr;
+  int32_t* perm = nullptr;
+  int32_t* iperm = nullptr;
+  int64_t* a_colptr = nullptr;
+  int32_t* a_rowind = nullptr;
+  int64_t* csr_ptr = nullptr;
+  int32_t* csr_col = nullptr;
+  int32_t* csr_src = nullptr;
+  int4* tasks[chol::kNumTaskKinds] = {};
+  int4* asm_src = nullptr;
+  int64_t* fg_ptr = nullptr;
+  int32_t* fg_row = nullptr;
+  int32_t* fg_ent = nullptr;
+  size_t bytes = 0;
+};
+
+struct chol_sym {
+  Sym S;
+  DevSym dev;
+  chol_ctx* ctx = nullptr;  // context that holds dev (set at upload)
+  int64_t max_bwd_per_level = 0;
+};
+
+struct chol_num {
+  chol_ctx* ctx = nullptr;
+  const chol_sym* sym = nullptr;
+  int precision = CHOL_FP64;
+  int assembly = CHOL_ASSEMBLY_ATOMIC;
+  void* L = nullptr;           // panels (double, or float for CHOL_MIXED)
+  SnDev* d_sn = nullptr;
+  MatDev* d_mat = nullptr;
+  unsigned long long* d_err = nullptr;  // [0] failing column + 1, [1] map misses,
+                                        // [2] FP64 pivot redos
+  double* d_vals = nullptr;    // device copy of A's values (assembly and residual)
+  double* d_stage = nullptr;   // owner assembly staging
+  double* d_scale = nullptr;   // CHOL_MIXED: equilibration a_jj^{-1/2}
+  // solve workspace, grown on demand
+  int64_t ws_nrhs = 0;
+  double* d_y = nullptr;
+  double* d_w = nullptr;
+  double* d_part = nullptr;
+  double* d_bx = nullptr;      // host-call staging of B / X
+  double* d_fstage = nullptr;  // owner-ordered forward-solve staging
+  // refinement workspace
+  int64_t rws_nrhs = 0;
+  double* d_rr = nullptr;      // residual
+  double* d_rd = nullptr;      // correction
+  double* d_rb = nullptr;      // host-call staging of B
+  unsigned long long* d_norm = nullptr;  // per-column max |r|, max |x|, and ||A||_inf
+  double anorm = -1.0;         // ||A||_inf of the current values (-1: not computed)
+  chol_num* fb = nullptr;      // FP64 factor made when refinement of a mixed one stalls
+};
+
+
+namespace chol {
+namespace rt {
+
+// Per-level task lists of one matrix or of a batch: kind k at level l is
+// d[k][off[k][l] .. off[k][l+1]) (device), with algorithmic flops flops[k][l] (host).
+struct TaskView {
+  const int4* d[kNumTaskKinds] = {};
+  const int64_t* off[kNumTaskKinds] = {};
+  const double* flops[kNumTaskKinds] = {};
+  const int4* asm_src = nullptr;
+  int32_t nlev = 0;
+  int max_width = 0;
+  const int4* level(int k, int32_t l, int* count) const {
+    *count = (int)(off[k][l + 1] - off[k][l]);
+    return d[k] + off[k][l];
+  }
+};
+
+int enqueue_assembly(chol_num* f);
+int enqueue_factor(chol_num* f);
+// Releases the device memory of every batch of c (called by chol_destroy).
+void detach_batches(chol_ctx* c);
+TaskView sym_view(const chol_sym* sym);
+int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
+                   bool f32, bool owner);
+void fill_descriptors(const chol_num* f, int mat, int32_t sn_base, std::vector<SnDev>* sn,
+                      MatDev* md);
+
+int dev_alloc(chol_ctx* c, void** p, size_t bytes);
+void dev_free(chol_ctx* c, void* p);
+void prof_begin(chol_ctx* c);
+void prof_end(chol_ctx* c, int k, double flops, double bytes);
+const int4* task_ptr(const chol_sym* s, int kind, int32_t level, int* count);
+int ensure_uploaded(chol_ctx* c, chol_sym* s);
+int ensure_attrs(chol_ctx* c);
+int ensure_solve_ws(chol_num* f, int64_t nrhs);
+int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx);
+int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int precision,
+                int assembly, chol_num** out);
+
+}  // namespace rt
+}  // namespace chol

@@ -20,6 +20,7 @@
 
 #include "chol_internal.h"
 #include "kernels.h"
+#include "launch_util.h"
 
 namespace chol {
 
@@ -110,50 +111,53 @@ __device__ void load_l11(const SnDev& d, double* L11, double* rdiag) {
 // staging slots (q * kSolveRows + ii) * nrhs + c instead of atomics into y.
 template <typename P, bool STAGE>
 __global__ void __launch_bounds__(kSolveThreads)
-    k_fwd(const int4* __restrict__ tasks, const SnDev* __restrict__ sns, int64_t ldv, int nrhs,
+    k_fwd(const int4* __restrict__ tasks, int ntasks, const SnDev* __restrict__ sns, int64_t ldv, int nrhs,
           double* __restrict__ y, double* __restrict__ w, double* __restrict__ fstage) {
   extern __shared__ __align__(16) double sm[];
-  const int4 tk = tasks[blockIdx.x];
-  const SnDev d = sns[tk.x];
-  const int n = d.n, m = d.m, u = m - n;
-  double* L11 = sm;
-  double* rdiag = L11 + n * n;
-  double* xs = rdiag + n;
-  for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
-    const int c = idx / n, j = idx - c * n;
-    xs[idx] = y[c * ldv + d.col0 + j];
-  }
-  load_l11<P>(d, L11, rdiag);
-  if (threadIdx.x < 32) warp_trisolve<true>(L11, rdiag, xs, n, nrhs);
-  __syncthreads();
-  if (tk.y == 0)
+  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+    const int4 tk = tasks[tq];
+    const SnDev d = sns[tk.x];
+    const int n = d.n, m = d.m, u = m - n;
+    double* L11 = sm;
+    double* rdiag = L11 + n * n;
+    double* xs = rdiag + n;
     for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
       const int c = idx / n, j = idx - c * n;
-      w[c * ldv + d.col0 + j] = xs[idx];
+      xs[idx] = y[c * ldv + d.col0 + j];
     }
-  const int i = tk.y + threadIdx.x;
-  if (i < u) {
-    const P* L = reinterpret_cast<const P*>(d.L) + n + i;
-    const int64_t grow = d.rows[n + i];
-    for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
-      double acc[kRhsChunk];
-#pragma unroll
-      for (int c = 0; c < kRhsChunk; c++) acc[c] = 0.0;
-      for (int j = 0; j < n; j++) {
-        const double l = (double)L[(int64_t)j * m];
-#pragma unroll
-        for (int c = 0; c < kRhsChunk; c++)
-          if (c0 + c < nrhs) acc[c] += l * xs[(c0 + c) * n + j];
+    load_l11<P>(d, L11, rdiag);
+    if (threadIdx.x < 32) warp_trisolve<true>(L11, rdiag, xs, n, nrhs);
+    __syncthreads();
+    if (tk.y == 0)
+      for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+        const int c = idx / n, j = idx - c * n;
+        w[c * ldv + d.col0 + j] = xs[idx];
       }
-#pragma unroll
-      for (int c = 0; c < kRhsChunk; c++) {
-        if (c0 + c >= nrhs) continue;
-        if (STAGE)
-          fstage[((int64_t)blockIdx.x * kSolveRows + threadIdx.x) * nrhs + c0 + c] = acc[c];
-        else
-          atomicAdd(&y[(int64_t)(c0 + c) * ldv + grow], -acc[c]);
+    const int i = tk.y + threadIdx.x;
+    if (i < u) {
+      const P* L = reinterpret_cast<const P*>(d.L) + n + i;
+      const int64_t grow = d.rows[n + i];
+      for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
+        double acc[kRhsChunk];
+  #pragma unroll
+        for (int c = 0; c < kRhsChunk; c++) acc[c] = 0.0;
+        for (int j = 0; j < n; j++) {
+          const double l = (double)L[(int64_t)j * m];
+  #pragma unroll
+          for (int c = 0; c < kRhsChunk; c++)
+            if (c0 + c < nrhs) acc[c] += l * xs[(c0 + c) * n + j];
+        }
+  #pragma unroll
+        for (int c = 0; c < kRhsChunk; c++) {
+          if (c0 + c >= nrhs) continue;
+          if (STAGE)
+            fstage[((int64_t)tq * kSolveRows + threadIdx.x) * nrhs + c0 + c] = acc[c];
+          else
+            atomicAdd(&y[(int64_t)(c0 + c) * ldv + grow], -acc[c]);
+        }
       }
     }
+    __syncthreads();
   }
 }
 
@@ -176,28 +180,31 @@ __global__ void k_fwd_gather(const int32_t* __restrict__ fg_row, const int64_t* 
 // Backward partials: the level's task q = blockIdx.x writes part[q * W * nrhs + c * W + j].
 template <typename P>
 __global__ void __launch_bounds__(kSolveThreads)
-    k_bwd_partial(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
+    k_bwd_partial(const int4* __restrict__ tasks, int ntasks, const SnDev* __restrict__ sns,
                   int64_t ldv, int nrhs, int W, const double* __restrict__ w,
                   double* __restrict__ part) {
   extern __shared__ __align__(16) double sm[];
-  const int4 tk = tasks[blockIdx.x];
-  const SnDev d = sns[tk.x];
-  const int n = d.n, m = d.m, u = m - n;
-  const int rb = min(kSolveRows, u - tk.y);
-  double* xg = sm;  // rb x nrhs
-  for (int idx = threadIdx.x; idx < rb * nrhs; idx += blockDim.x) {
-    const int c = idx / rb, i = idx - c * rb;
-    xg[idx] = w[c * ldv + d.rows[n + tk.y + i]];
-  }
-  __syncthreads();
-  double* out = part + (int64_t)blockIdx.x * W * nrhs;
-  const P* L = reinterpret_cast<const P*>(d.L) + n + tk.y;
-  for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
-    const int c = idx / n, j = idx - c * n;
-    double acc = 0.0;
-    const P* col = L + (int64_t)j * m;
-    for (int i = 0; i < rb; i++) acc += (double)col[i] * xg[c * rb + i];
-    out[c * W + j] = acc;
+  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+    const int4 tk = tasks[tq];
+    const SnDev d = sns[tk.x];
+    const int n = d.n, m = d.m, u = m - n;
+    const int rb = min(kSolveRows, u - tk.y);
+    double* xg = sm;  // rb x nrhs
+    for (int idx = threadIdx.x; idx < rb * nrhs; idx += blockDim.x) {
+      const int c = idx / rb, i = idx - c * rb;
+      xg[idx] = w[c * ldv + d.rows[n + tk.y + i]];
+    }
+    __syncthreads();
+    double* out = part + (int64_t)tq * W * nrhs;
+    const P* L = reinterpret_cast<const P*>(d.L) + n + tk.y;
+    for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+      const int c = idx / n, j = idx - c * n;
+      double acc = 0.0;
+      const P* col = L + (int64_t)j * m;
+      for (int i = 0; i < rb; i++) acc += (double)col[i] * xg[c * rb + i];
+      out[c * W + j] = acc;
+    }
+    __syncthreads();
   }
 }
 
@@ -205,30 +212,33 @@ __global__ void __launch_bounds__(kSolveThreads)
 // a global index into the backward task list, base the first task of this level.
 template <typename P>
 __global__ void __launch_bounds__(kSolveThreads)
-    k_bwd_diag(const int4* __restrict__ tasks, int64_t base, const SnDev* __restrict__ sns,
+    k_bwd_diag(const int4* __restrict__ tasks, int ntasks, int64_t base, const SnDev* __restrict__ sns,
                int64_t ldv, int nrhs, int W, const double* __restrict__ part,
                double* __restrict__ w) {
   extern __shared__ __align__(16) double sm[];
-  const int4 tk = tasks[blockIdx.x];
-  const SnDev d = sns[tk.x];
-  const int n = d.n;
-  double* L11 = sm;
-  double* rdiag = L11 + n * n;
-  double* xs = rdiag + n;
-  const int u = d.m - n;
-  for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
-    const int c = idx / n, j = idx - c * n;
-    double v = w[c * ldv + d.col0 + j];
-    if (u > 0)
-      for (int q = 0; q < tk.z; q++) v -= part[(tk.y - base + q) * W * nrhs + c * W + j];
-    xs[idx] = v;
-  }
-  load_l11<P>(d, L11, rdiag);
-  if (threadIdx.x < 32) warp_trisolve<false>(L11, rdiag, xs, n, nrhs);
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
-    const int c = idx / n, j = idx - c * n;
-    w[c * ldv + d.col0 + j] = xs[idx];
+  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+    const int4 tk = tasks[tq];
+    const SnDev d = sns[tk.x];
+    const int n = d.n;
+    double* L11 = sm;
+    double* rdiag = L11 + n * n;
+    double* xs = rdiag + n;
+    const int u = d.m - n;
+    for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+      const int c = idx / n, j = idx - c * n;
+      double v = w[c * ldv + d.col0 + j];
+      if (u > 0)
+        for (int q = 0; q < tk.z; q++) v -= part[(tk.y - base + q) * W * nrhs + c * W + j];
+      xs[idx] = v;
+    }
+    load_l11<P>(d, L11, rdiag);
+    if (threadIdx.x < 32) warp_trisolve<false>(L11, rdiag, xs, n, nrhs);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+      const int c = idx / n, j = idx - c * n;
+      w[c * ldv + d.col0 + j] = xs[idx];
+    }
+    __syncthreads();
   }
 }
 
@@ -258,9 +268,11 @@ static void fwd_t(const int4* tasks, int ntasks, const SnDev* sns, int64_t ldv, 
                   double* y, double* w, double* fstage, cudaStream_t st) {
   const size_t sm = solve_smem(W, nrhs);
   if (fstage)
-    k_fwd<P, true><<<ntasks, kSolveThreads, sm, st>>>(tasks, sns, ldv, nrhs, y, w, fstage);
+    k_fwd<P, true><<<persistent_grid(k_fwd<P, true>, kSolveThreads, sm, ntasks), kSolveThreads,
+                     sm, st>>>(tasks, ntasks, sns, ldv, nrhs, y, w, fstage);
   else
-    k_fwd<P, false><<<ntasks, kSolveThreads, sm, st>>>(tasks, sns, ldv, nrhs, y, w, nullptr);
+    k_fwd<P, false><<<persistent_grid(k_fwd<P, false>, kSolveThreads, sm, ntasks), kSolveThreads,
+                      sm, st>>>(tasks, ntasks, sns, ldv, nrhs, y, w, nullptr);
 }
 
 void launch_fwd(const int4* tasks, int ntasks, const SnDev* sns, int64_t ldv, int nrhs, int W,
@@ -282,12 +294,16 @@ template <typename P>
 static void bwd_t(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* diag_tasks,
                   int ndiag, const SnDev* sns, int64_t ldv, int nrhs, int W, double* w,
                   double* part, cudaStream_t st) {
-  if (nbwd > 0)
-    k_bwd_partial<P><<<nbwd, kSolveThreads, (size_t)kSolveRows * nrhs * sizeof(double), st>>>(
-        bwd_tasks, sns, ldv, nrhs, W, w, part);
-  if (ndiag > 0)
-    k_bwd_diag<P><<<ndiag, kSolveThreads, solve_smem(W, nrhs), st>>>(diag_tasks, bwd_base, sns,
-                                                                     ldv, nrhs, W, part, w);
+  if (nbwd > 0) {
+    const size_t sp = (size_t)kSolveRows * nrhs * sizeof(double);
+    k_bwd_partial<P><<<persistent_grid(k_bwd_partial<P>, kSolveThreads, sp, nbwd), kSolveThreads,
+                       sp, st>>>(bwd_tasks, nbwd, sns, ldv, nrhs, W, w, part);
+  }
+  if (ndiag > 0) {
+    const size_t sm = solve_smem(W, nrhs);
+    k_bwd_diag<P><<<persistent_grid(k_bwd_diag<P>, kSolveThreads, sm, ndiag), kSolveThreads, sm,
+                    st>>>(diag_tasks, ndiag, bwd_base, sns, ldv, nrhs, W, part, w);
+  }
 }
 
 void launch_bwd(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* diag_tasks,
