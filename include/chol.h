@@ -239,6 +239,65 @@ int chol_sym_set_tile_policy(chol_sym* sym, const chol_tile_policy* policy);
 int chol_autotune(chol_ctx* ctx, chol_num* num, int reps, chol_tile_policy* best,
                   double* best_ms);
 
+/* ---- serving -----------------------------------------------------------------------
+ * A server takes SPD systems as they arrive and answers each with a solution refined to
+ * its residual target (the paper has no serving layer).  Worker slots -- each a thread
+ * with its own context and stream on opts.device -- take the oldest queued requests that
+ * fit the HBM budget (up to max_batch at a time), factor them together as one batch,
+ * refine every request and complete it; a request that arrives while other groups are on
+ * the GPU starts as soon as a slot and memory are free (continuous batching).  Symbolic
+ * analyses stay resident per slot, keyed by pattern.  The budget is split: each slot may
+ * keep analyses worth budget / (4 slots) resident, the groups in flight share the rest;
+ * a request larger than that share alone completes with CHOL_E_OOM. */
+typedef struct chol_server chol_server;
+typedef struct chol_server_opts {
+  int device;
+  int slots;          /* worker slots (concurrent groups); 0 = 2 */
+  int max_batch;      /* requests factored together; 0 = 16 */
+  size_t hbm_budget;  /* device bytes the server may hold; 0 = no limit */
+  int width_cap;      /* as chol_opts; 0 = 64 */
+  int assembly;       /* as chol_opts */
+  int sym_cache;      /* analyses cached per slot; 0 = 64 */
+} chol_server_opts;
+
+typedef struct chol_request {
+  int64_t n;
+  const int64_t* colptr;  /* lower CSC of A, host (copied by chol_submit) */
+  const int32_t* rowind;
+  const double* vals;
+  const int32_t* perm;    /* ordering, perm[new] = old (copied) */
+  int64_t nrhs;           /* >= 1 */
+  const double* B;        /* n x nrhs column-major, host (copied) */
+  int64_t ldb;
+  double* X;              /* n x nrhs host output; must stay valid until the request ends */
+  int64_t ldx;
+  int precision;          /* CHOL_FP64 or CHOL_MIXED */
+  double tol;             /* residual target; 0 = 1e-12 */
+} chol_request;
+
+typedef struct chol_result {
+  int status;             /* CHOL_OK, or the error of the request */
+  int iterations;         /* refinement steps */
+  int fell_back;          /* a CHOL_MIXED request needed the FP64 factor */
+  double residual;        /* max_c ||b - A x||_inf / (||A||_inf ||x||_inf) */
+  double t_submit, t_start, t_done;  /* seconds on the server clock */
+  int batch_size;         /* requests factored in the same group */
+} chol_result;
+
+void chol_default_server_opts(chol_server_opts* opts);
+int chol_server_create(const chol_server_opts* opts, chol_server** out);
+/* Queues a request and returns at once with its ticket. */
+int chol_submit(chol_server* srv, const chol_request* req, uint64_t* ticket);
+/* CHOL_PENDING while the request runs; CHOL_OK with *result once it has ended (X then
+ * holds the solution); a ticket is reported once. */
+int chol_poll(chol_server* srv, uint64_t ticket, chol_result* result);
+/* Blocks until the request has ended, then as chol_poll. */
+int chol_wait(chol_server* srv, uint64_t ticket, chol_result* result);
+/* Seconds since the server was created (the clock of chol_result's times). */
+double chol_server_clock(chol_server* srv);
+/* Stops the slots (requests still queued are dropped) and frees the server. */
+void chol_server_destroy(chol_server* srv);
+
 /* ---- tracing ------------------------------------------------------------------------
  * Per-kernel-kind accounting of the device work a context enqueues: the launch count is
  * always kept; with profiling on, every launch is bracketed by CUDA events on the context

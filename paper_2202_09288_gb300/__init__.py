@@ -53,6 +53,25 @@ class chol_tile_policy(C.Structure):
                 ("min_level_tiles64", C.c_int)]
 
 
+class chol_server_opts(C.Structure):
+    _fields_ = [("device", C.c_int), ("slots", C.c_int), ("max_batch", C.c_int),
+                ("hbm_budget", C.c_size_t), ("width_cap", C.c_int), ("assembly", C.c_int),
+                ("sym_cache", C.c_int)]
+
+
+class chol_request(C.Structure):
+    _fields_ = [("n", C.c_int64), ("colptr", C.c_void_p), ("rowind", C.c_void_p),
+                ("vals", C.c_void_p), ("perm", C.c_void_p), ("nrhs", C.c_int64),
+                ("B", C.c_void_p), ("ldb", C.c_int64), ("X", C.c_void_p), ("ldx", C.c_int64),
+                ("precision", C.c_int), ("tol", C.c_double)]
+
+
+class chol_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("fell_back", C.c_int),
+                ("residual", C.c_double), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double), ("batch_size", C.c_int)]
+
+
 class chol_prof_entry(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double),
                 ("timed", C.c_int64), ("flops", C.c_double), ("bytes", C.c_double)]
@@ -86,6 +105,13 @@ EXPORTS = {
     "chol_sym_get_tile_policy": (_I, [_P, C.POINTER(chol_tile_policy)]),
     "chol_sym_set_tile_policy": (_I, [_P, C.POINTER(chol_tile_policy)]),
     "chol_autotune": (_I, [_P, _P, _I, C.POINTER(chol_tile_policy), C.POINTER(C.c_double)]),
+    "chol_default_server_opts": (None, [C.POINTER(chol_server_opts)]),
+    "chol_server_create": (_I, [C.POINTER(chol_server_opts), C.POINTER(_P)]),
+    "chol_submit": (_I, [_P, C.POINTER(chol_request), C.POINTER(C.c_uint64)]),
+    "chol_poll": (_I, [_P, C.c_uint64, C.POINTER(chol_result)]),
+    "chol_wait": (_I, [_P, C.c_uint64, C.POINTER(chol_result)]),
+    "chol_server_clock": (C.c_double, [_P]),
+    "chol_server_destroy": (None, [_P]),
     "chol_profile_enable": (_I, [_P, _I]),
     "chol_profile_read": (_I, [_P, C.POINTER(chol_prof_entry), _I, C.POINTER(_I)]),
     "chol_profile_reset": (_I, [_P]),
@@ -435,6 +461,69 @@ class Batch:
     def close(self):
         if self.handle:
             chol_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _result_dict(r: chol_result) -> dict:
+    return {f: getattr(r, f) for f, _ in chol_result._fields_}
+
+
+class Server:
+    """Request server with continuous batching (chol_server_create / chol_submit /
+    chol_poll / chol_wait).  Host arrays of a request are copied at submit, except X, which
+    the server fills: the Server keeps it alive until the result has been collected."""
+
+    def __init__(self, device=0, slots=2, max_batch=16, hbm_budget=0, width_cap=64,
+                 assembly=CHOL_ASSEMBLY_ATOMIC, sym_cache=64):
+        o = chol_server_opts()
+        lib().chol_default_server_opts(C.byref(o))
+        o.device, o.slots, o.max_batch, o.hbm_budget = device, slots, max_batch, hbm_budget
+        o.width_cap, o.assembly, o.sym_cache = width_cap, assembly, sym_cache
+        h = C.c_void_p()
+        _check(lib().chol_server_create(C.byref(o), C.byref(h)), "chol_server_create")
+        self.handle = h.value
+        self._outputs = {}
+
+    def submit(self, A, perm, B, precision=CHOL_FP64, tol=1e-12) -> int:
+        B2 = np.asfortranarray(np.asarray(B, dtype=np.float64).reshape(A.n, -1))
+        X = np.zeros_like(B2, order="F")
+        colptr = np.ascontiguousarray(A.colptr, np.int64)
+        rowind = np.ascontiguousarray(A.rowind, np.int32)
+        vals = np.ascontiguousarray(A.vals, np.float64)
+        perm = np.ascontiguousarray(perm, np.int32)
+        q = chol_request(A.n, colptr.ctypes.data, rowind.ctypes.data, vals.ctypes.data,
+                         perm.ctypes.data, B2.shape[1], B2.ctypes.data, A.n, X.ctypes.data,
+                         A.n, precision, tol)
+        t = C.c_uint64()
+        _check(lib().chol_submit(self.handle, C.byref(q), C.byref(t)), "chol_submit")
+        self._outputs[t.value] = X
+        return t.value
+
+    def poll(self, ticket):
+        r = chol_result()
+        rc = lib().chol_poll(self.handle, ticket, C.byref(r))
+        if rc == CHOL_PENDING:
+            return None
+        _check(rc, "chol_poll")
+        return self._outputs.pop(ticket), _result_dict(r)
+
+    def wait(self, ticket):
+        r = chol_result()
+        _check(lib().chol_wait(self.handle, ticket, C.byref(r)), "chol_wait")
+        return self._outputs.pop(ticket), _result_dict(r)
+
+    def clock(self) -> float:
+        return lib().chol_server_clock(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib().chol_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

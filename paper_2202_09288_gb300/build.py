@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "libchol.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["analyze.cpp", "api.cu", "factor_kernels.cu", "solve_kernels.cu", "noalloc.cu",
-           "refine_kernels.cu", "batch.cu"]
+           "refine_kernels.cu", "batch.cu", "serve.cu"]
 
 
 def nvcc() -> str:

@@ -386,7 +386,7 @@ void free_num_buffers(chol_num* f) {
 
 // Allocates a factor and enqueues its numeric factorization of vals.
 int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int precision,
-                int assembly, chol_num** out) {
+                int assembly, chol_num** out, bool factor_now) {
   const Sym& S = sym->S;
   chol_num* f = new (std::nothrow) chol_num();
   if (!f) return CHOL_E_OOM;
@@ -424,7 +424,43 @@ int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int p
     return CHOL_E_CUDA;
   }
   *out = f;
-  return chol_refactorize(c, f, vals, where);
+  if (factor_now) return chol_refactorize(c, f, vals, where);
+  if (S.nnz_a > 0 && vals)
+    CK(cudaMemcpyAsync(f->d_vals, vals, (size_t)S.nnz_a * 8,
+                       where == CHOL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       c->stream));
+  return CHOL_OK;
+}
+
+size_t sym_upload_bytes(const chol_sym* sym) {
+  const Sym& S = sym->S;
+  size_t b = S.rows.size() * 4 + S.col2sn.size() * 4 + S.amap.size() * 8 + S.perm.size() * 4 +
+             S.iperm.size() * 4 + S.a_colptr.size() * 8 + S.a_rowind.size() * 4 +
+             S.csr_ptr.size() * 8 + S.csr_col.size() * 4 + S.csr_src.size() * 4 +
+             S.asm_src.size() * 4 + S.fg_ptr.size() * 8 + S.fg_row.size() * 4 +
+             S.fg_ent.size() * 4;
+  for (int k = 0; k < chol::kNumTaskKinds; k++) b += S.tasks[k].size() * 4;
+  return b + 64 * 16;
+}
+
+size_t solve_ws_bytes(const chol_sym* sym, int64_t k, int assembly) {
+  const Sym& S = sym->S;
+  int64_t mb = 0;
+  for (int32_t l = 0; l < S.nlev; l++)
+    mb = std::max(mb, S.task_off[chol::kTaskBwd][l + 1] - S.task_off[chol::kTaskBwd][l]);
+  size_t b = 3 * (size_t)S.n * k * 8 + (size_t)mb * S.width_cap * k * 8;
+  if (assembly == CHOL_ASSEMBLY_OWNER) b += (size_t)S.max_fwd_per_level * chol::kSolveRows * k * 8;
+  return b + 3 * (size_t)S.n * k * 8 + kNormSlots * 8;  // + refinement workspace
+}
+
+size_t factor_bytes(const chol_sym* sym, int precision, int assembly) {
+  const Sym& S = sym->S;
+  const size_t esz = precision == CHOL_MIXED ? 4 : 8;
+  size_t b = (size_t)S.l_storage * esz + (size_t)S.ns * sizeof(SnDev) + sizeof(MatDev) + 32 +
+             (size_t)S.nnz_a * 8;
+  if (precision == CHOL_MIXED) b += (size_t)S.n * 8;
+  if (assembly == CHOL_ASSEMBLY_OWNER) b += (size_t)S.stage_elems * 8;
+  return b;
 }
 
 int ensure_refine_ws(chol_num* f, int64_t k) {
@@ -749,7 +785,7 @@ int chol_factorize(chol_ctx* c, const chol_sym* sym_c, const double* vals, int w
   int rc = ensure_uploaded(c, sym);
   if (rc) return rc;
   if ((rc = ensure_attrs(c))) return rc;
-  return make_factor(c, sym, vals, where, precision, c->opts.assembly, out);
+  return make_factor(c, sym, vals, where, precision, c->opts.assembly, out, true);
 }
 
 int chol_refactorize(chol_ctx* c, chol_num* f, const double* vals, int where) {
@@ -902,7 +938,7 @@ int chol_refine(chol_ctx* c, chol_num* f, int64_t nrhs, const double* B, int64_t
       // the mixed factor cannot deliver tol: factor A in FP64 once and refine with it
       if (!f->fb) {
         if ((rc = make_factor(c, const_cast<chol_sym*>(f->sym), f->d_vals, CHOL_DEVICE,
-                              CHOL_FP64, f->assembly, &f->fb)))
+                              CHOL_FP64, f->assembly, &f->fb, true)))
           return rc;
         if ((rc = chol_factor_status(c, f->fb, nullptr))) return rc;
       }

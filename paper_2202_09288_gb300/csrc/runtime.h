@@ -149,8 +149,15 @@ int ensure_uploaded(chol_ctx* c, chol_sym* s);
 int ensure_attrs(chol_ctx* c);
 int ensure_solve_ws(chol_num* f, int64_t nrhs);
 int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx);
+// Allocates a factor of sym and copies vals into it; with factor_now it also enqueues the
+// factorization (otherwise a batch will factor it).
 int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int precision,
-                int assembly, chol_num** out);
+                int assembly, chol_num** out, bool factor_now);
+// Bytes of device memory a factor of sym holds (panels, values, descriptors, staging).
+size_t factor_bytes(const chol_sym* sym, int precision, int assembly);
+// Bytes of the device copy of sym, and of the solve + refinement workspace for k columns.
+size_t sym_upload_bytes(const chol_sym* sym);
+size_t solve_ws_bytes(const chol_sym* sym, int64_t k, int assembly);
 
 }  // namespace rt
 }  // namespace chol

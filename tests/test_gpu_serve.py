@@ -1,0 +1,110 @@
+"""GPU tests of the request server (continuous batching under an HBM budget): every
+request is answered to its residual target, results do not depend on what else was in
+flight (owner-ordered assembly: bitwise), admission respects the budget, and a request
+larger than the budget fails cleanly while the server keeps serving."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2202_09288_gb300 as P
+from paper_2202_09288_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+def shifted(A, sigma):
+    """A + sigma diag(A): a new numeric matrix on the same pattern."""
+    vals = A.vals.copy()
+    vals[A.colptr[:-1]] *= 1.0 + sigma
+    return inputs.SpdMatrix(A.n, A.colptr, A.rowind, vals, A.grid, A.dofs)
+
+
+def request_mix(count, seed):
+    u = (inputs.uniform(seed, 11, 4 * count) + 1.0) / 2.0
+    out = []
+    for r in range(count):
+        if u[4 * r] < 0.5:
+            A, perm = inputs.workload(f"lap2d_{int(10 + 30 * u[4 * r + 1])}")
+        else:
+            A, perm = inputs.workload(f"diff3d7_{int(5 + 9 * u[4 * r + 1])}")
+        A = shifted(A, u[4 * r + 2])
+        nrhs = 1 + int(8 * u[4 * r + 3]) % 8
+        B = A.to_scipy_full() @ inputs.rhs_block(seed + r, A.n, nrhs)
+        out.append((A, perm, np.asfortranarray(B)))
+    return out
+
+
+def test_served_requests_meet_tolerance(torch):
+    reqs = request_mix(40, 1)
+    srv = P.Server(slots=2, max_batch=8)
+    tickets = []
+    for i, (A, perm, B) in enumerate(reqs):
+        prec = P.CHOL_MIXED if i % 2 else P.CHOL_FP64
+        tickets.append(srv.submit(A, perm, B, precision=prec, tol=1e-12))
+    for t, (A, perm, B) in zip(tickets, reqs):
+        X, res = srv.wait(t)
+        assert res["status"] == P.CHOL_OK, res
+        assert res["residual"] <= 1e-12
+        assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, B, X) <= 1e-12
+        assert res["t_submit"] <= res["t_start"] <= res["t_done"]
+        assert 1 <= res["batch_size"] <= 8
+    srv.close()
+
+
+def test_poll_reports_once(torch):
+    (A, perm, B), = request_mix(1, 5)
+    srv = P.Server(slots=1, max_batch=1)
+    t = srv.submit(A, perm, B)
+    got = None
+    while got is None:
+        got = srv.poll(t)
+    X, res = got
+    assert res["status"] == P.CHOL_OK
+    with pytest.raises(P.CholError):
+        srv.poll(t)  # a ticket is reported once
+    srv.close()
+
+
+def test_alone_and_in_the_mix_are_bitwise_equal(torch):
+    reqs = request_mix(12, 2)
+    alone = P.Server(slots=1, max_batch=1, assembly=P.CHOL_ASSEMBLY_OWNER)
+    ref = [alone.wait(alone.submit(A, perm, B, precision=P.CHOL_MIXED)) for A, perm, B in reqs]
+    alone.close()
+    mix = P.Server(slots=2, max_batch=6, assembly=P.CHOL_ASSEMBLY_OWNER)
+    tickets = [mix.submit(A, perm, B, precision=P.CHOL_MIXED) for A, perm, B in reqs]
+    results = [mix.wait(t) for t in tickets]
+    mix.close()
+    assert max(res["batch_size"] for _, res in results) > 1  # groups really were shared
+    for (X_mix, res_mix), (X_alone, res_alone) in zip(results, ref):
+        assert res_alone["batch_size"] == 1
+        assert np.array_equal(X_mix, X_alone)
+        assert res_mix["iterations"] == res_alone["iterations"]
+
+
+def test_admission_under_a_small_budget(torch):
+    reqs = request_mix(10, 3)
+    # room for about one of the larger requests at a time
+    srv = P.Server(slots=2, max_batch=8, hbm_budget=96 << 20)
+    tickets = [srv.submit(A, perm, B) for A, perm, B in reqs]
+    big = inputs.laplacian_2d_5pt(700)  # needs far more than the budget
+    bp = inputs.nested_dissection(big.grid)
+    t_big = srv.submit(big, bp, np.ones((big.n, 1)))
+    for t, (A, perm, B) in zip(tickets, reqs):
+        X, res = srv.wait(t)
+        assert res["status"] == P.CHOL_OK
+        assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, B, X) <= 1e-12
+    X, res = srv.wait(t_big)
+    assert res["status"] == P.CHOL_E_OOM
+    # the server still serves after the refusal
+    A, perm, B = reqs[0]
+    X, res = srv.wait(srv.submit(A, perm, B))
+    assert res["status"] == P.CHOL_OK
+    srv.close()
