@@ -222,14 +222,19 @@ void slot_loop(chol_server* srv, Slot* s) {
       status[i] = rc;
       if (!rc) live.push_back(nums[i]);
     }
-    if (!live.empty()) {
+    // one batch per precision (a batch runs one kernel family)
+    for (int prec : {CHOL_FP64, CHOL_MIXED}) {
+      std::vector<chol_num*> part;
+      for (chol_num* f : live)
+        if (f->precision == prec) part.push_back(f);
+      if (part.empty()) continue;
       chol_batch* b = nullptr;
-      int rc = chol_batch_create(s->ctx, (int)live.size(), live.data(), &b);
+      int rc = chol_batch_create(s->ctx, (int)part.size(), part.data(), &b);
       if (!rc) rc = chol_batch_factorize(s->ctx, b, nullptr, CHOL_DEVICE, 0);
       if (b) chol_batch_free(b);
       if (rc)
         for (size_t i = 0; i < group.size(); i++)
-          if (nums[i]) status[i] = rc;
+          if (nums[i] && nums[i]->precision == prec) status[i] = rc;
     }
     // refine every request to its target and complete it
     for (size_t i = 0; i < group.size(); i++) {
