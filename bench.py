@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -165,6 +166,195 @@ def run_reference(args, rank: int, world: int):
     return 0
 
 
+def _events(torch, n):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def run_batched(args):
+    """Plain per-level launches vs autotuned tiles vs a CUDA-graph batch (one matrix), and a
+    batch of several matrices vs factoring them one after another."""
+    import torch
+
+    import paper_2202_09288_gb300 as P
+    from paper_2202_09288_gb300 import inputs
+
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = P.Context(width_cap=args.width, stream=stream.cuda_stream)
+    prec = P.CHOL_MIXED if args.precision == "mixed" else P.CHOL_FP64
+    A, perm = inputs.workload(args.workload)
+    sym = P.Symbolic(ctx, A, perm)
+    F = sym.info["flops"]
+    vals_d = torch.from_numpy(A.vals).cuda()
+    torch.cuda.synchronize()
+    num = P.Factor(ctx, sym, vals_d, precision=prec)
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        e0, e1 = _events(torch, 2)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    plain_ms = timed(lambda: num.refactor(vals_d), args.steps)
+    default_policy = P.chol_sym_get_tile_policy(sym.handle)
+    policy, _ = num.autotune(reps=1)
+    tuned_ms = timed(lambda: num.refactor(vals_d), args.steps)
+    batch = P.Batch(ctx, [num])
+    graph_ms = timed(lambda: batch.factorize(use_graph=True), args.steps)
+    assert num.status()[0] == P.CHOL_OK
+    batch.close()
+    # several matrices of one family: one after another vs one batch (graph replay)
+    mname, mcount = args.multi.split(":")
+    mcount = int(mcount)
+    M, mperm = inputs.workload(mname)
+    msym = P.Symbolic(ctx, M, mperm)
+    mvals = [torch.from_numpy(M.vals * (1.0 + 0.1 * i)).cuda() for i in range(mcount)]
+    torch.cuda.synchronize()
+    mnums = [P.Factor(ctx, msym, v, precision=prec) for v in mvals]
+    seq_ms = timed(lambda: [f.refactor(v) for f, v in zip(mnums, mvals)], args.steps)
+    mbatch = P.Batch(ctx, mnums)
+    mb_ms = timed(lambda: mbatch.factorize(use_graph=True), args.steps)
+    ok = all(f.status()[0] == P.CHOL_OK for f in mnums)
+    mbatch.close()
+    MF = msym.info["flops"] * mcount
+    line = {
+        "metric": METRIC, "mode": "batched", "value": F / (graph_ms * 1e-3) / 1e9,
+        "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": graph_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == P.CHOL_MIXED else "f64",
+        "data": "synthetic",
+        "config": dict(workload_config(args), n=A.n, flops_per_step=F,
+                       nlevels=sym.info["nlevels"]),
+        "plain_per_level_ms": plain_ms, "autotuned_ms": tuned_ms, "graph_batch_ms": graph_ms,
+        "default_tile_policy": default_policy, "autotuned_tile_policy": policy,
+        "multi": {"matrix": mname, "count": mcount, "sequential_ms": seq_ms,
+                  "batched_graph_ms": mb_ms, "speedup": seq_ms / mb_ms,
+                  "batched_gflops": MF / (mb_ms * 1e-3) / 1e9, "all_ok": ok},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def serve_requests(count, seed):
+    """The serving workload: 2D 5-point or 3D 7-point SPD systems (probability 1/2 each)
+    with n log-uniform in [1e3, 2e5] (k = round(sqrt n) or round(cbrt n)), a diagonal shift
+    sigma ~ U[0, 1) times the diagonal (new values on a shared pattern), 1-8 right-hand sides
+    with b = A x_true, x_true ~ U[-1, 1) (one block of 8 per pattern)."""
+    from paper_2202_09288_gb300 import inputs
+
+    u = (inputs.uniform(seed, 12, 4 * count) + 1.0) / 2.0
+    patterns = {}
+    out = []
+    for r in range(count):
+        n = math.exp(math.log(1e3) + u[4 * r + 1] * (math.log(2e5) - math.log(1e3)))
+        if u[4 * r] < 0.5:
+            key = ("lap2d", max(2, round(n ** 0.5)))
+        else:
+            key = ("diff3d7", max(2, round(n ** (1.0 / 3.0))))
+        if key not in patterns:
+            A, perm = inputs.workload(f"{key[0]}_{key[1]}")
+            patterns[key] = (A, perm, A.to_scipy_full(), A.vals[A.colptr[:-1]],
+                             inputs.rhs_block(seed * 1000 + len(patterns), A.n, 8))
+        A, perm, Afull, diag, Xp = patterns[key]
+        sigma = u[4 * r + 2]
+        vals = A.vals.copy()
+        vals[A.colptr[:-1]] *= 1.0 + sigma
+        Ar = inputs.SpdMatrix(A.n, A.colptr, A.rowind, vals, A.grid, A.dofs)
+        nrhs = 1 + min(7, int(8 * u[4 * r + 3]))
+        X = Xp[:, :nrhs]
+        B = np.asfortranarray(Afull @ X + (sigma * diag)[:, None] * X)  # (A + sigma D) X
+        out.append((Ar, perm, B))
+    return out
+
+
+def run_serve(args):
+    """Request stream through the server: closed loop (all requests queued at once) for
+    throughput, then Poisson arrivals at 0.5 and 0.9 of that throughput for latency."""
+    import threading
+
+    import torch  # noqa: F401  (CUDA context of this process)
+
+    import paper_2202_09288_gb300 as P
+    from paper_2202_09288_gb300 import inputs
+
+    prec = P.CHOL_MIXED if args.precision == "mixed" else P.CHOL_FP64
+    reqs = serve_requests(args.requests, 4)
+    srv = P.Server(slots=2, max_batch=16, hbm_budget=64 << 30, width_cap=args.width)
+    # warm-up: module load, analysis caches of the first patterns
+    for t in [srv.submit(A, p, B, precision=prec, tol=args.tol) for A, p, B in reqs[:20]]:
+        srv.wait(t)
+
+    def run(arrivals):
+        """arrivals: None (all at once) or submit times relative to the start."""
+        tickets = [None] * len(reqs)
+        start = srv.clock()
+
+        def submitter():
+            for i, (A, p, B) in enumerate(reqs):
+                if arrivals is not None:
+                    dt = start + arrivals[i] - srv.clock()
+                    if dt > 0:
+                        time.sleep(dt)
+                tickets[i] = srv.submit(A, p, B, precision=prec, tol=args.tol)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join() if arrivals is None else None
+        res = []
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                time.sleep(1e-4)
+            res.append(srv.wait(tickets[i])[1])
+        th.join()
+        return res
+
+    closed = run(None)
+    t_first = min(r["t_submit"] for r in closed)
+    t_last = max(r["t_done"] for r in closed)
+    span = t_last - t_first
+    rate = len(reqs) / span
+    solves = sum(B.shape[1] for _, _, B in reqs)
+    out = {"closed_loop": {"requests": len(reqs), "seconds": span, "requests_per_s": rate,
+                           "solves_per_s": solves / span}}
+    for load in (0.5, 0.9):
+        lam = load * rate
+        uu = (inputs.uniform(40 + int(load * 10), 13, len(reqs)) + 1.0) / 2.0
+        gaps = -np.log(np.maximum(uu, 1e-300)) / lam
+        arr = np.cumsum(gaps) - gaps[0]
+        res = run(list(arr))
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+        span_o = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        out[f"poisson_{load}"] = {
+            "arrival_rate_per_s": lam, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "mean_batch": float(np.mean([r["batch_size"] for r in res])),
+            "solves_per_s": solves / span_o,
+            "max_residual": float(max(r["residual"] for r in res)),
+            "failed": int(sum(r["status"] != 0 for r in res))}
+    srv.close()
+    allres = closed
+    line = {
+        "metric": METRIC, "mode": "serve", "value": out["closed_loop"]["solves_per_s"],
+        "unit": "solves/s", "n_gpus": 1, "steps": len(reqs), "warmup": 20,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == P.CHOL_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": "serving stream: 2D 5-pt / 3D 7-pt, n log-uniform [1e3, 2e5], "
+                               "1-8 RHS, 64 GB budget, 2 slots, groups of <= 16",
+                   "precision": args.precision, "tol": args.tol},
+        "p50_ms": out["poisson_0.9"]["p50_ms"], "p99_ms": out["poisson_0.9"]["p99_ms"],
+        "max_residual": float(max(r["residual"] for r in allres)),
+        "failed": int(sum(r["status"] != 0 for r in allres)),
+        **out,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def workload_config(args):
     return {"workload": args.workload, "n": None, "precision": args.precision,
             "nrhs": args.nrhs,
@@ -189,6 +379,13 @@ def main():
                     help="mixed: FP32 factor + FP64 iterative refinement to --tol")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--mode", default="factor", choices=["factor", "batched", "serve"],
+                    help="factor: one matrix per step (default); batched: plain per-level "
+                         "launches vs autotuned tiles vs CUDA-graph batches; serve: request "
+                         "stream through the server")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--multi", default="st27x3_24:8",
+                    help="batched mode: name:count of the multi-matrix batch")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -196,6 +393,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.mode == "batched":
+        return run_batched(args)
+    if args.mode == "serve":
+        return run_serve(args)
 
     import torch
 

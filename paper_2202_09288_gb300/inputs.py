@@ -286,10 +286,9 @@ def nested_dissection(grid: tuple, dofs: int = 1, leaf: int = 64) -> np.ndarray:
 
     def natural(lo, hi):
         xs = np.arange(lo[0], hi[0])
-        ys = np.arange(lo[1], hi[1])
-        zs = np.arange(lo[2], hi[2])
-        zz, yy, xx = np.meshgrid(zs, ys, xs, indexing="ij")
-        return (xx + kx * (yy + ky * zz)).ravel()
+        ys = np.arange(lo[1], hi[1]) * kx
+        zs = np.arange(lo[2], hi[2]) * (kx * ky)
+        return (zs[:, None, None] + ys[None, :, None] + xs[None, None, :]).ravel()
 
     def rec(lo, hi):
         ext = [hi[a] - lo[a] for a in range(3)]
