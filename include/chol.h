@@ -246,7 +246,8 @@ int chol_autotune(chol_ctx* ctx, chol_num* num, int reps, chol_tile_policy* best
  * fit the HBM budget (up to max_batch at a time), factor them together as one batch,
  * refine every request and complete it; a request that arrives while other groups are on
  * the GPU starts as soon as a slot and memory are free (continuous batching).  Symbolic
- * analyses stay resident per slot, keyed by pattern.  The budget is split: each slot may
+ * analyses run on host analyzer threads ahead of the slots, are shared by pattern, and
+ * their device copies stay resident per slot.  The budget is split: each slot may
  * keep analyses worth budget / (4 slots) resident, the groups in flight share the rest;
  * a request larger than that share alone completes with CHOL_E_OOM. */
 typedef struct chol_server chol_server;
@@ -257,7 +258,9 @@ typedef struct chol_server_opts {
   size_t hbm_budget;  /* device bytes the server may hold; 0 = no limit */
   int width_cap;      /* as chol_opts; 0 = 64 */
   int assembly;       /* as chol_opts */
-  int sym_cache;      /* analyses cached per slot; 0 = 64 */
+  int sym_cache;      /* device copies of analyses cached per slot; 0 = 64 (the shared
+                         host cache keeps 4x as many) */
+  int analyzers;      /* host threads running symbolic analyses ahead of the slots; 0 = 4 */
 } chol_server_opts;
 
 typedef struct chol_request {

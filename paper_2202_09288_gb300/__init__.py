@@ -56,7 +56,7 @@ class chol_tile_policy(C.Structure):
 class chol_server_opts(C.Structure):
     _fields_ = [("device", C.c_int), ("slots", C.c_int), ("max_batch", C.c_int),
                 ("hbm_budget", C.c_size_t), ("width_cap", C.c_int), ("assembly", C.c_int),
-                ("sym_cache", C.c_int)]
+                ("sym_cache", C.c_int), ("analyzers", C.c_int)]
 
 
 class chol_request(C.Structure):

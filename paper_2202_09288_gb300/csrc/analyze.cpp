@@ -320,6 +320,25 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
       }
     }
     S->stage_elems = std::max(S->stage_elems, stage);
+    for (int k = 0; k < kNumTaskKinds; k++)
+      S->task_off[k][l + 1] = (int64_t)S->tasks[k].size() / 4;
+    S->max_fwd_per_level = std::max(S->max_fwd_per_level, S->task_off[kTaskFwd][l + 1] -
+                                                              S->task_off[kTaskFwd][l]);
+  }
+  build_schur_tasks(S, TilePolicy());
+  return CHOL_OK;
+}
+
+void build_owner_lists(Sym* S) {
+  if (S->owner_lists) return;
+  S->tasks[kTaskAsm].clear();
+  S->task_off[kTaskAsm].assign(S->nlev + 1, 0);
+  S->asm_src.clear();
+  S->fg_lvl.assign(1, 0);
+  S->fg_ptr.assign(1, 0);
+  S->fg_row.clear();
+  S->fg_ent.clear();
+  for (int32_t l = 0; l < S->nlev; l++) {
     // owner assembly groups: for every target supernode t hit by this level, per block
     // of 32 target columns, the sources s of this level in ascending order
     {
@@ -359,12 +378,10 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
         g = h;
       }
     }
-    for (int k = 0; k < kNumTaskKinds; k++)
-      S->task_off[k][l + 1] = (int64_t)S->tasks[k].size() / 4;
+    S->task_off[kTaskAsm][l + 1] = (int64_t)S->tasks[kTaskAsm].size() / 4;
     // owner-ordered forward-solve gather lists of this level
     {
       const int64_t f0 = S->task_off[kTaskFwd][l], f1 = S->task_off[kTaskFwd][l + 1];
-      S->max_fwd_per_level = std::max(S->max_fwd_per_level, f1 - f0);
       std::vector<std::pair<int32_t, int32_t>> ent;  // (target row, slot)
       for (int64_t q = f0; q < f1; q++) {
         const int32_t s = S->tasks[kTaskFwd][4 * q], r0 = S->tasks[kTaskFwd][4 * q + 1];
@@ -389,8 +406,7 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
       S->fg_lvl.push_back((int64_t)S->fg_row.size());
     }
   }
-  build_schur_tasks(S, TilePolicy());
-  return CHOL_OK;
+  S->owner_lists = true;
 }
 
 void build_schur_tasks(Sym* S, const TilePolicy& policy) {

@@ -169,6 +169,51 @@ int ensure_uploaded(chol_ctx* c, chol_sym* s) {
   return CHOL_OK;
 }
 
+chol_sym* clone_sym(const chol_sym* src) {
+  chol_sym* s = new (std::nothrow) chol_sym();
+  if (!s) return nullptr;
+  try {
+    s->S = src->S;
+  } catch (...) {
+    delete s;
+    return nullptr;
+  }
+  return s;
+}
+
+// Builds the owner-assembly lists of sym on first use by an owner-mode factor and, if sym
+// is already on the device, uploads them.
+int ensure_owner_lists(chol_ctx* c, chol_sym* s) {
+  if (s->S.owner_lists) return CHOL_OK;
+  try {
+    chol::build_owner_lists(&s->S);
+  } catch (...) {
+    return CHOL_E_OOM;
+  }
+  if (s->ctx != c) return CHOL_OK;  // uploaded with everything else later
+  DevSym& d = s->dev;
+  const Sym& S = s->S;
+  dev_free(c, d.asm_src);
+  dev_free(c, d.fg_ptr);
+  dev_free(c, d.fg_row);
+  dev_free(c, d.fg_ent);
+  dev_free(c, d.tasks[chol::kTaskAsm]);
+  d.asm_src = nullptr;
+  d.fg_ptr = nullptr;
+  d.fg_row = d.fg_ent = nullptr;
+  d.tasks[chol::kTaskAsm] = nullptr;
+  size_t acc = 0;
+  int rc;
+  if ((rc = upload(c, reinterpret_cast<int32_t**>(&d.asm_src), S.asm_src, &acc)) ||
+      (rc = upload(c, &d.fg_ptr, S.fg_ptr, &acc)) || (rc = upload(c, &d.fg_row, S.fg_row, &acc)) ||
+      (rc = upload(c, &d.fg_ent, S.fg_ent, &acc)) ||
+      (rc = upload(c, reinterpret_cast<int32_t**>(&d.tasks[chol::kTaskAsm]), S.tasks[chol::kTaskAsm],
+                   &acc)))
+    return rc;
+  d.bytes += acc;
+  return CHOL_OK;
+}
+
 int ensure_attrs(chol_ctx* c) {
   if (c->attrs_set) return CHOL_OK;
   int rc = chol::set_factor_kernel_attrs(chol::kMaxWidth);
@@ -388,6 +433,10 @@ void free_num_buffers(chol_num* f) {
 int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int precision,
                 int assembly, chol_num** out, bool factor_now) {
   const Sym& S = sym->S;
+  if (assembly == CHOL_ASSEMBLY_OWNER) {
+    int rc0 = ensure_owner_lists(c, sym);
+    if (rc0) return rc0;
+  }
   chol_num* f = new (std::nothrow) chol_num();
   if (!f) return CHOL_E_OOM;
   f->ctx = c;

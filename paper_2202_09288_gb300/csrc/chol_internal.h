@@ -103,6 +103,7 @@ struct Sym {
   std::vector<int64_t> fg_lvl, fg_ptr;
   std::vector<int32_t> fg_row, fg_ent;
   int64_t max_fwd_per_level = 0;
+  bool owner_lists = false;  // asm groups and gather lists built (build_owner_lists)
   // algorithmic flops of each task kind per level (POTRF n(n+1)(2n+1)/6, TRSM u n^2,
   // Schur u(u+1)n per supernode; they add up to sum_j c_j^2) and panel bytes per level
   std::vector<double> lvl_flops[kNumTaskKinds];
@@ -114,6 +115,9 @@ struct Sym {
 // Host analysis (analyze.cpp).  Returns CHOL_OK or CHOL_E_INVALID.
 int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32_t* perm,
             int width_cap, Sym* out);
+// Builds the owner-assembly groups (kTaskAsm, asm_src) and the owner-ordered forward-solve
+// gather lists; only factors with owner-ordered assembly need them.
+void build_owner_lists(Sym* S);
 // (Re)builds the Schur tile task lists of every level under a tile policy.
 void build_schur_tasks(Sym* S, const TilePolicy& policy);
 

@@ -155,6 +155,8 @@ int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int p
                 int assembly, chol_num** out, bool factor_now);
 // Bytes of device memory a factor of sym holds (panels, values, descriptors, staging).
 size_t factor_bytes(const chol_sym* sym, int precision, int assembly);
+// A copy of the host analysis of src, not bound to any device (nullptr when out of memory).
+chol_sym* clone_sym(const chol_sym* src);
 // Bytes of the device copy of sym, and of the solve + refinement workspace for k columns.
 size_t sym_upload_bytes(const chol_sym* sym);
 size_t solve_ws_bytes(const chol_sym* sym, int64_t k, int assembly);

@@ -6,8 +6,9 @@
 // together as one batch (level l of every member in one launch per kernel kind), refine
 // every request's solution to its residual target, and complete it.  Requests that arrive
 // while a group is on the GPU are admitted by the next free slot as soon as memory allows,
-// so groups overlap on the device.  Symbolic analyses stay resident in a per-slot cache
-// keyed by the pattern, so repeated patterns skip analysis and upload.
+// so groups overlap on the device.  Host analyses run on analyzer threads ahead of the
+// slots and are shared through a cache keyed by the pattern; each slot keeps the device
+// copies of the analyses it used, so repeated patterns skip both analysis and upload.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -16,6 +17,7 @@
 #include <cstring>
 #include <deque>
 #include <list>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -29,8 +31,20 @@ using namespace chol::rt;
 
 namespace {
 
+// A host analysis shared by every slot (made once by an analyzer thread).
+struct Proto {
+  uint64_t key = 0;
+  bool ready = false;
+  int rc = CHOL_OK;
+  chol_sym* sym = nullptr;  // host only: slots clone it before uploading
+  ~Proto() {
+    if (sym) chol_free_sym(sym);
+  }
+};
+
 struct Request {
   uint64_t ticket = 0;
+  std::shared_ptr<Proto> proto;
   uint64_t key = 0;  // pattern hash
   int64_t n = 0, nrhs = 0;
   std::vector<int64_t> colptr;
@@ -75,7 +89,12 @@ struct chol_server {
   std::chrono::steady_clock::time_point t0;
   std::mutex mu;  // queue, results, budget
   std::condition_variable cv_work, cv_done, cv_mem;
-  std::deque<Request*> queue;
+  std::deque<Request*> incoming;  // submitted, not yet analyzed
+  std::deque<Request*> queue;     // analyzed, waiting for a slot
+  std::condition_variable cv_analyze, cv_proto;
+  std::unordered_map<uint64_t, std::shared_ptr<Proto>> protos;
+  std::deque<uint64_t> proto_order;  // insertion order, for eviction
+  std::vector<std::thread> analyzers;
   std::unordered_map<uint64_t, chol_result> done;
   std::unordered_map<uint64_t, bool> pending;
   uint64_t next_ticket = 1;
@@ -93,19 +112,22 @@ struct chol_server {
 
 namespace {
 
-// Cached analysis of r's pattern on slot s (analysis on this thread if missing).
+// Slot s's copy of the analysis of r's pattern (cloned from the shared one if missing).
 SymEntry* get_sym(chol_server* srv, Slot* s, const Request& r, int* rc) {
   auto it = s->index.find(r.key);
   if (it != s->index.end()) {
     s->lru.splice(s->lru.begin(), s->lru, it->second);
     return &*s->lru.begin();
   }
-  chol_opts o;
-  chol_default_opts(&o);
-  o.width_cap = srv->opts.width_cap;
-  chol_sym* sym = nullptr;
-  *rc = chol_analyze(&o, r.n, r.colptr.data(), r.rowind.data(), r.perm.data(), &sym);
-  if (*rc) return nullptr;
+  if (r.proto->rc) {
+    *rc = r.proto->rc;
+    return nullptr;
+  }
+  chol_sym* sym = clone_sym(r.proto->sym);
+  if (!sym) {
+    *rc = CHOL_E_OOM;
+    return nullptr;
+  }
   s->lru.push_front({r.key, sym, sym_upload_bytes(sym), false, 0});
   s->index[r.key] = s->lru.begin();
   return &*s->lru.begin();
@@ -143,6 +165,69 @@ void finish(chol_server* srv, Request* r, const chol_result& res) {
   }
   srv->cv_done.notify_all();
   delete r;
+}
+
+// Analyzer thread: takes submitted requests, finds or makes the shared analysis of their
+// pattern, and passes them on to the slots.
+void analyzer_loop(chol_server* srv) {
+  for (;;) {
+    Request* r = nullptr;
+    std::shared_ptr<Proto> pr;
+    bool mine = false;
+    {
+      std::unique_lock<std::mutex> lock(srv->mu);
+      srv->cv_analyze.wait(lock, [&] { return srv->stop || !srv->incoming.empty(); });
+      if (srv->stop) return;
+      r = srv->incoming.front();
+      srv->incoming.pop_front();
+      auto it = srv->protos.find(r->key);
+      if (it == srv->protos.end()) {
+        pr = std::make_shared<Proto>();
+        pr->key = r->key;
+        srv->protos[r->key] = pr;
+        srv->proto_order.push_back(r->key);
+        mine = true;
+        // bound the cache: drop the oldest finished analyses (requests keep theirs alive)
+        while (srv->proto_order.size() > 4 * (size_t)srv->opts.sym_cache) {
+          const uint64_t k = srv->proto_order.front();
+          auto jt = srv->protos.find(k);
+          if (jt != srv->protos.end() && !jt->second->ready) break;
+          srv->proto_order.pop_front();
+          if (jt != srv->protos.end()) srv->protos.erase(jt);
+        }
+      } else {
+        pr = it->second;
+      }
+    }
+    if (mine) {
+      chol_opts o;
+      chol_default_opts(&o);
+      o.width_cap = srv->opts.width_cap;
+      chol_sym* sym = nullptr;
+      const int rc = chol_analyze(&o, r->n, r->colptr.data(), r->rowind.data(), r->perm.data(),
+                                  &sym);
+      {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        pr->sym = sym;
+        pr->rc = rc;
+        pr->ready = true;
+      }
+      srv->cv_proto.notify_all();
+    } else {
+      std::unique_lock<std::mutex> lock(srv->mu);
+      srv->cv_proto.wait(lock, [&] { return srv->stop || pr->ready; });
+      if (srv->stop) {
+        delete r;
+        return;
+      }
+    }
+    r->proto = pr;
+    {
+      std::lock_guard<std::mutex> lock(srv->mu);
+      srv->queue.push_back(r);
+    }
+    srv->cv_work.notify_one();
+  }
 }
 
 void slot_loop(chol_server* srv, Slot* s) {
@@ -281,6 +366,7 @@ void chol_default_server_opts(chol_server_opts* o) {
   o->width_cap = 64;
   o->assembly = CHOL_ASSEMBLY_ATOMIC;
   o->sym_cache = 64;
+  o->analyzers = 4;
 }
 
 int chol_server_create(const chol_server_opts* opts, chol_server** out) {
@@ -314,6 +400,8 @@ int chol_server_create(const chol_server_opts* opts, chol_server** out) {
     srv->slots.push_back(s);
   }
   for (Slot* s : srv->slots) s->th = std::thread(slot_loop, srv, s);
+  const int na = srv->opts.analyzers > 0 ? srv->opts.analyzers : 4;
+  for (int i = 0; i < na; i++) srv->analyzers.emplace_back(analyzer_loop, srv);
   *out = srv;
   return CHOL_OK;
 }
@@ -355,10 +443,10 @@ int chol_submit(chol_server* srv, const chol_request* q, uint64_t* ticket) {
     r->ticket = srv->next_ticket++;
     r->t_submit = srv->now();
     srv->pending[r->ticket] = true;
-    srv->queue.push_back(r);
+    srv->incoming.push_back(r);
     *ticket = r->ticket;
   }
-  srv->cv_work.notify_one();
+  srv->cv_analyze.notify_one();
   return CHOL_OK;
 }
 
@@ -393,6 +481,10 @@ void chol_server_destroy(chol_server* srv) {
   }
   srv->cv_work.notify_all();
   srv->cv_mem.notify_all();
+  srv->cv_analyze.notify_all();
+  srv->cv_proto.notify_all();
+  for (std::thread& t : srv->analyzers)
+    if (t.joinable()) t.join();
   for (Slot* s : srv->slots)
     if (s->th.joinable()) s->th.join();
   for (Slot* s : srv->slots) {
@@ -401,6 +493,8 @@ void chol_server_destroy(chol_server* srv) {
     delete s;
   }
   for (Request* r : srv->queue) delete r;
+  for (Request* r : srv->incoming) delete r;
+  srv->protos.clear();
   delete srv;
 }
 
