@@ -6,8 +6,10 @@
 // solve from the root down (a supernode needs the solution on its off-diagonal rows, which
 // belong to ancestors).
 //
-// Vectors are n x nrhs column-major in the permuted numbering, ld = n, always FP64; the
-// panels are FP64 or FP32 (mixed-precision factor), read and widened to FP64.
+// Vectors are n x nrhs column-major in the permuted numbering, ld = n, stored in FP64.  The
+// arithmetic runs in the precision of the panels: FP64 for an FP64 factor; FP32 for the
+// FP32 factor of the mixed path, whose solves only produce refinement corrections (the
+// FP64 residual of the refinement loop restores FP64 accuracy).
 //   forward  task {s, r0}: y_s <- L11^{-1} y_s (redundantly in every task of s; the task
 //            with r0 = 0 stores it in w), then y[rows[n+i]] -= L21[i, :] y_s for its rows,
 //            by atomics, or (owner order) staged and summed per row in a fixed order.
@@ -56,32 +58,31 @@ constexpr int kRhsChunk = 8;
 // Warp-level triangular solve of the n x n lower L11 (smem, column-major ld n) against
 // xs (smem, n x nrhs, ld n).  Forward: xs <- L11^{-1} xs.  Backward: xs <- L11^{-T} xs.
 // Lane l owns rows l, l+32, l+64, l+96 (n <= 128).
-template <bool FORWARD>
-__device__ void warp_trisolve(const double* L11, const double* rdiag, double* xs, int n,
-                              int nrhs) {
+template <bool FORWARD, typename CT>
+__device__ void warp_trisolve(const CT* L11, const CT* rdiag, CT* xs, int n, int nrhs) {
   const int lane = threadIdx.x & 31;
   for (int c = 0; c < nrhs; c++) {
-    double v[4];
+    CT v[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const int r = lane + 32 * q;
-      v[q] = r < n ? xs[c * n + r] : 0.0;
+      v[q] = r < n ? xs[c * n + r] : CT(0);
     }
     for (int jj = 0; jj < n; jj++) {
       const int j = FORWARD ? jj : n - 1 - jj;
       const int qj = j >> 5, lj = j & 31;
-      double own = v[0];
+      CT own = v[0];
       if (qj == 1) own = v[1];
       if (qj == 2) own = v[2];
       if (qj == 3) own = v[3];
-      const double xj = __shfl_sync(0xffffffffu, own, lj) * rdiag[j];
+      const CT xj = __shfl_sync(0xffffffffu, own, lj) * rdiag[j];
 #pragma unroll
       for (int q = 0; q < 4; q++) {
         const int r = lane + 32 * q;
         if (r == j) v[q] = xj;
         else if (FORWARD ? (r > j && r < n) : (r < j)) {
           // forward: row r of column j of L11; backward: (L^T)_{r j} = L_{j r}
-          const double l = FORWARD ? L11[j * n + r] : L11[r * n + j];
+          const CT l = FORWARD ? L11[j * n + r] : L11[r * n + j];
           v[q] -= l * xj;
         }
       }
@@ -95,15 +96,15 @@ __device__ void warp_trisolve(const double* L11, const double* rdiag, double* xs
 }
 
 template <typename P>
-__device__ void load_l11(const SnDev& d, double* L11, double* rdiag) {
+__device__ void load_l11(const SnDev& d, P* L11, P* rdiag) {
   const P* L = reinterpret_cast<const P*>(d.L);
   const int n = d.n;
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int c = idx / n, r = idx - c * n;
-    L11[idx] = r >= c ? (double)L[(int64_t)c * d.m + r] : 0.0;
+    L11[idx] = r >= c ? L[(int64_t)c * d.m + r] : P(0);
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) rdiag[j] = 1.0 / L11[j * n + j];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rdiag[j] = P(1) / L11[j * n + j];
   __syncthreads();
 }
 
@@ -114,16 +115,17 @@ __global__ void __launch_bounds__(kSolveThreads)
     k_fwd(const int4* __restrict__ tasks, int ntasks, const SnDev* __restrict__ sns, int64_t ldv, int nrhs,
           double* __restrict__ y, double* __restrict__ w, double* __restrict__ fstage) {
   extern __shared__ __align__(16) double sm[];
+  P* smp = reinterpret_cast<P*>(sm);
   for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
-    double* L11 = sm;
-    double* rdiag = L11 + n * n;
-    double* xs = rdiag + n;
+    P* L11 = smp;
+    P* rdiag = L11 + n * n;
+    P* xs = rdiag + n;
     for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
       const int c = idx / n, j = idx - c * n;
-      xs[idx] = y[c * ldv + d.col0 + j];
+      xs[idx] = (P)y[c * ldv + d.col0 + j];
     }
     load_l11<P>(d, L11, rdiag);
     if (threadIdx.x < 32) warp_trisolve<true>(L11, rdiag, xs, n, nrhs);
@@ -138,11 +140,11 @@ __global__ void __launch_bounds__(kSolveThreads)
       const P* L = reinterpret_cast<const P*>(d.L) + n + i;
       const int64_t grow = d.rows[n + i];
       for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
-        double acc[kRhsChunk];
+        P acc[kRhsChunk];
   #pragma unroll
-        for (int c = 0; c < kRhsChunk; c++) acc[c] = 0.0;
+        for (int c = 0; c < kRhsChunk; c++) acc[c] = P(0);
         for (int j = 0; j < n; j++) {
-          const double l = (double)L[(int64_t)j * m];
+          const P l = L[(int64_t)j * m];
   #pragma unroll
           for (int c = 0; c < kRhsChunk; c++)
             if (c0 + c < nrhs) acc[c] += l * xs[(c0 + c) * n + j];
@@ -151,9 +153,9 @@ __global__ void __launch_bounds__(kSolveThreads)
         for (int c = 0; c < kRhsChunk; c++) {
           if (c0 + c >= nrhs) continue;
           if (STAGE)
-            fstage[((int64_t)tq * kSolveRows + threadIdx.x) * nrhs + c0 + c] = acc[c];
+            fstage[((int64_t)tq * kSolveRows + threadIdx.x) * nrhs + c0 + c] = (double)acc[c];
           else
-            atomicAdd(&y[(int64_t)(c0 + c) * ldv + grow], -acc[c]);
+            atomicAdd(&y[(int64_t)(c0 + c) * ldv + grow], -(double)acc[c]);
         }
       }
     }
@@ -189,20 +191,20 @@ __global__ void __launch_bounds__(kSolveThreads)
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
     const int rb = min(kSolveRows, u - tk.y);
-    double* xg = sm;  // rb x nrhs
+    P* xg = reinterpret_cast<P*>(sm);  // rb x nrhs
     for (int idx = threadIdx.x; idx < rb * nrhs; idx += blockDim.x) {
       const int c = idx / rb, i = idx - c * rb;
-      xg[idx] = w[c * ldv + d.rows[n + tk.y + i]];
+      xg[idx] = (P)w[c * ldv + d.rows[n + tk.y + i]];
     }
     __syncthreads();
     double* out = part + (int64_t)tq * W * nrhs;
     const P* L = reinterpret_cast<const P*>(d.L) + n + tk.y;
     for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
       const int c = idx / n, j = idx - c * n;
-      double acc = 0.0;
+      P acc = P(0);
       const P* col = L + (int64_t)j * m;
-      for (int i = 0; i < rb; i++) acc += (double)col[i] * xg[c * rb + i];
-      out[c * W + j] = acc;
+      for (int i = 0; i < rb; i++) acc += col[i] * xg[c * rb + i];
+      out[c * W + j] = (double)acc;
     }
     __syncthreads();
   }
@@ -216,20 +218,21 @@ __global__ void __launch_bounds__(kSolveThreads)
                int64_t ldv, int nrhs, int W, const double* __restrict__ part,
                double* __restrict__ w) {
   extern __shared__ __align__(16) double sm[];
+  P* smp = reinterpret_cast<P*>(sm);
   for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n;
-    double* L11 = sm;
-    double* rdiag = L11 + n * n;
-    double* xs = rdiag + n;
+    P* L11 = smp;
+    P* rdiag = L11 + n * n;
+    P* xs = rdiag + n;
     const int u = d.m - n;
     for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
       const int c = idx / n, j = idx - c * n;
       double v = w[c * ldv + d.col0 + j];
       if (u > 0)
         for (int q = 0; q < tk.z; q++) v -= part[(tk.y - base + q) * W * nrhs + c * W + j];
-      xs[idx] = v;
+      xs[idx] = (P)v;
     }
     load_l11<P>(d, L11, rdiag);
     if (threadIdx.x < 32) warp_trisolve<false>(L11, rdiag, xs, n, nrhs);
