@@ -197,9 +197,10 @@ int chol_refine(chol_ctx* ctx, chol_num* num, int64_t nrhs, const double* B, int
  * needs about 8 * (2 n k + per-level partial sums) bytes; larger requests fail with
  * CHOL_E_SCRATCH before any work is enqueued.  The first call on a device looks up the
  * array's device address (with that device current); make that first call before any
- * stream capture.  All calls share the array and leave its contents behind (nothing in
- * it needs clearing); calls whose device work overlaps (other streams or contexts on the
- * same device) race on it and must be ordered by the caller. */
+ * stream capture.  All calls share the array and leave its contents behind; each call
+ * clears the work-queue counters at its head (all that must start at zero).  Calls whose
+ * device work overlaps (other streams or contexts on the same device) race on it and must
+ * be ordered by the caller. */
 int chol_solve_noalloc(chol_ctx* ctx, const chol_num* num, int64_t nrhs, const double* B,
                        int64_t ldb, double* X, int64_t ldx);
 size_t chol_noalloc_scratch_bytes(void);

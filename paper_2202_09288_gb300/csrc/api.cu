@@ -278,37 +278,39 @@ TaskView sym_view(const chol_sym* sym) {
 // Per level: POTRF, TRSM, the Schur tile classes and (owner mode) the ordered assembly,
 // each one launch over the level's tasks of every matrix in the view.
 int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
-                   bool f32, bool owner) {
+                   bool f32, bool owner, int* ctr) {
   cudaStream_t st = c->stream;
+  CK(cudaMemsetAsync(ctr, 0, factor_counters(v.nlev) * sizeof(int), st));
   const float tau = (float)(c->opts.pivot_tau > 0 ? c->opts.pivot_tau : 1e-5);
   const int kp = f32 ? kProfPotrfF32 : kProfPotrf, kt = f32 ? kProfTrsmF32 : kProfTrsm;
   const int ks = f32 ? kProfSchur64F32 : kProfSchur64;
   for (int32_t l = 0; l < v.nlev; l++) {
     int cnt;
+    int* q = ctr + 6 * l;  // this level's work-queue counters
     const int4* t = v.level(chol::kTaskPotrf, l, &cnt);
     if (cnt > 0) {
       prof_begin(c);
-      chol::launch_potrf(t, cnt, sns, mats, v.max_width, f32, tau, st);
+      chol::launch_potrf(t, cnt, q, sns, mats, v.max_width, f32, tau, st);
       prof_end(c, kp, v.flops[chol::kTaskPotrf][l], 0.0);
     }
     t = v.level(chol::kTaskTrsm, l, &cnt);
     if (cnt > 0) {
       prof_begin(c);
-      chol::launch_trsm(t, cnt, sns, v.max_width, f32, st);
+      chol::launch_trsm(t, cnt, q + 1, sns, v.max_width, f32, st);
       prof_end(c, kt, v.flops[chol::kTaskTrsm][l], 0.0);
     }
     for (int cls = 0; cls < chol::kNumTileClasses; cls++) {
       t = v.level(chol::kTaskSchur64 + cls, l, &cnt);
       if (cnt <= 0) continue;
       prof_begin(c);
-      chol::launch_schur(cls, t, cnt, sns, mats, owner, f32, st);
+      chol::launch_schur(cls, t, cnt, q + 2 + cls, sns, mats, owner, f32, st);
       prof_end(c, ks + cls, v.flops[chol::kTaskSchur64 + cls][l], 0.0);
     }
     if (owner) {
       t = v.level(chol::kTaskAsm, l, &cnt);
       if (cnt > 0) {
         prof_begin(c);
-        chol::launch_assemble_owner(t, cnt, v.asm_src, sns, mats, f32, st);
+        chol::launch_assemble_owner(t, cnt, q + 5, v.asm_src, sns, mats, f32, st);
         prof_end(c, kProfAsmOwner, 0.0, 0.0);
       }
     }
@@ -322,7 +324,7 @@ int enqueue_factor(chol_num* f) {
   int rc = enqueue_assembly(f);
   if (rc) return rc;
   return enqueue_levels(f->ctx, sym_view(f->sym), f->d_sn, f->d_mat,
-                        f->precision == CHOL_MIXED, f->assembly == CHOL_ASSEMBLY_OWNER);
+                        f->precision == CHOL_MIXED, f->assembly == CHOL_ASSEMBLY_OWNER, f->d_ctr);
 }
 
 // Device descriptors of f's supernodes (matrix slot `mat`) and of f itself.
@@ -388,6 +390,8 @@ int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X
   const bool f32 = f->precision == CHOL_MIXED;
   const double* scale = f32 ? f->d_scale : nullptr;
   const double vec = 8.0 * n * nrhs;
+  int* sq = f->d_ctr + factor_counters(S.nlev);  // solve work-queue counters
+  CK(cudaMemsetAsync(sq, 0, solve_counters(S.nlev) * sizeof(int), st));
   prof_begin(c);
   chol::launch_gather_perm(B, ldb, sym->dev.perm, scale, n, nrhs, f->d_y, st);
   prof_end(c, kProfPerm, 0.0, 2 * vec + 4.0 * n);
@@ -395,7 +399,8 @@ int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X
     int cnt;
     const int4* t = task_ptr(sym, chol::kTaskFwd, l, &cnt);
     prof_begin(c);
-    chol::launch_fwd(t, cnt, f->d_sn, n, nrhs, W, f->d_y, f->d_w, f->d_fstage, f32, st);
+    chol::launch_fwd(t, cnt, sq + 3 * l, f->d_sn, n, nrhs, W, f->d_y, f->d_w, f->d_fstage, f32,
+                     st);
     if (f->d_fstage)
       chol::launch_fwd_gather(sym->dev.fg_row + S.fg_lvl[l], sym->dev.fg_ptr + S.fg_lvl[l],
                               sym->dev.fg_ent, S.fg_lvl[l + 1] - S.fg_lvl[l], n, nrhs,
@@ -407,8 +412,8 @@ int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X
     const int4* tb = task_ptr(sym, chol::kTaskBwd, l, &nb);
     const int4* td = task_ptr(sym, chol::kTaskPotrf, l, &nd);
     prof_begin(c);
-    chol::launch_bwd(tb, nb, S.task_off[chol::kTaskBwd][l], td, nd, f->d_sn, n, nrhs, W,
-                     f->d_w, f->d_part, f32, st);
+    chol::launch_bwd(tb, nb, sq + 3 * l + 1, S.task_off[chol::kTaskBwd][l], td, nd, f->d_sn, n,
+                     nrhs, W, f->d_w, f->d_part, f32, st);
     prof_end(c, kProfBwd, 0.0, S.lvl_panel_bytes[l] * (f32 ? 0.5 : 1.0));
   }
   prof_begin(c);
@@ -421,7 +426,7 @@ int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X
 void free_num_buffers(chol_num* f) {
   chol_ctx* c = f->ctx;
   if (!c) return;
-  void* ptrs[] = {f->L, f->d_sn, f->d_mat, f->d_err, f->d_vals, f->d_stage, f->d_scale,
+  void* ptrs[] = {f->L, f->d_sn, f->d_mat, f->d_err, f->d_ctr, f->d_vals, f->d_stage, f->d_scale,
                   f->d_y, f->d_w, f->d_bx, f->d_part, f->d_fstage, f->d_rr, f->d_rd,
                   f->d_rb, f->d_norm};
   for (void* p : ptrs) dev_free(c, p);
@@ -451,6 +456,8 @@ int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int p
       (rc = dev_alloc(c, (void**)&f->d_sn, (size_t)S.ns * sizeof(SnDev))) ||
       (rc = dev_alloc(c, (void**)&f->d_mat, sizeof(MatDev))) ||
       (rc = dev_alloc(c, (void**)&f->d_err, 4 * sizeof(unsigned long long))) ||
+      (rc = dev_alloc(c, (void**)&f->d_ctr,
+                      (factor_counters(S.nlev) + solve_counters(S.nlev)) * sizeof(int))) ||
       (rc = dev_alloc(c, (void**)&f->d_vals, (size_t)S.nnz_a * 8)) ||
       (f32 && (rc = dev_alloc(c, (void**)&f->d_scale, (size_t)S.n * 8))) ||
       (assembly == CHOL_ASSEMBLY_OWNER &&
@@ -612,12 +619,14 @@ int refine_pass(chol_num* f, chol_num* g, int k, const double* B, int64_t ldb, d
 
 namespace chol {
 
-// Workspace, in doubles, of a device-pointer solve of k <= 32 right-hand sides: y and w
-// (n k each), the backward partials (max tasks of a level x W x k) and, for owner
-// assembly, the forward staging (max tasks of a level x kSolveRows x k).
+// Workspace, in doubles, of a device-pointer solve of k <= 32 right-hand sides: the
+// work-queue counters (3 per level), y and w (n k each), the backward partials (max tasks
+// of a level x W x k) and, for owner assembly, the forward staging (max tasks of a level x
+// kSolveRows x k).
 size_t solve_scratch_doubles(const chol_num* f, int64_t k) {
   const Sym& S = f->sym->S;
-  size_t d = 2 * (size_t)S.n * k + (size_t)f->sym->max_bwd_per_level * S.width_cap * k;
+  size_t d = (rt::solve_counters(S.nlev) * sizeof(int) + 255) / 256 * 256 / sizeof(double);
+  d += 2 * (size_t)S.n * k + (size_t)f->sym->max_bwd_per_level * S.width_cap * k;
   if (f->assembly == CHOL_ASSEMBLY_OWNER) d += (size_t)S.max_fwd_per_level * kSolveRows * k;
   return d;
 }
@@ -633,7 +642,11 @@ int enqueue_solve_ws(chol_ctx* c, const chol_num* f, int k, const double* B, int
   const int W = S.width_cap;
   const bool f32 = f->precision == CHOL_MIXED;
   const double* scale = f32 ? f->d_scale : nullptr;
-  double* y = ws;
+  int* sq = reinterpret_cast<int*>(ws);  // work-queue counters, then the vectors
+  const size_t qd = (solve_counters(S.nlev) * sizeof(int) + 255) / 256 * 256 / sizeof(double);
+  if (cudaMemsetAsync(sq, 0, solve_counters(S.nlev) * sizeof(int), st) != cudaSuccess)
+    return CHOL_E_CUDA;
+  double* y = ws + qd;
   double* w = y + (size_t)n * k;
   double* part = w + (size_t)n * k;
   double* fstage = nullptr;
@@ -644,7 +657,7 @@ int enqueue_solve_ws(chol_ctx* c, const chol_num* f, int k, const double* B, int
   for (int32_t l = 0; l < S.nlev; l++) {
     int cnt;
     const int4* t = task_ptr(sym, kTaskFwd, l, &cnt);
-    launch_fwd(t, cnt, f->d_sn, n, k, W, y, w, fstage, f32, st);
+    launch_fwd(t, cnt, sq + 3 * l, f->d_sn, n, k, W, y, w, fstage, f32, st);
     if (fstage)
       launch_fwd_gather(sym->dev.fg_row + S.fg_lvl[l], sym->dev.fg_ptr + S.fg_lvl[l],
                         sym->dev.fg_ent, S.fg_lvl[l + 1] - S.fg_lvl[l], n, k, fstage, y, st);
@@ -654,7 +667,8 @@ int enqueue_solve_ws(chol_ctx* c, const chol_num* f, int k, const double* B, int
     int nb, nd;
     const int4* tb = task_ptr(sym, kTaskBwd, l, &nb);
     const int4* td = task_ptr(sym, kTaskPotrf, l, &nd);
-    launch_bwd(tb, nb, S.task_off[kTaskBwd][l], td, nd, f->d_sn, n, k, W, w, part, f32, st);
+    launch_bwd(tb, nb, sq + 3 * l + 1, S.task_off[kTaskBwd][l], td, nd, f->d_sn, n, k, W, w,
+               part, f32, st);
     c->prof[kProfBwd].launches++;
   }
   launch_scatter_perm(w, sym->dev.perm, scale, n, k, X, ldx, st);

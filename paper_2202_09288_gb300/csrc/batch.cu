@@ -34,6 +34,7 @@ struct chol_batch {
   int4* d_asm_src = nullptr;
   SnDev* d_sn = nullptr;
   MatDev* d_mat = nullptr;
+  int* d_ctr = nullptr;  // work-queue counters of the batch's launches
   int32_t nlev = 0;
   int max_width = 0;
   // captured factorization
@@ -54,6 +55,8 @@ void batch_release(chol_batch* b) {
   dev_free(b->ctx, b->d_asm_src);
   dev_free(b->ctx, b->d_sn);
   dev_free(b->ctx, b->d_mat);
+  dev_free(b->ctx, b->d_ctr);
+  b->d_ctr = nullptr;
   for (int k = 0; k < chol::kNumTaskKinds; k++) b->d_tasks[k] = nullptr;
   b->d_asm_src = nullptr;
   b->d_sn = nullptr;
@@ -80,7 +83,7 @@ int enqueue_batch(chol_batch* b) {
     int rc = enqueue_assembly(f);
     if (rc) return rc;
   }
-  return enqueue_levels(b->ctx, batch_view(b), b->d_sn, b->d_mat, b->f32, b->owner);
+  return enqueue_levels(b->ctx, batch_view(b), b->d_sn, b->d_mat, b->f32, b->owner, b->d_ctr);
 }
 
 const int kFactorKinds[] = {chol::kTaskPotrf, chol::kTaskTrsm, chol::kTaskSchur64,
@@ -175,7 +178,8 @@ int chol_batch_create(chol_ctx* c, int count, chol_num* const* nums, chol_batch*
     const size_t ab = b->asm_src.size() * sizeof(int32_t);
     if (!(rc = dev_alloc(c, (void**)&b->d_asm_src, ab)) &&
         !(rc = dev_alloc(c, (void**)&b->d_sn, sn.size() * sizeof(SnDev))) &&
-        !(rc = dev_alloc(c, (void**)&b->d_mat, mats.size() * sizeof(MatDev)))) {
+        !(rc = dev_alloc(c, (void**)&b->d_mat, mats.size() * sizeof(MatDev))) &&
+        !(rc = dev_alloc(c, (void**)&b->d_ctr, factor_counters(b->nlev) * sizeof(int)))) {
       if ((ab && cudaMemcpyAsync(b->d_asm_src, b->asm_src.data(), ab, cudaMemcpyHostToDevice,
                                  c->stream) != cudaSuccess) ||
           cudaMemcpyAsync(b->d_sn, sn.data(), sn.size() * sizeof(SnDev), cudaMemcpyHostToDevice,

@@ -61,12 +61,18 @@ __global__ void k_assemble(const double* __restrict__ vals, const int64_t* __res
 // One CTA per supernode; the n x n lower block is factored in shared memory by the
 // unblocked right-looking column algorithm: pivot sqrt, column scale, rank-1 update.
 template <typename T>
-__global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, int ntasks,
+__global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                const SnDev* __restrict__ sns,
                                                const MatDev* __restrict__ mats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
-  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+  __shared__ int s_next_task;
+  for (;;) {
+    // persistent CTA: take the next task of this launch from its work-queue counter
+    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int tq = s_next_task;
+    if (tq >= ntasks) break;
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
@@ -111,10 +117,16 @@ __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, i
 // Task {s, r0}: rows r0 .. r0+31 of L21 (panel rows n + r0 + t), one row per thread:
 // x_j = (a_j - sum_{k<j} x_k L_jk) / L_jj, i.e. L21 = A21 L11^{-T}.
 template <typename T>
-__global__ void __launch_bounds__(kTrsmRows) k_trsm(const int4* __restrict__ tasks, int ntasks,
+__global__ void __launch_bounds__(kTrsmRows) k_trsm(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                     const SnDev* __restrict__ sns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+  __shared__ int s_next_task;
+  for (;;) {
+    // persistent CTA: take the next task of this launch from its work-queue counter
+    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int tq = s_next_task;
+    if (tq >= ntasks) break;
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
@@ -232,7 +244,7 @@ __device__ __forceinline__ void dmma_884(double (&c)[2], double a, double b) {
 
 template <int TILE, bool OWNER>
 __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
-    k_schur_f64(const int4* __restrict__ tasks, int ntasks, const SnDev* __restrict__ sns,
+    k_schur_f64(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue, const SnDev* __restrict__ sns,
                 const MatDev* __restrict__ mats) {
   using Cfg = SchurCfg<TILE>;
   constexpr int KC = Cfg::KC, LDS = Cfg::LDS, MB = Cfg::MB;
@@ -241,7 +253,13 @@ __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
   double* As = sh;              // [KC][LDS]: As[kk][ii] = L21[i0 + ii][kc + kk]
   double* Bs = sh + KC * LDS;   // [KC][LDS]: Bs[kk][jj] = L21[k0 + jj][kc + kk]
 
-  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+  __shared__ int s_next_task;
+  for (;;) {
+    // persistent CTA: take the next task of this launch from its work-queue counter
+    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int tq = s_next_task;
+    if (tq >= ntasks) break;
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
@@ -319,7 +337,7 @@ struct SchurF32Cfg {
 
 template <int TILE, bool OWNER>
 __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
-    k_schur_f32(const int4* __restrict__ tasks, int ntasks, const SnDev* __restrict__ sns,
+    k_schur_f32(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue, const SnDev* __restrict__ sns,
                 const MatDev* __restrict__ mats) {
   using Cfg = SchurF32Cfg<TILE>;
   constexpr int KC = Cfg::KC, LDS = Cfg::LDS, S = Cfg::S;
@@ -327,7 +345,13 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
                                                                      : TILE * (TILE + 1)];
   float* As = sh;
   float* Bs = sh + KC * LDS;
-  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+  __shared__ int s_next_task;
+  for (;;) {
+    // persistent CTA: take the next task of this launch from its work-queue counter
+    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int tq = s_next_task;
+    if (tq >= ntasks) break;
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
@@ -383,12 +407,18 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
 // factored in FP32; if any pivot falls below tau (tau times the original diagonal, which
 // is 1 after equilibration), the block is factored again in FP64 from an FP64 copy of
 // its values, and the FP64 result is rounded into the panel.  err[2] counts such redos.
-__global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ tasks, int ntasks,
+__global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                      const SnDev* __restrict__ sns,
                                                      const MatDev* __restrict__ mats,
                                                      float tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+  __shared__ int s_next_task;
+  for (;;) {
+    // persistent CTA: take the next task of this launch from its work-queue counter
+    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int tq = s_next_task;
+    if (tq >= ntasks) break;
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
@@ -468,10 +498,16 @@ constexpr int kAsmRowChunk = 1024;
 
 template <typename T>
 __global__ void __launch_bounds__(kAsmThreads)
-    k_assemble_owner(const int4* __restrict__ groups, int ntasks, const int4* __restrict__ srcs,
+    k_assemble_owner(const int4* __restrict__ groups, int ntasks, int* __restrict__ queue, const int4* __restrict__ srcs,
                      const SnDev* __restrict__ sns, const MatDev* __restrict__ mats) {
   __shared__ int relpos[kAsmRowChunk];
-  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+  __shared__ int s_next_task;
+  for (;;) {
+    // persistent CTA: take the next task of this launch from its work-queue counter
+    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int tq = s_next_task;
+    if (tq >= ntasks) break;
     const int4 g = groups[tq];
     const SnDev td = sns[g.x];
     const MatDev md = mats[td.mat];
@@ -518,83 +554,84 @@ static size_t trsm_smem(int w) {
   return ((size_t)w * w + w + (size_t)w * kTrsmRows) * sizeof(double);
 }
 
-void launch_potrf(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
-                  int max_width, bool f32, float tau, cudaStream_t st) {
+void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
+                  const MatDev* mats, int max_width, bool f32, float tau, cudaStream_t st) {
   if (ntasks <= 0) return;
   if (f32) {
     const size_t sm = potrf_mixed_smem(max_width);
     k_potrf_mixed<<<persistent_grid(k_potrf_mixed, 128, sm, ntasks), 128, sm, st>>>(
-        tasks, ntasks, sns, mats, tau);
+        tasks, ntasks, queue, sns, mats, tau);
   } else {
     const size_t sm = potrf_smem(max_width);
     k_potrf<double><<<persistent_grid(k_potrf<double>, 128, sm, ntasks), 128, sm, st>>>(
-        tasks, ntasks, sns, mats);
+        tasks, ntasks, queue, sns, mats);
   }
 }
 
 template <typename T>
-static void trsm_t(const int4* tasks, int ntasks, const SnDev* sns, int max_width, cudaStream_t st) {
+static void trsm_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int max_width,
+                   cudaStream_t st) {
   const size_t sm = trsm_smem(max_width);
   k_trsm<T><<<persistent_grid(k_trsm<T>, kTrsmRows, sm, ntasks), kTrsmRows, sm, st>>>(
-      tasks, ntasks, sns);
+      tasks, ntasks, queue, sns);
 }
 
-void launch_trsm(const int4* tasks, int ntasks, const SnDev* sns, int max_width, bool f32,
-                 cudaStream_t st) {
+void launch_trsm(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int max_width,
+                 bool f32, cudaStream_t st) {
   if (ntasks <= 0) return;
-  if (f32) trsm_t<float>(tasks, ntasks, sns, max_width, st);
-  else trsm_t<double>(tasks, ntasks, sns, max_width, st);
+  if (f32) trsm_t<float>(tasks, ntasks, queue, sns, max_width, st);
+  else trsm_t<double>(tasks, ntasks, queue, sns, max_width, st);
 }
 
 template <int T, bool OWNER>
-static void schur_f64_t(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
-                        cudaStream_t st) {
+static void schur_f64_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
+                        const MatDev* mats, cudaStream_t st) {
   constexpr int th = SchurCfg<T>::THREADS;
   k_schur_f64<T, OWNER><<<persistent_grid(k_schur_f64<T, OWNER>, th, 0, ntasks), th, 0, st>>>(
-      tasks, ntasks, sns, mats);
+      tasks, ntasks, queue, sns, mats);
 }
 
 template <int T, bool OWNER>
-static void schur_f32_t(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
-                        cudaStream_t st) {
+static void schur_f32_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
+                        const MatDev* mats, cudaStream_t st) {
   constexpr int th = SchurF32Cfg<T>::THREADS;
   k_schur_f32<T, OWNER><<<persistent_grid(k_schur_f32<T, OWNER>, th, 0, ntasks), th, 0, st>>>(
-      tasks, ntasks, sns, mats);
+      tasks, ntasks, queue, sns, mats);
 }
 
 template <bool OWNER>
-static void schur_cls(int cls, bool f32, const int4* tasks, int ntasks, const SnDev* sns,
-                      const MatDev* mats, cudaStream_t st) {
+static void schur_cls(int cls, bool f32, const int4* tasks, int ntasks, int* queue,
+                      const SnDev* sns, const MatDev* mats, cudaStream_t st) {
   if (f32) {
-    if (cls == kTile64) schur_f32_t<64, OWNER>(tasks, ntasks, sns, mats, st);
-    else if (cls == kTile32) schur_f32_t<32, OWNER>(tasks, ntasks, sns, mats, st);
-    else schur_f32_t<16, OWNER>(tasks, ntasks, sns, mats, st);
+    if (cls == kTile64) schur_f32_t<64, OWNER>(tasks, ntasks, queue, sns, mats, st);
+    else if (cls == kTile32) schur_f32_t<32, OWNER>(tasks, ntasks, queue, sns, mats, st);
+    else schur_f32_t<16, OWNER>(tasks, ntasks, queue, sns, mats, st);
   } else {
-    if (cls == kTile64) schur_f64_t<64, OWNER>(tasks, ntasks, sns, mats, st);
-    else if (cls == kTile32) schur_f64_t<32, OWNER>(tasks, ntasks, sns, mats, st);
-    else schur_f64_t<16, OWNER>(tasks, ntasks, sns, mats, st);
+    if (cls == kTile64) schur_f64_t<64, OWNER>(tasks, ntasks, queue, sns, mats, st);
+    else if (cls == kTile32) schur_f64_t<32, OWNER>(tasks, ntasks, queue, sns, mats, st);
+    else schur_f64_t<16, OWNER>(tasks, ntasks, queue, sns, mats, st);
   }
 }
 
-void launch_schur(int cls, const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
-                  bool owner, bool f32, cudaStream_t st) {
+void launch_schur(int cls, const int4* tasks, int ntasks, int* queue, const SnDev* sns,
+                  const MatDev* mats, bool owner, bool f32, cudaStream_t st) {
   if (ntasks <= 0) return;
-  if (owner) schur_cls<true>(cls, f32, tasks, ntasks, sns, mats, st);
-  else schur_cls<false>(cls, f32, tasks, ntasks, sns, mats, st);
+  if (owner) schur_cls<true>(cls, f32, tasks, ntasks, queue, sns, mats, st);
+  else schur_cls<false>(cls, f32, tasks, ntasks, queue, sns, mats, st);
 }
 
 template <typename T>
-static void asm_owner_t(const int4* groups, int ngroups, const int4* srcs, const SnDev* sns,
-                        const MatDev* mats, cudaStream_t st) {
+static void asm_owner_t(const int4* groups, int ngroups, int* queue, const int4* srcs,
+                        const SnDev* sns, const MatDev* mats, cudaStream_t st) {
   k_assemble_owner<T><<<persistent_grid(k_assemble_owner<T>, kAsmThreads, 0, ngroups),
-                        kAsmThreads, 0, st>>>(groups, ngroups, srcs, sns, mats);
+                        kAsmThreads, 0, st>>>(groups, ngroups, queue, srcs, sns, mats);
 }
 
-void launch_assemble_owner(const int4* groups, int ngroups, const int4* srcs, const SnDev* sns,
-                           const MatDev* mats, bool f32, cudaStream_t st) {
+void launch_assemble_owner(const int4* groups, int ngroups, int* queue, const int4* srcs,
+                           const SnDev* sns, const MatDev* mats, bool f32, cudaStream_t st) {
   if (ngroups <= 0) return;
-  if (f32) asm_owner_t<float>(groups, ngroups, srcs, sns, mats, st);
-  else asm_owner_t<double>(groups, ngroups, srcs, sns, mats, st);
+  if (f32) asm_owner_t<float>(groups, ngroups, queue, srcs, sns, mats, st);
+  else asm_owner_t<double>(groups, ngroups, queue, srcs, sns, mats, st);
 }
 
 template <typename K>

@@ -9,10 +9,11 @@
 // is one fixed array in the library's device image, sized kNoAllocScratchBytes.
 //
 // The array lives in every GPU that loads the library until the process exits.  Every
-// call uses the same array and leaves its contents behind: nothing in the solve needs it
-// cleared, because each pass writes every workspace entry it later reads.  Two calls
-// whose device work overlaps (different streams, or different contexts on one device)
-// race on the array, so the caller must order them.
+// call uses the same array and leaves its contents behind: the only part that must start
+// at zero, the work-queue counters of the solve's launches at its head, is cleared by each
+// call; every other workspace entry is written before it is read.  Two calls whose device
+// work overlaps (different streams, or different contexts on one device) race on the
+// array, so the caller must order them.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -89,6 +89,7 @@ struct chol_num {
   void* L = nullptr;           // panels (double, or float for CHOL_MIXED)
   SnDev* d_sn = nullptr;
   MatDev* d_mat = nullptr;
+  int* d_ctr = nullptr;        // work-queue counters: factor launches, then solve launches
   unsigned long long* d_err = nullptr;  // [0] failing column + 1, [1] map misses,
                                         // [2] FP64 pivot redos
   double* d_vals = nullptr;    // device copy of A's values (assembly and residual)
@@ -135,8 +136,12 @@ int enqueue_factor(chol_num* f);
 // Releases the device memory of every batch of c (called by chol_destroy).
 void detach_batches(chol_ctx* c);
 TaskView sym_view(const chol_sym* sym);
+// Work-queue counters (one int per persistent launch): 6 per level for a factorization
+// (POTRF, TRSM, three Schur tile classes, owner assembly), 3 per level for a solve.
+inline size_t factor_counters(int32_t nlev) { return 6 * (size_t)nlev + 8; }
+inline size_t solve_counters(int32_t nlev) { return 3 * (size_t)nlev + 8; }
 int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
-                   bool f32, bool owner);
+                   bool f32, bool owner, int* ctr);
 void fill_descriptors(const chol_num* f, int mat, int32_t sn_base, std::vector<SnDev>* sn,
                       MatDev* md);
 

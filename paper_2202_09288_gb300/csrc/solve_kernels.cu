@@ -112,11 +112,17 @@ __device__ void load_l11(const SnDev& d, P* L11, P* rdiag) {
 // staging slots (q * kSolveRows + ii) * nrhs + c instead of atomics into y.
 template <typename P, bool STAGE>
 __global__ void __launch_bounds__(kSolveThreads)
-    k_fwd(const int4* __restrict__ tasks, int ntasks, const SnDev* __restrict__ sns, int64_t ldv, int nrhs,
+    k_fwd(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue, const SnDev* __restrict__ sns, int64_t ldv, int nrhs,
           double* __restrict__ y, double* __restrict__ w, double* __restrict__ fstage) {
   extern __shared__ __align__(16) double sm[];
   P* smp = reinterpret_cast<P*>(sm);
-  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+  __shared__ int s_next_task;
+  for (;;) {
+    // persistent CTA: take the next task of this launch from its work-queue counter
+    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int tq = s_next_task;
+    if (tq >= ntasks) break;
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
@@ -182,11 +188,17 @@ __global__ void k_fwd_gather(const int32_t* __restrict__ fg_row, const int64_t* 
 // Backward partials: the level's task q = blockIdx.x writes part[q * W * nrhs + c * W + j].
 template <typename P>
 __global__ void __launch_bounds__(kSolveThreads)
-    k_bwd_partial(const int4* __restrict__ tasks, int ntasks, const SnDev* __restrict__ sns,
+    k_bwd_partial(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue, const SnDev* __restrict__ sns,
                   int64_t ldv, int nrhs, int W, const double* __restrict__ w,
                   double* __restrict__ part) {
   extern __shared__ __align__(16) double sm[];
-  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+  __shared__ int s_next_task;
+  for (;;) {
+    // persistent CTA: take the next task of this launch from its work-queue counter
+    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int tq = s_next_task;
+    if (tq >= ntasks) break;
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
@@ -214,12 +226,18 @@ __global__ void __launch_bounds__(kSolveThreads)
 // a global index into the backward task list, base the first task of this level.
 template <typename P>
 __global__ void __launch_bounds__(kSolveThreads)
-    k_bwd_diag(const int4* __restrict__ tasks, int ntasks, int64_t base, const SnDev* __restrict__ sns,
+    k_bwd_diag(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue, int64_t base, const SnDev* __restrict__ sns,
                int64_t ldv, int nrhs, int W, const double* __restrict__ part,
                double* __restrict__ w) {
   extern __shared__ __align__(16) double sm[];
   P* smp = reinterpret_cast<P*>(sm);
-  for (int tq = blockIdx.x; tq < ntasks; tq += gridDim.x) {
+  __shared__ int s_next_task;
+  for (;;) {
+    // persistent CTA: take the next task of this launch from its work-queue counter
+    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int tq = s_next_task;
+    if (tq >= ntasks) break;
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n;
@@ -267,22 +285,22 @@ void launch_scatter_perm(const double* w, const int32_t* perm, const double* sca
 }
 
 template <typename P>
-static void fwd_t(const int4* tasks, int ntasks, const SnDev* sns, int64_t ldv, int nrhs, int W,
-                  double* y, double* w, double* fstage, cudaStream_t st) {
+static void fwd_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int64_t ldv,
+                  int nrhs, int W, double* y, double* w, double* fstage, cudaStream_t st) {
   const size_t sm = solve_smem(W, nrhs);
   if (fstage)
     k_fwd<P, true><<<persistent_grid(k_fwd<P, true>, kSolveThreads, sm, ntasks), kSolveThreads,
-                     sm, st>>>(tasks, ntasks, sns, ldv, nrhs, y, w, fstage);
+                     sm, st>>>(tasks, ntasks, queue, sns, ldv, nrhs, y, w, fstage);
   else
     k_fwd<P, false><<<persistent_grid(k_fwd<P, false>, kSolveThreads, sm, ntasks), kSolveThreads,
-                      sm, st>>>(tasks, ntasks, sns, ldv, nrhs, y, w, nullptr);
+                      sm, st>>>(tasks, ntasks, queue, sns, ldv, nrhs, y, w, nullptr);
 }
 
-void launch_fwd(const int4* tasks, int ntasks, const SnDev* sns, int64_t ldv, int nrhs, int W,
-                double* y, double* w, double* fstage, bool f32, cudaStream_t st) {
+void launch_fwd(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int64_t ldv,
+                int nrhs, int W, double* y, double* w, double* fstage, bool f32, cudaStream_t st) {
   if (ntasks <= 0) return;
-  if (f32) fwd_t<float>(tasks, ntasks, sns, ldv, nrhs, W, y, w, fstage, st);
-  else fwd_t<double>(tasks, ntasks, sns, ldv, nrhs, W, y, w, fstage, st);
+  if (f32) fwd_t<float>(tasks, ntasks, queue, sns, ldv, nrhs, W, y, w, fstage, st);
+  else fwd_t<double>(tasks, ntasks, queue, sns, ldv, nrhs, W, y, w, fstage, st);
 }
 
 void launch_fwd_gather(const int32_t* fg_row, const int64_t* fg_ptr, const int32_t* fg_ent,
@@ -294,26 +312,30 @@ void launch_fwd_gather(const int32_t* fg_row, const int64_t* fg_ptr, const int32
 }
 
 template <typename P>
-static void bwd_t(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* diag_tasks,
-                  int ndiag, const SnDev* sns, int64_t ldv, int nrhs, int W, double* w,
-                  double* part, cudaStream_t st) {
+static void bwd_t(const int4* bwd_tasks, int nbwd, int* queues, int64_t bwd_base,
+                  const int4* diag_tasks, int ndiag, const SnDev* sns, int64_t ldv, int nrhs,
+                  int W, double* w, double* part, cudaStream_t st) {
   if (nbwd > 0) {
     const size_t sp = (size_t)kSolveRows * nrhs * sizeof(double);
     k_bwd_partial<P><<<persistent_grid(k_bwd_partial<P>, kSolveThreads, sp, nbwd), kSolveThreads,
-                       sp, st>>>(bwd_tasks, nbwd, sns, ldv, nrhs, W, w, part);
+                       sp, st>>>(bwd_tasks, nbwd, queues, sns, ldv, nrhs, W, w, part);
   }
   if (ndiag > 0) {
     const size_t sm = solve_smem(W, nrhs);
     k_bwd_diag<P><<<persistent_grid(k_bwd_diag<P>, kSolveThreads, sm, ndiag), kSolveThreads, sm,
-                    st>>>(diag_tasks, ndiag, bwd_base, sns, ldv, nrhs, W, part, w);
+                    st>>>(diag_tasks, ndiag, queues + 1, bwd_base, sns, ldv, nrhs, W, part, w);
   }
 }
 
-void launch_bwd(const int4* bwd_tasks, int nbwd, int64_t bwd_base, const int4* diag_tasks,
-                int ndiag, const SnDev* sns, int64_t ldv, int nrhs, int W, double* w,
-                double* part, bool f32, cudaStream_t st) {
-  if (f32) bwd_t<float>(bwd_tasks, nbwd, bwd_base, diag_tasks, ndiag, sns, ldv, nrhs, W, w, part, st);
-  else bwd_t<double>(bwd_tasks, nbwd, bwd_base, diag_tasks, ndiag, sns, ldv, nrhs, W, w, part, st);
+void launch_bwd(const int4* bwd_tasks, int nbwd, int* queues, int64_t bwd_base,
+                const int4* diag_tasks, int ndiag, const SnDev* sns, int64_t ldv, int nrhs,
+                int W, double* w, double* part, bool f32, cudaStream_t st) {
+  if (f32)
+    bwd_t<float>(bwd_tasks, nbwd, queues, bwd_base, diag_tasks, ndiag, sns, ldv, nrhs, W, w,
+                 part, st);
+  else
+    bwd_t<double>(bwd_tasks, nbwd, queues, bwd_base, diag_tasks, ndiag, sns, ldv, nrhs, W, w,
+                  part, st);
 }
 
 template <typename K>
