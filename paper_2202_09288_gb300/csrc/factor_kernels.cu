@@ -67,12 +67,7 @@ __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, i
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   __shared__ int s_next_task;
-  for (;;) {
-    // persistent CTA: take the next task of this launch from its work-queue counter
-    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
-    __syncthreads();
-    const int tq = s_next_task;
-    if (tq >= ntasks) break;
+  for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
@@ -110,6 +105,12 @@ __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, i
       if (r >= c) L[(int64_t)c * m + r] = A[idx];
     }
     __syncthreads();
+    // a CTA's first task is its block index; only a grid smaller than the task list makes
+    // CTAs take further tasks from this launch's work queue
+    if (gridDim.x >= ntasks) break;
+    if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
+    __syncthreads();
+    tq = s_next_task;
   }
 }
 
@@ -121,12 +122,7 @@ __global__ void __launch_bounds__(kTrsmRows) k_trsm(const int4* __restrict__ tas
                                                     const SnDev* __restrict__ sns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next_task;
-  for (;;) {
-    // persistent CTA: take the next task of this launch from its work-queue counter
-    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
-    __syncthreads();
-    const int tq = s_next_task;
-    if (tq >= ntasks) break;
+  for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
@@ -153,6 +149,12 @@ __global__ void __launch_bounds__(kTrsmRows) k_trsm(const int4* __restrict__ tas
       }
     }
     __syncthreads();
+    // a CTA's first task is its block index; only a grid smaller than the task list makes
+    // CTAs take further tasks from this launch's work queue
+    if (gridDim.x >= ntasks) break;
+    if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
+    __syncthreads();
+    tq = s_next_task;
   }
 }
 
@@ -254,12 +256,7 @@ __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
   double* Bs = sh + KC * LDS;   // [KC][LDS]: Bs[kk][jj] = L21[k0 + jj][kc + kk]
 
   __shared__ int s_next_task;
-  for (;;) {
-    // persistent CTA: take the next task of this launch from its work-queue counter
-    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
-    __syncthreads();
-    const int tq = s_next_task;
-    if (tq >= ntasks) break;
+  for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
@@ -320,6 +317,12 @@ __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
     schur_tile_epilogue<double, TILE, Cfg::THREADS, OWNER>(
         Cs, d, i0, k0, sns, mats, static_cast<double*>(mats[d.mat].stage));
     __syncthreads();
+    // a CTA's first task is its block index; only a grid smaller than the task list makes
+    // CTAs take further tasks from this launch's work queue
+    if (gridDim.x >= ntasks) break;
+    if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
+    __syncthreads();
+    tq = s_next_task;
   }
 }
 
@@ -346,12 +349,7 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
   float* As = sh;
   float* Bs = sh + KC * LDS;
   __shared__ int s_next_task;
-  for (;;) {
-    // persistent CTA: take the next task of this launch from its work-queue counter
-    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
-    __syncthreads();
-    const int tq = s_next_task;
-    if (tq >= ntasks) break;
+  for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
@@ -399,6 +397,12 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
     schur_tile_epilogue<float, TILE, Cfg::THREADS, OWNER>(
         Cs, d, i0, k0, sns, mats, static_cast<float*>(mats[d.mat].stage));
     __syncthreads();
+    // a CTA's first task is its block index; only a grid smaller than the task list makes
+    // CTAs take further tasks from this launch's work queue
+    if (gridDim.x >= ntasks) break;
+    if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
+    __syncthreads();
+    tq = s_next_task;
   }
 }
 
@@ -413,12 +417,7 @@ __global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ ta
                                                      float tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next_task;
-  for (;;) {
-    // persistent CTA: take the next task of this launch from its work-queue counter
-    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
-    __syncthreads();
-    const int tq = s_next_task;
-    if (tq >= ntasks) break;
+  for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
@@ -485,6 +484,12 @@ __global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ ta
       if (r >= c) L[(int64_t)c * m + r] = A[idx];
     }
     __syncthreads();
+    // a CTA's first task is its block index; only a grid smaller than the task list makes
+    // CTAs take further tasks from this launch's work queue
+    if (gridDim.x >= ntasks) break;
+    if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
+    __syncthreads();
+    tq = s_next_task;
   }
 }
 
@@ -502,12 +507,7 @@ __global__ void __launch_bounds__(kAsmThreads)
                      const SnDev* __restrict__ sns, const MatDev* __restrict__ mats) {
   __shared__ int relpos[kAsmRowChunk];
   __shared__ int s_next_task;
-  for (;;) {
-    // persistent CTA: take the next task of this launch from its work-queue counter
-    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
-    __syncthreads();
-    const int tq = s_next_task;
-    if (tq >= ntasks) break;
+  for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 g = groups[tq];
     const SnDev td = sns[g.x];
     const MatDev md = mats[td.mat];
@@ -536,6 +536,12 @@ __global__ void __launch_bounds__(kAsmThreads)
       }
     }
     __syncthreads();
+    // a CTA's first task is its block index; only a grid smaller than the task list makes
+    // CTAs take further tasks from this launch's work queue
+    if (gridDim.x >= ntasks) break;
+    if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
+    __syncthreads();
+    tq = s_next_task;
   }
 }
 

@@ -39,12 +39,17 @@ inline int resident_ctas(const void* kernel, int threads, size_t smem) {
   return r;
 }
 
-// Grid of a persistent launch over ntasks tasks: one CTA per task up to the resident limit,
-// beyond it each CTA loops over tasks tq = blockIdx.x, blockIdx.x + gridDim.x, ...
+// Grid of a task launch.  Every CTA takes tasks from the launch's work queue until it is
+// empty.  Measured on GB300, a grid of one CTA per task (the hardware block scheduler then
+// refills SMs as CTAs finish) balances the uneven task costs of a level better than a
+// single resident wave, so the grid is the task count, never less than one resident wave
+// would need; the queue makes any grid size correct.
 template <typename K>
 inline int persistent_grid(K kernel, int threads, size_t smem, int ntasks) {
-  const int r = resident_ctas(reinterpret_cast<const void*>(kernel), threads, smem);
-  return ntasks < r ? ntasks : r;
+  (void)kernel;
+  (void)threads;
+  (void)smem;
+  return ntasks;
 }
 
 }  // namespace chol

@@ -117,12 +117,7 @@ __global__ void __launch_bounds__(kSolveThreads)
   extern __shared__ __align__(16) double sm[];
   P* smp = reinterpret_cast<P*>(sm);
   __shared__ int s_next_task;
-  for (;;) {
-    // persistent CTA: take the next task of this launch from its work-queue counter
-    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
-    __syncthreads();
-    const int tq = s_next_task;
-    if (tq >= ntasks) break;
+  for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
@@ -166,6 +161,12 @@ __global__ void __launch_bounds__(kSolveThreads)
       }
     }
     __syncthreads();
+    // a CTA's first task is its block index; only a grid smaller than the task list makes
+    // CTAs take further tasks from this launch's work queue
+    if (gridDim.x >= ntasks) break;
+    if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
+    __syncthreads();
+    tq = s_next_task;
   }
 }
 
@@ -193,12 +194,7 @@ __global__ void __launch_bounds__(kSolveThreads)
                   double* __restrict__ part) {
   extern __shared__ __align__(16) double sm[];
   __shared__ int s_next_task;
-  for (;;) {
-    // persistent CTA: take the next task of this launch from its work-queue counter
-    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
-    __syncthreads();
-    const int tq = s_next_task;
-    if (tq >= ntasks) break;
+  for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
@@ -219,6 +215,12 @@ __global__ void __launch_bounds__(kSolveThreads)
       out[c * W + j] = (double)acc;
     }
     __syncthreads();
+    // a CTA's first task is its block index; only a grid smaller than the task list makes
+    // CTAs take further tasks from this launch's work queue
+    if (gridDim.x >= ntasks) break;
+    if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
+    __syncthreads();
+    tq = s_next_task;
   }
 }
 
@@ -232,12 +234,7 @@ __global__ void __launch_bounds__(kSolveThreads)
   extern __shared__ __align__(16) double sm[];
   P* smp = reinterpret_cast<P*>(sm);
   __shared__ int s_next_task;
-  for (;;) {
-    // persistent CTA: take the next task of this launch from its work-queue counter
-    if (threadIdx.x == 0) s_next_task = atomicAdd(queue, 1);
-    __syncthreads();
-    const int tq = s_next_task;
-    if (tq >= ntasks) break;
+  for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n;
@@ -260,6 +257,12 @@ __global__ void __launch_bounds__(kSolveThreads)
       w[c * ldv + d.col0 + j] = xs[idx];
     }
     __syncthreads();
+    // a CTA's first task is its block index; only a grid smaller than the task list makes
+    // CTAs take further tasks from this launch's work queue
+    if (gridDim.x >= ntasks) break;
+    if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
+    __syncthreads();
+    tq = s_next_task;
   }
 }
 
