@@ -171,10 +171,13 @@ __device__ __forceinline__ void schur_tile_epilogue(const T* Cs, const SnDev& d,
                                                     const SnDev* __restrict__ sns,
                                                     const MatDev* __restrict__ mats,
                                                     T* __restrict__ stage) {
+  constexpr int RB = THREADS >= TILE ? THREADS / TILE : 1;  // runs resolved at a time
+  constexpr int LANES = THREADS < 32 ? THREADS : 32;
+  __shared__ int tcol[TILE];                 // target supernode of every tile column
   __shared__ int run_start[TILE + 1];
   __shared__ int run_t[TILE];
   __shared__ int nruns;
-  __shared__ int relpos[TILE];
+  __shared__ int relpos[RB][TILE];
   const int tid = threadIdx.x;
   const int n = d.n, u = d.m - d.n;
   const int32_t* rows = d.rows + n;  // off-diagonal rows of s
@@ -189,34 +192,61 @@ __device__ __forceinline__ void schur_tile_epilogue(const T* Cs, const SnDev& d,
     return;
   }
   const MatDev md = mats[d.mat];
-  // runs of tile columns with the same target supernode
-  if (tid == 0) {
-    int nr = 0, prev = -1;
-    for (int kk = 0; kk < klim; kk++) {
-      const int t = md.col2sn[rows[k0 + kk]];
-      if (t != prev) { run_start[nr] = kk; run_t[nr] = t; nr++; prev = t; }
+  // targets of the tile columns, all at once
+  for (int kk = tid; kk < klim; kk += THREADS) tcol[kk] = md.col2sn[rows[k0 + kk]];
+  __syncthreads();
+  // runs of columns with the same target, found with warp ballots by the first warp
+  if (tid < LANES) {
+    const unsigned mask = LANES == 32 ? 0xffffffffu : ((1u << LANES) - 1u);
+    int nr = 0;
+    for (int base = 0; base < klim; base += LANES) {
+      const int kk = base + tid;
+      const bool start = kk < klim && (kk == 0 || tcol[kk] != tcol[kk - 1]);
+      const unsigned b = __ballot_sync(mask, start);
+      if (start) {
+        const int q = nr + __popc(b & ((1u << tid) - 1u));
+        run_start[q] = kk;
+        run_t[q] = tcol[kk];
+      }
+      nr += __popc(b);
     }
-    run_start[nr] = klim;
-    nruns = nr;
+    if (tid == 0) {
+      run_start[nr] = klim;
+      nruns = nr;
+    }
   }
   __syncthreads();
-  for (int r = 0; r < nruns; r++) {
-    const SnDev td = sns[md.sn_base + run_t[r]];
-    const int kb = run_start[r], ke = run_start[r + 1];
-    // relative map of the tile rows inside the target's rows (rows >= the run's first
-    // column row are all present in the target, by the elimination-tree property)
-    for (int ii = tid; ii < ilim; ii += THREADS) {
-      const int gi = i0 + ii;
-      relpos[ii] = gi >= k0 + kb ? relative_row(md, td.rows, td.m, rows[gi]) : -1;
+  for (int r0 = 0; r0 < nruns; r0 += RB) {
+    // relative map of the tile rows inside each target's rows (rows at or below the run's
+    // first column row are all present in the target, by the elimination-tree property)
+    for (int idx = tid; idx < RB * TILE; idx += THREADS) {
+      const int rr = idx / TILE, ii = idx - rr * TILE;
+      const int r = r0 + rr;
+      if (r < nruns && ii < ilim) {
+        const int gi = i0 + ii;
+        int p = -1;
+        if (gi >= k0 + run_start[r]) {
+          const SnDev& td = sns[md.sn_base + run_t[r]];
+          const int key = rows[gi];
+          // rows inside the target's own columns sit at key - col0
+          p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
+        }
+        relpos[rr][ii] = p;
+      }
     }
     __syncthreads();
-    T* Lt = reinterpret_cast<T*>(td.L);
-    const int w = ke - kb;
-    for (int idx = tid; idx < w * TILE; idx += THREADS) {
-      const int kk = kb + idx / TILE, ii = idx % TILE;
-      if (ii < ilim && i0 + ii >= k0 + kk && relpos[ii] >= 0) {
-        const int c = rows[k0 + kk] - td.col0;
-        atomicAdd(&Lt[(int64_t)c * td.m + relpos[ii]], -Cs[kk * (TILE + 1) + ii]);
+    for (int rr = 0; rr < RB && r0 + rr < nruns; rr++) {
+      const int r = r0 + rr;
+      const SnDev& td = sns[md.sn_base + run_t[r]];
+      T* Lt = reinterpret_cast<T*>(td.L);
+      const int kb = run_start[r], w = run_start[r + 1] - kb;
+      for (int idx = tid; idx < w * TILE; idx += THREADS) {
+        const int kk = kb + idx / TILE, ii = idx % TILE;
+        const int p = relpos[rr][ii];
+        if (ii < ilim && i0 + ii >= k0 + kk && p >= 0) {
+          const int c = rows[k0 + kk] - td.col0;
+          atomicAdd(&Lt[(int64_t)c * td.m + p], -Cs[kk * (TILE + 1) + ii]);
+        }
       }
     }
     __syncthreads();
