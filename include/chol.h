@@ -222,20 +222,26 @@ int chol_batch_factorize(chol_ctx* ctx, chol_batch* batch, const double* const* 
                          int where, int use_graph);
 void chol_batch_free(chol_batch* batch);
 
-/* Schur tile sizes per supernode size class: 64x64 tiles for supernodes with at least
- * min_rows_tile64 off-diagonal rows on levels holding at least min_level_tiles64 such
- * tiles, else 32x32 from min_rows_tile32 rows, else 16x16.  Default {64, 17, 304}. */
+/* Schur tile sizes per supernode size class: 128x128 tiles for supernodes with at least
+ * min_rows_tile128 off-diagonal rows on levels holding at least min_level_tiles128 such
+ * tiles, else 64x64 tiles from min_rows_tile64 rows on levels holding at least
+ * min_level_tiles64 such tiles, else 32x32 from min_rows_tile32 rows, else 16x16.
+ * Default {64, 17, 304, 128, 304}.  A 128x128 tile of an FP32 (mixed-precision) factor is
+ * one tcgen05 tensor-core task (3xTF32); of an FP64 factor, four 64x64 tasks.  All
+ * fields >= 1 except the two level thresholds (>= 0); anything else is CHOL_E_INVALID. */
 typedef struct chol_tile_policy {
   int min_rows_tile64;
   int min_rows_tile32;
   int min_level_tiles64;
+  int min_rows_tile128;
+  int min_level_tiles128;
 } chol_tile_policy;
 int chol_sym_get_tile_policy(const chol_sym* sym, chol_tile_policy* policy);
 /* Rebuilds the Schur task lists of sym (and its device copy); factors made from sym use
  * the new lists from their next factorization; existing batches keep their own copy. */
 int chol_sym_set_tile_policy(chol_sym* sym, const chol_tile_policy* policy);
 /* Autotuner: times refactorizations of num (reps each) under candidate tile policies by
- * coordinate descent over the three thresholds, keeps the fastest in num's analysis,
+ * coordinate descent over the five thresholds, keeps the fastest in num's analysis,
  * stores it in *best (and its time in *best_ms) and leaves num factored under it. */
 int chol_autotune(chol_ctx* ctx, chol_num* num, int reps, chol_tile_policy* best,
                   double* best_ms);

@@ -50,7 +50,8 @@ class chol_refine_info(C.Structure):
 
 class chol_tile_policy(C.Structure):
     _fields_ = [("min_rows_tile64", C.c_int), ("min_rows_tile32", C.c_int),
-                ("min_level_tiles64", C.c_int)]
+                ("min_level_tiles64", C.c_int), ("min_rows_tile128", C.c_int),
+                ("min_level_tiles128", C.c_int)]
 
 
 class chol_server_opts(C.Structure):
@@ -340,7 +341,10 @@ def chol_sym_get_tile_policy(sym) -> dict:
 
 
 def chol_sym_set_tile_policy(sym, policy: dict) -> None:
-    p = chol_tile_policy(**policy)
+    p = chol_tile_policy()
+    _check(lib().chol_sym_get_tile_policy(sym, C.byref(p)), "chol_sym_get_tile_policy")
+    for f, v in policy.items():  # fields not given keep their current value
+        setattr(p, f, v)
     _check(lib().chol_sym_set_tile_policy(sym, C.byref(p)), "chol_sym_set_tile_policy")
 
 

@@ -24,9 +24,11 @@ namespace chol {
 
 namespace {
 
-// Tile class of a supernode's Schur update (u off-diagonal rows), given how many 64-tiles
-// its level holds.
-int choose_tile_class(const TilePolicy& p, int64_t u, int64_t level_tiles64) {
+// Tile class of a supernode's Schur update (u off-diagonal rows), given how many 64- and
+// 128-tiles its level holds.
+int choose_tile_class(const TilePolicy& p, int64_t u, int64_t level_tiles64,
+                      int64_t level_tiles128) {
+  if (u >= p.min_rows_tile128 && level_tiles128 >= p.min_level_tiles128) return kTile128;
   if (u >= p.min_rows_tile64 && level_tiles64 >= p.min_level_tiles64) return kTile64;
   if (u >= p.min_rows_tile32) return kTile32;
   return kTile16;
@@ -411,32 +413,36 @@ void build_owner_lists(Sym* S) {
 
 void build_schur_tasks(Sym* S, const TilePolicy& policy) {
   S->policy = policy;
-  for (int k = kTaskSchur64; k <= kTaskSchur16; k++) {
+  for (int cls = 0; cls < kNumTileClasses; cls++) {
+    const int k = schur_kind(cls);
     S->tasks[k].clear();
     S->task_off[k].assign(S->nlev + 1, 0);
     S->lvl_flops[k].assign(S->nlev, 0.0);
   }
   for (int32_t l = 0; l < S->nlev; l++) {
-    int64_t tiles64 = 0;
+    int64_t tiles64 = 0, tiles128 = 0;
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
       const int32_t s = S->lvl_sn[q];
       const int64_t u = S->sn_m[s] - (S->sn_start[s + 1] - S->sn_start[s]);
-      const int64_t nt = (u + 63) / 64;
+      const int64_t nt = (u + 63) / 64, nt2 = (u + 127) / 128;
       tiles64 += nt * (nt + 1) / 2;
+      tiles128 += nt2 * (nt2 + 1) / 2;
     }
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
       const int32_t s = S->lvl_sn[q];
       const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
       const int32_t u = S->sn_m[s] - w;
       if (u <= 0) continue;
-      const int cls = choose_tile_class(policy, u, tiles64);
-      const int T = tile_of_class(cls);
-      S->lvl_flops[kTaskSchur64 + cls][l] += (double)u * (u + 1.0) * w;
+      const int cls = choose_tile_class(policy, u, tiles64, tiles128);
+      const int T = tile_of_class(cls), k = schur_kind(cls);
+      S->lvl_flops[k][l] += (double)u * (u + 1.0) * w;
       for (int32_t i0 = 0; i0 < u; i0 += T)
-        for (int32_t k0 = 0; k0 <= i0; k0 += T) push4(S->tasks[kTaskSchur64 + cls], s, i0, k0, 0);
+        for (int32_t k0 = 0; k0 <= i0; k0 += T) push4(S->tasks[k], s, i0, k0, T);
     }
-    for (int k = kTaskSchur64; k <= kTaskSchur16; k++)
+    for (int cls = 0; cls < kNumTileClasses; cls++) {
+      const int k = schur_kind(cls);
       S->task_off[k][l + 1] = (int64_t)S->tasks[k].size() / 4;
+    }
   }
 }
 

@@ -220,6 +220,8 @@ int ensure_attrs(chol_ctx* c) {
   if (rc) return rc;
   rc = chol::set_solve_kernel_attrs(chol::kMaxWidth, 32);
   if (rc) return rc;
+  rc = chol::set_tc_kernel_attrs();
+  if (rc) return rc;
   c->attrs_set = true;
   return CHOL_OK;
 }
@@ -241,7 +243,8 @@ int enqueue_assembly(chol_num* f) {
   const bool f32 = f->precision == CHOL_MIXED;
   const size_t esz = f32 ? sizeof(float) : sizeof(double);
   // err[0] = smallest failing column + 1, kept by atomicMin: starts at all ones (none);
-  // err[1] = relative-map misses, err[2] = FP64 pivot redos: start at 0
+  // err[1] = relative-map misses, err[2] = FP64 pivot redos, err[3] = tensor-core wait
+  // timeouts: start at 0
   CK(cudaMemsetAsync(f->d_err, 0xff, sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(f->d_err + 1, 0, 3 * sizeof(unsigned long long), st));
   f->anorm = -1.0;
@@ -283,10 +286,9 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
   CK(cudaMemsetAsync(ctr, 0, factor_counters(v.nlev) * sizeof(int), st));
   const float tau = (float)(c->opts.pivot_tau > 0 ? c->opts.pivot_tau : 1e-5);
   const int kp = f32 ? kProfPotrfF32 : kProfPotrf, kt = f32 ? kProfTrsmF32 : kProfTrsm;
-  const int ks = f32 ? kProfSchur64F32 : kProfSchur64;
   for (int32_t l = 0; l < v.nlev; l++) {
     int cnt;
-    int* q = ctr + 6 * l;  // this level's work-queue counters
+    int* q = ctr + kFactorCountersPerLevel * l;  // this level's work-queue counters
     const int4* t = v.level(chol::kTaskPotrf, l, &cnt);
     if (cnt > 0) {
       prof_begin(c);
@@ -300,17 +302,18 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
       prof_end(c, kt, v.flops[chol::kTaskTrsm][l], 0.0);
     }
     for (int cls = 0; cls < chol::kNumTileClasses; cls++) {
-      t = v.level(chol::kTaskSchur64 + cls, l, &cnt);
+      const int kind = chol::schur_kind(cls);
+      t = v.level(kind, l, &cnt);
       if (cnt <= 0) continue;
       prof_begin(c);
       chol::launch_schur(cls, t, cnt, q + 2 + cls, sns, mats, owner, f32, st);
-      prof_end(c, ks + cls, v.flops[chol::kTaskSchur64 + cls][l], 0.0);
+      prof_end(c, prof_schur_kind(cls, f32), v.flops[kind][l], 0.0);
     }
     if (owner) {
       t = v.level(chol::kTaskAsm, l, &cnt);
       if (cnt > 0) {
         prof_begin(c);
-        chol::launch_assemble_owner(t, cnt, q + 5, v.asm_src, sns, mats, f32, st);
+        chol::launch_assemble_owner(t, cnt, q + 2 + chol::kNumTileClasses, v.asm_src, sns, mats, f32, st);
         prof_end(c, kProfAsmOwner, 0.0, 0.0);
       }
     }
@@ -870,10 +873,11 @@ int chol_refactorize(chol_ctx* c, chol_num* f, const double* vals, int where) {
 
 int chol_factor_status(chol_ctx* c, const chol_num* f, int64_t* bad_col) {
   if (!c || !f || f->ctx != c) return CHOL_E_INVALID;
-  unsigned long long ee[3] = {0, 0, 0};
-  CK(cudaMemcpyAsync(ee, f->d_err, 24, cudaMemcpyDeviceToHost, c->stream));
+  unsigned long long ee[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(ee, f->d_err, sizeof(ee), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaGetLastError());
+  if (ee[3]) return CHOL_E_TIMEOUT;  // a bounded tensor-core wait gave up
   if (ee[1]) return CHOL_E_INVALID;  // internal relative-map inconsistency
   const unsigned long long e = ee[0];
   if (e != ~0ull) {

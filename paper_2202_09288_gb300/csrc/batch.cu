@@ -86,8 +86,9 @@ int enqueue_batch(chol_batch* b) {
   return enqueue_levels(b->ctx, batch_view(b), b->d_sn, b->d_mat, b->f32, b->owner, b->d_ctr);
 }
 
-const int kFactorKinds[] = {chol::kTaskPotrf, chol::kTaskTrsm, chol::kTaskSchur64,
-                            chol::kTaskSchur32, chol::kTaskSchur16, chol::kTaskAsm};
+const int kFactorKinds[] = {chol::kTaskPotrf,   chol::kTaskTrsm,     chol::kTaskSchur64,
+                            chol::kTaskSchur32, chol::kTaskSchur16, chol::kTaskSchur128,
+                            chol::kTaskAsm};
 
 }  // namespace
 
@@ -280,21 +281,27 @@ int chol_sym_get_tile_policy(const chol_sym* s, chol_tile_policy* p) {
   p->min_rows_tile64 = s->S.policy.min_rows_tile64;
   p->min_rows_tile32 = s->S.policy.min_rows_tile32;
   p->min_level_tiles64 = s->S.policy.min_level_tiles64;
+  p->min_rows_tile128 = s->S.policy.min_rows_tile128;
+  p->min_level_tiles128 = s->S.policy.min_level_tiles128;
   return CHOL_OK;
 }
 
 int chol_sym_set_tile_policy(chol_sym* s, const chol_tile_policy* p) {
-  if (!s || !p || p->min_rows_tile64 < 1 || p->min_rows_tile32 < 1 || p->min_level_tiles64 < 0)
+  if (!s || !p || p->min_rows_tile64 < 1 || p->min_rows_tile32 < 1 || p->min_level_tiles64 < 0 ||
+      p->min_rows_tile128 < 1 || p->min_level_tiles128 < 0)
     return CHOL_E_INVALID;
   chol::TilePolicy tp;
   tp.min_rows_tile64 = p->min_rows_tile64;
   tp.min_rows_tile32 = p->min_rows_tile32;
   tp.min_level_tiles64 = p->min_level_tiles64;
+  tp.min_rows_tile128 = p->min_rows_tile128;
+  tp.min_level_tiles128 = p->min_level_tiles128;
   chol::build_schur_tasks(&s->S, tp);
   if (!s->ctx) return CHOL_OK;
   chol_ctx* c = s->ctx;
   if (cudaSetDevice(c->opts.device) != cudaSuccess) return CHOL_E_NODEVICE;
-  for (int k = chol::kTaskSchur64; k <= chol::kTaskSchur16; k++) {
+  for (int cls = 0; cls < chol::kNumTileClasses; cls++) {
+    const int k = chol::schur_kind(cls);
     dev_free(c, s->dev.tasks[k]);
     s->dev.tasks[k] = nullptr;
     const size_t bytes = s->S.tasks[k].size() * sizeof(int32_t);
@@ -347,16 +354,19 @@ int chol_autotune(chol_ctx* c, chol_num* num, int reps, chol_tile_policy* best, 
   chol_sym_get_tile_policy(num->sym, &cur);
   double cur_ms = 0.0;
   int rc = time_policy(c, num, cur, reps, &cur_ms);
-  // coordinate descent over the three thresholds
-  const int lt[] = {0, 152, 304, 608, 1216};
-  const int r64[] = {32, 48, 64, 96, 128};
-  const int r32[] = {1, 9, 17, 25, 33};
-  for (int pass = 0; pass < 3 && !rc; pass++) {
-    const int* vals = pass == 0 ? lt : (pass == 1 ? r64 : r32);
+  // coordinate descent over the five thresholds (1 << 30 rows: no 128-wide tiles)
+  static const int kCand[5][5] = {{0, 152, 304, 608, 1216},
+                                  {32, 48, 64, 96, 128},
+                                  {1, 9, 17, 25, 33},
+                                  {128, 192, 256, 512, 1 << 30},
+                                  {0, 152, 304, 608, 1216}};
+  for (int pass = 0; pass < 5 && !rc; pass++) {
+    const int* vals = kCand[pass];
     for (int q = 0; q < 5 && !rc; q++) {
       chol_tile_policy p = cur;
-      int* field = pass == 0 ? &p.min_level_tiles64
-                             : (pass == 1 ? &p.min_rows_tile64 : &p.min_rows_tile32);
+      int* fields[5] = {&p.min_level_tiles64, &p.min_rows_tile64, &p.min_rows_tile32,
+                        &p.min_rows_tile128, &p.min_level_tiles128};
+      int* field = fields[pass];
       if (*field == vals[q]) continue;
       *field = vals[q];
       double ms = 0.0;

@@ -16,9 +16,12 @@ constexpr int kSolveRows = 128;  // off-diagonal rows per solve task
 constexpr int kMaxWidth = 128;   // hard limit on the width cap W (diagonal block in smem)
 
 // Schur tile classes: the update U = L21 L21^T of a supernode is cut into lower-triangular
-// T x T tiles, T in {64, 32, 16}.
-enum SchurClass { kTile64 = 0, kTile32 = 1, kTile16 = 2, kNumTileClasses = 3 };
-inline int tile_of_class(int c) { return c == kTile64 ? 64 : (c == kTile32 ? 32 : 16); }
+// T x T tiles, T in {128, 64, 32, 16}.  128-tiles run on tcgen05 tensor cores (TF32) in
+// the mixed-precision factor and as four 64-sub-tiles in FP64.
+enum SchurClass { kTile64 = 0, kTile32 = 1, kTile16 = 2, kTile128 = 3, kNumTileClasses = 4 };
+inline int tile_of_class(int c) {
+  return c == kTile128 ? 128 : (c == kTile64 ? 64 : (c == kTile32 ? 32 : 16));
+}
 
 // Task kinds of the per-level schedule.  Every task is an int4 {s, a, b, c}.
 enum TaskKind {
@@ -30,8 +33,10 @@ enum TaskKind {
   kTaskFwd = 5,     // {s, r0, -, -}: forward-solve block
   kTaskBwd = 6,     // {s, r0, -, -}: backward-solve partial block
   kTaskAsm = 7,     // {t, cb, first, end}: owner assembly group (see Sym::asm_src)
-  kNumTaskKinds = 8
+  kTaskSchur128 = 8,  // {s, i0, k0, 128}: 128 x 128 tile of U_s
+  kNumTaskKinds = 9
 };
+inline int schur_kind(int cls) { return cls == kTile128 ? kTaskSchur128 : kTaskSchur64 + cls; }
 
 // Device descriptor of one supernode (absolute device pointers: descriptors of several
 // matrices can be concatenated into one batch).
@@ -52,15 +57,20 @@ struct alignas(16) MatDev {
   unsigned long long* err;        // err[0]: smallest failing column + 1 (all ones = none),
                                   // kept by atomicMin;
                                   // err[1]: relative-map misses (internal check, 0 expected)
+                                  // err[2]: FP64 pivot redos of the mixed factor
+                                  // err[3]: tensor-core waits that gave up (0 expected)
 };
 
-// Which Schur tile size a supernode gets (autotuned per matrix family): 64x64 tiles when it
-// has at least min_rows_tile64 off-diagonal rows and its level holds at least
-// min_level_tiles64 such tiles, else 32x32 from min_rows_tile32 rows, else 16x16.
+// Which Schur tile size a supernode gets (autotuned per matrix family): 128x128 tiles when
+// it has at least min_rows_tile128 off-diagonal rows and its level holds at least
+// min_level_tiles128 such tiles, else 64x64 under the same rule with the 64 thresholds, else
+// 32x32 from min_rows_tile32 rows, else 16x16.
 struct TilePolicy {
   int min_rows_tile64 = 64;
   int min_rows_tile32 = 17;
   int min_level_tiles64 = 2 * 152;
+  int min_rows_tile128 = 128;
+  int min_level_tiles128 = 2 * 152;
 };
 
 // Host-side symbolic analysis result.

@@ -1,0 +1,132 @@
+// device_common.cuh -- device helpers shared by the factorization kernels: the relative
+// row lookup, error recording, and the epilogue that applies a finished Schur tile.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "chol_internal.h"
+
+namespace chol {
+
+__device__ __forceinline__ int lower_bound_dev(const int32_t* a, int n, int key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void record_error(const MatDev& md, int col) {
+  atomicMin(md.err, (unsigned long long)col + 1ull);
+}
+
+// Position of `key` in the sorted row list of a target supernode, or -1 (and a count in
+// err[1]) if it is missing: the elimination-tree property guarantees it is present, so a
+// miss is an internal inconsistency and the write is skipped rather than misdirected.
+__device__ __forceinline__ int relative_row(const MatDev& md, const int32_t* rows, int m,
+                                            int key) {
+  const int p = lower_bound_dev(rows, m, key);
+  if (p >= m || rows[p] != key) {
+    atomicAdd(md.err + 1, 1ull);
+    return -1;
+  }
+  return p;
+}
+
+// Applies a finished T x T tile of U_s (in shared memory, Cs[kk * (TILE + 1) + ii], rows
+// i0 + ii and columns k0 + kk of the off-diagonal part of s): each entry U(i, k), i >= k,
+// is subtracted from the target panel t owning column rows[k] -- column rows[k] - col0(t),
+// row position of rows[i] inside t's row list (the relative map, found by binary search in
+// t's sorted rows once per tile row and target).
+//   OWNER == false: atomicAdd into the panel.
+//   OWNER == true : the tile is written to the level staging buffer (U_s column-major,
+//                   ld u) and k_assemble_owner applies it later in a fixed order.
+template <typename T, int TILE, int THREADS, bool OWNER>
+__device__ __forceinline__ void schur_tile_epilogue(const T* Cs, const SnDev& d, int i0, int k0,
+                                                    const SnDev* __restrict__ sns,
+                                                    const MatDev* __restrict__ mats,
+                                                    T* __restrict__ stage) {
+  constexpr int RB = THREADS >= TILE ? THREADS / TILE : 1;  // runs resolved at a time
+  constexpr int LANES = THREADS < 32 ? THREADS : 32;
+  __shared__ int tcol[TILE];                 // target supernode of every tile column
+  __shared__ int run_start[TILE + 1];
+  __shared__ int run_t[TILE];
+  __shared__ int nruns;
+  __shared__ int relpos[RB][TILE];
+  const int tid = threadIdx.x;
+  const int n = d.n, u = d.m - d.n;
+  const int32_t* rows = d.rows + n;  // off-diagonal rows of s
+  const int ilim = min(TILE, u - i0), klim = min(TILE, u - k0);
+  if (OWNER) {
+    T* U = stage + d.ustage;
+    for (int idx = tid; idx < klim * TILE; idx += THREADS) {
+      const int kk = idx / TILE, ii = idx - kk * TILE;
+      if (ii < ilim && i0 + ii >= k0 + kk)
+        U[(int64_t)(k0 + kk) * u + i0 + ii] = Cs[kk * (TILE + 1) + ii];
+    }
+    return;
+  }
+  const MatDev md = mats[d.mat];
+  // targets of the tile columns, all at once
+  for (int kk = tid; kk < klim; kk += THREADS) tcol[kk] = md.col2sn[rows[k0 + kk]];
+  __syncthreads();
+  // runs of columns with the same target, found with warp ballots by the first warp
+  if (tid < LANES) {
+    const unsigned mask = LANES == 32 ? 0xffffffffu : ((1u << LANES) - 1u);
+    int nr = 0;
+    for (int base = 0; base < klim; base += LANES) {
+      const int kk = base + tid;
+      const bool start = kk < klim && (kk == 0 || tcol[kk] != tcol[kk - 1]);
+      const unsigned b = __ballot_sync(mask, start);
+      if (start) {
+        const int q = nr + __popc(b & ((1u << tid) - 1u));
+        run_start[q] = kk;
+        run_t[q] = tcol[kk];
+      }
+      nr += __popc(b);
+    }
+    if (tid == 0) {
+      run_start[nr] = klim;
+      nruns = nr;
+    }
+  }
+  __syncthreads();
+  for (int r0 = 0; r0 < nruns; r0 += RB) {
+    // relative map of the tile rows inside each target's rows (rows at or below the run's
+    // first column row are all present in the target, by the elimination-tree property)
+    for (int idx = tid; idx < RB * TILE; idx += THREADS) {
+      const int rr = idx / TILE, ii = idx - rr * TILE;
+      const int r = r0 + rr;
+      if (r < nruns && ii < ilim) {
+        const int gi = i0 + ii;
+        int p = -1;
+        if (gi >= k0 + run_start[r]) {
+          const SnDev& td = sns[md.sn_base + run_t[r]];
+          const int key = rows[gi];
+          // rows inside the target's own columns sit at key - col0
+          p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
+        }
+        relpos[rr][ii] = p;
+      }
+    }
+    __syncthreads();
+    for (int rr = 0; rr < RB && r0 + rr < nruns; rr++) {
+      const int r = r0 + rr;
+      const SnDev& td = sns[md.sn_base + run_t[r]];
+      T* Lt = reinterpret_cast<T*>(td.L);
+      const int kb = run_start[r], w = run_start[r + 1] - kb;
+      for (int idx = tid; idx < w * TILE; idx += THREADS) {
+        const int kk = kb + idx / TILE, ii = idx % TILE;
+        const int p = relpos[rr][ii];
+        if (ii < ilim && i0 + ii >= k0 + kk && p >= 0) {
+          const int c = rows[k0 + kk] - td.col0;
+          atomicAdd(&Lt[(int64_t)c * td.m + p], -Cs[kk * (TILE + 1) + ii]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace chol

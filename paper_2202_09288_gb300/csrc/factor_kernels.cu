@@ -19,34 +19,9 @@
 #include "chol_internal.h"
 #include "kernels.h"
 #include "launch_util.h"
+#include "device_common.cuh"
 
 namespace chol {
-
-__device__ __forceinline__ int lower_bound_dev(const int32_t* a, int n, int key) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (a[mid] < key) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ void record_error(const MatDev& md, int col) {
-  atomicMin(md.err, (unsigned long long)col + 1ull);
-}
-
-// Position of `key` in the sorted row list of a target supernode, or -1 (and a count in
-// err[1]) if it is missing: the elimination-tree property guarantees it is present, so a
-// miss is an internal inconsistency and the write is skipped rather than misdirected.
-__device__ __forceinline__ int relative_row(const MatDev& md, const int32_t* rows, int m,
-                                            int key) {
-  const int p = lower_bound_dev(rows, m, key);
-  if (p >= m || rows[p] != key) {
-    atomicAdd(md.err + 1, 1ull);
-    return -1;
-  }
-  return p;
-}
 
 // ---- assembly of A into the zeroed panels ------------------------------------------------
 template <typename T>
@@ -158,101 +133,6 @@ __global__ void __launch_bounds__(kTrsmRows) k_trsm(const int4* __restrict__ tas
   }
 }
 
-// Applies a finished T x T tile of U_s (in shared memory, Cs[kk * (TILE + 1) + ii], rows
-// i0 + ii and columns k0 + kk of the off-diagonal part of s): each entry U(i, k), i >= k,
-// is subtracted from the target panel t owning column rows[k] -- column rows[k] - col0(t),
-// row position of rows[i] inside t's row list (the relative map, found by binary search in
-// t's sorted rows once per tile row and target).
-//   OWNER == false: atomicAdd into the panel.
-//   OWNER == true : the tile is written to the level staging buffer (U_s column-major,
-//                   ld u) and k_assemble_owner applies it later in a fixed order.
-template <typename T, int TILE, int THREADS, bool OWNER>
-__device__ __forceinline__ void schur_tile_epilogue(const T* Cs, const SnDev& d, int i0, int k0,
-                                                    const SnDev* __restrict__ sns,
-                                                    const MatDev* __restrict__ mats,
-                                                    T* __restrict__ stage) {
-  constexpr int RB = THREADS >= TILE ? THREADS / TILE : 1;  // runs resolved at a time
-  constexpr int LANES = THREADS < 32 ? THREADS : 32;
-  __shared__ int tcol[TILE];                 // target supernode of every tile column
-  __shared__ int run_start[TILE + 1];
-  __shared__ int run_t[TILE];
-  __shared__ int nruns;
-  __shared__ int relpos[RB][TILE];
-  const int tid = threadIdx.x;
-  const int n = d.n, u = d.m - d.n;
-  const int32_t* rows = d.rows + n;  // off-diagonal rows of s
-  const int ilim = min(TILE, u - i0), klim = min(TILE, u - k0);
-  if (OWNER) {
-    T* U = stage + d.ustage;
-    for (int idx = tid; idx < klim * TILE; idx += THREADS) {
-      const int kk = idx / TILE, ii = idx - kk * TILE;
-      if (ii < ilim && i0 + ii >= k0 + kk)
-        U[(int64_t)(k0 + kk) * u + i0 + ii] = Cs[kk * (TILE + 1) + ii];
-    }
-    return;
-  }
-  const MatDev md = mats[d.mat];
-  // targets of the tile columns, all at once
-  for (int kk = tid; kk < klim; kk += THREADS) tcol[kk] = md.col2sn[rows[k0 + kk]];
-  __syncthreads();
-  // runs of columns with the same target, found with warp ballots by the first warp
-  if (tid < LANES) {
-    const unsigned mask = LANES == 32 ? 0xffffffffu : ((1u << LANES) - 1u);
-    int nr = 0;
-    for (int base = 0; base < klim; base += LANES) {
-      const int kk = base + tid;
-      const bool start = kk < klim && (kk == 0 || tcol[kk] != tcol[kk - 1]);
-      const unsigned b = __ballot_sync(mask, start);
-      if (start) {
-        const int q = nr + __popc(b & ((1u << tid) - 1u));
-        run_start[q] = kk;
-        run_t[q] = tcol[kk];
-      }
-      nr += __popc(b);
-    }
-    if (tid == 0) {
-      run_start[nr] = klim;
-      nruns = nr;
-    }
-  }
-  __syncthreads();
-  for (int r0 = 0; r0 < nruns; r0 += RB) {
-    // relative map of the tile rows inside each target's rows (rows at or below the run's
-    // first column row are all present in the target, by the elimination-tree property)
-    for (int idx = tid; idx < RB * TILE; idx += THREADS) {
-      const int rr = idx / TILE, ii = idx - rr * TILE;
-      const int r = r0 + rr;
-      if (r < nruns && ii < ilim) {
-        const int gi = i0 + ii;
-        int p = -1;
-        if (gi >= k0 + run_start[r]) {
-          const SnDev& td = sns[md.sn_base + run_t[r]];
-          const int key = rows[gi];
-          // rows inside the target's own columns sit at key - col0
-          p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
-        }
-        relpos[rr][ii] = p;
-      }
-    }
-    __syncthreads();
-    for (int rr = 0; rr < RB && r0 + rr < nruns; rr++) {
-      const int r = r0 + rr;
-      const SnDev& td = sns[md.sn_base + run_t[r]];
-      T* Lt = reinterpret_cast<T*>(td.L);
-      const int kb = run_start[r], w = run_start[r + 1] - kb;
-      for (int idx = tid; idx < w * TILE; idx += THREADS) {
-        const int kk = kb + idx / TILE, ii = idx % TILE;
-        const int p = relpos[rr][ii];
-        if (ii < ilim && i0 + ii >= k0 + kk && p >= 0) {
-          const int c = rows[k0 + kk] - td.col0;
-          atomicAdd(&Lt[(int64_t)c * td.m + p], -Cs[kk * (TILE + 1) + ii]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
 // ---- Schur update tiles ---------------------------------------------------------------------
 // Task {s, i0, k0}: the T x T tile of U_s = L21 L21^T at rows i0.., columns k0.. (offsets
 // into the off-diagonal rows of s), computed with FP64 m8n8k4 DMMA, then handed to
@@ -277,7 +157,7 @@ __device__ __forceinline__ void dmma_884(double (&c)[2], double a, double b) {
 template <int TILE, bool OWNER>
 __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
     k_schur_f64(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue, const SnDev* __restrict__ sns,
-                const MatDev* __restrict__ mats) {
+                const MatDev* __restrict__ mats, int vsplit) {
   using Cfg = SchurCfg<TILE>;
   constexpr int KC = Cfg::KC, LDS = Cfg::LDS, MB = Cfg::MB;
   __shared__ __align__(16) double sh[2 * KC * LDS > TILE * (TILE + 1) ? 2 * KC * LDS
@@ -286,11 +166,20 @@ __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
   double* Bs = sh + KC * LDS;   // [KC][LDS]: Bs[kk][jj] = L21[k0 + jj][kc + kk]
 
   __shared__ int s_next_task;
-  for (int tq = blockIdx.x; tq < ntasks;) {
-    const int4 tk = tasks[tq];
+  // with vsplit > 0 every task is 2^vsplit virtual tasks, one per sub-tile
+  const int nv = ntasks << vsplit;
+  for (int tq = blockIdx.x; tq < nv;) {
+    const int4 tk = tasks[tq >> vsplit];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
-    const int i0 = tk.y, k0 = tk.z;
+    // a task covers a (tk.w x tk.w) block of U_s; blocks larger than this kernel's tile
+    // are done as TILE x TILE sub-tiles, skipping those wholly above the diagonal
+    const int span = tk.w > TILE ? tk.w : TILE;
+    const int sub_lo = vsplit ? (tq & ((1 << vsplit) - 1)) : 0;
+    const int sub_hi = vsplit ? sub_lo + 1 : (span / TILE) * (span / TILE);
+    for (int sub = sub_lo; sub < sub_hi; sub++) {
+    const int i0 = tk.y + (sub / (span / TILE)) * TILE, k0 = tk.z + (sub % (span / TILE)) * TILE;
+    if (i0 + TILE - 1 < k0 || i0 >= u || k0 >= u) continue;
     const double* L = reinterpret_cast<const double*>(d.L);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp / Cfg::WARPS_N, wn = warp % Cfg::WARPS_N;
@@ -347,9 +236,11 @@ __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
     schur_tile_epilogue<double, TILE, Cfg::THREADS, OWNER>(
         Cs, d, i0, k0, sns, mats, static_cast<double*>(mats[d.mat].stage));
     __syncthreads();
+    }
+    __syncthreads();
     // a CTA's first task is its block index; only a grid smaller than the task list makes
     // CTAs take further tasks from this launch's work queue
-    if (gridDim.x >= ntasks) break;
+    if (gridDim.x >= nv) break;
     if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
     __syncthreads();
     tq = s_next_task;
@@ -383,7 +274,12 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
-    const int i0 = tk.y, k0 = tk.z;
+    // a task covers a (tk.w x tk.w) block of U_s; blocks larger than this kernel's tile
+    // are done as TILE x TILE sub-tiles, skipping those wholly above the diagonal
+    const int span = tk.w > TILE ? tk.w : TILE;
+    for (int sub = 0; sub < (span / TILE) * (span / TILE); sub++) {
+    const int i0 = tk.y + (sub / (span / TILE)) * TILE, k0 = tk.z + (sub % (span / TILE)) * TILE;
+    if (i0 + TILE - 1 < k0 || i0 >= u || k0 >= u) continue;
     const float* L = reinterpret_cast<const float*>(d.L);
     const int tid = threadIdx.x, tx = tid % S, ty = tid / S;
     float acc[4][4];
@@ -426,6 +322,8 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
     __syncthreads();
     schur_tile_epilogue<float, TILE, Cfg::THREADS, OWNER>(
         Cs, d, i0, k0, sns, mats, static_cast<float*>(mats[d.mat].stage));
+    __syncthreads();
+    }
     __syncthreads();
     // a CTA's first task is its block index; only a grid smaller than the task list makes
     // CTAs take further tasks from this launch's work queue
@@ -621,10 +519,10 @@ void launch_trsm(const int4* tasks, int ntasks, int* queue, const SnDev* sns, in
 
 template <int T, bool OWNER>
 static void schur_f64_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
-                        const MatDev* mats, cudaStream_t st) {
+                        const MatDev* mats, cudaStream_t st, int vsplit = 0) {
   constexpr int th = SchurCfg<T>::THREADS;
-  k_schur_f64<T, OWNER><<<persistent_grid(k_schur_f64<T, OWNER>, th, 0, ntasks), th, 0, st>>>(
-      tasks, ntasks, queue, sns, mats);
+  k_schur_f64<T, OWNER><<<persistent_grid(k_schur_f64<T, OWNER>, th, 0, ntasks << vsplit), th, 0,
+                         st>>>(tasks, ntasks, queue, sns, mats, vsplit);
 }
 
 template <int T, bool OWNER>
@@ -639,11 +537,14 @@ template <bool OWNER>
 static void schur_cls(int cls, bool f32, const int4* tasks, int ntasks, int* queue,
                       const SnDev* sns, const MatDev* mats, cudaStream_t st) {
   if (f32) {
-    if (cls == kTile64) schur_f32_t<64, OWNER>(tasks, ntasks, queue, sns, mats, st);
+    if (cls == kTile128) launch_schur_tc(tasks, ntasks, queue, sns, mats, OWNER, st);
+    else if (cls == kTile64) schur_f32_t<64, OWNER>(tasks, ntasks, queue, sns, mats, st);
     else if (cls == kTile32) schur_f32_t<32, OWNER>(tasks, ntasks, queue, sns, mats, st);
     else schur_f32_t<16, OWNER>(tasks, ntasks, queue, sns, mats, st);
   } else {
-    if (cls == kTile64) schur_f64_t<64, OWNER>(tasks, ntasks, queue, sns, mats, st);
+    // FP64 128-wide tasks run as four 64 x 64 virtual tasks of the DMMA kernel
+    if (cls == kTile128) schur_f64_t<64, OWNER>(tasks, ntasks, queue, sns, mats, st, 2);
+    else if (cls == kTile64) schur_f64_t<64, OWNER>(tasks, ntasks, queue, sns, mats, st);
     else if (cls == kTile32) schur_f64_t<32, OWNER>(tasks, ntasks, queue, sns, mats, st);
     else schur_f64_t<16, OWNER>(tasks, ntasks, queue, sns, mats, st);
   }

@@ -21,6 +21,10 @@ void launch_schur(int cls, const int4* tasks, int ntasks, int* queue, const SnDe
 void launch_assemble_owner(const int4* groups, int ngroups, int* queue, const int4* srcs,
                            const SnDev* sns, const MatDev* mats, bool f32, cudaStream_t st);
 int set_factor_kernel_attrs(int max_width);
+// 128 x 128 FP32 Schur tiles on the tcgen05 tensor cores (3xTF32), tc_kernels.cu.
+void launch_schur_tc(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
+                     const MatDev* mats, bool owner, cudaStream_t st);
+int set_tc_kernel_attrs();
 
 void launch_gather_perm(const double* B, int64_t ldb, const int32_t* perm, const double* scale,
                         int64_t n, int nrhs, double* y, cudaStream_t st);

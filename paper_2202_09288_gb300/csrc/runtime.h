@@ -20,13 +20,20 @@ using chol::Sym;
 enum ProfKindId {
   kProfAssemble, kProfPotrf, kProfTrsm, kProfSchur64, kProfSchur32, kProfSchur16,
   kProfAsmOwner, kProfFwd, kProfBwd, kProfPerm, kProfScale, kProfPotrfF32, kProfTrsmF32,
-  kProfSchur64F32, kProfSchur32F32, kProfSchur16F32, kProfRefine, kProfGraph, kNumProf
+  kProfSchur64F32, kProfSchur32F32, kProfSchur16F32, kProfRefine, kProfGraph, kProfSchur128,
+  kProfSchur128Tc, kNumProf
 };
 inline const char* const kProfNames[kNumProf] = {
     "assemble",    "potrf_f64",   "trsm_f64",    "schur64_f64",  "schur32_f64",
     "schur16_f64", "assemble_owner", "solve_fwd", "solve_bwd",   "solve_perm",
     "equilibrate", "potrf_f32",   "trsm_f32",    "schur64_f32",  "schur32_f32",
-    "schur16_f32", "refine",      "batch_graph"};
+    "schur16_f32", "refine",      "batch_graph", "schur128_f64", "schur128_tc"};
+
+// Tracing kind of a Schur tile class.
+inline int prof_schur_kind(int cls, bool f32) {
+  if (cls == chol::kTile128) return f32 ? kProfSchur128Tc : kProfSchur128;
+  return (f32 ? kProfSchur64F32 : kProfSchur64) + cls;
+}
 
 struct ProfPending {
   int kind;
@@ -136,9 +143,10 @@ int enqueue_factor(chol_num* f);
 // Releases the device memory of every batch of c (called by chol_destroy).
 void detach_batches(chol_ctx* c);
 TaskView sym_view(const chol_sym* sym);
-// Work-queue counters (one int per persistent launch): 6 per level for a factorization
-// (POTRF, TRSM, three Schur tile classes, owner assembly), 3 per level for a solve.
-inline size_t factor_counters(int32_t nlev) { return 6 * (size_t)nlev + 8; }
+// Work-queue counters (one int per persistent launch): 7 per level for a factorization
+// (POTRF, TRSM, four Schur tile classes, owner assembly), 3 per level for a solve.
+constexpr int kFactorCountersPerLevel = 3 + chol::kNumTileClasses;
+inline size_t factor_counters(int32_t nlev) { return kFactorCountersPerLevel * (size_t)nlev + 8; }
 inline size_t solve_counters(int32_t nlev) { return 3 * (size_t)nlev + 8; }
 int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
                    bool f32, bool owner, int* ctr);

@@ -104,20 +104,44 @@ def test_owner_batch_is_bitwise_equal_to_alone(torch):
     batch.close()
 
 
-@pytest.mark.parametrize("policy", [
-    {"min_rows_tile64": 1, "min_rows_tile32": 1, "min_level_tiles64": 0},        # all 64
-    {"min_rows_tile64": 10 ** 6, "min_rows_tile32": 10 ** 6, "min_level_tiles64": 0},  # all 16
-    {"min_rows_tile64": 10 ** 6, "min_rows_tile32": 1, "min_level_tiles64": 0},  # all 32
-])
-def test_tile_policies_are_correct(torch, policy):
-    ctx = P.Context()
+NO128 = {"min_rows_tile128": 1 << 30, "min_level_tiles128": 0}
+POLICIES = [
+    {"min_rows_tile64": 1, "min_rows_tile32": 1, "min_level_tiles64": 0, **NO128},  # all 64
+    {"min_rows_tile64": 10 ** 6, "min_rows_tile32": 10 ** 6, "min_level_tiles64": 0,
+     **NO128},                                                                    # all 16
+    {"min_rows_tile64": 10 ** 6, "min_rows_tile32": 1, "min_level_tiles64": 0, **NO128},  # 32
+    {"min_rows_tile64": 1, "min_rows_tile32": 1, "min_level_tiles64": 0,
+     "min_rows_tile128": 1, "min_level_tiles128": 0},                             # all 128
+]
+
+
+@pytest.mark.parametrize("policy", POLICIES)
+@pytest.mark.parametrize("assembly", [P.CHOL_ASSEMBLY_ATOMIC, P.CHOL_ASSEMBLY_OWNER])
+def test_tile_policies_are_correct(torch, policy, assembly):
+    ctx = P.Context(assembly=assembly)
     A, perm = problem("st27x3_11")
     ref = oracle.cholesky(A, perm)
     sym = P.Symbolic(ctx, A, perm)
     P.chol_sym_set_tile_policy(sym.handle, policy)
     assert P.chol_sym_get_tile_policy(sym.handle) == policy
+    P.chol_profile_enable(ctx.handle, True)
     num = P.Factor(ctx, sym, A.vals)
+    prof = P.chol_profile_read(ctx.handle)
+    if policy["min_rows_tile128"] == 1:  # 128-wide tasks run as 64 x 64 virtual tasks
+        assert prof["schur128_f64"]["launches"] > 0
+        assert prof["schur64_f64"]["launches"] == 0
     check_member(ctx, num, A, perm, ref)
+
+
+def test_tile_policy_rejects_bad_thresholds(torch):
+    ctx = P.Context()
+    A, perm = problem("lap2d_23")
+    sym = P.Symbolic(ctx, A, perm)
+    before = P.chol_sym_get_tile_policy(sym.handle)
+    for bad in [{"min_rows_tile64": 0}, {"min_rows_tile128": 0}, {"min_level_tiles128": -1}]:
+        with pytest.raises(P.CholError):
+            P.chol_sym_set_tile_policy(sym.handle, bad)
+    assert P.chol_sym_get_tile_policy(sym.handle) == before
 
 
 def test_autotuner(torch):
@@ -127,6 +151,7 @@ def test_autotuner(torch):
     sym = P.Symbolic(ctx, A, perm)
     num = P.Factor(ctx, sym, A.vals)
     policy, ms = num.autotune(reps=1)
-    assert ms > 0 and set(policy) == {"min_rows_tile64", "min_rows_tile32", "min_level_tiles64"}
+    assert ms > 0 and set(policy) == {"min_rows_tile64", "min_rows_tile32", "min_level_tiles64",
+                                      "min_rows_tile128", "min_level_tiles128"}
     assert P.chol_sym_get_tile_policy(sym.handle) == policy
     check_member(ctx, num, A, perm, ref)

@@ -139,3 +139,66 @@ def test_mixed_device_pointers_and_owner_determinism(torch):
     Xd2, _ = num.refine(Bd, tol=REFINE_TOL)
     torch.cuda.synchronize()
     assert np.array_equal(Xd2.cpu().numpy().T, X)
+
+
+TC_ON = {"min_rows_tile128": 1, "min_level_tiles128": 0}
+TC_OFF = {"min_rows_tile128": 1 << 30}
+
+
+def mixed_factor(A, perm, policy, assembly=P.CHOL_ASSEMBLY_ATOMIC):
+    ctx = P.Context(assembly=assembly)
+    sym = P.Symbolic(ctx, A, perm)
+    P.chol_sym_set_tile_policy(sym.handle, policy)
+    P.chol_profile_enable(ctx.handle, True)
+    num = P.Factor(ctx, sym, A.vals, precision=P.CHOL_MIXED)
+    prof = P.chol_profile_read(ctx.handle)
+    return ctx, sym, num, prof
+
+
+def dense_problem(n):
+    A = inputs.random_spd_dense(n, 4)
+    return A, np.arange(A.n, dtype=np.int32)
+
+
+@pytest.mark.parametrize("name", ["lap2d_64", "st27x3_11", "dense_300"])
+@pytest.mark.parametrize("assembly", [P.CHOL_ASSEMBLY_ATOMIC, P.CHOL_ASSEMBLY_OWNER])
+def test_tensor_core_tiles_match_oracle(torch, name, assembly):
+    """128 x 128 Schur tiles on the tcgen05 tensor cores (3xTF32, FP32 accumulation): the
+    FP32 factor of S A S matches the oracle's FP64 factor to FP32 rounding, the tasks ran
+    on the tensor-core kernel, and the ragged tails (tile rows past the update's end,
+    supernode widths that are not multiples of the MMA's K = 8) are covered."""
+    A, perm = dense_problem(300) if name == "dense_300" else inputs.workload(name)
+    ref = oracle.cholesky(scaled_matrix(A), perm)
+    ctx, sym, num, prof = mixed_factor(A, perm, TC_ON, assembly)
+    assert num.status()[0] == P.CHOL_OK
+    assert prof["schur128_tc"]["launches"] > 0
+    lp, li, lx = num.export()
+    assert np.array_equal(li, ref.li)
+    err = np.linalg.norm(lx - ref.lx) / np.linalg.norm(ref.lx)
+    assert err <= 2e-6, err
+    # and the tensor-core factor agrees with the SIMT FP32 factor to FP32 rounding
+    _, _, simt, prof_simt = mixed_factor(A, perm, TC_OFF, assembly)
+    assert prof_simt["schur128_tc"]["launches"] == 0
+    lx2 = simt.export()[2]
+    assert np.linalg.norm(lx - lx2) / np.linalg.norm(lx2) <= 2e-6
+
+
+@pytest.mark.parametrize("name", ["diff3d7_14", "st27x3_11"])
+def test_tensor_core_factor_refines_to_fp64(torch, name):
+    A, perm = inputs.workload(name)
+    ctx, sym, num, prof = mixed_factor(A, perm, TC_ON)
+    assert prof["schur128_tc"]["launches"] > 0
+    B = np.asfortranarray(A.to_scipy_full() @ inputs.rhs_block(12, A.n, 4))
+    X, info = num.refine(B, tol=REFINE_TOL)
+    assert not info["fell_back"]
+    assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, B, X) <= REFINE_TOL
+
+
+def test_tensor_core_owner_mode_is_bitwise_reproducible(torch):
+    A, perm = inputs.workload("st27x3_11")
+    _, _, a, _ = mixed_factor(A, perm, TC_ON, P.CHOL_ASSEMBLY_OWNER)
+    _, _, b, _ = mixed_factor(A, perm, TC_ON, P.CHOL_ASSEMBLY_OWNER)
+    lx = a.export()[2]
+    assert np.array_equal(lx, b.export()[2])
+    a.refactor(A.vals)
+    assert np.array_equal(lx, a.export()[2])
