@@ -80,6 +80,12 @@ typedef struct chol_opts {
   size_t hbm_budget;  /* bytes of device memory the context may hold; 0 = no limit */
   double pivot_tau;   /* CHOL_MIXED: a pivot below pivot_tau * a_jj redoes the supernode's
                          diagonal block in FP64; 0 = default 1e-5 */
+  double relax;       /* relaxed amalgamation (Sec. 2): a fundamental supernode joins the
+                         one before it when that one's last column is its child and the
+                         merged panel stays mostly nonzero -- explicit zeros at most 1/2 of
+                         it for merged widths <= 16, 1/5 for widths <= 64, else `relax`.
+                         0 = default 0.05; negative = fundamental supernodes only.  The
+                         factor's pattern, export and flop count stay those of the exact L */
 } chol_opts;
 
 typedef struct chol_sym_stats {
@@ -93,9 +99,13 @@ typedef struct chol_sym_stats {
   double flops;       /* sum_j c_j^2, c_j = entries of column j of L */
   int64_t max_width;  /* widest supernode */
   int64_t max_rows;   /* most rows in a supernode */
+  double flops_panel; /* sum of c^2 over the columns of the (padded) panels: the operations
+                         the factorization performs, >= flops under relaxed amalgamation */
+  int64_t nfundamental; /* fundamental supernodes (before amalgamation and the width cap) */
 } chol_sym_stats;
 
-/* Fills *opts with the defaults (device 0, own stream, W = 64, atomic assembly). */
+/* Fills *opts with the defaults (device 0, own stream, W = 64, atomic assembly,
+ * pivot_tau 1e-5, relax 0.05). */
 void chol_default_opts(chol_opts* opts);
 
 /* Library version as major*10000 + minor*100 + patch. */
@@ -128,6 +138,11 @@ int chol_sym_info(const chol_sym* sym, chol_sym_stats* stats);
  * nsuper entries (0 for supernodes without children, else 1 + the children's maximum). */
 int chol_sym_export(const chol_sym* sym, int32_t* parent, int64_t* colcount,
                     int32_t* sn_start, int32_t* sn_level);
+/* Copies the row lists of the supernode panels: supernode s holds rows[rowptr[s] ..
+ * rowptr[s+1]) in ascending order, its own columns first (rowptr: nsuper+1 entries).  Under
+ * relaxed amalgamation a column's rows in L are a subset of its panel's rows from its own
+ * position on; otherwise they are equal. */
+int chol_sym_rows(const chol_sym* sym, int64_t* rowptr, int32_t* rows);
 void chol_free_sym(chol_sym* sym);
 
 /* Numeric factorization of B = P^T A P (Sec. 3, Listing 1, reorganized per level).

@@ -34,13 +34,15 @@ class CholError(RuntimeError):
 
 class chol_opts(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("width_cap", C.c_int),
-                ("assembly", C.c_int), ("hbm_budget", C.c_size_t), ("pivot_tau", C.c_double)]
+                ("assembly", C.c_int), ("hbm_budget", C.c_size_t), ("pivot_tau", C.c_double),
+                ("relax", C.c_double)]
 
 
 class chol_sym_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz_a", C.c_int64), ("nnz_l", C.c_int64),
                 ("l_storage", C.c_int64), ("nsuper", C.c_int64), ("nlevels", C.c_int64),
-                ("flops", C.c_double), ("max_width", C.c_int64), ("max_rows", C.c_int64)]
+                ("flops", C.c_double), ("max_width", C.c_int64), ("max_rows", C.c_int64),
+                ("flops_panel", C.c_double), ("nfundamental", C.c_int64)]
 
 
 class chol_refine_info(C.Structure):
@@ -89,6 +91,7 @@ EXPORTS = {
     "chol_analyze": (_I, [C.POINTER(chol_opts), _I64, _P, _P, _P, C.POINTER(_P)]),
     "chol_sym_info": (_I, [_P, C.POINTER(chol_sym_stats)]),
     "chol_sym_export": (_I, [_P, _P, _P, _P, _P]),
+    "chol_sym_rows": (_I, [_P, _P, _P]),
     "chol_free_sym": (None, [_P]),
     "chol_factorize": (_I, [_P, _P, _P, _I, _I, C.POINTER(_P)]),
     "chol_refactorize": (_I, [_P, _P, _P, _I]),
@@ -204,6 +207,16 @@ def chol_sym_export(sym) -> dict:
     _check(lib().chol_sym_export(sym, parent.ctypes.data, cc.ctypes.data, start.ctypes.data,
                                  level.ctypes.data), "chol_sym_export")
     return {"parent": parent, "colcount": cc, "sn_start": start, "sn_level": level}
+
+
+def chol_sym_rows(sym) -> tuple:
+    """(rowptr, rows): the row list of every supernode panel."""
+    ns = chol_sym_info(sym)["nsuper"]
+    rowptr = np.zeros(ns + 1, np.int64)
+    _check(lib().chol_sym_rows(sym, rowptr.ctypes.data, None), "chol_sym_rows")
+    rows = np.zeros(int(rowptr[-1]), np.int32)
+    _check(lib().chol_sym_rows(sym, None, rows.ctypes.data), "chol_sym_rows")
+    return rowptr, rows
 
 
 def chol_free_sym(sym) -> None:
@@ -374,17 +387,20 @@ def chol_profile_reset(ctx) -> None:
 
 # ---- small object wrappers used by the tests and the bench -------------------------------
 def make_opts(device: int = 0, width_cap: int = 64, assembly: int = CHOL_ASSEMBLY_ATOMIC,
-              stream: int | None = None, hbm_budget: int = 0) -> chol_opts:
+              stream: int | None = None, hbm_budget: int = 0, relax: float = 0.0) -> chol_opts:
+    """relax: 0 = the library default, < 0 = fundamental supernodes only."""
     o = chol_default_opts()
     o.device, o.width_cap, o.assembly, o.hbm_budget = device, width_cap, assembly, hbm_budget
     o.stream = stream
+    if relax:
+        o.relax = relax
     return o
 
 
 class Context:
     def __init__(self, device: int = 0, width_cap: int = 64, assembly: int = CHOL_ASSEMBLY_ATOMIC,
-                 stream: int | None = None, hbm_budget: int = 0):
-        self.opts = make_opts(device, width_cap, assembly, stream, hbm_budget)
+                 stream: int | None = None, hbm_budget: int = 0, relax: float = 0.0):
+        self.opts = make_opts(device, width_cap, assembly, stream, hbm_budget, relax)
         self.handle = chol_create(self.opts)
 
     def close(self):

@@ -41,7 +41,7 @@ void push4(std::vector<int32_t>& v, int32_t a, int32_t b, int32_t c, int32_t d) 
 }  // namespace
 
 int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32_t* perm,
-            int width_cap, Sym* S) {
+            int width_cap, double relax, Sym* S) {
   if (n < 0 || n >= (int64_t(1) << 31) || !colptr || (n > 0 && (!rowind || !perm)))
     return CHOL_E_INVALID;
   if (width_cap <= 0) width_cap = 64;
@@ -168,11 +168,47 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
   }
   const int64_t nf = (int64_t)fstart.size();
   fstart.push_back((int32_t)n);
-  std::vector<int32_t> f_of(n);
-  for (int64_t f = 0; f < nf; f++)
-    for (int32_t j = fstart[f]; j < fstart[f + 1]; j++) f_of[j] = (int32_t)f;
+  S->n_fundamental = nf;
 
-  // ---- row structures of the fundamental supernodes -----------------------------------
+  // ---- relaxed amalgamation (Sec. 2: padding that buys wider dense blocks) ---------------
+  // A supernode absorbs the next fundamental supernode f when f holds the parent of its last
+  // column (the columns stay contiguous, the ordering is unchanged) and the merged panel
+  // keeps few explicit zeros: at most 1/2 of its lower trapezoid for merged widths up to 16
+  // columns, 1/5 up to 64, else `relax`.  The merged panel's rows are its own columns
+  // followed by the rows below f; every absorbed column's rows lie among them, so it gains
+  // (n + m_f - m) zero rows, n and m being the width and rows before the merge.
+  std::vector<int32_t> rstart;  // relaxed supernode starts
+  std::vector<int64_t> rm;      // relaxed supernode rows
+  double zopen = 0.0;            // explicit zeros of the supernode being grown
+  for (int64_t f = 0; f < nf; f++) {
+    const int64_t wf = fstart[f + 1] - fstart[f], mf = S->colcount[fstart[f]];
+    bool merge = false;
+    if (f > 0 && relax > 0 && S->parent[fstart[f] - 1] == fstart[f]) {
+      const int64_t cn = fstart[f] - rstart.back(), cm = rm.back();
+      const double nn = (double)(cn + wf), mm = (double)(cn + mf);
+      const double z = zopen + (double)cn * (double)(cn + mf - cm);
+      const double zf = z / (nn * mm - nn * (nn - 1.0) / 2.0);
+      merge = (nn <= 16 && zf <= 0.5) || (nn <= 64 && zf <= 0.2) || zf <= relax;
+      if (merge) {
+        zopen = z;
+        rm.back() = cn + mf;
+      }
+    }
+    if (!merge) {
+      rstart.push_back(fstart[f]);
+      rm.push_back(mf);
+      zopen = 0.0;
+    }
+  }
+  const int64_t nr = (int64_t)rstart.size();
+  rstart.push_back((int32_t)n);
+  std::vector<int32_t> r_of(n);
+  for (int64_t r = 0; r < nr; r++)
+    for (int32_t j = rstart[r]; j < rstart[r + 1]; j++) r_of[j] = (int32_t)r;
+
+  // ---- row structures of the relaxed supernodes ----------------------------------------
+  // rows(R) = columns of R, then the rows below R's last column of B's columns in R and of
+  // the row lists of R's children (Sec. 2, elimination tree)
   // B's lower entries by column: column c holds rows r > c with B_rc != 0 (transpose of rc)
   std::vector<int64_t> cp(n + 1, 0);
   for (int64_t p = 0; p < rp[n]; p++) cp[rc[p] + 1]++;
@@ -183,15 +219,15 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
     for (int64_t i = 0; i < n; i++)
       for (int64_t p = rp[i]; p < rp[i + 1]; p++) cr[fill[rc[p]]++] = (int32_t)i;
   }
-  std::vector<int64_t> frp(nf + 1, 0);
+  std::vector<int64_t> frp(nr + 1, 0);
   std::vector<int32_t> frows;
   frows.reserve((size_t)std::min<int64_t>(S->nnz_l, (int64_t)64 << 20));
-  std::vector<int32_t> fhead(nf, -1), fnext(nf, -1);
+  std::vector<int32_t> fhead(nr, -1), fnext(nr, -1);
   {
     std::vector<int32_t> mark(n, -1);
     std::vector<int32_t> tmp;
-    for (int64_t f = 0; f < nf; f++) {
-      const int32_t a = fstart[f], l = fstart[f + 1] - 1;
+    for (int64_t f = 0; f < nr; f++) {
+      const int32_t a = rstart[f], l = rstart[f + 1] - 1;
       tmp.clear();
       for (int32_t j = a; j <= l; j++) tmp.push_back(j);
       for (int32_t j = a; j <= l; j++)
@@ -205,23 +241,23 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
           if (i > l && mark[i] != f) { mark[i] = (int32_t)f; tmp.push_back(i); }
         }
       std::sort(tmp.begin() + (l - a + 1), tmp.end());
-      if ((int64_t)tmp.size() != S->colcount[a]) return CHOL_E_INVALID;  // inconsistent
+      if ((int64_t)tmp.size() != rm[f]) return CHOL_E_INVALID;  // inconsistent
       frows.insert(frows.end(), tmp.begin(), tmp.end());
       frp[f + 1] = (int64_t)frows.size();
       int32_t par = S->parent[l];
       if (par >= 0) {
-        int32_t pf = f_of[par];
+        int32_t pf = r_of[par];
         fnext[f] = fhead[pf];
         fhead[pf] = (int32_t)f;
       }
     }
   }
 
-  // ---- width cap: cut fundamental supernodes into chunks ------------------------------
+  // ---- width cap: cut relaxed supernodes into chunks ----------------------------------
   S->sn_start.clear();
   std::vector<int32_t> chunk_f;
-  for (int64_t f = 0; f < nf; f++)
-    for (int32_t j = fstart[f]; j < fstart[f + 1]; j += width_cap) {
+  for (int64_t f = 0; f < nr; f++)
+    for (int32_t j = rstart[f]; j < rstart[f + 1]; j += width_cap) {
       S->sn_start.push_back(j);
       chunk_f.push_back((int32_t)f);
     }
@@ -234,10 +270,11 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
   S->sn_valptr.assign(ns + 1, 0);
   S->rows.clear();
   S->max_width = S->max_rows = 0;
+  S->flops_panel = 0.0;
   for (int32_t s = 0; s < ns; s++) {
     const int32_t a = S->sn_start[s], b = S->sn_start[s + 1];
     const int32_t f = chunk_f[s];
-    const int64_t off = a - fstart[f];
+    const int64_t off = a - rstart[f];
     for (int32_t j = a; j < b; j++) S->col2sn[j] = s;
     const int64_t m = (frp[f + 1] - frp[f]) - off;
     S->sn_m[s] = (int32_t)m;
@@ -246,6 +283,8 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
     S->sn_valptr[s + 1] = S->sn_valptr[s] + m * (int64_t)(b - a);
     S->max_width = std::max<int64_t>(S->max_width, b - a);
     S->max_rows = std::max<int64_t>(S->max_rows, m);
+    // the operations the panels really take: sum of c^2 over the padded columns
+    for (int64_t k = 0; k < b - a; k++) S->flops_panel += (double)(m - k) * (double)(m - k);
   }
   S->l_storage = S->sn_valptr[ns];
   S->sn_parent.assign(ns, -1);

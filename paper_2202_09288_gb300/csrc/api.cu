@@ -721,6 +721,7 @@ void chol_default_opts(chol_opts* o) {
   o->width_cap = 64;
   o->assembly = CHOL_ASSEMBLY_ATOMIC;
   o->pivot_tau = 1e-5;
+  o->relax = 0.05;
 }
 
 int chol_create(const chol_opts* opts, chol_ctx** out) {
@@ -794,7 +795,8 @@ int chol_analyze(const chol_opts* opts, int64_t n, const int64_t* colptr,
   if (!s) return CHOL_E_OOM;
   int rc;
   try {
-    rc = chol::analyze(n, colptr, rowind, perm, opts ? opts->width_cap : 64, &s->S);
+    const double relax = !opts || opts->relax == 0.0 ? 0.05 : opts->relax;
+    rc = chol::analyze(n, colptr, rowind, perm, opts ? opts->width_cap : 64, relax, &s->S);
   } catch (const std::bad_alloc&) {
     rc = CHOL_E_OOM;
   } catch (...) {
@@ -817,6 +819,8 @@ int chol_sym_info(const chol_sym* s, chol_sym_stats* st) {
   st->flops = S.flops;
   st->max_width = S.max_width;
   st->max_rows = S.max_rows;
+  st->flops_panel = S.flops_panel;
+  st->nfundamental = S.n_fundamental;
   return CHOL_OK;
 }
 
@@ -828,6 +832,14 @@ int chol_sym_export(const chol_sym* s, int32_t* parent, int64_t* colcount, int32
   if (colcount) std::copy(S.colcount.begin(), S.colcount.end(), colcount);
   if (sn_start) std::copy(S.sn_start.begin(), S.sn_start.end(), sn_start);
   if (sn_level) std::copy(S.sn_level.begin(), S.sn_level.end(), sn_level);
+  return CHOL_OK;
+}
+
+int chol_sym_rows(const chol_sym* s, int64_t* rowptr, int32_t* rows) {
+  if (!s) return CHOL_E_INVALID;
+  const Sym& S = s->S;
+  if (rowptr) std::copy(S.sn_rowptr.begin(), S.sn_rowptr.end(), rowptr);
+  if (rows) std::copy(S.rows.begin(), S.rows.end(), rows);
   return CHOL_OK;
 }
 
@@ -906,21 +918,53 @@ int chol_factor_export(chol_ctx* c, const chol_num* f, int64_t* Lp, int32_t* Li,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
-  int64_t pos = 0;
-  if (Lp) Lp[0] = 0;
-  for (int32_t s = 0; s < S.ns; s++) {
-    const int32_t n = S.sn_start[s + 1] - S.sn_start[s], m = S.sn_m[s];
-    const int32_t* rows = S.rows.data() + S.sn_rowptr[s];
-    for (int32_t jj = 0; jj < n; jj++) {
-      for (int32_t r = jj; r < m; r++) {
-        if (Li) Li[pos] = rows[r];
-        if (Lx) {
-          const int64_t q = S.sn_valptr[s] + (int64_t)jj * m + r;
-          Lx[pos] = f32 ? (double)panels32[q] : panels[q];
-        }
-        pos++;
+  // The exact pattern of L, by row subtrees of B = P^T A P: row i of L holds the columns met
+  // walking up the elimination tree from every k < i with B_ik != 0 until i.  Panels of
+  // relaxed supernodes also hold explicit zeros outside this pattern; they are skipped.
+  const int64_t n = S.n;
+  std::vector<int64_t> next;
+  std::vector<int32_t> cursor, mark;
+  try {
+    next.resize(n);
+    cursor.resize(n);
+    mark.assign(n, -1);
+  } catch (...) {
+    return CHOL_E_OOM;
+  }
+  int64_t acc = 0;
+  for (int64_t j = 0; j < n; j++) {
+    next[j] = acc;
+    if (Lp) Lp[j] = acc;
+    acc += S.colcount[j];
+    cursor[j] = j - S.sn_start[S.col2sn[j]];  // the diagonal's row in its panel
+  }
+  if (Lp) Lp[n] = acc;
+  auto emit = [&](int32_t i, int32_t j) -> bool {
+    const int64_t q = next[j]++;
+    if (Li) Li[q] = i;
+    if (Lx) {
+      const int32_t s = S.col2sn[j], m = S.sn_m[s];
+      const int32_t* rows = S.rows.data() + S.sn_rowptr[s];
+      int32_t r = cursor[j];
+      while (r < m && rows[r] != i) r++;
+      if (r == m) return false;
+      cursor[j] = r;
+      const int64_t v = S.sn_valptr[s] + (int64_t)(j - S.sn_start[s]) * m + r;
+      Lx[q] = f32 ? (double)panels32[v] : panels[v];
+    }
+    return true;
+  };
+  for (int32_t i = 0; i < (int32_t)n; i++) {
+    mark[i] = i;
+    if (!emit(i, i)) return CHOL_E_INVALID;
+    const int32_t ai = S.perm[i];
+    for (int64_t p = S.csr_ptr[ai]; p < S.csr_ptr[ai + 1]; p++) {
+      const int32_t k = S.iperm[S.csr_col[p]];
+      if (k >= i) continue;
+      for (int32_t j = k; mark[j] != i; j = S.parent[j]) {
+        mark[j] = i;
+        if (!emit(i, j)) return CHOL_E_INVALID;  // panel rows miss an entry of L
       }
-      if (Lp) Lp[S.sn_start[s] + jj + 1] = pos;
     }
   }
   return CHOL_OK;

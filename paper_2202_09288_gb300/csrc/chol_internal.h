@@ -118,13 +118,17 @@ struct Sym {
   // Schur u(u+1)n per supernode; they add up to sum_j c_j^2) and panel bytes per level
   std::vector<double> lvl_flops[kNumTaskKinds];
   std::vector<double> lvl_panel_bytes;
-  double flops = 0.0;
+  double flops = 0.0;        // sum of c_j^2 over the exact factor
+  double flops_panel = 0.0;  // the same over the padded panels (relaxed amalgamation)
   int64_t nnz_l = 0, l_storage = 0, max_width = 0, max_rows = 0;
+  int64_t n_fundamental = 0;  // fundamental supernodes before amalgamation and the cap
 };
 
-// Host analysis (analyze.cpp).  Returns CHOL_OK or CHOL_E_INVALID.
+// Host analysis (analyze.cpp).  relax > 0 enables relaxed amalgamation with that largest
+// share of explicit zeros for wide merges; relax <= 0 keeps the fundamental supernodes.
+// Returns CHOL_OK or CHOL_E_INVALID.
 int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32_t* perm,
-            int width_cap, Sym* out);
+            int width_cap, double relax, Sym* out);
 // Builds the owner-assembly groups (kTaskAsm, asm_src) and the owner-ordered forward-solve
 // gather lists; only factors with owner-ordered assembly need them.
 void build_owner_lists(Sym* S);

@@ -12,7 +12,8 @@ CASES = ["lap2d_16", "lap2d_64", "lap3d_9", "st27x3_6", "diff3d7_10"]
 
 
 def both(A, perm, W):
-    sym = P.Symbolic(P.make_opts(width_cap=W), A, perm)
+    # the oracle's partition is the fundamental one: no relaxed amalgamation here
+    sym = P.Symbolic(P.make_opts(width_cap=W, relax=-1.0), A, perm)
     got = sym.export()
     bp, bi, bx = oracle.permute(A.n, A.colptr, A.rowind, A.vals, perm)
     parent, cc, lp, li = oracle.symbolic(A.n, bp, bi)
@@ -59,7 +60,7 @@ def test_fig1_tree_levels():
     a = np.eye(6) * 4.0
     for i, j in [(3, 0), (3, 1), (4, 2), (5, 3), (5, 4)]:
         a[i, j] = a[j, i] = -1.0
-    sym = P.Symbolic(None, inputs.from_dense(a), np.arange(6, dtype=np.int32))
+    sym = P.Symbolic(P.make_opts(relax=-1.0), inputs.from_dense(a), np.arange(6, dtype=np.int32))
     e = sym.export()
     assert list(e["sn_level"]) == [0, 0, 0, 1, 1, 2]
 
@@ -112,3 +113,79 @@ def test_create_without_gpu_fails_cleanly():
     with pytest.raises(P.CholError) as e:
         P.Context()
     assert e.value.status == P.CHOL_E_NODEVICE
+
+
+def check_panels_cover_l(sym, A, perm, exact):
+    """Every column's rows in L (the oracle's symbolic pattern) lie in its panel's rows from
+    the column's own position on; with fundamental supernodes they are equal."""
+    got = sym.export()
+    rowptr, rows = P.chol_sym_rows(sym.handle)
+    bp, bi, bx = oracle.permute(A.n, A.colptr, A.rowind, A.vals, perm)
+    parent, cc, lp, li = oracle.symbolic(A.n, bp, bi)
+    start = got["sn_start"]
+    for s in range(len(start) - 1):
+        r = rows[rowptr[s]:rowptr[s + 1]]
+        assert np.all(np.diff(r) > 0)
+        w = start[s + 1] - start[s]
+        assert np.array_equal(r[:w], np.arange(start[s], start[s + 1]))
+        for jj in range(w):
+            j = start[s] + jj
+            col = li[lp[j]:lp[j + 1]]
+            if exact:
+                assert np.array_equal(r[jj:], col)
+            else:
+                assert np.all(np.isin(col, r[jj:]))
+    return got, parent, cc
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("W", [64, 128, 5])
+def test_relaxed_amalgamation(name, W):
+    """Relaxed supernodes (Sec. 2: explicit zeros buy wider dense blocks): the panels
+    cover L, the etree and counts are untouched, the reported flops stay those of the
+    exact L, the explicit zeros stay within the merge rule's largest share (1/2), and the
+    level sets follow the definition over the relaxed tree (Fig. 1)."""
+    A, perm = inputs.workload(name)
+    sym = P.Symbolic(P.make_opts(width_cap=W), A, perm)
+    got, parent, cc = check_panels_cover_l(sym, A, perm, exact=False)
+    assert np.array_equal(got["parent"], parent) and np.array_equal(got["colcount"], cc)
+    info = sym.info
+    assert info["flops"] == float(np.sum(cc.astype(np.float64) ** 2))
+    assert info["nnz_l"] == int(cc.sum())
+    fund = P.Symbolic(P.make_opts(width_cap=W, relax=-1.0), A, perm).info
+    assert info["nfundamental"] == fund["nfundamental"]
+    assert info["nsuper"] <= fund["nsuper"]
+    assert info["flops_panel"] >= info["flops"]
+    assert fund["flops_panel"] == fund["flops"]
+    start = got["sn_start"]
+    wdt = np.diff(start).astype(np.int64)
+    m = cc[start[:-1]].astype(np.int64)  # rows of a panel = count of its first column...
+    rowptr, _ = P.chol_sym_rows(sym.handle)
+    m = np.diff(rowptr)                  # ...only without padding: take the panel's own
+    lower = int(np.sum(m * wdt - wdt * (wdt - 1) // 2))
+    assert info["l_storage"] >= lower >= info["nnz_l"]
+    assert lower - info["nnz_l"] <= 0.5 * lower
+    assert info["max_width"] <= W
+    # levels: 0 without children, else 1 + the children's largest
+    col2sn = np.repeat(np.arange(len(start) - 1), wdt)
+    lv = np.zeros(len(start) - 1, np.int64)
+    for s in range(len(start) - 1):
+        par = parent[start[s + 1] - 1]
+        if par >= 0:
+            t = col2sn[par]
+            lv[t] = max(lv[t], lv[s] + 1)
+    assert np.array_equal(got["sn_level"], lv)
+
+
+def test_relaxed_amalgamation_merges_narrow_supernodes():
+    A, perm = inputs.workload("diff3d7_10")
+    relaxed = P.Symbolic(P.make_opts(), A, perm).info
+    fund = P.Symbolic(P.make_opts(relax=-1.0), A, perm).info
+    assert relaxed["nsuper"] < fund["nsuper"] / 2
+    assert relaxed["flops_panel"] <= 1.5 * relaxed["flops"]  # small fronts: up to 1/2 zeros
+
+
+def test_fundamental_panels_equal_l():
+    A, perm = inputs.workload("lap3d_9")
+    sym = P.Symbolic(P.make_opts(relax=-1.0), A, perm)
+    check_panels_cover_l(sym, A, perm, exact=True)
