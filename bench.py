@@ -540,7 +540,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
         "data": "synthetic",
         "config": dict(workload_config(args), n=n, nnz_a=A.nnz_lower, nnz_l=sym.info["nnz_l"],
-                       flops_per_step=F, nsuper=sym.info["nsuper"],
+                       flops_per_step=F, flops_panel=sym.info["flops_panel"],
+                       nsuper=sym.info["nsuper"], nfundamental=sym.info["nfundamental"],
                        nlevels=sym.info["nlevels"],
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "factor_ms": fac_ms, "solve_ms": sol_ms,
