@@ -378,6 +378,11 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed: FP32 factor + FP64 iterative refinement to --tol")
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--policy", default="",
+                    help="Schur tile policy overrides as JSON, e.g. "
+                         "'{\"min_rows_tile128\": 1073741824}' (no 128-wide tiles)")
+    ap.add_argument("--relax", type=float, default=0.0,
+                    help="relaxed amalgamation zero share (0: library default, <0: off)")
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--mode", default="factor", choices=["factor", "batched", "serve"],
                     help="factor: one matrix per step (default); batched: plain per-level "
@@ -422,8 +427,11 @@ def main():
     torch.cuda.set_stream(stream)
     ctx = P.Context(device=local, width_cap=args.width,
                     assembly=P.CHOL_ASSEMBLY_OWNER if args.assembly == "owner"
-                    else P.CHOL_ASSEMBLY_ATOMIC, stream=stream.cuda_stream)
+                    else P.CHOL_ASSEMBLY_ATOMIC, stream=stream.cuda_stream,
+                    relax=args.relax)
     sym = P.Symbolic(ctx, A, perm)
+    if args.policy:
+        P.chol_sym_set_tile_policy(sym.handle, json.loads(args.policy))
     F = sym.info["flops"]
     vals_d = torch.from_numpy(A.vals).cuda()
     b_d = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()  # (k, n): column c = row c
@@ -543,6 +551,7 @@ def main():
                        flops_per_step=F, flops_panel=sym.info["flops_panel"],
                        nsuper=sym.info["nsuper"], nfundamental=sym.info["nfundamental"],
                        nlevels=sym.info["nlevels"],
+                       tile_policy=P.chol_sym_get_tile_policy(sym.handle),
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "factor_ms": fac_ms, "solve_ms": sol_ms,
         "factor_gflops": F / (fac_ms * 1e-3) / 1e9,

@@ -8,3 +8,35 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def fig1_tree():
+    """The Fig. 1 example (Sec. 3) from tests/golden/fig1_tree.txt: (edges, level sets),
+    supernode labels 1-based as printed."""
+    edges, levels = [], []
+    with open(os.path.join(GOLDEN, "fig1_tree.txt")) as f:
+        for line in f:
+            parts = line.split()
+            if not parts or parts[0].startswith("#"):
+                continue
+            if parts[0] == "edge":
+                edges.append((int(parts[1]), int(parts[2])))
+            elif parts[0] == "level":
+                levels.append(sorted(int(x) for x in parts[1:]))
+    return edges, levels
+
+
+def fig1_matrix():
+    """An SPD matrix whose elimination tree is the Fig. 1 tree (one column per
+    supernode): A_ij != 0 for every edge (child i, parent j), diagonally dominant."""
+    import numpy as np
+    from paper_2202_09288_gb300 import inputs
+    edges, _ = fig1_tree()
+    n = 1 + max(max(e) for e in edges)
+    a = np.eye(n - 1) * 4.0
+    for c, p in edges:
+        a[c - 1, p - 1] = a[p - 1, c - 1] = -1.0
+    return inputs.from_dense(a)

@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import paper_2202_09288_gb300 as P
+from conftest import fig1_matrix, fig1_tree
 from paper_2202_09288_gb300 import inputs
 
 CASES = ["lap2d_16", "lap2d_64", "lap3d_9", "st27x3_6", "diff3d7_10"]
@@ -57,12 +58,14 @@ def test_random_patterns_and_perms():
 
 
 def test_fig1_tree_levels():
-    a = np.eye(6) * 4.0
-    for i, j in [(3, 0), (3, 1), (4, 2), (5, 3), (5, 4)]:
-        a[i, j] = a[j, i] = -1.0
-    sym = P.Symbolic(P.make_opts(relax=-1.0), inputs.from_dense(a), np.arange(6, dtype=np.int32))
+    """Sec. 3, Fig. 1 (tests/golden/fig1_tree.txt): the library's level sets."""
+    edges, levels = fig1_tree()
+    A = fig1_matrix()
+    sym = P.Symbolic(P.make_opts(relax=-1.0), A, np.arange(A.n, dtype=np.int32))
     e = sym.export()
-    assert list(e["sn_level"]) == [0, 0, 0, 1, 1, 2]
+    assert sorted((j + 1, int(p) + 1) for j, p in enumerate(e["parent"]) if p >= 0) == sorted(edges)
+    lv = e["sn_level"]
+    assert [sorted(int(s) + 1 for s in np.nonzero(lv == l)[0]) for l in range(lv.max() + 1)] == levels
 
 
 def test_empty_and_one():

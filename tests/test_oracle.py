@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from conftest import fig1_matrix, fig1_tree
 from paper_2202_09288_gb300 import inputs
 
 
@@ -114,18 +115,15 @@ def test_symbolic_vs_graph_elimination(seed):
 
 
 def test_fig1_level_sets():
-    """Sec. 3, Fig. 1: supernodes 1,2 -> 4; 3 -> 5; 4,5 -> 6.  The best parallel
-    schedule is {1,2,3}, then {4,5}, then {6}."""
-    n = 6
-    a = np.eye(n) * 4.0
-    for i, j in [(3, 0), (3, 1), (4, 2), (5, 3), (5, 4)]:
-        a[i, j] = a[j, i] = -1.0
-    f = oracle.cholesky(inputs.from_dense(a))
-    assert list(f.parent) == [3, 3, 4, 5, 5, -1]
+    """Sec. 3, Fig. 1 (tests/golden/fig1_tree.txt): the oracle's elimination tree and level
+    sets of a matrix built on the printed tree equal the printed tree and schedule."""
+    edges, levels = fig1_tree()
+    f = oracle.cholesky(fig1_matrix())
+    assert sorted((j + 1, int(p) + 1) for j, p in enumerate(f.parent) if p >= 0) == sorted(edges)
     start, sp, lv = f.supernodes(64)
-    assert list(start) == [0, 1, 2, 3, 4, 5, 6]
+    assert list(start) == list(range(f.n + 1))  # no two of them form a supernode
     sets = [sorted(int(s) + 1 for s in np.nonzero(lv == l)[0]) for l in range(lv.max() + 1)]
-    assert sets == [[1, 2, 3], [4, 5], [6]]
+    assert sets == levels
 
 
 def test_dense_supernode_and_width_cap():
