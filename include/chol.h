@@ -86,7 +86,16 @@ typedef struct chol_opts {
                          it for merged widths <= 16, 1/5 for widths <= 64, else `relax`.
                          0 = default 0.05; negative = fundamental supernodes only.  The
                          factor's pattern, export and flop count stay those of the exact L */
+  int fp64_schur;     /* CHOL_FP64 factors: how the 128x128 Schur tiles are computed.
+                         CHOL_SCHUR_OZAKI (default): on the bf16 tensor cores (tcgen05) by
+                         splitting every L21 row into 8 exact 7-bit slices scaled by a power
+                         of two; slice products accumulate exactly, so the tile carries FP64
+                         accuracy (representation error < 2^-57 of the row maximum).  Needs
+                         W <= 64 (else DMMA).  CHOL_SCHUR_DMMA: FP64 mma.sync tiles. */
 } chol_opts;
+
+#define CHOL_SCHUR_OZAKI 0
+#define CHOL_SCHUR_DMMA 1
 
 typedef struct chol_sym_stats {
   int64_t n;          /* order of A */

@@ -23,6 +23,7 @@ CHOL_E_TIMEOUT, CHOL_E_NODEVICE, CHOL_E_STALL, CHOL_E_SCRATCH = -5, -6, -7, -8
 CHOL_HOST, CHOL_DEVICE = 0, 1
 CHOL_ASSEMBLY_ATOMIC, CHOL_ASSEMBLY_OWNER = 0, 1
 CHOL_FP64, CHOL_MIXED = 0, 1
+CHOL_SCHUR_OZAKI, CHOL_SCHUR_DMMA = 0, 1
 
 
 class CholError(RuntimeError):
@@ -35,7 +36,7 @@ class CholError(RuntimeError):
 class chol_opts(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("width_cap", C.c_int),
                 ("assembly", C.c_int), ("hbm_budget", C.c_size_t), ("pivot_tau", C.c_double),
-                ("relax", C.c_double)]
+                ("relax", C.c_double), ("fp64_schur", C.c_int)]
 
 
 class chol_sym_stats(C.Structure):
@@ -387,11 +388,13 @@ def chol_profile_reset(ctx) -> None:
 
 # ---- small object wrappers used by the tests and the bench -------------------------------
 def make_opts(device: int = 0, width_cap: int = 64, assembly: int = CHOL_ASSEMBLY_ATOMIC,
-              stream: int | None = None, hbm_budget: int = 0, relax: float = 0.0) -> chol_opts:
+              stream: int | None = None, hbm_budget: int = 0, relax: float = 0.0,
+              fp64_schur: int = CHOL_SCHUR_OZAKI) -> chol_opts:
     """relax: 0 = the library default, < 0 = fundamental supernodes only."""
     o = chol_default_opts()
     o.device, o.width_cap, o.assembly, o.hbm_budget = device, width_cap, assembly, hbm_budget
     o.stream = stream
+    o.fp64_schur = fp64_schur
     if relax:
         o.relax = relax
     return o
@@ -399,8 +402,9 @@ def make_opts(device: int = 0, width_cap: int = 64, assembly: int = CHOL_ASSEMBL
 
 class Context:
     def __init__(self, device: int = 0, width_cap: int = 64, assembly: int = CHOL_ASSEMBLY_ATOMIC,
-                 stream: int | None = None, hbm_budget: int = 0, relax: float = 0.0):
-        self.opts = make_opts(device, width_cap, assembly, stream, hbm_budget, relax)
+                 stream: int | None = None, hbm_budget: int = 0, relax: float = 0.0,
+                 fp64_schur: int = CHOL_SCHUR_OZAKI):
+        self.opts = make_opts(device, width_cap, assembly, stream, hbm_budget, relax, fp64_schur)
         self.handle = chol_create(self.opts)
 
     def close(self):

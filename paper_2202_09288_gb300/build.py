@@ -13,8 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libchol.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["analyze.cpp", "api.cu", "factor_kernels.cu", "tc_kernels.cu", "solve_kernels.cu",
-           "noalloc.cu", "refine_kernels.cu", "batch.cu", "serve.cu"]
+SOURCES = ["analyze.cpp", "api.cu", "factor_kernels.cu", "tc_kernels.cu", "oz_kernels.cu",
+           "solve_kernels.cu", "noalloc.cu", "refine_kernels.cu", "batch.cu", "serve.cu"]
 
 
 def nvcc() -> str:

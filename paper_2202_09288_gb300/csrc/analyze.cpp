@@ -452,12 +452,14 @@ void build_owner_lists(Sym* S) {
 
 void build_schur_tasks(Sym* S, const TilePolicy& policy) {
   S->policy = policy;
-  for (int cls = 0; cls < kNumTileClasses; cls++) {
-    const int k = schur_kind(cls);
+  const int kinds[] = {kTaskSchur64, kTaskSchur32, kTaskSchur16, kTaskSchur128, kTaskOzSlice};
+  for (int k : kinds) {
     S->tasks[k].clear();
     S->task_off[k].assign(S->nlev + 1, 0);
     S->lvl_flops[k].assign(S->nlev, 0.0);
   }
+  S->lvl_ozrows.assign(S->nlev, 0);
+  S->oz_rows = 0;
   for (int32_t l = 0; l < S->nlev; l++) {
     int64_t tiles64 = 0, tiles128 = 0;
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
@@ -467,6 +469,7 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
       tiles64 += nt * (nt + 1) / 2;
       tiles128 += nt2 * (nt2 + 1) / 2;
     }
+    int64_t ozrow = 0;
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
       const int32_t s = S->lvl_sn[q];
       const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
@@ -475,13 +478,19 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
       const int cls = choose_tile_class(policy, u, tiles64, tiles128);
       const int T = tile_of_class(cls), k = schur_kind(cls);
       S->lvl_flops[k][l] += (double)u * (u + 1.0) * w;
-      for (int32_t i0 = 0; i0 < u; i0 += T)
-        for (int32_t k0 = 0; k0 <= i0; k0 += T) push4(S->tasks[k], s, i0, k0, T);
+      if (cls == kTile128) {
+        for (int32_t i0 = 0; i0 < u; i0 += T)
+          for (int32_t k0 = 0; k0 <= i0; k0 += T) push4(S->tasks[k], s, i0, k0, (int32_t)ozrow);
+        for (int32_t r0 = 0; r0 < u; r0 += 128) push4(S->tasks[kTaskOzSlice], s, r0, (int32_t)ozrow, 0);
+        ozrow += (u + 7) / 8 * 8;
+      } else {
+        for (int32_t i0 = 0; i0 < u; i0 += T)
+          for (int32_t k0 = 0; k0 <= i0; k0 += T) push4(S->tasks[k], s, i0, k0, T);
+      }
     }
-    for (int cls = 0; cls < kNumTileClasses; cls++) {
-      const int k = schur_kind(cls);
-      S->task_off[k][l + 1] = (int64_t)S->tasks[k].size() / 4;
-    }
+    S->lvl_ozrows[l] = ozrow;
+    if (ozrow > 0) S->oz_rows = std::max(S->oz_rows, ozrow + 128);
+    for (int k : kinds) S->task_off[k][l + 1] = (int64_t)S->tasks[k].size() / 4;
   }
 }
 

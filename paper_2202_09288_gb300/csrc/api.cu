@@ -222,6 +222,8 @@ int ensure_attrs(chol_ctx* c) {
   if (rc) return rc;
   rc = chol::set_tc_kernel_attrs();
   if (rc) return rc;
+  rc = chol::set_oz_kernel_attrs();
+  if (rc) return rc;
   c->attrs_set = true;
   return CHOL_OK;
 }
@@ -280,8 +282,12 @@ TaskView sym_view(const chol_sym* sym) {
 
 // Per level: POTRF, TRSM, the Schur tile classes and (owner mode) the ordered assembly,
 // each one launch over the level's tasks of every matrix in the view.
+bool use_oz(const chol_ctx* c, const chol_sym* sym) {
+  return c->opts.fp64_schur == CHOL_SCHUR_OZAKI && sym->S.max_width <= 64;
+}
+
 int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
-                   bool f32, bool owner, int* ctr) {
+                   bool f32, bool owner, int* ctr, void* oz, int64_t oz_rows) {
   cudaStream_t st = c->stream;
   CK(cudaMemsetAsync(ctr, 0, factor_counters(v.nlev) * sizeof(int), st));
   const float tau = (float)(c->opts.pivot_tau > 0 ? c->opts.pivot_tau : 1e-5);
@@ -301,13 +307,24 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
       chol::launch_trsm(t, cnt, q + 1, sns, v.max_width, f32, st);
       prof_end(c, kt, v.flops[chol::kTaskTrsm][l], 0.0);
     }
+    const bool tc64 = !f32 && oz != nullptr;  // FP64 128-tiles on the bf16 tensor cores
+    if (tc64) {
+      t = v.level(chol::kTaskOzSlice, l, &cnt);
+      if (cnt > 0) {
+        prof_begin(c);
+        chol::launch_oz_slice(t, cnt, sns, oz, oz_rows, st);
+        prof_end(c, kProfOzSlice, 0.0, 0.0);
+      }
+    }
     for (int cls = 0; cls < chol::kNumTileClasses; cls++) {
       const int kind = chol::schur_kind(cls);
       t = v.level(kind, l, &cnt);
       if (cnt <= 0) continue;
+      const bool ozc = tc64 && cls == chol::kTile128;
       prof_begin(c);
-      chol::launch_schur(cls, t, cnt, q + 2 + cls, sns, mats, owner, f32, st);
-      prof_end(c, prof_schur_kind(cls, f32), v.flops[kind][l], 0.0);
+      if (ozc) chol::launch_schur_oz(t, cnt, q + 2 + cls, sns, mats, owner, oz, oz_rows, st);
+      else chol::launch_schur(cls, t, cnt, q + 2 + cls, sns, mats, owner, f32, st);
+      prof_end(c, prof_schur_kind(cls, f32, ozc), v.flops[kind][l], 0.0);
     }
     if (owner) {
       t = v.level(chol::kTaskAsm, l, &cnt);
@@ -323,11 +340,42 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
 }
 
 // Enqueues the numeric factorization of the values in f->d_vals.
+// Slice scratch of a factor's FP64 tensor-core Schur tiles, grown to the analysis' need
+// (a new tile policy can raise it) and zeroed when allocated.
+int ensure_oz(chol_num* f, void** oz, int64_t* rows) {
+  *oz = nullptr;
+  *rows = 0;
+  const Sym& S = f->sym->S;
+  if (f->precision == CHOL_MIXED || !use_oz(f->ctx, f->sym) || S.oz_rows <= 0) return CHOL_OK;
+  if (f->oz_cap < S.oz_rows) {
+    chol_ctx* c = f->ctx;
+    // the stream may still use the old scratch: free it only after the stream drains
+    if (f->d_oz) {
+      CK(cudaStreamSynchronize(c->stream));
+      dev_free(c, f->d_oz);
+      f->d_oz = nullptr;
+      f->oz_cap = 0;
+    }
+    const size_t bytes = chol::oz_scratch_bytes(S.oz_rows);
+    int rc = dev_alloc(c, &f->d_oz, bytes);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(f->d_oz, 0, bytes, c->stream));
+    f->oz_cap = S.oz_rows;
+  }
+  *oz = f->d_oz;
+  *rows = f->oz_cap;
+  return CHOL_OK;
+}
+
 int enqueue_factor(chol_num* f) {
   int rc = enqueue_assembly(f);
   if (rc) return rc;
+  void* oz;
+  int64_t oz_rows;
+  if ((rc = ensure_oz(f, &oz, &oz_rows))) return rc;
   return enqueue_levels(f->ctx, sym_view(f->sym), f->d_sn, f->d_mat,
-                        f->precision == CHOL_MIXED, f->assembly == CHOL_ASSEMBLY_OWNER, f->d_ctr);
+                        f->precision == CHOL_MIXED, f->assembly == CHOL_ASSEMBLY_OWNER, f->d_ctr,
+                        oz, oz_rows);
 }
 
 // Device descriptors of f's supernodes (matrix slot `mat`) and of f itself.
@@ -431,7 +479,7 @@ void free_num_buffers(chol_num* f) {
   if (!c) return;
   void* ptrs[] = {f->L, f->d_sn, f->d_mat, f->d_err, f->d_ctr, f->d_vals, f->d_stage, f->d_scale,
                   f->d_y, f->d_w, f->d_bx, f->d_part, f->d_fstage, f->d_rr, f->d_rd,
-                  f->d_rb, f->d_norm};
+                  f->d_rb, f->d_norm, f->d_oz};
   for (void* p : ptrs) dev_free(c, p);
   c->nums.erase(f);
   f->ctx = nullptr;
@@ -519,6 +567,7 @@ size_t factor_bytes(const chol_sym* sym, int precision, int assembly) {
              (size_t)S.nnz_a * 8;
   if (precision == CHOL_MIXED) b += (size_t)S.n * 8;
   if (assembly == CHOL_ASSEMBLY_OWNER) b += (size_t)S.stage_elems * 8;
+  if (precision != CHOL_MIXED && S.oz_rows > 0) b += chol::oz_scratch_bytes(S.oz_rows);
   return b;
 }
 
@@ -732,7 +781,8 @@ int chol_create(const chol_opts* opts, chol_ctx** out) {
   if (opts) c->opts = *opts; else chol_default_opts(&c->opts);
   if (c->opts.width_cap <= 0) c->opts.width_cap = 64;
   if (c->opts.width_cap > chol::kMaxWidth ||
-      (c->opts.assembly != CHOL_ASSEMBLY_ATOMIC && c->opts.assembly != CHOL_ASSEMBLY_OWNER)) {
+      (c->opts.assembly != CHOL_ASSEMBLY_ATOMIC && c->opts.assembly != CHOL_ASSEMBLY_OWNER) ||
+      (c->opts.fp64_schur != CHOL_SCHUR_OZAKI && c->opts.fp64_schur != CHOL_SCHUR_DMMA)) {
     delete c;
     return CHOL_E_INVALID;
   }

@@ -35,6 +35,8 @@ struct chol_batch {
   SnDev* d_sn = nullptr;
   MatDev* d_mat = nullptr;
   int* d_ctr = nullptr;  // work-queue counters of the batch's launches
+  void* d_oz = nullptr;  // FP64 tensor-core Schur tiles: slice scratch of all members
+  int64_t oz_rows = 0;
   int32_t nlev = 0;
   int max_width = 0;
   // captured factorization
@@ -56,7 +58,9 @@ void batch_release(chol_batch* b) {
   dev_free(b->ctx, b->d_sn);
   dev_free(b->ctx, b->d_mat);
   dev_free(b->ctx, b->d_ctr);
+  dev_free(b->ctx, b->d_oz);
   b->d_ctr = nullptr;
+  b->d_oz = nullptr;
   for (int k = 0; k < chol::kNumTaskKinds; k++) b->d_tasks[k] = nullptr;
   b->d_asm_src = nullptr;
   b->d_sn = nullptr;
@@ -83,12 +87,13 @@ int enqueue_batch(chol_batch* b) {
     int rc = enqueue_assembly(f);
     if (rc) return rc;
   }
-  return enqueue_levels(b->ctx, batch_view(b), b->d_sn, b->d_mat, b->f32, b->owner, b->d_ctr);
+  return enqueue_levels(b->ctx, batch_view(b), b->d_sn, b->d_mat, b->f32, b->owner, b->d_ctr,
+                        b->d_oz, b->oz_rows);
 }
 
-const int kFactorKinds[] = {chol::kTaskPotrf,   chol::kTaskTrsm,     chol::kTaskSchur64,
-                            chol::kTaskSchur32, chol::kTaskSchur16, chol::kTaskSchur128,
-                            chol::kTaskAsm};
+const int kFactorKinds[] = {chol::kTaskPotrf,    chol::kTaskTrsm,     chol::kTaskSchur64,
+                            chol::kTaskSchur32,  chol::kTaskSchur16, chol::kTaskSchur128,
+                            chol::kTaskOzSlice, chol::kTaskAsm};
 
 }  // namespace
 
@@ -140,16 +145,32 @@ int chol_batch_create(chol_ctx* c, int count, chol_num* const* nums, chol_batch*
     b->off[k].assign(b->nlev + 1, 0);
     b->flops[k].assign(b->nlev, 0.0);
   }
+  // FP64 tensor-core Schur tiles: each member's slice rows of a level follow the previous
+  // members' in one batch scratch
+  const bool oz = !b->f32 && use_oz(c, nums[0]->sym);
+  std::vector<int64_t> ozbase(count);
   for (int32_t l = 0; l < b->nlev; l++) {
+    int64_t total = 0;
+    for (int i = 0; i < count; i++) {
+      const Sym& S = nums[i]->sym->S;
+      ozbase[i] = total;
+      if (l < S.nlev) total += S.lvl_ozrows[l];
+    }
+    if (oz && total > 0) b->oz_rows = std::max(b->oz_rows, total + 128);
     for (int k : kFactorKinds) {
       for (int i = 0; i < count; i++) {
         const Sym& S = nums[i]->sym->S;
         if (l >= S.nlev) continue;
         for (int64_t q = S.task_off[k][l]; q < S.task_off[k][l + 1]; q++) {
           const int32_t* t = &S.tasks[k][4 * q];
+          const int32_t zb = (int32_t)ozbase[i];
           if (k == chol::kTaskAsm) {  // {t, cb, first, end}: target and source range move
             b->tasks[k].insert(b->tasks[k].end(),
                                {t[0] + base[i], t[1], t[2] + src_base[i], t[3] + src_base[i]});
+          } else if (k == chol::kTaskSchur128) {  // {s, i0, k0, oz}
+            b->tasks[k].insert(b->tasks[k].end(), {t[0] + base[i], t[1], t[2], t[3] + zb});
+          } else if (k == chol::kTaskOzSlice) {   // {s, r0, oz, -}
+            b->tasks[k].insert(b->tasks[k].end(), {t[0] + base[i], t[1], t[2] + zb, t[3]});
           } else {
             b->tasks[k].insert(b->tasks[k].end(), {t[0] + base[i], t[1], t[2], t[3]});
           }
@@ -180,7 +201,12 @@ int chol_batch_create(chol_ctx* c, int count, chol_num* const* nums, chol_batch*
     if (!(rc = dev_alloc(c, (void**)&b->d_asm_src, ab)) &&
         !(rc = dev_alloc(c, (void**)&b->d_sn, sn.size() * sizeof(SnDev))) &&
         !(rc = dev_alloc(c, (void**)&b->d_mat, mats.size() * sizeof(MatDev))) &&
-        !(rc = dev_alloc(c, (void**)&b->d_ctr, factor_counters(b->nlev) * sizeof(int)))) {
+        !(rc = dev_alloc(c, (void**)&b->d_ctr, factor_counters(b->nlev) * sizeof(int))) &&
+        !(b->oz_rows > 0 &&
+          (rc = dev_alloc(c, &b->d_oz, chol::oz_scratch_bytes(b->oz_rows))))) {
+      if (b->d_oz && cudaMemsetAsync(b->d_oz, 0, chol::oz_scratch_bytes(b->oz_rows), c->stream) !=
+                         cudaSuccess)
+        rc = CHOL_E_CUDA;
       if ((ab && cudaMemcpyAsync(b->d_asm_src, b->asm_src.data(), ab, cudaMemcpyHostToDevice,
                                  c->stream) != cudaSuccess) ||
           cudaMemcpyAsync(b->d_sn, sn.data(), sn.size() * sizeof(SnDev), cudaMemcpyHostToDevice,
@@ -300,8 +326,8 @@ int chol_sym_set_tile_policy(chol_sym* s, const chol_tile_policy* p) {
   if (!s->ctx) return CHOL_OK;
   chol_ctx* c = s->ctx;
   if (cudaSetDevice(c->opts.device) != cudaSuccess) return CHOL_E_NODEVICE;
-  for (int cls = 0; cls < chol::kNumTileClasses; cls++) {
-    const int k = chol::schur_kind(cls);
+  for (int cls = 0; cls <= chol::kNumTileClasses; cls++) {  // the Schur kinds, then slices
+    const int k = cls < chol::kNumTileClasses ? chol::schur_kind(cls) : chol::kTaskOzSlice;
     dev_free(c, s->dev.tasks[k]);
     s->dev.tasks[k] = nullptr;
     const size_t bytes = s->S.tasks[k].size() * sizeof(int32_t);

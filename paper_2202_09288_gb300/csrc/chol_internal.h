@@ -16,8 +16,19 @@ constexpr int kSolveRows = 128;  // off-diagonal rows per solve task
 constexpr int kMaxWidth = 128;   // hard limit on the width cap W (diagonal block in smem)
 
 // Schur tile classes: the update U = L21 L21^T of a supernode is cut into lower-triangular
-// T x T tiles, T in {128, 64, 32, 16}.  128-tiles run on tcgen05 tensor cores (TF32) in
-// the mixed-precision factor and as four 64-sub-tiles in FP64.
+// T x T tiles, T in {128, 64, 32, 16}.  128-tiles run on tcgen05 tensor cores: 3xTF32 in
+// the mixed-precision factor, bf16 operand slices in FP64 (or, with the DMMA option, as
+// four 64 x 64 FP64 tiles).
+//
+// FP64 on bf16 tensor cores (operand splitting): a row r of L21 is scaled by 2^-e_r
+// (max |L21[r,:]| < 2^e_r) and cut into kOzSlices integer slices of 7 bits,
+//   L21[r,k] 2^-e_r = sum_p s_p[r,k] 2^(-7(p+1)),  |s_0| <= 128, |s_p| <= 64 (p > 0),
+// each exact in bf16.  Slice products are accumulated exactly in FP32 (every partial sum
+// of one diagonal p+q stays below 2^24 for K <= 128), and
+//   U[i,k] = 2^(e_i+e_k) sum_{p+q < kOzSlices} 2^(-7(p+q+2)) sum_kk s_p[i,kk] s_q[k,kk].
+// The representation error is below 2^-57 of the row maximum.
+constexpr int kOzSlices = 8;
+constexpr int kOzRowBytes = 128;  // one slice row: 64 bf16 (K <= 64), 128-byte swizzled
 enum SchurClass { kTile64 = 0, kTile32 = 1, kTile16 = 2, kTile128 = 3, kNumTileClasses = 4 };
 inline int tile_of_class(int c) {
   return c == kTile128 ? 128 : (c == kTile64 ? 64 : (c == kTile32 ? 32 : 16));
@@ -33,8 +44,9 @@ enum TaskKind {
   kTaskFwd = 5,     // {s, r0, -, -}: forward-solve block
   kTaskBwd = 6,     // {s, r0, -, -}: backward-solve partial block
   kTaskAsm = 7,     // {t, cb, first, end}: owner assembly group (see Sym::asm_src)
-  kTaskSchur128 = 8,  // {s, i0, k0, 128}: 128 x 128 tile of U_s
-  kNumTaskKinds = 9
+  kTaskSchur128 = 8,  // {s, i0, k0, oz}: 128 x 128 tile of U_s; oz = first slice row of s
+  kTaskOzSlice = 9,   // {s, r0, oz, -}: slices of L21 rows r0 .. r0+127 of s (FP64 only)
+  kNumTaskKinds = 10
 };
 inline int schur_kind(int cls) { return cls == kTile128 ? kTaskSchur128 : kTaskSchur64 + cls; }
 
@@ -104,6 +116,10 @@ struct Sym {
   std::vector<int64_t> task_off[kNumTaskKinds];   // nlev + 1
   // owner assembly: staging offsets of U_s inside its level's buffer, and the size
   int64_t stage_elems = 0;
+  // slice rows of the 128-tile supernodes of each level (rounded up to 8 per supernode),
+  // and the largest level's count plus one tile of slack (rows a tile may read past u)
+  std::vector<int64_t> lvl_ozrows;
+  int64_t oz_rows = 0;
   std::vector<int64_t> sn_ustage;  // ns
   // sources of the owner-assembly groups: {s, kb, ke, 0}, columns [kb, ke) of U_s
   std::vector<int32_t> asm_src;

@@ -172,9 +172,10 @@ __global__ void __launch_bounds__(SchurCfg<TILE>::THREADS)
     const int4 tk = tasks[tq >> vsplit];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
-    // a task covers a (tk.w x tk.w) block of U_s; blocks larger than this kernel's tile
-    // are done as TILE x TILE sub-tiles, skipping those wholly above the diagonal
-    const int span = tk.w > TILE ? tk.w : TILE;
+    // a task covers a (tk.w x tk.w) block of U_s (128 x 128 for the 128 class, whose .w
+    // holds the slice offset instead); blocks larger than this kernel's tile are done as
+    // TILE x TILE sub-tiles, skipping those wholly above the diagonal
+    const int span = vsplit ? TILE << (vsplit >> 1) : (tk.w > TILE ? tk.w : TILE);
     const int sub_lo = vsplit ? (tq & ((1 << vsplit) - 1)) : 0;
     const int sub_hi = vsplit ? sub_lo + 1 : (span / TILE) * (span / TILE);
     for (int sub = sub_lo; sub < sub_hi; sub++) {

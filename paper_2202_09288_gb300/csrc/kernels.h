@@ -25,6 +25,16 @@ int set_factor_kernel_attrs(int max_width);
 void launch_schur_tc(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                      const MatDev* mats, bool owner, cudaStream_t st);
 int set_tc_kernel_attrs();
+// FP64 128 x 128 Schur tiles on the bf16 tensor cores by operand splitting, oz_kernels.cu:
+// per level, first the slices of every 128-tile supernode's L21 (kTaskOzSlice tasks), then
+// the tiles.  oz is a zeroed scratch of oz_scratch_bytes(oz_rows) bytes.
+void launch_oz_slice(const int4* tasks, int ntasks, const SnDev* sns, void* oz, int64_t oz_rows,
+                     cudaStream_t st);
+void launch_schur_oz(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
+                     const MatDev* mats, bool owner, const void* oz, int64_t oz_rows,
+                     cudaStream_t st);
+size_t oz_scratch_bytes(int64_t oz_rows);
+int set_oz_kernel_attrs();
 
 void launch_gather_perm(const double* B, int64_t ldb, const int32_t* perm, const double* scale,
                         int64_t n, int nrhs, double* y, cudaStream_t st);

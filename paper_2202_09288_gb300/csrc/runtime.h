@@ -21,17 +21,18 @@ enum ProfKindId {
   kProfAssemble, kProfPotrf, kProfTrsm, kProfSchur64, kProfSchur32, kProfSchur16,
   kProfAsmOwner, kProfFwd, kProfBwd, kProfPerm, kProfScale, kProfPotrfF32, kProfTrsmF32,
   kProfSchur64F32, kProfSchur32F32, kProfSchur16F32, kProfRefine, kProfGraph, kProfSchur128,
-  kProfSchur128Tc, kNumProf
+  kProfSchur128Tc, kProfOzSlice, kProfSchur128Oz, kNumProf
 };
 inline const char* const kProfNames[kNumProf] = {
     "assemble",    "potrf_f64",   "trsm_f64",    "schur64_f64",  "schur32_f64",
     "schur16_f64", "assemble_owner", "solve_fwd", "solve_bwd",   "solve_perm",
     "equilibrate", "potrf_f32",   "trsm_f32",    "schur64_f32",  "schur32_f32",
-    "schur16_f32", "refine",      "batch_graph", "schur128_f64", "schur128_tc"};
+    "schur16_f32", "refine",      "batch_graph", "schur128_f64", "schur128_tc",
+    "oz_slice",    "schur128_oz"};
 
-// Tracing kind of a Schur tile class.
-inline int prof_schur_kind(int cls, bool f32) {
-  if (cls == chol::kTile128) return f32 ? kProfSchur128Tc : kProfSchur128;
+// Tracing kind of a Schur tile class (oz: FP64 128-tiles on the bf16 tensor cores).
+inline int prof_schur_kind(int cls, bool f32, bool oz = false) {
+  if (cls == chol::kTile128) return f32 ? kProfSchur128Tc : (oz ? kProfSchur128Oz : kProfSchur128);
   return (f32 ? kProfSchur64F32 : kProfSchur64) + cls;
 }
 
@@ -102,6 +103,8 @@ struct chol_num {
   double* d_vals = nullptr;    // device copy of A's values (assembly and residual)
   double* d_stage = nullptr;   // owner assembly staging
   double* d_scale = nullptr;   // CHOL_MIXED: equilibration a_jj^{-1/2}
+  void* d_oz = nullptr;        // FP64 tensor-core Schur: operand slices (zeroed scratch)
+  int64_t oz_cap = 0;          // slice rows d_oz holds
   // solve workspace, grown on demand
   int64_t ws_nrhs = 0;
   double* d_y = nullptr;
@@ -148,8 +151,12 @@ TaskView sym_view(const chol_sym* sym);
 constexpr int kFactorCountersPerLevel = 3 + chol::kNumTileClasses;
 inline size_t factor_counters(int32_t nlev) { return kFactorCountersPerLevel * (size_t)nlev + 8; }
 inline size_t solve_counters(int32_t nlev) { return 3 * (size_t)nlev + 8; }
+// oz / oz_rows: slice scratch of FP64 128-tiles on the bf16 tensor cores (null: those
+// tiles run as 64 x 64 DMMA tiles)
 int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
-                   bool f32, bool owner, int* ctr);
+                   bool f32, bool owner, int* ctr, void* oz = nullptr, int64_t oz_rows = 0);
+// Whether FP64 factors of sym under c's options use the bf16 tensor-core Schur tiles.
+bool use_oz(const chol_ctx* c, const chol_sym* sym);
 void fill_descriptors(const chol_num* f, int mat, int32_t sn_base, std::vector<SnDev>* sn,
                       MatDev* md);
 
