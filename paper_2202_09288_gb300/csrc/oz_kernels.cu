@@ -34,7 +34,7 @@ namespace chol {
 
 namespace {
 
-constexpr int kOzThreads = 256;
+constexpr int kOzThreads = 512;
 constexpr int kOzM = 128;                                  // tile rows (UMMA M)
 constexpr int kOzN = 64;                                   // columns per half (UMMA N)
 constexpr uint32_t kOzASlice = kOzM * kOzRowBytes;         // 16 KB
@@ -110,20 +110,6 @@ __device__ __forceinline__ void oz_commit(uint32_t bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void oz_tmem_load32(uint32_t addr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(double lo, double hi) {
   const __nv_bfloat16 a = __float2bfloat16_rn((float)lo), b = __float2bfloat16_rn((float)hi);
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
@@ -180,6 +166,30 @@ __global__ void __launch_bounds__(128)
   reinterpret_cast<int32_t*>(oz + kOzSlices * stride)[row] = e;
 }
 
+// Eight accumulator columns of this warp's 32 TMEM lanes (one row per thread).
+__device__ __forceinline__ void oz_tmem_load8(uint32_t addr, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// An FP32 value holding an integer of magnitude below 2^22, as that integer: adding
+// 1.5 * 2^23 puts it in the low mantissa bits.
+__device__ __forceinline__ int32_t oz_int(uint32_t f) {
+  return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
+}
+
+// 2^e as a double (e in the normal range; others through ldexp).
+__device__ __forceinline__ double oz_pow2(int e) {
+  return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
+                                   : ldexp(1.0, e);
+}
+
+constexpr int kOzMaxRuns = 16;  // column targets per task whose relative rows are cached
+
 template <bool OWNER>
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_schur_oz(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
@@ -191,8 +201,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   unsigned char* B = A + kOzABytes;
   __shared__ __align__(8) uint64_t bar_ld, bar_mma;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_eA[kOzM], s_eB[2][kOzN], s_tcol[2][kOzN];
-  __shared__ int s_next, s_fail;
+  __shared__ int s_eA[kOzM], s_eB[2 * kOzN];
+  __shared__ int s_tcol[2 * kOzN], s_run[2 * kOzN], s_col[2 * kOzN];
+  __shared__ int s_run_start[2 * kOzN + 1];
+  __shared__ double* s_rL[kOzMaxRuns];
+  __shared__ int s_rm[kOzMaxRuns];
+  __shared__ int s_rp[kOzMaxRuns][kOzM];
+  __shared__ int s_nruns, s_next, s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t bld = smem_u32(&bar_ld), bmma = smem_u32(&bar_mma);
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
@@ -215,6 +230,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = oz_idesc();
+  const uint64_t da0 = oz_desc(smem_u32(A)), db0 = oz_desc(smem_u32(B));
   uint32_t ld_phase = 0, mma_phase = 0;  // parity of the next phase of each barrier
   // thread 0: copies / MMAs issued but not yet observed complete, and their phase parity
   bool ld_inflight = false, mma_inflight = false;
@@ -235,13 +251,16 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     ld_inflight = true;
     ld_parity = ld_phase;
   };
+  // thread 0: D_{p+q} (+)= S_p S_q^T for every slice pair p + q < kOzSlices; a K step of
+  // 16 bf16 advances both descriptors by 32 bytes (2 in the address field)
   auto issue_mmas = [&](int ksteps) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     for (int p = 0; p < kOzSlices; p++)
       for (int q = 0; p + q < kOzSlices; q++)
         for (int ks = 0; ks < ksteps; ks++)
-          oz_mma(tmem + (uint32_t)((p + q) * kOzN), oz_desc(smem_u32(A + p * kOzASlice) + ks * 32),
-                 oz_desc(smem_u32(B + q * kOzBSlice) + ks * 32), idesc,
+          oz_mma(tmem + (uint32_t)((p + q) * kOzN),
+                 da0 + (uint64_t)((p * kOzASlice) >> 4) + 2 * ks,
+                 db0 + (uint64_t)((q * kOzBSlice) >> 4) + 2 * ks, idesc,
                  (p > 0 || ks > 0) ? 1u : 0u);
     oz_commit(bmma);
     mma_inflight = true;
@@ -260,29 +279,71 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int32_t* rows = d.rows + n;
     const MatDev md = mats[d.mat];
     // this task's exponents and column targets (the previous task's epilogue is done)
-    for (int i = tid; i < kOzM; i += kOzThreads)
-      s_eA[i] = (i0 + i < u) ? exps[tk.w + i0 + i] : 0;
-    for (int idx = tid; idx < 2 * kOzN; idx += kOzThreads) {
-      const int h = idx / kOzN, kk = idx % kOzN, gk = k0 + h * kOzN + kk;
-      s_eB[h][kk] = gk < u ? exps[tk.w + gk] : 0;
-      s_tcol[h][kk] = gk < u ? md.col2sn[rows[gk]] : -1;
+    for (int i = tid; i < kOzM; i += kOzThreads) s_eA[i] = (i0 + i < u) ? exps[tk.w + i0 + i] : 0;
+    for (int kk = tid; kk < 2 * kOzN; kk += kOzThreads) {
+      const int gk = k0 + kk;
+      s_eB[kk] = gk < u ? exps[tk.w + gk] : 0;
+      s_tcol[kk] = gk < u ? md.col2sn[rows[gk]] : -1;
     }
     if (tid == 0) s_next = gridDim.x >= ntasks ? ntasks : gridDim.x + atomicAdd(queue, 1);
     __syncthreads();
+    // thread 0: the MMAs of the first half as soon as its operands are in
+    if (tid == 0) {
+      if (!oz_wait(bld, ld_phase)) s_fail = 1;
+      else {
+        ld_inflight = false;
+        issue_mmas(ksteps);
+      }
+    }
+    ld_phase ^= 1;
+    if (!OWNER) {
+      // runs of tile columns with one target (first warp, ballots), then the relative rows
+      // of the tile rows inside the first kOzMaxRuns targets, while the tensor cores work
+      if (warp == 0) {
+        int nr = 0;
+        for (int base = 0; base < 2 * kOzN; base += 32) {
+          const int kk = base + lane;
+          const bool live = k0 + kk < u;
+          const bool start = live && (kk == 0 || s_tcol[kk] != s_tcol[kk - 1]);
+          const unsigned b = __ballot_sync(0xffffffffu, start);
+          if (start) s_run_start[nr + __popc(b & ((1u << lane) - 1u))] = kk;
+          nr += __popc(b);
+        }
+        __syncwarp();
+        if (lane == 0) s_nruns = nr;
+        for (int r = lane; r < nr; r += 32) {
+          const int kb = s_run_start[r];
+          const int ke = r + 1 < nr ? s_run_start[r + 1] : min(2 * kOzN, u - k0);
+          const SnDev& td = sns[md.sn_base + s_tcol[kb]];
+          if (r < kOzMaxRuns) {
+            s_rL[r] = reinterpret_cast<double*>(td.L);
+            s_rm[r] = td.m;
+          }
+          for (int kk = kb; kk < ke; kk++) {
+            s_run[kk] = r;
+            s_col[kk] = rows[k0 + kk] - td.col0;
+          }
+        }
+      }
+      __syncthreads();
+      const int nrc = min(s_nruns, kOzMaxRuns);
+      for (int idx = tid; idx < nrc * kOzM; idx += kOzThreads) {
+        const int r = idx / kOzM, i = idx - r * kOzM, gi = i0 + i;
+        int p = -1;
+        if (gi < u && gi >= k0 + s_run_start[r]) {
+          const SnDev& td = sns[md.sn_base + s_tcol[s_run_start[r]]];
+          const int key = rows[gi];
+          p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
+        }
+        s_rp[r][i] = p;
+      }
+    }
     const int next = s_next;
     const int i = 32 * (warp & 3) + lane;  // this thread's tile row
     const int gi = i0 + i;
     const int eA = s_eA[i];
-    double acc[32];
+    const int c0 = 16 * (warp >> 2);       // this thread's 16 columns of a half
     for (int h = 0; h < nh; h++) {
-      if (h == 0) {
-        // the task's A slices and the first half's B slices landed; thread 0 issues the
-        // MMAs (the second half's were issued during the first half's scatter)
-        if (!oz_wait(bld, ld_phase)) s_fail = 1;
-        else if (tid == 0) ld_inflight = false;
-        ld_phase ^= 1;
-        if (tid == 0 && !s_fail) issue_mmas(ksteps);
-      }
       if (!oz_wait(bmma, mma_phase)) s_fail = 1;
       else if (tid == 0) mma_inflight = false;
       mma_phase ^= 1;
@@ -294,60 +355,76 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (h + 1 < nh) issue_loads(tk, h + 1, false);
         else if (next < ntasks) issue_loads(tasks[next], 0, true);
       }
-      // accumulators -> FP64, smallest weights first
-      const int c0 = 32 * (warp >> 2);
+      // accumulators -> integers -> W = V_hi 2^20 + round(V_lo / 2^8), where
+      // V_hi = sum_{d<4} D_d 2^(7(3-d)), V_lo = sum_{d>=4} D_d 2^(7(7-d)) (|D_d| < 2^22,
+      // |V_hi| < 2^42, |V_lo| < 2^44), so U = W 2^(e_i + e_k - 55)
+      double val[16];
 #pragma unroll
-      for (int j = 0; j < 32; j++) acc[j] = 0.0;
-#pragma unroll 1
-      for (int dd = kOzSlices - 1; dd >= 0; dd--) {
-        uint32_t v[32];
-        oz_tmem_load32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(dd * kOzN + c0), v);
-        const double wgt = ldexp(1.0, -7 * (dd + 2));
+      for (int cc = 0; cc < 2; cc++) {
+        long long vh[8], vl[8];
 #pragma unroll
-        for (int j = 0; j < 32; j++) acc[j] += (double)__uint_as_float(v[j]) * wgt;
+        for (int j = 0; j < 8; j++) vh[j] = vl[j] = 0;
+        const uint32_t ta =
+            tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 8 * cc);
+#pragma unroll
+        for (int dd = 0; dd < kOzSlices; dd++) {
+          uint32_t v[8];
+          oz_tmem_load8(ta + (uint32_t)(dd * kOzN), v);
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            if (dd < 4) vh[j] = vh[j] * 128 + oz_int(v[j]);
+            else vl[j] = vl[j] * 128 + oz_int(v[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          const long long w = vh[j] * (1ll << 20) + ((vl[j] + 128) >> 8);
+          val[8 * cc + j] = (double)w * oz_pow2(eA + s_eB[h * kOzN + c0 + 8 * cc + j] - 55);
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncthreads();
       // tensor memory is free: the second half's MMAs run during this half's scatter
-      if (h + 1 < nh && tid == 0) {
-        if (!oz_wait(bld, ld_phase)) s_fail = 1;
-        else {
-          ld_inflight = false;
-          issue_mmas(ksteps);
+      if (h + 1 < nh) {
+        if (tid == 0) {
+          if (!oz_wait(bld, ld_phase)) s_fail = 1;
+          else {
+            ld_inflight = false;
+            issue_mmas(ksteps);
+          }
         }
+        ld_phase ^= 1;  // every thread counts the second half's load
       }
-      if (h + 1 < nh) ld_phase ^= 1;  // every thread counts the half-1 load
       // scatter this thread's row of the half
       if (gi < u) {
-        const int kh0 = k0 + h * kOzN + c0;
+        const int kb = h * kOzN + c0;  // tile column of val[0]
         if (OWNER) {
           double* U = static_cast<double*>(md.stage) + d.ustage;
 #pragma unroll
-          for (int j = 0; j < 32; j++) {
-            const int gk = kh0 + j;
-            if (gk < u && gk <= gi)
-              U[(int64_t)gk * u + gi] = ldexp(acc[j], eA + s_eB[h][c0 + j]);
+          for (int j = 0; j < 16; j++) {
+            const int gk = k0 + kb + j;
+            if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = val[j];
           }
         } else {
-          int cur_t = -1, p = -1, mt = 0, col0 = 0;
-          double* Lt = nullptr;
           const int key = rows[gi];
 #pragma unroll
-          for (int j = 0; j < 32; j++) {
-            const int gk = kh0 + j;
+          for (int j = 0; j < 16; j++) {
+            const int kk = kb + j, gk = k0 + kk;
             if (gk >= u || gk > gi) continue;
-            const int t = s_tcol[h][c0 + j];
-            if (t != cur_t) {
-              const SnDev& td = sns[md.sn_base + t];
-              cur_t = t;
-              mt = td.m;
-              col0 = td.col0;
+            const int r = s_run[kk];
+            double* Lt;
+            int mt, p;
+            if (r < kOzMaxRuns) {
+              Lt = s_rL[r];
+              mt = s_rm[r];
+              p = s_rp[r][i];
+            } else {  // beyond the cached targets: look the row up here
+              const SnDev& td = sns[md.sn_base + s_tcol[kk]];
               Lt = reinterpret_cast<double*>(td.L);
+              mt = td.m;
               p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
             }
-            if (p >= 0)
-              atomicAdd(&Lt[(int64_t)(rows[gk] - col0) * mt + p],
-                        -ldexp(acc[j], eA + s_eB[h][c0 + j]));
+            if (p >= 0) atomicAdd(&Lt[(int64_t)s_col[kk] * mt + p], -val[j]);
           }
         }
       }
