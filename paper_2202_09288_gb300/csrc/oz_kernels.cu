@@ -110,60 +110,100 @@ __device__ __forceinline__ void oz_commit(uint32_t bar) {
       : "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(double lo, double hi) {
-  const __nv_bfloat16 a = __float2bfloat16_rn((float)lo), b = __float2bfloat16_rn((float)hi);
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-}
-
 }  // namespace
 
-// Slices of L21 rows r0 .. r0+127 of supernode s (one row per thread), written at slice
-// row oz + r; rows u .. roundup(u, 8) get zero slices.
-__global__ void __launch_bounds__(128)
+// bf16 bits of an integer of magnitude at most 256 (exact).
+__device__ __forceinline__ uint32_t oz_bf16_of_int(int v) {
+  if (v == 0) return 0u;
+  const uint32_t a = (uint32_t)(v < 0 ? -v : v);
+  const int e = 31 - __clz(a);  // a in [2^e, 2^(e+1))
+  return (v < 0 ? 0x8000u : 0u) | ((uint32_t)(127 + e) << 7) | ((a << (7 - e)) & 0x7Fu);
+}
+
+// x 2^(56 - e) as an integer (|x| < 2^e, so |result| < 2^56), truncated toward zero below
+// 2^0 (an error below 2^(e-56)); subnormal x give 0.
+__device__ __forceinline__ long long oz_fixed(double x, int e) {
+  const long long bits = __double_as_longlong(x);
+  const int exb = (int)((bits >> 52) & 0x7FF);
+  if (exb == 0) return 0;
+  const long long mant = (bits & ((1ll << 52) - 1)) | (1ll << 52);  // x = mant 2^(exb-1075)
+  const int sh = exb - 1019 - e;
+  const long long M = sh >= 0 ? mant << sh : (sh > -64 ? mant >> -sh : 0);
+  return bits < 0 ? -M : M;
+}
+
+constexpr int kOzSliceThreads = 256;
+constexpr int kOzSliceLd = kOzM + 1;  // padded column stride of the staged block
+
+// Slices of the L21 rows r0 .. r0+127 of supernode s, at slice rows oz + r (rows u ..
+// roundup(u, 8) get zero slices).  The block is staged column by column through shared
+// memory (coalesced loads); a row's exponent e_r is that of its largest entry; each
+// entry becomes the 56-bit fixed-point integer x 2^(56-e_r), cut into 8 balanced digits
+// of 7 bits (round to nearest: |s_0| <= 128, |s_p| <= 64, exact); thread t writes the
+// 16-byte chunk t % 8 of row t / 8 of every slice (coalesced, pre-swizzled).
+__global__ void __launch_bounds__(kOzSliceThreads)
     k_oz_slice(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
                uint8_t* __restrict__ oz, int64_t oz_rows) {
+  extern __shared__ __align__(16) double xs[];  // [n][kOzSliceLd]
+  __shared__ int s_e[kOzM];
   const int4 tk = tasks[blockIdx.x];
   const SnDev d = sns[tk.x];
   const int n = d.n, m = d.m, u = m - n;
-  const int r = tk.y + threadIdx.x;
-  if (r >= ((u + 7) & ~7)) return;
-  const double* L = reinterpret_cast<const double*>(d.L) + n + r;  // L21[r, k] = L[k * m]
-  const bool live = r < u;
-  double amax = 0.0;
-  if (live)
-    for (int k = 0; k < n; k++) amax = fmax(amax, fabs(L[(int64_t)k * m]));
-  int e = 0;
-  if (amax > 0.0) frexp(amax, &e);  // amax = f 2^e, f in [0.5, 1)
-  const double sc = ldexp(1.0, -e);
-  const int64_t row = tk.z + (int64_t)r;
+  const int r0 = tk.y;
+  const int rows = min(kOzM, ((u + 7) & ~7) - r0);  // slice rows this block owns
+  const double* L = reinterpret_cast<const double*>(d.L) + n + r0;  // L21[r0 + i, k] = L[k m + i]
+  for (int idx = threadIdx.x; idx < n * kOzM; idx += kOzSliceThreads) {
+    const int k = idx / kOzM, i = idx - k * kOzM;
+    xs[k * kOzSliceLd + i] = (r0 + i < u) ? L[(int64_t)k * m + i] : 0.0;
+  }
+  __syncthreads();
+  const int64_t row0 = tk.z + (int64_t)r0;
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
-  uint8_t* base = oz + (size_t)row * kOzRowBytes;
-  for (int c = 0; c < kOzRowBytes / 16; c++) {
-    double x[8];
+  if (threadIdx.x < kOzM) {
+    const int i = threadIdx.x;
+    double amax = 0.0;
+    for (int k = 0; k < n; k++) amax = fmax(amax, fabs(xs[k * kOzSliceLd + i]));
+    // amax = f 2^e with f in [0.5, 1): the exponent field minus 1022 (0 for zero rows)
+    const int e = amax > 0.0 ? (int)((__double_as_longlong(amax) >> 52) & 0x7FF) - 1022 : 0;
+    s_e[i] = e;
+    if (i < rows) reinterpret_cast<int32_t*>(oz + kOzSlices * stride)[row0 + i] = e;
+  }
+  __syncthreads();
+  for (int item = threadIdx.x; item < kOzM * 8; item += kOzSliceThreads) {
+    const int i = item >> 3, pc = item & 7;  // row, physical 16-byte chunk
+    if (i >= rows) continue;
+    const int c = pc ^ (int)((row0 + i) & 7);  // logical chunk: columns 8c .. 8c+7
+    const int e = s_e[i];
+    long long R[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) {
       const int k = 8 * c + j;
-      x[j] = (live && k < n) ? L[(int64_t)k * m] * sc : 0.0;
+      R[j] = k < n ? oz_fixed(xs[k * kOzSliceLd + i], e) : 0;
     }
-    const uint32_t chunk = (uint32_t)((c ^ (int)(row & 7)) << 4);
+    uint8_t* dst = oz + (size_t)(row0 + i) * kOzRowBytes + pc * 16;
 #pragma unroll
     for (int p = 0; p < kOzSlices; p++) {
-      double s[8];
+      const int w = 49 - 7 * p;  // weight of digit p: 2^w
+      uint32_t h[8];
 #pragma unroll
       for (int j = 0; j < 8; j++) {
-        const double y = x[j] * 128.0;
-        s[j] = rint(y);
-        x[j] = y - s[j];  // exact: the fraction of y
+        long long dgt;
+        if (p + 1 < kOzSlices) {
+          dgt = (R[j] + (1ll << (w - 1))) >> w;
+          R[j] -= dgt << w;
+        } else {
+          dgt = R[j];  // the last digit takes the exact remainder (|R| <= 2^6)
+        }
+        h[j] = oz_bf16_of_int((int)dgt);
       }
-      uint4 w;
-      w.x = pack_bf16(s[0], s[1]);
-      w.y = pack_bf16(s[2], s[3]);
-      w.z = pack_bf16(s[4], s[5]);
-      w.w = pack_bf16(s[6], s[7]);
-      *reinterpret_cast<uint4*>(base + p * stride + chunk) = w;
+      uint4 v;
+      v.x = h[0] | (h[1] << 16);
+      v.y = h[2] | (h[3] << 16);
+      v.z = h[4] | (h[5] << 16);
+      v.w = h[6] | (h[7] << 16);
+      *reinterpret_cast<uint4*>(dst + p * stride) = v;
     }
   }
-  reinterpret_cast<int32_t*>(oz + kOzSlices * stride)[row] = e;
 }
 
 // Eight accumulator columns of this warp's 32 TMEM lanes (one row per thread).
@@ -182,13 +222,41 @@ __device__ __forceinline__ int32_t oz_int(uint32_t f) {
   return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
 }
 
-// 2^e as a double (e in the normal range; others through ldexp).
-__device__ __forceinline__ double oz_pow2(int e) {
-  return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
-                                   : ldexp(1.0, e);
+// W 2^E as a double, rounded to nearest (ties to even), with integer operations only (the
+// FP64 pipe is the scarce unit); results outside the normal range go through ldexp.
+__device__ __forceinline__ double oz_to_double(long long W, int E) {
+  if (W == 0) return 0.0;
+  const unsigned long long sign = W < 0 ? (1ull << 63) : 0ull;
+  unsigned long long a = W < 0 ? (unsigned long long)(-W) : (unsigned long long)W;
+  const int lz = __clzll((long long)a);
+  a <<= lz;  // leading one at bit 63: W = a 2^(-lz)
+  unsigned long long mant = a >> 11;
+  const unsigned long long rem = a & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) mant++;
+  int e2 = 63 - lz;  // |W| = mant 2^(e2 - 52)
+  if (mant >> 53) {
+    mant >>= 1;
+    e2++;
+  }
+  const int be = e2 + E + 1023;
+  if (be <= 0 || be >= 2047) return ldexp((double)W, E);
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1))));
 }
 
 constexpr int kOzMaxRuns = 16;  // column targets per task whose relative rows are cached
+
+// Per-task metadata, double-buffered: a task's scatter reads one copy while the next
+// task's is being built.
+struct OzMeta {
+  int eA[kOzM], eB[2 * kOzN];
+  int tcol[2 * kOzN], run[2 * kOzN], col[2 * kOzN];
+  int run_start[2 * kOzN + 1];
+  double* rL[kOzMaxRuns];
+  int rm[kOzMaxRuns];
+  int rp[kOzMaxRuns][kOzM];
+  int nruns, next;
+};
 
 template <bool OWNER>
 __global__ void __launch_bounds__(kOzThreads, 1)
@@ -201,13 +269,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   unsigned char* B = A + kOzABytes;
   __shared__ __align__(8) uint64_t bar_ld, bar_mma;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_eA[kOzM], s_eB[2 * kOzN];
-  __shared__ int s_tcol[2 * kOzN], s_run[2 * kOzN], s_col[2 * kOzN];
-  __shared__ int s_run_start[2 * kOzN + 1];
-  __shared__ double* s_rL[kOzMaxRuns];
-  __shared__ int s_rm[kOzMaxRuns];
-  __shared__ int s_rp[kOzMaxRuns][kOzM];
-  __shared__ int s_nruns, s_next, s_fail;
+  __shared__ OzMeta meta[2];
+  __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t bld = smem_u32(&bar_ld), bmma = smem_u32(&bar_mma);
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
@@ -231,10 +294,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = oz_idesc();
   const uint64_t da0 = oz_desc(smem_u32(A)), db0 = oz_desc(smem_u32(B));
-  uint32_t ld_phase = 0, mma_phase = 0;  // parity of the next phase of each barrier
-  // thread 0: copies / MMAs issued but not yet observed complete, and their phase parity
+  // thread 0 only: the load barrier's next phase, and what is in flight
+  uint32_t ld_phase = 0;
   bool ld_inflight = false, mma_inflight = false;
   uint32_t ld_parity = 0, mma_parity = 0;
+  uint32_t mma_phase = 0;  // every thread: parity of the next MMA commit
 
   // thread 0: bulk copies of a task's A slices and of one half's B slices
   auto issue_loads = [&](const int4& t, int h, bool with_a) {
@@ -251,9 +315,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     ld_inflight = true;
     ld_parity = ld_phase;
   };
-  // thread 0: D_{p+q} (+)= S_p S_q^T for every slice pair p + q < kOzSlices; a K step of
-  // 16 bf16 advances both descriptors by 32 bytes (2 in the address field)
-  auto issue_mmas = [&](int ksteps) {
+  // thread 0: wait for the operands, then D_{p+q} (+)= S_p S_q^T for every slice pair
+  // p + q < kOzSlices; a K step of 16 bf16 advances both descriptors by 32 bytes (2 in the
+  // address field).  Returns false if the wait gave up.
+  auto load_and_mma = [&](int ksteps) -> bool {
+    if (!oz_wait(bld, ld_phase)) return false;
+    ld_phase ^= 1;
+    ld_inflight = false;
     asm volatile("tcgen05.fence::after_thread_sync;");
     for (int p = 0; p < kOzSlices; p++)
       for (int q = 0; p + q < kOzSlices; q++)
@@ -265,11 +333,18 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     oz_commit(bmma);
     mma_inflight = true;
     mma_parity = mma_phase;
+    return true;
   };
+  auto ksteps_of = [&](const int4& t) { return (sns[t.x].n + 15) >> 4; };
 
   int tq = blockIdx.x;
-  if (tid == 0 && tq < ntasks) issue_loads(tasks[tq], 0, true);
+  if (tid == 0 && tq < ntasks) {
+    issue_loads(tasks[tq], 0, true);
+    if (!load_and_mma(ksteps_of(tasks[tq]))) s_fail = 1;
+  }
+  int buf = 0;
   while (tq < ntasks) {
+    // the first half's MMAs of this task are running
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, u = d.m - n;
@@ -278,24 +353,16 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int nh = (k0 + kOzN < u) ? 2 : 1;
     const int32_t* rows = d.rows + n;
     const MatDev md = mats[d.mat];
-    // this task's exponents and column targets (the previous task's epilogue is done)
-    for (int i = tid; i < kOzM; i += kOzThreads) s_eA[i] = (i0 + i < u) ? exps[tk.w + i0 + i] : 0;
+    OzMeta& M = meta[buf];
+    for (int i = tid; i < kOzM; i += kOzThreads) M.eA[i] = (i0 + i < u) ? exps[tk.w + i0 + i] : 0;
     for (int kk = tid; kk < 2 * kOzN; kk += kOzThreads) {
       const int gk = k0 + kk;
-      s_eB[kk] = gk < u ? exps[tk.w + gk] : 0;
-      s_tcol[kk] = gk < u ? md.col2sn[rows[gk]] : -1;
+      M.eB[kk] = gk < u ? exps[tk.w + gk] : 0;
+      M.tcol[kk] = gk < u ? md.col2sn[rows[gk]] : -1;
     }
-    if (tid == 0) s_next = gridDim.x >= ntasks ? ntasks : gridDim.x + atomicAdd(queue, 1);
+    if (tid == 0) M.next = gridDim.x >= ntasks ? ntasks : gridDim.x + atomicAdd(queue, 1);
     __syncthreads();
-    // thread 0: the MMAs of the first half as soon as its operands are in
-    if (tid == 0) {
-      if (!oz_wait(bld, ld_phase)) s_fail = 1;
-      else {
-        ld_inflight = false;
-        issue_mmas(ksteps);
-      }
-    }
-    ld_phase ^= 1;
+    if (s_fail) break;
     if (!OWNER) {
       // runs of tile columns with one target (first warp, ballots), then the relative rows
       // of the tile rows inside the first kOzMaxRuns targets, while the tensor cores work
@@ -304,53 +371,57 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         for (int base = 0; base < 2 * kOzN; base += 32) {
           const int kk = base + lane;
           const bool live = k0 + kk < u;
-          const bool start = live && (kk == 0 || s_tcol[kk] != s_tcol[kk - 1]);
+          const bool start = live && (kk == 0 || M.tcol[kk] != M.tcol[kk - 1]);
           const unsigned b = __ballot_sync(0xffffffffu, start);
-          if (start) s_run_start[nr + __popc(b & ((1u << lane) - 1u))] = kk;
+          if (start) M.run_start[nr + __popc(b & ((1u << lane) - 1u))] = kk;
           nr += __popc(b);
         }
         __syncwarp();
-        if (lane == 0) s_nruns = nr;
+        if (lane == 0) M.nruns = nr;
         for (int r = lane; r < nr; r += 32) {
-          const int kb = s_run_start[r];
-          const int ke = r + 1 < nr ? s_run_start[r + 1] : min(2 * kOzN, u - k0);
-          const SnDev& td = sns[md.sn_base + s_tcol[kb]];
+          const int kb = M.run_start[r];
+          const int ke = r + 1 < nr ? M.run_start[r + 1] : min(2 * kOzN, u - k0);
+          const SnDev& td = sns[md.sn_base + M.tcol[kb]];
           if (r < kOzMaxRuns) {
-            s_rL[r] = reinterpret_cast<double*>(td.L);
-            s_rm[r] = td.m;
+            M.rL[r] = reinterpret_cast<double*>(td.L);
+            M.rm[r] = td.m;
           }
           for (int kk = kb; kk < ke; kk++) {
-            s_run[kk] = r;
-            s_col[kk] = rows[k0 + kk] - td.col0;
+            M.run[kk] = r;
+            M.col[kk] = rows[k0 + kk] - td.col0;
           }
         }
       }
       __syncthreads();
-      const int nrc = min(s_nruns, kOzMaxRuns);
+      const int nrc = min(M.nruns, kOzMaxRuns);
       for (int idx = tid; idx < nrc * kOzM; idx += kOzThreads) {
         const int r = idx / kOzM, i = idx - r * kOzM, gi = i0 + i;
         int p = -1;
-        if (gi < u && gi >= k0 + s_run_start[r]) {
-          const SnDev& td = sns[md.sn_base + s_tcol[s_run_start[r]]];
+        if (gi < u && gi >= k0 + M.run_start[r]) {
+          const SnDev& td = sns[md.sn_base + M.tcol[M.run_start[r]]];
           const int key = rows[gi];
           p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
         }
-        s_rp[r][i] = p;
+        M.rp[r][i] = p;
       }
     }
-    const int next = s_next;
+    const int next = M.next;
     const int i = 32 * (warp & 3) + lane;  // this thread's tile row
     const int gi = i0 + i;
-    const int eA = s_eA[i];
+    const int eA = M.eA[i];
     const int c0 = 16 * (warp >> 2);       // this thread's 16 columns of a half
+    bool stop = false;  // s_fail seen right after a barrier: the same in every thread
     for (int h = 0; h < nh; h++) {
       if (!oz_wait(bmma, mma_phase)) s_fail = 1;
       else if (tid == 0) mma_inflight = false;
       mma_phase ^= 1;
       __syncthreads();
-      if (s_fail) break;
+      if (s_fail) {
+        stop = true;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      // shared memory is free: start the next operands while this half is applied
+      // shared memory is free: start the next operands while the accumulators are read
       if (tid == 0) {
         if (h + 1 < nh) issue_loads(tk, h + 1, false);
         else if (next < ntasks) issue_loads(tasks[next], 0, true);
@@ -377,23 +448,20 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           }
         }
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-          const long long w = vh[j] * (1ll << 20) + ((vl[j] + 128) >> 8);
-          val[8 * cc + j] = (double)w * oz_pow2(eA + s_eB[h * kOzN + c0 + 8 * cc + j] - 55);
-        }
+        for (int j = 0; j < 8; j++)
+          val[8 * cc + j] = oz_to_double(vh[j] * (1ll << 20) + ((vl[j] + 128) >> 8),
+                                         eA + M.eB[h * kOzN + c0 + 8 * cc + j] - 55);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncthreads();
-      // tensor memory is free: the second half's MMAs run during this half's scatter
-      if (h + 1 < nh) {
-        if (tid == 0) {
-          if (!oz_wait(bld, ld_phase)) s_fail = 1;
-          else {
-            ld_inflight = false;
-            issue_mmas(ksteps);
-          }
+      // tensor memory is free: the next MMAs (this task's second half, or the next task's
+      // first) run during this half's scatter
+      if (tid == 0) {
+        if (h + 1 < nh) {
+          if (!load_and_mma(ksteps)) s_fail = 1;
+        } else if (next < ntasks) {
+          if (!load_and_mma(ksteps_of(tasks[next]))) s_fail = 1;
         }
-        ld_phase ^= 1;  // every thread counts the second half's load
       }
       // scatter this thread's row of the half
       if (gi < u) {
@@ -411,31 +479,30 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           for (int j = 0; j < 16; j++) {
             const int kk = kb + j, gk = k0 + kk;
             if (gk >= u || gk > gi) continue;
-            const int r = s_run[kk];
+            const int r = M.run[kk];
             double* Lt;
             int mt, p;
             if (r < kOzMaxRuns) {
-              Lt = s_rL[r];
-              mt = s_rm[r];
-              p = s_rp[r][i];
+              Lt = M.rL[r];
+              mt = M.rm[r];
+              p = M.rp[r][i];
             } else {  // beyond the cached targets: look the row up here
-              const SnDev& td = sns[md.sn_base + s_tcol[kk]];
+              const SnDev& td = sns[md.sn_base + M.tcol[kk]];
               Lt = reinterpret_cast<double*>(td.L);
               mt = td.m;
               p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
             }
-            if (p >= 0) atomicAdd(&Lt[(int64_t)s_col[kk] * mt + p], -val[j]);
+            if (p >= 0) atomicAdd(&Lt[(int64_t)M.col[kk] * mt + p], -val[j]);
           }
         }
       }
     }
-    __syncthreads();
-    if (s_fail) {
-      if (tid == 0) atomicAdd(md.err + 3, 1ull);
-      break;
-    }
+    if (stop) break;
+    buf ^= 1;
     tq = next;
   }
+  __syncthreads();
+  if (s_fail && tid == 0 && ntasks > 0) atomicAdd(mats[sns[tasks[min(tq, ntasks - 1)].x].mat].err + 3, 1ull);
   // bounded waits for anything still in flight before the memory is released
   if (tid == 0) {
     if (mma_inflight) oz_wait(bmma, mma_parity);
@@ -451,7 +518,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 void launch_oz_slice(const int4* tasks, int ntasks, const SnDev* sns, void* oz, int64_t oz_rows,
                      cudaStream_t st) {
   if (ntasks <= 0) return;
-  k_oz_slice<<<ntasks, 128, 0, st>>>(tasks, sns, static_cast<uint8_t*>(oz), oz_rows);
+  k_oz_slice<<<ntasks, kOzSliceThreads, (size_t)64 * kOzSliceLd * sizeof(double), st>>>(
+      tasks, sns, static_cast<uint8_t*>(oz), oz_rows);
 }
 
 void launch_schur_oz(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
@@ -474,7 +542,9 @@ size_t oz_scratch_bytes(int64_t oz_rows) {
 }
 
 int set_oz_kernel_attrs() {
-  if (cudaFuncSetAttribute(k_schur_oz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(64 * kOzSliceLd * sizeof(double))) != cudaSuccess ||
+      cudaFuncSetAttribute(k_schur_oz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kOzSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_schur_oz<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kOzSmem) != cudaSuccess)
