@@ -34,50 +34,54 @@ __global__ void k_assemble(const double* __restrict__ vals, const int64_t* __res
 
 // ---- POTRF of each diagonal block ---------------------------------------------------------
 // One CTA per supernode; the n x n lower block is factored in shared memory by the
-// unblocked right-looking column algorithm: pivot sqrt, column scale, rank-1 update.
+// right-looking column algorithm.  Column j's pivot p_j = A_jj is final once columns < j are
+// applied, so one pass per column does the whole rank-1 update with the unscaled column,
+// A_rc -= A_rj A_cj / p_j (j < c <= r), and one barrier separates the columns; the columns
+// are scaled by p_j^{-1/2} (and the diagonal set to p_j^{1/2}) at the end.  Rows are spread
+// over the threads (two threads per row for n <= 64, alternate columns).
 template <typename T>
 __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                const SnDev* __restrict__ sns,
                                                const MatDev* __restrict__ mats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
+  __shared__ T piv[kMaxWidth], rpiv[kMaxWidth];
   __shared__ int s_next_task;
   for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
     T* L = reinterpret_cast<T*>(d.L);
-    __shared__ T piv_inv;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       int c = idx / n, r = idx - c * n;
       A[idx] = r >= c ? L[(int64_t)c * m + r] : T(0);
     }
     __syncthreads();
+    const bool two = n <= 64;                    // two threads per row
+    const int r = two ? (threadIdx.x & 63) : threadIdx.x;
+    const int cpar = two ? (threadIdx.x >> 6) : 0, cstep = two ? 2 : 1;
     for (int j = 0; j < n; j++) {
-      if (threadIdx.x == 0) {
-        T p = A[j * n + j];
-        if (!(p > T(0))) {
-          record_error(mats[d.mat], d.col0 + j);
-          p = T(1);
-        }
-        T s = sqrt(p);
-        A[j * n + j] = s;
-        piv_inv = T(1) / s;
+      T p = A[j * n + j];
+      if (!(p > T(0))) {
+        if (threadIdx.x == 0) record_error(mats[d.mat], d.col0 + j);
+        p = T(1);
       }
-      __syncthreads();
-      const T inv = piv_inv;
-      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] *= inv;
-      __syncthreads();
-      const int nt = n - j - 1;
-      for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
-        int c = idx / nt, r = idx - c * nt;
-        if (r >= c) A[(j + 1 + c) * n + j + 1 + r] -= A[j * n + j + 1 + r] * A[j * n + j + 1 + c];
+      if (threadIdx.x == 0) piv[j] = p;
+      if (r > j && r < n) {
+        const T arj = A[j * n + r] * (T(1) / p);
+        for (int c = j + 1 + cpar; c <= r; c += cstep) A[c * n + r] -= arj * A[j * n + c];
       }
       __syncthreads();
     }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const T sq = sqrt(piv[j]);
+      piv[j] = sq;
+      rpiv[j] = T(1) / sq;
+    }
+    __syncthreads();
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      int c = idx / n, r = idx - c * n;
-      if (r >= c) L[(int64_t)c * m + r] = A[idx];
+      const int c = idx / n, rr = idx - c * n;
+      if (rr >= c) L[(int64_t)c * m + rr] = rr == c ? piv[c] : A[idx] * rpiv[c];
     }
     __syncthreads();
     // a CTA's first task is its block index; only a grid smaller than the task list makes
@@ -90,11 +94,63 @@ __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, i
 }
 
 // ---- TRSM of the off-diagonal rows --------------------------------------------------------
-// Task {s, r0}: rows r0 .. r0+31 of L21 (panel rows n + r0 + t), one row per thread:
-// x_j = (a_j - sum_{k<j} x_k L_jk) / L_jj, i.e. L21 = A21 L11^{-T}.
+// Task {s, r0}: rows r0 .. r0+kTrsmRows-1 of L21 (panel rows n + r0 + t), L21 = A21 L11^{-T},
+// one row per thread: x_j = (a_j - sum_{k<j} x_k L_jk) / L_jj.
+//   k_trsm_reg (W <= 64): the row lives in registers and is updated right-looking
+//     (x_k -= x_j L_kj for all k > j once x_j is final), so the FMAs of a column are
+//     independent; L11 is staged once per 128 rows.
+//   k_trsm (any W <= 128): the same substitution with the partial rows in shared memory,
+//     one warp at a time over the task's rows.
 template <typename T>
-__global__ void __launch_bounds__(kTrsmRows) k_trsm(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
-                                                    const SnDev* __restrict__ sns) {
+__global__ void __launch_bounds__(kTrsmRows) k_trsm_reg(const int4* __restrict__ tasks, int ntasks,
+                                                        int* __restrict__ queue,
+                                                        const SnDev* __restrict__ sns) {
+  __shared__ T Lc[64 * 64];  // Lc[j * 64 + k] = L11[k][j]
+  __shared__ T rd[64];
+  __shared__ int s_next_task;
+  for (int tq = blockIdx.x; tq < ntasks;) {
+    const int4 tk = tasks[tq];
+    const SnDev d = sns[tk.x];
+    const int n = d.n, m = d.m;
+    T* L = reinterpret_cast<T*>(d.L);
+    for (int idx = threadIdx.x; idx < n * 64; idx += blockDim.x) {
+      const int j = idx >> 6, k = idx & 63;
+      Lc[idx] = (k >= j && k < n) ? L[(int64_t)j * m + k] : T(0);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) rd[j] = T(1) / Lc[j * 64 + j];
+    __syncthreads();
+    const int row = n + tk.y + threadIdx.x;
+    if (row < m) {
+      T x[64];
+#pragma unroll
+      for (int k = 0; k < 64; k++) x[k] = k < n ? L[(int64_t)k * m + row] : T(0);
+#pragma unroll
+      for (int j = 0; j < 64; j++) {
+        if (j < n) {
+          x[j] *= rd[j];
+#pragma unroll
+          for (int k = j + 1; k < 64; k++)
+            if (k < n) x[k] -= x[j] * Lc[j * 64 + k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 64; k++)
+        if (k < n) L[(int64_t)k * m + row] = x[k];
+    }
+    __syncthreads();
+    // a CTA's first task is its block index; only a grid smaller than the task list makes
+    // CTAs take further tasks from this launch's work queue
+    if (gridDim.x >= ntasks) break;
+    if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
+    __syncthreads();
+    tq = s_next_task;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_trsm(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
+                                             const SnDev* __restrict__ sns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next_task;
   for (int tq = blockIdx.x; tq < ntasks;) {
@@ -113,19 +169,20 @@ __global__ void __launch_bounds__(kTrsmRows) k_trsm(const int4* __restrict__ tas
     for (int j = threadIdx.x; j < n; j += blockDim.x) rdiag[j] = T(1) / L11[j * n + j];
     __syncthreads();
     const int t = threadIdx.x;
-    const int row = n + tk.y + t;
-    if (row < m) {
-      for (int j = 0; j < n; j++) {
-        T acc = L[(int64_t)j * m + row];
-        for (int k = 0; k < j; k++) acc -= X[k * kTrsmRows + t] * L11[k * n + j];
-        acc *= rdiag[j];
-        X[j * kTrsmRows + t] = acc;
-        L[(int64_t)j * m + row] = acc;
+    for (int sub = 0; sub < kTrsmRows; sub += 32) {
+      const int row = n + tk.y + sub + t;
+      if (row < m) {
+        for (int j = 0; j < n; j++) {
+          T acc = L[(int64_t)j * m + row];
+          for (int k = 0; k < j; k++) acc -= X[k * 32 + t] * L11[k * n + j];
+          acc *= rdiag[j];
+          X[j * 32 + t] = acc;
+          L[(int64_t)j * m + row] = acc;
+        }
       }
+      __syncwarp();
     }
     __syncthreads();
-    // a CTA's first task is its block index; only a grid smaller than the task list makes
-    // CTAs take further tasks from this launch's work queue
     if (gridDim.x >= ntasks) break;
     if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
     __syncthreads();
@@ -485,9 +542,7 @@ void launch_assemble(const double* vals, const int64_t* amap, int64_t nnz, void*
 
 static size_t potrf_smem(int w) { return (size_t)w * w * sizeof(double); }
 static size_t potrf_mixed_smem(int w) { return (size_t)w * w * (sizeof(double) + sizeof(float)); }
-static size_t trsm_smem(int w) {
-  return ((size_t)w * w + w + (size_t)w * kTrsmRows) * sizeof(double);
-}
+static size_t trsm_smem(int w) { return ((size_t)w * w + w + (size_t)w * 32) * sizeof(double); }
 
 void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                   const MatDev* mats, int max_width, bool f32, float tau, cudaStream_t st) {
@@ -506,9 +561,13 @@ void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
 template <typename T>
 static void trsm_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int max_width,
                    cudaStream_t st) {
+  if (max_width <= 64) {
+    k_trsm_reg<T><<<persistent_grid(k_trsm_reg<T>, kTrsmRows, 0, ntasks), kTrsmRows, 0, st>>>(
+        tasks, ntasks, queue, sns);
+    return;
+  }
   const size_t sm = trsm_smem(max_width);
-  k_trsm<T><<<persistent_grid(k_trsm<T>, kTrsmRows, sm, ntasks), kTrsmRows, sm, st>>>(
-      tasks, ntasks, queue, sns);
+  k_trsm<T><<<persistent_grid(k_trsm<T>, 32, sm, ntasks), 32, sm, st>>>(tasks, ntasks, queue, sns);
 }
 
 void launch_trsm(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int max_width,

@@ -63,8 +63,8 @@ __device__ __forceinline__ uint64_t oz_desc(uint32_t addr) {
 
 // Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B (format 1), both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__device__ __forceinline__ uint32_t oz_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzN >> 3) << 17) |
+__device__ __forceinline__ uint32_t oz_idesc(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(kOzM >> 4) << 24);
 }
 
@@ -206,13 +206,17 @@ __global__ void __launch_bounds__(kOzSliceThreads)
   }
 }
 
-// Eight accumulator columns of this warp's 32 TMEM lanes (one row per thread).
+// Eight accumulator columns of this warp's 32 TMEM lanes (one row per thread); the caller
+// waits (tcgen05.wait::ld) before using them.
 __device__ __forceinline__ void oz_tmem_load8(uint32_t addr, uint32_t (&r)[8]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7])
       : "r"(addr));
+}
+
+__device__ __forceinline__ void oz_tmem_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -221,6 +225,18 @@ __device__ __forceinline__ void oz_tmem_load8(uint32_t addr, uint32_t (&r)[8]) {
 __device__ __forceinline__ int32_t oz_int(uint32_t f) {
   return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
 }
+
+// Four diagonals D_d .. D_d+3 of eight columns -> sum_j D_(d+j) 2^(7(3-j)) (< 2^44 in
+// magnitude): two int32 Horner steps, one 64-bit combination.
+__device__ __forceinline__ void oz_combine4(const uint32_t (&v)[4][8], long long (&out)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int hi = oz_int(v[0][j]) * 128 + oz_int(v[1][j]);  // |.| < 2^30
+    const int lo = oz_int(v[2][j]) * 128 + oz_int(v[3][j]);
+    out[j] = (long long)hi * (1ll << 14) + lo;
+  }
+}
+
 
 // W 2^E as a double, rounded to nearest (ties to even), with integer operations only (the
 // FP64 pipe is the scarce unit); results outside the normal range go through ldexp.
@@ -292,7 +308,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = oz_idesc();
+  // N = 64, 128, 192, 256: one MMA covers up to 4 consecutive B slices
+  const uint32_t idesc[4] = {oz_idesc(kOzN), oz_idesc(2 * kOzN), oz_idesc(3 * kOzN),
+                             oz_idesc(4 * kOzN)};
   const uint64_t da0 = oz_desc(smem_u32(A)), db0 = oz_desc(smem_u32(B));
   // thread 0 only: the load barrier's next phase, and what is in flight
   uint32_t ld_phase = 0;
@@ -316,20 +334,26 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     ld_parity = ld_phase;
   };
   // thread 0: wait for the operands, then D_{p+q} (+)= S_p S_q^T for every slice pair
-  // p + q < kOzSlices; a K step of 16 bf16 advances both descriptors by 32 bytes (2 in the
-  // address field).  Returns false if the wait gave up.
+  // p + q < kOzSlices.  The B slices lie one after another in shared memory, so one MMA of
+  // S_p against slices q0 .. q0+3 (N up to 256) writes the accumulators of the diagonals
+  // p+q0 .. p+q0+3 when its TMEM address starts at diagonal p + q0: 12 MMAs per K step
+  // instead of 36 (the issue rate of a single thread, not the tensor cores, bounds small
+  // MMAs).  A K step of 16 bf16 advances both descriptors by 32 bytes (2 in the address
+  // field).  Returns false if the wait gave up.
   auto load_and_mma = [&](int ksteps) -> bool {
     if (!oz_wait(bld, ld_phase)) return false;
     ld_phase ^= 1;
     ld_inflight = false;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    for (int p = 0; p < kOzSlices; p++)
-      for (int q = 0; p + q < kOzSlices; q++)
-        for (int ks = 0; ks < ksteps; ks++)
-          oz_mma(tmem + (uint32_t)((p + q) * kOzN),
+    for (int ks = 0; ks < ksteps; ks++)
+      for (int p = 0; p < kOzSlices; p++)
+        for (int q0 = 0; p + q0 < kOzSlices; q0 += 4) {
+          const int nq = min(4, kOzSlices - p - q0);
+          oz_mma(tmem + (uint32_t)((p + q0) * kOzN),
                  da0 + (uint64_t)((p * kOzASlice) >> 4) + 2 * ks,
-                 db0 + (uint64_t)((q * kOzBSlice) >> 4) + 2 * ks, idesc,
+                 db0 + (uint64_t)((q0 * kOzBSlice) >> 4) + 2 * ks, idesc[nq - 1],
                  (p > 0 || ks > 0) ? 1u : 0u);
+        }
     oz_commit(bmma);
     mma_inflight = true;
     mma_parity = mma_phase;
@@ -433,19 +457,21 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 #pragma unroll
       for (int cc = 0; cc < 2; cc++) {
         long long vh[8], vl[8];
-#pragma unroll
-        for (int j = 0; j < 8; j++) vh[j] = vl[j] = 0;
         const uint32_t ta =
             tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 8 * cc);
+        {
+          uint32_t v[4][8];
 #pragma unroll
-        for (int dd = 0; dd < kOzSlices; dd++) {
-          uint32_t v[8];
-          oz_tmem_load8(ta + (uint32_t)(dd * kOzN), v);
+          for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)(dd * kOzN), v[dd]);
+          oz_tmem_wait();
+          oz_combine4(v, vh);
+        }
+        {
+          uint32_t v[4][8];
 #pragma unroll
-          for (int j = 0; j < 8; j++) {
-            if (dd < 4) vh[j] = vh[j] * 128 + oz_int(v[j]);
-            else vl[j] = vl[j] * 128 + oz_int(v[j]);
-          }
+          for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)((4 + dd) * kOzN), v[dd]);
+          oz_tmem_wait();
+          oz_combine4(v, vl);
         }
 #pragma unroll
         for (int j = 0; j < 8; j++)
