@@ -39,13 +39,10 @@ constexpr int kOzM = 128;                                  // tile rows (UMMA M)
 constexpr int kOzN = 64;                                   // columns per half (UMMA N)
 constexpr uint32_t kOzASlice = kOzM * kOzRowBytes;         // 16 KB
 constexpr uint32_t kOzBSlice = kOzN * kOzRowBytes;         // 8 KB
-constexpr int kOzQ = 32;                                   // columns per quarter
-constexpr uint32_t kOzQSlice = kOzQ * kOzRowBytes;         // 4 KB: one slice of a quarter
-constexpr uint32_t kOzQBytes = kOzSlices * kOzQSlice;      // 32 KB: a quarter's B operand
-constexpr int kOzSetCols = kOzSlices * kOzQ;               // 256: TMEM columns of a set
 constexpr uint32_t kOzABytes = kOzSlices * kOzASlice;      // 128 KB
-constexpr size_t kOzSmem = 1024 + kOzABytes + 2 * kOzQBytes;  // + alignment slack
-constexpr uint32_t kOzTmemCols = 2 * kOzSetCols;          // 512: two sets of 8 diagonals
+constexpr uint32_t kOzBBytes = kOzSlices * kOzBSlice;      // 64 KB
+constexpr size_t kOzSmem = 1024 + kOzABytes + kOzBBytes;   // + alignment slack
+constexpr uint32_t kOzTmemCols = kOzSlices * kOzN;         // 512: one accumulator per diagonal
 constexpr long long kOzSpinLimit = 1ll << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -285,14 +282,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   extern __shared__ __align__(1024) unsigned char oz_sm[];
   unsigned char* A =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz_sm) + 1023) & ~uintptr_t(1023));
-  unsigned char* Bq[2] = {A + kOzABytes, A + kOzABytes + kOzQBytes};  // quarter buffers
-  __shared__ __align__(8) uint64_t bar_a, bar_b[2], bar_mma;
+  unsigned char* B = A + kOzABytes;
+  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
   __shared__ uint32_t tmem_base;
   __shared__ OzMeta meta[2];
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t ba = smem_u32(&bar_a), bmma = smem_u32(&bar_mma);
-  const uint32_t bb[2] = {smem_u32(&bar_b[0]), smem_u32(&bar_b[1])};
+  const uint32_t bld = smem_u32(&bar_ld), bmma = smem_u32(&bar_mma);
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
   const int32_t* exps = reinterpret_cast<const int32_t*>(oz + kOzSlices * stride);
 
@@ -304,9 +300,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   }
   if (tid == 0) {
     s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ba));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bb[0]));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bb[1]));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bld));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bmma));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -314,87 +308,73 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  // N = (8 - p) x 32: the MMA of slice p against slices 0 .. 7-p of a quarter
-  uint32_t idesc[kOzSlices];
-#pragma unroll
-  for (int p = 0; p < kOzSlices; p++) idesc[p] = oz_idesc((kOzSlices - p) * kOzQ);
-  const uint64_t da0 = oz_desc(smem_u32(A));
-  const uint64_t db0[2] = {oz_desc(smem_u32(Bq[0])), oz_desc(smem_u32(Bq[1]))};
-  // thread 0 only: next phase parity of the load barriers, and what is in flight
-  uint32_t a_phase = 0, b_phase[2] = {0, 0};
-  bool a_inflight = false, b_inflight[2] = {false, false}, mma_inflight = false;
-  uint32_t a_parity = 0, b_parity[2] = {0, 0}, mma_parity = 0;
+  // N = 64, 128, 192, 256: one MMA covers up to 4 consecutive B slices
+  const uint32_t idesc[4] = {oz_idesc(kOzN), oz_idesc(2 * kOzN), oz_idesc(3 * kOzN),
+                             oz_idesc(4 * kOzN)};
+  const uint64_t da0 = oz_desc(smem_u32(A)), db0 = oz_desc(smem_u32(B));
+  // thread 0 only: the load barrier's next phase, and what is in flight
+  uint32_t ld_phase = 0;
+  bool ld_inflight = false, mma_inflight = false;
+  uint32_t ld_parity = 0, mma_parity = 0;
   uint32_t mma_phase = 0;  // every thread: parity of the next MMA commit
 
-  auto load_a = [&](const int4& t) {
-    oz_expect(ba, kOzABytes);
+  // thread 0: bulk copies of a task's A slices and of one half's B slices
+  auto issue_loads = [&](const int4& t, int h, bool with_a) {
+    const uint32_t bytes = (with_a ? kOzABytes : 0u) + kOzBBytes;
+    oz_expect(bld, bytes);
+    if (with_a)
+      for (int p = 0; p < kOzSlices; p++)
+        oz_bulk_load(smem_u32(A + p * kOzASlice),
+                     oz + p * stride + (size_t)(t.w + t.y) * kOzRowBytes, kOzASlice, bld);
     for (int p = 0; p < kOzSlices; p++)
-      oz_bulk_load(smem_u32(A + p * kOzASlice),
-                   oz + p * stride + (size_t)(t.w + t.y) * kOzRowBytes, kOzASlice, ba);
-    a_inflight = true;
-    a_parity = a_phase;
+      oz_bulk_load(smem_u32(B + p * kOzBSlice),
+                   oz + p * stride + (size_t)(t.w + t.z + kOzN * h) * kOzRowBytes, kOzBSlice,
+                   bld);
+    ld_inflight = true;
+    ld_parity = ld_phase;
   };
-  // the 32 B rows of quarter j of task t, every slice, into buffer b
-  auto load_b = [&](const int4& t, int j, int b) {
-    oz_expect(bb[b], kOzQBytes);
-    for (int p = 0; p < kOzSlices; p++)
-      oz_bulk_load(smem_u32(Bq[b] + p * kOzQSlice),
-                   oz + p * stride + (size_t)(t.w + t.z + kOzQ * j) * kOzRowBytes, kOzQSlice,
-                   bb[b]);
-    b_inflight[b] = true;
-    b_parity[b] = b_phase[b];
-  };
-  auto wait_a = [&]() -> bool {
-    if (!oz_wait(ba, a_phase)) return false;
-    a_phase ^= 1;
-    a_inflight = false;
-    return true;
-  };
-  auto wait_b = [&](int b) -> bool {
-    if (!oz_wait(bb[b], b_phase[b])) return false;
-    b_phase[b] ^= 1;
-    b_inflight[b] = false;
-    return true;
-  };
-  // D_{p+q} (+)= S_p S_q^T for p + q < 8 into TMEM set s (diagonal d at 32 d): one MMA per
-  // slice p against the quarter's slices 0 .. 7-p (contiguous in shared memory) with its
-  // TMEM address at diagonal p; a K step of 16 bf16 advances both descriptors by 32 bytes.
-  auto issue_mma = [&](int ksteps, int b, int set) {
+  // thread 0: wait for the operands, then D_{p+q} (+)= S_p S_q^T for every slice pair
+  // p + q < kOzSlices.  The B slices lie one after another in shared memory, so one MMA of
+  // S_p against slices q0 .. q0+3 (N up to 256) writes the accumulators of the diagonals
+  // p+q0 .. p+q0+3 when its TMEM address starts at diagonal p + q0: 12 MMAs per K step
+  // instead of 36 (the issue rate of a single thread, not the tensor cores, bounds small
+  // MMAs).  A K step of 16 bf16 advances both descriptors by 32 bytes (2 in the address
+  // field).  Returns false if the wait gave up.
+  auto load_and_mma = [&](int ksteps) -> bool {
+    if (!oz_wait(bld, ld_phase)) return false;
+    ld_phase ^= 1;
+    ld_inflight = false;
     asm volatile("tcgen05.fence::after_thread_sync;");
     for (int ks = 0; ks < ksteps; ks++)
-#pragma unroll
       for (int p = 0; p < kOzSlices; p++)
-        oz_mma(tmem + (uint32_t)(set * kOzSetCols + p * kOzQ),
-               da0 + (uint64_t)((p * kOzASlice) >> 4) + 2 * ks, db0[b] + 2 * ks, idesc[p],
-               (p > 0 || ks > 0) ? 1u : 0u);
+        for (int q0 = 0; p + q0 < kOzSlices; q0 += 4) {
+          const int nq = min(4, kOzSlices - p - q0);
+          oz_mma(tmem + (uint32_t)((p + q0) * kOzN),
+                 da0 + (uint64_t)((p * kOzASlice) >> 4) + 2 * ks,
+                 db0 + (uint64_t)((q0 * kOzBSlice) >> 4) + 2 * ks, idesc[nq - 1],
+                 (p > 0 || ks > 0) ? 1u : 0u);
+        }
     oz_commit(bmma);
     mma_inflight = true;
     mma_parity = mma_phase;
-  };
-  auto quarters_of = [&](const int4& t) {
-    const SnDev& dd = sns[t.x];
-    return min(4, (dd.m - dd.n - t.z + kOzQ - 1) / kOzQ);
+    return true;
   };
   auto ksteps_of = [&](const int4& t) { return (sns[t.x].n + 15) >> 4; };
 
   int tq = blockIdx.x;
-  int qg = 0;  // quarters processed by this CTA: buffer and TMEM set parity
   if (tid == 0 && tq < ntasks) {
-    const int4 t0 = tasks[tq];
-    load_a(t0);
-    load_b(t0, 0, 0);
-    if (!wait_a() || !wait_b(0)) s_fail = 1;
-    else issue_mma(ksteps_of(t0), 0, 0);
+    issue_loads(tasks[tq], 0, true);
+    if (!load_and_mma(ksteps_of(tasks[tq]))) s_fail = 1;
   }
   int buf = 0;
   while (tq < ntasks) {
-    // the MMAs of this task's first quarter are running
+    // the first half's MMAs of this task are running
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, u = d.m - n;
     const int i0 = tk.y, k0 = tk.z;
     const int ksteps = (n + 15) >> 4;
-    const int nq = quarters_of(tk);
+    const int nh = (k0 + kOzN < u) ? 2 : 1;
     const int32_t* rows = d.rows + n;
     const MatDev md = mats[d.mat];
     OzMeta& M = meta[buf];
@@ -453,10 +433,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int i = 32 * (warp & 3) + lane;  // this thread's tile row
     const int gi = i0 + i;
     const int eA = M.eA[i];
-    const int c8 = 8 * (warp >> 2);        // this thread's 8 columns of a quarter
+    const int c0 = 16 * (warp >> 2);       // this thread's 16 columns of a half
     bool stop = false;  // s_fail seen right after a barrier: the same in every thread
-    for (int j = 0; j < nq; j++, qg++) {
-      const int set = qg & 1;
+    for (int h = 0; h < nh; h++) {
       if (!oz_wait(bmma, mma_phase)) s_fail = 1;
       else if (tid == 0) mma_inflight = false;
       mma_phase ^= 1;
@@ -466,68 +445,65 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      // thread 0: operands and MMAs of the next quarter (this task's, or the next task's
-      // first) into the other TMEM set, which the previous quarter's drain has released
+      // shared memory is free: start the next operands while the accumulators are read
       if (tid == 0) {
-        const int b = (qg + 1) & 1;
-        bool ok = true;
-        if (j + 1 < nq) {
-          load_b(tk, j + 1, b);
-          ok = wait_b(b);
-          if (ok) issue_mma(ksteps, b, b);
-        } else if (next < ntasks) {
-          const int4 tn = tasks[next];
-          load_a(tn);
-          load_b(tn, 0, b);
-          ok = wait_a() && wait_b(b);
-          if (ok) issue_mma(ksteps_of(tn), b, b);
-        }
-        if (!ok) s_fail = 1;
+        if (h + 1 < nh) issue_loads(tk, h + 1, false);
+        else if (next < ntasks) issue_loads(tasks[next], 0, true);
       }
-      // accumulators of this quarter -> integers -> W = V_hi 2^20 + round(V_lo / 2^8),
+      // accumulators -> integers -> W = V_hi 2^20 + round(V_lo / 2^8), where
       // V_hi = sum_{d<4} D_d 2^(7(3-d)), V_lo = sum_{d>=4} D_d 2^(7(7-d)) (|D_d| < 2^22,
-      // |V_hi| < 2^42, |V_lo| < 2^44): U = W 2^(e_i + e_k - 55)
-      double val[8];
-      {
+      // |V_hi| < 2^42, |V_lo| < 2^44), so U = W 2^(e_i + e_k - 55)
+      double val[16];
+#pragma unroll
+      for (int cc = 0; cc < 2; cc++) {
         long long vh[8], vl[8];
-        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
-                            (uint32_t)(set * kOzSetCols + c8);
+        const uint32_t ta =
+            tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 8 * cc);
         {
           uint32_t v[4][8];
 #pragma unroll
-          for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)(dd * kOzQ), v[dd]);
+          for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)(dd * kOzN), v[dd]);
           oz_tmem_wait();
           oz_combine4(v, vh);
         }
         {
           uint32_t v[4][8];
 #pragma unroll
-          for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)((4 + dd) * kOzQ), v[dd]);
+          for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)((4 + dd) * kOzN), v[dd]);
           oz_tmem_wait();
           oz_combine4(v, vl);
         }
 #pragma unroll
-        for (int jj = 0; jj < 8; jj++)
-          val[jj] = oz_to_double(vh[jj] * (1ll << 20) + ((vl[jj] + 128) >> 8),
-                                 eA + M.eB[kOzQ * j + c8 + jj] - 55);
+        for (int j = 0; j < 8; j++)
+          val[8 * cc + j] = oz_to_double(vh[j] * (1ll << 20) + ((vl[j] + 128) >> 8),
+                                         eA + M.eB[h * kOzN + c0 + 8 * cc + j] - 55);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();  // this TMEM set is free for the quarter after next
-      // scatter this thread's row of the quarter
+      __syncthreads();
+      // tensor memory is free: the next MMAs (this task's second half, or the next task's
+      // first) run during this half's scatter
+      if (tid == 0) {
+        if (h + 1 < nh) {
+          if (!load_and_mma(ksteps)) s_fail = 1;
+        } else if (next < ntasks) {
+          if (!load_and_mma(ksteps_of(tasks[next]))) s_fail = 1;
+        }
+      }
+      // scatter this thread's row of the half
       if (gi < u) {
-        const int kb = kOzQ * j + c8;  // tile column of val[0]
+        const int kb = h * kOzN + c0;  // tile column of val[0]
         if (OWNER) {
           double* U = static_cast<double*>(md.stage) + d.ustage;
 #pragma unroll
-          for (int jj = 0; jj < 8; jj++) {
-            const int gk = k0 + kb + jj;
-            if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = val[jj];
+          for (int j = 0; j < 16; j++) {
+            const int gk = k0 + kb + j;
+            if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = val[j];
           }
         } else {
           const int key = rows[gi];
 #pragma unroll
-          for (int jj = 0; jj < 8; jj++) {
-            const int kk = kb + jj, gk = k0 + kk;
+          for (int j = 0; j < 16; j++) {
+            const int kk = kb + j, gk = k0 + kk;
             if (gk >= u || gk > gi) continue;
             const int r = M.run[kk];
             double* Lt;
@@ -542,7 +518,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
               mt = td.m;
               p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
             }
-            if (p >= 0) atomicAdd(&Lt[(int64_t)M.col[kk] * mt + p], -val[jj]);
+            if (p >= 0) atomicAdd(&Lt[(int64_t)M.col[kk] * mt + p], -val[j]);
           }
         }
       }
@@ -552,14 +528,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     tq = next;
   }
   __syncthreads();
-  if (s_fail && tid == 0 && ntasks > 0)
-    atomicAdd(mats[sns[tasks[min(tq, ntasks - 1)].x].mat].err + 3, 1ull);
+  if (s_fail && tid == 0 && ntasks > 0) atomicAdd(mats[sns[tasks[min(tq, ntasks - 1)].x].mat].err + 3, 1ull);
   // bounded waits for anything still in flight before the memory is released
   if (tid == 0) {
     if (mma_inflight) oz_wait(bmma, mma_parity);
-    if (a_inflight) oz_wait(ba, a_parity);
-    for (int b = 0; b < 2; b++)
-      if (b_inflight[b]) oz_wait(bb[b], b_parity[b]);
+    if (ld_inflight) oz_wait(bld, ld_parity);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
