@@ -100,9 +100,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+KERNEL_SOURCES = ("factor_kernels.cu", "oz_kernels.cu", "tc_kernels.cu", "device_common.cuh",
+                  "chol_internal.h")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the device kernel sources: a stored ncu traffic figure is used only while
+    the kernels it was measured on are unchanged."""
     h = hashlib.sha256()
-    for f in ("factor_kernels.cu",):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2202_09288_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

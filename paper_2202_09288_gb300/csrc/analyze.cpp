@@ -287,6 +287,27 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
     for (int64_t k = 0; k < b - a; k++) S->flops_panel += (double)(m - k) * (double)(m - k);
   }
   S->l_storage = S->sn_valptr[ns];
+  // runs of each supernode's off-diagonal rows by target supernode (the relative map's
+  // index; the map itself is built on the device)
+  S->sn_run0.assign(ns + 1, 0);
+  S->run_a.clear();
+  S->run_t.clear();
+  S->run_base.clear();
+  S->relmap_size = 0;
+  for (int32_t s = 0; s < ns; s++) {
+    const int32_t w = S->sn_start[s + 1] - S->sn_start[s], u = S->sn_m[s] - w;
+    const int32_t* r = S->rows.data() + S->sn_rowptr[s] + w;
+    for (int32_t i = 0; i < u; i++) {
+      const int32_t t = S->col2sn[r[i]];
+      if (i == 0 || t != S->run_t.back() || (int32_t)S->run_t.size() == S->sn_run0[s]) {
+        S->run_a.push_back(i);
+        S->run_t.push_back(t);
+        S->run_base.push_back(S->relmap_size - i);
+        S->relmap_size += u - i;
+      }
+    }
+    S->sn_run0[s + 1] = (int32_t)S->run_a.size();
+  }
   S->sn_parent.assign(ns, -1);
   S->sn_level.assign(ns, 0);
   for (int32_t s = 0; s < ns; s++) {

@@ -123,8 +123,10 @@ void free_devsym(chol_sym* s) {
   if (!s->ctx) return;
   chol_ctx* c = s->ctx;
   DevSym& d = s->dev;
-  void* ptrs[] = {d.rows, d.col2sn, d.amap, d.perm, d.iperm, d.a_colptr, d.a_rowind,
-                  d.csr_ptr, d.csr_col, d.csr_src, d.asm_src, d.fg_ptr, d.fg_row, d.fg_ent};
+  void* ptrs[] = {d.rows,     d.col2sn,   d.amap,   d.perm,    d.iperm,  d.a_colptr,
+                  d.a_rowind, d.csr_ptr,  d.csr_col, d.csr_src, d.asm_src, d.fg_ptr,
+                  d.fg_row,   d.fg_ent,   d.sn_start, d.sn_rowptr, d.sn_run0, d.run_a,
+                  d.run_t,    d.run_base, d.relmap};
   for (void* p : ptrs) dev_free(c, p);
   for (int k = 0; k < chol::kNumTaskKinds; k++) dev_free(c, d.tasks[k]);
   d = DevSym();
@@ -160,6 +162,38 @@ int ensure_uploaded(chol_ctx* c, chol_sym* s) {
       free_devsym(s);
       return rc;
     }
+  // the relative map, built once per pattern on the device
+  unsigned long long* miss = nullptr;
+  if ((rc = upload(c, &d.sn_start, S.sn_start, &acc)) ||
+      (rc = upload(c, &d.sn_rowptr, S.sn_rowptr, &acc)) ||
+      (rc = upload(c, &d.sn_run0, S.sn_run0, &acc)) || (rc = upload(c, &d.run_a, S.run_a, &acc)) ||
+      (rc = upload(c, &d.run_t, S.run_t, &acc)) ||
+      (rc = upload(c, &d.run_base, S.run_base, &acc)) ||
+      (rc = dev_alloc(c, (void**)&d.relmap, (size_t)S.relmap_size * sizeof(int32_t))) ||
+      (rc = dev_alloc(c, (void**)&miss, sizeof(unsigned long long)))) {
+    dev_free(c, miss);
+    free_devsym(s);
+    return rc;
+  }
+  acc += (size_t)S.relmap_size * sizeof(int32_t);
+  unsigned long long hmiss = 0;
+  if (cudaMemsetAsync(miss, 0, sizeof(hmiss), c->stream) != cudaSuccess) rc = CHOL_E_CUDA;
+  if (!rc) {
+    chol::launch_build_relmap(S.ns, d.sn_start, d.sn_rowptr, d.rows, d.sn_run0, d.run_a, d.run_t,
+                              d.run_base, d.relmap, miss, c->stream);
+    if (cudaMemcpyAsync(&hmiss, miss, sizeof(hmiss), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      rc = CHOL_E_CUDA;
+    else if (hmiss)
+      rc = CHOL_E_INVALID;  // rows missing from an ancestor: an inconsistent analysis
+  }
+  dev_free(c, miss);
+  if (rc) {
+    cudaGetLastError();
+    free_devsym(s);
+    return rc;
+  }
   d.bytes = acc;
   d.device = c->opts.device;
   int64_t mb = 0;
@@ -395,8 +429,13 @@ void fill_descriptors(const chol_num* f, int mat, int32_t sn_base, std::vector<S
     d.col0 = S.sn_start[s];
     d.mat = mat;
     d.ustage = S.sn_ustage[s];
+    d.run0 = S.sn_run0[s];
+    d.nrun = S.sn_run0[s + 1] - S.sn_run0[s];
   }
   md->col2sn = sym->dev.col2sn;
+  md->run_a = sym->dev.run_a;
+  md->run_base = sym->dev.run_base;
+  md->relmap = sym->dev.relmap;
   md->sn_base = sn_base;
   md->pad0 = 0;
   md->stage = f->d_stage;
@@ -547,6 +586,8 @@ size_t sym_upload_bytes(const chol_sym* sym) {
              S.asm_src.size() * 4 + S.fg_ptr.size() * 8 + S.fg_row.size() * 4 +
              S.fg_ent.size() * 4;
   for (int k = 0; k < chol::kNumTaskKinds; k++) b += S.tasks[k].size() * 4;
+  b += (size_t)S.relmap_size * 4 + S.run_a.size() * 16 + S.sn_run0.size() * 4 +
+       S.sn_start.size() * 4 + S.sn_rowptr.size() * 8;
   return b + 64 * 16;
 }
 

@@ -59,6 +59,7 @@ struct alignas(16) SnDev {
   int32_t col0;         // first column
   int32_t mat;          // index into the MatDev array
   int64_t ustage;       // owner assembly: offset of U_s in the level staging buffer (-1 none)
+  int32_t run0, nrun;   // target runs of the off-diagonal rows (MatDev::run_a / run_base)
 };
 
 struct alignas(16) MatDev {
@@ -66,6 +67,13 @@ struct alignas(16) MatDev {
   int32_t sn_base;                // index of supernode 0 of this matrix in the SnDev array
   int32_t pad0;
   void* stage;                    // owner assembly: the level staging buffer of this matrix
+  // relative map: the off-diagonal rows of supernode s fall into runs of one target each;
+  // run r starts at row position run_a[r] (0-based among the u off-diagonal rows) and the
+  // position inside the target's row list of off-diagonal row i >= run_a[r] is
+  // relmap[run_base[r] + i] (run_base already has run_a subtracted)
+  const int32_t* run_a;
+  const int64_t* run_base;
+  const int32_t* relmap;
   unsigned long long* err;        // err[0]: smallest failing column + 1 (all ones = none),
                                   // kept by atomicMin;
                                   // err[1]: relative-map misses (internal check, 0 expected)
@@ -116,6 +124,11 @@ struct Sym {
   std::vector<int64_t> task_off[kNumTaskKinds];   // nlev + 1
   // owner assembly: staging offsets of U_s inside its level's buffer, and the size
   int64_t stage_elems = 0;
+  // relative map (see MatDev): runs of each supernode's off-diagonal rows by target,
+  // sn_run0[s] .. sn_run0[s+1]; run_a / run_t / run_base per run; relmap_size entries
+  std::vector<int32_t> sn_run0, run_a, run_t;
+  std::vector<int64_t> run_base;
+  int64_t relmap_size = 0;
   // slice rows of the 128-tile supernodes of each level (rounded up to 8 per supernode),
   // and the largest level's count plus one tile of slack (rows a tile may read past u)
   std::vector<int64_t> lvl_ozrows;

@@ -21,24 +21,21 @@ __device__ __forceinline__ void record_error(const MatDev& md, int col) {
   atomicMin(md.err, (unsigned long long)col + 1ull);
 }
 
-// Position of `key` in the sorted row list of a target supernode, or -1 (and a count in
-// err[1]) if it is missing: the elimination-tree property guarantees it is present, so a
-// miss is an internal inconsistency and the write is skipped rather than misdirected.
-__device__ __forceinline__ int relative_row(const MatDev& md, const int32_t* rows, int m,
-                                            int key) {
-  const int p = lower_bound_dev(rows, m, key);
-  if (p >= m || rows[p] != key) {
-    atomicAdd(md.err + 1, 1ull);
-    return -1;
+// Index of the target run of supernode d that holds its off-diagonal row position pos
+// (runs start at increasing positions, the first at 0).
+__device__ __forceinline__ int find_run(const MatDev& md, const SnDev& d, int pos) {
+  int lo = d.run0, hi = d.run0 + d.nrun - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (md.run_a[mid] <= pos) lo = mid; else hi = mid - 1;
   }
-  return p;
+  return lo;
 }
 
 // Applies a finished T x T tile of U_s (in shared memory, Cs[kk * (TILE + 1) + ii], rows
 // i0 + ii and columns k0 + kk of the off-diagonal part of s): each entry U(i, k), i >= k,
 // is subtracted from the target panel t owning column rows[k] -- column rows[k] - col0(t),
-// row position of rows[i] inside t's row list (the relative map, found by binary search in
-// t's sorted rows once per tile row and target).
+// row position of rows[i] inside t's row list (the relative map built once per pattern).
 //   OWNER == false: atomicAdd into the panel.
 //   OWNER == true : the tile is written to the level staging buffer (U_s column-major,
 //                   ld u) and k_assemble_owner applies it later in a fixed order.
@@ -52,6 +49,7 @@ __device__ __forceinline__ void schur_tile_epilogue(const T* Cs, const SnDev& d,
   __shared__ int tcol[TILE];                 // target supernode of every tile column
   __shared__ int run_start[TILE + 1];
   __shared__ int run_t[TILE];
+  __shared__ long long run_rb[TILE];         // relative-map base of every run
   __shared__ int nruns;
   __shared__ int relpos[RB][TILE];
   const int tid = threadIdx.x;
@@ -83,6 +81,7 @@ __device__ __forceinline__ void schur_tile_epilogue(const T* Cs, const SnDev& d,
         const int q = nr + __popc(b & ((1u << tid) - 1u));
         run_start[q] = kk;
         run_t[q] = tcol[kk];
+        run_rb[q] = md.run_base[find_run(md, d, k0 + kk)];
       }
       nr += __popc(b);
     }
@@ -93,21 +92,15 @@ __device__ __forceinline__ void schur_tile_epilogue(const T* Cs, const SnDev& d,
   }
   __syncthreads();
   for (int r0 = 0; r0 < nruns; r0 += RB) {
-    // relative map of the tile rows inside each target's rows (rows at or below the run's
-    // first column row are all present in the target, by the elimination-tree property)
+    // positions of the tile rows inside each target's rows, from the relative map (rows at
+    // or below the run's first column row are all present in the target, by the
+    // elimination-tree property)
     for (int idx = tid; idx < RB * TILE; idx += THREADS) {
       const int rr = idx / TILE, ii = idx - rr * TILE;
       const int r = r0 + rr;
       if (r < nruns && ii < ilim) {
         const int gi = i0 + ii;
-        int p = -1;
-        if (gi >= k0 + run_start[r]) {
-          const SnDev& td = sns[md.sn_base + run_t[r]];
-          const int key = rows[gi];
-          // rows inside the target's own columns sit at key - col0
-          p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
-        }
-        relpos[rr][ii] = p;
+        relpos[rr][ii] = gi >= k0 + run_start[r] ? md.relmap[run_rb[r] + gi] : -1;
       }
     }
     __syncthreads();

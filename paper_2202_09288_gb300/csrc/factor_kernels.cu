@@ -504,11 +504,11 @@ __global__ void __launch_bounds__(kAsmThreads)
       const int u = sd.m - sd.n;
       const int32_t* rows = sd.rows + sd.n;
       const T* U = static_cast<const T*>(md.stage) + sd.ustage;
+      const long long rb = md.run_base[find_run(md, sd, sr.y)];
       for (int ib = sr.y; ib < u; ib += kAsmRowChunk) {
         const int ilen = min(kAsmRowChunk, u - ib);
         __syncthreads();
-        for (int ii = threadIdx.x; ii < ilen; ii += blockDim.x)
-          relpos[ii] = relative_row(md, td.rows, td.m, rows[ib + ii]);
+        for (int ii = threadIdx.x; ii < ilen; ii += blockDim.x) relpos[ii] = md.relmap[rb + ib + ii];
         __syncthreads();
         const int kw = sr.z - sr.y;
         for (int idx = threadIdx.x; idx < kw * ilen; idx += blockDim.x) {
@@ -529,6 +529,53 @@ __global__ void __launch_bounds__(kAsmThreads)
     __syncthreads();
     tq = s_next_task;
   }
+}
+
+// ---- relative map -------------------------------------------------------------------------
+// One CTA per supernode s: for every target run q of s (rows from run_a[q] on belong to the
+// run's target t or to later targets, all of them rows of t by the elimination-tree
+// property) the position of each row inside t's sorted row list; a row missing from t (an
+// internal inconsistency) is stored as -1 and counted in *miss.
+__global__ void k_build_relmap(const int32_t* __restrict__ sn_start, const int64_t* __restrict__ sn_rowptr,
+                               const int32_t* __restrict__ rows, const int32_t* __restrict__ sn_run0,
+                               const int32_t* __restrict__ run_a, const int32_t* __restrict__ run_t,
+                               const int64_t* __restrict__ run_base, int32_t* __restrict__ relmap,
+                               unsigned long long* __restrict__ miss) {
+  const int s = blockIdx.x;
+  const int n = sn_start[s + 1] - sn_start[s];
+  const int64_t rp = sn_rowptr[s];
+  const int u = (int)(sn_rowptr[s + 1] - rp) - n;
+  const int32_t* r = rows + rp + n;
+  for (int q = sn_run0[s]; q < sn_run0[s + 1]; q++) {
+    const int t = run_t[q];
+    const int tn = sn_start[t + 1] - sn_start[t], tcol0 = sn_start[t];
+    const int64_t trp = sn_rowptr[t];
+    const int tm = (int)(sn_rowptr[t + 1] - trp);
+    const int32_t* tr = rows + trp;
+    for (int i = run_a[q] + threadIdx.x; i < u; i += blockDim.x) {
+      const int key = r[i];
+      int p;
+      if (key - tcol0 < tn) {
+        p = key - tcol0;  // one of t's own columns
+      } else {
+        p = lower_bound_dev(tr, tm, key);
+        if (p >= tm || tr[p] != key) {
+          p = -1;
+          atomicAdd(miss, 1ull);
+        }
+      }
+      relmap[run_base[q] + i] = p;
+    }
+  }
+}
+
+void launch_build_relmap(int32_t ns, const int32_t* sn_start, const int64_t* sn_rowptr,
+                         const int32_t* rows, const int32_t* sn_run0, const int32_t* run_a,
+                         const int32_t* run_t, const int64_t* run_base, int32_t* relmap,
+                         unsigned long long* miss, cudaStream_t st) {
+  if (ns <= 0) return;
+  k_build_relmap<<<ns, 256, 0, st>>>(sn_start, sn_rowptr, rows, sn_run0, run_a, run_t, run_base,
+                                     relmap, miss);
 }
 
 // ---- launchers --------------------------------------------------------------------------------

@@ -21,6 +21,11 @@ void launch_schur(int cls, const int4* tasks, int ntasks, int* queue, const SnDe
 void launch_assemble_owner(const int4* groups, int ngroups, int* queue, const int4* srcs,
                            const SnDev* sns, const MatDev* mats, bool f32, cudaStream_t st);
 int set_factor_kernel_attrs(int max_width);
+// The relative map of a pattern (MatDev::relmap), one CTA per supernode; misses counted.
+void launch_build_relmap(int32_t ns, const int32_t* sn_start, const int64_t* sn_rowptr,
+                         const int32_t* rows, const int32_t* sn_run0, const int32_t* run_a,
+                         const int32_t* run_t, const int64_t* run_base, int32_t* relmap,
+                         unsigned long long* miss, cudaStream_t st);
 // 128 x 128 FP32 Schur tiles on the tcgen05 tensor cores (3xTF32), tc_kernels.cu.
 void launch_schur_tc(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                      const MatDev* mats, bool owner, cudaStream_t st);

@@ -270,6 +270,7 @@ struct OzMeta {
   int run_start[2 * kOzN + 1];
   double* rL[kOzMaxRuns];
   int rm[kOzMaxRuns];
+  long long rb[2 * kOzN];  // relative-map base of every run
   int rp[kOzMaxRuns][kOzM];
   int nruns, next;
 };
@@ -406,6 +407,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           const int kb = M.run_start[r];
           const int ke = r + 1 < nr ? M.run_start[r + 1] : min(2 * kOzN, u - k0);
           const SnDev& td = sns[md.sn_base + M.tcol[kb]];
+          M.rb[r] = md.run_base[find_run(md, d, k0 + kb)];
           if (r < kOzMaxRuns) {
             M.rL[r] = reinterpret_cast<double*>(td.L);
             M.rm[r] = td.m;
@@ -420,13 +422,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int nrc = min(M.nruns, kOzMaxRuns);
       for (int idx = tid; idx < nrc * kOzM; idx += kOzThreads) {
         const int r = idx / kOzM, i = idx - r * kOzM, gi = i0 + i;
-        int p = -1;
-        if (gi < u && gi >= k0 + M.run_start[r]) {
-          const SnDev& td = sns[md.sn_base + M.tcol[M.run_start[r]]];
-          const int key = rows[gi];
-          p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
-        }
-        M.rp[r][i] = p;
+        M.rp[r][i] = (gi < u && gi >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + gi] : -1;
       }
     }
     const int next = M.next;
@@ -500,7 +496,6 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = val[j];
           }
         } else {
-          const int key = rows[gi];
 #pragma unroll
           for (int j = 0; j < 16; j++) {
             const int kk = kb + j, gk = k0 + kk;
@@ -512,11 +507,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
               Lt = M.rL[r];
               mt = M.rm[r];
               p = M.rp[r][i];
-            } else {  // beyond the cached targets: look the row up here
+            } else {  // beyond the cached targets: read the relative map here
               const SnDev& td = sns[md.sn_base + M.tcol[kk]];
               Lt = reinterpret_cast<double*>(td.L);
               mt = td.m;
-              p = (key - td.col0 < td.n) ? key - td.col0 : relative_row(md, td.rows, td.m, key);
+              p = md.relmap[M.rb[r] + gi];
             }
             if (p >= 0) atomicAdd(&Lt[(int64_t)M.col[kk] * mt + p], -val[j]);
           }

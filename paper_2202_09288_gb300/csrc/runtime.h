@@ -79,6 +79,14 @@ struct DevSym {
   int64_t* fg_ptr = nullptr;
   int32_t* fg_row = nullptr;
   int32_t* fg_ent = nullptr;
+  // relative map (MatDev::relmap) and the arrays it is built from
+  int32_t* sn_start = nullptr;
+  int64_t* sn_rowptr = nullptr;
+  int32_t* sn_run0 = nullptr;
+  int32_t* run_a = nullptr;
+  int32_t* run_t = nullptr;
+  int64_t* run_base = nullptr;
+  int32_t* relmap = nullptr;
   size_t bytes = 0;
 };
 
