@@ -233,7 +233,7 @@ __device__ __forceinline__ void oz_combine4(const uint32_t (&v)[4][8], long long
   for (int j = 0; j < 8; j++) {
     const int hi = oz_int(v[0][j]) * 128 + oz_int(v[1][j]);  // |.| < 2^30
     const int lo = oz_int(v[2][j]) * 128 + oz_int(v[3][j]);
-    out[j] = (long long)hi * (1ll << 14) + lo;
+    out[j] = (long long)((unsigned long long)(long long)hi << 14) + lo;  // hi 2^14 + lo
   }
 }
 
@@ -471,7 +471,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         }
 #pragma unroll
         for (int j = 0; j < 8; j++)
-          val[8 * cc + j] = oz_to_double(vh[j] * (1ll << 20) + ((vl[j] + 128) >> 8),
+          val[8 * cc + j] = oz_to_double((long long)((unsigned long long)vh[j] << 20) +
+                                             ((vl[j] + 128) >> 8),
                                          eA + M.eB[h * kOzN + c0 + 8 * cc + j] - 55);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
