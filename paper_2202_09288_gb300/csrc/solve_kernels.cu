@@ -53,7 +53,6 @@ __global__ void k_scatter_perm(const double* __restrict__ w, const int32_t* __re
 }
 
 constexpr int kSolveThreads = kSolveRows;  // one off-diagonal row per thread
-constexpr int kRhsChunk = 8;
 
 // Warp-level triangular solve of the n x n lower L11 (smem, column-major ld n) against
 // xs (smem, n x nrhs, ld n).  Forward: xs <- L11^{-1} xs.  Backward: xs <- L11^{-T} xs.
@@ -61,7 +60,9 @@ constexpr int kRhsChunk = 8;
 template <bool FORWARD, typename CT>
 __device__ void warp_trisolve(const CT* L11, const CT* rdiag, CT* xs, int n, int nrhs) {
   const int lane = threadIdx.x & 31;
-  for (int c = 0; c < nrhs; c++) {
+  // the CTA's warps share the right-hand sides: warp w solves columns w, w + nwarps, ...
+  const int nwarps = blockDim.x >> 5;
+  for (int c = threadIdx.x >> 5; c < nrhs; c += nwarps) {
     CT v[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
@@ -110,7 +111,7 @@ __device__ void load_l11(const SnDev& d, P* L11, P* rdiag) {
 
 // smem: L11 n*n, rdiag n, xs n*nrhs.  STAGE: the off-diagonal products go to the level's
 // staging slots (q * kSolveRows + ii) * nrhs + c instead of atomics into y.
-template <typename P, bool STAGE>
+template <typename P, bool STAGE, int NR>
 __global__ void __launch_bounds__(kSolveThreads)
     k_fwd(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue, const SnDev* __restrict__ sns, int64_t ldv, int nrhs,
           double* __restrict__ y, double* __restrict__ w, double* __restrict__ fstage) {
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(kSolveThreads)
       xs[idx] = (P)y[c * ldv + d.col0 + j];
     }
     load_l11<P>(d, L11, rdiag);
-    if (threadIdx.x < 32) warp_trisolve<true>(L11, rdiag, xs, n, nrhs);
+    warp_trisolve<true>(L11, rdiag, xs, n, nrhs);
     __syncthreads();
     if (tk.y == 0)
       for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
@@ -140,18 +141,19 @@ __global__ void __launch_bounds__(kSolveThreads)
     if (i < u) {
       const P* L = reinterpret_cast<const P*>(d.L) + n + i;
       const int64_t grow = d.rows[n + i];
-      for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
-        P acc[kRhsChunk];
+      // NR (>= nrhs) right-hand sides per pass: each panel entry is read once
+      for (int c0 = 0; c0 < nrhs; c0 += NR) {
+        P acc[NR];
   #pragma unroll
-        for (int c = 0; c < kRhsChunk; c++) acc[c] = P(0);
+        for (int c = 0; c < NR; c++) acc[c] = P(0);
         for (int j = 0; j < n; j++) {
           const P l = L[(int64_t)j * m];
   #pragma unroll
-          for (int c = 0; c < kRhsChunk; c++)
+          for (int c = 0; c < NR; c++)
             if (c0 + c < nrhs) acc[c] += l * xs[(c0 + c) * n + j];
         }
   #pragma unroll
-        for (int c = 0; c < kRhsChunk; c++) {
+        for (int c = 0; c < NR; c++) {
           if (c0 + c >= nrhs) continue;
           if (STAGE)
             fstage[((int64_t)tq * kSolveRows + threadIdx.x) * nrhs + c0 + c] = (double)acc[c];
@@ -186,8 +188,11 @@ __global__ void k_fwd_gather(const int32_t* __restrict__ fg_row, const int64_t* 
   }
 }
 
-// Backward partials: the level's task q = blockIdx.x writes part[q * W * nrhs + c * W + j].
-template <typename P>
+// Backward partials: the level's task q writes part[q * W * nrhs + c * W + j] =
+// sum_{i in block} L21[i, j] x[rows[n + i], c].  Column j is read once for all NR (>= nrhs)
+// right-hand sides: for n <= 64 two threads share a column (halves of the block's rows,
+// combined through shared memory), otherwise one thread per column.
+template <typename P, int NR>
 __global__ void __launch_bounds__(kSolveThreads)
     k_bwd_partial(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue, const SnDev* __restrict__ sns,
                   int64_t ldv, int nrhs, int W, const double* __restrict__ w,
@@ -199,20 +204,41 @@ __global__ void __launch_bounds__(kSolveThreads)
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
     const int rb = min(kSolveRows, u - tk.y);
-    P* xg = reinterpret_cast<P*>(sm);  // rb x nrhs
+    P* xg = reinterpret_cast<P*>(sm);       // rb x nrhs
+    P* red = xg + kSolveRows * NR;          // n x nrhs partial sums of the second half
     for (int idx = threadIdx.x; idx < rb * nrhs; idx += blockDim.x) {
       const int c = idx / rb, i = idx - c * rb;
       xg[idx] = (P)w[c * ldv + d.rows[n + tk.y + i]];
     }
     __syncthreads();
     double* out = part + (int64_t)tq * W * nrhs;
-    const P* L = reinterpret_cast<const P*>(d.L) + n + tk.y;
-    for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
-      const int c = idx / n, j = idx - c * n;
-      P acc = P(0);
-      const P* col = L + (int64_t)j * m;
-      for (int i = 0; i < rb; i++) acc += col[i] * xg[c * rb + i];
-      out[c * W + j] = (double)acc;
+    const bool two = n <= kSolveThreads / 2;
+    const int j = two ? (threadIdx.x % (kSolveThreads / 2)) : threadIdx.x;
+    const int h = two ? threadIdx.x / (kSolveThreads / 2) : 0;
+    const int half = two ? (rb + 1) / 2 : rb;
+    const int ib = h * half, ie = min(rb, ib + half);
+    P acc[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) acc[c] = P(0);
+    if (j < n) {
+      const P* col = reinterpret_cast<const P*>(d.L) + (int64_t)j * m + n + tk.y;
+      for (int i = ib; i < ie; i++) {
+        const P l = col[i];
+#pragma unroll
+        for (int c = 0; c < NR; c++)
+          if (c < nrhs) acc[c] += l * xg[c * rb + i];
+      }
+    }
+    if (two && h == 1 && j < n) {
+#pragma unroll
+      for (int c = 0; c < NR; c++)
+        if (c < nrhs) red[c * n + j] = acc[c];
+    }
+    __syncthreads();
+    if (h == 0 && j < n) {
+#pragma unroll
+      for (int c = 0; c < NR; c++)
+        if (c < nrhs) out[c * W + j] = (double)(two ? acc[c] + red[c * n + j] : acc[c]);
     }
     __syncthreads();
     // a CTA's first task is its block index; only a grid smaller than the task list makes
@@ -250,7 +276,7 @@ __global__ void __launch_bounds__(kSolveThreads)
       xs[idx] = (P)v;
     }
     load_l11<P>(d, L11, rdiag);
-    if (threadIdx.x < 32) warp_trisolve<false>(L11, rdiag, xs, n, nrhs);
+    warp_trisolve<false>(L11, rdiag, xs, n, nrhs);
     __syncthreads();
     for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
       const int c = idx / n, j = idx - c * n;
@@ -287,16 +313,46 @@ void launch_scatter_perm(const double* w, const int32_t* perm, const double* sca
   k_scatter_perm<<<grid_for(n * nrhs), 256, 0, st>>>(w, perm, scale, n, nrhs, X, ldx);
 }
 
+template <typename P, int NR>
+static void fwd_nr(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int64_t ldv,
+                   int nrhs, int W, double* y, double* w, double* fstage, cudaStream_t st) {
+  const size_t sm = solve_smem(W, nrhs);
+  if (fstage)
+    k_fwd<P, true, NR><<<persistent_grid(k_fwd<P, true, NR>, kSolveThreads, sm, ntasks),
+                         kSolveThreads, sm, st>>>(tasks, ntasks, queue, sns, ldv, nrhs, y, w,
+                                                  fstage);
+  else
+    k_fwd<P, false, NR><<<persistent_grid(k_fwd<P, false, NR>, kSolveThreads, sm, ntasks),
+                          kSolveThreads, sm, st>>>(tasks, ntasks, queue, sns, ldv, nrhs, y, w,
+                                                   nullptr);
+}
+
+// right-hand sides per pass of the panel products: the smallest of 1, 4, 16, 32 >= nrhs
+static inline int rhs_pass(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 4 ? 4 : nrhs <= 16 ? 16 : 32; }
+
 template <typename P>
 static void fwd_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int64_t ldv,
                   int nrhs, int W, double* y, double* w, double* fstage, cudaStream_t st) {
-  const size_t sm = solve_smem(W, nrhs);
-  if (fstage)
-    k_fwd<P, true><<<persistent_grid(k_fwd<P, true>, kSolveThreads, sm, ntasks), kSolveThreads,
-                     sm, st>>>(tasks, ntasks, queue, sns, ldv, nrhs, y, w, fstage);
-  else
-    k_fwd<P, false><<<persistent_grid(k_fwd<P, false>, kSolveThreads, sm, ntasks), kSolveThreads,
-                      sm, st>>>(tasks, ntasks, queue, sns, ldv, nrhs, y, w, nullptr);
+  switch (rhs_pass(nrhs)) {
+    case 1: fwd_nr<P, 1>(tasks, ntasks, queue, sns, ldv, nrhs, W, y, w, fstage, st); break;
+    case 4: fwd_nr<P, 4>(tasks, ntasks, queue, sns, ldv, nrhs, W, y, w, fstage, st); break;
+    case 16: fwd_nr<P, 16>(tasks, ntasks, queue, sns, ldv, nrhs, W, y, w, fstage, st); break;
+    default: fwd_nr<P, 32>(tasks, ntasks, queue, sns, ldv, nrhs, W, y, w, fstage, st); break;
+  }
+}
+
+static inline size_t bwd_partial_smem(int W, int nr) {
+  return ((size_t)kSolveRows * nr + (size_t)W * nr) * sizeof(double);
+}
+
+template <typename P, int NR>
+static void bwd_partial_nr(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
+                           int64_t ldv, int nrhs, int W, const double* w, double* part,
+                           cudaStream_t st) {
+  const size_t sp = bwd_partial_smem(W, NR);
+  k_bwd_partial<P, NR><<<persistent_grid(k_bwd_partial<P, NR>, kSolveThreads, sp, ntasks),
+                         kSolveThreads, sp, st>>>(tasks, ntasks, queue, sns, ldv, nrhs, W, w,
+                                                  part);
 }
 
 void launch_fwd(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int64_t ldv,
@@ -319,9 +375,12 @@ static void bwd_t(const int4* bwd_tasks, int nbwd, int* queues, int64_t bwd_base
                   const int4* diag_tasks, int ndiag, const SnDev* sns, int64_t ldv, int nrhs,
                   int W, double* w, double* part, cudaStream_t st) {
   if (nbwd > 0) {
-    const size_t sp = (size_t)kSolveRows * nrhs * sizeof(double);
-    k_bwd_partial<P><<<persistent_grid(k_bwd_partial<P>, kSolveThreads, sp, nbwd), kSolveThreads,
-                       sp, st>>>(bwd_tasks, nbwd, queues, sns, ldv, nrhs, W, w, part);
+    switch (rhs_pass(nrhs)) {
+      case 1: bwd_partial_nr<P, 1>(bwd_tasks, nbwd, queues, sns, ldv, nrhs, W, w, part, st); break;
+      case 4: bwd_partial_nr<P, 4>(bwd_tasks, nbwd, queues, sns, ldv, nrhs, W, w, part, st); break;
+      case 16: bwd_partial_nr<P, 16>(bwd_tasks, nbwd, queues, sns, ldv, nrhs, W, w, part, st); break;
+      default: bwd_partial_nr<P, 32>(bwd_tasks, nbwd, queues, sns, ldv, nrhs, W, w, part, st); break;
+    }
   }
   if (ndiag > 0) {
     const size_t sm = solve_smem(W, nrhs);
@@ -347,13 +406,23 @@ static bool set_smem(K kernel, size_t bytes) {
          cudaSuccess;
 }
 
+template <typename P, int NR>
+static bool set_solve_nr(size_t sm, size_t sp) {
+  return set_smem(k_fwd<P, false, NR>, sm) && set_smem(k_fwd<P, true, NR>, sm) &&
+         set_smem(k_bwd_partial<P, NR>, sp);
+}
+
 int set_solve_kernel_attrs(int W, int max_nrhs) {
   const size_t sm = solve_smem(W, max_nrhs);
-  const size_t sp = (size_t)kSolveRows * max_nrhs * sizeof(double);
-  bool ok = set_smem(k_fwd<double, false>, sm) && set_smem(k_fwd<double, true>, sm) &&
-            set_smem(k_fwd<float, false>, sm) && set_smem(k_fwd<float, true>, sm) &&
-            set_smem(k_bwd_diag<double>, sm) && set_smem(k_bwd_diag<float>, sm) &&
-            set_smem(k_bwd_partial<double>, sp) && set_smem(k_bwd_partial<float>, sp);
+  bool ok = set_smem(k_bwd_diag<double>, sm) && set_smem(k_bwd_diag<float>, sm) &&
+            set_solve_nr<double, 1>(sm, bwd_partial_smem(W, 1)) &&
+            set_solve_nr<double, 4>(sm, bwd_partial_smem(W, 4)) &&
+            set_solve_nr<double, 16>(sm, bwd_partial_smem(W, 16)) &&
+            set_solve_nr<double, 32>(sm, bwd_partial_smem(W, 32)) &&
+            set_solve_nr<float, 1>(sm, bwd_partial_smem(W, 1)) &&
+            set_solve_nr<float, 4>(sm, bwd_partial_smem(W, 4)) &&
+            set_solve_nr<float, 16>(sm, bwd_partial_smem(W, 16)) &&
+            set_solve_nr<float, 32>(sm, bwd_partial_smem(W, 32));
   return ok ? CHOL_OK : CHOL_E_CUDA;
 }
 
