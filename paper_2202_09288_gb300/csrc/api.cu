@@ -341,12 +341,14 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
       chol::launch_trsm(t, cnt, q + 1, sns, v.max_width, f32, st);
       prof_end(c, kt, v.flops[chol::kTaskTrsm][l], 0.0);
     }
-    const bool tc64 = !f32 && oz != nullptr;  // FP64 128-tiles on the bf16 tensor cores
-    if (tc64) {
+    // 128-tiles on the tensor cores: FP64 by bf16 slices, FP32 by TF32 hi/lo parts; their
+    // operands are prepared per level after TRSM
+    if (oz) {
       t = v.level(chol::kTaskOzSlice, l, &cnt);
       if (cnt > 0) {
         prof_begin(c);
-        chol::launch_oz_slice(t, cnt, sns, oz, oz_rows, st);
+        if (f32) chol::launch_tf32_split(t, cnt, sns, v.max_width, oz, oz_rows, st);
+        else chol::launch_oz_slice(t, cnt, sns, oz, oz_rows, st);
         prof_end(c, kProfOzSlice, 0.0, 0.0);
       }
     }
@@ -354,11 +356,12 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
       const int kind = chol::schur_kind(cls);
       t = v.level(kind, l, &cnt);
       if (cnt <= 0) continue;
-      const bool ozc = tc64 && cls == chol::kTile128;
+      const bool tcc = oz && cls == chol::kTile128;
       prof_begin(c);
-      if (ozc) chol::launch_schur_oz(t, cnt, q + 2 + cls, sns, mats, owner, oz, oz_rows, st);
+      if (tcc && f32) chol::launch_schur_tc(t, cnt, q + 2 + cls, sns, mats, owner, oz, oz_rows, st);
+      else if (tcc) chol::launch_schur_oz(t, cnt, q + 2 + cls, sns, mats, owner, oz, oz_rows, st);
       else chol::launch_schur(cls, t, cnt, q + 2 + cls, sns, mats, owner, f32, st);
-      prof_end(c, prof_schur_kind(cls, f32, ozc), v.flops[kind][l], 0.0);
+      prof_end(c, prof_schur_kind(cls, f32, tcc && !f32), v.flops[kind][l], 0.0);
     }
     if (owner) {
       t = v.level(chol::kTaskAsm, l, &cnt);
@@ -380,7 +383,9 @@ int ensure_oz(chol_num* f, void** oz, int64_t* rows) {
   *oz = nullptr;
   *rows = 0;
   const Sym& S = f->sym->S;
-  if (f->precision == CHOL_MIXED || !use_oz(f->ctx, f->sym) || S.oz_rows <= 0) return CHOL_OK;
+  // FP64: bf16 slices (W <= 64, unless the DMMA tiles are asked for); FP32: TF32 parts
+  const bool need = f->precision == CHOL_MIXED ? true : use_oz(f->ctx, f->sym);
+  if (!need || S.oz_rows <= 0) return CHOL_OK;
   if (f->oz_cap < S.oz_rows) {
     chol_ctx* c = f->ctx;
     // the stream may still use the old scratch: free it only after the stream drains

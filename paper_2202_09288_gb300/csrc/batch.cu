@@ -147,7 +147,7 @@ int chol_batch_create(chol_ctx* c, int count, chol_num* const* nums, chol_batch*
   }
   // FP64 tensor-core Schur tiles: each member's slice rows of a level follow the previous
   // members' in one batch scratch
-  const bool oz = !b->f32 && use_oz(c, nums[0]->sym);
+  const bool oz = b->f32 || use_oz(c, nums[0]->sym);  // tensor-core 128-tiles need the scratch
   std::vector<int64_t> ozbase(count);
   for (int32_t l = 0; l < b->nlev; l++) {
     int64_t total = 0;

@@ -320,7 +320,7 @@ struct SchurF32Cfg {
 template <int TILE, bool OWNER>
 __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
     k_schur_f32(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue, const SnDev* __restrict__ sns,
-                const MatDev* __restrict__ mats) {
+                const MatDev* __restrict__ mats, int vsplit) {
   using Cfg = SchurF32Cfg<TILE>;
   constexpr int KC = Cfg::KC, LDS = Cfg::LDS, S = Cfg::S;
   __shared__ __align__(16) float sh[2 * KC * LDS > TILE * (TILE + 1) ? 2 * KC * LDS
@@ -328,14 +328,19 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
   float* As = sh;
   float* Bs = sh + KC * LDS;
   __shared__ int s_next_task;
-  for (int tq = blockIdx.x; tq < ntasks;) {
-    const int4 tk = tasks[tq];
+  // with vsplit > 0 every task is 2^vsplit virtual tasks, one per sub-tile
+  const int nv = ntasks << vsplit;
+  for (int tq = blockIdx.x; tq < nv;) {
+    const int4 tk = tasks[tq >> vsplit];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
-    // a task covers a (tk.w x tk.w) block of U_s; blocks larger than this kernel's tile
-    // are done as TILE x TILE sub-tiles, skipping those wholly above the diagonal
-    const int span = tk.w > TILE ? tk.w : TILE;
-    for (int sub = 0; sub < (span / TILE) * (span / TILE); sub++) {
+    // a task covers a (tk.w x tk.w) block of U_s (128 x 128 for the 128 class, whose .w
+    // holds the slice offset instead); blocks larger than this kernel's tile are done as
+    // TILE x TILE sub-tiles, skipping those wholly above the diagonal
+    const int span = vsplit ? TILE << (vsplit >> 1) : (tk.w > TILE ? tk.w : TILE);
+    const int sub_lo = vsplit ? (tq & ((1 << vsplit) - 1)) : 0;
+    const int sub_hi = vsplit ? sub_lo + 1 : (span / TILE) * (span / TILE);
+    for (int sub = sub_lo; sub < sub_hi; sub++) {
     const int i0 = tk.y + (sub / (span / TILE)) * TILE, k0 = tk.z + (sub % (span / TILE)) * TILE;
     if (i0 + TILE - 1 < k0 || i0 >= u || k0 >= u) continue;
     const float* L = reinterpret_cast<const float*>(d.L);
@@ -385,7 +390,7 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
     __syncthreads();
     // a CTA's first task is its block index; only a grid smaller than the task list makes
     // CTAs take further tasks from this launch's work queue
-    if (gridDim.x >= ntasks) break;
+    if (gridDim.x >= nv) break;
     if (threadIdx.x == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
     __syncthreads();
     tq = s_next_task;
@@ -634,17 +639,18 @@ static void schur_f64_t(const int4* tasks, int ntasks, int* queue, const SnDev* 
 
 template <int T, bool OWNER>
 static void schur_f32_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
-                        const MatDev* mats, cudaStream_t st) {
+                        const MatDev* mats, cudaStream_t st, int vsplit = 0) {
   constexpr int th = SchurF32Cfg<T>::THREADS;
-  k_schur_f32<T, OWNER><<<persistent_grid(k_schur_f32<T, OWNER>, th, 0, ntasks), th, 0, st>>>(
-      tasks, ntasks, queue, sns, mats);
+  k_schur_f32<T, OWNER><<<persistent_grid(k_schur_f32<T, OWNER>, th, 0, ntasks << vsplit), th, 0,
+                         st>>>(tasks, ntasks, queue, sns, mats, vsplit);
 }
 
 template <bool OWNER>
 static void schur_cls(int cls, bool f32, const int4* tasks, int ntasks, int* queue,
                       const SnDev* sns, const MatDev* mats, cudaStream_t st) {
   if (f32) {
-    if (cls == kTile128) launch_schur_tc(tasks, ntasks, queue, sns, mats, OWNER, st);
+    // 128-wide tasks without the tensor-core scratch: four 64 x 64 virtual tasks
+    if (cls == kTile128) schur_f32_t<64, OWNER>(tasks, ntasks, queue, sns, mats, st, 2);
     else if (cls == kTile64) schur_f32_t<64, OWNER>(tasks, ntasks, queue, sns, mats, st);
     else if (cls == kTile32) schur_f32_t<32, OWNER>(tasks, ntasks, queue, sns, mats, st);
     else schur_f32_t<16, OWNER>(tasks, ntasks, queue, sns, mats, st);

@@ -26,9 +26,14 @@ void launch_build_relmap(int32_t ns, const int32_t* sn_start, const int64_t* sn_
                          const int32_t* rows, const int32_t* sn_run0, const int32_t* run_a,
                          const int32_t* run_t, const int64_t* run_base, int32_t* relmap,
                          unsigned long long* miss, cudaStream_t st);
-// 128 x 128 FP32 Schur tiles on the tcgen05 tensor cores (3xTF32), tc_kernels.cu.
+// 128 x 128 FP32 Schur tiles on the tcgen05 tensor cores (3xTF32), tc_kernels.cu: per
+// level, the hi/lo TF32 parts of the 128-tile supernodes' L21 (kTaskOzSlice tasks) into the
+// zeroed scratch oz (oz_scratch_bytes(oz_rows)), then the tiles.
+void launch_tf32_split(const int4* tasks, int ntasks, const SnDev* sns, int max_width, void* oz,
+                       int64_t oz_rows, cudaStream_t st);
 void launch_schur_tc(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
-                     const MatDev* mats, bool owner, cudaStream_t st);
+                     const MatDev* mats, bool owner, const void* oz, int64_t oz_rows,
+                     cudaStream_t st);
 int set_tc_kernel_attrs();
 // FP64 128 x 128 Schur tiles on the bf16 tensor cores by operand splitting, oz_kernels.cu:
 // per level, first the slices of every 128-tile supernode's L21 (kTaskOzSlice tasks), then

@@ -1,18 +1,26 @@
 // tc_kernels.cu -- Schur update tiles of the mixed-precision factor on the fifth-generation
-// tensor cores (tcgen05) of sm_103a.
+// tensor cores (tcgen05) of sm_103a: TF32 products accumulated in FP32.
 //
-// A task {s, i0, k0, 128} is the 128 x 128 tile U_s[i0.., k0..] = L21[i0.., :] L21[k0.., :]^T
-// of a supernode's Schur update (the SYRK/GEMM of Sec. 3, Listing 1).  L21 is FP32 and the
-// tile is accumulated in FP32 in tensor memory by tcgen05.mma kind::tf32 with the 3xTF32
-// split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = tf32(a), a_lo = tf32(a - a_hi)),
-// which keeps FP32-level accuracy.  Per K chunk of 32 columns, the CTA's threads stage the
-// four operand tiles (A hi/lo, B hi/lo; 16 KB each) into shared memory in the 128-byte-
-// swizzled K-major layout, one thread issues the MMAs and commits them to an mbarrier, and
-// the CTA waits for it (bounded).  The finished tile is read from tensor memory with
-// tcgen05.ld into shared memory and applied by the common Schur epilogue.
-//
-// Every wait is bounded: after kTcSpinLimit polls the kernel records a timeout in err[3],
-// waits once more (bounded) for its MMAs in flight, frees its tensor memory and returns.
+// A task {s, i0, k0, oz} is the 128 x 128 tile U_s[i0.., k0..] = L21[i0.., :] L21[k0.., :]^T
+// of a supernode's Schur update (the SYRK/GEMM of Sec. 3, Listing 1) on FP32 panels, with
+// the 3xTF32 split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = tf32(a),
+// a_lo = tf32(a - a_hi)), which keeps FP32-level accuracy.  Two kernels per level:
+//   k_tf32_split  the hi and lo parts of every L21 row of the level's 128-tile supernodes,
+//                 in planes (part, 32-column chunk) of 128-byte rows whose 16-byte pieces
+//                 are pre-swizzled for the tensor cores' 128-byte swizzle;
+//   k_schur_tf32  a persistent CTA per SM.  One producer thread (its own warp) streams each
+//                 task's operand chunks (A hi/lo, B hi/lo: 64 KB) into a 3-stage shared
+//                 memory ring with bulk copies and issues the MMAs (M = N = 128, three per
+//                 K step of 8) into one of four 128-column tensor-memory accumulators;
+//                 16 consumer warps read finished accumulators (tcgen05.ld, one row per
+//                 thread) and scatter them into the ancestors with FP32 atomics (or write
+//                 the owner staging buffer), using the relative map.  Loads, MMAs and the
+//                 scatter of different tasks overlap through mbarriers: stage full/empty,
+//                 accumulator full/empty, and a ring that hands the task sequence to the
+//                 consumers.
+// Every wait is bounded: after kTfSpinLimit polls the thread records a timeout in err[3]
+// and stops; its partners then time out as well, waits for copies and MMAs in flight are
+// bounded too, and the tensor memory is freed before the kernel returns.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -26,14 +34,18 @@ namespace chol {
 
 namespace {
 
-constexpr int kTc = 128;             // tile edge: UMMA M = N = 128, cta_group::1
-constexpr int kTcK = 32;             // K columns staged per chunk (128 bytes of FP32 per row)
-constexpr int kTcThreads = 128;
-constexpr uint32_t kTcOperandBytes = kTc * kTcK * 4;             // 16 KB
-constexpr uint32_t kTcCsBytes = kTc * (kTc + 1) * 4;              // epilogue tile
-constexpr uint32_t kTcBody = 4 * kTcOperandBytes > kTcCsBytes ? 4 * kTcOperandBytes : kTcCsBytes;
-constexpr size_t kTcSmem = 1024 + kTcBody;                        // + alignment slack
-constexpr long long kTcSpinLimit = 1ll << 24;
+constexpr int kTfM = 128;                          // tile edge (UMMA M = N = 128)
+constexpr int kTfChunk = 32;                       // K columns per chunk: 128 B of FP32
+constexpr uint32_t kTfPlane = kTfM * kOzRowBytes;  // 16 KB: 128 rows of one (part, chunk)
+constexpr int kTfStages = 3;
+constexpr uint32_t kTfStageBytes = 4 * kTfPlane;   // A hi, A lo, B hi, B lo of one chunk
+constexpr size_t kTfSmem = 1024 + kTfStages * kTfStageBytes;
+constexpr int kTfSlots = 4;                        // accumulators of 128 TMEM columns
+constexpr int kTfConsumers = 512;                  // 16 warps: drain + scatter
+constexpr int kTfThreads = kTfConsumers + 32;      // + the producer warp
+constexpr int kTfRing = 16;
+constexpr int kTfMaxRuns = 16;
+constexpr long long kTfSpinLimit = 1ll << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -45,18 +57,9 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// Byte offset of element (row r, column k) of a 128 x 32 FP32 operand tile in the K-major
-// layout with 128-byte swizzle: rows are 128 bytes, 8-row groups 1024 bytes apart, and the
-// 16-byte chunk index within a row is XORed with the row index modulo 8.
-__device__ __forceinline__ uint32_t swz(int r, int k) {
-  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) +
-                    (k & 3) * 4);
-}
-
-// Shared-memory matrix descriptor: start address, leading byte offset (unused by swizzled
-// K-major layouts), stride byte offset 1024 between 8-row groups, descriptor version 1,
-// swizzle mode 128B.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: 8-row groups 1024 bytes
+// apart, descriptor version 1, leading byte offset unused (16).
+__device__ __forceinline__ uint64_t tf_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);
   d |= (uint64_t)(16 >> 4) << 16;
@@ -66,15 +69,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major,
-// N >> 3 at bit 17, M >> 4 at bit 24.
-__device__ __forceinline__ uint32_t idesc_tf32() {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTc >> 3) << 17) |
-         ((uint32_t)(kTc >> 4) << 24);
+// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B (format 2), both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t tf_idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTfM >> 3) << 17) |
+         ((uint32_t)(kTfM >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kTcSpinLimit; it++) {
+__device__ __forceinline__ bool tf_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < kTfSpinLimit; it++) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -87,16 +90,40 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
+__device__ __forceinline__ void tf_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tf_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tf_bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                             uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tf_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-// 32 consecutive accumulator columns of this warp's 32 TMEM lanes (one row per thread).
-__device__ __forceinline__ void tmem_load32(uint32_t addr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tf_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// 32 accumulator columns of this warp's 32 TMEM lanes (one row per thread).
+__device__ __forceinline__ void tf_tmem_load32(uint32_t addr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
       "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -110,139 +137,350 @@ __device__ __forceinline__ void tmem_load32(uint32_t addr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// barrier among the consumer warps only (the producer warp runs on its own)
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kTfConsumers) : "memory");
+}
+
+struct TfMeta {
+  int tcol[kTfM], run[kTfM], col[kTfM];
+  int run_start[kTfM + 1];
+  long long rb[kTfM];
+  float* rL[kTfMaxRuns];
+  int rm[kTfMaxRuns];
+  int rp[kTfMaxRuns][kTfM];
+  int nruns;
+};
+
 }  // namespace
 
+// hi and lo TF32 parts of the L21 rows r0 .. r0+127 of supernode s at slice rows oz + r:
+// plane (part p, chunk c) at oz + (4 p + c) oz_rows 128 B, 16-byte piece q of a row (its
+// columns 32 c + 4 q .. +3) stored at piece q ^ (row & 7).  Rows u .. roundup(u, 8) and
+// columns n .. are zero.
+__global__ void __launch_bounds__(256)
+    k_tf32_split(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
+                 uint8_t* __restrict__ oz, int64_t oz_rows) {
+  extern __shared__ __align__(16) float xf[];  // [n][kTfM]
+  const int4 tk = tasks[blockIdx.x];
+  const SnDev d = sns[tk.x];
+  const int n = d.n, m = d.m, u = m - n;
+  const int r0 = tk.y;
+  const int rows = min(kTfM, ((u + 7) & ~7) - r0);
+  const int nch = (n + kTfChunk - 1) / kTfChunk;
+  const float* L = reinterpret_cast<const float*>(d.L) + n + r0;
+  for (int idx = threadIdx.x; idx < n * kTfM; idx += blockDim.x) {
+    const int k = idx / kTfM, i = idx - k * kTfM;
+    xf[idx] = (r0 + i < u) ? L[(int64_t)k * m + i] : 0.f;
+  }
+  __syncthreads();
+  const int64_t row0 = tk.z + (int64_t)r0;
+  const size_t stride = (size_t)oz_rows * kOzRowBytes;
+  for (int item = threadIdx.x; item < kTfM * 8 * nch; item += blockDim.x) {
+    const int c = item / (kTfM * 8), rest = item - c * (kTfM * 8);
+    const int i = rest >> 3, pc = rest & 7;  // row, physical 16-byte piece
+    if (i >= rows) continue;
+    const int q = pc ^ (int)((row0 + i) & 7);
+    float hi[4], lo[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int k = kTfChunk * c + 4 * q + j;
+      const float x = k < n ? xf[k * kTfM + i] : 0.f;
+      hi[j] = to_tf32(x);
+      lo[j] = to_tf32(x - hi[j]);
+    }
+    uint8_t* dst = oz + (size_t)(row0 + i) * kOzRowBytes + pc * 16;
+    *reinterpret_cast<float4*>(dst + (size_t)c * stride) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<float4*>(dst + (size_t)(4 + c) * stride) =
+        make_float4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
 template <bool OWNER>
-__global__ void __launch_bounds__(kTcThreads)
-    k_schur_tc(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
-               const SnDev* __restrict__ sns, const MatDev* __restrict__ mats) {
-  extern __shared__ __align__(1024) unsigned char tc_sm[];
-  unsigned char* base =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_sm) + 1023) & ~uintptr_t(1023));
-  unsigned char* Ahi = base;
-  unsigned char* Alo = base + kTcOperandBytes;
-  unsigned char* Bhi = base + 2 * kTcOperandBytes;
-  unsigned char* Blo = base + 3 * kTcOperandBytes;
-  float* Cs = reinterpret_cast<float*>(base);  // reused once the MMAs of a tile are done
-  __shared__ __align__(8) uint64_t mbar;
+__global__ void __launch_bounds__(kTfThreads, 1)
+    k_schur_tf32(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
+                 const SnDev* __restrict__ sns, const MatDev* __restrict__ mats,
+                 const uint8_t* __restrict__ oz, int64_t oz_rows) {
+  extern __shared__ __align__(1024) unsigned char tf_sm[];
+  unsigned char* stage_base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tf_sm) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t st_full[kTfStages], st_empty[kTfStages];
+  __shared__ __align__(8) uint64_t acc_full[kTfSlots], acc_empty[kTfSlots];
+  __shared__ __align__(8) uint64_t ring_full[kTfRing];
+  __shared__ int ring[kTfRing];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_next_task;
+  __shared__ TfMeta meta[2];
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t bar = smem_u32(&mbar);
+  const size_t stride = (size_t)oz_rows * kOzRowBytes;
+
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base)),
-                 "r"(kTc));
+                 "r"(kTfSlots * kTfM));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
     s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    for (int i = 0; i < kTfStages; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&st_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&st_empty[i])));
+    }
+    for (int i = 0; i < kTfSlots; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[i])),
+                   "r"(kTfConsumers / 32));
+    }
+    for (int i = 0; i < kTfRing; i++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ring_full[i])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_tf32();
-  uint32_t phase = 0;
-  bool inflight = false;  // MMAs committed whose completion was not observed
 
-  for (int tq = blockIdx.x; tq < ntasks;) {
-    const int4 tk = tasks[tq];
-    const SnDev d = sns[tk.x];
-    const int n = d.n, m = d.m, u = m - n;
-    const int i0 = tk.y, k0 = tk.z;
-    const float* L = reinterpret_cast<const float*>(d.L);
-    for (int kc = 0; kc < n; kc += kTcK) {
-      const int kw = min(kTcK, n - kc);
-      for (int idx = tid; idx < kTc * kTcK; idx += kTcThreads) {
-        const int r = idx & (kTc - 1), k = idx >> 7;
-        float a = 0.f, b = 0.f;
-        if (k < kw) {
-          const int64_t col = (int64_t)(kc + k) * m + n;
-          if (i0 + r < u) a = L[col + i0 + r];
-          if (k0 + r < u) b = L[col + k0 + r];
+  if (warp == kTfConsumers / 32) {
+    // ---------------- producer: operand loads and MMAs, one thread ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tf_idesc();
+      // chunks whose loads are issued but whose MMAs are not, oldest first: task index,
+      // chunk, chunks of the task, task ordinal (accumulator slot and ring entry)
+      int p_tq[kTfStages], p_c[kTfStages], p_nch[kTfStages], p_ord[kTfStages];
+      int head = 0, npend = 0;
+      long long item = 0;  // chunk loads issued (stage = item % kTfStages)
+      long long done = 0;  // chunks whose MMAs are issued
+      int cur_tq = blockIdx.x, cur_c = 0, cur_nch = 0, ord = 0;
+      bool more = cur_tq < ntasks, ok = true;
+      ring[0] = more ? cur_tq : ntasks;
+      tf_arrive(smem_u32(&ring_full[0]));
+      if (more) cur_nch = (sns[tasks[cur_tq].x].n + kTfChunk - 1) / kTfChunk;
+      while (ok && (more || npend > 0)) {
+        // issue chunk loads up to the ring depth
+        while (more && npend < kTfStages) {
+          const int s = (int)(item % kTfStages);
+          if (item >= kTfStages &&  // the stage's previous MMAs must have read it
+              !tf_wait(smem_u32(&st_empty[s]), (uint32_t)(((item / kTfStages) - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          const int4 t = tasks[cur_tq];
+          unsigned char* sb = stage_base + (size_t)s * kTfStageBytes;
+          const uint32_t bar = smem_u32(&st_full[s]);
+          const uint8_t* arow = oz + (size_t)(t.w + t.y) * kOzRowBytes;
+          const uint8_t* brow = oz + (size_t)(t.w + t.z) * kOzRowBytes;
+          tf_expect(bar, kTfStageBytes);
+          tf_bulk_load(smem_u32(sb), arow + (size_t)cur_c * stride, kTfPlane, bar);
+          tf_bulk_load(smem_u32(sb + kTfPlane), arow + (size_t)(4 + cur_c) * stride, kTfPlane, bar);
+          tf_bulk_load(smem_u32(sb + 2 * kTfPlane), brow + (size_t)cur_c * stride, kTfPlane, bar);
+          tf_bulk_load(smem_u32(sb + 3 * kTfPlane), brow + (size_t)(4 + cur_c) * stride, kTfPlane,
+                       bar);
+          const int slot = (head + npend) % kTfStages;
+          p_tq[slot] = cur_tq;
+          p_c[slot] = cur_c;
+          p_nch[slot] = cur_nch;
+          p_ord[slot] = ord;
+          npend++;
+          item++;
+          // next chunk, or next task (whose index the consumers learn through the ring)
+          if (++cur_c >= cur_nch) {
+            cur_tq = gridDim.x >= ntasks ? ntasks : (int)gridDim.x + atomicAdd(queue, 1);
+            ord++;
+            more = cur_tq < ntasks;
+            ring[ord % kTfRing] = more ? cur_tq : ntasks;
+            tf_arrive(smem_u32(&ring_full[ord % kTfRing]));
+            cur_c = 0;
+            if (more) cur_nch = (sns[tasks[cur_tq].x].n + kTfChunk - 1) / kTfChunk;
+          }
         }
-        const float ah = to_tf32(a), bh = to_tf32(b);
-        const uint32_t o = swz(r, k);
-        *reinterpret_cast<float*>(Ahi + o) = ah;
-        *reinterpret_cast<float*>(Alo + o) = to_tf32(a - ah);
-        *reinterpret_cast<float*>(Bhi + o) = bh;
-        *reinterpret_cast<float*>(Blo + o) = to_tf32(b - bh);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
+        if (!ok || npend == 0) break;
+        // MMAs of the oldest pending chunk
+        const int s = (int)(done % kTfStages);
+        if (!tf_wait(smem_u32(&st_full[s]), (uint32_t)((done / kTfStages) & 1))) {
+          ok = false;
+          break;
+        }
+        const int acc = p_ord[head] % kTfSlots;
+        if (p_c[head] == 0 && p_ord[head] >= kTfSlots &&  // wait for the drain of the slot
+            !tf_wait(smem_u32(&acc_empty[acc]), (uint32_t)(((p_ord[head] / kTfSlots) - 1) & 1))) {
+          ok = false;
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const int ksteps = (kw + 7) >> 3;  // K = 8 per tf32 MMA
-        for (int kk = 0; kk < ksteps; kk++) {
-          const uint64_t ah = smem_desc(smem_u32(Ahi) + kk * 32);
-          const uint64_t al = smem_desc(smem_u32(Alo) + kk * 32);
-          const uint64_t bh = smem_desc(smem_u32(Bhi) + kk * 32);
-          const uint64_t bl = smem_desc(smem_u32(Blo) + kk * 32);
-          mma_tf32(tmem, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-          mma_tf32(tmem, ah, bl, idesc, 1u);
-          mma_tf32(tmem, al, bh, idesc, 1u);
+        const int n = sns[tasks[p_tq[head]].x].n;
+        const int kw = min(kTfChunk, n - kTfChunk * p_c[head]);
+        const uint32_t sa = smem_u32(stage_base + (size_t)s * kTfStageBytes);
+        const uint64_t ahi = tf_desc(sa), alo = tf_desc(sa + kTfPlane);
+        const uint64_t bhi = tf_desc(sa + 2 * kTfPlane), blo = tf_desc(sa + 3 * kTfPlane);
+        const uint32_t dt = tmem + (uint32_t)(acc * kTfM);
+        for (int kk = 0; kk < (kw + 7) / 8; kk++) {  // K steps of 8 TF32 = 32 bytes
+          tf_mma(dt, ahi + 2 * kk, bhi + 2 * kk, idesc, (p_c[head] > 0 || kk > 0) ? 1u : 0u);
+          tf_mma(dt, ahi + 2 * kk, blo + 2 * kk, idesc, 1u);
+          tf_mma(dt, alo + 2 * kk, bhi + 2 * kk, idesc, 1u);
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                bar)
-            : "memory");
+        tf_commit(smem_u32(&st_empty[s]));  // the stage is free once these MMAs are done
+        if (p_c[head] + 1 == p_nch[head]) tf_commit(smem_u32(&acc_full[acc]));
+        head = (head + 1) % kTfStages;
+        npend--;
+        done++;
       }
-      inflight = true;
-      if (!mbar_wait(bar, phase)) s_fail = 1;  // benign race: every writer stores 1
-      else inflight = false;
-      phase ^= 1;
-      __syncthreads();
-      if (s_fail) {
-        if (tid == 0) atomicAdd(mats[d.mat].err + 3, 1ull);
+      if (!ok) {
+        s_fail = 1;
+        // the consumers stop at their next ring wait on an end marker
+        ring[(ord + 1) % kTfRing] = ntasks;
+        tf_arrive(smem_u32(&ring_full[(ord + 1) % kTfRing]));
+      }
+      // bounded waits for the MMAs and copies still in flight
+      if (done > 0)
+        tf_wait(smem_u32(&st_empty[(done - 1) % kTfStages]), (uint32_t)(((done - 1) / kTfStages) & 1));
+      for (long long q = done; q < item; q++)
+        tf_wait(smem_u32(&st_full[q % kTfStages]), (uint32_t)((q / kTfStages) & 1));
+    }
+  } else {
+    // ---------------- consumers: metadata, accumulator drain, scatter ----------------
+    int ord = 0, buf = 0;
+    while (true) {
+      const int rs = ord % kTfRing;
+      if (!tf_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kTfRing) & 1))) {
+        s_fail = 1;
         break;
       }
-    }
-    if (s_fail) break;
-    // accumulator -> shared tile Cs[col * (kTc + 1) + row]
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int row = warp * 32 + lane;
-#pragma unroll 1
-    for (int cc = 0; cc < kTc / 32; cc++) {
-      uint32_t r[32];
-      tmem_load32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), r);
+      const int tq = ring[rs];
+      if (tq >= ntasks) break;
+      const int4 tk = tasks[tq];
+      const SnDev d = sns[tk.x];
+      const int n = d.n, u = d.m - n;
+      const int i0 = tk.y, k0 = tk.z;
+      const int32_t* rows = d.rows + n;
+      const MatDev md = mats[d.mat];
+      TfMeta& M = meta[buf];
+      if (!OWNER) {
+        for (int kk = tid; kk < kTfM; kk += kTfConsumers) {
+          const int gk = k0 + kk;
+          M.tcol[kk] = gk < u ? md.col2sn[rows[gk]] : -1;
+        }
+        consumer_sync();
+        if (warp == 0) {
+          int nr = 0;
+          for (int base = 0; base < kTfM; base += 32) {
+            const int kk = base + lane;
+            const bool start = k0 + kk < u && (kk == 0 || M.tcol[kk] != M.tcol[kk - 1]);
+            const unsigned b = __ballot_sync(0xffffffffu, start);
+            if (start) M.run_start[nr + __popc(b & ((1u << lane) - 1u))] = kk;
+            nr += __popc(b);
+          }
+          __syncwarp();
+          if (lane == 0) M.nruns = nr;
+          for (int r = lane; r < nr; r += 32) {
+            const int kb = M.run_start[r];
+            const int ke = r + 1 < nr ? M.run_start[r + 1] : min(kTfM, u - k0);
+            const SnDev& td = sns[md.sn_base + M.tcol[kb]];
+            M.rb[r] = md.run_base[find_run(md, d, k0 + kb)];
+            if (r < kTfMaxRuns) {
+              M.rL[r] = reinterpret_cast<float*>(td.L);
+              M.rm[r] = td.m;
+            }
+            for (int kk = kb; kk < ke; kk++) {
+              M.run[kk] = r;
+              M.col[kk] = rows[k0 + kk] - td.col0;
+            }
+          }
+        }
+        consumer_sync();
+        const int nrc = min(M.nruns, kTfMaxRuns);
+        for (int idx = tid; idx < nrc * kTfM; idx += kTfConsumers) {
+          const int r = idx / kTfM, i = idx - r * kTfM, gi = i0 + i;
+          M.rp[r][i] = (gi < u && gi >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + gi] : -1;
+        }
+        consumer_sync();
+      }
+      // the finished accumulator of this task
+      const int acc = ord % kTfSlots;
+      if (!tf_wait(smem_u32(&acc_full[acc]), (uint32_t)((ord / kTfSlots) & 1))) {
+        s_fail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int i = 32 * (warp & 3) + lane;  // this thread's tile row
+      const int c0 = 32 * (warp >> 2);       // and its 32 columns
+      uint32_t v[32];
+      tf_tmem_load32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(acc * kTfM + c0), v);
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) tf_arrive(smem_u32(&acc_empty[acc]));
+      const int gi = i0 + i;
+      if (gi < u) {
+        if (OWNER) {
+          float* U = static_cast<float*>(md.stage) + d.ustage;
 #pragma unroll
-      for (int j = 0; j < 32; j++) Cs[(cc * 32 + j) * (kTc + 1) + row] = __uint_as_float(r[j]);
+          for (int j = 0; j < 32; j++) {
+            const int gk = k0 + c0 + j;
+            if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = __uint_as_float(v[j]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; j++) {
+            const int kk = c0 + j, gk = k0 + kk;
+            if (gk >= u || gk > gi) continue;
+            const int r = M.run[kk];
+            float* Lt;
+            int mt, p;
+            if (r < kTfMaxRuns) {
+              Lt = M.rL[r];
+              mt = M.rm[r];
+              p = M.rp[r][i];
+            } else {  // beyond the cached targets: read the relative map here
+              const SnDev& td = sns[md.sn_base + M.tcol[kk]];
+              Lt = reinterpret_cast<float*>(td.L);
+              mt = td.m;
+              p = md.relmap[M.rb[r] + gi];
+            }
+            if (p >= 0) atomicAdd(&Lt[(int64_t)M.col[kk] * mt + p], -__uint_as_float(v[j]));
+          }
+        }
+      }
+      ord++;
+      buf ^= 1;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    schur_tile_epilogue<float, kTc, kTcThreads, OWNER>(Cs, d, i0, k0, sns, mats,
-                                                       static_cast<float*>(mats[d.mat].stage));
-    __syncthreads();
-    if (gridDim.x >= ntasks) break;
-    if (tid == 0) s_next_task = gridDim.x + atomicAdd(queue, 1);
-    __syncthreads();
-    tq = s_next_task;
   }
-  if (s_fail && inflight) mbar_wait(bar, phase ^ 1);  // let the MMAs in flight finish (bounded)
+  __syncthreads();
+  if (s_fail && tid == 0 && ntasks > 0) atomicAdd(mats[sns[tasks[0].x].mat].err + 3, 1ull);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTc));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTfSlots * kTfM));
+}
+
+void launch_tf32_split(const int4* tasks, int ntasks, const SnDev* sns, int max_width, void* oz,
+                       int64_t oz_rows, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  k_tf32_split<<<ntasks, 256, (size_t)max_width * kTfM * sizeof(float), st>>>(
+      tasks, sns, static_cast<uint8_t*>(oz), oz_rows);
 }
 
 void launch_schur_tc(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
-                     const MatDev* mats, bool owner, cudaStream_t st) {
+                     const MatDev* mats, bool owner, const void* oz, int64_t oz_rows,
+                     cudaStream_t st) {
   if (ntasks <= 0) return;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = ntasks < sms ? ntasks : sms;  // one resident CTA per SM, tasks by queue
+  const uint8_t* z = static_cast<const uint8_t*>(oz);
   if (owner)
-    k_schur_tc<true><<<ntasks, kTcThreads, kTcSmem, st>>>(tasks, ntasks, queue, sns, mats);
+    k_schur_tf32<true><<<grid, kTfThreads, kTfSmem, st>>>(tasks, ntasks, queue, sns, mats, z, oz_rows);
   else
-    k_schur_tc<false><<<ntasks, kTcThreads, kTcSmem, st>>>(tasks, ntasks, queue, sns, mats);
+    k_schur_tf32<false><<<grid, kTfThreads, kTfSmem, st>>>(tasks, ntasks, queue, sns, mats, z, oz_rows);
 }
 
 int set_tc_kernel_attrs() {
-  if (cudaFuncSetAttribute(k_schur_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kTcSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_schur_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kTcSmem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_schur_tf32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kTfSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_schur_tf32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kTfSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tf32_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kMaxWidth * kTfM * sizeof(float))) != cudaSuccess)
     return CHOL_E_CUDA;
   return CHOL_OK;
 }
