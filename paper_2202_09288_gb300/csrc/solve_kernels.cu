@@ -146,7 +146,19 @@ __global__ void __launch_bounds__(kSolveThreads)
         P acc[NR];
   #pragma unroll
         for (int c = 0; c < NR; c++) acc[c] = P(0);
-        for (int j = 0; j < n; j++) {
+        // eight independent panel loads per step: the loads, not the FMAs, are the latency
+        int j = 0;
+        for (; j + 8 <= n; j += 8) {
+          P l[8];
+  #pragma unroll
+          for (int q = 0; q < 8; q++) l[q] = L[(int64_t)(j + q) * m];
+  #pragma unroll
+          for (int q = 0; q < 8; q++)
+  #pragma unroll
+            for (int c = 0; c < NR; c++)
+              if (c0 + c < nrhs) acc[c] += l[q] * xs[(c0 + c) * n + j + q];
+        }
+        for (; j < n; j++) {
           const P l = L[(int64_t)j * m];
   #pragma unroll
           for (int c = 0; c < NR; c++)
@@ -222,7 +234,18 @@ __global__ void __launch_bounds__(kSolveThreads)
     for (int c = 0; c < NR; c++) acc[c] = P(0);
     if (j < n) {
       const P* col = reinterpret_cast<const P*>(d.L) + (int64_t)j * m + n + tk.y;
-      for (int i = ib; i < ie; i++) {
+      int i = ib;
+      for (; i + 8 <= ie; i += 8) {  // eight independent loads per step
+        P l[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) l[q] = col[i + q];
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+#pragma unroll
+          for (int c = 0; c < NR; c++)
+            if (c < nrhs) acc[c] += l[q] * xg[c * rb + i + q];
+      }
+      for (; i < ie; i++) {
         const P l = col[i];
 #pragma unroll
         for (int c = 0; c < NR; c++)
