@@ -402,12 +402,37 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
 // factored in FP32; if any pivot falls below tau (tau times the original diagonal, which
 // is 1 after equilibration), the block is factored again in FP64 from an FP64 copy of
 // its values, and the FP64 result is rounded into the panel.  err[2] counts such redos.
+// One pass of the right-looking factorization of the n x n block A (shared memory,
+// column-major) with one barrier per column: A_rc -= A_rj A_cj / p_j for j < c <= r (rows
+// spread over the threads, two per row for n <= 64), pivots p_j kept in piv.  Stops at the
+// first column whose pivot fails accept(p), returning it (every thread reads the same
+// pivot, so all stop together), else returns n.  The caller scales the columns.
+template <typename T, typename Accept>
+__device__ int potrf_pass(T* A, int n, T* piv, Accept accept) {
+  const bool two = n <= 64;
+  const int r = two ? (threadIdx.x & 63) : threadIdx.x;
+  const int cpar = two ? (threadIdx.x >> 6) : 0, cstep = two ? 2 : 1;
+  for (int j = 0; j < n; j++) {
+    const T p = A[j * n + j];
+    if (!accept(p)) return j;
+    if (threadIdx.x == 0) piv[j] = p;
+    if (r > j && r < n) {
+      const T arj = A[j * n + r] * (T(1) / p);
+      for (int c = j + 1 + cpar; c <= r; c += cstep) A[c * n + r] -= arj * A[j * n + c];
+    }
+    __syncthreads();
+  }
+  return n;
+}
+
 __global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                      const SnDev* __restrict__ sns,
                                                      const MatDev* __restrict__ mats,
                                                      float tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next_task;
+  __shared__ float fpiv[kMaxWidth];
+  __shared__ double dpiv[kMaxWidth];
   for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
@@ -415,10 +440,6 @@ __global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ ta
     float* L = reinterpret_cast<float*>(d.L);
     double* D = reinterpret_cast<double*>(smem_raw);   // n x n FP64 copy
     float* A = reinterpret_cast<float*>(D + n * n);    // n x n FP32 work block
-    __shared__ float fpiv_inv;
-    __shared__ double dpiv_inv;
-    __shared__ int redo;
-    if (threadIdx.x == 0) redo = 0;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       int c = idx / n, r = idx - c * n;
       const float v = r >= c ? L[(int64_t)c * m + r] : 0.f;
@@ -426,53 +447,27 @@ __global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ ta
       D[idx] = (double)v;
     }
     __syncthreads();
-    for (int j = 0; j < n; j++) {
-      if (threadIdx.x == 0) {
-        float p = A[j * n + j];
-        if (!(p >= tau)) { redo = 1; p = 1.f; }
-        const float s = sqrtf(p);
-        A[j * n + j] = s;
-        fpiv_inv = 1.f / s;
-      }
-      __syncthreads();
-      if (redo) break;
-      const float inv = fpiv_inv;
-      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[j * n + i] *= inv;
-      __syncthreads();
-      const int nt = n - j - 1;
-      for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
-        int c = idx / nt, r = idx - c * nt;
-        if (r >= c) A[(j + 1 + c) * n + j + 1 + r] -= A[j * n + j + 1 + r] * A[j * n + j + 1 + c];
-      }
-      __syncthreads();
-    }
-    if (redo) {
+    const int stop = potrf_pass<float>(A, n, fpiv, [&](float p) { return p >= tau; });
+    if (stop < n) {
+      // a small FP32 pivot: the whole block again in FP64 from the FP64 copy
       if (threadIdx.x == 0) atomicAdd(mats[d.mat].err + 2, 1ull);
-      for (int j = 0; j < n; j++) {
-        if (threadIdx.x == 0) {
-          double p = D[j * n + j];
-          if (!(p > 0.0)) { record_error(mats[d.mat], d.col0 + j); p = 1.0; }
-          const double s = sqrt(p);
-          D[j * n + j] = s;
-          dpiv_inv = 1.0 / s;
-        }
-        __syncthreads();
-        const double inv = dpiv_inv;
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) D[j * n + i] *= inv;
-        __syncthreads();
-        const int nt = n - j - 1;
-        for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
-          int c = idx / nt, r = idx - c * nt;
-          if (r >= c) D[(j + 1 + c) * n + j + 1 + r] -= D[j * n + j + 1 + r] * D[j * n + j + 1 + c];
-        }
-        __syncthreads();
-      }
-      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) A[idx] = (float)D[idx];
+      const MatDev md = mats[d.mat];
+      const int bad = potrf_pass<double>(D, n, dpiv, [](double p) { return p > 0.0; });
+      if (bad < n && threadIdx.x == 0) record_error(md, d.col0 + bad);
+      for (int j = threadIdx.x; j < n; j += blockDim.x)
+        dpiv[j] = j < bad ? sqrt(dpiv[j]) : 1.0;
       __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      int c = idx / n, r = idx - c * n;
-      if (r >= c) L[(int64_t)c * m + r] = A[idx];
+      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int c = idx / n, rr = idx - c * n;
+        if (rr >= c) L[(int64_t)c * m + rr] = rr == c ? (float)dpiv[c] : (float)(D[idx] / dpiv[c]);
+      }
+    } else {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) fpiv[j] = sqrtf(fpiv[j]);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int c = idx / n, rr = idx - c * n;
+        if (rr >= c) L[(int64_t)c * m + rr] = rr == c ? fpiv[c] : A[idx] / fpiv[c];
+      }
     }
     __syncthreads();
     // a CTA's first task is its block index; only a grid smaller than the task list makes
