@@ -34,15 +34,19 @@ namespace chol {
 
 namespace {
 
-constexpr int kOzThreads = 512;
+constexpr int kOzConsumers = 512;                          // 16 warps: drain + scatter
+constexpr int kOzThreads = kOzConsumers + 32;              // + the producer warp
+constexpr int kOzRing = 16;
 constexpr int kOzM = 128;                                  // tile rows (UMMA M)
 constexpr int kOzN = 64;                                   // columns per half (UMMA N)
 constexpr uint32_t kOzASlice = kOzM * kOzRowBytes;         // 16 KB
-constexpr uint32_t kOzBSlice = kOzN * kOzRowBytes;         // 8 KB
+constexpr int kOzQ = 32;                                   // columns per quarter
+constexpr uint32_t kOzQSlice = kOzQ * kOzRowBytes;         // 4 KB: one slice of a quarter
+constexpr uint32_t kOzQBytes = kOzSlices * kOzQSlice;      // 32 KB: a quarter's B operand
+constexpr int kOzSetCols = kOzSlices * kOzQ;               // 256: TMEM columns of a set
 constexpr uint32_t kOzABytes = kOzSlices * kOzASlice;      // 128 KB
-constexpr uint32_t kOzBBytes = kOzSlices * kOzBSlice;      // 64 KB
-constexpr size_t kOzSmem = 1024 + kOzABytes + kOzBBytes;   // + alignment slack
-constexpr uint32_t kOzTmemCols = kOzSlices * kOzN;         // 512: one accumulator per diagonal
+constexpr size_t kOzSmem = 1024 + kOzABytes + 2 * kOzQBytes;  // + alignment slack
+constexpr uint32_t kOzTmemCols = 2 * kOzSetCols;          // 512: two sets of 8 diagonals
 constexpr long long kOzSpinLimit = 1ll << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -272,9 +276,25 @@ struct OzMeta {
   int rm[kOzMaxRuns];
   long long rb[2 * kOzN];  // relative-map base of every run
   int rp[kOzMaxRuns][kOzM];
-  int nruns, next;
+  int nruns;
 };
 
+// barrier among the consumer warps only (the producer warp runs on its own)
+__device__ __forceinline__ void oz_consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kOzConsumers) : "memory");
+}
+
+__device__ __forceinline__ void oz_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// A task is done as 128 x 32 quarters.  The producer thread (its own warp) loads the task's
+// A slices once and the B slices of every quarter into one of two quarter buffers, and
+// issues each quarter's MMAs into one of two TMEM sets of 8 diagonals x 32 columns; the 16
+// consumer warps drain a finished set (and release it) while the tensor cores compute the
+// next quarter, then scatter.  Barriers: a_full (A slices in), b_full[2] (quarter B
+// buffers in), acc_full[2] (a set's MMAs done: also frees the B buffer they read),
+// acc_empty[2] (a set drained), ring_full[] (the task order, for the consumers).
 template <bool OWNER>
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_schur_oz(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
@@ -283,13 +303,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   extern __shared__ __align__(1024) unsigned char oz_sm[];
   unsigned char* A =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz_sm) + 1023) & ~uintptr_t(1023));
-  unsigned char* B = A + kOzABytes;
-  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  unsigned char* Bq0 = A + kOzABytes;  // quarter buffers: Bq0, Bq0 + kOzQBytes
+  __shared__ __align__(8) uint64_t a_full, b_full[2], acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t ring_full[kOzRing];
+  __shared__ int ring[kOzRing];
   __shared__ uint32_t tmem_base;
   __shared__ OzMeta meta[2];
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t bld = smem_u32(&bar_ld), bmma = smem_u32(&bar_mma);
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
   const int32_t* exps = reinterpret_cast<const int32_t*>(oz + kOzSlices * stride);
 
@@ -301,235 +322,272 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   }
   if (tid == 0) {
     s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bld));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bmma));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&a_full)));
+    for (int i = 0; i < 2; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&b_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[i])),
+                   "r"(kOzConsumers / 32));
+    }
+    for (int i = 0; i < kOzRing; i++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ring_full[i])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  // N = 64, 128, 192, 256: one MMA covers up to 4 consecutive B slices
-  const uint32_t idesc[4] = {oz_idesc(kOzN), oz_idesc(2 * kOzN), oz_idesc(3 * kOzN),
-                             oz_idesc(4 * kOzN)};
-  const uint64_t da0 = oz_desc(smem_u32(A)), db0 = oz_desc(smem_u32(B));
-  // thread 0 only: the load barrier's next phase, and what is in flight
-  uint32_t ld_phase = 0;
-  bool ld_inflight = false, mma_inflight = false;
-  uint32_t ld_parity = 0, mma_parity = 0;
-  uint32_t mma_phase = 0;  // every thread: parity of the next MMA commit
 
-  // thread 0: bulk copies of a task's A slices and of one half's B slices
-  auto issue_loads = [&](const int4& t, int h, bool with_a) {
-    const uint32_t bytes = (with_a ? kOzABytes : 0u) + kOzBBytes;
-    oz_expect(bld, bytes);
-    if (with_a)
-      for (int p = 0; p < kOzSlices; p++)
-        oz_bulk_load(smem_u32(A + p * kOzASlice),
-                     oz + p * stride + (size_t)(t.w + t.y) * kOzRowBytes, kOzASlice, bld);
-    for (int p = 0; p < kOzSlices; p++)
-      oz_bulk_load(smem_u32(B + p * kOzBSlice),
-                   oz + p * stride + (size_t)(t.w + t.z + kOzN * h) * kOzRowBytes, kOzBSlice,
-                   bld);
-    ld_inflight = true;
-    ld_parity = ld_phase;
-  };
-  // thread 0: wait for the operands, then D_{p+q} (+)= S_p S_q^T for every slice pair
-  // p + q < kOzSlices.  The B slices lie one after another in shared memory, so one MMA of
-  // S_p against slices q0 .. q0+3 (N up to 256) writes the accumulators of the diagonals
-  // p+q0 .. p+q0+3 when its TMEM address starts at diagonal p + q0: 12 MMAs per K step
-  // instead of 36 (the issue rate of a single thread, not the tensor cores, bounds small
-  // MMAs).  A K step of 16 bf16 advances both descriptors by 32 bytes (2 in the address
-  // field).  Returns false if the wait gave up.
-  auto load_and_mma = [&](int ksteps) -> bool {
-    if (!oz_wait(bld, ld_phase)) return false;
-    ld_phase ^= 1;
-    ld_inflight = false;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    for (int ks = 0; ks < ksteps; ks++)
-      for (int p = 0; p < kOzSlices; p++)
-        for (int q0 = 0; p + q0 < kOzSlices; q0 += 4) {
-          const int nq = min(4, kOzSlices - p - q0);
-          oz_mma(tmem + (uint32_t)((p + q0) * kOzN),
-                 da0 + (uint64_t)((p * kOzASlice) >> 4) + 2 * ks,
-                 db0 + (uint64_t)((q0 * kOzBSlice) >> 4) + 2 * ks, idesc[nq - 1],
-                 (p > 0 || ks > 0) ? 1u : 0u);
-        }
-    oz_commit(bmma);
-    mma_inflight = true;
-    mma_parity = mma_phase;
-    return true;
-  };
-  auto ksteps_of = [&](const int4& t) { return (sns[t.x].n + 15) >> 4; };
-
-  int tq = blockIdx.x;
-  if (tid == 0 && tq < ntasks) {
-    issue_loads(tasks[tq], 0, true);
-    if (!load_and_mma(ksteps_of(tasks[tq]))) s_fail = 1;
-  }
-  int buf = 0;
-  while (tq < ntasks) {
-    // the first half's MMAs of this task are running
-    const int4 tk = tasks[tq];
-    const SnDev d = sns[tk.x];
-    const int n = d.n, u = d.m - n;
-    const int i0 = tk.y, k0 = tk.z;
-    const int ksteps = (n + 15) >> 4;
-    const int nh = (k0 + kOzN < u) ? 2 : 1;
-    const int32_t* rows = d.rows + n;
-    const MatDev md = mats[d.mat];
-    OzMeta& M = meta[buf];
-    for (int i = tid; i < kOzM; i += kOzThreads) M.eA[i] = (i0 + i < u) ? exps[tk.w + i0 + i] : 0;
-    for (int kk = tid; kk < 2 * kOzN; kk += kOzThreads) {
-      const int gk = k0 + kk;
-      M.eB[kk] = gk < u ? exps[tk.w + gk] : 0;
-      M.tcol[kk] = gk < u ? md.col2sn[rows[gk]] : -1;
-    }
-    if (tid == 0) M.next = gridDim.x >= ntasks ? ntasks : gridDim.x + atomicAdd(queue, 1);
-    __syncthreads();
-    if (s_fail) break;
-    if (!OWNER) {
-      // runs of tile columns with one target (first warp, ballots), then the relative rows
-      // of the tile rows inside the first kOzMaxRuns targets, while the tensor cores work
-      if (warp == 0) {
-        int nr = 0;
-        for (int base = 0; base < 2 * kOzN; base += 32) {
-          const int kk = base + lane;
-          const bool live = k0 + kk < u;
-          const bool start = live && (kk == 0 || M.tcol[kk] != M.tcol[kk - 1]);
-          const unsigned b = __ballot_sync(0xffffffffu, start);
-          if (start) M.run_start[nr + __popc(b & ((1u << lane) - 1u))] = kk;
-          nr += __popc(b);
-        }
-        __syncwarp();
-        if (lane == 0) M.nruns = nr;
-        for (int r = lane; r < nr; r += 32) {
-          const int kb = M.run_start[r];
-          const int ke = r + 1 < nr ? M.run_start[r + 1] : min(2 * kOzN, u - k0);
-          const SnDev& td = sns[md.sn_base + M.tcol[kb]];
-          M.rb[r] = md.run_base[find_run(md, d, k0 + kb)];
-          if (r < kOzMaxRuns) {
-            M.rL[r] = reinterpret_cast<double*>(td.L);
-            M.rm[r] = td.m;
+  if (warp == kOzConsumers / 32) {
+    // ---------------- producer: operand loads and MMAs, one thread ----------------
+    if (lane == 0) {
+      // N = (8 - p) x 32: the MMA of slice p against slices 0 .. 7-p of a quarter
+      uint32_t idesc[kOzSlices];
+#pragma unroll
+      for (int p = 0; p < kOzSlices; p++) idesc[p] = oz_idesc((kOzSlices - p) * kOzQ);
+      const uint64_t da0 = oz_desc(smem_u32(A));
+      const uint64_t db[2] = {oz_desc(smem_u32(Bq0)), oz_desc(smem_u32(Bq0 + kOzQBytes))};
+      long long a_issued = 0, b_issued[2] = {0, 0};  // loads issued per barrier
+      auto load_a = [&](const int4& t) {
+        const uint32_t bar = smem_u32(&a_full);
+        oz_expect(bar, kOzABytes);
+        for (int p = 0; p < kOzSlices; p++)
+          oz_bulk_load(smem_u32(A + p * kOzASlice),
+                       oz + p * stride + (size_t)(t.w + t.y) * kOzRowBytes, kOzASlice, bar);
+        a_issued++;
+      };
+      auto load_b = [&](const int4& t, int j, int b) {
+        const uint32_t bar = smem_u32(&b_full[b]);
+        unsigned char* dst = Bq0 + b * kOzQBytes;
+        oz_expect(bar, kOzQBytes);
+        for (int p = 0; p < kOzSlices; p++)
+          oz_bulk_load(smem_u32(dst + p * kOzQSlice),
+                       oz + p * stride + (size_t)(t.w + t.z + kOzQ * j) * kOzRowBytes, kOzQSlice,
+                       bar);
+        b_issued[b]++;
+      };
+      auto quarters = [&](const int4& t) {
+        const SnDev& dd = sns[t.x];
+        return min(4, (dd.m - dd.n - t.z + kOzQ - 1) / kOzQ);
+      };
+      bool ok = true;
+      long long q = 0;          // quarters issued (set and buffer = q & 1)
+      long long a_use = 0;      // A loads completed-and-waited
+      int ord = 0;
+      int tq = blockIdx.x;
+      ring[0] = tq < ntasks ? tq : ntasks;
+      oz_arrive(smem_u32(&ring_full[0]));
+      if (tq < ntasks) {
+        load_a(tasks[tq]);
+        load_b(tasks[tq], 0, 0);
+      }
+      while (ok && tq < ntasks) {
+        const int4 t = tasks[tq];
+        const int nq = quarters(t);
+        const int ks = (sns[t.x].n + 15) >> 4;
+        if (!oz_wait(smem_u32(&a_full), (uint32_t)(a_use & 1))) { ok = false; break; }
+        a_use++;
+        // the next task is fetched now so its first quarter can be prefetched
+        const int next = gridDim.x >= ntasks ? ntasks : (int)gridDim.x + atomicAdd(queue, 1);
+        for (int j = 0; j < nq && ok; j++, q++) {
+          const int b = (int)(q & 1);
+          if (!oz_wait(smem_u32(&b_full[b]), (uint32_t)((q >> 1) & 1)) ||
+              (q >= 2 &&  // the set was drained (quarter q - 2)
+               !oz_wait(smem_u32(&acc_empty[b]), (uint32_t)(((q >> 1) - 1) & 1)))) {
+            ok = false;
+            break;
           }
-          for (int kk = kb; kk < ke; kk++) {
-            M.run[kk] = r;
-            M.col[kk] = rows[k0 + kk] - td.col0;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          for (int k = 0; k < ks; k++)
+#pragma unroll
+            for (int p = 0; p < kOzSlices; p++)
+              oz_mma(tmem + (uint32_t)(b * kOzSetCols + p * kOzQ),
+                     da0 + (uint64_t)((p * kOzASlice) >> 4) + 2 * k, db[b] + 2 * k, idesc[p],
+                     (p > 0 || k > 0) ? 1u : 0u);
+          oz_commit(smem_u32(&acc_full[b]));
+          // prefetch the next quarter into the other buffer (its MMAs, quarter q - 1, must
+          // be done); the next task's A waits for this quarter's MMAs
+          const bool last = j + 1 == nq;
+          if (!last || next < ntasks) {
+            if (q >= 1 && !oz_wait(smem_u32(&acc_full[b ^ 1]), (uint32_t)(((q - 1) >> 1) & 1))) {
+              ok = false;
+              break;
+            }
+            if (last) {
+              if (!oz_wait(smem_u32(&acc_full[b]), (uint32_t)((q >> 1) & 1))) { ok = false; break; }
+              load_a(tasks[next]);
+              load_b(tasks[next], 0, b ^ 1);
+            } else {
+              load_b(t, j + 1, b ^ 1);
+            }
           }
         }
+        if (!ok) break;
+        ord++;
+        tq = next;
+        ring[ord % kOzRing] = tq < ntasks ? tq : ntasks;
+        oz_arrive(smem_u32(&ring_full[ord % kOzRing]));
       }
-      __syncthreads();
-      const int nrc = min(M.nruns, kOzMaxRuns);
-      for (int idx = tid; idx < nrc * kOzM; idx += kOzThreads) {
-        const int r = idx / kOzM, i = idx - r * kOzM, gi = i0 + i;
-        M.rp[r][i] = (gi < u && gi >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + gi] : -1;
+      if (!ok) {
+        s_fail = 1;
+        ring[(ord + 1) % kOzRing] = ntasks;
+        oz_arrive(smem_u32(&ring_full[(ord + 1) % kOzRing]));
       }
+      // bounded waits for the MMAs and copies still in flight (a quarter's B buffer is
+      // waited once per quarter issued: b_issued[b] - (quarters on b) loads remain)
+      if (q >= 1) oz_wait(smem_u32(&acc_full[(q - 1) & 1]), (uint32_t)(((q - 1) >> 1) & 1));
+      for (int b = 0; b < 2; b++) {
+        const long long waited = (q + 1 - b) >> 1;  // quarters issued on buffer b
+        if (b_issued[b] > waited) oz_wait(smem_u32(&b_full[b]), (uint32_t)(waited & 1));
+      }
+      if (a_issued > a_use) oz_wait(smem_u32(&a_full), (uint32_t)(a_use & 1));
     }
-    const int next = M.next;
+  } else {
+    // ---------------- consumers: metadata, set drain, scatter ----------------
+    int ord = 0, buf = 0;
+    long long q = 0;
     const int i = 32 * (warp & 3) + lane;  // this thread's tile row
-    const int gi = i0 + i;
-    const int eA = M.eA[i];
-    const int c0 = 16 * (warp >> 2);       // this thread's 16 columns of a half
-    bool stop = false;  // s_fail seen right after a barrier: the same in every thread
-    for (int h = 0; h < nh; h++) {
-      if (!oz_wait(bmma, mma_phase)) s_fail = 1;
-      else if (tid == 0) mma_inflight = false;
-      mma_phase ^= 1;
-      __syncthreads();
-      if (s_fail) {
-        stop = true;
+    const int c8 = 8 * (warp >> 2);        // this thread's 8 columns of a quarter
+    while (true) {
+      const int rs = ord % kOzRing;
+      if (!oz_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kOzRing) & 1))) {
+        s_fail = 1;
         break;
       }
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      // shared memory is free: start the next operands while the accumulators are read
-      if (tid == 0) {
-        if (h + 1 < nh) issue_loads(tk, h + 1, false);
-        else if (next < ntasks) issue_loads(tasks[next], 0, true);
+      const int tq = ring[rs];
+      if (tq >= ntasks) break;
+      const int4 tk = tasks[tq];
+      const SnDev d = sns[tk.x];
+      const int n = d.n, u = d.m - n;
+      const int i0 = tk.y, k0 = tk.z;
+      const int nq = min(4, (u - k0 + kOzQ - 1) / kOzQ);
+      const int32_t* rows = d.rows + n;
+      const MatDev md = mats[d.mat];
+      OzMeta& M = meta[buf];
+      for (int r = tid; r < kOzM; r += kOzConsumers) M.eA[r] = (i0 + r < u) ? exps[tk.w + i0 + r] : 0;
+      for (int kk = tid; kk < 2 * kOzN; kk += kOzConsumers) {
+        const int gk = k0 + kk;
+        M.eB[kk] = gk < u ? exps[tk.w + gk] : 0;
+        M.tcol[kk] = gk < u ? md.col2sn[rows[gk]] : -1;
       }
-      // accumulators -> integers -> W = V_hi 2^20 + round(V_lo / 2^8), where
-      // V_hi = sum_{d<4} D_d 2^(7(3-d)), V_lo = sum_{d>=4} D_d 2^(7(7-d)) (|D_d| < 2^22,
-      // |V_hi| < 2^42, |V_lo| < 2^44), so U = W 2^(e_i + e_k - 55)
-      double val[16];
-#pragma unroll
-      for (int cc = 0; cc < 2; cc++) {
-        long long vh[8], vl[8];
-        const uint32_t ta =
-            tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 8 * cc);
-        {
-          uint32_t v[4][8];
-#pragma unroll
-          for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)(dd * kOzN), v[dd]);
-          oz_tmem_wait();
-          oz_combine4(v, vh);
-        }
-        {
-          uint32_t v[4][8];
-#pragma unroll
-          for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)((4 + dd) * kOzN), v[dd]);
-          oz_tmem_wait();
-          oz_combine4(v, vl);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; j++)
-          val[8 * cc + j] = oz_to_double((long long)((unsigned long long)vh[j] << 20) +
-                                             ((vl[j] + 128) >> 8),
-                                         eA + M.eB[h * kOzN + c0 + 8 * cc + j] - 55);
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-      // tensor memory is free: the next MMAs (this task's second half, or the next task's
-      // first) run during this half's scatter
-      if (tid == 0) {
-        if (h + 1 < nh) {
-          if (!load_and_mma(ksteps)) s_fail = 1;
-        } else if (next < ntasks) {
-          if (!load_and_mma(ksteps_of(tasks[next]))) s_fail = 1;
-        }
-      }
-      // scatter this thread's row of the half
-      if (gi < u) {
-        const int kb = h * kOzN + c0;  // tile column of val[0]
-        if (OWNER) {
-          double* U = static_cast<double*>(md.stage) + d.ustage;
-#pragma unroll
-          for (int j = 0; j < 16; j++) {
-            const int gk = k0 + kb + j;
-            if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = val[j];
+      oz_consumer_sync();
+      if (!OWNER) {
+        if (warp == 0) {
+          int nr = 0;
+          for (int base = 0; base < 2 * kOzN; base += 32) {
+            const int kk = base + lane;
+            const bool start = k0 + kk < u && (kk == 0 || M.tcol[kk] != M.tcol[kk - 1]);
+            const unsigned bl = __ballot_sync(0xffffffffu, start);
+            if (start) M.run_start[nr + __popc(bl & ((1u << lane) - 1u))] = kk;
+            nr += __popc(bl);
           }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; j++) {
-            const int kk = kb + j, gk = k0 + kk;
-            if (gk >= u || gk > gi) continue;
-            const int r = M.run[kk];
-            double* Lt;
-            int mt, p;
+          __syncwarp();
+          if (lane == 0) M.nruns = nr;
+          for (int r = lane; r < nr; r += 32) {
+            const int kb = M.run_start[r];
+            const int ke = r + 1 < nr ? M.run_start[r + 1] : min(2 * kOzN, u - k0);
+            const SnDev& td = sns[md.sn_base + M.tcol[kb]];
+            M.rb[r] = md.run_base[find_run(md, d, k0 + kb)];
             if (r < kOzMaxRuns) {
-              Lt = M.rL[r];
-              mt = M.rm[r];
-              p = M.rp[r][i];
-            } else {  // beyond the cached targets: read the relative map here
-              const SnDev& td = sns[md.sn_base + M.tcol[kk]];
-              Lt = reinterpret_cast<double*>(td.L);
-              mt = td.m;
-              p = md.relmap[M.rb[r] + gi];
+              M.rL[r] = reinterpret_cast<double*>(td.L);
+              M.rm[r] = td.m;
             }
-            if (p >= 0) atomicAdd(&Lt[(int64_t)M.col[kk] * mt + p], -val[j]);
+            for (int kk = kb; kk < ke; kk++) {
+              M.run[kk] = r;
+              M.col[kk] = rows[k0 + kk] - td.col0;
+            }
+          }
+        }
+        oz_consumer_sync();
+        const int nrc = min(M.nruns, kOzMaxRuns);
+        for (int idx = tid; idx < nrc * kOzM; idx += kOzConsumers) {
+          const int r = idx / kOzM, ii = idx - r * kOzM, g = i0 + ii;
+          M.rp[r][ii] = (g < u && g >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + g] : -1;
+        }
+        oz_consumer_sync();
+      }
+      const int gi = i0 + i;
+      const int eA = M.eA[i];
+      bool stop = false;
+      for (int j = 0; j < nq; j++, q++) {
+        const int b = (int)(q & 1);
+        if (!oz_wait(smem_u32(&acc_full[b]), (uint32_t)((q >> 1) & 1))) {
+          s_fail = 1;
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // the 8 diagonals of this thread's 8 columns -> integers -> W = V_hi 2^20 +
+        // round(V_lo / 2^8) (V_hi = sum_{d<4} D_d 2^(7(3-d)), V_lo = sum_{d>=4} D_d
+        // 2^(7(7-d)), |D_d| < 2^22): U = W 2^(e_i + e_k - 55)
+        double val[8];
+        {
+          long long vh[8], vl[8];
+          const uint32_t ta =
+              tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * kOzSetCols + c8);
+          {
+            uint32_t v[4][8];
+#pragma unroll
+            for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)(dd * kOzQ), v[dd]);
+            oz_tmem_wait();
+            oz_combine4(v, vh);
+          }
+          {
+            uint32_t v[4][8];
+#pragma unroll
+            for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)((4 + dd) * kOzQ), v[dd]);
+            oz_tmem_wait();
+            oz_combine4(v, vl);
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          __syncwarp();
+          if (lane == 0) oz_arrive(smem_u32(&acc_empty[b]));
+#pragma unroll
+          for (int jj = 0; jj < 8; jj++) {
+            const long long w = (long long)((unsigned long long)vh[jj] << 20) + ((vl[jj] + 128) >> 8);
+            val[jj] = oz_to_double(OWNER ? w : -w, eA + M.eB[kOzQ * j + c8 + jj] - 55);
+          }
+        }
+        // scatter this thread's row of the quarter (val holds -U for the atomics)
+        if (gi < u) {
+          const int kb = kOzQ * j + c8;
+          if (OWNER) {
+            double* U = static_cast<double*>(md.stage) + d.ustage;
+#pragma unroll
+            for (int jj = 0; jj < 8; jj++) {
+              const int gk = k0 + kb + jj;
+              if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = val[jj];
+            }
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 8; jj++) {
+              const int kk = kb + jj, gk = k0 + kk;
+              if (gk >= u || gk > gi) continue;
+              const int r = M.run[kk];
+              double* Lt;
+              int mt, p;
+              if (r < kOzMaxRuns) {
+                Lt = M.rL[r];
+                mt = M.rm[r];
+                p = M.rp[r][i];
+              } else {  // beyond the cached targets: read the relative map here
+                const SnDev& td = sns[md.sn_base + M.tcol[kk]];
+                Lt = reinterpret_cast<double*>(td.L);
+                mt = td.m;
+                p = md.relmap[M.rb[r] + gi];
+              }
+              if (p >= 0) atomicAdd(&Lt[(int64_t)M.col[kk] * mt + p], val[jj]);
+            }
           }
         }
       }
+      if (stop) break;
+      ord++;
+      buf ^= 1;
     }
-    if (stop) break;
-    buf ^= 1;
-    tq = next;
   }
   __syncthreads();
-  if (s_fail && tid == 0 && ntasks > 0) atomicAdd(mats[sns[tasks[min(tq, ntasks - 1)].x].mat].err + 3, 1ull);
-  // bounded waits for anything still in flight before the memory is released
-  if (tid == 0) {
-    if (mma_inflight) oz_wait(bmma, mma_parity);
-    if (ld_inflight) oz_wait(bld, ld_parity);
-  }
+  if (s_fail && tid == 0 && ntasks > 0) atomicAdd(mats[sns[tasks[0].x].mat].err + 3, 1ull);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
