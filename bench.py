@@ -40,6 +40,7 @@ NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0  # nominal dense FP64 / BF16 rates of a G
 FALLBACK_BF16_TFLOPS = 1900.0
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 OZ_PRODUCTS = 36  # slice pairs p + q < 8 of the FP64 tensor-core Schur tiles
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 rates of a GB300
 
 
 def measured_peaks():
@@ -550,6 +551,14 @@ def main():
                 "peak_source": f"bf16 tensor {peak_src} {peaks['bf16_tflops']} TFLOP/s; achieved "
                                f"= {OZ_PRODUCTS} bf16 slice products x the tiles' FP64 flops / "
                                "time (FP64-equivalent rate = achieved / 36)"}
+    elif dom == "schur128_tc":
+        # FP32 tiles on the TF32 tensor cores: three TF32 products per FP32 product
+        achieved *= 3
+        tf32_peak = peaks["bf16_tflops"] * NOMINAL_TF32_OVER_BF16
+        roof = {"bound": "tensor", "peak": tf32_peak,
+                "peak_source": f"TF32 = {peak_src} bf16 {peaks['bf16_tflops']} TFLOP/s x nominal "
+                               "TF32/bf16 1.1/2.25; achieved = 3 TF32 products (3xTF32) x the "
+                               "tiles' FP32 flops / time"}
     elif dom.endswith("_f64"):
         roof = {"bound": "tensor", "peak": fp64_peak_tflops,
                 "peak_source": f"FP64 = {peak_src} bf16 {peaks['bf16_tflops']} TFLOP/s x "
