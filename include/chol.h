@@ -250,7 +250,7 @@ void chol_batch_free(chol_batch* batch);
  * min_rows_tile128 off-diagonal rows on levels holding at least min_level_tiles128 such
  * tiles, else 64x64 tiles from min_rows_tile64 rows on levels holding at least
  * min_level_tiles64 such tiles, else 32x32 from min_rows_tile32 rows, else 16x16.
- * Default {64, 17, 304, 128, 304}.  A 128x128 tile of an FP32 (mixed-precision) factor is
+ * Default {64, 17, 304, 128, 0}.  A 128x128 tile of an FP32 (mixed-precision) factor is
  * one tcgen05 tensor-core task (3xTF32); of an FP64 factor, four 64x64 tasks.  All
  * fields >= 1 except the two level thresholds (>= 0); anything else is CHOL_E_INVALID. */
 typedef struct chol_tile_policy {

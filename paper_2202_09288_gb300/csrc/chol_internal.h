@@ -90,7 +90,7 @@ struct TilePolicy {
   int min_rows_tile32 = 17;
   int min_level_tiles64 = 2 * 152;
   int min_rows_tile128 = 128;
-  int min_level_tiles128 = 2 * 152;
+  int min_level_tiles128 = 0;
 };
 
 // Host-side symbolic analysis result.

@@ -32,20 +32,96 @@ __global__ void k_assemble(const double* __restrict__ vals, const int64_t* __res
     L[amap[p]] = (T)vals[p];
 }
 
+// Blocked right-looking Cholesky of the n x n block A (shared memory, column-major, lower
+// part used; 128 threads): per block of 16 columns, (1) the 16 x 16 diagonal block by one
+// warp (lane = row, __syncwarp between columns), (2) the rows below it by forward
+// substitution, one row per thread in registers, (3) the trailing lower triangle minus the
+// block's rank-16 product, the row's 16 values in registers.  Three barriers per 16 columns.
+// A holds L on return (diagonal included).  A pivot p that fails accept(p) stops the
+// factorization (all threads see the same shared flag) and its column is returned; n
+// otherwise.
+template <typename T, typename Accept>
+__device__ int potrf_blocked(T* A, int n, Accept accept) {
+  constexpr int B = 16;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_bad = n;
+  __syncthreads();
+  for (int kb = 0; kb < n; kb += B) {
+    const int nb = min(B, n - kb);
+    // (1) diagonal block
+    if (warp == 0) {
+      for (int j = 0; j < nb; j++) {
+        const int cj = kb + j;
+        const T p = A[cj * n + cj];
+        if (!accept(p)) {
+          if (lane == 0) s_bad = cj;
+          break;
+        }
+        const T sq = sqrt(p), inv = T(1) / sq;
+        __syncwarp();
+        if (lane > j && lane < nb) A[cj * n + kb + lane] *= inv;
+        if (lane == j) A[cj * n + cj] = sq;
+        __syncwarp();
+        if (lane > j && lane < nb) {
+          const T lr = A[cj * n + kb + lane];
+          for (int c = j + 1; c <= lane; c++) A[(kb + c) * n + kb + lane] -= lr * A[cj * n + kb + c];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (s_bad < n) return s_bad;
+    // (2) rows below: x = a L_bb^{-T}
+    const int r = kb + nb + tid;
+    if (r < n) {
+      T x[B];
+#pragma unroll
+      for (int j = 0; j < B; j++) {
+        if (j < nb) {
+          T acc = A[(kb + j) * n + r];
+#pragma unroll
+          for (int k = 0; k < j; k++) acc -= x[k] * A[(kb + k) * n + kb + j];
+          x[j] = acc / A[(kb + j) * n + kb + j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < B; j++)
+        if (j < nb) A[(kb + j) * n + r] = x[j];
+    }
+    __syncthreads();
+    // (3) trailing update: A_rc -= sum_k L_rk L_ck for kb + nb <= c <= r
+    const int t0 = kb + nb, nt = n - t0;
+    if (nt > 0) {
+      const bool two = nt <= 64;
+      const int rr = t0 + (two ? (tid & 63) : tid);
+      const int cpar = two ? (tid >> 6) : 0, cstep = two ? 2 : 1;
+      if (rr < n) {
+        T lr[B];
+#pragma unroll
+        for (int k = 0; k < B; k++) lr[k] = k < nb ? A[(kb + k) * n + rr] : T(0);
+        for (int c = t0 + cpar; c <= rr; c += cstep) {
+          T acc = T(0);
+#pragma unroll
+          for (int k = 0; k < B; k++) acc += lr[k] * A[(kb + k) * n + c];
+          A[c * n + rr] -= acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return n;
+}
+
 // ---- POTRF of each diagonal block ---------------------------------------------------------
-// One CTA per supernode; the n x n lower block is factored in shared memory by the
-// right-looking column algorithm.  Column j's pivot p_j = A_jj is final once columns < j are
-// applied, so one pass per column does the whole rank-1 update with the unscaled column,
-// A_rc -= A_rj A_cj / p_j (j < c <= r), and one barrier separates the columns; the columns
-// are scaled by p_j^{-1/2} (and the diagonal set to p_j^{1/2}) at the end.  Rows are spread
-// over the threads (two threads per row for n <= 64, alternate columns).
+// One CTA per supernode; the n x n lower block is factored in shared memory by the blocked
+// right-looking algorithm (potrf_blocked).
 template <typename T>
 __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                const SnDev* __restrict__ sns,
                                                const MatDev* __restrict__ mats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
-  __shared__ T piv[kMaxWidth], rpiv[kMaxWidth];
   __shared__ int s_next_task;
   for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
@@ -57,31 +133,12 @@ __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, i
       A[idx] = r >= c ? L[(int64_t)c * m + r] : T(0);
     }
     __syncthreads();
-    const bool two = n <= 64;                    // two threads per row
-    const int r = two ? (threadIdx.x & 63) : threadIdx.x;
-    const int cpar = two ? (threadIdx.x >> 6) : 0, cstep = two ? 2 : 1;
-    for (int j = 0; j < n; j++) {
-      T p = A[j * n + j];
-      if (!(p > T(0))) {
-        if (threadIdx.x == 0) record_error(mats[d.mat], d.col0 + j);
-        p = T(1);
-      }
-      if (threadIdx.x == 0) piv[j] = p;
-      if (r > j && r < n) {
-        const T arj = A[j * n + r] * (T(1) / p);
-        for (int c = j + 1 + cpar; c <= r; c += cstep) A[c * n + r] -= arj * A[j * n + c];
-      }
-      __syncthreads();
-    }
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const T sq = sqrt(piv[j]);
-      piv[j] = sq;
-      rpiv[j] = T(1) / sq;
-    }
-    __syncthreads();
+    // a non-positive pivot is an error (not SPD); the rest of the block is left as is
+    const int bad = potrf_blocked<T>(A, n, [](T p) { return p > T(0); });
+    if (bad < n && threadIdx.x == 0) record_error(mats[d.mat], d.col0 + bad);
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       const int c = idx / n, rr = idx - c * n;
-      if (rr >= c) L[(int64_t)c * m + rr] = rr == c ? piv[c] : A[idx] * rpiv[c];
+      if (rr >= c) L[(int64_t)c * m + rr] = A[idx];
     }
     __syncthreads();
     // a CTA's first task is its block index; only a grid smaller than the task list makes
@@ -402,37 +459,12 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
 // factored in FP32; if any pivot falls below tau (tau times the original diagonal, which
 // is 1 after equilibration), the block is factored again in FP64 from an FP64 copy of
 // its values, and the FP64 result is rounded into the panel.  err[2] counts such redos.
-// One pass of the right-looking factorization of the n x n block A (shared memory,
-// column-major) with one barrier per column: A_rc -= A_rj A_cj / p_j for j < c <= r (rows
-// spread over the threads, two per row for n <= 64), pivots p_j kept in piv.  Stops at the
-// first column whose pivot fails accept(p), returning it (every thread reads the same
-// pivot, so all stop together), else returns n.  The caller scales the columns.
-template <typename T, typename Accept>
-__device__ int potrf_pass(T* A, int n, T* piv, Accept accept) {
-  const bool two = n <= 64;
-  const int r = two ? (threadIdx.x & 63) : threadIdx.x;
-  const int cpar = two ? (threadIdx.x >> 6) : 0, cstep = two ? 2 : 1;
-  for (int j = 0; j < n; j++) {
-    const T p = A[j * n + j];
-    if (!accept(p)) return j;
-    if (threadIdx.x == 0) piv[j] = p;
-    if (r > j && r < n) {
-      const T arj = A[j * n + r] * (T(1) / p);
-      for (int c = j + 1 + cpar; c <= r; c += cstep) A[c * n + r] -= arj * A[j * n + c];
-    }
-    __syncthreads();
-  }
-  return n;
-}
-
 __global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                      const SnDev* __restrict__ sns,
                                                      const MatDev* __restrict__ mats,
                                                      float tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next_task;
-  __shared__ float fpiv[kMaxWidth];
-  __shared__ double dpiv[kMaxWidth];
   for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
@@ -447,26 +479,20 @@ __global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ ta
       D[idx] = (double)v;
     }
     __syncthreads();
-    const int stop = potrf_pass<float>(A, n, fpiv, [&](float p) { return p >= tau; });
+    const int stop = potrf_blocked<float>(A, n, [&](float p) { return p >= tau; });
     if (stop < n) {
       // a small FP32 pivot: the whole block again in FP64 from the FP64 copy
       if (threadIdx.x == 0) atomicAdd(mats[d.mat].err + 2, 1ull);
-      const MatDev md = mats[d.mat];
-      const int bad = potrf_pass<double>(D, n, dpiv, [](double p) { return p > 0.0; });
-      if (bad < n && threadIdx.x == 0) record_error(md, d.col0 + bad);
-      for (int j = threadIdx.x; j < n; j += blockDim.x)
-        dpiv[j] = j < bad ? sqrt(dpiv[j]) : 1.0;
-      __syncthreads();
+      const int bad = potrf_blocked<double>(D, n, [](double p) { return p > 0.0; });
+      if (bad < n && threadIdx.x == 0) record_error(mats[d.mat], d.col0 + bad);
       for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int c = idx / n, rr = idx - c * n;
-        if (rr >= c) L[(int64_t)c * m + rr] = rr == c ? (float)dpiv[c] : (float)(D[idx] / dpiv[c]);
+        if (rr >= c) L[(int64_t)c * m + rr] = (float)D[idx];
       }
     } else {
-      for (int j = threadIdx.x; j < n; j += blockDim.x) fpiv[j] = sqrtf(fpiv[j]);
-      __syncthreads();
       for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int c = idx / n, rr = idx - c * n;
-        if (rr >= c) L[(int64_t)c * m + rr] = rr == c ? fpiv[c] : A[idx] / fpiv[c];
+        if (rr >= c) L[(int64_t)c * m + rr] = A[idx];
       }
     }
     __syncthreads();
