@@ -103,13 +103,16 @@ class ClockSampler:
 
 KERNEL_SOURCES = ("factor_kernels.cu", "oz_kernels.cu", "tc_kernels.cu", "device_common.cuh",
                   "chol_internal.h")
+# the source files that define each traced kernel kind (its device code and shared helpers)
+KIND_SOURCES = {"schur128_oz": ("oz_kernels.cu", "device_common.cuh"),
+                "schur128_tc": ("tc_kernels.cu", "device_common.cuh")}
 
 
-def kernel_source_hash() -> str:
-    """Hash of the device kernel sources: a stored ncu traffic figure is used only while
-    the kernels it was measured on are unchanged."""
+def kernel_source_hash(kind: str | None = None) -> str:
+    """Hash of the device sources of a kernel kind (all kernel sources if unknown): a stored
+    ncu traffic figure is used only while the kernel it was measured on is unchanged."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KIND_SOURCES.get(kind, KERNEL_SOURCES):
         with open(os.path.join(ROOT, "paper_2202_09288_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -125,7 +128,7 @@ def ncu_traffic(kernel: str, flops_per_launch: float):
     with open(path) as f:
         d = json.load(f)
     e = d.get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return e["dram_bytes_per_flop"] * flops_per_launch
 
