@@ -11,7 +11,8 @@
 // device atomics or an owner-pulls assembly in a fixed order.
 //
 // FP64 throughput on GB300 is ~1 TFLOP/s for both DFMA and the FP64 `mma.sync` (DMMA)
-// path, with DMMA a few percent ahead; the Schur tiles therefore use m8n8k4 DMMA.
+// path, with DMMA a few percent ahead; the 32- and 64-wide Schur tiles here use m8n8k4
+// DMMA, the 128-wide ones the bf16 tensor cores (oz_kernels.cu).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,90 +33,148 @@ __global__ void k_assemble(const double* __restrict__ vals, const int64_t* __res
     L[amap[p]] = (T)vals[p];
 }
 
-// Blocked right-looking Cholesky of the n x n block A (shared memory, column-major, lower
-// part used; 128 threads): per block of 16 columns, (1) the 16 x 16 diagonal block by one
-// warp (lane = row, __syncwarp between columns), (2) the rows below it by forward
-// substitution, one row per thread in registers, (3) the trailing lower triangle minus the
-// block's rank-16 product, the row's 16 values in registers.  Three barriers per 16 columns.
-// A holds L on return (diagonal included).  A pivot p that fails accept(p) stops the
-// factorization (all threads see the same shared flag) and its column is returned; n
-// otherwise.
+// ---- diagonal-block Cholesky ---------------------------------------------------------------
+// Cost model on this part: an FP64 warp instruction occupies its SM sub-partition's FP64 unit
+// for ~64 cycles whether 1 or 32 lanes are active, a dependent DFMA chain advances one step
+// per ~64 cycles, and the library's double sqrt and reciprocal take ~690 and ~440 cycles.
+// The factorization is therefore organized so that (a) the serial per-column chain holds as
+// few FP64 instructions as possible and (b) the bulk of the work runs with every lane busy.
+
+// FMA in the block's precision.
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+// y = p^{-1/2} of a positive normal pivot: an FP32 seed y0 and one third-order correction.
+// With r = 1 - p y0^2, p^{-1/2} = y0 (1 - r)^{-1/2} = y0 (1 + r/2 + 3r^2/8 + O(r^3)); the seed
+// has |r| < 2^-20, so the dropped term is below 2^-58 relative, and the result is within an
+// ulp or so.  p is first scaled by an even power of two into [1, 4) with integer exponent
+// arithmetic (no FP32 overflow or underflow) and the result scaled back the same way: four
+// FP64 instructions in all.  Subnormal, infinite and NaN p take the library path.
+__device__ __forceinline__ double pivot_rsqrt(double p) {
+  const int hi = __double2hiint(p), lo = __double2loint(p);
+  const int ebits = (hi >> 20) & 0x7ff;
+  if (ebits == 0 || ebits == 0x7ff) return 1.0 / sqrt(p);
+  const int s = (ebits - 1023) & ~1;  // even, so that p 2^-s lies in [1, 4)
+  const double ps = __hiloint2double(hi - s * (1 << 20), lo);
+  const float y0f = rsqrtf((float)ps);
+  const double y0 = (double)y0f, c1 = (double)(0.5f * y0f), c2 = (double)(0.375f * y0f);
+  const double h = ps * y0;
+  const double r = fma(-h, y0, 1.0);
+  const double q = fma(r, c2, c1);  // y0/2 + 3 y0 r / 8
+  const double y = fma(q, r, y0);
+  return __hiloint2double(__double2hiint(y) - (s / 2) * (1 << 20), __double2loint(y));
+}
+// FP32: the hardware estimate and one Newton step.
+__device__ __forceinline__ float pivot_rsqrt(float p) {
+  const float y0 = rsqrtf(p);
+  const float r = fmaf(-p * y0, y0, 1.f);
+  return fmaf(0.5f * y0, r, y0);
+}
+
+// Right-looking Cholesky of the n x n block A (shared memory, column-major A[c * n + r]; only
+// the lower triangle is read or written) with a one-column lookahead and one barrier per
+// column.  Step j (column j final and scaled): warp 0 finishes column j+1 -- its update by
+// column j, the pivot's reciprocal square root, the scaling (the diagonal becomes p y =
+// sqrt(p)) -- while the other warps apply column j to columns j+2..n-1, the trailing lower
+// triangle flattened column-major over their threads, four elements per thread in flight.
+// Returns the first column whose pivot fails accept(p), else n.  A failed pivot does not stop
+// the loop (every thread passes the same barriers); the caller discards the block.
 template <typename T, typename Accept>
-__device__ int potrf_blocked(T* A, int n, Accept accept) {
-  constexpr int B = 16;
+__device__ int potrf_lookahead(T* A, int n, Accept accept) {
   __shared__ int s_bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_bad = n;
+  const int nupd = blockDim.x - 32;  // threads of the trailing update
+  if (warp == 0) {
+    const T p = A[0];
+    const T y = pivot_rsqrt(p);
+    if (lane == 0) s_bad = accept(p) ? n : 0;
+    __syncwarp();
+    for (int r = lane; r < n; r += 32) A[r] = (r == 0 ? p : A[r]) * y;
+  }
   __syncthreads();
-  for (int kb = 0; kb < n; kb += B) {
-    const int nb = min(B, n - kb);
-    // (1) diagonal block
+  for (int j = 0; j + 1 < n; j++) {
+    const T* lj = A + j * n;
     if (warp == 0) {
-      for (int j = 0; j < nb; j++) {
-        const int cj = kb + j;
-        const T p = A[cj * n + cj];
-        if (!accept(p)) {
-          if (lane == 0) s_bad = cj;
-          break;
+      const int c = j + 1;
+      T* ac = A + c * n;
+      const T lc = lj[c];
+      for (int r = c + lane; r < n; r += 32) ac[r] = fma_t(-lj[r], lc, ac[r]);
+      __syncwarp();
+      const T p = ac[c];
+      const T y = pivot_rsqrt(p);
+      if (lane == 0 && s_bad == n && !accept(p)) s_bad = c;
+      __syncwarp();
+      for (int r = c + lane; r < n; r += 32) ac[r] = (r == c ? p : ac[r]) * y;
+    } else {
+      const int k0 = j + 2, m = n - k0;
+      const int tri = m * (m + 1) / 2, w = 2 * m + 1;
+      for (int e0 = tid - 32; e0 < tri; e0 += 4 * nupd) {
+        int pos[4];
+        T lr[4], lcv[4], av[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int e = e0 + q * nupd;
+          pos[q] = -1;
+          if (e < tri) {
+            // column-major position e of the m x m lower triangle -> (c, r), r >= c:
+            // column c starts at c (2m - c + 1) / 2
+            int c = (int)((w - sqrtf((float)(w * w - 8 * e))) * 0.5f);
+            int cs = c * (w - c) / 2;
+            if (e < cs) {
+              c--;
+              cs = c * (w - c) / 2;
+            } else if (e >= cs + (m - c)) {
+              cs += m - c;
+              c++;
+            }
+            const int r = c + (e - cs);
+            pos[q] = (k0 + c) * n + k0 + r;
+            lr[q] = lj[k0 + r];
+            lcv[q] = lj[k0 + c];
+            av[q] = A[pos[q]];
+          }
         }
-        const T sq = sqrt(p), inv = T(1) / sq;
-        __syncwarp();
-        if (lane > j && lane < nb) A[cj * n + kb + lane] *= inv;
-        if (lane == j) A[cj * n + cj] = sq;
-        __syncwarp();
-        if (lane > j && lane < nb) {
-          const T lr = A[cj * n + kb + lane];
-          for (int c = j + 1; c <= lane; c++) A[(kb + c) * n + kb + lane] -= lr * A[cj * n + kb + c];
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    if (s_bad < n) return s_bad;
-    // (2) rows below: x = a L_bb^{-T}
-    const int r = kb + nb + tid;
-    if (r < n) {
-      T x[B];
 #pragma unroll
-      for (int j = 0; j < B; j++) {
-        if (j < nb) {
-          T acc = A[(kb + j) * n + r];
-#pragma unroll
-          for (int k = 0; k < j; k++) acc -= x[k] * A[(kb + k) * n + kb + j];
-          x[j] = acc / A[(kb + j) * n + kb + j];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < B; j++)
-        if (j < nb) A[(kb + j) * n + r] = x[j];
-    }
-    __syncthreads();
-    // (3) trailing update: A_rc -= sum_k L_rk L_ck for kb + nb <= c <= r
-    const int t0 = kb + nb, nt = n - t0;
-    if (nt > 0) {
-      const bool two = nt <= 64;
-      const int rr = t0 + (two ? (tid & 63) : tid);
-      const int cpar = two ? (tid >> 6) : 0, cstep = two ? 2 : 1;
-      if (rr < n) {
-        T lr[B];
-#pragma unroll
-        for (int k = 0; k < B; k++) lr[k] = k < nb ? A[(kb + k) * n + rr] : T(0);
-        for (int c = t0 + cpar; c <= rr; c += cstep) {
-          T acc = T(0);
-#pragma unroll
-          for (int k = 0; k < B; k++) acc += lr[k] * A[(kb + k) * n + c];
-          A[c * n + rr] -= acc;
-        }
+        for (int q = 0; q < 4; q++)
+          if (pos[q] >= 0) A[pos[q]] = fma_t(-lr[q], lcv[q], av[q]);
       }
     }
     __syncthreads();
   }
-  return n;
+  return s_bad;
+}
+
+// Asynchronous 4- or 8-byte global -> shared copy (cp.async, L1-allocating).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The lower triangle of a supernode's n x n diagonal block (panel column c, rows c..n-1, leading
+// dimension m) into A (column-major, leading dimension n): one warp per column, lanes along the
+// rows, every copy in flight at once.  Followed by cp_async_wait_all and a barrier.
+template <typename T>
+__device__ __forceinline__ void stage_diag_block(T* A, const T* __restrict__ L, int n, int m) {
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int c = threadIdx.x >> 5; c < n; c += nwarp)
+    for (int r = c + lane; r < n; r += 32) cp_async_elem(A + c * n + r, L + (int64_t)c * m + r);
+}
+template <typename T, typename S>
+__device__ __forceinline__ void store_diag_block(T* __restrict__ L, const S* A, int n, int m) {
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int c = threadIdx.x >> 5; c < n; c += nwarp)
+    for (int r = c + lane; r < n; r += 32) L[(int64_t)c * m + r] = (T)A[c * n + r];
 }
 
 // ---- POTRF of each diagonal block ---------------------------------------------------------
-// One CTA per supernode; the n x n lower block is factored in shared memory by the blocked
-// right-looking algorithm (potrf_blocked).
+// One CTA (128 threads) per supernode; the n x n block is factored in shared memory by
+// potrf_lookahead.  A non-positive pivot is an error (not SPD), recorded with its column.
 template <typename T>
 __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                const SnDev* __restrict__ sns,
@@ -128,18 +187,12 @@ __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, i
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
     T* L = reinterpret_cast<T*>(d.L);
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      int c = idx / n, r = idx - c * n;
-      A[idx] = r >= c ? L[(int64_t)c * m + r] : T(0);
-    }
+    stage_diag_block(A, L, n, m);
+    cp_async_wait_all();
     __syncthreads();
-    // a non-positive pivot is an error (not SPD); the rest of the block is left as is
-    const int bad = potrf_blocked<T>(A, n, [](T p) { return p > T(0); });
+    const int bad = potrf_lookahead<T>(A, n, [](T p) { return p > T(0); });
     if (bad < n && threadIdx.x == 0) record_error(mats[d.mat], d.col0 + bad);
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int c = idx / n, rr = idx - c * n;
-      if (rr >= c) L[(int64_t)c * m + rr] = A[idx];
-    }
+    store_diag_block(L, A, n, m);
     __syncthreads();
     // a CTA's first task is its block index; only a grid smaller than the task list makes
     // CTAs take further tasks from this launch's work queue
@@ -457,43 +510,39 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
 // ---- POTRF of the mixed-precision factor ---------------------------------------------------
 // FP32 panels of the equilibrated matrix (unit diagonal before updates).  The block is
 // factored in FP32; if any pivot falls below tau (tau times the original diagonal, which
-// is 1 after equilibration), the block is factored again in FP64 from an FP64 copy of
-// its values, and the FP64 result is rounded into the panel.  err[2] counts such redos.
+// is 1 after equilibration), the block is factored again in FP64 from the panel's values,
+// which are still unchanged in global memory, and the FP64 result is rounded into the panel.
+// err[2] counts such redos.  The FP64 block overlays the FP32 one in shared memory.
 __global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                      const SnDev* __restrict__ sns,
                                                      const MatDev* __restrict__ mats,
                                                      float tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next_task;
+  float* A = reinterpret_cast<float*>(smem_raw);    // n x n FP32 work block
+  double* D = reinterpret_cast<double*>(smem_raw);  // n x n FP64 block of a redo
   for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
     float* L = reinterpret_cast<float*>(d.L);
-    double* D = reinterpret_cast<double*>(smem_raw);   // n x n FP64 copy
-    float* A = reinterpret_cast<float*>(D + n * n);    // n x n FP32 work block
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      int c = idx / n, r = idx - c * n;
-      const float v = r >= c ? L[(int64_t)c * m + r] : 0.f;
-      A[idx] = v;
-      D[idx] = (double)v;
-    }
+    stage_diag_block(A, L, n, m);
+    cp_async_wait_all();
     __syncthreads();
-    const int stop = potrf_blocked<float>(A, n, [&](float p) { return p >= tau; });
+    const int stop = potrf_lookahead<float>(A, n, [&](float p) { return p >= tau; });
     if (stop < n) {
-      // a small FP32 pivot: the whole block again in FP64 from the FP64 copy
+      // a small FP32 pivot: the whole block again in FP64 (the barrier that ended the FP32
+      // pass is behind every thread, so D may overwrite A)
       if (threadIdx.x == 0) atomicAdd(mats[d.mat].err + 2, 1ull);
-      const int bad = potrf_blocked<double>(D, n, [](double p) { return p > 0.0; });
+      const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+      for (int c = threadIdx.x >> 5; c < n; c += nwarp)
+        for (int r = c + lane; r < n; r += 32) D[c * n + r] = (double)L[(int64_t)c * m + r];
+      __syncthreads();
+      const int bad = potrf_lookahead<double>(D, n, [](double p) { return p > 0.0; });
       if (bad < n && threadIdx.x == 0) record_error(mats[d.mat], d.col0 + bad);
-      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int c = idx / n, rr = idx - c * n;
-        if (rr >= c) L[(int64_t)c * m + rr] = (float)D[idx];
-      }
+      store_diag_block(L, D, n, m);
     } else {
-      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int c = idx / n, rr = idx - c * n;
-        if (rr >= c) L[(int64_t)c * m + rr] = A[idx];
-      }
+      store_diag_block(L, A, n, m);
     }
     __syncthreads();
     // a CTA's first task is its block index; only a grid smaller than the task list makes
@@ -614,7 +663,7 @@ void launch_assemble(const double* vals, const int64_t* amap, int64_t nnz, void*
 }
 
 static size_t potrf_smem(int w) { return (size_t)w * w * sizeof(double); }
-static size_t potrf_mixed_smem(int w) { return (size_t)w * w * (sizeof(double) + sizeof(float)); }
+static size_t potrf_mixed_smem(int w) { return (size_t)w * w * sizeof(double); }  // FP64 redo overlays FP32
 static size_t trsm_smem(int w) { return ((size_t)w * w + w + (size_t)w * 32) * sizeof(double); }
 
 void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
