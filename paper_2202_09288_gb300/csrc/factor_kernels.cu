@@ -71,25 +71,55 @@ __device__ __forceinline__ float pivot_rsqrt(float p) {
   return fmaf(0.5f * y0, r, y0);
 }
 
+// Position table of the trailing update: the lower triangle of columns 2..n-1 taken column by
+// column from the last (column n-1: 1 entry, column n-2: 2, ...), entry (C << 8) | R.  At step j
+// the entries of columns j+2..n-1 are the first (n-j-2)(n-j-1)/2, so every step's work is a
+// prefix, dealt evenly over the threads, and no index arithmetic is repeated per step.
+__device__ __forceinline__ void build_update_table(uint16_t* tab, int n) {
+  const int mm = n - 2, tot = mm > 0 ? mm * (mm + 1) / 2 : 0;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    int cc = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    if (cc * (cc + 1) / 2 > e) cc--;
+    else if ((cc + 1) * (cc + 2) / 2 <= e) cc++;
+    const int C = n - 1 - cc, R = C + (e - cc * (cc + 1) / 2);
+    tab[e] = (uint16_t)((C << 8) | R);
+  }
+}
+__host__ __device__ constexpr size_t update_table_bytes(int w) {
+  return w > 2 ? (size_t)(w - 2) * (w - 1) / 2 * sizeof(uint16_t) : 0;
+}
+
 // Right-looking Cholesky of the n x n block A (shared memory, column-major A[c * n + r]; only
-// the lower triangle is read or written) with a one-column lookahead and one barrier per
-// column.  Step j (column j final and scaled): warp 0 finishes column j+1 -- its update by
-// column j, the pivot's reciprocal square root, the scaling (the diagonal becomes p y =
-// sqrt(p)) -- while the other warps apply column j to columns j+2..n-1, the trailing lower
-// triangle flattened column-major over their threads, four elements per thread in flight.
-// Returns the first column whose pivot fails accept(p), else n.  A failed pivot does not stop
-// the loop (every thread passes the same barriers); the caller discards the block.
+// the lower triangle is read or written; n <= 128) with a one-column lookahead and one barrier
+// per column.  Step j (column j final and scaled): warp 0 finishes column j+1 in registers --
+// its update by column j, the pivot (a shuffle from the lane holding the diagonal), its
+// reciprocal square root, the scaling (the diagonal becomes p y = sqrt(p)) -- while the other
+// warps apply column j to columns j+2..n-1 through the position table (build_update_table),
+// four elements per thread in flight.  Returns the first column whose pivot fails accept(p),
+// else n.  A failed pivot does not stop the loop (every thread passes the same barriers); the
+// caller discards the block.
 template <typename T, typename Accept>
-__device__ int potrf_lookahead(T* A, int n, Accept accept) {
+__device__ int potrf_lookahead(T* A, int n, const uint16_t* tab, Accept accept) {
   __shared__ int s_bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nupd = blockDim.x - 32;  // threads of the trailing update
   if (warp == 0) {
-    const T p = A[0];
+    T v[4];
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+      if (32 * g >= n) break;
+      const int r = 32 * g + lane;
+      v[g] = r < n ? A[r] : T(0);
+    }
+    const T p = __shfl_sync(0xffffffffu, v[0], 0);
     const T y = pivot_rsqrt(p);
     if (lane == 0) s_bad = accept(p) ? n : 0;
-    __syncwarp();
-    for (int r = lane; r < n; r += 32) A[r] = (r == 0 ? p : A[r]) * y;
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+      if (32 * g >= n) break;
+      const int r = 32 * g + lane;
+      if (r < n) A[r] = v[g] * y;
+    }
   }
   __syncthreads();
   for (int j = 0; j + 1 < n; j++) {
@@ -98,39 +128,36 @@ __device__ int potrf_lookahead(T* A, int n, Accept accept) {
       const int c = j + 1;
       T* ac = A + c * n;
       const T lc = lj[c];
-      for (int r = c + lane; r < n; r += 32) ac[r] = fma_t(-lj[r], lc, ac[r]);
-      __syncwarp();
-      const T p = ac[c];
+      T v[4];
+#pragma unroll
+      for (int g = 0; g < 4; g++) {
+        if (c + 32 * g >= n) break;
+        const int r = c + 32 * g + lane;
+        v[g] = r < n ? fma_t(-lj[r], lc, ac[r]) : T(0);
+      }
+      const T p = __shfl_sync(0xffffffffu, v[0], 0);  // lane 0 holds row c
       const T y = pivot_rsqrt(p);
       if (lane == 0 && s_bad == n && !accept(p)) s_bad = c;
-      __syncwarp();
-      for (int r = c + lane; r < n; r += 32) ac[r] = (r == c ? p : ac[r]) * y;
+#pragma unroll
+      for (int g = 0; g < 4; g++) {
+        if (c + 32 * g >= n) break;
+        const int r = c + 32 * g + lane;
+        if (r < n) ac[r] = v[g] * y;
+      }
     } else {
-      const int k0 = j + 2, m = n - k0;
-      const int tri = m * (m + 1) / 2, w = 2 * m + 1;
-      for (int e0 = tid - 32; e0 < tri; e0 += 4 * nupd) {
+      const int m = n - j - 2, tot = m * (m + 1) / 2;
+      for (int e0 = tid - 32; e0 < tot; e0 += 4 * nupd) {
         int pos[4];
         T lr[4], lcv[4], av[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
           const int e = e0 + q * nupd;
           pos[q] = -1;
-          if (e < tri) {
-            // column-major position e of the m x m lower triangle -> (c, r), r >= c:
-            // column c starts at c (2m - c + 1) / 2
-            int c = (int)((w - sqrtf((float)(w * w - 8 * e))) * 0.5f);
-            int cs = c * (w - c) / 2;
-            if (e < cs) {
-              c--;
-              cs = c * (w - c) / 2;
-            } else if (e >= cs + (m - c)) {
-              cs += m - c;
-              c++;
-            }
-            const int r = c + (e - cs);
-            pos[q] = (k0 + c) * n + k0 + r;
-            lr[q] = lj[k0 + r];
-            lcv[q] = lj[k0 + c];
+          if (e < tot) {
+            const int ent = tab[e], C = ent >> 8, R = ent & 255;
+            pos[q] = C * n + R;
+            lr[q] = lj[R];
+            lcv[q] = lj[C];
             av[q] = A[pos[q]];
           }
         }
@@ -187,10 +214,12 @@ __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, i
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
     T* L = reinterpret_cast<T*>(d.L);
+    uint16_t* tab = reinterpret_cast<uint16_t*>(smem_raw + (size_t)n * n * sizeof(double));
     stage_diag_block(A, L, n, m);
+    build_update_table(tab, n);
     cp_async_wait_all();
     __syncthreads();
-    const int bad = potrf_lookahead<T>(A, n, [](T p) { return p > T(0); });
+    const int bad = potrf_lookahead<T>(A, n, tab, [](T p) { return p > T(0); });
     if (bad < n && threadIdx.x == 0) record_error(mats[d.mat], d.col0 + bad);
     store_diag_block(L, A, n, m);
     __syncthreads();
@@ -526,10 +555,12 @@ __global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ ta
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
     float* L = reinterpret_cast<float*>(d.L);
+    uint16_t* tab = reinterpret_cast<uint16_t*>(smem_raw + (size_t)n * n * sizeof(double));
     stage_diag_block(A, L, n, m);
+    build_update_table(tab, n);
     cp_async_wait_all();
     __syncthreads();
-    const int stop = potrf_lookahead<float>(A, n, [&](float p) { return p >= tau; });
+    const int stop = potrf_lookahead<float>(A, n, tab, [&](float p) { return p >= tau; });
     if (stop < n) {
       // a small FP32 pivot: the whole block again in FP64 (the barrier that ended the FP32
       // pass is behind every thread, so D may overwrite A)
@@ -538,7 +569,7 @@ __global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ ta
       for (int c = threadIdx.x >> 5; c < n; c += nwarp)
         for (int r = c + lane; r < n; r += 32) D[c * n + r] = (double)L[(int64_t)c * m + r];
       __syncthreads();
-      const int bad = potrf_lookahead<double>(D, n, [](double p) { return p > 0.0; });
+      const int bad = potrf_lookahead<double>(D, n, tab, [](double p) { return p > 0.0; });
       if (bad < n && threadIdx.x == 0) record_error(mats[d.mat], d.col0 + bad);
       store_diag_block(L, D, n, m);
     } else {
@@ -662,8 +693,10 @@ void launch_assemble(const double* vals, const int64_t* amap, int64_t nnz, void*
   else k_assemble<double><<<blocks, 256, 0, st>>>(vals, amap, nnz, (double*)L);
 }
 
-static size_t potrf_smem(int w) { return (size_t)w * w * sizeof(double); }
-static size_t potrf_mixed_smem(int w) { return (size_t)w * w * sizeof(double); }  // FP64 redo overlays FP32
+static size_t potrf_smem(int w) { return (size_t)w * w * sizeof(double) + update_table_bytes(w); }
+static size_t potrf_mixed_smem(int w) {  // the FP64 block of a redo overlays the FP32 one
+  return (size_t)w * w * sizeof(double) + update_table_bytes(w);
+}
 static size_t trsm_smem(int w) { return ((size_t)w * w + w + (size_t)w * 32) * sizeof(double); }
 
 void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
