@@ -11,7 +11,7 @@
 namespace chol {
 
 // Row blocks and tile shapes of the device task lists.
-constexpr int kTrsmRows = 128;   // off-diagonal rows per TRSM task (one row per thread)
+constexpr int kTrsmRows = 32;    // off-diagonal rows per TRSM task (one row per lane)
 constexpr int kSolveRows = 128;  // off-diagonal rows per solve task
 constexpr int kMaxWidth = 128;   // hard limit on the width cap W (diagonal block in smem)
 

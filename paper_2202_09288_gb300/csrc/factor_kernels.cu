@@ -187,10 +187,14 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // dimension m) into A (column-major, leading dimension n): one warp per column, lanes along the
 // rows, every copy in flight at once.  Followed by cp_async_wait_all and a barrier.
 template <typename T>
-__device__ __forceinline__ void stage_diag_block(T* A, const T* __restrict__ L, int n, int m) {
+__device__ __forceinline__ void stage_diag_block_ld(T* A, int lda, const T* __restrict__ L, int n, int m) {
   const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   for (int c = threadIdx.x >> 5; c < n; c += nwarp)
-    for (int r = c + lane; r < n; r += 32) cp_async_elem(A + c * n + r, L + (int64_t)c * m + r);
+    for (int r = c + lane; r < n; r += 32) cp_async_elem(A + c * lda + r, L + (int64_t)c * m + r);
+}
+template <typename T>
+__device__ __forceinline__ void stage_diag_block(T* A, const T* __restrict__ L, int n, int m) {
+  stage_diag_block_ld(A, n, L, n, m);
 }
 template <typename T, typename S>
 __device__ __forceinline__ void store_diag_block(T* __restrict__ L, const S* A, int n, int m) {
@@ -233,51 +237,100 @@ __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, i
 }
 
 // ---- TRSM of the off-diagonal rows --------------------------------------------------------
-// Task {s, r0}: rows r0 .. r0+kTrsmRows-1 of L21 (panel rows n + r0 + t), L21 = A21 L11^{-T},
-// one row per thread: x_j = (a_j - sum_{k<j} x_k L_jk) / L_jj.
-//   k_trsm_reg (W <= 64): the row lives in registers and is updated right-looking
-//     (x_k -= x_j L_kj for all k > j once x_j is final), so the FMAs of a column are
-//     independent; L11 is staged once per 128 rows.
-//   k_trsm (any W <= 128): the same substitution with the partial rows in shared memory,
-//     one warp at a time over the task's rows.
+// Task {s, r0}: rows r0 .. r0+kTrsmRows-1 of L21 (panel rows n + r0 + lane), L21 = A21 L11^{-T},
+// i.e. for each row x_j = (a_j - sum_{k<j} x_k L_jk) / L_jj.
+//   k_trsm (any W <= 128): the substitution itself, one thread per row, partial rows in
+//     shared memory.
+// k_trsm_blk (W <= 64): a task's 32 rows (lane = row) are solved by all four warps at once,
+//   16 columns at a time.  Block b (columns 16b .. 16b+15, diagonal block D_b of L11): every
+//   warp takes four of its columns (w, w+4, w+8, w+12) and subtracts the products with the
+//   solved columns of the earlier blocks, acc_k = a_k - sum_{j<16b} x_j L_kj; the partial
+//   vectors are exchanged through shared memory and the block is finished as x_b = D_b^{-1}
+//   acc_b with D_b^{-1} (lower triangular, formed per task by forward substitution on the
+//   unit vectors).  Each warp thus issues about a quarter of a row's FMAs: on this part an
+//   FP64 warp instruction holds its warp for ~64 cycles, so the row-per-thread form above
+//   (every FMA of the row in one warp) is four times longer per task.
 template <typename T>
-__global__ void __launch_bounds__(kTrsmRows) k_trsm_reg(const int4* __restrict__ tasks, int ntasks,
-                                                        int* __restrict__ queue,
-                                                        const SnDev* __restrict__ sns) {
-  __shared__ T Lc[64 * 64];  // Lc[j * 64 + k] = L11[k][j]
-  __shared__ T rd[64];
+constexpr size_t trsm_blk_smem() { return (64 * 64 + 64 * 32 + 16 * 32 + 4 * 16 * 16 + 64) * sizeof(T); }
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_trsm_blk(const int4* __restrict__ tasks, int ntasks,
+                                                  int* __restrict__ queue,
+                                                  const SnDev* __restrict__ sns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ls = reinterpret_cast<T*>(smem_raw);  // Ls[c * 64 + r] = L11[r][c]
+  T* Xs = Ls + 64 * 64;                     // Xs[k * 32 + lane]: solved column k of the rows
+  T* Acc = Xs + 64 * 32;                    // Acc[kk * 32 + lane]: block column kk before D_b^{-1}
+  T* Dv = Acc + 16 * 32;                    // Dv[b * 256 + k * 16 + i] = (D_b^{-1})[k][i], k >= i
+  T* rd = Dv + 4 * 16 * 16;                 // 1 / L11[k][k]
   __shared__ int s_next_task;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m;
     T* L = reinterpret_cast<T*>(d.L);
-    for (int idx = threadIdx.x; idx < n * 64; idx += blockDim.x) {
-      const int j = idx >> 6, k = idx & 63;
-      Lc[idx] = (k >= j && k < n) ? L[(int64_t)j * m + k] : T(0);
+    stage_diag_block_ld(Ls, 64, L, n, m);
+    // the warp's own columns k = 16 (q >> 2) + w + 4 (q & 3) of this task's row
+    const int row = n + tk.y + lane;
+    const bool live = row < m;
+    T a[16];
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+      const int k = 16 * (q >> 2) + w + 4 * (q & 3);
+      a[q] = (live && k < n) ? L[(int64_t)k * m + row] : T(0);
     }
+    cp_async_wait_all();
     __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) rd[j] = T(1) / Lc[j * 64 + j];
+    if (threadIdx.x < n) rd[threadIdx.x] = T(1) / Ls[threadIdx.x * 65];
     __syncthreads();
-    const int row = n + tk.y + threadIdx.x;
-    if (row < m) {
-      T x[64];
-#pragma unroll
-      for (int k = 0; k < 64; k++) x[k] = k < n ? L[(int64_t)k * m + row] : T(0);
-#pragma unroll
-      for (int j = 0; j < 64; j++) {
-        if (j < n) {
-          x[j] *= rd[j];
-#pragma unroll
-          for (int k = j + 1; k < 64; k++)
-            if (k < n) x[k] -= x[j] * Lc[j * 64 + k];
+    if (threadIdx.x < 64) {
+      const int b = threadIdx.x >> 4, i = threadIdx.x & 15, c0 = 16 * b;
+      if (c0 + i < n) {
+        T* dv = Dv + b * 256;
+        dv[i * 16 + i] = rd[c0 + i];
+        for (int k = i + 1; k < 16 && c0 + k < n; k++) {
+          T s = T(0);
+          for (int j = i; j < k; j++) s = fma_t(Ls[(c0 + j) * 64 + c0 + k], dv[j * 16 + i], s);
+          dv[k * 16 + i] = -s * rd[c0 + k];
         }
       }
-#pragma unroll
-      for (int k = 0; k < 64; k++)
-        if (k < n) L[(int64_t)k * m + row] = x[k];
     }
     __syncthreads();
+    T out[16] = {};
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      if (16 * b >= n) break;
+      T acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[q] = a[4 * b + q];
+      const T* lrow = Ls + 16 * b + w;  // + j * 64 + 4 q: L11[16b + w + 4q][j]
+      for (int j = 0; j < 16 * b; j++) {
+        const T xj = Xs[j * 32 + lane];
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[q] = fma_t(-xj, lrow[j * 64 + 4 * q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) Acc[(w + 4 * q) * 32 + lane] = acc[q];
+      __syncthreads();
+      const T* dv = Dv + b * 256;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int kk = w + 4 * q;
+        T s = T(0);
+        for (int i = 0; i <= kk; i++) s = fma_t(Acc[i * 32 + lane], dv[kk * 16 + i], s);
+        out[4 * b + q] = s;
+        Xs[(16 * b + kk) * 32 + lane] = s;
+      }
+      __syncthreads();
+    }
+    if (live) {
+#pragma unroll
+      for (int q = 0; q < 16; q++) {
+        const int k = 16 * (q >> 2) + w + 4 * (q & 3);
+        if (k < n) L[(int64_t)k * m + row] = out[q];
+      }
+    }
     // a CTA's first task is its block index; only a grid smaller than the task list makes
     // CTAs take further tasks from this launch's work queue
     if (gridDim.x >= ntasks) break;
@@ -717,7 +770,8 @@ template <typename T>
 static void trsm_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int max_width,
                    cudaStream_t st) {
   if (max_width <= 64) {
-    k_trsm_reg<T><<<persistent_grid(k_trsm_reg<T>, kTrsmRows, 0, ntasks), kTrsmRows, 0, st>>>(
+    constexpr size_t sm = trsm_blk_smem<T>();
+    k_trsm_blk<T><<<persistent_grid(k_trsm_blk<T>, 128, sm, ntasks), 128, sm, st>>>(
         tasks, ntasks, queue, sns);
     return;
   }
@@ -796,6 +850,8 @@ static bool set_smem(K kernel, size_t bytes) {
 int set_factor_kernel_attrs(int max_width) {
   bool ok = set_smem(k_potrf<double>, potrf_smem(max_width)) &&
             set_smem(k_potrf_mixed, potrf_mixed_smem(max_width)) &&
+            set_smem(k_trsm_blk<double>, trsm_blk_smem<double>()) &&
+            set_smem(k_trsm_blk<float>, trsm_blk_smem<float>()) &&
             set_smem(k_trsm<double>, trsm_smem(max_width)) &&
             set_smem(k_trsm<float>, trsm_smem(max_width));
   return ok ? CHOL_OK : CHOL_E_CUDA;
