@@ -268,10 +268,12 @@ constexpr int kOzMaxRuns = 16;  // column targets per task whose relative rows a
 
 // Per-task metadata, double-buffered: a task's scatter reads one copy while the next
 // task's is being built.
+static_assert(2 * kOzN == 128, "the run count sums four 32-column words");
 struct OzMeta {
   int eA[kOzM], eB[2 * kOzN];
   int tcol[2 * kOzN], run[2 * kOzN], col[2 * kOzN];
   int run_start[2 * kOzN + 1];
+  int wcnt[2 * kOzN / 32];  // run starts per 32 columns
   double* rL[kOzMaxRuns];
   int rm[kOzMaxRuns];
   long long rb[2 * kOzN];  // relative-map base of every run
@@ -472,31 +474,36 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       }
       oz_consumer_sync();
       if (!OWNER) {
-        if (warp == 0) {
-          int nr = 0;
-          for (int base = 0; base < 2 * kOzN; base += 32) {
-            const int kk = base + lane;
-            const bool start = k0 + kk < u && (kk == 0 || M.tcol[kk] != M.tcol[kk - 1]);
-            const unsigned bl = __ballot_sync(0xffffffffu, start);
-            if (start) M.run_start[nr + __popc(bl & ((1u << lane) - 1u))] = kk;
-            nr += __popc(bl);
-          }
-          __syncwarp();
-          if (lane == 0) M.nruns = nr;
-          for (int r = lane; r < nr; r += 32) {
-            const int kb = M.run_start[r];
-            const int ke = r + 1 < nr ? M.run_start[r + 1] : min(2 * kOzN, u - k0);
-            const SnDev& td = sns[md.sn_base + M.tcol[kb]];
-            M.rb[r] = md.run_base[find_run(md, d, k0 + kb)];
-            if (r < kOzMaxRuns) {
-              M.rL[r] = reinterpret_cast<double*>(td.L);
-              M.rm[r] = td.m;
+        // runs of equal target among the tile's columns, one thread per column (warps 0-3):
+        // a column starts a run when its target differs from its left neighbour's; its run
+        // index is the number of starts up to it, less one
+        const bool colthr = tid < 2 * kOzN;
+        bool start = false;
+        unsigned bl = 0;
+        if (colthr) {
+          start = k0 + tid < u && (tid == 0 || M.tcol[tid] != M.tcol[tid - 1]);
+          bl = __ballot_sync(0xffffffffu, start);
+          if (lane == 0) M.wcnt[warp] = __popc(bl);
+        }
+        oz_consumer_sync();
+        if (colthr) {
+          int off = 0;
+          for (int w2 = 0; w2 < warp; w2++) off += M.wcnt[w2];
+          if (k0 + tid < u) {
+            const int r = off + __popc(bl & ((2u << lane) - 1u)) - 1;
+            const SnDev& td = sns[md.sn_base + M.tcol[tid]];
+            M.run[tid] = r;
+            M.col[tid] = rows[k0 + tid] - td.col0;
+            if (start) {  // the run's first column fetches its target and map base
+              M.run_start[r] = tid;
+              M.rb[r] = md.run_base[find_run(md, d, k0 + tid)];
+              if (r < kOzMaxRuns) {
+                M.rL[r] = reinterpret_cast<double*>(td.L);
+                M.rm[r] = td.m;
+              }
             }
-            for (int kk = kb; kk < ke; kk++) {
-              M.run[kk] = r;
-              M.col[kk] = rows[k0 + kk] - td.col0;
-            }
           }
+          if (tid == 0) M.nruns = M.wcnt[0] + M.wcnt[1] + M.wcnt[2] + M.wcnt[3];
         }
         oz_consumer_sync();
         const int nrc = min(M.nruns, kOzMaxRuns);
