@@ -35,7 +35,8 @@ namespace chol {
 namespace {
 
 constexpr int kOzConsumers = 512;                          // 16 warps: drain + scatter
-constexpr int kOzThreads = kOzConsumers + 32;              // + the producer warp
+constexpr int kOzMetaThreads = 128;                        // 4 warps: per-task metadata
+constexpr int kOzThreads = kOzConsumers + 32 + kOzMetaThreads;  // + the producer warp
 constexpr int kOzRing = 16;
 constexpr int kOzM = 128;                                  // tile rows (UMMA M)
 constexpr int kOzN = 64;                                   // columns per half (UMMA N)
@@ -266,8 +267,8 @@ __device__ __forceinline__ double oz_to_double(long long W, int E) {
 
 constexpr int kOzMaxRuns = 16;  // column targets per task whose relative rows are cached
 
-// Per-task metadata, double-buffered: a task's scatter reads one copy while the next
-// task's is being built.
+// Per-task metadata, double-buffered: the metadata warps build the next task's copy while
+// the consumers scatter with the current one.
 static_assert(2 * kOzN == 128, "the run count sums four 32-column words");
 struct OzMeta {
   int eA[kOzM], eB[2 * kOzN];
@@ -281,9 +282,9 @@ struct OzMeta {
   int nruns;
 };
 
-// barrier among the consumer warps only (the producer warp runs on its own)
-__device__ __forceinline__ void oz_consumer_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kOzConsumers) : "memory");
+// barrier among the metadata warps only
+__device__ __forceinline__ void oz_meta_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kOzMetaThreads) : "memory");
 }
 
 __device__ __forceinline__ void oz_arrive(uint32_t bar) {
@@ -294,9 +295,11 @@ __device__ __forceinline__ void oz_arrive(uint32_t bar) {
 // A slices once and the B slices of every quarter into one of two quarter buffers, and
 // issues each quarter's MMAs into one of two TMEM sets of 8 diagonals x 32 columns; the 16
 // consumer warps drain a finished set (and release it) while the tensor cores compute the
-// next quarter, then scatter.  Barriers: a_full (A slices in), b_full[2] (quarter B
-// buffers in), acc_full[2] (a set's MMAs done: also frees the B buffer they read),
-// acc_empty[2] (a set drained), ring_full[] (the task order, for the consumers).
+// next quarter, then scatter; four metadata warps build each task's exponents, column
+// targets and relative rows ahead of use.  Barriers: a_full (A slices in), b_full[2]
+// (quarter B buffers in), acc_full[2] (a set's MMAs done: also frees the B buffer they
+// read), acc_empty[2] (a set drained), meta_full[2] / meta_empty[2] (a metadata buffer
+// built / released), ring_full[] (the task order, for the consumers and metadata warps).
 template <bool OWNER>
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_schur_oz(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
@@ -310,7 +313,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __shared__ __align__(8) uint64_t ring_full[kOzRing];
   __shared__ int ring[kOzRing];
   __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t meta_full[2], meta_empty[2];
   __shared__ OzMeta meta[2];
+  __shared__ int s_mtq;  // the metadata warps' next task (or ntasks: stop)
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
@@ -333,6 +338,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     }
     for (int i = 0; i < kOzRing; i++)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ring_full[i])));
+    for (int i = 0; i < 2; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&meta_full[i])),
+                   "r"(kOzMetaThreads));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&meta_empty[i])),
+                   "r"(kOzConsumers / 32));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -444,15 +455,87 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       }
       if (a_issued > a_use) oz_wait(smem_u32(&a_full), (uint32_t)(a_use & 1));
     }
+  } else if (warp > kOzConsumers / 32) {
+    // ---------------- metadata warps: one thread per tile row / column ----------------
+    // For each task in ring order, into meta[ord & 1] once the consumers have released it:
+    // the rows' and columns' slice exponents, every column's target supernode, the runs of
+    // equal target (ballot per 32 columns), each column's run and column inside its target,
+    // per run the relative-map base and target panel, and the relative rows of the first
+    // kOzMaxRuns runs.  Thread 0 alone waits on the ring and on the buffer, so that the
+    // group's decisions are uniform.
+    const int mt = tid - (kOzConsumers + 32), mwarp = mt >> 5;
+    for (int ord = 0;; ord++) {
+      const int buf = ord & 1;
+      if (mt == 0) {
+        const int rs = ord % kOzRing;
+        int tq = ntasks;
+        if (!oz_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kOzRing) & 1)) ||
+            (ring[rs] < ntasks && ord >= 2 &&
+             !oz_wait(smem_u32(&meta_empty[buf]), (uint32_t)(((ord >> 1) - 1) & 1))))
+          s_fail = 1;
+        else
+          tq = ring[rs];
+        s_mtq = tq;
+      }
+      oz_meta_sync();
+      const int tq = s_mtq;
+      oz_meta_sync();  // s_mtq is rewritten only after every thread has read it
+      if (tq >= ntasks) break;
+      OzMeta& M = meta[buf];
+      const int4 tk = tasks[tq];
+      const SnDev d = sns[tk.x];
+      const int n = d.n, u = d.m - n, i0 = tk.y, k0 = tk.z;
+      const int gk = k0 + mt;
+      M.eA[mt] = (i0 + mt < u) ? exps[tk.w + i0 + mt] : 0;
+      M.eB[mt] = gk < u ? exps[tk.w + gk] : 0;
+      if (!OWNER) {
+        const int32_t* rows = d.rows + n;
+        const MatDev md = mats[d.mat];
+        const int grow = gk < u ? rows[gk] : 0;
+        const int tc = gk < u ? md.col2sn[grow] : -1;
+        M.tcol[mt] = tc;
+        oz_meta_sync();
+        // a column starts a run when its target differs from its left neighbour's; its run
+        // index is the number of starts up to it, less one
+        const bool start = gk < u && (mt == 0 || M.tcol[mt - 1] != tc);
+        const unsigned bl = __ballot_sync(0xffffffffu, start);
+        if (lane == 0) M.wcnt[mwarp] = __popc(bl);
+        oz_meta_sync();
+        int off = 0;
+        for (int w2 = 0; w2 < mwarp; w2++) off += M.wcnt[w2];
+        if (gk < u) {
+          const int r = off + __popc(bl & ((2u << lane) - 1u)) - 1;
+          const SnDev& td = sns[md.sn_base + tc];
+          M.run[mt] = r;
+          M.col[mt] = grow - td.col0;
+          if (start) {  // the run's first column fetches its target and map base
+            M.run_start[r] = mt;
+            M.rb[r] = md.run_base[find_run(md, d, gk)];
+            if (r < kOzMaxRuns) {
+              M.rL[r] = reinterpret_cast<double*>(td.L);
+              M.rm[r] = td.m;
+            }
+          }
+        }
+        if (mt == 0) M.nruns = M.wcnt[0] + M.wcnt[1] + M.wcnt[2] + M.wcnt[3];
+        oz_meta_sync();
+        const int nrc = min(M.nruns, kOzMaxRuns);
+        for (int idx = mt; idx < nrc * kOzM; idx += kOzMetaThreads) {
+          const int r = idx / kOzM, ii = idx - r * kOzM, g = i0 + ii;
+          M.rp[r][ii] = (g < u && g >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + g] : -1;
+        }
+      }
+      oz_arrive(smem_u32(&meta_full[buf]));  // each thread after its own writes
+    }
   } else {
-    // ---------------- consumers: metadata, set drain, scatter ----------------
-    int ord = 0, buf = 0;
+    // ---------------- consumers: set drain and scatter ----------------
+    // Each wait's outcome is made uniform over the warp (tcgen05.ld is warp-collective).
     long long q = 0;
     const int i = 32 * (warp & 3) + lane;  // this thread's tile row
     const int c8 = 8 * (warp >> 2);        // this thread's 8 columns of a quarter
-    while (true) {
-      const int rs = ord % kOzRing;
-      if (!oz_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kOzRing) & 1))) {
+    for (int ord = 0;; ord++) {
+      const int rs = ord % kOzRing, buf = ord & 1;
+      if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kOzRing) & 1)))) {
         s_fail = 1;
         break;
       }
@@ -463,62 +546,18 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int n = d.n, u = d.m - n;
       const int i0 = tk.y, k0 = tk.z;
       const int nq = min(4, (u - k0 + kOzQ - 1) / kOzQ);
-      const int32_t* rows = d.rows + n;
       const MatDev md = mats[d.mat];
-      OzMeta& M = meta[buf];
-      for (int r = tid; r < kOzM; r += kOzConsumers) M.eA[r] = (i0 + r < u) ? exps[tk.w + i0 + r] : 0;
-      for (int kk = tid; kk < 2 * kOzN; kk += kOzConsumers) {
-        const int gk = k0 + kk;
-        M.eB[kk] = gk < u ? exps[tk.w + gk] : 0;
-        M.tcol[kk] = gk < u ? md.col2sn[rows[gk]] : -1;
-      }
-      oz_consumer_sync();
-      if (!OWNER) {
-        // runs of equal target among the tile's columns, one thread per column (warps 0-3):
-        // a column starts a run when its target differs from its left neighbour's; its run
-        // index is the number of starts up to it, less one
-        const bool colthr = tid < 2 * kOzN;
-        bool start = false;
-        unsigned bl = 0;
-        if (colthr) {
-          start = k0 + tid < u && (tid == 0 || M.tcol[tid] != M.tcol[tid - 1]);
-          bl = __ballot_sync(0xffffffffu, start);
-          if (lane == 0) M.wcnt[warp] = __popc(bl);
-        }
-        oz_consumer_sync();
-        if (colthr) {
-          int off = 0;
-          for (int w2 = 0; w2 < warp; w2++) off += M.wcnt[w2];
-          if (k0 + tid < u) {
-            const int r = off + __popc(bl & ((2u << lane) - 1u)) - 1;
-            const SnDev& td = sns[md.sn_base + M.tcol[tid]];
-            M.run[tid] = r;
-            M.col[tid] = rows[k0 + tid] - td.col0;
-            if (start) {  // the run's first column fetches its target and map base
-              M.run_start[r] = tid;
-              M.rb[r] = md.run_base[find_run(md, d, k0 + tid)];
-              if (r < kOzMaxRuns) {
-                M.rL[r] = reinterpret_cast<double*>(td.L);
-                M.rm[r] = td.m;
-              }
-            }
-          }
-          if (tid == 0) M.nruns = M.wcnt[0] + M.wcnt[1] + M.wcnt[2] + M.wcnt[3];
-        }
-        oz_consumer_sync();
-        const int nrc = min(M.nruns, kOzMaxRuns);
-        for (int idx = tid; idx < nrc * kOzM; idx += kOzConsumers) {
-          const int r = idx / kOzM, ii = idx - r * kOzM, g = i0 + ii;
-          M.rp[r][ii] = (g < u && g >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + g] : -1;
-        }
-        oz_consumer_sync();
+      const OzMeta& M = meta[buf];
+      if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&meta_full[buf]), (uint32_t)((ord >> 1) & 1)))) {
+        s_fail = 1;
+        break;
       }
       const int gi = i0 + i;
       const int eA = M.eA[i];
       bool stop = false;
       for (int j = 0; j < nq; j++, q++) {
         const int b = (int)(q & 1);
-        if (!oz_wait(smem_u32(&acc_full[b]), (uint32_t)((q >> 1) & 1))) {
+        if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&acc_full[b]), (uint32_t)((q >> 1) & 1)))) {
           s_fail = 1;
           stop = true;
           break;
@@ -589,8 +628,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         }
       }
       if (stop) break;
-      ord++;
-      buf ^= 1;
+      __syncwarp();
+      if (lane == 0) oz_arrive(smem_u32(&meta_empty[buf]));
     }
   }
   __syncthreads();

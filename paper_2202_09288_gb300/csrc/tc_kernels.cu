@@ -12,12 +12,13 @@
 //                 task's operand chunks (A hi/lo, B hi/lo: 64 KB) into a 3-stage shared
 //                 memory ring with bulk copies and issues the MMAs (M = N = 128, three per
 //                 K step of 8) into one of four 128-column tensor-memory accumulators;
-//                 16 consumer warps read finished accumulators (tcgen05.ld, one row per
-//                 thread) and scatter them into the ancestors with FP32 atomics (or write
-//                 the owner staging buffer), using the relative map.  Loads, MMAs and the
-//                 scatter of different tasks overlap through mbarriers: stage full/empty,
-//                 accumulator full/empty, and a ring that hands the task sequence to the
-//                 consumers.
+//                 four metadata warps build each task's column targets and relative rows
+//                 ahead of use, into one of two buffers; 16 consumer warps read finished
+//                 accumulators (tcgen05.ld, one row per thread) and scatter them into the
+//                 ancestors with FP32 atomics (or write the owner staging buffer).  Loads,
+//                 MMAs, metadata and the scatter of different tasks overlap through
+//                 mbarriers: stage full/empty, accumulator full/empty, metadata full/empty,
+//                 and a ring that hands the task sequence to the consumers.
 // Every wait is bounded: after kTfSpinLimit polls the thread records a timeout in err[3]
 // and stops; its partners then time out as well, waits for copies and MMAs in flight are
 // bounded too, and the tensor memory is freed before the kernel returns.
@@ -42,7 +43,8 @@ constexpr uint32_t kTfStageBytes = 4 * kTfPlane;   // A hi, A lo, B hi, B lo of 
 constexpr size_t kTfSmem = 1024 + kTfStages * kTfStageBytes;
 constexpr int kTfSlots = 4;                        // accumulators of 128 TMEM columns
 constexpr int kTfConsumers = 512;                  // 16 warps: drain + scatter
-constexpr int kTfThreads = kTfConsumers + 32;      // + the producer warp
+constexpr int kTfMetaThreads = 128;                // 4 warps: per-task column metadata
+constexpr int kTfThreads = kTfConsumers + 32 + kTfMetaThreads;  // + the producer warp
 constexpr int kTfRing = 16;
 constexpr int kTfMaxRuns = 16;
 constexpr long long kTfSpinLimit = 1ll << 24;
@@ -137,9 +139,9 @@ __device__ __forceinline__ void tf_tmem_load32(uint32_t addr, uint32_t (&r)[32])
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// barrier among the consumer warps only (the producer warp runs on its own)
-__device__ __forceinline__ void consumer_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kTfConsumers) : "memory");
+// barrier among the metadata warps only
+__device__ __forceinline__ void meta_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kTfMetaThreads) : "memory");
 }
 
 static_assert(kTfM == 128, "the run count sums four 32-column words");
@@ -211,7 +213,9 @@ __global__ void __launch_bounds__(kTfThreads, 1)
   __shared__ __align__(8) uint64_t ring_full[kTfRing];
   __shared__ int ring[kTfRing];
   __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t meta_full[2], meta_empty[2];
   __shared__ TfMeta meta[2];
+  __shared__ int s_mtq;  // the metadata warps' next task (or ntasks: stop)
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
@@ -235,6 +239,12 @@ __global__ void __launch_bounds__(kTfThreads, 1)
     }
     for (int i = 0; i < kTfRing; i++)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ring_full[i])));
+    for (int i = 0; i < 2; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&meta_full[i])),
+                   "r"(kTfMetaThreads));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&meta_empty[i])),
+                   "r"(kTfConsumers / 32));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -338,12 +348,81 @@ __global__ void __launch_bounds__(kTfThreads, 1)
       for (long long q = done; q < item; q++)
         tf_wait(smem_u32(&st_full[q % kTfStages]), (uint32_t)((q / kTfStages) & 1));
     }
+  } else if (warp > kTfConsumers / 32) {
+    // ---------------- metadata warps: one thread per tile column ----------------
+    // For each task in ring order, into meta[ord & 1] once the consumers have released it:
+    // every column's target supernode, the runs of equal target (ballot per 32 columns), each
+    // column's run and column inside its target, per run the relative-map base and target
+    // panel, and the relative rows of the first kTfMaxRuns runs.  Thread 0 alone waits on
+    // the ring and on the buffer, so that the group's decisions are uniform.
+    const int mt = tid - (kTfConsumers + 32), mwarp = mt >> 5;
+    for (int ord = 0;; ord++) {
+      const int buf = ord & 1;
+      if (mt == 0) {
+        const int rs = ord % kTfRing;
+        int tq = ntasks;
+        if (!tf_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kTfRing) & 1)) ||
+            (ring[rs] < ntasks && ord >= 2 &&
+             !tf_wait(smem_u32(&meta_empty[buf]), (uint32_t)(((ord >> 1) - 1) & 1))))
+          s_fail = 1;
+        else
+          tq = ring[rs];
+        s_mtq = tq;
+      }
+      meta_sync();
+      const int tq = s_mtq;
+      meta_sync();  // s_mtq is rewritten only after every thread has read it
+      if (tq >= ntasks) break;
+      TfMeta& M = meta[buf];
+      if (!OWNER) {
+        const int4 tk = tasks[tq];
+        const SnDev d = sns[tk.x];
+        const int n = d.n, u = d.m - n, i0 = tk.y, k0 = tk.z;
+        const int32_t* rows = d.rows + n;
+        const MatDev md = mats[d.mat];
+        const int gk = k0 + mt;
+        const int grow = gk < u ? rows[gk] : 0;
+        const int tc = gk < u ? md.col2sn[grow] : -1;
+        M.tcol[mt] = tc;
+        meta_sync();
+        // a column starts a run when its target differs from its left neighbour's; its run
+        // index is the number of starts up to it, less one
+        const bool start = gk < u && (mt == 0 || M.tcol[mt - 1] != tc);
+        const unsigned bl = __ballot_sync(0xffffffffu, start);
+        if (lane == 0) M.wcnt[mwarp] = __popc(bl);
+        meta_sync();
+        int off = 0;
+        for (int w2 = 0; w2 < mwarp; w2++) off += M.wcnt[w2];
+        if (gk < u) {
+          const int r = off + __popc(bl & ((2u << lane) - 1u)) - 1;
+          const SnDev& td = sns[md.sn_base + tc];
+          M.run[mt] = r;
+          M.col[mt] = grow - td.col0;
+          if (start) {  // the run's first column fetches its target and map base
+            M.run_start[r] = mt;
+            M.rb[r] = md.run_base[find_run(md, d, gk)];
+            if (r < kTfMaxRuns) {
+              M.rL[r] = reinterpret_cast<float*>(td.L);
+              M.rm[r] = td.m;
+            }
+          }
+        }
+        if (mt == 0) M.nruns = M.wcnt[0] + M.wcnt[1] + M.wcnt[2] + M.wcnt[3];
+        meta_sync();
+        const int nrc = min(M.nruns, kTfMaxRuns);
+        for (int idx = mt; idx < nrc * kTfM; idx += kTfMetaThreads) {
+          const int r = idx / kTfM, i = idx - r * kTfM, gi = i0 + i;
+          M.rp[r][i] = (gi < u && gi >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + gi] : -1;
+        }
+      }
+      tf_arrive(smem_u32(&meta_full[buf]));  // each thread after its own writes
+    }
   } else {
-    // ---------------- consumers: metadata, accumulator drain, scatter ----------------
-    int ord = 0, buf = 0;
-    while (true) {
-      const int rs = ord % kTfRing;
-      if (!tf_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kTfRing) & 1))) {
+    // ---------------- consumers: accumulator drain and scatter ----------------
+    // Each wait's outcome is made uniform over the warp (tcgen05.ld is warp-collective).
+    for (int ord = 0;; ord++) {
+      const int rs = ord % kTfRing, buf = ord & 1;
+      if (!__all_sync(0xffffffffu, tf_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kTfRing) & 1)))) {
         s_fail = 1;
         break;
       }
@@ -353,57 +432,11 @@ __global__ void __launch_bounds__(kTfThreads, 1)
       const SnDev d = sns[tk.x];
       const int n = d.n, u = d.m - n;
       const int i0 = tk.y, k0 = tk.z;
-      const int32_t* rows = d.rows + n;
       const MatDev md = mats[d.mat];
-      TfMeta& M = meta[buf];
-      if (!OWNER) {
-        for (int kk = tid; kk < kTfM; kk += kTfConsumers) {
-          const int gk = k0 + kk;
-          M.tcol[kk] = gk < u ? md.col2sn[rows[gk]] : -1;
-        }
-        consumer_sync();
-        // runs of equal target among the tile's columns, one thread per column (warps 0-3):
-        // a column starts a run when its target differs from its left neighbour's; its run
-        // index is the number of starts up to it, less one
-        const bool colthr = tid < kTfM;
-        bool start = false;
-        unsigned bl = 0;
-        if (colthr) {
-          start = k0 + tid < u && (tid == 0 || M.tcol[tid] != M.tcol[tid - 1]);
-          bl = __ballot_sync(0xffffffffu, start);
-          if (lane == 0) M.wcnt[warp] = __popc(bl);
-        }
-        consumer_sync();
-        if (colthr) {
-          int off = 0;
-          for (int w2 = 0; w2 < warp; w2++) off += M.wcnt[w2];
-          if (k0 + tid < u) {
-            const int r = off + __popc(bl & ((2u << lane) - 1u)) - 1;
-            const SnDev& td = sns[md.sn_base + M.tcol[tid]];
-            M.run[tid] = r;
-            M.col[tid] = rows[k0 + tid] - td.col0;
-            if (start) {  // the run's first column fetches its target and map base
-              M.run_start[r] = tid;
-              M.rb[r] = md.run_base[find_run(md, d, k0 + tid)];
-              if (r < kTfMaxRuns) {
-                M.rL[r] = reinterpret_cast<float*>(td.L);
-                M.rm[r] = td.m;
-              }
-            }
-          }
-          if (tid == 0) M.nruns = M.wcnt[0] + M.wcnt[1] + M.wcnt[2] + M.wcnt[3];
-        }
-        consumer_sync();
-        const int nrc = min(M.nruns, kTfMaxRuns);
-        for (int idx = tid; idx < nrc * kTfM; idx += kTfConsumers) {
-          const int r = idx / kTfM, i = idx - r * kTfM, gi = i0 + i;
-          M.rp[r][i] = (gi < u && gi >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + gi] : -1;
-        }
-        consumer_sync();
-      }
-      // the finished accumulator of this task
+      const TfMeta& M = meta[buf];
       const int acc = ord % kTfSlots;
-      if (!tf_wait(smem_u32(&acc_full[acc]), (uint32_t)((ord / kTfSlots) & 1))) {
+      if (!__all_sync(0xffffffffu, tf_wait(smem_u32(&meta_full[buf]), (uint32_t)((ord >> 1) & 1)) &&
+                                       tf_wait(smem_u32(&acc_full[acc]), (uint32_t)((ord / kTfSlots) & 1)))) {
         s_fail = 1;
         break;
       }
@@ -446,8 +479,8 @@ __global__ void __launch_bounds__(kTfThreads, 1)
           }
         }
       }
-      ord++;
-      buf ^= 1;
+      __syncwarp();
+      if (lane == 0) tf_arrive(smem_u32(&meta_empty[buf]));
     }
   }
   __syncthreads();
