@@ -271,15 +271,17 @@ constexpr int kOzMaxRuns = 16;  // column targets per task whose relative rows a
 // the consumers scatter with the current one.
 static_assert(2 * kOzN == 128, "the run count sums four 32-column words");
 struct OzMeta {
+  double* cp[2 * kOzN];  // each column's target panel column (its relative rows are added)
   int eA[kOzM], eB[2 * kOzN];
-  int tcol[2 * kOzN], run[2 * kOzN], col[2 * kOzN];
+  int tcol[2 * kOzN], run[2 * kOzN];
   int run_start[2 * kOzN + 1];
   int wcnt[2 * kOzN / 32];  // run starts per 32 columns
-  double* rL[kOzMaxRuns];
-  int rm[kOzMaxRuns];
   long long rb[2 * kOzN];  // relative-map base of every run
   int rp[kOzMaxRuns][kOzM];
   int nruns;
+  int u, i0, k0;           // the task: update order, tile origin
+  const int32_t* relmap;   // for runs beyond the cached ones
+  double* ustage;          // owner assembly: this supernode's staged U
 };
 
 // barrier among the metadata warps only
@@ -485,12 +487,19 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int4 tk = tasks[tq];
       const SnDev d = sns[tk.x];
       const int n = d.n, u = d.m - n, i0 = tk.y, k0 = tk.z;
+      const MatDev md = mats[d.mat];
       const int gk = k0 + mt;
       M.eA[mt] = (i0 + mt < u) ? exps[tk.w + i0 + mt] : 0;
       M.eB[mt] = gk < u ? exps[tk.w + gk] : 0;
+      if (mt == 0) {
+        M.u = u;
+        M.i0 = i0;
+        M.k0 = k0;
+        M.relmap = md.relmap;
+        M.ustage = OWNER ? static_cast<double*>(md.stage) + d.ustage : nullptr;
+      }
       if (!OWNER) {
         const int32_t* rows = d.rows + n;
-        const MatDev md = mats[d.mat];
         const int grow = gk < u ? rows[gk] : 0;
         const int tc = gk < u ? md.col2sn[grow] : -1;
         M.tcol[mt] = tc;
@@ -507,14 +516,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           const int r = off + __popc(bl & ((2u << lane) - 1u)) - 1;
           const SnDev& td = sns[md.sn_base + tc];
           M.run[mt] = r;
-          M.col[mt] = grow - td.col0;
-          if (start) {  // the run's first column fetches its target and map base
+          M.cp[mt] = reinterpret_cast<double*>(td.L) + (int64_t)(grow - td.col0) * td.m;
+          if (start) {  // the run's first column fetches its map base
             M.run_start[r] = mt;
             M.rb[r] = md.run_base[find_run(md, d, gk)];
-            if (r < kOzMaxRuns) {
-              M.rL[r] = reinterpret_cast<double*>(td.L);
-              M.rm[r] = td.m;
-            }
           }
         }
         if (mt == 0) M.nruns = M.wcnt[0] + M.wcnt[1] + M.wcnt[2] + M.wcnt[3];
@@ -539,19 +544,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         s_fail = 1;
         break;
       }
-      const int tq = ring[rs];
-      if (tq >= ntasks) break;
-      const int4 tk = tasks[tq];
-      const SnDev d = sns[tk.x];
-      const int n = d.n, u = d.m - n;
-      const int i0 = tk.y, k0 = tk.z;
-      const int nq = min(4, (u - k0 + kOzQ - 1) / kOzQ);
-      const MatDev md = mats[d.mat];
+      if (ring[rs] >= ntasks) break;
       const OzMeta& M = meta[buf];
       if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&meta_full[buf]), (uint32_t)((ord >> 1) & 1)))) {
         s_fail = 1;
         break;
       }
+      const int u = M.u, i0 = M.i0, k0 = M.k0;
+      const int nq = min(4, (u - k0 + kOzQ - 1) / kOzQ);
       const int gi = i0 + i;
       const int eA = M.eA[i];
       bool stop = false;
@@ -598,31 +598,25 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (gi < u) {
           const int kb = kOzQ * j + c8;
           if (OWNER) {
-            double* U = static_cast<double*>(md.stage) + d.ustage;
+            double* U = M.ustage;
 #pragma unroll
             for (int jj = 0; jj < 8; jj++) {
               const int gk = k0 + kb + jj;
               if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = val[jj];
             }
           } else {
+            // the relative row changes only with the run, which is the same for every lane
+            int rprev = -1, p = -1;
 #pragma unroll
             for (int jj = 0; jj < 8; jj++) {
               const int kk = kb + jj, gk = k0 + kk;
               if (gk >= u || gk > gi) continue;
               const int r = M.run[kk];
-              double* Lt;
-              int mt, p;
-              if (r < kOzMaxRuns) {
-                Lt = M.rL[r];
-                mt = M.rm[r];
-                p = M.rp[r][i];
-              } else {  // beyond the cached targets: read the relative map here
-                const SnDev& td = sns[md.sn_base + M.tcol[kk]];
-                Lt = reinterpret_cast<double*>(td.L);
-                mt = td.m;
-                p = md.relmap[M.rb[r] + gi];
+              if (r != rprev) {
+                rprev = r;
+                p = r < kOzMaxRuns ? M.rp[r][i] : M.relmap[M.rb[r] + gi];
               }
-              if (p >= 0) atomicAdd(&Lt[(int64_t)M.col[kk] * mt + p], val[jj]);
+              if (p >= 0) atomicAdd(M.cp[kk] + p, val[jj]);
             }
           }
         }

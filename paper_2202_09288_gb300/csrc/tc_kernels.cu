@@ -146,14 +146,16 @@ __device__ __forceinline__ void meta_sync() {
 
 static_assert(kTfM == 128, "the run count sums four 32-column words");
 struct TfMeta {
-  int tcol[kTfM], run[kTfM], col[kTfM];
+  float* cp[kTfM];  // each column's target panel column (its relative rows are added)
+  int tcol[kTfM], run[kTfM];
   int run_start[kTfM + 1];
   int wcnt[kTfM / 32];  // run starts per 32 columns
-  long long rb[kTfM];
-  float* rL[kTfMaxRuns];
-  int rm[kTfMaxRuns];
+  long long rb[kTfM];   // relative-map base of every run
   int rp[kTfMaxRuns][kTfM];
   int nruns;
+  int u, i0, k0;                 // the task: update order, tile origin
+  const int32_t* relmap;         // for runs beyond the cached ones
+  float* ustage;                 // owner assembly: this supernode's staged U
 };
 
 }  // namespace
@@ -374,12 +376,19 @@ __global__ void __launch_bounds__(kTfThreads, 1)
       meta_sync();  // s_mtq is rewritten only after every thread has read it
       if (tq >= ntasks) break;
       TfMeta& M = meta[buf];
+      const int4 tk = tasks[tq];
+      const SnDev d = sns[tk.x];
+      const int n = d.n, u = d.m - n, i0 = tk.y, k0 = tk.z;
+      const MatDev md = mats[d.mat];
+      if (mt == 0) {
+        M.u = u;
+        M.i0 = i0;
+        M.k0 = k0;
+        M.relmap = md.relmap;
+        M.ustage = OWNER ? static_cast<float*>(md.stage) + d.ustage : nullptr;
+      }
       if (!OWNER) {
-        const int4 tk = tasks[tq];
-        const SnDev d = sns[tk.x];
-        const int n = d.n, u = d.m - n, i0 = tk.y, k0 = tk.z;
         const int32_t* rows = d.rows + n;
-        const MatDev md = mats[d.mat];
         const int gk = k0 + mt;
         const int grow = gk < u ? rows[gk] : 0;
         const int tc = gk < u ? md.col2sn[grow] : -1;
@@ -397,14 +406,10 @@ __global__ void __launch_bounds__(kTfThreads, 1)
           const int r = off + __popc(bl & ((2u << lane) - 1u)) - 1;
           const SnDev& td = sns[md.sn_base + tc];
           M.run[mt] = r;
-          M.col[mt] = grow - td.col0;
-          if (start) {  // the run's first column fetches its target and map base
+          M.cp[mt] = reinterpret_cast<float*>(td.L) + (int64_t)(grow - td.col0) * td.m;
+          if (start) {  // the run's first column fetches its map base
             M.run_start[r] = mt;
             M.rb[r] = md.run_base[find_run(md, d, gk)];
-            if (r < kTfMaxRuns) {
-              M.rL[r] = reinterpret_cast<float*>(td.L);
-              M.rm[r] = td.m;
-            }
           }
         }
         if (mt == 0) M.nruns = M.wcnt[0] + M.wcnt[1] + M.wcnt[2] + M.wcnt[3];
@@ -426,13 +431,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
         s_fail = 1;
         break;
       }
-      const int tq = ring[rs];
-      if (tq >= ntasks) break;
-      const int4 tk = tasks[tq];
-      const SnDev d = sns[tk.x];
-      const int n = d.n, u = d.m - n;
-      const int i0 = tk.y, k0 = tk.z;
-      const MatDev md = mats[d.mat];
+      if (ring[rs] >= ntasks) break;
       const TfMeta& M = meta[buf];
       const int acc = ord % kTfSlots;
       if (!__all_sync(0xffffffffu, tf_wait(smem_u32(&meta_full[buf]), (uint32_t)((ord >> 1) & 1)) &&
@@ -441,6 +440,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
+      const int u = M.u, i0 = M.i0, k0 = M.k0;
       const int i = 32 * (warp & 3) + lane;  // this thread's tile row
       const int c0 = 32 * (warp >> 2);       // and its 32 columns
       uint32_t v[32];
@@ -451,31 +451,25 @@ __global__ void __launch_bounds__(kTfThreads, 1)
       const int gi = i0 + i;
       if (gi < u) {
         if (OWNER) {
-          float* U = static_cast<float*>(md.stage) + d.ustage;
+          float* U = M.ustage;
 #pragma unroll
           for (int j = 0; j < 32; j++) {
             const int gk = k0 + c0 + j;
             if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = __uint_as_float(v[j]);
           }
         } else {
+          // the relative row changes only with the run, which is the same for every lane
+          int rprev = -1, p = -1;
 #pragma unroll
           for (int j = 0; j < 32; j++) {
             const int kk = c0 + j, gk = k0 + kk;
             if (gk >= u || gk > gi) continue;
             const int r = M.run[kk];
-            float* Lt;
-            int mt, p;
-            if (r < kTfMaxRuns) {
-              Lt = M.rL[r];
-              mt = M.rm[r];
-              p = M.rp[r][i];
-            } else {  // beyond the cached targets: read the relative map here
-              const SnDev& td = sns[md.sn_base + M.tcol[kk]];
-              Lt = reinterpret_cast<float*>(td.L);
-              mt = td.m;
-              p = md.relmap[M.rb[r] + gi];
+            if (r != rprev) {
+              rprev = r;
+              p = r < kTfMaxRuns ? M.rp[r][i] : M.relmap[M.rb[r] + gi];
             }
-            if (p >= 0) atomicAdd(&Lt[(int64_t)M.col[kk] * mt + p], -__uint_as_float(v[j]));
+            if (p >= 0) atomicAdd(M.cp[kk] + p, -__uint_as_float(v[j]));
           }
         }
       }
