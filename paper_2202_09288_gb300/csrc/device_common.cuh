@@ -122,4 +122,30 @@ __device__ __forceinline__ void schur_tile_epilogue(const T* Cs, const SnDev& d,
   }
 }
 
+// Asynchronous 4- or 8-byte global -> shared copy (cp.async, L1-allocating).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The lower triangle of a supernode's n x n diagonal block (panel column c, rows c..n-1, leading
+// dimension m) into A (column-major, leading dimension lda, or n): one warp per column, lanes
+// along the rows, every copy in flight at once.  Followed by cp_async_wait_all and a barrier.
+template <typename T>
+__device__ __forceinline__ void stage_diag_block_ld(T* A, int lda, const T* __restrict__ L, int n, int m) {
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int c = threadIdx.x >> 5; c < n; c += nwarp)
+    for (int r = c + lane; r < n; r += 32) cp_async_elem(A + c * lda + r, L + (int64_t)c * m + r);
+}
+template <typename T>
+__device__ __forceinline__ void stage_diag_block(T* A, const T* __restrict__ L, int n, int m) {
+  stage_diag_block_ld(A, n, L, n, m);
+}
+
 }  // namespace chol

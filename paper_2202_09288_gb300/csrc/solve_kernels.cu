@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "chol_internal.h"
+#include "device_common.cuh"
 #include "kernels.h"
 #include "launch_util.h"
 
@@ -96,15 +97,14 @@ __device__ void warp_trisolve(const CT* L11, const CT* rdiag, CT* xs, int n, int
   }
 }
 
+// The lower triangle of L11 (the only part warp_trisolve reads) with every copy in flight
+// at once, then the reciprocals of its diagonal.
 template <typename P>
 __device__ void load_l11(const SnDev& d, P* L11, P* rdiag) {
-  const P* L = reinterpret_cast<const P*>(d.L);
-  const int n = d.n;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int c = idx / n, r = idx - c * n;
-    L11[idx] = r >= c ? L[(int64_t)c * d.m + r] : P(0);
-  }
+  stage_diag_block(L11, reinterpret_cast<const P*>(d.L), d.n, d.m);
+  cp_async_wait_all();
   __syncthreads();
+  const int n = d.n;
   for (int j = threadIdx.x; j < n; j += blockDim.x) rdiag[j] = P(1) / L11[j * n + j];
   __syncthreads();
 }
@@ -291,12 +291,21 @@ __global__ void __launch_bounds__(kSolveThreads)
     P* rdiag = L11 + n * n;
     P* xs = rdiag + n;
     const int u = d.m - n;
+    // w_s minus the partials of the supernode's backward tasks, summed in a fixed order with
+    // eight loads in flight
+    const int nq = u > 0 ? tk.z : 0;
     for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
       const int c = idx / n, j = idx - c * n;
-      double v = w[c * ldv + d.col0 + j];
-      if (u > 0)
-        for (int q = 0; q < tk.z; q++) v -= part[(tk.y - base + q) * W * nrhs + c * W + j];
-      xs[idx] = (P)v;
+      const double* pp = part + (tk.y - base) * W * nrhs + c * W + j;
+      const int64_t ps = (int64_t)W * nrhs;
+      double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int q = 0;
+      for (; q + 8 <= nq; q += 8) {
+#pragma unroll
+        for (int t = 0; t < 8; t++) a[t] += pp[(q + t) * ps];
+      }
+      for (; q < nq; q++) a[0] += pp[q * ps];
+      xs[idx] = (P)(w[c * ldv + d.col0 + j] - (((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]))));
     }
     load_l11<P>(d, L11, rdiag);
     warp_trisolve<false>(L11, rdiag, xs, n, nrhs);
