@@ -265,6 +265,19 @@ __device__ __forceinline__ double oz_to_double(long long W, int E) {
       (long long)(sign | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1))));
 }
 
+// The same value through the FP64 unit's conversion (cvt.rn.f64.s64 rounds to nearest,
+// ties to even, like oz_to_double) and an exponent-field add (exact inside the normal
+// range): bitwise the same result.  The consumers send half of their columns this way, so
+// that the conversions are shared between the otherwise idle FP64 unit and the integer ALU.
+__device__ __forceinline__ double oz_to_double_cvt(long long W, int E) {
+  if (W == 0) return 0.0;
+  const double d = __ll2double_rn(W);
+  const long long bits = __double_as_longlong(d);
+  const int be = (int)((bits >> 52) & 0x7ff) + E;
+  if (be <= 0 || be >= 2047) return ldexp(d, E);
+  return __longlong_as_double(bits + ((long long)E << 52));
+}
+
 constexpr int kOzMaxRuns = 16;  // column targets per task whose relative rows are cached
 
 // Per-task metadata, double-buffered: the metadata warps build the next task's copy while
@@ -591,7 +604,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 #pragma unroll
           for (int jj = 0; jj < 8; jj++) {
             const long long w = (long long)((unsigned long long)vh[jj] << 20) + ((vl[jj] + 128) >> 8);
-            val[jj] = oz_to_double(OWNER ? w : -w, eA + M.eB[kOzQ * j + c8 + jj] - 55);
+            const int e = eA + M.eB[kOzQ * j + c8 + jj] - 55;
+            val[jj] = (jj & 1) ? oz_to_double_cvt(OWNER ? w : -w, e) : oz_to_double(OWNER ? w : -w, e);
           }
         }
         // scatter this thread's row of the quarter (val holds -U for the atomics)
