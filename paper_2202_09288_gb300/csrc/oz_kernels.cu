@@ -268,6 +268,7 @@ struct OzMeta {
   int tcol[2 * kOzN], run[2 * kOzN];
   int run_start[2 * kOzN + 1];
   int wcnt[2 * kOzN / 32];  // run starts per 32 columns
+  int fcnt[kOzMetaThreads / 32];  // the supernode's runs before the tile, per warp
   long long rb[2 * kOzN];  // relative-map base of every run
   int rp[kOzMaxRuns][kOzM];
   int nruns;
@@ -495,6 +496,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         const int grow = gk < u ? rows[gk] : 0;
         const int tc = gk < u ? md.col2sn[grow] : -1;
         M.tcol[mt] = tc;
+        // the supernode's runs that start after position 0 and at or before k0: their count
+        // is the index (from run0) of the run holding the tile's first column; the tile's
+        // runs are that run and the ones after it, in order (runs split where the target
+        // changes, and so do the tile's)
+        int before = 0;
+        for (int t = 1 + mt; t < d.nrun; t += kOzMetaThreads) before += md.run_a[d.run0 + t] <= k0 ? 1 : 0;
+        before = __reduce_add_sync(0xffffffffu, before);
+        if (lane == 0) M.fcnt[mwarp] = before;
         oz_meta_sync();
         // a column starts a run when its target differs from its left neighbour's; its run
         // index is the number of starts up to it, less one
@@ -504,6 +513,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         oz_meta_sync();
         int off = 0;
         for (int w2 = 0; w2 < mwarp; w2++) off += M.wcnt[w2];
+        const int first = d.run0 + M.fcnt[0] + M.fcnt[1] + M.fcnt[2] + M.fcnt[3];
         if (gk < u) {
           const int r = off + __popc(bl & ((2u << lane) - 1u)) - 1;
           const SnDev& td = sns[md.sn_base + tc];
@@ -511,7 +521,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           M.cp[mt] = reinterpret_cast<double*>(td.L) + (int64_t)(grow - td.col0) * td.m;
           if (start) {  // the run's first column fetches its map base
             M.run_start[r] = mt;
-            M.rb[r] = md.run_base[find_run(md, d, gk)];
+            M.rb[r] = md.run_base[first + r];
           }
         }
         if (mt == 0) M.nruns = M.wcnt[0] + M.wcnt[1] + M.wcnt[2] + M.wcnt[3];
