@@ -60,6 +60,8 @@ def lib():
         L.orc_spmv.argtypes = [i64, p, p, p, p, p]
         L.orc_residual.argtypes = [i64, p, p, p, i64, p, i64, p, i64, p]
         L.orc_llt_error.argtypes = [i64, p, p, p, p, p, p, p, p]
+        L.orc_opt_d.argtypes = [i64, C.c_int32, p, p]
+        L.orc_hybrid_uses_blas.argtypes = [i64, C.c_int32, i64]
         _lib = L
     return _lib
 
@@ -166,6 +168,22 @@ def residual(n, colptr, rowind, vals, B, X):
     lib().orc_residual(n, _ptr(colptr), _ptr(rowind), _ptr(vals), B.shape[1], _ptr(B), n,
                        _ptr(X), n, C.byref(rel))
     return rel.value
+
+
+def opt_d(n, counts) -> int:
+    """Threshold D of the OPT-D heuristic (Sec. 4.1, Algorithm 1) for outer tasks with the
+    given numbers of inner tasks."""
+    c = _c(np.asarray(counts, dtype=np.int32), np.int32)
+    d = C.c_int32()
+    rc = lib().orc_opt_d(int(n), len(c), _ptr(c) if len(c) else None, C.byref(d))
+    if rc != 0:
+        raise ValueError(f"orc_opt_d: {rc}")
+    return d.value
+
+
+def hybrid_uses_blas(n, nsuper, nnz) -> bool:
+    """The hybrid switch of Sec. 4.3: True selects multi-threaded BLAS per supernode."""
+    return bool(lib().orc_hybrid_uses_blas(int(n), int(nsuper), int(nnz)))
 
 
 def llt_error(n, bp, bi, bx, lp, li, lx):

@@ -332,3 +332,51 @@ int orc_llt_error(int64_t n, const int64_t* Bp, const int32_t* Bi, const double*
   *b_f = sqrt(b2);
   return 0;
 }
+
+/*
+ * Task-granularity threshold D of the OPT-D heuristic (Sec. 4.1, Algorithm 1), in the
+ * paper's order and names:
+ *   goalTasks = max(1.1 nsuper, n / 14);
+ *   maxChildren = max_i C[i];  T[k] = number of outer tasks with exactly k inner tasks
+ *   (a bucket count);
+ *   D = maxChildren + 1, numOuterTasks = 0, numTasks = nsuper; then, while
+ *   (numTasks < goalTasks or D > 0.3 maxChildren or numOuterTasks < nsuper / 1000) and
+ *   D > 0: D = D - 1, numOuterTasks += T[D], numTasks += D T[D].
+ * C[i] >= 0 is the number of inner tasks of outer task i.  Returns 0 and D in *D_out, or
+ * ORC_EINVAL (negative count, nsuper < 0) / ORC_ENOMEM.
+ */
+int orc_opt_d(int64_t n, int32_t nsuper, const int32_t* C, int32_t* D_out) {
+  if (nsuper < 0 || n < 0 || (nsuper > 0 && !C) || !D_out) return ORC_EINVAL;
+  int32_t maxc = 0;
+  for (int32_t i = 0; i < nsuper; i++) {
+    if (C[i] < 0) return ORC_EINVAL;
+    if (C[i] > maxc) maxc = C[i];
+  }
+  int64_t* T = (int64_t*)calloc((size_t)maxc + 1, sizeof(int64_t));
+  if (!T) return ORC_ENOMEM;
+  for (int32_t i = 0; i < nsuper; i++) T[C[i]]++;
+  const double goal = fmax(1.1 * (double)nsuper, (double)n / 14.0);
+  int64_t D = (int64_t)maxc + 1, outer = 0;
+  double tasks = (double)nsuper;
+  while ((tasks < goal || (double)D > 0.3 * (double)maxc || (double)outer < (double)nsuper / 1000.0) &&
+         D > 0) {
+    D--;
+    outer += T[D];
+    tasks += (double)D * (double)T[D];
+  }
+  free(T);
+  *D_out = (int32_t)D;
+  return 0;
+}
+
+/*
+ * The hybrid switch of Sec. 4.3: multi-threaded BLAS on each supernode (returns 1) when the
+ * average supernode size n / nsuper exceeds 50, or exceeds 20 while the density
+ * nnz / (n n) of the matrix is below 1e-4; otherwise the nested-task heuristic (returns 0).
+ */
+int orc_hybrid_uses_blas(int64_t n, int32_t nsuper, int64_t nnz) {
+  if (n <= 0 || nsuper <= 0) return 0;
+  const double avg = (double)n / (double)nsuper;
+  const double density = (double)nnz / ((double)n * (double)n);
+  return avg > 50.0 || (avg > 20.0 && density < 1e-4);
+}

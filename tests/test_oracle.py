@@ -3,6 +3,7 @@ library routines (numpy.linalg.cholesky), a textbook row-oriented Cholesky in pu
 Python, graph elimination by brute force, closed forms (1D Laplacian), the paper's
 Fig. 1 level sets (Sec. 3) and exact invariants."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -228,3 +229,48 @@ def test_residual_and_spmv_definitions():
     x2 = inputs.uniform(3, 5, 25)
     assert np.allclose(oracle.spmv(25, A2.colptr, A2.rowind, A2.vals, x2), A2.to_dense() @ x2,
                        rtol=0, atol=1e-14)
+
+
+# ---- OPT-D threshold (Sec. 4.1, Algorithm 1) and the hybrid switch (Sec. 4.3) -------------
+
+def _opt_d_cases():
+    path = os.path.join(os.path.dirname(__file__), "golden", "opt_d_cases.txt")
+    cases = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        n, counts, d, why = [f.strip() for f in line.split(";")]
+        c = []
+        for item in counts.split(","):
+            v, rep = item.split("*")
+            c += [int(v)] * int(rep)
+        cases.append((int(n), c, int(d), why))
+    return cases
+
+
+@pytest.mark.parametrize("case", _opt_d_cases(), ids=lambda c: c[3])
+def test_opt_d_hand_computed(case):
+    n, counts, d, _ = case
+    assert oracle.opt_d(n, counts) == d
+
+
+def test_opt_d_bounds_and_empty():
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        ns = int(rng.integers(1, 400))
+        c = rng.integers(0, 60, size=ns)
+        d = oracle.opt_d(int(rng.integers(1, 100000)), c)
+        assert 0 <= d <= c.max() + 1
+    assert oracle.opt_d(100, []) == 0
+    with pytest.raises(ValueError):
+        oracle.opt_d(10, [1, -1])
+
+
+def test_hybrid_switch_cases():
+    # average supernode size n / nsuper and density nnz / n^2, by hand
+    assert oracle.hybrid_uses_blas(1000, 10, 10**6)          # avg 100 > 50
+    assert oracle.hybrid_uses_blas(1000, 40, 50)             # avg 25 > 20, density 5e-5 < 1e-4
+    assert not oracle.hybrid_uses_blas(1000, 40, 1000)       # avg 25, density 1e-3
+    assert not oracle.hybrid_uses_blas(1000, 100, 10)        # avg 10
+    assert not oracle.hybrid_uses_blas(1000, 20, 10)         # avg exactly 50 is not above 50
