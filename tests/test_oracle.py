@@ -273,4 +273,5 @@ def test_hybrid_switch_cases():
     assert oracle.hybrid_uses_blas(1000, 40, 50)             # avg 25 > 20, density 5e-5 < 1e-4
     assert not oracle.hybrid_uses_blas(1000, 40, 1000)       # avg 25, density 1e-3
     assert not oracle.hybrid_uses_blas(1000, 100, 10)        # avg 10
-    assert not oracle.hybrid_uses_blas(1000, 20, 10)         # avg exactly 50 is not above 50
+    assert not oracle.hybrid_uses_blas(1000, 20, 10**5)      # avg exactly 50 (not above), density 0.1
+    assert oracle.hybrid_uses_blas(1000, 20, 10)             # avg 50 > 20 and density 1e-5 < 1e-4
