@@ -43,6 +43,9 @@ OZ_PRODUCTS = 36  # slice pairs p + q < 8 of the FP64 tensor-core Schur tiles
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 rates of a GB300
 
 
+
+GRANULARITY = {"tiles": 0, "optd": 1, "optd_cost": 2, "hybrid": 3}
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -393,6 +396,9 @@ def main():
     ap.add_argument("--policy", default="",
                     help="Schur tile policy overrides as JSON, e.g. "
                          "'{\"min_rows_tile128\": 1073741824}' (no 128-wide tiles)")
+    ap.add_argument("--granularity", default="tiles", choices=list(GRANULARITY),
+                    help="Schur task granularity: size thresholds alone (tiles), or the paper's "
+                         "OPT-D / OPT-D-COST / hybrid rules applied to the tiles")
     ap.add_argument("--fp64-schur", default="ozaki", choices=["ozaki", "dmma"],
                     help="FP64 128-wide Schur tiles: bf16 tensor-core slices or FP64 DMMA")
     ap.add_argument("--relax", type=float, default=0.0,
@@ -448,6 +454,8 @@ def main():
     sym = P.Symbolic(ctx, A, perm)
     if args.policy:
         P.chol_sym_set_tile_policy(sym.handle, json.loads(args.policy))
+    if args.granularity != "tiles":
+        P.chol_sym_set_tile_policy(sym.handle, {"granularity": GRANULARITY[args.granularity]})
     F = sym.info["flops"]
     vals_d = torch.from_numpy(A.vals).cuda()
     b_d = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()  # (k, n): column c = row c
@@ -586,6 +594,7 @@ def main():
                        nsuper=sym.info["nsuper"], nfundamental=sym.info["nfundamental"],
                        nlevels=sym.info["nlevels"],
                        tile_policy=P.chol_sym_get_tile_policy(sym.handle),
+                       granularity=P.chol_sym_granularity(sym.handle),
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "factor_ms": fac_ms, "solve_ms": sol_ms,
         "factor_gflops": F / (fac_ms * 1e-3) / 1e9,

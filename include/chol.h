@@ -250,20 +250,45 @@ void chol_batch_free(chol_batch* batch);
  * min_rows_tile128 off-diagonal rows on levels holding at least min_level_tiles128 such
  * tiles, else 64x64 tiles from min_rows_tile64 rows on levels holding at least
  * min_level_tiles64 such tiles, else 32x32 from min_rows_tile32 rows, else 16x16.
- * Default {64, 17, 304, 128, 0}.  A 128x128 tile of an FP32 (mixed-precision) factor is
- * one tcgen05 tensor-core task (3xTF32); of an FP64 factor, four 64x64 tasks.  All
- * fields >= 1 except the two level thresholds (>= 0); anything else is CHOL_E_INVALID. */
+ * A 128x128 tile is one tcgen05 tensor-core task: 3xTF32 for an FP32 (mixed-precision)
+ * factor, exact bf16 operand slices for an FP64 factor (four 64x64 DMMA tasks under
+ * CHOL_SCHUR_DMMA).
+ * granularity (Sec. 4 of the paper, re-targeted to tiles): CHOL_GRAN_TILES uses the size
+ * thresholds alone.  Otherwise a supernode's Schur update is an outer task and the tiles
+ * the thresholds give it are its inner tasks; an outer task with more than D inner tasks
+ * (D by the OPT-D heuristic, Algorithm 1, over all supernodes) is split into those tiles,
+ * the others are done whole (the coarsest tile that covers the update in one task, 128
+ * wide above 64 rows).  CHOL_GRAN_OPTD_COST also keeps whole an outer task whose tiles
+ * would carry fewer than 50,000 flops each (OPT-D-COST); CHOL_GRAN_HYBRID takes
+ * CHOL_GRAN_TILES when the average supernode size is above 50, or above 20 with density
+ * nnz(A) / n^2 below 1e-4, and CHOL_GRAN_OPTD_COST otherwise.
+ * Default {64, 17, 304, 128, 0, CHOL_GRAN_TILES}.  All thresholds >= 1 except the two
+ * level thresholds (>= 0), granularity one of the four; anything else is CHOL_E_INVALID. */
+#define CHOL_GRAN_TILES 0
+#define CHOL_GRAN_OPTD 1
+#define CHOL_GRAN_OPTD_COST 2
+#define CHOL_GRAN_HYBRID 3
 typedef struct chol_tile_policy {
   int min_rows_tile64;
   int min_rows_tile32;
   int min_level_tiles64;
   int min_rows_tile128;
   int min_level_tiles128;
+  int granularity;
 } chol_tile_policy;
 int chol_sym_get_tile_policy(const chol_sym* sym, chol_tile_policy* policy);
 /* Rebuilds the Schur task lists of sym (and its device copy); factors made from sym use
  * the new lists from their next factorization; existing batches keep their own copy. */
 int chol_sym_set_tile_policy(chol_sym* sym, const chol_tile_policy* policy);
+/* The threshold D of the OPT-D heuristic (Sec. 4.1, Algorithm 1) for nsuper outer tasks
+ * with counts[i] inner tasks each (host array, counts[i] >= 0; NULL allowed when nsuper
+ * is 0) and matrix size n: the outer tasks with more than D inner tasks are the ones to
+ * split.  CHOL_E_INVALID on n < 0, nsuper < 0 or a negative count. */
+int chol_opt_d(int64_t n, int32_t nsuper, const int32_t* counts, int32_t* D);
+/* The granularity rule of sym's current task lists: *rule the CHOL_GRAN_* value applied
+ * (CHOL_GRAN_HYBRID resolved to the rule it chose), *D its threshold (-1 under
+ * CHOL_GRAN_TILES), *nsplit the number of supernodes whose Schur update is split. */
+int chol_sym_granularity(const chol_sym* sym, int* rule, int32_t* D, int32_t* nsplit);
 /* Autotuner: times refactorizations of num (reps each) under candidate tile policies by
  * coordinate descent over the five thresholds, keeps the fastest in num's analysis,
  * stores it in *best (and its time in *best_ms) and leaves num factored under it. */

@@ -24,6 +24,7 @@ CHOL_HOST, CHOL_DEVICE = 0, 1
 CHOL_ASSEMBLY_ATOMIC, CHOL_ASSEMBLY_OWNER = 0, 1
 CHOL_FP64, CHOL_MIXED = 0, 1
 CHOL_SCHUR_OZAKI, CHOL_SCHUR_DMMA = 0, 1
+CHOL_GRAN_TILES, CHOL_GRAN_OPTD, CHOL_GRAN_OPTD_COST, CHOL_GRAN_HYBRID = 0, 1, 2, 3
 
 
 class CholError(RuntimeError):
@@ -54,7 +55,8 @@ class chol_refine_info(C.Structure):
 class chol_tile_policy(C.Structure):
     _fields_ = [("min_rows_tile64", C.c_int), ("min_rows_tile32", C.c_int),
                 ("min_level_tiles64", C.c_int), ("min_rows_tile128", C.c_int),
-                ("min_level_tiles128", C.c_int)]
+                ("min_level_tiles128", C.c_int),
+                ("granularity", C.c_int)]
 
 
 class chol_server_opts(C.Structure):
@@ -110,6 +112,8 @@ EXPORTS = {
     "chol_sym_get_tile_policy": (_I, [_P, C.POINTER(chol_tile_policy)]),
     "chol_sym_set_tile_policy": (_I, [_P, C.POINTER(chol_tile_policy)]),
     "chol_autotune": (_I, [_P, _P, _I, C.POINTER(chol_tile_policy), C.POINTER(C.c_double)]),
+    "chol_opt_d": (_I, [C.c_int64, C.c_int32, _P, C.POINTER(C.c_int32)]),
+    "chol_sym_granularity": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "chol_default_server_opts": (None, [C.POINTER(chol_server_opts)]),
     "chol_server_create": (_I, [C.POINTER(chol_server_opts), C.POINTER(_P)]),
     "chol_submit": (_I, [_P, C.POINTER(chol_request), C.POINTER(C.c_uint64)]),
@@ -360,6 +364,24 @@ def chol_sym_set_tile_policy(sym, policy: dict) -> None:
     for f, v in policy.items():  # fields not given keep their current value
         setattr(p, f, v)
     _check(lib().chol_sym_set_tile_policy(sym, C.byref(p)), "chol_sym_set_tile_policy")
+
+
+def chol_opt_d(n: int, counts) -> int:
+    """Threshold D of the OPT-D heuristic (Sec. 4.1, Algorithm 1) for outer tasks with the
+    given numbers of inner tasks."""
+    c = np.ascontiguousarray(counts, dtype=np.int32)
+    d = C.c_int32()
+    _check(lib().chol_opt_d(int(n), len(c), c.ctypes.data_as(C.c_void_p) if len(c) else None,
+                            C.byref(d)), "chol_opt_d")
+    return d.value
+
+
+def chol_sym_granularity(sym) -> dict:
+    """The granularity rule of sym's task lists: {"rule", "D", "nsplit"}."""
+    rule, d, nsplit = C.c_int(), C.c_int32(), C.c_int32()
+    _check(lib().chol_sym_granularity(sym, C.byref(rule), C.byref(d), C.byref(nsplit)),
+           "chol_sym_granularity")
+    return {"rule": rule.value, "D": d.value, "nsplit": nsplit.value}
 
 
 def chol_autotune(ctx, num, reps=1) -> tuple[dict, float]:

@@ -34,6 +34,14 @@ int choose_tile_class(const TilePolicy& p, int64_t u, int64_t level_tiles64,
   return kTile16;
 }
 
+// The coarsest tile class that covers an update of u rows in one task (128 wide above 64).
+int whole_tile_class(int64_t u) {
+  if (u <= 16) return kTile16;
+  if (u <= 32) return kTile32;
+  if (u <= 64) return kTile64;
+  return kTile128;
+}
+
 void push4(std::vector<int32_t>& v, int32_t a, int32_t b, int32_t c, int32_t d) {
   v.push_back(a); v.push_back(b); v.push_back(c); v.push_back(d);
 }
@@ -471,6 +479,30 @@ void build_owner_lists(Sym* S) {
   S->owner_lists = true;
 }
 
+int32_t opt_d_threshold(int64_t n, int32_t nsuper, const int32_t* counts) {
+  // outer tasks by their number of inner tasks (a counting sort), walked from the largest
+  // count down: lowering D to d splits the outer tasks with d inner tasks, adding d tasks
+  // each; stop once the task total reaches max(1.1 nsuper, n / 14), D is at most 30 % of
+  // the largest count and at least 0.1 % of the outer tasks are split (Sec. 4.1)
+  int32_t top = 0;
+  for (int32_t i = 0; i < nsuper; i++) top = std::max(top, counts[i]);
+  std::vector<int64_t> with(static_cast<size_t>(top) + 1, 0);
+  for (int32_t i = 0; i < nsuper; i++) with[counts[i]]++;
+  const double goal = std::max(1.1 * nsuper, static_cast<double>(n) / 14.0);
+  int64_t d = static_cast<int64_t>(top) + 1, split = 0;
+  double total = nsuper;
+  auto keep_lowering = [&] {
+    return total < goal || static_cast<double>(d) > 0.3 * top ||
+           static_cast<double>(split) < nsuper / 1000.0;
+  };
+  while (d > 0 && keep_lowering()) {
+    --d;
+    split += with[d];
+    total += static_cast<double>(d) * static_cast<double>(with[d]);
+  }
+  return static_cast<int32_t>(d);
+}
+
 void build_schur_tasks(Sym* S, const TilePolicy& policy) {
   S->policy = policy;
   const int kinds[] = {kTaskSchur64, kTaskSchur32, kTaskSchur16, kTaskSchur128, kTaskOzSlice};
@@ -481,6 +513,8 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
   }
   S->lvl_ozrows.assign(S->nlev, 0);
   S->oz_rows = 0;
+  // pass 1: every supernode's tile class under the size thresholds
+  std::vector<int8_t> cls0(S->ns, kTile16);
   for (int32_t l = 0; l < S->nlev; l++) {
     int64_t tiles64 = 0, tiles128 = 0;
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
@@ -490,13 +524,56 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
       tiles64 += nt * (nt + 1) / 2;
       tiles128 += nt2 * (nt2 + 1) / 2;
     }
+    for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
+      const int32_t s = S->lvl_sn[q];
+      const int64_t u = S->sn_m[s] - (S->sn_start[s + 1] - S->sn_start[s]);
+      cls0[s] = static_cast<int8_t>(choose_tile_class(policy, u, tiles64, tiles128));
+    }
+  }
+  // the granularity rule (Sec. 4): which outer tasks (Schur updates) are split into tiles
+  int rule = policy.granularity;
+  if (rule == kGranHybrid) {
+    const double nnz_full = 2.0 * static_cast<double>(S->nnz_a) - static_cast<double>(S->n);
+    const double avg = S->ns > 0 ? static_cast<double>(S->n) / S->ns : 0.0;
+    const double density =
+        S->n > 0 ? nnz_full / (static_cast<double>(S->n) * static_cast<double>(S->n)) : 0.0;
+    rule = (avg > 50.0 || (avg > 20.0 && density < 1e-4)) ? kGranTiles : kGranOptDCost;
+  }
+  std::vector<uint8_t> whole(S->ns, 0);
+  S->gran_rule = rule;
+  S->gran_D = -1;
+  S->gran_split = 0;
+  if (rule != kGranTiles) {
+    std::vector<int32_t> inner(S->ns, 0);
+    for (int32_t s = 0; s < S->ns; s++) {
+      const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
+      const int64_t u = S->sn_m[s] - w, T = tile_of_class(cls0[s]);
+      const int64_t nt = (u + T - 1) / T;
+      inner[s] = u > 0 ? static_cast<int32_t>(std::min<int64_t>(nt * (nt + 1) / 2, INT32_MAX)) : 0;
+    }
+    const int32_t D = opt_d_threshold(S->n, S->ns, inner.data());
+    S->gran_D = D;
+    for (int32_t s = 0; s < S->ns; s++) {
+      const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
+      const int64_t T = tile_of_class(cls0[s]);
+      bool split = inner[s] > D;
+      // OPT-D-COST (Sec. 4.2): inner tasks of fewer than 50,000 flops are not worth a task
+      if (split && rule == kGranOptDCost && 2.0 * T * T * w < 50000.0) split = false;
+      if (inner[s] > 0) {
+        if (split) S->gran_split++;
+        else whole[s] = 1;
+      }
+    }
+  }
+  // pass 2: the task lists
+  for (int32_t l = 0; l < S->nlev; l++) {
     int64_t ozrow = 0;
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
       const int32_t s = S->lvl_sn[q];
       const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
       const int32_t u = S->sn_m[s] - w;
       if (u <= 0) continue;
-      const int cls = choose_tile_class(policy, u, tiles64, tiles128);
+      const int cls = whole[s] ? whole_tile_class(u) : cls0[s];
       const int T = tile_of_class(cls), k = schur_kind(cls);
       S->lvl_flops[k][l] += (double)u * (u + 1.0) * w;
       if (cls == kTile128) {

@@ -309,12 +309,30 @@ int chol_sym_get_tile_policy(const chol_sym* s, chol_tile_policy* p) {
   p->min_level_tiles64 = s->S.policy.min_level_tiles64;
   p->min_rows_tile128 = s->S.policy.min_rows_tile128;
   p->min_level_tiles128 = s->S.policy.min_level_tiles128;
+  p->granularity = s->S.policy.granularity;
+  return CHOL_OK;
+}
+
+int chol_opt_d(int64_t n, int32_t nsuper, const int32_t* counts, int32_t* D) {
+  if (n < 0 || nsuper < 0 || !D || (nsuper > 0 && !counts)) return CHOL_E_INVALID;
+  for (int32_t i = 0; i < nsuper; i++)
+    if (counts[i] < 0) return CHOL_E_INVALID;
+  *D = chol::opt_d_threshold(n, nsuper, counts);
+  return CHOL_OK;
+}
+
+int chol_sym_granularity(const chol_sym* s, int* rule, int32_t* D, int32_t* nsplit) {
+  if (!s) return CHOL_E_INVALID;
+  if (rule) *rule = s->S.gran_rule;
+  if (D) *D = s->S.gran_D;
+  if (nsplit) *nsplit = s->S.gran_split;
   return CHOL_OK;
 }
 
 int chol_sym_set_tile_policy(chol_sym* s, const chol_tile_policy* p) {
   if (!s || !p || p->min_rows_tile64 < 1 || p->min_rows_tile32 < 1 || p->min_level_tiles64 < 0 ||
-      p->min_rows_tile128 < 1 || p->min_level_tiles128 < 0)
+      p->min_rows_tile128 < 1 || p->min_level_tiles128 < 0 || p->granularity < CHOL_GRAN_TILES ||
+      p->granularity > CHOL_GRAN_HYBRID)
     return CHOL_E_INVALID;
   chol::TilePolicy tp;
   tp.min_rows_tile64 = p->min_rows_tile64;
@@ -322,6 +340,7 @@ int chol_sym_set_tile_policy(chol_sym* s, const chol_tile_policy* p) {
   tp.min_level_tiles64 = p->min_level_tiles64;
   tp.min_rows_tile128 = p->min_rows_tile128;
   tp.min_level_tiles128 = p->min_level_tiles128;
+  tp.granularity = p->granularity;
   chol::build_schur_tasks(&s->S, tp);
   if (!s->ctx) return CHOL_OK;
   chol_ctx* c = s->ctx;

@@ -85,12 +85,24 @@ struct alignas(16) MatDev {
 // it has at least min_rows_tile128 off-diagonal rows and its level holds at least
 // min_level_tiles128 such tiles, else 64x64 under the same rule with the 64 thresholds, else
 // 32x32 from min_rows_tile32 rows, else 16x16.
+// granularity: kGranTiles uses the size thresholds alone; the other rules apply the
+// paper's task-granularity heuristics (Sec. 4) to GPU tiles: a supernode's Schur update is
+// the outer task, its tiles under the size thresholds the inner tasks it would create; an
+// outer task with more than D inner tasks (D from OPT-D, Sec. 4.1, Algorithm 1) is split
+// into those tiles, the others are kept whole (the coarsest tile class that covers the
+// update in one task, 128 wide above 64 rows); kGranOptDCost also keeps whole any outer
+// task whose inner tasks would each carry fewer than 50,000 flops (OPT-D-COST, Sec. 4.2);
+// kGranHybrid takes the size thresholds when the average supernode size is above 50, or
+// above 20 with density below 1e-4, and OPT-D-COST otherwise (the hybrid rule, Sec. 4.3).
+enum Granularity { kGranTiles = 0, kGranOptD = 1, kGranOptDCost = 2, kGranHybrid = 3 };
+
 struct TilePolicy {
   int min_rows_tile64 = 64;
   int min_rows_tile32 = 17;
   int min_level_tiles64 = 2 * 152;
   int min_rows_tile128 = 128;
   int min_level_tiles128 = 0;
+  int granularity = kGranTiles;
 };
 
 // Host-side symbolic analysis result.
@@ -151,6 +163,10 @@ struct Sym {
   double flops_panel = 0.0;  // the same over the padded panels (relaxed amalgamation)
   int64_t nnz_l = 0, l_storage = 0, max_width = 0, max_rows = 0;
   int64_t n_fundamental = 0;  // fundamental supernodes before amalgamation and the cap
+  // the granularity rule applied by the last build_schur_tasks (kGranHybrid resolved), its
+  // threshold D (-1 under kGranTiles) and the number of outer tasks split
+  int gran_rule = kGranTiles;
+  int32_t gran_D = -1, gran_split = 0;
 };
 
 // Host analysis (analyze.cpp).  relax > 0 enables relaxed amalgamation with that largest
@@ -163,5 +179,8 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
 void build_owner_lists(Sym* S);
 // (Re)builds the Schur tile task lists of every level under a tile policy.
 void build_schur_tasks(Sym* S, const TilePolicy& policy);
+// Threshold D of OPT-D (Sec. 4.1, Algorithm 1) for nsuper outer tasks with counts[i] >= 0
+// inner tasks each, n the matrix size.
+int32_t opt_d_threshold(int64_t n, int32_t nsuper, const int32_t* counts);
 
 }  // namespace chol

@@ -192,3 +192,50 @@ def test_fundamental_panels_equal_l():
     A, perm = inputs.workload("lap3d_9")
     sym = P.Symbolic(P.make_opts(relax=-1.0), A, perm)
     check_panels_cover_l(sym, A, perm, exact=True)
+
+
+# ---- task granularity (Sec. 4: OPT-D, OPT-D-COST, hybrid) applied to Schur tiles ---------
+
+def test_opt_d_library_matches_oracle():
+    rng = np.random.default_rng(11)
+    for _ in range(100):
+        ns = int(rng.integers(0, 400))
+        c = rng.integers(0, int(rng.integers(1, 5000)), size=ns)
+        n = int(rng.integers(0, 10 ** 6))
+        assert P.chol_opt_d(n, c) == oracle.opt_d(n, c)
+    with pytest.raises(P.CholError):
+        P.chol_opt_d(10, [3, -1])
+
+
+SIZE_ONLY = {"min_rows_tile64": 64, "min_rows_tile32": 17, "min_level_tiles64": 0,
+             "min_rows_tile128": 128, "min_level_tiles128": 0}
+
+
+@pytest.mark.parametrize("name", ["st27x3_8", "lap3d_12", "diff3d7_12", "lap2d_64"])
+def test_granularity_rules(name):
+    A, perm = inputs.workload(name)
+    sym = P.Symbolic(P.make_opts(width_cap=64), A, perm)
+    start = sym.export()["sn_start"]
+    rowptr, _ = P.chol_sym_rows(sym.handle)
+    w = np.diff(start).astype(np.int64)
+    u = np.diff(rowptr).astype(np.int64) - w
+    # inner tasks of each outer task under the size thresholds alone (level counts off)
+    T = np.where(u >= 128, 128, np.where(u >= 64, 64, np.where(u >= 17, 32, 16)))
+    nt = (u + T - 1) // T
+    inner = np.where(u > 0, nt * (nt + 1) // 2, 0)
+    D = oracle.opt_d(A.n, inner)
+    P.chol_sym_set_tile_policy(sym.handle, {**SIZE_ONLY, "granularity": P.CHOL_GRAN_TILES})
+    assert P.chol_sym_granularity(sym.handle) == {"rule": 0, "D": -1, "nsplit": 0}
+    P.chol_sym_set_tile_policy(sym.handle, {**SIZE_ONLY, "granularity": P.CHOL_GRAN_OPTD})
+    assert P.chol_sym_granularity(sym.handle) == {"rule": P.CHOL_GRAN_OPTD, "D": D,
+                                                  "nsplit": int(np.sum(inner > D))}
+    P.chol_sym_set_tile_policy(sym.handle, {**SIZE_ONLY, "granularity": P.CHOL_GRAN_OPTD_COST})
+    costly = 2.0 * T * T * w >= 50000.0
+    assert P.chol_sym_granularity(sym.handle) == {"rule": P.CHOL_GRAN_OPTD_COST, "D": D,
+                                                  "nsplit": int(np.sum((inner > D) & costly))}
+    P.chol_sym_set_tile_policy(sym.handle, {**SIZE_ONLY, "granularity": P.CHOL_GRAN_HYBRID})
+    blas = oracle.hybrid_uses_blas(A.n, len(w), 2 * sym.info["nnz_a"] - A.n)
+    got = P.chol_sym_granularity(sym.handle)
+    assert got["rule"] == (P.CHOL_GRAN_TILES if blas else P.CHOL_GRAN_OPTD_COST)
+    with pytest.raises(P.CholError):
+        P.chol_sym_set_tile_policy(sym.handle, {"granularity": 4})

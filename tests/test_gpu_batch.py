@@ -123,7 +123,8 @@ def test_tile_policies_are_correct(torch, policy, assembly):
     ref = oracle.cholesky(A, perm)
     sym = P.Symbolic(ctx, A, perm)
     P.chol_sym_set_tile_policy(sym.handle, policy)
-    assert P.chol_sym_get_tile_policy(sym.handle) == policy
+    got = P.chol_sym_get_tile_policy(sym.handle)
+    assert {k: got[k] for k in policy} == policy and got["granularity"] == P.CHOL_GRAN_TILES
     P.chol_profile_enable(ctx.handle, True)
     num = P.Factor(ctx, sym, A.vals)
     prof = P.chol_profile_read(ctx.handle)
@@ -152,6 +153,27 @@ def test_autotuner(torch):
     num = P.Factor(ctx, sym, A.vals)
     policy, ms = num.autotune(reps=1)
     assert ms > 0 and set(policy) == {"min_rows_tile64", "min_rows_tile32", "min_level_tiles64",
-                                      "min_rows_tile128", "min_level_tiles128"}
+                                      "min_rows_tile128", "min_level_tiles128", "granularity"}
     assert P.chol_sym_get_tile_policy(sym.handle) == policy
     check_member(ctx, num, A, perm, ref)
+
+
+@pytest.mark.parametrize("rule", [P.CHOL_GRAN_OPTD, P.CHOL_GRAN_OPTD_COST, P.CHOL_GRAN_HYBRID])
+@pytest.mark.parametrize("precision", [P.CHOL_FP64, P.CHOL_MIXED])
+def test_granularity_rules_are_correct(torch, rule, precision):
+    """The OPT-D / OPT-D-COST / hybrid task granularity (Sec. 4) only regroups the Schur
+    tiles: the factor matches the oracle (FP64) or refines to 1e-12 (mixed)."""
+    ctx = P.Context()
+    A, perm = problem("st27x3_11")
+    sym = P.Symbolic(ctx, A, perm)
+    P.chol_sym_set_tile_policy(sym.handle, {"granularity": rule})
+    g = P.chol_sym_granularity(sym.handle)
+    assert g["D"] >= 0 or g["rule"] == P.CHOL_GRAN_TILES
+    num = P.Factor(ctx, sym, A.vals, precision)
+    if precision == P.CHOL_FP64:
+        check_member(ctx, num, A, perm, oracle.cholesky(A, perm))
+    else:
+        B = np.asfortranarray(A.to_scipy_full() @ inputs.rhs_block(8, A.n, 1))
+        X, info = num.refine(B, tol=1e-12)
+        assert info["residual"] <= 1e-12
+        assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, B, X) <= 1e-12
