@@ -216,22 +216,25 @@ __global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, i
 // i.e. for each row x_j = (a_j - sum_{k<j} x_k L_jk) / L_jj.
 //   k_trsm (any W <= 128): the substitution itself, one thread per row, partial rows in
 //     shared memory.
-// k_trsm_blk (W <= 64): a task's 32 rows (lane = row) are solved by all four warps at once,
-//   16 columns at a time.  Block b (columns 16b .. 16b+15, diagonal block D_b of L11): every
-//   warp takes four of its columns (w, w+4, w+8, w+12) and subtracts the products with the
-//   solved columns of the earlier blocks, acc_k = a_k - sum_{j<16b} x_j L_kj; the partial
+// k_trsm_blk (W <= 64): a task's 32 rows (lane = row) are solved by all kTrsmWarps warps at
+//   once, 16 columns at a time.  Block b (columns 16b .. 16b+15, diagonal block D_b of L11):
+//   warp w takes the block's columns w, w + kTrsmWarps, ... and subtracts the products with
+//   the solved columns of the earlier blocks, acc_k = a_k - sum_{j<16b} x_j L_kj; the partial
 //   vectors are exchanged through shared memory and the block is finished as x_b = D_b^{-1}
 //   acc_b with D_b^{-1} (lower triangular, formed per task by forward substitution on the
-//   unit vectors).  Each warp thus issues about a quarter of a row's FMAs: on this part an
-//   FP64 warp instruction holds its warp for ~64 cycles, so the row-per-thread form above
-//   (every FMA of the row in one warp) is four times longer per task.
+//   unit vectors).  Each warp thus issues 1/kTrsmWarps of a row's FMAs: on this part an FP64
+//   warp instruction holds its warp for ~64 cycles, so the per-task latency (what the
+//   single-supernode levels of the elimination tree's top wait for) falls with the warps.
+constexpr int kTrsmWarps = 8;
+constexpr int kTrsmCols = 16 / kTrsmWarps;  // columns of a block per warp
+
 template <typename T>
 constexpr size_t trsm_blk_smem() { return (64 * 64 + 64 * 32 + 16 * 32 + 4 * 16 * 16 + 64) * sizeof(T); }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_trsm_blk(const int4* __restrict__ tasks, int ntasks,
-                                                  int* __restrict__ queue,
-                                                  const SnDev* __restrict__ sns) {
+__global__ void __launch_bounds__(32 * kTrsmWarps) k_trsm_blk(const int4* __restrict__ tasks, int ntasks,
+                                                              int* __restrict__ queue,
+                                                              const SnDev* __restrict__ sns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ls = reinterpret_cast<T*>(smem_raw);  // Ls[c * 64 + r] = L11[r][c]
   T* Xs = Ls + 64 * 64;                     // Xs[k * 32 + lane]: solved column k of the rows
@@ -246,15 +249,17 @@ __global__ void __launch_bounds__(128) k_trsm_blk(const int4* __restrict__ tasks
     const int n = d.n, m = d.m;
     T* L = reinterpret_cast<T*>(d.L);
     stage_diag_block_ld(Ls, 64, L, n, m);
-    // the warp's own columns k = 16 (q >> 2) + w + 4 (q & 3) of this task's row
+    // the warp's own columns k = 16 b + w + kTrsmWarps q of this task's row
     const int row = n + tk.y + lane;
     const bool live = row < m;
-    T a[16];
+    T a[4 * kTrsmCols];
 #pragma unroll
-    for (int q = 0; q < 16; q++) {
-      const int k = 16 * (q >> 2) + w + 4 * (q & 3);
-      a[q] = (live && k < n) ? L[(int64_t)k * m + row] : T(0);
-    }
+    for (int b = 0; b < 4; b++)
+#pragma unroll
+      for (int q = 0; q < kTrsmCols; q++) {
+        const int k = 16 * b + w + kTrsmWarps * q;
+        a[b * kTrsmCols + q] = (live && k < n) ? L[(int64_t)k * m + row] : T(0);
+      }
     cp_async_wait_all();
     __syncthreads();
     if (threadIdx.x < n) rd[threadIdx.x] = T(1) / Ls[threadIdx.x * 65];
@@ -272,39 +277,41 @@ __global__ void __launch_bounds__(128) k_trsm_blk(const int4* __restrict__ tasks
       }
     }
     __syncthreads();
-    T out[16] = {};
+    T out[4 * kTrsmCols] = {};
 #pragma unroll
     for (int b = 0; b < 4; b++) {
       if (16 * b >= n) break;
-      T acc[4];
+      T acc[kTrsmCols];
 #pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] = a[4 * b + q];
-      const T* lrow = Ls + 16 * b + w;  // + j * 64 + 4 q: L11[16b + w + 4q][j]
+      for (int q = 0; q < kTrsmCols; q++) acc[q] = a[b * kTrsmCols + q];
+      const T* lrow = Ls + 16 * b + w;  // + j * 64 + kTrsmWarps q: L11[16b + w + kTrsmWarps q][j]
       for (int j = 0; j < 16 * b; j++) {
         const T xj = Xs[j * 32 + lane];
 #pragma unroll
-        for (int q = 0; q < 4; q++) acc[q] = fma_t(-xj, lrow[j * 64 + 4 * q], acc[q]);
+        for (int q = 0; q < kTrsmCols; q++) acc[q] = fma_t(-xj, lrow[j * 64 + kTrsmWarps * q], acc[q]);
       }
 #pragma unroll
-      for (int q = 0; q < 4; q++) Acc[(w + 4 * q) * 32 + lane] = acc[q];
+      for (int q = 0; q < kTrsmCols; q++) Acc[(w + kTrsmWarps * q) * 32 + lane] = acc[q];
       __syncthreads();
       const T* dv = Dv + b * 256;
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int kk = w + 4 * q;
+      for (int q = 0; q < kTrsmCols; q++) {
+        const int kk = w + kTrsmWarps * q;
         T s = T(0);
         for (int i = 0; i <= kk; i++) s = fma_t(Acc[i * 32 + lane], dv[kk * 16 + i], s);
-        out[4 * b + q] = s;
+        out[b * kTrsmCols + q] = s;
         Xs[(16 * b + kk) * 32 + lane] = s;
       }
       __syncthreads();
     }
     if (live) {
 #pragma unroll
-      for (int q = 0; q < 16; q++) {
-        const int k = 16 * (q >> 2) + w + 4 * (q & 3);
-        if (k < n) L[(int64_t)k * m + row] = out[q];
-      }
+      for (int b = 0; b < 4; b++)
+#pragma unroll
+        for (int q = 0; q < kTrsmCols; q++) {
+          const int k = 16 * b + w + kTrsmWarps * q;
+          if (k < n) L[(int64_t)k * m + row] = out[b * kTrsmCols + q];
+        }
     }
     // a CTA's first task is its block index; only a grid smaller than the task list makes
     // CTAs take further tasks from this launch's work queue
@@ -746,7 +753,7 @@ static void trsm_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns, 
                    cudaStream_t st) {
   if (max_width <= 64) {
     constexpr size_t sm = trsm_blk_smem<T>();
-    k_trsm_blk<T><<<persistent_grid(k_trsm_blk<T>, 128, sm, ntasks), 128, sm, st>>>(
+    k_trsm_blk<T><<<persistent_grid(k_trsm_blk<T>, 32 * kTrsmWarps, sm, ntasks), 32 * kTrsmWarps, sm, st>>>(
         tasks, ntasks, queue, sns);
     return;
   }
