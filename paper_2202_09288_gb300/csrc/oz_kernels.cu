@@ -23,7 +23,6 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
-#include <algorithm>
 #include <cstdint>
 
 #include "chol_internal.h"
@@ -298,7 +297,7 @@ __device__ __forceinline__ void oz_arrive(uint32_t bar) {
 // built / released), ring_full[] (the task order, for the consumers and metadata warps).
 template <bool OWNER>
 __global__ void __launch_bounds__(kOzThreads, 1)
-    k_schur_oz(const int4* __restrict__ tasks, int ntasks, int chunk, int* __restrict__ queue,
+    k_schur_oz(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                const SnDev* __restrict__ sns, const MatDev* __restrict__ mats,
                const uint8_t* __restrict__ oz, int64_t oz_rows) {
   extern __shared__ __align__(1024) unsigned char oz_sm[];
@@ -383,13 +382,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       long long q = 0;          // quarters issued (set and buffer = q & 1)
       long long a_use = 0;      // A loads completed-and-waited
       int ord = 0;
-      // tasks are claimed in chunks of `chunk` consecutive ones (chunk 0 .. gridDim.x - 1
-      // first, then from the queue): the task list holds each row panel's tiles one after
-      // another, so consecutive tasks of a chunk often share their A rows, which then stay
-      // in shared memory
-      const int nchunks = (ntasks + chunk - 1) / chunk;
-      int tq = (int)blockIdx.x < nchunks ? (int)blockIdx.x * chunk : ntasks;
-      int tend = min(tq + chunk, ntasks);
+      int tq = blockIdx.x;
       ring[0] = tq < ntasks ? tq : ntasks;
       oz_arrive(smem_u32(&ring_full[0]));
       if (tq < ntasks) {
@@ -400,18 +393,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         const int4 t = tasks[tq];
         const int nq = quarters(t);
         const int ks = (sns[t.x].n + 15) >> 4;
-        if (a_issued > a_use) {  // this task's A rows were loaded (not kept from the last task)
-          if (!oz_wait(smem_u32(&a_full), (uint32_t)(a_use & 1))) { ok = false; break; }
-          a_use++;
-        }
+        if (!oz_wait(smem_u32(&a_full), (uint32_t)(a_use & 1))) { ok = false; break; }
+        a_use++;
         // the next task is fetched now so its first quarter can be prefetched
-        int next = tq + 1, next_end = tend;
-        if (next >= tend) {
-          const int c = (int)gridDim.x >= nchunks ? nchunks : (int)gridDim.x + atomicAdd(queue, 1);
-          next = c < nchunks ? c * chunk : ntasks;
-          next_end = min(next + chunk, ntasks);
-        }
-        const bool same_a = next < ntasks && tasks[next].x == t.x && tasks[next].y == t.y;
+        const int next = gridDim.x >= ntasks ? ntasks : (int)gridDim.x + atomicAdd(queue, 1);
         for (int j = 0; j < nq && ok; j++, q++) {
           const int b = (int)(q & 1);
           if (!oz_wait(smem_u32(&b_full[b]), (uint32_t)((q >> 1) & 1)) ||
@@ -437,10 +422,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
               break;
             }
             if (last) {
-              if (!same_a) {  // new A rows: once this quarter's MMAs have read the old ones
-                if (!oz_wait(smem_u32(&acc_full[b]), (uint32_t)((q >> 1) & 1))) { ok = false; break; }
-                load_a(tasks[next]);
-              }
+              if (!oz_wait(smem_u32(&acc_full[b]), (uint32_t)((q >> 1) & 1))) { ok = false; break; }
+              load_a(tasks[next]);
               load_b(tasks[next], 0, b ^ 1);
             } else {
               load_b(t, j + 1, b ^ 1);
@@ -450,7 +433,6 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (!ok) break;
         ord++;
         tq = next;
-        tend = next_end;
         ring[ord % kOzRing] = tq < ntasks ? tq : ntasks;
         oz_arrive(smem_u32(&ring_full[ord % kOzRing]));
       }
@@ -670,15 +652,12 @@ void launch_schur_oz(const int4* tasks, int ntasks, int* queue, const SnDev* sns
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // chunks of up to 4 consecutive tasks once there are at least two chunks per SM
-  const int chunk = std::max(1, std::min(4, ntasks / (2 * sms)));
-  const int nchunks = (ntasks + chunk - 1) / chunk;
-  const int grid = nchunks < sms ? nchunks : sms;  // one resident CTA per SM, chunks by queue
+  const int grid = ntasks < sms ? ntasks : sms;  // one resident CTA per SM, tasks by queue
   const uint8_t* z = static_cast<const uint8_t*>(oz);
   if (owner)
-    k_schur_oz<true><<<grid, kOzThreads, kOzSmem, st>>>(tasks, ntasks, chunk, queue, sns, mats, z, oz_rows);
+    k_schur_oz<true><<<grid, kOzThreads, kOzSmem, st>>>(tasks, ntasks, queue, sns, mats, z, oz_rows);
   else
-    k_schur_oz<false><<<grid, kOzThreads, kOzSmem, st>>>(tasks, ntasks, chunk, queue, sns, mats, z, oz_rows);
+    k_schur_oz<false><<<grid, kOzThreads, kOzSmem, st>>>(tasks, ntasks, queue, sns, mats, z, oz_rows);
 }
 
 size_t oz_scratch_bytes(int64_t oz_rows) {
