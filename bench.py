@@ -153,6 +153,33 @@ def oracle_sample(name: str):
     return flops, dt, x
 
 
+def tasks_sample(name: str, width: int, relax: float):
+    """Times the multi-core CPU baseline of the paper's tasking (left-looking supernodal
+    factorization as OpenMP tasks, Sec. 3 and 4) on all host cores, one factorization per
+    policy (best of two), on the same sample and supernode partition as the GPU path."""
+    import cpu_tasks
+    import paper_2202_09288_gb300 as P
+    from paper_2202_09288_gb300 import inputs
+
+    A, perm = inputs.workload(name)
+    sym = P.Symbolic(P.make_opts(width_cap=width, relax=relax), A, perm)
+    rowptr, rows = P.chol_sym_rows(sym.handle)
+    start = sym.export()["sn_start"]
+    F = sym.info["flops"]
+    cores = os.cpu_count() or 1
+    out = {}
+    for pol in cpu_tasks.POLICIES:
+        best, D, inner = float("inf"), -1, 0
+        for _ in range(2):
+            pan = cpu_tasks.factor(A, perm, start, rowptr, rows, pol, threads=cores)
+            best, D, inner = min(best, pan.seconds), pan.D, pan.inner_tasks
+        out[pol] = {"gflops": F / best / 1e9, "seconds": best, "D": D, "inner_tasks": inner}
+    return {"value": out["optd_cost"]["gflops"], "unit": "GFLOP/s", "cores": cores,
+            "kind": "paper tasking (OPT-D-COST, OpenMP, plain-loop dense kernels)",
+            "sample": f"{name}: one FP64 factorization ({F:.3e} flops) per policy, best of 2",
+            "policies": out}
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return 0
@@ -635,6 +662,7 @@ def main():
             "value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
             "sample": f"{args.cpu_sample}: one FP64 factorization + 1-RHS solve "
                       f"({fl:.3e} flops, {dt:.1f} s) by the single-thread C oracle"}
+        line["cpu_tasks_baseline"] = tasks_sample(args.cpu_sample, args.width, args.relax)
     if rank == 0:
         print(json.dumps(line))
     if dist:
