@@ -526,11 +526,16 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         }
         if (mt == 0) M.nruns = M.wcnt[0] + M.wcnt[1] + M.wcnt[2] + M.wcnt[3];
         oz_meta_sync();
-        const int nrc = min(M.nruns, kOzMaxRuns);
-        for (int idx = mt; idx < nrc * kOzM; idx += kOzMetaThreads) {
-          const int r = idx / kOzM, ii = idx - r * kOzM, g = i0 + ii;
-          M.rp[r][ii] = (g < u && g >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + g] : -1;
-        }
+        // relative rows of the cached runs: this thread's tile row in each, all loads in flight
+        static_assert(kOzMetaThreads == kOzM, "one metadata thread per tile row");
+        const int nrc = min(M.nruns, kOzMaxRuns), g = i0 + mt;
+        int rpv[kOzMaxRuns];
+#pragma unroll
+        for (int r = 0; r < kOzMaxRuns; r++)
+          rpv[r] = (r < nrc && g < u && g >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + g] : -1;
+#pragma unroll
+        for (int r = 0; r < kOzMaxRuns; r++)
+          if (r < nrc) M.rp[r][mt] = rpv[r];
       }
       oz_arrive(smem_u32(&meta_full[buf]));  // each thread after its own writes
     }

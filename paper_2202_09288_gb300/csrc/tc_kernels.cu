@@ -424,11 +424,16 @@ __global__ void __launch_bounds__(kTfThreads, 1)
         }
         if (mt == 0) M.nruns = M.wcnt[0] + M.wcnt[1] + M.wcnt[2] + M.wcnt[3];
         meta_sync();
-        const int nrc = min(M.nruns, kTfMaxRuns);
-        for (int idx = mt; idx < nrc * kTfM; idx += kTfMetaThreads) {
-          const int r = idx / kTfM, i = idx - r * kTfM, gi = i0 + i;
-          M.rp[r][i] = (gi < u && gi >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + gi] : -1;
-        }
+        // relative rows of the cached runs: this thread's tile row in each, all loads in flight
+        static_assert(kTfMetaThreads == kTfM, "one metadata thread per tile row");
+        const int nrc = min(M.nruns, kTfMaxRuns), gi = i0 + mt;
+        int rpv[kTfMaxRuns];
+#pragma unroll
+        for (int r = 0; r < kTfMaxRuns; r++)
+          rpv[r] = (r < nrc && gi < u && gi >= k0 + M.run_start[r]) ? md.relmap[M.rb[r] + gi] : -1;
+#pragma unroll
+        for (int r = 0; r < kTfMaxRuns; r++)
+          if (r < nrc) M.rp[r][mt] = rpv[r];
       }
       tf_arrive(smem_u32(&meta_full[buf]));  // each thread after its own writes
     }
