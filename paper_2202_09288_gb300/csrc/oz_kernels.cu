@@ -8,16 +8,18 @@
 //               L21[r,k] = 2^e_r sum_p s_p[r,k] 2^(-7(p+1)) + (error < 2^(e_r-57)),
 //               stored as bf16 (exact) in rows of 128 bytes, 16-byte chunks pre-swizzled
 //               for the tensor cores' 128-byte swizzle;
-//   k_schur_oz  a 128 x 128 task is done as two 128 x 64 halves.  The 8 A slices (the
-//               task's 128 rows) and 8 B slices (the half's 64 rows) are brought into
-//               shared memory by bulk copies; one thread issues, for every slice pair
-//               p + q < 8, the bf16 MMAs of D_{p+q} += S_p S_q^T into the tensor-memory
-//               accumulator of the diagonal p + q (8 x 64 columns).  Every partial sum of
-//               a diagonal is an integer below 2^23 (K <= 64), so FP32 accumulation is
-//               exact.  The epilogue reads the accumulators (lane = tile row), forms
-//               U[i,k] = 2^(e_i+e_k) sum_d 2^(-7(d+2)) D_d[i,k] in FP64 and scatters it
-//               into the ancestors with FP64 atomics (or writes the owner staging buffer)
-//               while the tensor cores already compute the next half.
+//   k_schur_oz  a 128 x 128 task is done as four 128 x 32 quarters.  The 8 A slices
+//               (the task's 128 rows) and each quarter's 8 B slices (its 32 rows) are
+//               brought into shared memory by bulk copies; one producer thread issues,
+//               for every slice pair p + q < 8, the bf16 MMAs of D_{p+q} += S_p S_q^T into
+//               the quarter's set of tensor-memory accumulators (one per diagonal p + q,
+//               8 x 32 columns; two sets).  Every partial sum of a diagonal is an integer
+//               below 2^22 (K <= 64), so FP32 accumulation is exact.  Consumer warps read a
+//               finished set (lane = tile row), release it, form U[i,k] = 2^(e_i+e_k)
+//               sum_d 2^(-7(d+2)) D_d[i,k] as an FP64 value (integer combination, one
+//               int64 -> double conversion) and scatter it into the ancestors with FP64
+//               atomics (or write the owner staging buffer) while the tensor cores compute
+//               the next quarter; metadata warps prepare each task's targets one task ahead.
 // Every wait is bounded: after kOzSpinLimit polls the kernel records a timeout in err[3],
 // waits (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
 #include <cuda_bf16.h>
