@@ -146,14 +146,16 @@ __global__ void __launch_bounds__(kSolveThreads)
         P acc[NR];
   #pragma unroll
         for (int c = 0; c < NR; c++) acc[c] = P(0);
-        // eight independent panel loads per step: the loads, not the FMAs, are the latency
+        // independent panel loads per step (16 of FP32, 8 of FP64): the loads, not the FMAs,
+        // are the latency
+        constexpr int QB = sizeof(P) == 4 ? 16 : 8;
         int j = 0;
-        for (; j + 8 <= n; j += 8) {
-          P l[8];
+        for (; j + QB <= n; j += QB) {
+          P l[QB];
   #pragma unroll
-          for (int q = 0; q < 8; q++) l[q] = L[(int64_t)(j + q) * m];
+          for (int q = 0; q < QB; q++) l[q] = L[(int64_t)(j + q) * m];
   #pragma unroll
-          for (int q = 0; q < 8; q++)
+          for (int q = 0; q < QB; q++)
   #pragma unroll
             for (int c = 0; c < NR; c++)
               if (c0 + c < nrhs) acc[c] += l[q] * xs[(c0 + c) * n + j + q];
@@ -234,13 +236,14 @@ __global__ void __launch_bounds__(kSolveThreads)
     for (int c = 0; c < NR; c++) acc[c] = P(0);
     if (j < n) {
       const P* col = reinterpret_cast<const P*>(d.L) + (int64_t)j * m + n + tk.y;
+      constexpr int QB = sizeof(P) == 4 ? 16 : 8;  // independent loads per step
       int i = ib;
-      for (; i + 8 <= ie; i += 8) {  // eight independent loads per step
-        P l[8];
+      for (; i + QB <= ie; i += QB) {
+        P l[QB];
 #pragma unroll
-        for (int q = 0; q < 8; q++) l[q] = col[i + q];
+        for (int q = 0; q < QB; q++) l[q] = col[i + q];
 #pragma unroll
-        for (int q = 0; q < 8; q++)
+        for (int q = 0; q < QB; q++)
 #pragma unroll
           for (int c = 0; c < NR; c++)
             if (c < nrhs) acc[c] += l[q] * xg[c * rb + i + q];
