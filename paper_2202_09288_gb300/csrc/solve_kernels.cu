@@ -146,9 +146,9 @@ __global__ void __launch_bounds__(kSolveThreads)
         P acc[NR];
   #pragma unroll
         for (int c = 0; c < NR; c++) acc[c] = P(0);
-        // independent panel loads per step (16 of FP32, 8 of FP64): the loads, not the FMAs,
-        // are the latency
-        constexpr int QB = sizeof(P) == 4 ? 16 : 8;
+        // independent panel loads per step (16 of FP32 for one right-hand side, else 8): the
+        // loads, not the FMAs, are the latency; more right-hand sides need the registers
+        constexpr int QB = (sizeof(P) == 4 && NR == 1) ? 16 : 8;
         int j = 0;
         for (; j + QB <= n; j += QB) {
           P l[QB];
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kSolveThreads)
     for (int c = 0; c < NR; c++) acc[c] = P(0);
     if (j < n) {
       const P* col = reinterpret_cast<const P*>(d.L) + (int64_t)j * m + n + tk.y;
-      constexpr int QB = sizeof(P) == 4 ? 16 : 8;  // independent loads per step
+      constexpr int QB = (sizeof(P) == 4 && NR == 1) ? 16 : 8;  // independent loads per step
       int i = ib;
       for (; i + QB <= ie; i += QB) {
         P l[QB];
