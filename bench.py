@@ -153,6 +153,24 @@ def oracle_sample(name: str):
     return flops, dt, x
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The largest x over all ranks: the timed region is the slowest rank's.  dist is
+    torch.distributed (any backend; device "cuda" for NCCL, "cpu" for gloo) or None."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world: int, flops_per_rank: float, seconds: float) -> float:
+    """Whole-job GFLOP/s of `world` independent replicas (weak scaling: every rank factors
+    its own matrix of flops_per_rank), over the slowest rank's time."""
+    return world * flops_per_rank / seconds / 1e9
+
+
 def tasks_sample(name: str, width: int, relax: float):
     """Times the multi-core CPU baseline of the paper's tasking (left-looking supernodal
     factorization as OpenMP tasks, Sec. 3 and 4) on all host cores, one factorization per
@@ -531,11 +549,7 @@ def main():
         dist.barrier()
     P.chol_profile_enable(ctx.handle, False)
     prof = P.chol_profile_read(ctx.handle)
-    total_ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), dist, "cuda")
     ms_step = total_ms / args.steps
     fac_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     sol_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
@@ -569,11 +583,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         host_step()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
 
     peaks, peak_src = measured_peaks()
     fp64_peak_tflops = peaks["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
@@ -607,7 +617,7 @@ def main():
                 "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 "
                                "TFLOP/s nominal; 72.0 measured by an FFMA loop"}
 
-    value = world * F / (ms_step * 1e-3) / 1e9
+    value = replica_rate(world, F, ms_step * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -628,7 +638,7 @@ def main():
         "fp64_peak_frac": (F / (fac_ms * 1e-3) / 1e12) / fp64_peak_tflops,
         "residual": resid,
         "gpu_launches": int(launches),
-        "e2e": {"value": world * F / e2e_s / 1e9, "unit": "GFLOP/s",
+        "e2e": {"value": replica_rate(world, F, e2e_s), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": int(A.vals.nbytes + b_h.nbytes),
                 "d2h_bytes_per_step": int(x_h.nbytes)},
         "roofline": {"bound": roof["bound"], "kernel": dom, "achieved": achieved,
