@@ -148,4 +148,18 @@ __device__ __forceinline__ void stage_diag_block(T* A, const T* __restrict__ L, 
   stage_diag_block_ld(A, n, L, n, m);
 }
 
+// Up to 128 off-diagonal rows of a supernode panel and its n columns into shared memory,
+// X[k * ld + i] = L21[i, k] (L21 column-major with leading dimension m, rows from the block's
+// first): rows below `valid` by cp.async, every copy in flight at once; rows from `valid` on
+// are zero.  Followed by cp_async_wait_all and a barrier.
+template <typename T>
+__device__ __forceinline__ void stage_row_block(T* X, int ld, const T* __restrict__ L21,
+                                                int64_t m, int n, int valid) {
+  for (int idx = threadIdx.x; idx < n * 128; idx += blockDim.x) {
+    const int k = idx >> 7, i = idx & 127;
+    if (i < valid) cp_async_elem(X + k * ld + i, L21 + (int64_t)k * m + i);
+    else X[k * ld + i] = T(0);
+  }
+}
+
 }  // namespace chol

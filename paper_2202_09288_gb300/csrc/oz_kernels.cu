@@ -144,7 +144,7 @@ constexpr int kOzSliceLd = kOzM + 1;  // padded column stride of the staged bloc
 
 // Slices of the L21 rows r0 .. r0+127 of supernode s, at slice rows oz + r (rows u ..
 // roundup(u, 8) get zero slices).  The block is staged column by column through shared
-// memory (coalesced loads); a row's exponent e_r is that of its largest entry; each
+// memory (cp.async, all copies in flight); a row's exponent e_r is that of its largest entry; each
 // entry becomes the 56-bit fixed-point integer x 2^(56-e_r), cut into 8 balanced digits
 // of 7 bits (round to nearest: |s_0| <= 128, |s_p| <= 64, exact); thread t writes the
 // 16-byte chunk t % 8 of row t / 8 of every slice (coalesced, pre-swizzled).
@@ -159,19 +159,21 @@ __global__ void __launch_bounds__(kOzSliceThreads)
   const int r0 = tk.y;
   const int rows = min(kOzM, ((u + 7) & ~7) - r0);  // slice rows this block owns
   const double* L = reinterpret_cast<const double*>(d.L) + n + r0;  // L21[r0 + i, k] = L[k m + i]
-  for (int idx = threadIdx.x; idx < n * kOzM; idx += kOzSliceThreads) {
-    const int k = idx / kOzM, i = idx - k * kOzM;
-    xs[k * kOzSliceLd + i] = (r0 + i < u) ? L[(int64_t)k * m + i] : 0.0;
-  }
+  static_assert(kOzM == 128, "stage_row_block stages 128 rows");
+  stage_row_block(xs, kOzSliceLd, L, m, n, u - r0);
+  cp_async_wait_all();
   __syncthreads();
   const int64_t row0 = tk.z + (int64_t)r0;
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
   if (threadIdx.x < kOzM) {
     const int i = threadIdx.x;
-    double amax = 0.0;
-    for (int k = 0; k < n; k++) amax = fmax(amax, fabs(xs[k * kOzSliceLd + i]));
-    // amax = f 2^e with f in [0.5, 1): the exponent field minus 1022 (0 for zero rows)
-    const int e = amax > 0.0 ? (int)((__double_as_longlong(amax) >> 52) & 0x7FF) - 1022 : 0;
+    // the largest entry's exponent field by integer comparison (the FP64 unit is slow):
+    // max |x| = f 2^e with f in [0.5, 1) has e = field - 1022 (0 for rows of zeros and
+    // subnormals, whose slices are zero)
+    int emax = 0;
+    for (int k = 0; k < n; k++)
+      emax = max(emax, (int)((__double_as_longlong(xs[k * kOzSliceLd + i]) >> 52) & 0x7FF));
+    const int e = emax > 0 ? emax - 1022 : 0;
     s_e[i] = e;
     if (i < rows) reinterpret_cast<int32_t*>(oz + kOzSlices * stride)[row0 + i] = e;
   }

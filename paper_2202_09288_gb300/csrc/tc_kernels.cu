@@ -176,10 +176,8 @@ __global__ void __launch_bounds__(256)
   const int rows = min(kTfM, ((u + 7) & ~7) - r0);
   const int nch = (n + kTfChunk - 1) / kTfChunk;
   const float* L = reinterpret_cast<const float*>(d.L) + n + r0;
-  for (int idx = threadIdx.x; idx < n * kTfM; idx += blockDim.x) {
-    const int k = idx / kTfM, i = idx - k * kTfM;
-    xf[idx] = (r0 + i < u) ? L[(int64_t)k * m + i] : 0.f;
-  }
+  stage_row_block(xf, kTfM, L, m, n, u - r0);
+  cp_async_wait_all();
   __syncthreads();
   const int64_t row0 = tk.z + (int64_t)r0;
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
