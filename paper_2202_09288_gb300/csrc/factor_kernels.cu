@@ -71,6 +71,10 @@ __device__ __forceinline__ float pivot_rsqrt(float p) {
   return fmaf(0.5f * y0, r, y0);
 }
 
+// Threads of a POTRF CTA: warp 0 finishes the next column, the others update the trailing
+// triangle (potrf_lookahead).
+constexpr int kPotrfThreads = 128;
+
 // Position table of the trailing update: the lower triangle of columns 2..n-1 taken column by
 // column from the last (column n-1: 1 entry, column n-2: 2, ...), entry (C << 8) | R.  At step j
 // the entries of columns j+2..n-1 are the first (n-j-2)(n-j-1)/2, so every step's work is a
@@ -179,10 +183,10 @@ __device__ __forceinline__ void store_diag_block(T* __restrict__ L, const S* A, 
 }
 
 // ---- POTRF of each diagonal block ---------------------------------------------------------
-// One CTA (128 threads) per supernode; the n x n block is factored in shared memory by
+// One CTA (kPotrfThreads threads) per supernode; the n x n block is factored in shared memory by
 // potrf_lookahead.  A non-positive pivot is an error (not SPD), recorded with its column.
 template <typename T>
-__global__ void __launch_bounds__(128) k_potrf(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
+__global__ void __launch_bounds__(kPotrfThreads) k_potrf(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                const SnDev* __restrict__ sns,
                                                const MatDev* __restrict__ mats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -577,7 +581,7 @@ __global__ void __launch_bounds__(SchurF32Cfg<TILE>::THREADS)
 // is 1 after equilibration), the block is factored again in FP64 from the panel's values,
 // which are still unchanged in global memory, and the FP64 result is rounded into the panel.
 // err[2] counts such redos.  The FP64 block overlays the FP32 one in shared memory.
-__global__ void __launch_bounds__(128) k_potrf_mixed(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
+__global__ void __launch_bounds__(kPotrfThreads) k_potrf_mixed(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                      const SnDev* __restrict__ sns,
                                                      const MatDev* __restrict__ mats,
                                                      float tau) {
@@ -739,11 +743,11 @@ void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
   if (ntasks <= 0) return;
   if (f32) {
     const size_t sm = potrf_mixed_smem(max_width);
-    k_potrf_mixed<<<persistent_grid(k_potrf_mixed, 128, sm, ntasks), 128, sm, st>>>(
+    k_potrf_mixed<<<persistent_grid(k_potrf_mixed, kPotrfThreads, sm, ntasks), kPotrfThreads, sm, st>>>(
         tasks, ntasks, queue, sns, mats, tau);
   } else {
     const size_t sm = potrf_smem(max_width);
-    k_potrf<double><<<persistent_grid(k_potrf<double>, 128, sm, ntasks), 128, sm, st>>>(
+    k_potrf<double><<<persistent_grid(k_potrf<double>, kPotrfThreads, sm, ntasks), kPotrfThreads, sm, st>>>(
         tasks, ntasks, queue, sns, mats);
   }
 }
