@@ -73,7 +73,7 @@ __device__ __forceinline__ float pivot_rsqrt(float p) {
 
 // Threads of a POTRF CTA: warp 0 finishes the next column, the others update the trailing
 // triangle (potrf_lookahead).
-constexpr int kPotrfThreads = 128;
+constexpr int kPotrfThreads = 256;
 
 // Position table of the trailing update: the lower triangle of columns 2..n-1 taken column by
 // column from the last (column n-1: 1 entry, column n-2: 2, ...), entry (C << 8) | R.  At step j
