@@ -289,6 +289,13 @@ int chol_opt_d(int64_t n, int32_t nsuper, const int32_t* counts, int32_t* D);
  * (CHOL_GRAN_HYBRID resolved to the rule it chose), *D its threshold (-1 under
  * CHOL_GRAN_TILES), *nsplit the number of supernodes whose Schur update is split. */
 int chol_sym_granularity(const chol_sym* sym, int* rule, int32_t* D, int32_t* nsplit);
+/* The Schur tile tasks of sym's current task lists, all levels and tile sizes: task q
+ * updates the tile of supernode s[q]'s Schur complement with rows i0[q] .. and columns
+ * k0[q] .. of its off-diagonal rows, tile[q] wide (128, 64, 32 or 16; clipped at the
+ * update's order).  With s == NULL only *count is set; otherwise the four host arrays must
+ * hold *count entries (the value a first call returned). */
+int chol_sym_schur_tiles(const chol_sym* sym, int32_t* s, int32_t* i0, int32_t* k0,
+                         int32_t* tile, int64_t* count);
 /* Autotuner: times refactorizations of num (reps each) under candidate tile policies by
  * coordinate descent over the five thresholds, keeps the fastest in num's analysis,
  * stores it in *best (and its time in *best_ms) and leaves num factored under it. */

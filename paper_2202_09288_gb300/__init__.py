@@ -114,6 +114,7 @@ EXPORTS = {
     "chol_autotune": (_I, [_P, _P, _I, C.POINTER(chol_tile_policy), C.POINTER(C.c_double)]),
     "chol_opt_d": (_I, [C.c_int64, C.c_int32, _P, C.POINTER(C.c_int32)]),
     "chol_sym_granularity": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "chol_sym_schur_tiles": (_I, [_P, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "chol_default_server_opts": (None, [C.POINTER(chol_server_opts)]),
     "chol_server_create": (_I, [C.POINTER(chol_server_opts), C.POINTER(_P)]),
     "chol_submit": (_I, [_P, C.POINTER(chol_request), C.POINTER(C.c_uint64)]),
@@ -382,6 +383,18 @@ def chol_sym_granularity(sym) -> dict:
     _check(lib().chol_sym_granularity(sym, C.byref(rule), C.byref(d), C.byref(nsplit)),
            "chol_sym_granularity")
     return {"rule": rule.value, "D": d.value, "nsplit": nsplit.value}
+
+
+def chol_sym_schur_tiles(sym) -> dict:
+    """Every Schur tile task of sym's current task lists: arrays s, i0, k0, tile."""
+    cnt = C.c_int64()
+    _check(lib().chol_sym_schur_tiles(sym, None, None, None, None, C.byref(cnt)),
+           "chol_sym_schur_tiles")
+    out = {k: np.zeros(cnt.value, dtype=np.int32) for k in ("s", "i0", "k0", "tile")}
+    _check(lib().chol_sym_schur_tiles(sym, *[out[k].ctypes.data_as(C.c_void_p)
+                                             for k in ("s", "i0", "k0", "tile")],
+                                      C.byref(cnt)), "chol_sym_schur_tiles")
+    return out
 
 
 def chol_autotune(ctx, num, reps=1) -> tuple[dict, float]:

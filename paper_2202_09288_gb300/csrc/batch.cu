@@ -321,6 +321,32 @@ int chol_opt_d(int64_t n, int32_t nsuper, const int32_t* counts, int32_t* D) {
   return CHOL_OK;
 }
 
+int chol_sym_schur_tiles(const chol_sym* sym, int32_t* s, int32_t* i0, int32_t* k0,
+                         int32_t* tile, int64_t* count) {
+  if (!sym || !count) return CHOL_E_INVALID;
+  const chol::Sym& S = sym->S;
+  int64_t total = 0;
+  for (int cls = 0; cls < chol::kNumTileClasses; cls++)
+    total += (int64_t)S.tasks[chol::schur_kind(cls)].size() / 4;
+  if (!s) {
+    *count = total;
+    return CHOL_OK;
+  }
+  if (*count < total || !i0 || !k0 || !tile) return CHOL_E_INVALID;
+  int64_t q = 0;
+  for (int cls = 0; cls < chol::kNumTileClasses; cls++) {
+    const std::vector<int32_t>& t = S.tasks[chol::schur_kind(cls)];
+    for (size_t e = 0; e < t.size(); e += 4, q++) {
+      s[q] = t[e];
+      i0[q] = t[e + 1];
+      k0[q] = t[e + 2];
+      tile[q] = chol::tile_of_class(cls);
+    }
+  }
+  *count = total;
+  return CHOL_OK;
+}
+
 int chol_sym_granularity(const chol_sym* s, int* rule, int32_t* D, int32_t* nsplit) {
   if (!s) return CHOL_E_INVALID;
   if (rule) *rule = s->S.gran_rule;

@@ -239,3 +239,24 @@ def test_granularity_rules(name):
     assert got["rule"] == (P.CHOL_GRAN_TILES if blas else P.CHOL_GRAN_OPTD_COST)
     with pytest.raises(P.CholError):
         P.chol_sym_set_tile_policy(sym.handle, {"granularity": 4})
+
+
+@pytest.mark.parametrize("name", ["st27x3_8", "lap3d_12", "diff3d7_12", "lap2d_64"])
+@pytest.mark.parametrize("rule", [0, 1, 2, 3])
+def test_schur_tiles_cover_each_update_once(name, rule):
+    """Under every granularity rule, the Schur tiles of each supernode cover the lower
+    triangle of its update U_s = L21 L21^T exactly once (tiles clipped at its order)."""
+    A, perm = inputs.workload(name)
+    sym = P.Symbolic(P.make_opts(width_cap=64), A, perm)
+    P.chol_sym_set_tile_policy(sym.handle, {"granularity": rule})
+    start = sym.export()["sn_start"]
+    rowptr, _ = P.chol_sym_rows(sym.handle)
+    u = np.diff(rowptr) - np.diff(start)
+    t = P.chol_sym_schur_tiles(sym.handle)
+    cover = {s: np.zeros((u[s], u[s]), dtype=np.int32) for s in range(len(u)) if u[s] > 0}
+    for s, i0, k0, T in zip(t["s"], t["i0"], t["k0"], t["tile"]):
+        assert k0 <= i0 and i0 % T == 0 and k0 % T == 0
+        cover[s][i0:i0 + T, k0:k0 + T] += 1
+    for s, c in cover.items():
+        low = c[np.tril_indices(len(c))]
+        assert low.min() == 1 and low.max() == 1, s
