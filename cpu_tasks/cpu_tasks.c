@@ -11,7 +11,7 @@
  *   CT_NONESTED   every update runs inside its supernode's task;
  *   CT_NESTED     every update is a task of its own (inner task), its result is
  *                 subtracted from the panel under a per-supernode lock;
- *   CT_OPTD       nested only for supernodes with more than D updates, D from the OPT-D
+ *   CT_OPTD       nested only for supernodes with at least D updates, D from the OPT-D
  *                 heuristic (Sec. 4.1, Algorithm 1);
  *   CT_OPTD_COST  as CT_OPTD, and an update of fewer than 50,000 flops stays inside its
  *                 supernode's task (Sec. 4.2).
@@ -165,8 +165,10 @@ static void ct_run(ct_problem* P, int32_t t);
 
 static void ct_factor_supernode(ct_problem* P, int32_t t) {
   const int64_t b = P->desc_ptr[t], e = P->desc_ptr[t + 1];
+  /* OPT-D: nested when the supernode receives at least D updates (Sec. 4.1) */
   const int nested_sn = P->policy == CT_NESTED ||
-                        ((P->policy == CT_OPTD || P->policy == CT_OPTD_COST) && e - b > P->D);
+                        ((P->policy == CT_OPTD || P->policy == CT_OPTD_COST) && e > b &&
+                         e - b >= P->D);
   if (nested_sn) {
     for (int64_t q = b; q < e; q++) {
       const int32_t d = P->desc_d[q], p1 = P->desc_p1[q], p2 = P->desc_p2[q];

@@ -178,6 +178,18 @@ int chol_factor_status(chol_ctx* ctx, const chol_num* num, int64_t* bad_col);
  * Lx float64[nnz_l], rows sorted, diagonal first.  Any pointer may be NULL. */
 int chol_factor_export(chol_ctx* ctx, const chol_num* num, int64_t* Lp, int32_t* Li,
                        double* Lx);
+
+/* Copies the raw supernode panels of supernodes first .. first+count-1 (Sec. 2: a supernode
+ * stores its columns as one dense block over the rows of its row list) to out, as float64
+ * (FP32 panels of a CHOL_MIXED factor are widened): panel s is the m_s x n_s column-major
+ * block of L[rows_s, sn_start[s] .. sn_start[s+1]) (m_s and rows_s from chol_sym_rows, n_s
+ * from chol_sym_export's sn_start), the panels one after another in supernode order, so out
+ * holds sum_s m_s n_s doubles.  Entries above the diagonal of a panel's leading n_s x n_s
+ * block are unspecified; under relaxed amalgamation a panel also holds explicit zeros of L.
+ * where: CHOL_HOST (returns once copied) or CHOL_DEVICE (device memory of the context's GPU,
+ * stream-ordered).  Errors: CHOL_E_INVALID for a range outside 0 .. nsuper. */
+int chol_factor_panels(chol_ctx* ctx, const chol_num* num, int64_t first, int64_t count,
+                       double* out, int where);
 void chol_free_num(chol_num* num);
 
 /* Solves A X = B (Sec. 1: L Y = P^T B, then L^T Z = Y, X = P Z) for nrhs right-hand
@@ -224,7 +236,10 @@ int chol_refine(chol_ctx* ctx, chol_num* num, int64_t nrhs, const double* B, int
  * stream capture.  All calls share the array and leave its contents behind; each call
  * clears the work-queue counters at its head (all that must start at zero).  Calls whose
  * device work overlaps (other streams or contexts on the same device) race on it and must
- * be ordered by the caller. */
+ * be ordered by the caller.  The array's address is kept for the life of the process: after
+ * a cudaDeviceReset of a device (which destroys the context it was looked up in) the entry
+ * point must not be used on that device again.  The call leaves the calling thread's
+ * current device as it found it. */
 int chol_solve_noalloc(chol_ctx* ctx, const chol_num* num, int64_t nrhs, const double* B,
                        int64_t ldb, double* X, int64_t ldx);
 size_t chol_noalloc_scratch_bytes(void);
@@ -233,8 +248,10 @@ size_t chol_noalloc_scratch_bytes(void);
  * A batch packs existing factors (same context, precision and assembly mode; any
  * patterns) so that level l of the batch -- level l, counted from the leaves, of every
  * member (Sec. 3, Fig. 1 applied across matrices) -- runs as one launch per kernel kind.
- * Kernels are persistent: each launch covers its task list with at most one wave of
- * CTAs.  With use_graph, the first chol_batch_factorize captures the whole launch
+ * A launch has one CTA per task of its list (the hardware block scheduler refills SMs as
+ * CTAs finish; measured faster than a single resident wave of CTAs taking tasks from a
+ * queue); the 128 x 128 tensor-core Schur launches are the exception, with one resident
+ * CTA per SM taking tasks from a work queue.  With use_graph, the first chol_batch_factorize captures the whole launch
  * sequence into a CUDA graph and later calls replay it.  Members stay usable on their own
  * (chol_solve, chol_refine, chol_factor_status); free the batch before its members. */
 typedef struct chol_batch chol_batch;
@@ -255,7 +272,7 @@ void chol_batch_free(chol_batch* batch);
  * CHOL_SCHUR_DMMA).
  * granularity (Sec. 4 of the paper, re-targeted to tiles): CHOL_GRAN_TILES uses the size
  * thresholds alone.  Otherwise a supernode's Schur update is an outer task and the tiles
- * the thresholds give it are its inner tasks; an outer task with more than D inner tasks
+ * the thresholds give it are its inner tasks; an outer task with at least D inner tasks
  * (D by the OPT-D heuristic, Algorithm 1, over all supernodes) is split into those tiles,
  * the others are done whole (the coarsest tile that covers the update in one task, 128
  * wide above 64 rows).  CHOL_GRAN_OPTD_COST also keeps whole an outer task whose tiles
@@ -282,8 +299,8 @@ int chol_sym_get_tile_policy(const chol_sym* sym, chol_tile_policy* policy);
 int chol_sym_set_tile_policy(chol_sym* sym, const chol_tile_policy* policy);
 /* The threshold D of the OPT-D heuristic (Sec. 4.1, Algorithm 1) for nsuper outer tasks
  * with counts[i] inner tasks each (host array, counts[i] >= 0; NULL allowed when nsuper
- * is 0) and matrix size n: the outer tasks with more than D inner tasks are the ones to
- * split.  CHOL_E_INVALID on n < 0, nsuper < 0 or a negative count. */
+ * is 0) and matrix size n: the outer tasks with at least D (and at least one) inner tasks
+ * are the ones to split.  CHOL_E_INVALID on n < 0, nsuper < 0 or a negative count. */
 int chol_opt_d(int64_t n, int32_t nsuper, const int32_t* counts, int32_t* D);
 /* The granularity rule of sym's current task lists: *rule the CHOL_GRAN_* value applied
  * (CHOL_GRAN_HYBRID resolved to the rule it chose), *D its threshold (-1 under
@@ -382,6 +399,11 @@ typedef struct chol_prof_entry {
 /* Turns event bracketing on (1) or off (0).  Events are recorded on the context stream;
  * do not enable while the stream is being captured into a CUDA graph. */
 int chol_profile_enable(chol_ctx* ctx, int on);
+/* Restricts event bracketing to the launches of one kernel kind (name as in
+ * chol_prof_entry.name, e.g. "schur128_oz"); NULL or "" brackets every kind again.  Launch
+ * counts are kept for every kind either way.  Bracketing one kind keeps the event overhead
+ * off the other launches of a timed region.  CHOL_E_INVALID for an unknown name. */
+int chol_profile_only(chol_ctx* ctx, const char* name);
 /* Synchronizes the stream, folds finished events in, and copies up to max entries; the
  * number of kinds is stored in *count.  Entries with zero launches are included. */
 int chol_profile_read(chol_ctx* ctx, chol_prof_entry* out, int max, int* count);

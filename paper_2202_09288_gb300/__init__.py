@@ -100,6 +100,7 @@ EXPORTS = {
     "chol_refactorize": (_I, [_P, _P, _P, _I]),
     "chol_factor_status": (_I, [_P, _P, C.POINTER(_I64)]),
     "chol_factor_export": (_I, [_P, _P, _P, _P, _P]),
+    "chol_factor_panels": (_I, [_P, _P, _I64, _I64, _P, _I]),
     "chol_free_num": (None, [_P]),
     "chol_solve": (_I, [_P, _P, _I64, _P, _I64, _P, _I64, _I]),
     "chol_refine": (_I, [_P, _P, _I64, _P, _I64, _P, _I64, _I, C.c_double, _I,
@@ -123,6 +124,7 @@ EXPORTS = {
     "chol_server_clock": (C.c_double, [_P]),
     "chol_server_destroy": (None, [_P]),
     "chol_profile_enable": (_I, [_P, _I]),
+    "chol_profile_only": (_I, [_P, C.c_char_p]),
     "chol_profile_read": (_I, [_P, C.POINTER(chol_prof_entry), _I, C.POINTER(_I)]),
     "chol_profile_reset": (_I, [_P]),
 }
@@ -175,15 +177,56 @@ def chol_version() -> int:
     return lib().chol_version()
 
 
+# device ordinal of every live context (for the argument checks of the device-pointer calls)
+_CTX_DEVICE: dict[int, int] = {}
+
+
 def chol_create(opts: chol_opts | None = None) -> int:
     h = C.c_void_p()
     _check(lib().chol_create(C.byref(opts) if opts is not None else None, C.byref(h)),
            "chol_create")
+    _CTX_DEVICE[h.value] = opts.device if opts is not None else 0
     return h.value
 
 
 def chol_destroy(ctx: int) -> None:
+    _CTX_DEVICE.pop(ctx, None)
     lib().chol_destroy(ctx)
+
+
+def _host_block(B, n_hint=None):
+    """A float64 host block as (array, n, k) laid out column-major (a 1-D vector is n x 1)."""
+    if B.dtype != np.float64:
+        raise ValueError(f"host arrays must be float64, not {B.dtype}")
+    B2 = B.reshape(B.shape[0], -1)
+    if not B2.flags.f_contiguous:
+        raise ValueError("host blocks must be column-major (Fortran) contiguous")
+    return B2, B2.shape[0], B2.shape[1]
+
+
+def _check_device_pair(ctx, B, X, where: str):
+    """Device tensors B, X for a solve on ctx: float64, contiguous, X shaped like B, both on
+    the context's GPU.  Returns (k, n): tensor rows are right-hand sides (shape (k, n)), a
+    1-D tensor is one right-hand side."""
+    import torch
+
+    for name, T in (("B", B), ("X", X)):
+        if not isinstance(T, torch.Tensor) or not T.is_cuda:
+            raise ValueError(f"{where}: {name} must be a CUDA tensor")
+        if T.dtype != torch.float64:
+            raise ValueError(f"{where}: {name} must be float64, not {T.dtype}")
+        if not T.is_contiguous():
+            raise ValueError(f"{where}: {name} must be contiguous")
+        if T.dim() not in (1, 2):
+            raise ValueError(f"{where}: {name} must have shape (n,) or (k, n)")
+    if tuple(X.shape) != tuple(B.shape):
+        raise ValueError(f"{where}: X has shape {tuple(X.shape)}, B has {tuple(B.shape)}")
+    dev = _CTX_DEVICE.get(ctx)
+    for name, T in (("B", B), ("X", X)):
+        if dev is not None and T.device.index != dev:
+            raise ValueError(f"{where}: {name} is on cuda:{T.device.index}, the context on "
+                             f"cuda:{dev}")
+    return (1, B.shape[0]) if B.dim() == 1 else (B.shape[0], B.shape[1])
 
 
 def chol_analyze(opts, n, colptr, rowind, perm) -> int:
@@ -258,31 +301,51 @@ def chol_factor_export(ctx, num, n, nnz_l):
     return lp, li, lx
 
 
+def chol_factor_panels(ctx, num, first, count, out):
+    """Copies the raw panels of supernodes first .. first+count-1 into out (a float64 numpy
+    array or CUDA tensor holding sum m_s n_s entries, contiguous)."""
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError("chol_factor_panels: out must be contiguous float64")
+        p, where = out.ctypes.data, CHOL_HOST
+    else:
+        import torch
+
+        if out.dtype != torch.float64 or not out.is_contiguous() or not out.is_cuda:
+            raise ValueError("chol_factor_panels: out must be a contiguous float64 CUDA tensor")
+        p, where = out.data_ptr(), CHOL_DEVICE
+    _check(lib().chol_factor_panels(ctx, num, int(first), int(count), p, where),
+           "chol_factor_panels")
+    return out
+
+
 def chol_free_num(num) -> None:
     lib().chol_free_num(num)
 
 
 def chol_solve(ctx, num, B, X=None):
     """Solves A X = B.  B: numpy (n,) / (n, k) Fortran-ordered, or a torch CUDA tensor laid
-    out column-major (shape (k, n) contiguous, i.e. column c is row c of the tensor)."""
+    out column-major (shape (k, n) contiguous, i.e. column c is row c of the tensor).  A
+    given X must match B (float64, same shape and layout, same device)."""
     if isinstance(B, np.ndarray):
         B2 = np.asfortranarray(B.reshape(B.shape[0], -1), dtype=np.float64)
         n, k = B2.shape
         if X is None:
             X = np.zeros((n, k), dtype=np.float64, order="F")
-        pb, wb = _ptr(B2)
-        px, wx = _ptr(X)
-        _check(lib().chol_solve(ctx, num, k, pb, n, px, n, CHOL_HOST), "chol_solve")
+        elif not isinstance(X, np.ndarray) or X.size != n * k:
+            raise ValueError("chol_solve: X must be a host array with as many entries as B")
+        X2, xn, xk = _host_block(X)
+        if (xn, xk) != (n, k):
+            raise ValueError(f"chol_solve: X is {xn} x {xk}, B is {n} x {k}")
+        _check(lib().chol_solve(ctx, num, k, B2.ctypes.data, n, X2.ctypes.data, n, CHOL_HOST),
+               "chol_solve")
         return X.reshape(B.shape) if B.ndim == 1 else X
     # torch device tensor: (k, n) contiguous = n x k column-major, ld = n
-    k, n = (1, B.shape[0]) if B.dim() == 1 else (B.shape[0], B.shape[1])
     if X is None:
         X = B.new_empty(B.shape)
-    pb, wb = _ptr(B)
-    px, wx = _ptr(X)
-    if wb != CHOL_DEVICE or wx != CHOL_DEVICE:
-        raise ValueError("torch tensors must live on the context's CUDA device")
-    _check(lib().chol_solve(ctx, num, k, pb, n, px, n, CHOL_DEVICE), "chol_solve")
+    k, n = _check_device_pair(ctx, B, X, "chol_solve")
+    _check(lib().chol_solve(ctx, num, k, B.data_ptr(), n, X.data_ptr(), n, CHOL_DEVICE),
+           "chol_solve")
     return X
 
 
@@ -299,8 +362,8 @@ def chol_refine(ctx, num, B, X=None, tol=1e-12, maxit=10, check=True):
                                tol, maxit, C.byref(info))
         out = X2.reshape(B.shape) if B.ndim == 1 else X2
     else:
-        k, n = (1, B.shape[0]) if B.dim() == 1 else (B.shape[0], B.shape[1])
         out = B.new_empty(B.shape) if X is None else X
+        k, n = _check_device_pair(ctx, B, out, "chol_refine")
         rc = lib().chol_refine(ctx, num, k, B.data_ptr(), n, out.data_ptr(), n, CHOL_DEVICE,
                                tol, maxit, C.byref(info))
     d = {"iterations": info.iterations, "fell_back": bool(info.fell_back),
@@ -313,12 +376,9 @@ def chol_refine(ctx, num, B, X=None, tol=1e-12, maxit=10, check=True):
 def chol_solve_noalloc(ctx, num, B, X):
     """Device-pointer solve without any device allocation (torch CUDA tensors laid out as
     in chol_solve: shape (k, n) contiguous, or (n,) for one right-hand side)."""
-    k, n = (1, B.shape[0]) if B.dim() == 1 else (B.shape[0], B.shape[1])
-    pb, wb = _ptr(B)
-    px, wx = _ptr(X)
-    if wb != CHOL_DEVICE or wx != CHOL_DEVICE:
-        raise ValueError("chol_solve_noalloc takes device tensors")
-    _check(lib().chol_solve_noalloc(ctx, num, k, pb, n, px, n), "chol_solve_noalloc")
+    k, n = _check_device_pair(ctx, B, X, "chol_solve_noalloc")
+    _check(lib().chol_solve_noalloc(ctx, num, k, B.data_ptr(), n, X.data_ptr(), n),
+           "chol_solve_noalloc")
     return X
 
 
@@ -406,6 +466,11 @@ def chol_autotune(ctx, num, reps=1) -> tuple[dict, float]:
 
 def chol_profile_enable(ctx, on: bool) -> None:
     _check(lib().chol_profile_enable(ctx, 1 if on else 0), "chol_profile_enable")
+
+
+def chol_profile_only(ctx, name=None) -> None:
+    """Brackets only the launches of kernel kind `name` with events (None: every kind)."""
+    _check(lib().chol_profile_only(ctx, name.encode() if name else None), "chol_profile_only")
 
 
 def chol_profile_read(ctx) -> dict:

@@ -480,27 +480,28 @@ void build_owner_lists(Sym* S) {
 }
 
 int32_t opt_d_threshold(int64_t n, int32_t nsuper, const int32_t* counts) {
-  // outer tasks by their number of inner tasks (a counting sort), walked from the largest
-  // count down: lowering D to d splits the outer tasks with d inner tasks, adding d tasks
-  // each; stop once the task total reaches max(1.1 nsuper, n / 14), D is at most 30 % of
-  // the largest count and at least 0.1 % of the outer tasks are split (Sec. 4.1)
+  // The threshold of Sec. 4.1 as a search: a threshold d splits the outer tasks with at least
+  // d inner tasks, so with split(d) those outer tasks and tasks(d) = nsuper + their inner
+  // tasks, D is the largest d in 1 .. max count at which
+  //   tasks(d) >= max(1.1 nsuper, n / 14),  d <= 0.3 max count,  split(d) >= nsuper / 1000,
+  // and 0 when no d meets all three.  split and tasks only grow as d falls and the middle
+  // condition holds below a bound, so the qualifying d form a range from 1 up to D, and one
+  // pass down a histogram of the counts with running suffix sums finds its top.
   int32_t top = 0;
   for (int32_t i = 0; i < nsuper; i++) top = std::max(top, counts[i]);
-  std::vector<int64_t> with(static_cast<size_t>(top) + 1, 0);
-  for (int32_t i = 0; i < nsuper; i++) with[counts[i]]++;
+  std::vector<int64_t> hist(static_cast<size_t>(top) + 1, 0);
+  for (int32_t i = 0; i < nsuper; i++) hist[counts[i]]++;
   const double goal = std::max(1.1 * nsuper, static_cast<double>(n) / 14.0);
-  int64_t d = static_cast<int64_t>(top) + 1, split = 0;
-  double total = nsuper;
-  auto keep_lowering = [&] {
-    return total < goal || static_cast<double>(d) > 0.3 * top ||
-           static_cast<double>(split) < nsuper / 1000.0;
-  };
-  while (d > 0 && keep_lowering()) {
-    --d;
-    split += with[d];
-    total += static_cast<double>(d) * static_cast<double>(with[d]);
+  int64_t split = 0;
+  double tasks = nsuper;
+  for (int64_t d = top; d >= 1; d--) {
+    split += hist[d];
+    tasks += static_cast<double>(d) * static_cast<double>(hist[d]);
+    if (tasks >= goal && static_cast<double>(d) <= 0.3 * top &&
+        static_cast<double>(split) >= nsuper / 1000.0)
+      return static_cast<int32_t>(d);
   }
-  return static_cast<int32_t>(d);
+  return 0;
 }
 
 void build_schur_tasks(Sym* S, const TilePolicy& policy) {
@@ -556,7 +557,9 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
     for (int32_t s = 0; s < S->ns; s++) {
       const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
       const int64_t T = tile_of_class(cls0[s]);
-      bool split = inner[s] > D;
+      // split when the update has at least D inner tasks (Sec. 4.1: "higher than or equal
+      // to D"); an update with none is never split
+      bool split = inner[s] > 0 && inner[s] >= D;
       // OPT-D-COST (Sec. 4.2): inner tasks of fewer than 50,000 flops are not worth a task
       if (split && rule == kGranOptDCost && 2.0 * T * T * w < 50000.0) split = false;
       if (inner[s] > 0) {

@@ -36,9 +36,11 @@ cudaEvent_t prof_event(chol_ctx* c) {
   return e;
 }
 
-// Brackets one launch of kind k (the launch count is always kept).
-void prof_begin(chol_ctx* c) {
-  if (!c->prof_on) return;
+// Brackets one launch of kind k (the launch count is always kept).  With a kind selected
+// by chol_profile_only, only launches of that kind are bracketed: prof_begin(c, k) of
+// another kind records nothing.
+void prof_begin(chol_ctx* c, int k) {
+  if (!c->prof_on || (c->prof_only >= 0 && k != c->prof_only)) return;
   c->open_event = prof_event(c);
   if (c->open_event) cudaEventRecord(c->open_event, c->stream);
 }
@@ -284,7 +286,7 @@ int enqueue_assembly(chol_num* f) {
   CK(cudaMemsetAsync(f->d_err, 0xff, sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(f->d_err + 1, 0, 3 * sizeof(unsigned long long), st));
   f->anorm = -1.0;
-  prof_begin(c);
+  prof_begin(c, f32 ? kProfScale : kProfAssemble);
   CK(cudaMemsetAsync(f->L, 0, (size_t)S.l_storage * esz, st));
   if (f32) {
     chol::launch_diag_scale(sym->dev.a_colptr, sym->dev.a_rowind, f->d_vals, sym->dev.iperm,
@@ -331,13 +333,13 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
     int* q = ctr + kFactorCountersPerLevel * l;  // this level's work-queue counters
     const int4* t = v.level(chol::kTaskPotrf, l, &cnt);
     if (cnt > 0) {
-      prof_begin(c);
+      prof_begin(c, kp);
       chol::launch_potrf(t, cnt, q, sns, mats, v.max_width, f32, tau, st);
       prof_end(c, kp, v.flops[chol::kTaskPotrf][l], 0.0);
     }
     t = v.level(chol::kTaskTrsm, l, &cnt);
     if (cnt > 0) {
-      prof_begin(c);
+      prof_begin(c, kt);
       chol::launch_trsm(t, cnt, q + 1, sns, v.max_width, f32, st);
       prof_end(c, kt, v.flops[chol::kTaskTrsm][l], 0.0);
     }
@@ -346,7 +348,7 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
     if (oz) {
       t = v.level(chol::kTaskOzSlice, l, &cnt);
       if (cnt > 0) {
-        prof_begin(c);
+        prof_begin(c, kProfOzSlice);
         if (f32) chol::launch_tf32_split(t, cnt, sns, v.max_width, oz, oz_rows, st);
         else chol::launch_oz_slice(t, cnt, sns, oz, oz_rows, st);
         prof_end(c, kProfOzSlice, 0.0, 0.0);
@@ -357,16 +359,17 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
       t = v.level(kind, l, &cnt);
       if (cnt <= 0) continue;
       const bool tcc = oz && cls == chol::kTile128;
-      prof_begin(c);
+      const int pk = prof_schur_kind(cls, f32, tcc && !f32);
+      prof_begin(c, pk);
       if (tcc && f32) chol::launch_schur_tc(t, cnt, q + 2 + cls, sns, mats, owner, oz, oz_rows, st);
       else if (tcc) chol::launch_schur_oz(t, cnt, q + 2 + cls, sns, mats, owner, oz, oz_rows, st);
       else chol::launch_schur(cls, t, cnt, q + 2 + cls, sns, mats, owner, f32, st);
-      prof_end(c, prof_schur_kind(cls, f32, tcc && !f32), v.flops[kind][l], 0.0);
+      prof_end(c, pk, v.flops[kind][l], 0.0);
     }
     if (owner) {
       t = v.level(chol::kTaskAsm, l, &cnt);
       if (cnt > 0) {
-        prof_begin(c);
+        prof_begin(c, kProfAsmOwner);
         chol::launch_assemble_owner(t, cnt, q + 2 + chol::kNumTileClasses, v.asm_src, sns, mats, f32, st);
         prof_end(c, kProfAsmOwner, 0.0, 0.0);
       }
@@ -474,9 +477,36 @@ int ensure_solve_ws(chol_num* f, int64_t nrhs) {
   return CHOL_OK;
 }
 
-// Device-pointer solve of nrhs <= 32 columns.
-int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx) {
-  chol_ctx* c = f->ctx;
+// Work buffers of one device solve of k <= 32 right-hand sides: the work-queue counters
+// (3 per level, zeroed by the solve), y and w (n x k each), the backward partial sums (the
+// most backward tasks of a level x W x k) and, for owner assembly, the forward staging (the
+// most forward tasks of a level x kSolveRows x k; null otherwise).
+struct SolveBufs {
+  int* sq;
+  double* y;
+  double* w;
+  double* part;
+  double* fstage;
+};
+
+// Tracing of one launch of the solve sequence: with trace, event brackets when profiling is
+// on (prof_begin / prof_end); without, only the launch count (no event is created).
+struct SolveTrace {
+  chol_ctx* c;
+  bool trace;
+  void begin(int kind) const {
+    if (trace) prof_begin(c, kind);
+  }
+  void end(int kind, double bytes) const {
+    if (trace) prof_end(c, kind, 0.0, bytes);
+    else c->prof[kind].launches++;
+  }
+};
+
+// The launch sequence of a device-pointer solve of k <= 32 columns (Sec. 1: L y = P^T b
+// over the levels from the leaves up, then L^T z = y from the root down, x = P z).
+int enqueue_solve_seq(chol_ctx* c, const chol_num* f, int k, const double* B, int64_t ldb,
+                      double* X, int64_t ldx, const SolveBufs& bf, bool trace) {
   const chol_sym* sym = f->sym;
   const Sym& S = sym->S;
   cudaStream_t st = c->stream;
@@ -484,38 +514,44 @@ int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X
   const int W = S.width_cap;
   const bool f32 = f->precision == CHOL_MIXED;
   const double* scale = f32 ? f->d_scale : nullptr;
-  const double vec = 8.0 * n * nrhs;
-  int* sq = f->d_ctr + factor_counters(S.nlev);  // solve work-queue counters
-  CK(cudaMemsetAsync(sq, 0, solve_counters(S.nlev) * sizeof(int), st));
-  prof_begin(c);
-  chol::launch_gather_perm(B, ldb, sym->dev.perm, scale, n, nrhs, f->d_y, st);
-  prof_end(c, kProfPerm, 0.0, 2 * vec + 4.0 * n);
+  const double vec = 8.0 * n * k;
+  const SolveTrace tr{c, trace};
+  CK(cudaMemsetAsync(bf.sq, 0, solve_counters(S.nlev) * sizeof(int), st));
+  tr.begin(kProfPerm);
+  chol::launch_gather_perm(B, ldb, sym->dev.perm, scale, n, k, bf.y, st);
+  tr.end(kProfPerm, 2 * vec + 4.0 * n);
   for (int32_t l = 0; l < S.nlev; l++) {
     int cnt;
     const int4* t = task_ptr(sym, chol::kTaskFwd, l, &cnt);
-    prof_begin(c);
-    chol::launch_fwd(t, cnt, sq + 3 * l, f->d_sn, n, nrhs, W, f->d_y, f->d_w, f->d_fstage, f32,
-                     st);
-    if (f->d_fstage)
+    tr.begin(kProfFwd);
+    chol::launch_fwd(t, cnt, bf.sq + 3 * l, f->d_sn, n, k, W, bf.y, bf.w, bf.fstage, f32, st);
+    if (bf.fstage)
       chol::launch_fwd_gather(sym->dev.fg_row + S.fg_lvl[l], sym->dev.fg_ptr + S.fg_lvl[l],
-                              sym->dev.fg_ent, S.fg_lvl[l + 1] - S.fg_lvl[l], n, nrhs,
-                              f->d_fstage, f->d_y, st);
-    prof_end(c, kProfFwd, 0.0, S.lvl_panel_bytes[l] * (f32 ? 0.5 : 1.0));
+                              sym->dev.fg_ent, S.fg_lvl[l + 1] - S.fg_lvl[l], n, k, bf.fstage,
+                              bf.y, st);
+    tr.end(kProfFwd, S.lvl_panel_bytes[l] * (f32 ? 0.5 : 1.0));
   }
   for (int32_t l = S.nlev - 1; l >= 0; l--) {
     int nb, nd;
     const int4* tb = task_ptr(sym, chol::kTaskBwd, l, &nb);
     const int4* td = task_ptr(sym, chol::kTaskPotrf, l, &nd);
-    prof_begin(c);
-    chol::launch_bwd(tb, nb, sq + 3 * l + 1, S.task_off[chol::kTaskBwd][l], td, nd, f->d_sn, n,
-                     nrhs, W, f->d_w, f->d_part, f32, st);
-    prof_end(c, kProfBwd, 0.0, S.lvl_panel_bytes[l] * (f32 ? 0.5 : 1.0));
+    tr.begin(kProfBwd);
+    chol::launch_bwd(tb, nb, bf.sq + 3 * l + 1, S.task_off[chol::kTaskBwd][l], td, nd, f->d_sn,
+                     n, k, W, bf.w, bf.part, f32, st);
+    tr.end(kProfBwd, S.lvl_panel_bytes[l] * (f32 ? 0.5 : 1.0));
   }
-  prof_begin(c);
-  chol::launch_scatter_perm(f->d_w, sym->dev.perm, scale, n, nrhs, X, ldx, st);
-  prof_end(c, kProfPerm, 0.0, 2 * vec + 4.0 * n);
+  tr.begin(kProfPerm);
+  chol::launch_scatter_perm(bf.w, sym->dev.perm, scale, n, k, X, ldx, st);
+  tr.end(kProfPerm, 2 * vec + 4.0 * n);
   CK(cudaGetLastError());
   return CHOL_OK;
+}
+
+// Device-pointer solve of nrhs <= 32 columns in the factor's own workspace.
+int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx) {
+  const SolveBufs bf{f->d_ctr + factor_counters(f->sym->S.nlev), f->d_y, f->d_w, f->d_part,
+                     f->d_fstage};
+  return enqueue_solve_seq(f->ctx, f, nrhs, B, ldb, X, ldx, bf, true);
 }
 
 void free_num_buffers(chol_num* f) {
@@ -642,7 +678,7 @@ int compute_anorm(chol_num* f) {
   const chol_sym* sym = f->sym;
   unsigned long long* slot = f->d_norm + 2 * 32;
   CK(cudaMemsetAsync(slot, 0, 8, c->stream));
-  prof_begin(c);
+  prof_begin(c, kProfRefine);
   chol::launch_anorm(sym->dev.csr_ptr, sym->dev.csr_src, f->d_vals, sym->S.n, slot, c->stream);
   prof_end(c, kProfRefine, 0.0, 0.0);
   unsigned long long v = 0;
@@ -661,7 +697,7 @@ int residual_norms(chol_num* f, int k, const double* B, int64_t ldb, const doubl
   const chol_sym* sym = f->sym;
   const int64_t n = sym->S.n;
   CK(cudaMemsetAsync(f->d_norm, 0, 2 * 32 * 8, c->stream));
-  prof_begin(c);
+  prof_begin(c, kProfRefine);
   chol::launch_residual(sym->dev.csr_ptr, sym->dev.csr_col, sym->dev.csr_src, f->d_vals, n, k, X,
                         ldx, B, ldb, f->d_rr, n, c->stream);
   chol::launch_absmax(f->d_rr, n, n, k, f->d_norm, c->stream);
@@ -705,7 +741,7 @@ int refine_pass(chol_num* f, chol_num* g, int k, const double* B, int64_t ldb, d
     if (stall >= 2) return CHOL_E_STALL;
     prev = rmax;
     if ((rc = enqueue_solve(g, k, f->d_rr, n, f->d_rd, n))) return rc;
-    prof_begin(c);
+    prof_begin(c, kProfRefine);
     chol::launch_axpy(X, ldx, f->d_rd, n, n, k, c->stream);
     prof_end(c, kProfRefine, (double)n * k, 24.0 * n * k);
     info->iterations++;
@@ -735,44 +771,16 @@ int enqueue_solve_ws(chol_ctx* c, const chol_num* f, int k, const double* B, int
                      double* X, int64_t ldx, double* ws) {
   const chol_sym* sym = f->sym;
   const Sym& S = sym->S;
-  cudaStream_t st = c->stream;
-  const int64_t n = S.n;
-  const int W = S.width_cap;
-  const bool f32 = f->precision == CHOL_MIXED;
-  const double* scale = f32 ? f->d_scale : nullptr;
-  int* sq = reinterpret_cast<int*>(ws);  // work-queue counters, then the vectors
-  const size_t qd = (solve_counters(S.nlev) * sizeof(int) + 255) / 256 * 256 / sizeof(double);
-  if (cudaMemsetAsync(sq, 0, solve_counters(S.nlev) * sizeof(int), st) != cudaSuccess)
-    return CHOL_E_CUDA;
-  double* y = ws + qd;
-  double* w = y + (size_t)n * k;
-  double* part = w + (size_t)n * k;
-  double* fstage = nullptr;
-  if (f->assembly == CHOL_ASSEMBLY_OWNER)
-    fstage = part + (size_t)sym->max_bwd_per_level * W * k;
-  launch_gather_perm(B, ldb, sym->dev.perm, scale, n, k, y, st);
-  c->prof[kProfPerm].launches++;
-  for (int32_t l = 0; l < S.nlev; l++) {
-    int cnt;
-    const int4* t = task_ptr(sym, kTaskFwd, l, &cnt);
-    launch_fwd(t, cnt, sq + 3 * l, f->d_sn, n, k, W, y, w, fstage, f32, st);
-    if (fstage)
-      launch_fwd_gather(sym->dev.fg_row + S.fg_lvl[l], sym->dev.fg_ptr + S.fg_lvl[l],
-                        sym->dev.fg_ent, S.fg_lvl[l + 1] - S.fg_lvl[l], n, k, fstage, y, st);
-    c->prof[kProfFwd].launches++;
-  }
-  for (int32_t l = S.nlev - 1; l >= 0; l--) {
-    int nb, nd;
-    const int4* tb = task_ptr(sym, kTaskBwd, l, &nb);
-    const int4* td = task_ptr(sym, kTaskPotrf, l, &nd);
-    launch_bwd(tb, nb, sq + 3 * l + 1, S.task_off[kTaskBwd][l], td, nd, f->d_sn, n, k, W, w,
-               part, f32, st);
-    c->prof[kProfBwd].launches++;
-  }
-  launch_scatter_perm(w, sym->dev.perm, scale, n, k, X, ldx, st);
-  c->prof[kProfPerm].launches++;
-  if (cudaGetLastError() != cudaSuccess) return CHOL_E_CUDA;
-  return CHOL_OK;
+  const size_t qd = (rt::solve_counters(S.nlev) * sizeof(int) + 255) / 256 * 256 / sizeof(double);
+  rt::SolveBufs bf;
+  bf.sq = reinterpret_cast<int*>(ws);  // work-queue counters, then the vectors
+  bf.y = ws + qd;
+  bf.w = bf.y + (size_t)S.n * k;
+  bf.part = bf.w + (size_t)S.n * k;
+  bf.fstage = f->assembly == CHOL_ASSEMBLY_OWNER
+                  ? bf.part + (size_t)sym->max_bwd_per_level * S.width_cap * k
+                  : nullptr;
+  return rt::enqueue_solve_seq(c, f, k, B, ldb, X, ldx, bf, false);
 }
 
 // Checks the arguments of a device-pointer solve; on success *n_out holds the order.
@@ -1066,6 +1074,55 @@ int chol_factor_export(chol_ctx* c, const chol_num* f, int64_t* Lp, int32_t* Li,
   return CHOL_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// out[i] = in[i] as a double (FP32 panels of a mixed factor, widened for export).
+__global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+int chol_factor_panels(chol_ctx* c, const chol_num* f, int64_t first, int64_t count,
+                       double* out, int where) {
+  if (!c || !f || f->ctx != c || (where != CHOL_HOST && where != CHOL_DEVICE)) return CHOL_E_INVALID;
+  const Sym& S = f->sym->S;
+  if (first < 0 || count < 0 || first > S.ns || count > S.ns - first) return CHOL_E_INVALID;
+  const int64_t v0 = S.sn_valptr[first], v1 = S.sn_valptr[first + count];
+  if (v1 == v0) return CHOL_OK;
+  if (!out) return CHOL_E_INVALID;
+  if (cudaSetDevice(c->opts.device) != cudaSuccess) return CHOL_E_NODEVICE;
+  const size_t nv = (size_t)(v1 - v0);
+  if (f->precision != CHOL_MIXED) {
+    CK(cudaMemcpyAsync(out, static_cast<const double*>(f->L) + v0, nv * sizeof(double),
+                       where == CHOL_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       c->stream));
+  } else if (where == CHOL_DEVICE) {
+    const int blocks = (int)std::min<int64_t>(((int64_t)nv + 255) / 256, 152 * 16);
+    k_widen<<<blocks, 256, 0, c->stream>>>(static_cast<const float*>(f->L) + v0, out, (int64_t)nv);
+    CK(cudaGetLastError());
+  } else {
+    std::vector<float> tmp;
+    try {
+      tmp.resize(nv);
+    } catch (...) {
+      return CHOL_E_OOM;
+    }
+    CK(cudaMemcpyAsync(tmp.data(), static_cast<const float*>(f->L) + v0, nv * sizeof(float),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < nv; i++) out[i] = (double)tmp[i];
+  }
+  if (where == CHOL_HOST) CK(cudaStreamSynchronize(c->stream));
+  return CHOL_OK;
+}
+
 void chol_free_num(chol_num* f) {
   if (!f) return;
   if (f->fb) chol_free_num(f->fb);
@@ -1173,6 +1230,20 @@ int chol_profile_enable(chol_ctx* c, int on) {
   if (!c) return CHOL_E_INVALID;
   c->prof_on = on != 0;
   return CHOL_OK;
+}
+
+int chol_profile_only(chol_ctx* c, const char* name) {
+  if (!c) return CHOL_E_INVALID;
+  if (!name || !name[0]) {
+    c->prof_only = -1;
+    return CHOL_OK;
+  }
+  for (int k = 0; k < kNumProf; k++)
+    if (strcmp(name, kProfNames[k]) == 0) {
+      c->prof_only = k;
+      return CHOL_OK;
+    }
+  return CHOL_E_INVALID;
 }
 
 int chol_profile_read(chol_ctx* c, chol_prof_entry* out, int max, int* count) {

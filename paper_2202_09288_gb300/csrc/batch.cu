@@ -282,7 +282,7 @@ int chol_batch_factorize(chol_ctx* c, chol_batch* b, const double* const* vals, 
     }
     b->graph = g;
   }
-  prof_begin(c);
+  prof_begin(c, kProfGraph);
   if (cudaGraphLaunch(b->exec, c->stream) != cudaSuccess) {
     cudaGetLastError();
     return CHOL_E_CUDA;

@@ -743,11 +743,11 @@ void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
   if (ntasks <= 0) return;
   if (f32) {
     const size_t sm = potrf_mixed_smem(max_width);
-    k_potrf_mixed<<<persistent_grid(k_potrf_mixed, kPotrfThreads, sm, ntasks), kPotrfThreads, sm, st>>>(
+    k_potrf_mixed<<<task_grid(k_potrf_mixed, kPotrfThreads, sm, ntasks), kPotrfThreads, sm, st>>>(
         tasks, ntasks, queue, sns, mats, tau);
   } else {
     const size_t sm = potrf_smem(max_width);
-    k_potrf<double><<<persistent_grid(k_potrf<double>, kPotrfThreads, sm, ntasks), kPotrfThreads, sm, st>>>(
+    k_potrf<double><<<task_grid(k_potrf<double>, kPotrfThreads, sm, ntasks), kPotrfThreads, sm, st>>>(
         tasks, ntasks, queue, sns, mats);
   }
 }
@@ -757,12 +757,12 @@ static void trsm_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns, 
                    cudaStream_t st) {
   if (max_width <= 64) {
     constexpr size_t sm = trsm_blk_smem<T>();
-    k_trsm_blk<T><<<persistent_grid(k_trsm_blk<T>, 32 * kTrsmWarps, sm, ntasks), 32 * kTrsmWarps, sm, st>>>(
+    k_trsm_blk<T><<<task_grid(k_trsm_blk<T>, 32 * kTrsmWarps, sm, ntasks), 32 * kTrsmWarps, sm, st>>>(
         tasks, ntasks, queue, sns);
     return;
   }
   const size_t sm = trsm_smem(max_width);
-  k_trsm<T><<<persistent_grid(k_trsm<T>, 32, sm, ntasks), 32, sm, st>>>(tasks, ntasks, queue, sns);
+  k_trsm<T><<<task_grid(k_trsm<T>, 32, sm, ntasks), 32, sm, st>>>(tasks, ntasks, queue, sns);
 }
 
 void launch_trsm(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int max_width,
@@ -776,7 +776,7 @@ template <int T, bool OWNER>
 static void schur_f64_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                         const MatDev* mats, cudaStream_t st, int vsplit = 0) {
   constexpr int th = SchurCfg<T>::THREADS;
-  k_schur_f64<T, OWNER><<<persistent_grid(k_schur_f64<T, OWNER>, th, 0, ntasks << vsplit), th, 0,
+  k_schur_f64<T, OWNER><<<task_grid(k_schur_f64<T, OWNER>, th, 0, ntasks << vsplit), th, 0,
                          st>>>(tasks, ntasks, queue, sns, mats, vsplit);
 }
 
@@ -784,7 +784,7 @@ template <int T, bool OWNER>
 static void schur_f32_t(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                         const MatDev* mats, cudaStream_t st, int vsplit = 0) {
   constexpr int th = SchurF32Cfg<T>::THREADS;
-  k_schur_f32<T, OWNER><<<persistent_grid(k_schur_f32<T, OWNER>, th, 0, ntasks << vsplit), th, 0,
+  k_schur_f32<T, OWNER><<<task_grid(k_schur_f32<T, OWNER>, th, 0, ntasks << vsplit), th, 0,
                          st>>>(tasks, ntasks, queue, sns, mats, vsplit);
 }
 
@@ -816,7 +816,7 @@ void launch_schur(int cls, const int4* tasks, int ntasks, int* queue, const SnDe
 template <typename T>
 static void asm_owner_t(const int4* groups, int ngroups, int* queue, const int4* srcs,
                         const SnDev* sns, const MatDev* mats, cudaStream_t st) {
-  k_assemble_owner<T><<<persistent_grid(k_assemble_owner<T>, kAsmThreads, 0, ngroups),
+  k_assemble_owner<T><<<task_grid(k_assemble_owner<T>, kAsmThreads, 0, ngroups),
                         kAsmThreads, 0, st>>>(groups, ngroups, queue, srcs, sns, mats);
 }
 

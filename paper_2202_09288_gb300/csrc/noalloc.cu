@@ -49,6 +49,21 @@ int scratch_address(int device, double** out) {
   return CHOL_OK;
 }
 
+// Runs the solve with `device` current and makes the caller's current device current again
+// on every return path (the caller may drive another GPU from the same thread).
+int solve_on_device(chol_ctx* ctx, const chol_num* num, int device, int64_t nrhs,
+                    int64_t chunk, const double* B, int64_t ldb, double* X, int64_t ldx) {
+  double* ws = nullptr;
+  int rc = scratch_address(device, &ws);
+  if (rc) return rc;
+  for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
+    const int k = (int)(nrhs - c0 < chunk ? nrhs - c0 : chunk);
+    rc = chol::enqueue_solve_ws(ctx, num, k, B + c0 * ldb, ldb, X + c0 * ldx, ldx, ws);
+    if (rc) return rc;
+  }
+  return CHOL_OK;
+}
+
 }  // namespace
 
 extern "C" size_t chol_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
@@ -62,16 +77,19 @@ extern "C" int chol_solve_noalloc(chol_ctx* ctx, const chol_num* num, int64_t nr
   const int64_t chunk = nrhs < 32 ? nrhs : 32;
   if (chol::solve_scratch_doubles(num, chunk) > kNoAllocScratchDoubles) return CHOL_E_SCRATCH;
   const int device = chol::ctx_device(ctx);
-  if (cudaSetDevice(device) != cudaSuccess) {
+  int caller = -1;
+  if (cudaGetDevice(&caller) != cudaSuccess) {
+    cudaGetLastError();
+    caller = -1;
+  }
+  if (caller != device && cudaSetDevice(device) != cudaSuccess) {
     cudaGetLastError();
     return CHOL_E_NODEVICE;
   }
-  double* ws = nullptr;
-  if ((rc = scratch_address(device, &ws))) return rc;
-  for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
-    const int k = (int)(nrhs - c0 < chunk ? nrhs - c0 : chunk);
-    rc = chol::enqueue_solve_ws(ctx, num, k, B + c0 * ldb, ldb, X + c0 * ldx, ldx, ws);
-    if (rc) return rc;
+  rc = solve_on_device(ctx, num, device, nrhs, chunk, B, ldb, X, ldx);
+  if (caller >= 0 && caller != device && cudaSetDevice(caller) != cudaSuccess) {
+    cudaGetLastError();
+    if (!rc) rc = CHOL_E_CUDA;
   }
-  return CHOL_OK;
+  return rc;
 }

@@ -51,6 +51,7 @@ struct chol_ctx {
   bool attrs_set = false;
   // tracing
   bool prof_on = false;
+  int prof_only = -1;  // kind whose launches alone are bracketed (-1: every kind)
   chol_prof_entry prof[kNumProf];
   std::vector<ProfPending> pending;
   std::vector<cudaEvent_t> spare_events;
@@ -170,7 +171,7 @@ void fill_descriptors(const chol_num* f, int mat, int32_t sn_base, std::vector<S
 
 int dev_alloc(chol_ctx* c, void** p, size_t bytes);
 void dev_free(chol_ctx* c, void* p);
-void prof_begin(chol_ctx* c);
+void prof_begin(chol_ctx* c, int kind);
 void prof_end(chol_ctx* c, int k, double flops, double bytes);
 const int4* task_ptr(const chol_sym* s, int kind, int32_t level, int* count);
 int ensure_uploaded(chol_ctx* c, chol_sym* s);

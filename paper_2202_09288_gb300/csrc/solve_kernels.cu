@@ -353,11 +353,11 @@ static void fwd_nr(const int4* tasks, int ntasks, int* queue, const SnDev* sns, 
                    int nrhs, int W, double* y, double* w, double* fstage, cudaStream_t st) {
   const size_t sm = solve_smem(W, nrhs);
   if (fstage)
-    k_fwd<P, true, NR><<<persistent_grid(k_fwd<P, true, NR>, kSolveThreads, sm, ntasks),
+    k_fwd<P, true, NR><<<task_grid(k_fwd<P, true, NR>, kSolveThreads, sm, ntasks),
                          kSolveThreads, sm, st>>>(tasks, ntasks, queue, sns, ldv, nrhs, y, w,
                                                   fstage);
   else
-    k_fwd<P, false, NR><<<persistent_grid(k_fwd<P, false, NR>, kSolveThreads, sm, ntasks),
+    k_fwd<P, false, NR><<<task_grid(k_fwd<P, false, NR>, kSolveThreads, sm, ntasks),
                           kSolveThreads, sm, st>>>(tasks, ntasks, queue, sns, ldv, nrhs, y, w,
                                                    nullptr);
 }
@@ -385,7 +385,7 @@ static void bwd_partial_nr(const int4* tasks, int ntasks, int* queue, const SnDe
                            int64_t ldv, int nrhs, int W, const double* w, double* part,
                            cudaStream_t st) {
   const size_t sp = bwd_partial_smem(W, NR);
-  k_bwd_partial<P, NR><<<persistent_grid(k_bwd_partial<P, NR>, kSolveThreads, sp, ntasks),
+  k_bwd_partial<P, NR><<<task_grid(k_bwd_partial<P, NR>, kSolveThreads, sp, ntasks),
                          kSolveThreads, sp, st>>>(tasks, ntasks, queue, sns, ldv, nrhs, W, w,
                                                   part);
 }
@@ -419,7 +419,7 @@ static void bwd_t(const int4* bwd_tasks, int nbwd, int* queues, int64_t bwd_base
   }
   if (ndiag > 0) {
     const size_t sm = solve_smem(W, nrhs);
-    k_bwd_diag<P><<<persistent_grid(k_bwd_diag<P>, kSolveThreads, sm, ndiag), kSolveThreads, sm,
+    k_bwd_diag<P><<<task_grid(k_bwd_diag<P>, kSolveThreads, sm, ndiag), kSolveThreads, sm,
                     st>>>(diag_tasks, ndiag, queues + 1, bwd_base, sns, ldv, nrhs, W, part, w);
   }
 }

@@ -40,3 +40,20 @@ def fig1_matrix():
     for c, p in edges:
         a[c - 1, p - 1] = a[p - 1, c - 1] = -1.0
     return inputs.from_dense(a)
+
+
+def column_error(lp, lx, ref_lx):
+    """max_j ||L[:, j] - L_ref[:, j]||_2 / ||L_ref[:, j]||_2 over the columns of two factors
+    stored on the same CSC pattern (lp): the relative-error tolerance applied to every
+    column, so that an error confined to small-magnitude entries cannot hide behind the
+    norm of the whole factor."""
+    import numpy as np
+    lp = np.asarray(lp, dtype=np.int64)
+    counts = np.diff(lp)
+    if counts.size == 0:
+        return 0.0
+    nz = counts > 0
+    starts = lp[:-1][nz]
+    d2 = np.add.reduceat((np.asarray(lx) - np.asarray(ref_lx)) ** 2, starts)
+    r2 = np.add.reduceat(np.asarray(ref_lx) ** 2, starts)
+    return float(np.sqrt(np.max(d2 / np.maximum(r2, np.finfo(float).tiny))))

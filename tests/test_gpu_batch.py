@@ -9,6 +9,7 @@ import pytest
 import oracle
 import paper_2202_09288_gb300 as P
 from paper_2202_09288_gb300 import inputs
+from conftest import column_error
 
 pytestmark = pytest.mark.gpu
 
@@ -43,6 +44,8 @@ def check_member(ctx, num, A, perm, ref):
     assert np.array_equal(li, ref.li)
     err = np.linalg.norm(lx - ref.lx) / np.linalg.norm(ref.lx)
     assert err <= FACTOR_TOL, err
+    cerr = column_error(lp, lx, ref.lx)
+    assert cerr <= FACTOR_TOL, cerr
     b = A.to_scipy_full() @ inputs.rhs_block(2, A.n, 1)[:, 0]
     x = num.solve(b)
     assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, b, x) <= RESID_TOL
@@ -65,6 +68,7 @@ def test_batch_of_different_matrices(torch, use_graph):
     for num, ref in zip(nums, refs):
         lx = num.export()[2]
         assert np.linalg.norm(lx - 2 * ref.lx) / np.linalg.norm(2 * ref.lx) <= FACTOR_TOL
+        assert column_error(ref.lp, lx, 2 * ref.lx) <= FACTOR_TOL
     batch.close()
 
 

@@ -3,13 +3,16 @@
 The factor L of B = P^T A P is unique (Sec. 1: A = L L^T); the device path reorganizes the
 left-looking supernodal algorithm (Sec. 3, Listing 1) per etree level, so it must give the
 oracle's L up to rounding: the pattern bit for bit and the values within 1e-12 relative
-Frobenius error; every solve must reach a relative residual <= 1e-13."""
+Frobenius error, over the whole factor and column by column; every solve must reach a
+relative residual <= 1e-13."""
 import numpy as np
 import pytest
 
 import oracle
 import paper_2202_09288_gb300 as P
 from paper_2202_09288_gb300 import inputs
+from conftest import column_error
+import llt_sample
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +59,8 @@ def check_factor(ctx, name, W):
     assert np.array_equal(lp, f.lp) and np.array_equal(li, f.li)
     err = np.linalg.norm(lx - f.lx) / np.linalg.norm(f.lx)
     assert err <= FACTOR_TOL, err
+    cerr = column_error(lp, lx, f.lx)
+    assert cerr <= FACTOR_TOL, cerr
     xt = inputs.rhs_block(3, A.n, 1)[:, 0]
     b = A.to_scipy_full() @ xt
     x = num.solve(b)
@@ -111,11 +116,13 @@ def test_device_values_and_refactorize(torch):
     assert num.status()[0] == P.CHOL_OK
     lx1 = num.export()[2]
     assert np.linalg.norm(lx1 - f.lx) / np.linalg.norm(f.lx) <= FACTOR_TOL
+    assert column_error(f.lp, lx1, f.lx) <= FACTOR_TOL
     # new values on the same pattern: 4 A has factor 2 L
     num.refactor(4.0 * A.vals)
     assert num.status()[0] == P.CHOL_OK
     lx2 = num.export()[2]
     assert np.linalg.norm(lx2 - 2.0 * f.lx) / np.linalg.norm(2.0 * f.lx) <= FACTOR_TOL
+    assert column_error(f.lp, lx2, 2.0 * f.lx) <= FACTOR_TOL
 
 
 def test_not_spd_reported(torch):
@@ -191,3 +198,49 @@ def test_full_size_st27x3_48_properties(torch):
     b = A.to_scipy_full() @ xt
     x = num.solve(b)
     assert oracle.residual(n, A.colptr, A.rowind, A.vals, b, x) <= RESID_TOL
+
+
+def test_full_size_st27x3_80_properties(torch):
+    """The 80^3 3-dof workload (n = 1,536,000, nnz(L) = 4.0e9), the largest single-GPU
+    configuration, factored in the launch configuration the bench times.  The oracle cannot
+    factor it, and exporting L as CSC would need ~50 GB of host memory, so rows of L are read
+    from the raw panels (copied on the device) at sampled columns -- the root separator's
+    last columns, whose updates run on the 128 x 128 tensor-core tiles, columns of the top
+    separators, and random ones -- and entries of L L^T are compared with B = P^T A P,
+    including fill entries where L L^T must cancel to 0; then solves are checked by their
+    residual and forward error (diagonally dominant by at least 1, so kappa is small)."""
+    ctx = P.Context()
+    A, perm = inputs.workload("st27x3_80")
+    sym = P.Symbolic(ctx, A, perm)
+    num = P.Factor(ctx, sym, torch.from_numpy(A.vals).cuda())
+    assert num.status()[0] == P.CHOL_OK
+    n = A.n
+    start = sym.export()["sn_start"]
+    rowptr, rows = P.chol_sym_rows(sym.handle)
+    w, m, valptr = llt_sample.panel_layout(start, rowptr)
+    panels = torch.empty(int(valptr[-1]), dtype=torch.float64, device="cuda")
+    P.chol_factor_panels(ctx.handle, num.handle, 0, len(w), panels)
+    torch.cuda.synchronize()
+
+    def gather(idx):
+        return panels[torch.from_numpy(idx).cuda()].cpu().numpy()
+
+    bp, bi, bx = oracle.permute(n, A.colptr, A.rowind, A.vals, perm)
+    col2sn = np.repeat(np.arange(len(w)), w)
+    u = (inputs.uniform(12, 8, 30) + 1.0) / 2.0
+    js = np.unique(np.concatenate([
+        np.arange(n - 6, n),                                  # the root separator's last columns
+        (n - 1 - u[:12] * 0.05 * n).astype(np.int64),         # the top separators
+        (u[12:] * n).astype(np.int64)]))                      # anywhere
+    pairs = llt_sample.sample_pairs(js, bp, bi, start, rowptr, rows, col2sn, 12, 4, 5)
+    need = np.unique(np.array(pairs).ravel())
+    Lrows = llt_sample.rows_of_l(need, start, rowptr, rows, gather)
+    del panels
+    err = llt_sample.max_llt_error(pairs, Lrows, bp, bi, bx)
+    assert err <= 1e-13, err
+    Afull = A.to_scipy_full()
+    Xt = inputs.rhs_block(4, n, 2)
+    Bm = np.asfortranarray(Afull @ Xt)
+    X = num.solve(Bm)
+    assert oracle.residual(n, A.colptr, A.rowind, A.vals, Bm, X) <= RESID_TOL
+    assert np.abs(X - Xt).max() <= 1e-11 * np.abs(Xt).max()

@@ -11,6 +11,7 @@ import pytest
 import oracle
 import paper_2202_09288_gb300 as P
 from paper_2202_09288_gb300 import inputs
+from conftest import column_error
 
 pytestmark = pytest.mark.gpu
 
@@ -73,6 +74,8 @@ def test_mixed_factor_matches_oracle_of_scaled_matrix(torch, name):
     assert np.array_equal(li, ref.li)
     err = np.linalg.norm(lx - ref.lx) / np.linalg.norm(ref.lx)
     assert err <= 2e-6, err  # FP32 rounding of a well-conditioned factor
+    cerr = column_error(lp, lx, ref.lx)
+    assert cerr <= 1e-5, cerr
 
 
 def test_refine_with_fp64_factor(torch):
@@ -176,6 +179,8 @@ def test_tensor_core_tiles_match_oracle(torch, name, assembly):
     assert np.array_equal(li, ref.li)
     err = np.linalg.norm(lx - ref.lx) / np.linalg.norm(ref.lx)
     assert err <= 2e-6, err
+    cerr = column_error(lp, lx, ref.lx)
+    assert cerr <= 1e-5, cerr
     # and the tensor-core factor agrees with the SIMT FP32 factor to FP32 rounding
     _, _, simt, prof_simt = mixed_factor(A, perm, TC_OFF, assembly)
     assert prof_simt["schur128_tc"]["launches"] == 0

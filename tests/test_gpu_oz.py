@@ -10,6 +10,7 @@ import pytest
 import oracle
 import paper_2202_09288_gb300 as P
 from paper_2202_09288_gb300 import inputs
+from conftest import column_error
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +64,11 @@ def test_oz_tiles_match_oracle(torch, name, assembly):
     assert np.array_equal(li, ref.li)
     err = np.linalg.norm(lx - ref.lx) / np.linalg.norm(ref.lx)
     assert err <= 1e-12, err
+    # column by column too: the slices' error is relative to each row's largest entry, and
+    # in the row-scaled case an error confined to the small rows would not move the norm
+    # of the whole factor
+    cerr = column_error(lp, lx, ref.lx)
+    assert cerr <= 1e-12, cerr
     b = A.to_scipy_full() @ inputs.rhs_block(5, A.n, 1)[:, 0]
     x = num.solve(b)
     assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, b, x) <= 1e-13
@@ -74,8 +80,10 @@ def test_oz_agrees_with_dmma(torch, name):
     _, _, oz, prof = factor(A, perm)
     _, _, dm, prof_dm = factor(A, perm, mode=P.CHOL_SCHUR_DMMA)
     assert prof_dm["schur128_oz"]["launches"] == 0 and prof_dm["schur128_f64"]["launches"] > 0
-    a, b = oz.export()[2], dm.export()[2]
+    lp, _, a = oz.export()
+    b = dm.export()[2]
     assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 1e-14
+    assert column_error(lp, a, b) <= 1e-13
 
 
 def test_oz_owner_bitwise_alone_and_batched(torch):
@@ -116,3 +124,4 @@ def test_oz_width_128_uses_dmma(torch):
     assert prof["schur128_oz"]["launches"] == 0
     lx = num.export()[2]
     assert np.linalg.norm(lx - ref.lx) / np.linalg.norm(ref.lx) <= 1e-12
+    assert column_error(ref.lp, lx, ref.lx) <= 1e-12

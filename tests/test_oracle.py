@@ -275,3 +275,61 @@ def test_hybrid_switch_cases():
     assert not oracle.hybrid_uses_blas(1000, 100, 10)        # avg 10
     assert not oracle.hybrid_uses_blas(1000, 20, 10**5)      # avg exactly 50 (not above), density 0.1
     assert oracle.hybrid_uses_blas(1000, 20, 10)             # avg 50 > 20 and density 1e-5 < 1e-4
+
+
+def _dense_b(f):
+    """B = P^T A P as a full dense symmetric matrix, from the oracle's lower CSC."""
+    B = np.zeros((f.n, f.n))
+    for j in range(f.n):
+        rows = f.bi[f.bp[j]:f.bp[j + 1]]
+        B[rows, j] = f.bx[f.bp[j]:f.bp[j + 1]]
+        B[j, rows] = f.bx[f.bp[j]:f.bp[j + 1]]
+    return B
+
+
+@pytest.mark.parametrize("name", ["lap2d_9", "st27x3_3", "diff3d7_5", "dense"])
+def test_llt_error_matches_dense_norm(name):
+    """||B - L L^T||_F / ||B||_F against the same quantity formed densely with numpy, on a
+    factor perturbed in every stored entry (so the error is far above rounding and a dropped
+    term, a missing factor 2 on the off-diagonal entries or a skipped diagonal shows)."""
+    if name == "dense":
+        A, perm = inputs.random_spd_dense(20, 4), None
+    else:
+        A, perm = inputs.workload(name)
+    f = oracle.cholesky(A, perm)
+    lx = f.lx * (1.0 + 1e-3 * inputs.uniform(21, 2, f.lx.size))
+    L = np.zeros((f.n, f.n))
+    for j in range(f.n):
+        L[f.li[f.lp[j]:f.lp[j + 1]], j] = lx[f.lp[j]:f.lp[j + 1]]
+    B = _dense_b(f)
+    want = np.linalg.norm(B - L @ L.T) / np.linalg.norm(B)
+    got = oracle.llt_error(f.n, f.bp, f.bi, f.bx, f.lp, f.li, lx)
+    assert want > 1e-6
+    assert abs(got - want) <= 1e-10 * want, (got, want)
+
+
+@pytest.mark.parametrize("which", ["offdiag", "diag"])
+def test_llt_error_single_entry_closed_form(which):
+    """L' = L + delta e_i e_j^T (entry (i, j) of the pattern) gives
+    L' L'^T - L L^T = delta (c e_i^T + e_i c^T) + delta^2 e_i e_i^T with c = L[:, j], whose
+    Frobenius norm squared is 2 delta^2 sum_{k != i} c_k^2 + (2 delta c_i + delta^2)^2.
+    L L^T equals B to rounding, so the oracle's ||B - L' L'^T||_F must be that value."""
+    A, perm = inputs.workload("lap2d_8")
+    f = oracle.cholesky(A, perm)
+    j = 17
+    q = f.lp[j] + (1 if which == "offdiag" else 0)  # first off-diagonal entry, or the pivot
+    i = int(f.li[q])
+    assert (i > j) == (which == "offdiag")
+    delta = 1e-4
+    lx = f.lx.copy()
+    lx[q] += delta
+    c = np.zeros(f.n)
+    c[f.li[f.lp[j]:f.lp[j + 1]]] = f.lx[f.lp[j]:f.lp[j + 1]]
+    e2 = 2 * delta ** 2 * (np.sum(c ** 2) - c[i] ** 2) + (2 * delta * c[i] + delta ** 2) ** 2
+    bnorm = np.sqrt(np.sum(np.where(f.bi == np.repeat(np.arange(f.n), np.diff(f.bp)), 1.0, 2.0)
+                           * f.bx ** 2))
+    want = np.sqrt(e2) / bnorm
+    got = oracle.llt_error(f.n, f.bp, f.bi, f.bx, f.lp, f.li, lx)
+    assert abs(got - want) <= 1e-9 * want, (got, want)
+    # the unperturbed factor sits at rounding level, far below the perturbation
+    assert oracle.llt_error(f.n, f.bp, f.bi, f.bx, f.lp, f.li, f.lx) <= 1e-6 * want
