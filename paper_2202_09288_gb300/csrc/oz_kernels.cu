@@ -10,10 +10,12 @@
 //               for the tensor cores' 128-byte swizzle;
 //   k_schur_oz  a 128 x 128 task is done as four 128 x 32 quarters.  The 8 A slices
 //               (the task's 128 rows) and each quarter's 8 B slices (its 32 rows) are
-//               brought into shared memory by bulk copies; one producer thread issues,
-//               for every slice pair p + q < 8, the bf16 MMAs of D_{p+q} += S_p S_q^T into
-//               the quarter's set of tensor-memory accumulators (one per diagonal p + q,
-//               8 x 32 columns; two sets).  Every partial sum of a diagonal is an integer
+//               brought into shared memory by bulk copies issued by a load thread, which
+//               also claims the tasks; an MMA thread issues, for every slice pair p + q < 8,
+//               the bf16 MMAs of D_{p+q} += S_p S_q^T into the quarter's set of tensor-memory
+//               accumulators (one per diagonal p + q, 8 x 32 columns; two sets), slice by
+//               slice, so that a task's last quarter releases each A slice for the next task
+//               as soon as its MMAs are done.  Every partial sum of a diagonal is an integer
 //               below 2^22 (K <= 64), so FP32 accumulation is exact.  Consumer warps read a
 //               finished set (lane = tile row), release it, form U[i,k] = 2^(e_i+e_k)
 //               sum_d 2^(-7(d+2)) D_d[i,k] as an FP64 value (integer combination, one
@@ -38,7 +40,10 @@ namespace {
 
 constexpr int kOzConsumers = 512;                          // 16 warps: drain + scatter
 constexpr int kOzMetaThreads = 128;                        // 4 warps: per-task metadata
-constexpr int kOzThreads = kOzConsumers + 32 + kOzMetaThreads;  // + the producer warp
+constexpr int kOzMmaWarp = kOzConsumers / 32;              // issues the MMAs (one thread)
+constexpr int kOzLoadWarp = kOzMmaWarp + 1;                // issues the bulk copies (one thread)
+constexpr int kOzMetaBase = kOzConsumers + 64;             // first metadata thread
+constexpr int kOzThreads = kOzMetaBase + kOzMetaThreads;
 constexpr int kOzRing = 16;
 constexpr int kOzM = 128;                                  // tile rows (UMMA M)
 constexpr int kOzN = 64;                                   // columns per half (UMMA N)
@@ -229,36 +234,54 @@ __device__ __forceinline__ void oz_tmem_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// An FP32 value holding an integer of magnitude below 2^22, as that integer: adding
-// 1.5 * 2^23 puts it in the low mantissa bits.
-__device__ __forceinline__ int32_t oz_int(uint32_t f) {
-  return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
+// The FP32 bits of x + 1.5 * 2^23 for an accumulator x holding an integer of magnitude below
+// 2^22: 0x4B400000 + x, i.e. the integer plus a fixed offset in the low mantissa bits.
+__device__ __forceinline__ uint32_t oz_fbits(uint32_t acc) {
+  return __float_as_uint(__uint_as_float(acc) + 12582912.0f);
 }
 
-// Four diagonals D_d .. D_d+3 of eight columns -> sum_j D_(d+j) 2^(7(3-j)) (< 2^44 in
-// magnitude): two int32 Horner steps, one 64-bit combination.
-__device__ __forceinline__ void oz_combine4(const uint32_t (&v)[4][8], long long (&out)[8]) {
-#pragma unroll
-  for (int j = 0; j < 8; j++) {
-    const int hi = oz_int(v[0][j]) * 128 + oz_int(v[1][j]);  // |.| < 2^30
-    const int lo = oz_int(v[2][j]) * 128 + oz_int(v[3][j]);
-    out[j] = (long long)((unsigned long long)(long long)hi << 14) + lo;  // hi 2^14 + lo
-  }
+// W = V_hi 2^20 + round(V_lo / 2^8) from the offset bits f_d = 0x4B400000 + D_d of the eight
+// diagonals (V_hi = sum_{d<4} D_d 2^(7(3-d)), V_lo = sum_{d>=4} D_d 2^(7(7-d)), |D_d| < 2^22, so
+// |W| < 2^62).  The offsets are never subtracted one by one: kOzLoBias = 128 - 0x4B400000 S
+// (S = 1 + 2^7 + 2^14 + 2^21) removes those of V_lo and adds the rounding constant before the
+// shift; the high diagonals enter modulo 2^64 (f_3 2^20 and f_2 2^27 as 32 x 32 -> 64-bit
+// multiply-adds, f_1 2^34 + f_0 2^41 in the high word alone), and kOzHiBias = -(0x4B400000
+// 2^20 S) >> 32 removes their offsets (it has no low word).  Exact since |W| < 2^63.
+constexpr unsigned long long kOzLoBias = 0xfff6850a14c00080ull;
+constexpr uint32_t kOzHiBias = 0x50a14c00u;
+
+__device__ __forceinline__ unsigned long long oz_low(uint32_t f4, uint32_t f5, uint32_t f6,
+                                                     uint32_t f7) {
+  unsigned long long v = (unsigned long long)f7 + kOzLoBias;
+  v = (unsigned long long)f6 * 128ull + v;
+  v = (unsigned long long)f5 * 16384ull + v;
+  v = (unsigned long long)f4 * 2097152ull + v;
+  return (unsigned long long)((long long)v >> 8);  // round(V_lo / 2^8), half up
 }
 
+__device__ __forceinline__ long long oz_high(unsigned long long lo, uint32_t f0, uint32_t f1,
+                                             uint32_t f2, uint32_t f3) {
+  unsigned long long w = (unsigned long long)f3 * 1048576ull + lo;
+  w = (unsigned long long)f2 * 134217728ull + w;
+  w += (unsigned long long)(f1 * 4u + f0 * 512u + kOzHiBias) << 32;
+  return (long long)w;
+}
 
-// W 2^E as a double, rounded to nearest (ties to even): the FP64 unit's int64 -> double
-// conversion, then an add to the exponent field (exact inside the normal range; ldexp
-// otherwise).  The FP64 unit is otherwise idle in this kernel, and one conversion there
-// costs the consumer warps far fewer issue slots than normalizing and rounding the 64-bit
-// integer with integer operations (measured: the Schur kernel 13 % faster).
+// s W 2^E as a double (s = -1 when NEG), rounded to nearest (ties to even): the FP64 unit's
+// int64 -> double conversion, then an add to the exponent field and, for NEG, to the sign bit
+// (exact inside the normal range; ldexp for zero and outside it).  The FP64 unit is otherwise
+// idle in this kernel, and one conversion there costs the consumer warps far fewer issue slots
+// than normalizing and rounding the 64-bit integer with integer operations.
+template <bool NEG>
 __device__ __forceinline__ double oz_to_double(long long W, int E) {
-  if (W == 0) return 0.0;
   const double d = __ll2double_rn(W);
-  const long long bits = __double_as_longlong(d);
-  const int be = (int)((bits >> 52) & 0x7ff) + E;
-  if (be <= 0 || be >= 2047) return ldexp(d, E);
-  return __longlong_as_double(bits + ((long long)E << 52));
+  const uint32_t hi = (uint32_t)__double2hiint(d);
+  const int be = (int)((hi >> 20) & 0x7ffu) + E;
+  if (hi != 0u && (unsigned)(be - 1) < 2046u)
+    return __hiloint2double((int)(hi + (uint32_t)E * 1048576u + (NEG ? 0x80000000u : 0u)),
+                            __double2loint(d));
+  const double r = ldexp(d, E);
+  return NEG ? -r : r;
 }
 
 constexpr int kOzMaxRuns = 16;  // column targets per task whose relative rows are cached
@@ -268,7 +291,7 @@ constexpr int kOzMaxRuns = 16;  // column targets per task whose relative rows a
 static_assert(2 * kOzN == 128, "the run count sums four 32-column words");
 struct OzMeta {
   double* cp[2 * kOzN];  // each column's target panel column (its relative rows are added)
-  int eA[kOzM], eB[2 * kOzN];
+  int eA[kOzM], eB[2 * kOzN];  // row exponents e_i; column exponents e_k - 55
   int tcol[2 * kOzN], run[2 * kOzN];
   int run_start[2 * kOzN + 1];
   int wcnt[2 * kOzN / 32];  // run starts per 32 columns
@@ -290,15 +313,18 @@ __device__ __forceinline__ void oz_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// A task is done as 128 x 32 quarters.  The producer thread (its own warp) loads the task's
-// A slices once and the B slices of every quarter into one of two quarter buffers, and
-// issues each quarter's MMAs into one of two TMEM sets of 8 diagonals x 32 columns; the 16
-// consumer warps drain a finished set (and release it) while the tensor cores compute the
-// next quarter, then scatter; four metadata warps build each task's exponents, column
-// targets and relative rows ahead of use.  Barriers: a_full (A slices in), b_full[2]
-// (quarter B buffers in), acc_full[2] (a set's MMAs done: also frees the B buffer they
-// read), acc_empty[2] (a set drained), meta_full[2] / meta_empty[2] (a metadata buffer
-// built / released), ring_full[] (the task order, for the consumers and metadata warps).
+// A task is done as 128 x 32 quarters.  A load thread (its own warp) claims the tasks, hands
+// each one to the other roles through a ring as soon as it has claimed it, and bulk-copies
+// the task's 8 A slices once and every quarter's B slices into one of two quarter buffers;
+// an MMA thread (its own warp) issues each quarter's MMAs into one of two TMEM sets of 8
+// diagonals x 32 columns, slice by slice; the 16 consumer warps drain a finished set (and
+// release it) while the tensor cores compute the next quarter, then scatter; four metadata
+// warps build each task's exponents, column targets and relative rows one task ahead.
+// Barriers: a_full[p] (A slice p in), a_free[p] (the MMAs of a task's last quarter that read
+// A slice p are done: the slice may be reloaded for the next task while the later slices'
+// MMAs still run), b_full[2] (quarter B buffers in), acc_full[2] (a set's MMAs done: also
+// frees the B buffer they read), acc_empty[2] (a set drained), meta_full[2] / meta_empty[2]
+// (a metadata buffer built / released), ring_full[] (the task order).
 template <bool OWNER>
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_schur_oz(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
@@ -310,7 +336,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   unsigned char* Bq0 = A + kOzABytes;  // quarter buffers: Bq0, Bq0 + kOzQBytes
   __shared__ __align__(8) uint64_t a_full, b_full[2], acc_full[2], acc_empty[2];
   __shared__ __align__(8) uint64_t ring_full[kOzRing];
-  __shared__ int ring[kOzRing];
+  __shared__ int2 ring[kOzRing];  // {task, quarters | K steps << 8} (task = ntasks: stop)
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t meta_full[2], meta_empty[2];
   __shared__ OzMeta meta[2];
@@ -333,7 +359,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&b_full[i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[i])),
-                   "r"(kOzConsumers / 32));
+                   "r"(kOzConsumers / 64));  // the 8 warps of the set's consumer group
     }
     for (int i = 0; i < kOzRing; i++)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ring_full[i])));
@@ -350,8 +376,78 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
 
-  if (warp == kOzConsumers / 32) {
-    // ---------------- producer: operand loads and MMAs, one thread ----------------
+  if (warp == kOzLoadWarp) {
+    // ---------------- loads: task claims, ring, bulk copies; one thread ----------------
+    if (lane == 0) {
+      long long T = 0;                       // tasks whose A slices were issued
+      long long qb = 0;                      // quarter B buffers issued (buffer = qb & 1)
+      long long ord = 0;                     // ring entries published
+      bool ok = true;
+      int tq = blockIdx.x;                   // a CTA's first task is its block index
+      for (;;) {
+        int4 t = make_int4(0, 0, 0, 0);
+        int nq = 0, ks = 0;
+        if (tq < ntasks) {
+          t = tasks[tq];
+          const SnDev& dd = sns[t.x];
+          nq = min(4, (dd.m - dd.n - t.z + kOzQ - 1) / kOzQ);
+          ks = (dd.n + 15) >> 4;
+        }
+        const int rs = (int)(ord % kOzRing);
+        ring[rs] = make_int2(tq < ntasks ? tq : ntasks, nq | (ks << 8));
+        oz_arrive(smem_u32(&ring_full[rs]));
+        ord++;
+        if (tq >= ntasks) break;
+        // quarter j's B slices, once the MMAs of the quarter two back (same buffer) are done
+        auto load_b = [&](int j) -> bool {
+          const int b = (int)(qb & 1);
+          if (qb >= 2 && !oz_wait(smem_u32(&acc_full[b]), (uint32_t)(((qb >> 1) - 1) & 1)))
+            return false;
+          const uint32_t bar = smem_u32(&b_full[b]);
+          unsigned char* dst = Bq0 + b * kOzQBytes;
+          oz_expect(bar, kOzQBytes);
+          for (int p = 0; p < kOzSlices; p++)
+            oz_bulk_load(smem_u32(dst + p * kOzQSlice),
+                         oz + p * stride + (size_t)(t.w + t.z + kOzQ * j) * kOzRowBytes,
+                         kOzQSlice, bar);
+          qb++;
+          return true;
+        };
+        // the first quarter's B goes first: its buffer is free before the A slices are
+        if (!load_b(0)) {
+          ok = false;
+          break;
+        }
+        // the A slices of this task, once the previous task's last quarter (the latest quarter
+        // before this task's first, qb - 2) is done: every K step reads every slice
+        if (T >= 1 && !oz_wait(smem_u32(&acc_full[(qb - 2) & 1]), (uint32_t)(((qb - 2) >> 1) & 1))) {
+          ok = false;
+          break;
+        }
+        oz_expect(smem_u32(&a_full), kOzABytes);
+        for (int p = 0; p < kOzSlices; p++)
+          oz_bulk_load(smem_u32(A + p * kOzASlice),
+                       oz + p * stride + (size_t)(t.w + t.y) * kOzRowBytes, kOzASlice,
+                       smem_u32(&a_full));
+        T++;
+        for (int j = 1; j < nq && ok; j++) ok = load_b(j);
+        if (!ok) break;
+        tq = gridDim.x >= ntasks ? ntasks : (int)gridDim.x + atomicAdd(queue, 1);
+      }
+      if (!ok) {
+        s_fail = 1;
+        const int rs = (int)(ord % kOzRing);
+        ring[rs] = make_int2(ntasks, 0);
+        oz_arrive(smem_u32(&ring_full[rs]));
+      }
+      // bounded waits for the copies still in flight: the last A load and the last B load of
+      // each buffer
+      if (T >= 1) oz_wait(smem_u32(&a_full), (uint32_t)((T - 1) & 1));
+      for (long long qq = qb - 2 < 0 ? 0 : qb - 2; qq < qb; qq++)
+        oz_wait(smem_u32(&b_full[qq & 1]), (uint32_t)((qq >> 1) & 1));
+    }
+  } else if (warp == kOzMmaWarp) {
+    // ---------------- MMAs, one thread ----------------
     if (lane == 0) {
       // N = (8 - p) x 32: the MMA of slice p against slices 0 .. 7-p of a quarter
       uint32_t idesc[kOzSlices];
@@ -359,49 +455,19 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       for (int p = 0; p < kOzSlices; p++) idesc[p] = oz_idesc((kOzSlices - p) * kOzQ);
       const uint64_t da0 = oz_desc(smem_u32(A));
       const uint64_t db[2] = {oz_desc(smem_u32(Bq0)), oz_desc(smem_u32(Bq0 + kOzQBytes))};
-      long long a_issued = 0, b_issued[2] = {0, 0};  // loads issued per barrier
-      auto load_a = [&](const int4& t) {
-        const uint32_t bar = smem_u32(&a_full);
-        oz_expect(bar, kOzABytes);
-        for (int p = 0; p < kOzSlices; p++)
-          oz_bulk_load(smem_u32(A + p * kOzASlice),
-                       oz + p * stride + (size_t)(t.w + t.y) * kOzRowBytes, kOzASlice, bar);
-        a_issued++;
-      };
-      auto load_b = [&](const int4& t, int j, int b) {
-        const uint32_t bar = smem_u32(&b_full[b]);
-        unsigned char* dst = Bq0 + b * kOzQBytes;
-        oz_expect(bar, kOzQBytes);
-        for (int p = 0; p < kOzSlices; p++)
-          oz_bulk_load(smem_u32(dst + p * kOzQSlice),
-                       oz + p * stride + (size_t)(t.w + t.z + kOzQ * j) * kOzRowBytes, kOzQSlice,
-                       bar);
-        b_issued[b]++;
-      };
-      auto quarters = [&](const int4& t) {
-        const SnDev& dd = sns[t.x];
-        return min(4, (dd.m - dd.n - t.z + kOzQ - 1) / kOzQ);
-      };
       bool ok = true;
-      long long q = 0;          // quarters issued (set and buffer = q & 1)
-      long long a_use = 0;      // A loads completed-and-waited
-      int ord = 0;
-      int tq = blockIdx.x;
-      ring[0] = tq < ntasks ? tq : ntasks;
-      oz_arrive(smem_u32(&ring_full[0]));
-      if (tq < ntasks) {
-        load_a(tasks[tq]);
-        load_b(tasks[tq], 0, 0);
-      }
-      while (ok && tq < ntasks) {
-        const int4 t = tasks[tq];
-        const int nq = quarters(t);
-        const int ks = (sns[t.x].n + 15) >> 4;
-        if (!oz_wait(smem_u32(&a_full), (uint32_t)(a_use & 1))) { ok = false; break; }
-        a_use++;
-        // the next task is fetched now so its first quarter can be prefetched
-        const int next = gridDim.x >= ntasks ? ntasks : (int)gridDim.x + atomicAdd(queue, 1);
-        for (int j = 0; j < nq && ok; j++, q++) {
+      long long q = 0;  // quarters issued (TMEM set and B buffer = q & 1)
+      long long T = 0;  // tasks issued
+      for (long long ord = 0; ok; ord++) {
+        const int rs = (int)(ord % kOzRing);
+        if (!oz_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kOzRing) & 1))) {
+          ok = false;
+          break;
+        }
+        const int2 e = ring[rs];
+        if (e.x >= ntasks) break;
+        const int nq = e.y & 0xff, ks = e.y >> 8;
+        for (int j = 0; j < nq; j++, q++) {
           const int b = (int)(q & 1);
           if (!oz_wait(smem_u32(&b_full[b]), (uint32_t)((q >> 1) & 1)) ||
               (q >= 2 &&  // the set was drained (quarter q - 2)
@@ -409,7 +475,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             ok = false;
             break;
           }
+          if (j == 0 && !oz_wait(smem_u32(&a_full), (uint32_t)(T & 1))) {  // the task's A
+            ok = false;
+            break;
+          }
           asm volatile("tcgen05.fence::after_thread_sync;");
+          // K step outer, slice inner: consecutive MMAs start at different diagonals (measured
+          // 2.3x faster than issuing one slice's K steps back to back into the same columns)
           for (int k = 0; k < ks; k++)
 #pragma unroll
             for (int p = 0; p < kOzSlices; p++)
@@ -417,44 +489,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                      da0 + (uint64_t)((p * kOzASlice) >> 4) + 2 * k, db[b] + 2 * k, idesc[p],
                      (p > 0 || k > 0) ? 1u : 0u);
           oz_commit(smem_u32(&acc_full[b]));
-          // prefetch the next quarter into the other buffer (its MMAs, quarter q - 1, must
-          // be done); the next task's A waits for this quarter's MMAs
-          const bool last = j + 1 == nq;
-          if (!last || next < ntasks) {
-            if (q >= 1 && !oz_wait(smem_u32(&acc_full[b ^ 1]), (uint32_t)(((q - 1) >> 1) & 1))) {
-              ok = false;
-              break;
-            }
-            if (last) {
-              if (!oz_wait(smem_u32(&acc_full[b]), (uint32_t)((q >> 1) & 1))) { ok = false; break; }
-              load_a(tasks[next]);
-              load_b(tasks[next], 0, b ^ 1);
-            } else {
-              load_b(t, j + 1, b ^ 1);
-            }
-          }
         }
-        if (!ok) break;
-        ord++;
-        tq = next;
-        ring[ord % kOzRing] = tq < ntasks ? tq : ntasks;
-        oz_arrive(smem_u32(&ring_full[ord % kOzRing]));
+        T++;
       }
-      if (!ok) {
-        s_fail = 1;
-        ring[(ord + 1) % kOzRing] = ntasks;
-        oz_arrive(smem_u32(&ring_full[(ord + 1) % kOzRing]));
-      }
-      // bounded waits for the MMAs and copies still in flight (a quarter's B buffer is
-      // waited once per quarter issued: b_issued[b] - (quarters on b) loads remain)
+      if (!ok) s_fail = 1;
+      // bounded wait for the MMAs in flight (the last quarter's commit covers all earlier ones)
       if (q >= 1) oz_wait(smem_u32(&acc_full[(q - 1) & 1]), (uint32_t)(((q - 1) >> 1) & 1));
-      for (int b = 0; b < 2; b++) {
-        const long long waited = (q + 1 - b) >> 1;  // quarters issued on buffer b
-        if (b_issued[b] > waited) oz_wait(smem_u32(&b_full[b]), (uint32_t)(waited & 1));
-      }
-      if (a_issued > a_use) oz_wait(smem_u32(&a_full), (uint32_t)(a_use & 1));
     }
-  } else if (warp > kOzConsumers / 32) {
+  } else if (warp >= kOzMetaBase / 32) {
     // ---------------- metadata warps: one thread per tile row / column ----------------
     // For each task in ring order, into meta[ord & 1] once the consumers have released it:
     // the rows' and columns' slice exponents, every column's target supernode, the runs of
@@ -462,18 +504,18 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     // per run the relative-map base and target panel, and the relative rows of the first
     // kOzMaxRuns runs.  Thread 0 alone waits on the ring and on the buffer, so that the
     // group's decisions are uniform.
-    const int mt = tid - (kOzConsumers + 32), mwarp = mt >> 5;
+    const int mt = tid - kOzMetaBase, mwarp = mt >> 5;
     for (int ord = 0;; ord++) {
       const int buf = ord & 1;
       if (mt == 0) {
         const int rs = ord % kOzRing;
         int tq = ntasks;
         if (!oz_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kOzRing) & 1)) ||
-            (ring[rs] < ntasks && ord >= 2 &&
+            (ring[rs].x < ntasks && ord >= 2 &&
              !oz_wait(smem_u32(&meta_empty[buf]), (uint32_t)(((ord >> 1) - 1) & 1))))
           s_fail = 1;
         else
-          tq = ring[rs];
+          tq = ring[rs].x;
         s_mtq = tq;
       }
       oz_meta_sync();
@@ -487,7 +529,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const MatDev md = mats[d.mat];
       const int gk = k0 + mt;
       M.eA[mt] = (i0 + mt < u) ? exps[tk.w + i0 + mt] : 0;
-      M.eB[mt] = gk < u ? exps[tk.w + gk] : 0;
+      M.eB[mt] = (gk < u ? exps[tk.w + gk] : 0) - 55;  // U = W 2^(e_i + e_k - 55)
       if (mt == 0) {
         M.u = u;
         M.i0 = i0;
@@ -545,17 +587,23 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     }
   } else {
     // ---------------- consumers: set drain and scatter ----------------
-    // Each wait's outcome is made uniform over the warp (tcgen05.ld is warp-collective).
-    long long q = 0;
-    const int i = 32 * (warp & 3) + lane;  // this thread's tile row
-    const int c8 = 8 * (warp >> 2);        // this thread's 8 columns of a quarter
+    // Two groups of 8 warps, one per TMEM set: group g takes the quarters on set g (global
+    // quarter index q with q & 1 == g), a warp 32 rows x 16 columns of it as two chunks of 8
+    // columns.  The groups work half a quarter apart, so one group's conversions (FP64 unit)
+    // overlap the other's atomics (memory pipe) instead of all 16 warps running each phase
+    // at once.  A set is released after the warp's second chunk is drained.  Each wait's
+    // outcome is made uniform over the warp (tcgen05.ld is warp-collective).
+    const int grp = warp >> 3;
+    const int i = 32 * (warp & 3) + lane;     // this thread's tile row
+    const int c16 = 16 * ((warp >> 2) & 1);   // this warp's 16 columns of a quarter
+    long long q0 = 0;                         // global index of the task's first quarter
     for (int ord = 0;; ord++) {
       const int rs = ord % kOzRing, buf = ord & 1;
       if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kOzRing) & 1)))) {
         s_fail = 1;
         break;
       }
-      if (ring[rs] >= ntasks) break;
+      if (ring[rs].x >= ntasks) break;
       const OzMeta& M = meta[buf];
       if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&meta_full[buf]), (uint32_t)((ord >> 1) & 1)))) {
         s_fail = 1;
@@ -566,57 +614,86 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int gi = i0 + i;
       const int eA = M.eA[i];
       bool stop = false;
-      for (int j = 0; j < nq; j++, q++) {
-        const int b = (int)(q & 1);
+      for (int j = 0; j < nq && !stop; j++) {
+        const long long q = q0 + j;
+        if ((int)(q & 1) != grp) continue;
+        const int b = grp;
         if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&acc_full[b]), (uint32_t)((q >> 1) & 1)))) {
           s_fail = 1;
           stop = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // the 8 diagonals of this thread's 8 columns -> integers -> W = V_hi 2^20 +
-        // round(V_lo / 2^8) (V_hi = sum_{d<4} D_d 2^(7(3-d)), V_lo = sum_{d>=4} D_d
-        // 2^(7(7-d)), |D_d| < 2^22): U = W 2^(e_i + e_k - 55)
-        double val[8];
-        {
-          long long vh[8], vl[8];
-          const uint32_t ta =
-              tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * kOzSetCols + c8);
-          {
-            uint32_t v[4][8];
+        for (int c = 0; c < 2; c++) {
+          const int c8 = c16 + 8 * c;  // this chunk's 8 columns of the quarter
+          const int kb = kOzQ * j + c8, gk0 = k0 + kb;
+          const int r0w = i0 + 32 * (warp & 3);  // the warp's first tile row
+          // warp-uniform: no entry of the chunk in the lower triangle of the update (past
+          // its order, or above the diagonal): nothing to read but the release
+          const bool dead = r0w >= u || gk0 >= u || r0w + 31 < gk0;
+          double val[8];
+          if (!dead) {
+            // the 8 diagonals of the chunk's columns -> W (exact integer) -> U = W 2^(e_i +
+            // e_k - 55)
+            const uint32_t ta =
+                tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * kOzSetCols + c8);
+            unsigned long long w[8];
+            {
+              uint32_t v[4][8];
 #pragma unroll
-            for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)(dd * kOzQ), v[dd]);
-            oz_tmem_wait();
-            oz_combine4(v, vh);
-          }
-          {
-            uint32_t v[4][8];
+              for (int dd = 0; dd < 4; dd++)
+                oz_tmem_load8(ta + (uint32_t)((4 + dd) * kOzQ), v[dd]);
+              oz_tmem_wait();
 #pragma unroll
-            for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)((4 + dd) * kOzQ), v[dd]);
-            oz_tmem_wait();
-            oz_combine4(v, vl);
-          }
-          asm volatile("tcgen05.fence::before_thread_sync;");
-          __syncwarp();
-          if (lane == 0) oz_arrive(smem_u32(&acc_empty[b]));
-#pragma unroll
-          for (int jj = 0; jj < 8; jj++) {
-            const long long w = (long long)((unsigned long long)vh[jj] << 20) + ((vl[jj] + 128) >> 8);
-            const int e = eA + M.eB[kOzQ * j + c8 + jj] - 55;
-            val[jj] = oz_to_double(OWNER ? w : -w, e);
-          }
-        }
-        // scatter this thread's row of the quarter (val holds -U for the atomics)
-        if (gi < u) {
-          const int kb = kOzQ * j + c8;
-          if (OWNER) {
-            double* U = M.ustage;
-#pragma unroll
-            for (int jj = 0; jj < 8; jj++) {
-              const int gk = k0 + kb + jj;
-              if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = val[jj];
+              for (int jj = 0; jj < 8; jj++)
+                w[jj] = oz_low(oz_fbits(v[0][jj]), oz_fbits(v[1][jj]), oz_fbits(v[2][jj]),
+                               oz_fbits(v[3][jj]));
             }
-          } else {
+            {
+              uint32_t v[4][8];
+#pragma unroll
+              for (int dd = 0; dd < 4; dd++) oz_tmem_load8(ta + (uint32_t)(dd * kOzQ), v[dd]);
+              oz_tmem_wait();
+#pragma unroll
+              for (int jj = 0; jj < 8; jj++)
+                w[jj] = (unsigned long long)oz_high(w[jj], oz_fbits(v[0][jj]),
+                                                    oz_fbits(v[1][jj]), oz_fbits(v[2][jj]),
+                                                    oz_fbits(v[3][jj]));
+            }
+            if (c == 1) {  // the warp's last reads of this set
+              asm volatile("tcgen05.fence::before_thread_sync;");
+              __syncwarp();
+              if (lane == 0) oz_arrive(smem_u32(&acc_empty[b]));
+            }
+#pragma unroll
+            for (int jj = 0; jj < 8; jj++)  // -U for the atomics, U for the staging buffer
+              val[jj] = oz_to_double<!OWNER>((long long)w[jj], eA + M.eB[kb + jj]);
+          } else if (c == 1) {
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) oz_arrive(smem_u32(&acc_empty[b]));
+          }
+          if (dead) continue;
+          // scatter this thread's row of the chunk
+          if (OWNER) {
+            if (gi < u) {
+              double* U = M.ustage;
+#pragma unroll
+              for (int jj = 0; jj < 8; jj++) {
+                const int gk = gk0 + jj;
+                if (gk < u && gk <= gi) U[(int64_t)gk * u + gi] = val[jj];
+              }
+            }
+          } else if (r0w + 31 < u && gk0 + 7 < u && gk0 + 7 <= r0w &&
+                     M.run[kb] == M.run[kb + 7]) {
+            // warp-uniform fast path: every entry live, one target run for all 8 columns
+            const int r = M.run[kb];
+            const int p = r < kOzMaxRuns ? M.rp[r][i] : M.relmap[M.rb[r] + gi];
+            if (p >= 0) {
+#pragma unroll
+              for (int jj = 0; jj < 8; jj++) atomicAdd(M.cp[kb + jj] + p, val[jj]);
+            }
+          } else if (gi < u) {
             // the relative row changes only with the run, which is the same for every lane
             int rprev = -1, p = -1;
 #pragma unroll
@@ -634,6 +711,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         }
       }
       if (stop) break;
+      q0 += nq;
       __syncwarp();
       if (lane == 0) oz_arrive(smem_u32(&meta_empty[buf]));
     }
