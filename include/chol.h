@@ -381,6 +381,17 @@ double chol_server_clock(chol_server* srv);
 /* Stops the slots (requests still queued are dropped) and frees the server. */
 void chol_server_destroy(chol_server* srv);
 
+/* Test hook for the failure path of the bounded device waits (not a tuning knob).  Every wait
+ * inside the 128 x 128 tensor-core Schur kernels gives up after 2^31 SM clock cycles (about a
+ * second; a working wait lasts microseconds).  With cycles > 0 the kernels' consumer warps
+ * wait, for at most that many cycles, on a barrier that nothing completes (standing in for an
+ * accumulator that never finishes), then give up: the kernel's other waits expire in turn,
+ * each role waits (bounded) for its own copies and MMAs in flight, the tensor memory is
+ * freed, every launch ends, later launches of the same factorization skip their work, and
+ * chol_factor_status reports CHOL_E_TIMEOUT; the context stays usable.  0 turns the hook off.
+ * CHOL_E_INVALID for cycles < 0. */
+int chol_set_device_wait(chol_ctx* ctx, long long cycles);
+
 /* ---- tracing ------------------------------------------------------------------------
  * Per-kernel-kind accounting of the device work a context enqueues: the launch count is
  * always kept; with profiling on, every launch is bracketed by CUDA events on the context

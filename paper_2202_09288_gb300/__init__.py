@@ -125,6 +125,7 @@ EXPORTS = {
     "chol_server_destroy": (None, [_P]),
     "chol_profile_enable": (_I, [_P, _I]),
     "chol_profile_only": (_I, [_P, C.c_char_p]),
+    "chol_set_device_wait": (_I, [_P, C.c_longlong]),
     "chol_profile_read": (_I, [_P, C.POINTER(chol_prof_entry), _I, C.POINTER(_I)]),
     "chol_profile_reset": (_I, [_P]),
 }
@@ -471,6 +472,11 @@ def chol_profile_enable(ctx, on: bool) -> None:
 def chol_profile_only(ctx, name=None) -> None:
     """Brackets only the launches of kernel kind `name` with events (None: every kind)."""
     _check(lib().chol_profile_only(ctx, name.encode() if name else None), "chol_profile_only")
+
+
+def chol_set_device_wait(ctx, cycles: int) -> None:
+    """Test hook: bound of the tensor-core Schur consumers' accumulator wait (0: default)."""
+    _check(lib().chol_set_device_wait(ctx, int(cycles)), "chol_set_device_wait")
 
 
 def chol_profile_read(ctx) -> dict:

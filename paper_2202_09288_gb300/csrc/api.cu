@@ -361,8 +361,10 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
       const bool tcc = oz && cls == chol::kTile128;
       const int pk = prof_schur_kind(cls, f32, tcc && !f32);
       prof_begin(c, pk);
-      if (tcc && f32) chol::launch_schur_tc(t, cnt, q + 2 + cls, sns, mats, owner, oz, oz_rows, st);
-      else if (tcc) chol::launch_schur_oz(t, cnt, q + 2 + cls, sns, mats, owner, oz, oz_rows, st);
+      if (tcc && f32)
+        chol::launch_schur_tc(t, cnt, q + 2 + cls, sns, mats, owner, oz, oz_rows, c->acc_wait, st);
+      else if (tcc)
+        chol::launch_schur_oz(t, cnt, q + 2 + cls, sns, mats, owner, oz, oz_rows, c->acc_wait, st);
       else chol::launch_schur(cls, t, cnt, q + 2 + cls, sns, mats, owner, f32, st);
       prof_end(c, pk, v.flops[kind][l], 0.0);
     }
@@ -1229,6 +1231,12 @@ int chol_refine(chol_ctx* c, chol_num* f, int64_t nrhs, const double* B, int64_t
 int chol_profile_enable(chol_ctx* c, int on) {
   if (!c) return CHOL_E_INVALID;
   c->prof_on = on != 0;
+  return CHOL_OK;
+}
+
+int chol_set_device_wait(chol_ctx* c, long long cycles) {
+  if (!c || cycles < 0) return CHOL_E_INVALID;
+  c->acc_wait = cycles;
   return CHOL_OK;
 }
 

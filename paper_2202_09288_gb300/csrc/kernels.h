@@ -31,9 +31,12 @@ void launch_build_relmap(int32_t ns, const int32_t* sn_start, const int64_t* sn_
 // zeroed scratch oz (oz_scratch_bytes(oz_rows)), then the tiles.
 void launch_tf32_split(const int4* tasks, int ntasks, const SnDev* sns, int max_width, void* oz,
                        int64_t oz_rows, cudaStream_t st);
+// acc_wait: 0 normally; > 0 is a test hook of the failure path: the consumer warps then wait
+// acc_wait SM clock cycles on a barrier that never completes (an accumulator that never
+// finishes) and give up.
 void launch_schur_tc(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                      const MatDev* mats, bool owner, const void* oz, int64_t oz_rows,
-                     cudaStream_t st);
+                     long long acc_wait, cudaStream_t st);
 int set_tc_kernel_attrs();
 // FP64 128 x 128 Schur tiles on the bf16 tensor cores by operand splitting, oz_kernels.cu:
 // per level, first the slices of every 128-tile supernode's L21 (kTaskOzSlice tasks), then
@@ -42,7 +45,7 @@ void launch_oz_slice(const int4* tasks, int ntasks, const SnDev* sns, void* oz, 
                      cudaStream_t st);
 void launch_schur_oz(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                      const MatDev* mats, bool owner, const void* oz, int64_t oz_rows,
-                     cudaStream_t st);
+                     long long acc_wait, cudaStream_t st);
 size_t oz_scratch_bytes(int64_t oz_rows);
 int set_oz_kernel_attrs();
 

@@ -22,7 +22,8 @@
 //               int64 -> double conversion) and scatter it into the ancestors with FP64
 //               atomics (or write the owner staging buffer) while the tensor cores compute
 //               the next quarter; metadata warps prepare each task's targets one task ahead.
-// Every wait is bounded: after kOzSpinLimit polls the kernel records a timeout in err[3],
+// Every wait is bounded in time (kOzWaitCycles SM clock cycles, about a second): then the
+// kernel records a timeout in err[3],
 // waits (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -55,7 +56,10 @@ constexpr int kOzSetCols = kOzSlices * kOzQ;               // 256: TMEM columns 
 constexpr uint32_t kOzABytes = kOzSlices * kOzASlice;      // 128 KB
 constexpr size_t kOzSmem = 1024 + kOzABytes + 2 * kOzQBytes;  // + alignment slack
 constexpr uint32_t kOzTmemCols = 2 * kOzSetCols;          // 512: two sets of 8 diagonals
-constexpr long long kOzSpinLimit = 1ll << 24;
+// Bound of every wait in SM clock cycles (~1 s at 2 GHz; the waits of a working launch last
+// microseconds).  Counted with clock64(), not in polls: a poll of mbarrier.try_wait may suspend
+// the thread for a hardware-defined time.
+constexpr long long kOzWaitCycles = 1ll << 31;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -80,8 +84,10 @@ __device__ __forceinline__ uint32_t oz_idesc(int N) {
          ((uint32_t)(kOzM >> 4) << 24);
 }
 
-__device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kOzSpinLimit; it++) {
+__device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity,
+                                        long long limit = kOzWaitCycles) {
+  const long long t0 = clock64();
+  for (;;) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -90,8 +96,8 @@ __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (clock64() - t0 > limit) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ void oz_expect(uint32_t bar, uint32_t bytes) {
@@ -329,7 +335,7 @@ template <bool OWNER>
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_schur_oz(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                const SnDev* __restrict__ sns, const MatDev* __restrict__ mats,
-               const uint8_t* __restrict__ oz, int64_t oz_rows) {
+               const uint8_t* __restrict__ oz, int64_t oz_rows, long long acc_wait) {
   extern __shared__ __align__(1024) unsigned char oz_sm[];
   unsigned char* A =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(oz_sm) + 1023) & ~uintptr_t(1023));
@@ -340,9 +346,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t meta_full[2], meta_empty[2];
   __shared__ OzMeta meta[2];
+  __shared__ __align__(8) uint64_t never;  // test hook: a barrier nothing completes
   __shared__ int s_mtq;  // the metadata warps' next task (or ntasks: stop)
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // a launch of an earlier level of this factorization already gave up on a wait: its
+  // updates are missing and the factorization is reported failed, so skip the work (before
+  // any barrier or tensor memory is set up); every thread reads the same word
+  if (ntasks > 0 && *(volatile unsigned long long*)(mats[sns[tasks[0].x].mat].err + 3) != 0) return;
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
   const int32_t* exps = reinterpret_cast<const int32_t*>(oz + kOzSlices * stride);
 
@@ -355,6 +366,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   if (tid == 0) {
     s_fail = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&a_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&never)));
     for (int i = 0; i < 2; i++) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&b_full[i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[i])));
@@ -618,7 +630,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         const long long q = q0 + j;
         if ((int)(q & 1) != grp) continue;
         const int b = grp;
-        if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&acc_full[b]), (uint32_t)((q >> 1) & 1)))) {
+        // acc_wait > 0 (a test hook): wait that long on a barrier that never completes instead,
+        // standing in for an accumulator that never finishes
+        const bool got = acc_wait > 0 ? oz_wait(smem_u32(&never), 0u, acc_wait)
+                                      : oz_wait(smem_u32(&acc_full[b]), (uint32_t)((q >> 1) & 1));
+        if (!__all_sync(0xffffffffu, got)) {
           s_fail = 1;
           stop = true;
           break;
@@ -734,7 +750,7 @@ void launch_oz_slice(const int4* tasks, int ntasks, const SnDev* sns, void* oz, 
 
 void launch_schur_oz(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                      const MatDev* mats, bool owner, const void* oz, int64_t oz_rows,
-                     cudaStream_t st) {
+                     long long acc_wait, cudaStream_t st) {
   if (ntasks <= 0) return;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -742,9 +758,11 @@ void launch_schur_oz(const int4* tasks, int ntasks, int* queue, const SnDev* sns
   const int grid = ntasks < sms ? ntasks : sms;  // one resident CTA per SM, tasks by queue
   const uint8_t* z = static_cast<const uint8_t*>(oz);
   if (owner)
-    k_schur_oz<true><<<grid, kOzThreads, kOzSmem, st>>>(tasks, ntasks, queue, sns, mats, z, oz_rows);
+    k_schur_oz<true><<<grid, kOzThreads, kOzSmem, st>>>(tasks, ntasks, queue, sns, mats, z, oz_rows,
+                                                       acc_wait);
   else
-    k_schur_oz<false><<<grid, kOzThreads, kOzSmem, st>>>(tasks, ntasks, queue, sns, mats, z, oz_rows);
+    k_schur_oz<false><<<grid, kOzThreads, kOzSmem, st>>>(tasks, ntasks, queue, sns, mats, z,
+                                                        oz_rows, acc_wait);
 }
 
 size_t oz_scratch_bytes(int64_t oz_rows) {

@@ -49,6 +49,7 @@ struct chol_ctx {
   cudaMemPool_t pool = nullptr;
   size_t held = 0;
   bool attrs_set = false;
+  long long acc_wait = 0;  // tensor-core Schur consumers' accumulator wait bound (0: default)
   // tracing
   bool prof_on = false;
   int prof_only = -1;  // kind whose launches alone are bracketed (-1: every kind)

@@ -19,7 +19,8 @@
 //                 MMAs, metadata and the scatter of different tasks overlap through
 //                 mbarriers: stage full/empty, accumulator full/empty, metadata full/empty,
 //                 and a ring that hands the task sequence to the consumers.
-// Every wait is bounded: after kTfSpinLimit polls the thread records a timeout in err[3]
+// Every wait is bounded in time (kTfWaitCycles SM clock cycles, about a second): then the
+// thread records a timeout in err[3]
 // and stops; its partners then time out as well, waits for copies and MMAs in flight are
 // bounded too, and the tensor memory is freed before the kernel returns.
 #include <cuda_runtime.h>
@@ -47,7 +48,9 @@ constexpr int kTfMetaThreads = 128;                // 4 warps: per-task column m
 constexpr int kTfThreads = kTfConsumers + 32 + kTfMetaThreads;  // + the producer warp
 constexpr int kTfRing = 16;
 constexpr int kTfMaxRuns = 16;
-constexpr long long kTfSpinLimit = 1ll << 24;
+// Bound of every wait in SM clock cycles (~1 s at 2 GHz), counted with clock64(): a poll of
+// mbarrier.try_wait may suspend the thread for a hardware-defined time.
+constexpr long long kTfWaitCycles = 1ll << 31;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -78,8 +81,10 @@ __device__ __forceinline__ uint32_t tf_idesc() {
          ((uint32_t)(kTfM >> 4) << 24);
 }
 
-__device__ __forceinline__ bool tf_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kTfSpinLimit; it++) {
+__device__ __forceinline__ bool tf_wait(uint32_t bar, uint32_t parity,
+                                        long long limit = kTfWaitCycles) {
+  const long long t0 = clock64();
+  for (;;) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -88,8 +93,8 @@ __device__ __forceinline__ bool tf_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (clock64() - t0 > limit) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ void tf_arrive(uint32_t bar) {
@@ -205,7 +210,7 @@ template <bool OWNER>
 __global__ void __launch_bounds__(kTfThreads, 1)
     k_schur_tf32(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                  const SnDev* __restrict__ sns, const MatDev* __restrict__ mats,
-                 const uint8_t* __restrict__ oz, int64_t oz_rows) {
+                 const uint8_t* __restrict__ oz, int64_t oz_rows, long long acc_wait) {
   extern __shared__ __align__(1024) unsigned char tf_sm[];
   unsigned char* stage_base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tf_sm) + 1023) & ~uintptr_t(1023));
@@ -218,7 +223,12 @@ __global__ void __launch_bounds__(kTfThreads, 1)
   __shared__ TfMeta meta[2];
   __shared__ int s_mtq;  // the metadata warps' next task (or ntasks: stop)
   __shared__ int s_fail;
+  __shared__ __align__(8) uint64_t never;  // test hook: a barrier nothing completes
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // a launch of an earlier level of this factorization already gave up on a wait: its
+  // updates are missing and the factorization is reported failed, so skip the work (before
+  // any barrier or tensor memory is set up); every thread reads the same word
+  if (ntasks > 0 && *(volatile unsigned long long*)(mats[sns[tasks[0].x].mat].err + 3) != 0) return;
   const size_t stride = (size_t)oz_rows * kOzRowBytes;
 
   if (warp == 0) {
@@ -246,6 +256,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&meta_empty[i])),
                    "r"(kTfConsumers / 32));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&never)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -448,7 +459,10 @@ __global__ void __launch_bounds__(kTfThreads, 1)
       const TfMeta& M = meta[buf];
       const int acc = ord % kTfSlots;
       if (!__all_sync(0xffffffffu, tf_wait(smem_u32(&meta_full[buf]), (uint32_t)((ord >> 1) & 1)) &&
-                                       tf_wait(smem_u32(&acc_full[acc]), (uint32_t)((ord / kTfSlots) & 1)))) {
+                                       (acc_wait > 0  // test hook: a barrier never completed
+                                            ? tf_wait(smem_u32(&never), 0u, acc_wait)
+                                            : tf_wait(smem_u32(&acc_full[acc]),
+                                                      (uint32_t)((ord / kTfSlots) & 1))))) {
         s_fail = 1;
         break;
       }
@@ -508,7 +522,7 @@ void launch_tf32_split(const int4* tasks, int ntasks, const SnDev* sns, int max_
 
 void launch_schur_tc(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                      const MatDev* mats, bool owner, const void* oz, int64_t oz_rows,
-                     cudaStream_t st) {
+                     long long acc_wait, cudaStream_t st) {
   if (ntasks <= 0) return;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -516,9 +530,11 @@ void launch_schur_tc(const int4* tasks, int ntasks, int* queue, const SnDev* sns
   const int grid = ntasks < sms ? ntasks : sms;  // one resident CTA per SM, tasks by queue
   const uint8_t* z = static_cast<const uint8_t*>(oz);
   if (owner)
-    k_schur_tf32<true><<<grid, kTfThreads, kTfSmem, st>>>(tasks, ntasks, queue, sns, mats, z, oz_rows);
+    k_schur_tf32<true><<<grid, kTfThreads, kTfSmem, st>>>(tasks, ntasks, queue, sns, mats, z,
+                                                         oz_rows, acc_wait);
   else
-    k_schur_tf32<false><<<grid, kTfThreads, kTfSmem, st>>>(tasks, ntasks, queue, sns, mats, z, oz_rows);
+    k_schur_tf32<false><<<grid, kTfThreads, kTfSmem, st>>>(tasks, ntasks, queue, sns, mats, z,
+                                                          oz_rows, acc_wait);
 }
 
 int set_tc_kernel_attrs() {
