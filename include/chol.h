@@ -222,6 +222,27 @@ int chol_refine(chol_ctx* ctx, chol_num* num, int64_t nrhs, const double* B, int
                 double* X, int64_t ldx, int where, double tol, int maxit,
                 chol_refine_info* info);
 
+/* Iterative refinement whose correction equations are solved by GMRES (GMRES-IR; not in the
+ * paper, whose factor is FP64 only): each step forms the FP64 residual r = b - A x with the
+ * original A and solves A d = r by flexible GMRES(restart) right-preconditioned with the
+ * factor (z = M^-1 v by the factor's triangular solves: an FP32 factor of the equilibrated
+ * matrix for CHOL_MIXED), orthonormalizing the Krylov basis in FP64 (classical Gram-Schmidt
+ * with one reorthogonalization), until the correction residual fell by 1e-6, then x += d.
+ * Plain refinement (chol_refine) contracts the error by about kappa(A) times the factor's
+ * accuracy per step and stalls for kappa(A) beyond ~1e7 with an FP32 factor; this converges
+ * for kappa(A) up to about the inverse square of the factor's accuracy.  Same arguments as
+ * chol_refine plus restart (Krylov vectors per GMRES cycle, 1..64; 0 = 30); maxit bounds the
+ * GMRES iterations of a right-hand side (0 = 10 restart).  Stops when the relative residual
+ * meets tol, or stalls when two refinement steps in a row fail to halve the residual or
+ * after maxit iterations; a stalled CHOL_MIXED factor falls back once to an FP64 factor of
+ * the same values (kept with the factor, as in chol_refine).  info->iterations counts GMRES
+ * iterations (each one factor solve and one SpMV).  Right-hand sides are done one after
+ * another; the call synchronizes.  Device workspace: (2 restart + 1) n doubles, kept with
+ * the factor.  Returns CHOL_OK, CHOL_E_STALL or an error. */
+int chol_refine_gmres(chol_ctx* ctx, chol_num* num, int64_t nrhs, const double* B, int64_t ldb,
+                      double* X, int64_t ldx, int where, double tol, int restart, int maxit,
+                      chol_refine_info* info);
+
 /* Device-pointer solve that allocates nothing (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they solve, e.g. code
  * capturing a stream in global capture mode, where cudaMalloc is an error, or a runtime

@@ -105,6 +105,8 @@ EXPORTS = {
     "chol_solve": (_I, [_P, _P, _I64, _P, _I64, _P, _I64, _I]),
     "chol_refine": (_I, [_P, _P, _I64, _P, _I64, _P, _I64, _I, C.c_double, _I,
                          C.POINTER(chol_refine_info)]),
+    "chol_refine_gmres": (_I, [_P, _P, _I64, _P, _I64, _P, _I64, _I, C.c_double, _I, _I,
+                               C.POINTER(chol_refine_info)]),
     "chol_solve_noalloc": (_I, [_P, _P, _I64, _P, _I64, _P, _I64]),
     "chol_noalloc_scratch_bytes": (C.c_size_t, []),
     "chol_batch_create": (_I, [_P, _I, C.POINTER(_P), C.POINTER(_P)]),
@@ -374,6 +376,29 @@ def chol_refine(ctx, num, B, X=None, tol=1e-12, maxit=10, check=True):
     return out, d
 
 
+def chol_refine_gmres(ctx, num, B, X=None, tol=1e-12, restart=0, maxit=0, check=True):
+    """GMRES-based iterative refinement (FGMRES preconditioned with the factor) to
+    ||b - A x||_inf / (||A||_inf ||x||_inf) <= tol; arguments and result as chol_refine."""
+    info = chol_refine_info()
+    if isinstance(B, np.ndarray):
+        B2 = np.asfortranarray(B.reshape(B.shape[0], -1), dtype=np.float64)
+        n, k = B2.shape
+        X2 = np.zeros((n, k), dtype=np.float64, order="F")
+        rc = lib().chol_refine_gmres(ctx, num, k, B2.ctypes.data, n, X2.ctypes.data, n,
+                                     CHOL_HOST, tol, restart, maxit, C.byref(info))
+        out = X2.reshape(B.shape) if B.ndim == 1 else X2
+    else:
+        out = B.new_empty(B.shape) if X is None else X
+        k, n = _check_device_pair(ctx, B, out, "chol_refine_gmres")
+        rc = lib().chol_refine_gmres(ctx, num, k, B.data_ptr(), n, out.data_ptr(), n,
+                                     CHOL_DEVICE, tol, restart, maxit, C.byref(info))
+    d = {"iterations": info.iterations, "fell_back": bool(info.fell_back),
+         "residual": info.residual, "pivot_redos": info.pivot_redos, "status": rc}
+    if rc != CHOL_OK and (check or rc != CHOL_E_STALL):
+        raise CholError(rc, "chol_refine_gmres")
+    return out, d
+
+
 def chol_solve_noalloc(ctx, num, B, X):
     """Device-pointer solve without any device allocation (torch CUDA tensors laid out as
     in chol_solve: shape (k, n) contiguous, or (n,) for one right-hand side)."""
@@ -569,6 +594,9 @@ class Factor:
 
     def refine(self, B, X=None, tol=1e-12, maxit=10, check=True):
         return chol_refine(self.ctx.handle, self.handle, B, X, tol, maxit, check)
+
+    def refine_gmres(self, B, X=None, tol=1e-12, restart=0, maxit=0, check=True):
+        return chol_refine_gmres(self.ctx.handle, self.handle, B, X, tol, restart, maxit, check)
 
     def __del__(self):
         try:

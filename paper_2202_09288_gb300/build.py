@@ -14,7 +14,8 @@ OUT = os.path.join(HERE, "libchol.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["analyze.cpp", "api.cu", "factor_kernels.cu", "tc_kernels.cu", "oz_kernels.cu",
-           "solve_kernels.cu", "noalloc.cu", "refine_kernels.cu", "batch.cu", "serve.cu"]
+           "solve_kernels.cu", "noalloc.cu", "refine_kernels.cu", "gmres.cu", "batch.cu",
+           "serve.cu"]
 
 
 def nvcc() -> str:

@@ -561,7 +561,8 @@ void free_num_buffers(chol_num* f) {
   if (!c) return;
   void* ptrs[] = {f->L, f->d_sn, f->d_mat, f->d_err, f->d_ctr, f->d_vals, f->d_stage, f->d_scale,
                   f->d_y, f->d_w, f->d_bx, f->d_part, f->d_fstage, f->d_rr, f->d_rd,
-                  f->d_rb, f->d_norm, f->d_oz};
+                  f->d_rb, f->d_norm, f->d_oz, f->d_gv, f->d_gz, f->d_gw, f->d_gpart,
+                  f->d_gh};
   for (void* p : ptrs) dev_free(c, p);
   c->nums.erase(f);
   f->ctx = nullptr;

@@ -130,6 +130,13 @@ struct chol_num {
   unsigned long long* d_norm = nullptr;  // per-column max |r|, max |x|, and ||A||_inf
   double anorm = -1.0;         // ||A||_inf of the current values (-1: not computed)
   chol_num* fb = nullptr;      // FP64 factor made when refinement of a mixed one stalls
+  // flexible-GMRES refinement workspace (chol_refine_gmres), grown on demand
+  int gm_cap = 0;              // Krylov vectors the workspace holds (restart length)
+  double* d_gv = nullptr;      // V: n x (cap + 1), orthonormal basis
+  double* d_gz = nullptr;      // Z: n x cap, preconditioned basis vectors
+  double* d_gw = nullptr;      // w: n
+  double* d_gpart = nullptr;   // dot-product partial sums
+  double* d_gh = nullptr;      // dot products / coefficients of one step
 };
 
 
@@ -178,6 +185,13 @@ const int4* task_ptr(const chol_sym* s, int kind, int32_t level, int* count);
 int ensure_uploaded(chol_ctx* c, chol_sym* s);
 int ensure_attrs(chol_ctx* c);
 int ensure_solve_ws(chol_num* f, int64_t nrhs);
+int ensure_refine_ws(chol_num* f, int64_t k);
+// ||A||_inf of f's values, computed once per set of values.
+int compute_anorm(chol_num* f);
+// R = B - A X into f's residual buffer (k <= 32 columns); *rel = max_c ||r_c||_inf /
+// (||A||_inf ||x_c||_inf), *rmax = max_c ||r_c||_inf (synchronizes).
+int residual_norms(chol_num* f, int k, const double* B, int64_t ldb, const double* X,
+                   int64_t ldx, double* rel, double* rmax);
 int enqueue_solve(chol_num* f, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx);
 // Allocates a factor of sym and copies vals into it; with factor_now it also enqueues the
 // factorization (otherwise a batch will factor it).

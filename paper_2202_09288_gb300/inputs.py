@@ -194,6 +194,27 @@ def diffusion_3d_7pt(k: int, seed: int, sigma: float = 1.5) -> SpdMatrix:
     return SpdMatrix(n, colptr, ri, v, grid=(k, k, k), name=f"diff3d7_{k}_s{sigma}")
 
 
+def floating_diffusion_3d_7pt(k: int, seed: int, sigma: float = 1.5,
+                              delta: float = 1e-10) -> SpdMatrix:
+    """The diffusion operator of diffusion_3d_7pt without its boundary terms (a floating,
+    Neumann body: every row sums to zero), plus delta times its diagonal.  SPD; its smallest
+    eigenvalue is ~delta relative to the largest, also after diagonal scaling, so the
+    condition number of diag(A)^-1/2 A diag(A)^-1/2 is ~2 / delta."""
+    a = diffusion_3d_7pt(k, seed, sigma)
+    vals = a.vals.copy()
+    first = a.colptr[:-1]
+    off = np.ones(vals.size, bool)
+    off[first] = False
+    cols = np.repeat(np.arange(a.n), np.diff(a.colptr))
+    # sum of the faces of every node: -(off-diagonal row sum of the full symmetric matrix)
+    faces = np.zeros(a.n)
+    np.add.at(faces, cols[off], -vals[off])
+    np.add.at(faces, a.rowind[off], -vals[off])
+    vals[first] = faces * (1.0 + delta)
+    return SpdMatrix(a.n, a.colptr, a.rowind, vals, grid=a.grid,
+                     name=f"floatdiff_{k}_s{sigma}_d{delta:g}")
+
+
 def _offsets27_forward():
     """The 13 neighbour offsets (dx, dy, dz) that point to a larger node index."""
     out = []
@@ -330,7 +351,9 @@ def workload(name: str) -> tuple[SpdMatrix, np.ndarray]:
     diff3d7_96    3D 7-point log-normal (sigma 1.5) diffusion, 96^3 (n = 884,736), seed 3
     st27x3_80     3D 27-point, 3 dofs/node, 80^3 (n = 1,536,000), seed 5
     Scaled-down members of the same families: ``st27x3_<k>``, ``diff3d7_<k>``,
-    ``lap2d_<k>``, ``lap3d_<k>``.
+    ``lap2d_<k>``, ``lap3d_<k>``; ``floatdiff_<k>``: the floating diffusion operator
+    (floating_diffusion_3d_7pt, sigma 1.5, delta 1e-10, seed 3), condition ~2e10 after
+    diagonal scaling.
     """
     fam, k = name.rsplit("_", 1)
     k = int(k)
@@ -342,6 +365,8 @@ def workload(name: str) -> tuple[SpdMatrix, np.ndarray]:
         a = stencil27_3dof(k, seed={48: 2, 80: 5}.get(k, 2))
     elif fam == "diff3d7":
         a = diffusion_3d_7pt(k, seed=3)
+    elif fam == "floatdiff":
+        a = floating_diffusion_3d_7pt(k, seed=3)
     else:
         raise ValueError(f"unknown workload {name}")
     return a, nested_dissection(a.grid, a.dofs)

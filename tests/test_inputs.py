@@ -72,3 +72,20 @@ def test_nd_dofs_consecutive():
     p = inputs.nested_dissection((4, 4, 4), 3, leaf=8)
     assert np.array_equal(p[1::3] - p[0::3], np.ones(64, np.int32))
     assert np.all(p[0::3] % 3 == 0)
+
+
+def test_floating_diffusion_is_spd_and_ill_conditioned():
+    """Rows of the floating operator sum to delta times the diagonal over (1 + delta); the
+    off-diagonal entries are those of the Dirichlet operator; after diagonal scaling the
+    condition number is ~2 / delta (eigenvalues of a small case)."""
+    k = 6
+    F = inputs.floating_diffusion_3d_7pt(k, 3, 1.5, 1e-6).to_scipy_full().toarray()
+    D = inputs.diffusion_3d_7pt(k, 3, 1.5).to_scipy_full().toarray()
+    off = ~np.eye(F.shape[0], dtype=bool)
+    assert np.array_equal(F[off], D[off])
+    d = np.diag(F)
+    np.testing.assert_allclose(F.sum(axis=1), d * 1e-6 / (1 + 1e-6), rtol=1e-6, atol=1e-12)
+    s = 1 / np.sqrt(d)
+    ev = np.linalg.eigvalsh(F * s[:, None] * s[None, :])
+    assert ev[0] > 0
+    assert 0.5 * 2e6 < ev[-1] / ev[0] < 2 * 2e6
