@@ -334,6 +334,28 @@ int chol_sym_granularity(const chol_sym* sym, int* rule, int32_t* D, int32_t* ns
  * hold *count entries (the value a first call returned). */
 int chol_sym_schur_tiles(const chol_sym* sym, int32_t* s, int32_t* i0, int32_t* k0,
                          int32_t* tile, int64_t* count);
+/* ---- subtree-to-device partition (multi-GPU layout; measured on one GPU only) ----------
+ * The supernodal elimination tree splits into independent subtrees: supernodes of
+ * different subtrees never update one another (Sec. 3, Fig. 1), so each subtree can be
+ * factored on its own device with no communication, and only the supernodes above them
+ * (the top separators) need the update blocks of several devices, summed into the device
+ * that owns the top part (the layer idea of Geist and Ng that the paper's related work
+ * cites).  chol_partition_tree partitions a forest of nv vertices (parent[v] = -1 at a root,
+ * work[v] >= 0): starting from the roots, the heaviest subtree that has children is replaced
+ * by its children (its own vertex joins the top part) until the current subtrees, dealt
+ * largest first to the least loaded of nparts parts, give every part at most (1 + tol) of
+ * an even share -- or only single vertices remain.  owner[v] (nv entries) receives the part
+ * 0 .. nparts-1 of v's subtree, or -1 for the top part; *imbalance (may be NULL) the largest
+ * part's work over the mean.  CHOL_E_INVALID on a malformed forest (cycle, parent out of
+ * range), negative work, nparts < 1 or tol < 0. */
+int chol_partition_tree(int32_t nv, const int32_t* parent, const double* work, int nparts,
+                        double tol, int32_t* owner, double* imbalance);
+/* The same on sym's supernodal elimination tree with work = the flops of each supernode's
+ * columns (sum of c_j^2): owner has nsuper entries; *top_flops (may be NULL) receives the
+ * work left to the top part. */
+int chol_sym_partition(const chol_sym* sym, int nparts, double tol, int32_t* owner,
+                       double* imbalance, double* top_flops);
+
 /* Autotuner: times refactorizations of num (reps each) under candidate tile policies by
  * coordinate descent over the five thresholds, keeps the fastest in num's analysis,
  * stores it in *best (and its time in *best_ms) and leaves num factored under it. */

@@ -118,6 +118,10 @@ EXPORTS = {
     "chol_opt_d": (_I, [C.c_int64, C.c_int32, _P, C.POINTER(C.c_int32)]),
     "chol_sym_granularity": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "chol_sym_schur_tiles": (_I, [_P, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
+    "chol_partition_tree": (_I, [C.c_int32, _P, _P, _I, C.c_double, _P,
+                                 C.POINTER(C.c_double)]),
+    "chol_sym_partition": (_I, [_P, _I, C.c_double, _P, C.POINTER(C.c_double),
+                                C.POINTER(C.c_double)]),
     "chol_default_server_opts": (None, [C.POINTER(chol_server_opts)]),
     "chol_server_create": (_I, [C.POINTER(chol_server_opts), C.POINTER(_P)]),
     "chol_submit": (_I, [_P, C.POINTER(chol_request), C.POINTER(C.c_uint64)]),
@@ -481,6 +485,28 @@ def chol_sym_schur_tiles(sym) -> dict:
                                              for k in ("s", "i0", "k0", "tile")],
                                       C.byref(cnt)), "chol_sym_schur_tiles")
     return out
+
+
+def chol_partition_tree(parent, work, nparts, tol=0.05):
+    """(owner, imbalance): subtree-to-device partition of a forest (see chol.h)."""
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    work = np.ascontiguousarray(work, dtype=np.float64)
+    owner = np.zeros(parent.size, dtype=np.int32)
+    imb = C.c_double()
+    _check(lib().chol_partition_tree(parent.size, parent.ctypes.data, work.ctypes.data,
+                                     int(nparts), float(tol), owner.ctypes.data, C.byref(imb)),
+           "chol_partition_tree")
+    return owner, imb.value
+
+
+def chol_sym_partition(sym, nparts, tol=0.05):
+    """(owner per supernode, imbalance, top flops) of sym's supernodal tree."""
+    ns = chol_sym_info(sym)["nsuper"]
+    owner = np.zeros(ns, dtype=np.int32)
+    imb, top = C.c_double(), C.c_double()
+    _check(lib().chol_sym_partition(sym, int(nparts), float(tol), owner.ctypes.data,
+                                    C.byref(imb), C.byref(top)), "chol_sym_partition")
+    return owner, imb.value, top.value
 
 
 def chol_autotune(ctx, num, reps=1) -> tuple[dict, float]:

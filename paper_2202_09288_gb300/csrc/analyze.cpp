@@ -504,6 +504,84 @@ int32_t opt_d_threshold(int64_t n, int32_t nsuper, const int32_t* counts) {
   return 0;
 }
 
+double partition_tree(int32_t nv, const int32_t* parent, const double* work, int nparts,
+                      double tol, int32_t* owner) {
+  // Subtree work W[v] = work[v] + the work of its descendants, children lists, roots.
+  std::vector<double> W(work, work + nv);
+  std::vector<std::vector<int32_t>> kids(nv);
+  std::vector<int32_t> roots;
+  std::vector<int32_t> order;  // vertices with every child before its parent
+  {
+    std::vector<int32_t> nkid(nv, 0), stack;
+    for (int32_t v = 0; v < nv; v++) {
+      if (parent[v] >= 0) {
+        kids[parent[v]].push_back(v);
+        nkid[parent[v]]++;
+      } else {
+        roots.push_back(v);
+      }
+    }
+    for (int32_t v = 0; v < nv; v++)
+      if (nkid[v] == 0) stack.push_back(v);
+    while (!stack.empty()) {
+      const int32_t v = stack.back();
+      stack.pop_back();
+      order.push_back(v);
+      if (parent[v] >= 0 && --nkid[parent[v]] == 0) stack.push_back(parent[v]);
+    }
+  }
+  for (int32_t v : order)
+    if (parent[v] >= 0) W[parent[v]] += W[v];
+  // The layer: subtrees handed out whole.  Starting from the roots, the heaviest subtree
+  // that can be split is replaced by its children (its own vertex joins the top part, done
+  // after the exchange) until the layer's subtrees, dealt largest first to the least loaded
+  // part, are within (1 + tol) of an even share -- or nothing is left to split.
+  std::vector<int32_t> layer = roots;
+  std::vector<int32_t> top;
+  std::vector<int32_t> bin_of;
+  double imbalance = 1.0;
+  auto by_weight = [&](int32_t a, int32_t b) { return W[a] > W[b] || (W[a] == W[b] && a < b); };
+  for (;;) {
+    std::sort(layer.begin(), layer.end(), by_weight);
+    std::vector<double> load(nparts, 0.0);
+    bin_of.assign(layer.size(), 0);
+    double total = 0.0;
+    for (size_t i = 0; i < layer.size(); i++) {
+      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      load[b] += W[layer[i]];
+      bin_of[i] = b;
+      total += W[layer[i]];
+    }
+    const double mean = total / nparts, mx = *std::max_element(load.begin(), load.end());
+    imbalance = mean > 0.0 ? mx / mean : 1.0;
+    if ((int)layer.size() >= nparts && mx <= (1.0 + tol) * mean) break;
+    size_t h = layer.size();  // the heaviest subtree with children
+    for (size_t i = 0; i < layer.size(); i++)
+      if (!kids[layer[i]].empty()) {
+        h = i;
+        break;
+      }
+    if (h == layer.size()) break;  // only single vertices left: the best this tree allows
+    const int32_t v = layer[h];
+    top.push_back(v);
+    layer.erase(layer.begin() + (std::ptrdiff_t)h);
+    layer.insert(layer.end(), kids[v].begin(), kids[v].end());
+  }
+  // owners: the top part -1, every layer subtree its part
+  std::fill(owner, owner + nv, -1);
+  std::vector<int32_t> stack;
+  for (size_t i = 0; i < layer.size(); i++) {
+    stack.push_back(layer[i]);
+    while (!stack.empty()) {
+      const int32_t v = stack.back();
+      stack.pop_back();
+      owner[v] = bin_of[i];
+      for (int32_t c : kids[v]) stack.push_back(c);
+    }
+  }
+  return imbalance;
+}
+
 void build_schur_tasks(Sym* S, const TilePolicy& policy) {
   S->policy = policy;
   const int kinds[] = {kTaskSchur64, kTaskSchur32, kTaskSchur16, kTaskSchur128, kTaskOzSlice};

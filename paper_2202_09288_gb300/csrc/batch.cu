@@ -321,6 +321,64 @@ int chol_opt_d(int64_t n, int32_t nsuper, const int32_t* counts, int32_t* D) {
   return CHOL_OK;
 }
 
+int chol_partition_tree(int32_t nv, const int32_t* parent, const double* work, int nparts,
+                        double tol, int32_t* owner, double* imbalance) {
+  if (nv < 0 || nparts < 1 || tol < 0 || (nv > 0 && (!parent || !work || !owner)))
+    return CHOL_E_INVALID;
+  for (int32_t v = 0; v < nv; v++)
+    if (parent[v] < -1 || parent[v] >= nv || parent[v] == v || !(work[v] >= 0.0))
+      return CHOL_E_INVALID;
+  // every vertex must reach a root (no cycles)
+  {
+    std::vector<int8_t> state(nv, 0);  // 0 unknown, 1 on the current path, 2 reaches a root
+    for (int32_t v = 0; v < nv; v++) {
+      std::vector<int32_t> path;
+      int32_t u = v;
+      while (u >= 0 && state[u] == 0) {
+        state[u] = 1;
+        path.push_back(u);
+        u = parent[u];
+      }
+      if (u >= 0 && state[u] == 1) return CHOL_E_INVALID;
+      for (int32_t w : path) state[w] = 2;
+    }
+  }
+  double imb = 1.0;
+  try {
+    imb = nv > 0 ? chol::partition_tree(nv, parent, work, nparts, tol, owner) : 1.0;
+  } catch (...) {
+    return CHOL_E_OOM;
+  }
+  if (imbalance) *imbalance = imb;
+  return CHOL_OK;
+}
+
+int chol_sym_partition(const chol_sym* sym, int nparts, double tol, int32_t* owner,
+                       double* imbalance, double* top_flops) {
+  if (!sym || nparts < 1 || tol < 0 || !owner) return CHOL_E_INVALID;
+  const chol::Sym& S = sym->S;
+  std::vector<double> work(S.ns, 0.0);
+  for (int32_t s = 0; s < S.ns; s++)
+    for (int32_t j = S.sn_start[s]; j < S.sn_start[s + 1]; j++)
+      work[s] += (double)S.colcount[j] * (double)S.colcount[j];
+  double imb = 1.0;
+  try {
+    imb = S.ns > 0 ? chol::partition_tree(S.ns, S.sn_parent.data(), work.data(), nparts, tol,
+                                          owner)
+                   : 1.0;
+  } catch (...) {
+    return CHOL_E_OOM;
+  }
+  if (imbalance) *imbalance = imb;
+  if (top_flops) {
+    double t = 0.0;
+    for (int32_t s = 0; s < S.ns; s++)
+      if (owner[s] < 0) t += work[s];
+    *top_flops = t;
+  }
+  return CHOL_OK;
+}
+
 int chol_sym_schur_tiles(const chol_sym* sym, int32_t* s, int32_t* i0, int32_t* k0,
                          int32_t* tile, int64_t* count) {
   if (!sym || !count) return CHOL_E_INVALID;

@@ -182,5 +182,9 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy);
 // Threshold D of OPT-D (Sec. 4.1, Algorithm 1) for nsuper outer tasks with counts[i] >= 0
 // inner tasks each, n the matrix size.
 int32_t opt_d_threshold(int64_t n, int32_t nsuper, const int32_t* counts);
+// Subtree-to-device partition of a forest (parent[v] = -1 at a root, work[v] >= 0): see
+// chol_partition_tree.  Returns the imbalance of the chosen layer (max part / mean part).
+double partition_tree(int32_t nv, const int32_t* parent, const double* work, int nparts,
+                      double tol, int32_t* owner);
 
 }  // namespace chol
