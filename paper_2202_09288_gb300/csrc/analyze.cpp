@@ -276,6 +276,7 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
   S->sn_m.assign(ns, 0);
   S->sn_rowptr.assign(ns + 1, 0);
   S->sn_valptr.assign(ns + 1, 0);
+  S->sn_dinvptr.assign(ns + 1, 0);
   S->rows.clear();
   S->max_width = S->max_rows = 0;
   S->flops_panel = 0.0;
@@ -289,12 +290,14 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
     S->rows.insert(S->rows.end(), frows.begin() + frp[f] + off, frows.begin() + frp[f + 1]);
     S->sn_rowptr[s + 1] = (int64_t)S->rows.size();
     S->sn_valptr[s + 1] = S->sn_valptr[s] + m * (int64_t)(b - a);
+    S->sn_dinvptr[s + 1] = S->sn_dinvptr[s] + (int64_t)(b - a) * (b - a);
     S->max_width = std::max<int64_t>(S->max_width, b - a);
     S->max_rows = std::max<int64_t>(S->max_rows, m);
     // the operations the panels really take: sum of c^2 over the padded columns
     for (int64_t k = 0; k < b - a; k++) S->flops_panel += (double)(m - k) * (double)(m - k);
   }
   S->l_storage = S->sn_valptr[ns];
+  S->l_dinv = S->sn_dinvptr[ns];
   // runs of each supernode's off-diagonal rows by target supernode (the relative map's
   // index; the map itself is built on the device)
   S->sn_run0.assign(ns + 1, 0);

@@ -377,6 +377,18 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
       }
     }
   }
+  // the inverses of all finished diagonal blocks, for the solves (supernodes of factors that
+  // keep them), in one launch over every POTRF task: nothing in the factorization needs
+  // them, and per level the top of the tree would serialize their n-step chains
+  {
+    const int64_t* o = v.off[chol::kTaskPotrf];
+    const int cnt = (int)(o[v.nlev] - o[0]);
+    if (cnt > 0) {
+      prof_begin(c, kProfDinv);
+      chol::launch_diag_inverse(v.d[chol::kTaskPotrf] + o[0], cnt, sns, f32, st);
+      prof_end(c, kProfDinv, 0.0, 0.0);
+    }
+  }
   CK(cudaGetLastError());
   return CHOL_OK;
 }
@@ -441,6 +453,7 @@ void fill_descriptors(const chol_num* f, int mat, int32_t sn_base, std::vector<S
     d.ustage = S.sn_ustage[s];
     d.run0 = S.sn_run0[s];
     d.nrun = S.sn_run0[s + 1] - S.sn_run0[s];
+    d.dinv = f->d_dinv ? (char*)f->d_dinv + (size_t)S.sn_dinvptr[s] * esz : nullptr;
   }
   md->col2sn = sym->dev.col2sn;
   md->run_a = sym->dev.run_a;
@@ -562,7 +575,7 @@ void free_num_buffers(chol_num* f) {
   void* ptrs[] = {f->L, f->d_sn, f->d_mat, f->d_err, f->d_ctr, f->d_vals, f->d_stage, f->d_scale,
                   f->d_y, f->d_w, f->d_bx, f->d_part, f->d_fstage, f->d_rr, f->d_rd,
                   f->d_rb, f->d_norm, f->d_oz, f->d_gv, f->d_gz, f->d_gw, f->d_gpart,
-                  f->d_gh};
+                  f->d_gh, f->d_dinv};
   for (void* p : ptrs) dev_free(c, p);
   c->nums.erase(f);
   f->ctx = nullptr;
@@ -595,7 +608,9 @@ int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int p
       (rc = dev_alloc(c, (void**)&f->d_vals, (size_t)S.nnz_a * 8)) ||
       (f32 && (rc = dev_alloc(c, (void**)&f->d_scale, (size_t)S.n * 8))) ||
       (assembly == CHOL_ASSEMBLY_OWNER &&
-       (rc = dev_alloc(c, (void**)&f->d_stage, (size_t)S.stage_elems * 8)))) {
+       (rc = dev_alloc(c, (void**)&f->d_stage, (size_t)S.stage_elems * 8))) ||
+      (S.max_width <= chol::kDinvMaxWidth &&
+       (rc = dev_alloc(c, &f->d_dinv, (size_t)S.l_dinv * esz)))) {
     free_num_buffers(f);
     delete f;
     return rc;
@@ -653,6 +668,7 @@ size_t factor_bytes(const chol_sym* sym, int precision, int assembly) {
   if (precision == CHOL_MIXED) b += (size_t)S.n * 8;
   if (assembly == CHOL_ASSEMBLY_OWNER) b += (size_t)S.stage_elems * 8;
   if (precision != CHOL_MIXED && S.oz_rows > 0) b += chol::oz_scratch_bytes(S.oz_rows);
+  if (S.max_width <= chol::kDinvMaxWidth) b += (size_t)S.l_dinv * esz;
   return b;
 }
 

@@ -60,6 +60,8 @@ struct alignas(16) SnDev {
   int32_t mat;          // index into the MatDev array
   int64_t ustage;       // owner assembly: offset of U_s in the level staging buffer (-1 none)
   int32_t run0, nrun;   // target runs of the off-diagonal rows (MatDev::run_a / run_base)
+  void* dinv;           // inverse of the diagonal block L11, n x n column-major (lower
+                        // triangle; the panel's precision), or null (not kept)
 };
 
 struct alignas(16) MatDev {
@@ -125,6 +127,7 @@ struct Sym {
   std::vector<int64_t> sn_rowptr;  // ns + 1 offsets into rows
   std::vector<int32_t> rows;
   std::vector<int64_t> sn_valptr;  // ns + 1 offsets into panel storage
+  std::vector<int64_t> sn_dinvptr; // ns + 1 offsets of the diagonal-block inverses (n_s^2 each)
   std::vector<int32_t> sn_parent, sn_level;
   std::vector<int32_t> col2sn;     // n
   std::vector<int64_t> amap;       // nnz_a: panel offset of every stored entry of A
@@ -162,6 +165,7 @@ struct Sym {
   double flops = 0.0;        // sum of c_j^2 over the exact factor
   double flops_panel = 0.0;  // the same over the padded panels (relaxed amalgamation)
   int64_t nnz_l = 0, l_storage = 0, max_width = 0, max_rows = 0;
+  int64_t l_dinv = 0;  // values of all diagonal-block inverses (sum of n_s^2)
   int64_t n_fundamental = 0;  // fundamental supernodes before amalgamation and the cap
   // the granularity rule applied by the last build_schur_tasks (kGranHybrid resolved), its
   // threshold D (-1 under kGranTiles) and the number of outer tasks split

@@ -733,6 +733,67 @@ void launch_assemble(const double* vals, const int64_t* amap, int64_t nnz, void*
 }
 
 static size_t potrf_smem(int w) { return (size_t)w * w * sizeof(double) + update_table_bytes(w); }
+
+constexpr int kDinvThreads = 256;
+template <typename P>
+constexpr size_t dinv_smem() {
+  return ((size_t)kDinvMaxWidth * kDinvMaxWidth + kDinvMaxWidth) * sizeof(P);
+}
+
+// Y = L11^-1 of the supernode of each task (POTRF tasks, one CTA per task) into d.dinv,
+// row-major n x n (dinv[r * n + c] = Y[r, c], zeros above the diagonal), in the panel's
+// precision; supernodes without dinv are skipped.  Forward substitution on all columns of
+// the identity at once, right-looking: with l'_ij = L_ij / L_jj and Z = I, step j (one
+// barrier) takes Z[i, c] -= l'_ij Z[j, c] for the rows i > j and columns c <= j (row j is
+// final by then); Y[i, c] = Z[i, c] / L_ii at the end: n (n^2 - 1) / 6 multiply-adds, the n
+// reciprocals once.  One n x n shared array holds both factors of each step: l' in the
+// strict lower triangle (column-major, S[c * n + r]) and the lower-triangular Z transposed
+// in the upper triangle and the diagonal (Z[i, c] at S[i * n + c]), so a warp's threads
+// update consecutive words.  The solves apply Y instead of substituting serially (each FP64
+// instruction holds its warp ~64 cycles, so a 64-step substitution chain costs ~10 us).
+template <typename P>
+__global__ void __launch_bounds__(kDinvThreads)
+    k_diag_inverse(const int4* __restrict__ tasks, const SnDev* __restrict__ sns) {
+  extern __shared__ __align__(16) double dsm[];
+  const SnDev d = sns[tasks[blockIdx.x].x];
+  if (!d.dinv) return;
+  const int n = d.n;
+  P* S = reinterpret_cast<P*>(dsm);
+  P* rd = S + n * n;
+  stage_diag_block(S, reinterpret_cast<const P*>(d.L), n, d.m);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rd[j] = P(1) / S[j * n + j];
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int c = idx / n, r = idx - c * n;
+    if (r > c) S[idx] *= rd[c];          // l'_rc
+    else S[idx] = r == c ? P(1) : P(0);  // Z[c, r] = I
+  }
+  __syncthreads();
+  for (int j = 0; j + 1 < n; j++) {
+    const int cols = j + 1, rows = n - 1 - j;
+    for (int idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
+      const int ii = idx / cols, c = idx - ii * cols, i = j + 1 + ii;
+      S[i * n + c] -= S[j * n + i] * S[j * n + c];
+    }
+    __syncthreads();
+  }
+  P* Y = reinterpret_cast<P*>(d.dinv);
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx / n, c = idx - r * n;
+    Y[idx] = c <= r ? S[idx] * rd[r] : P(0);
+  }
+}
+
+void launch_diag_inverse(const int4* tasks, int ntasks, const SnDev* sns, bool f32,
+                         cudaStream_t st) {
+  if (ntasks <= 0) return;
+  if (f32)
+    k_diag_inverse<float><<<ntasks, kDinvThreads, dinv_smem<float>(), st>>>(tasks, sns);
+  else
+    k_diag_inverse<double><<<ntasks, kDinvThreads, dinv_smem<double>(), st>>>(tasks, sns);
+}
 static size_t potrf_mixed_smem(int w) {  // the FP64 block of a redo overlays the FP32 one
   return (size_t)w * w * sizeof(double) + update_table_bytes(w);
 }
@@ -834,7 +895,9 @@ static bool set_smem(K kernel, size_t bytes) {
 }
 
 int set_factor_kernel_attrs(int max_width) {
-  bool ok = set_smem(k_potrf<double>, potrf_smem(max_width)) &&
+  bool ok = set_smem(k_diag_inverse<double>, dinv_smem<double>()) &&
+            set_smem(k_diag_inverse<float>, dinv_smem<float>()) &&
+            set_smem(k_potrf<double>, potrf_smem(max_width)) &&
             set_smem(k_potrf_mixed, potrf_mixed_smem(max_width)) &&
             set_smem(k_trsm_blk<double>, trsm_blk_smem<double>()) &&
             set_smem(k_trsm_blk<float>, trsm_blk_smem<float>()) &&

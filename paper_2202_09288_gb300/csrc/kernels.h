@@ -12,6 +12,12 @@ void launch_assemble(const double* vals, const int64_t* amap, int64_t nnz, void*
                      cudaStream_t st);
 // Task launches are persistent: at most one wave of CTAs, each taking its next task from the
 // zero-initialized work-queue counter `queue` (one counter per launch).
+// Widest supernode whose diagonal-block inverse the factor keeps (for the solves).
+constexpr int kDinvMaxWidth = 64;
+// Y = L11^-1 of every supernode of a POTRF task list whose descriptor has dinv set (the
+// blocks are final: after launch_potrf of the same level).
+void launch_diag_inverse(const int4* tasks, int ntasks, const SnDev* sns, bool f32,
+                         cudaStream_t st);
 void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                   const MatDev* mats, int max_width, bool f32, float tau, cudaStream_t st);
 void launch_trsm(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int max_width,

@@ -21,14 +21,14 @@ enum ProfKindId {
   kProfAssemble, kProfPotrf, kProfTrsm, kProfSchur64, kProfSchur32, kProfSchur16,
   kProfAsmOwner, kProfFwd, kProfBwd, kProfPerm, kProfScale, kProfPotrfF32, kProfTrsmF32,
   kProfSchur64F32, kProfSchur32F32, kProfSchur16F32, kProfRefine, kProfGraph, kProfSchur128,
-  kProfSchur128Tc, kProfOzSlice, kProfSchur128Oz, kNumProf
+  kProfSchur128Tc, kProfOzSlice, kProfSchur128Oz, kProfDinv, kNumProf
 };
 inline const char* const kProfNames[kNumProf] = {
     "assemble",    "potrf_f64",   "trsm_f64",    "schur64_f64",  "schur32_f64",
     "schur16_f64", "assemble_owner", "solve_fwd", "solve_bwd",   "solve_perm",
     "equilibrate", "potrf_f32",   "trsm_f32",    "schur64_f32",  "schur32_f32",
     "schur16_f32", "refine",      "batch_graph", "schur128_f64", "schur128_tc",
-    "oz_slice",    "schur128_oz"};
+    "oz_slice",    "schur128_oz", "diag_inverse"};
 
 // Tracing kind of a Schur tile class (oz: FP64 128-tiles on the bf16 tensor cores).
 inline int prof_schur_kind(int cls, bool f32, bool oz = false) {
@@ -114,6 +114,7 @@ struct chol_num {
   double* d_stage = nullptr;   // owner assembly staging
   double* d_scale = nullptr;   // CHOL_MIXED: equilibration a_jj^{-1/2}
   void* d_oz = nullptr;        // FP64 tensor-core Schur: operand slices (zeroed scratch)
+  void* d_dinv = nullptr;      // inverses of the diagonal blocks (W <= 64; panel precision)
   int64_t oz_cap = 0;          // slice rows d_oz holds
   // solve workspace, grown on demand
   int64_t ws_nrhs = 0;

@@ -16,6 +16,9 @@
 //   backward task {s, r0}: part_q[j, c] = sum_{i in block} L21[i, j] x[rows[n+i], c] into
 //            a staging slot q; then per supernode x_s = L11^{-T} (w_s - sum_q part_q), the
 //            partials summed in task order (deterministic).
+// Where the factor keeps the inverses Y = L11^{-1} of its diagonal blocks (formed once per
+// factorization), L11^{-1} y_s and L11^{-T} r_s are products with Y and Y^T, parallel over
+// the block's rows; otherwise they are substitutions, one step per column.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -109,7 +112,57 @@ __device__ void load_l11(const SnDev& d, P* L11, P* rdiag) {
   __syncthreads();
 }
 
-// smem: L11 n*n, rdiag n, xs n*nrhs.  STAGE: the off-diagonal products go to the level's
+// Y (row-major, lower triangle) into shared memory with leading dimension n + 1 (odd: the
+// threads of a warp reading one column of Y hit distinct banks), every copy in flight.
+template <typename P>
+__device__ void stage_dinv(P* Ys, const P* __restrict__ Y, int n) {
+  const int ld = n + 1;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx / n, k = idx - r * n;
+    if (k <= r) cp_async_elem(Ys + r * ld + k, Y + idx);
+  }
+}
+
+// xs = Y bin (FORWARD) or Y^T bin, n x nrhs (ld n), Y staged by stage_dinv.  Each output is a
+// dot product over the triangle's part of a row (forward: k <= r) or column (backward:
+// k >= r) of Y; with fewer outputs than threads the k range is cut into segments whose
+// partial sums are added in segment order through red (blockDim.x entries).  Ends with a
+// barrier.
+template <bool FORWARD, typename P>
+__device__ void dinv_apply(const P* Ys, const P* bin, P* xs, P* red, int n, int nrhs) {
+  const int ld = n + 1, items = n * nrhs, nt = blockDim.x;
+  const int nseg = items >= nt ? 1 : min(8, nt / items);
+  const int seg = (n + nseg - 1) / nseg;
+  for (int idx = threadIdx.x; idx < items * nseg; idx += nt) {
+    const int sg = idx / items, it = idx - sg * items;
+    const int c = it / n, r = it - c * n;
+    int k0 = sg * seg, k1 = min(n, k0 + seg);
+    if (FORWARD) k1 = min(k1, r + 1);
+    else k0 = max(k0, r);
+    const P* b = bin + c * n;
+    P a0 = P(0), a1 = P(0);
+    int k = k0;
+    for (; k + 1 < k1; k += 2) {
+      a0 += (FORWARD ? Ys[r * ld + k] : Ys[k * ld + r]) * b[k];
+      a1 += (FORWARD ? Ys[r * ld + k + 1] : Ys[(k + 1) * ld + r]) * b[k + 1];
+    }
+    if (k < k1) a0 += (FORWARD ? Ys[r * ld + k] : Ys[k * ld + r]) * b[k];
+    if (nseg == 1) xs[it] = a0 + a1;
+    else red[idx] = a0 + a1;
+  }
+  __syncthreads();
+  if (nseg > 1) {
+    for (int it = threadIdx.x; it < items; it += nt) {
+      P v = red[it];
+      for (int sg = 1; sg < nseg; sg++) v += red[sg * items + it];
+      xs[it] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// smem: L11 n*n, rdiag n, xs n*nrhs (substitution), or Y n*(n+1), b n*nrhs, xs n*nrhs,
+// red kSolveThreads (with Y).  STAGE: the off-diagonal products go to the level's
 // staging slots (q * kSolveRows + ii) * nrhs + c instead of atomics into y.
 template <typename P, bool STAGE, int NR>
 __global__ void __launch_bounds__(kSolveThreads)
@@ -122,16 +175,31 @@ __global__ void __launch_bounds__(kSolveThreads)
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n, m = d.m, u = m - n;
-    P* L11 = smp;
-    P* rdiag = L11 + n * n;
-    P* xs = rdiag + n;
-    for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
-      const int c = idx / n, j = idx - c * n;
-      xs[idx] = (P)y[c * ldv + d.col0 + j];
+    P* xs;
+    if (d.dinv) {
+      P* Ys = smp;
+      P* bin = Ys + n * (n + 1);
+      xs = bin + n * nrhs;
+      stage_dinv(Ys, reinterpret_cast<const P*>(d.dinv), n);
+      for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+        const int c = idx / n, j = idx - c * n;
+        bin[idx] = (P)y[c * ldv + d.col0 + j];
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      dinv_apply<true>(Ys, bin, xs, xs + n * nrhs, n, nrhs);
+    } else {
+      P* L11 = smp;
+      P* rdiag = L11 + n * n;
+      xs = rdiag + n;
+      for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+        const int c = idx / n, j = idx - c * n;
+        xs[idx] = (P)y[c * ldv + d.col0 + j];
+      }
+      load_l11<P>(d, L11, rdiag);
+      warp_trisolve<true>(L11, rdiag, xs, n, nrhs);
+      __syncthreads();
     }
-    load_l11<P>(d, L11, rdiag);
-    warp_trisolve<true>(L11, rdiag, xs, n, nrhs);
-    __syncthreads();
     if (tk.y == 0)
       for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
         const int c = idx / n, j = idx - c * n;
@@ -290,9 +358,11 @@ __global__ void __launch_bounds__(kSolveThreads)
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
     const int n = d.n;
+    const bool inv = d.dinv != nullptr;
     P* L11 = smp;
     P* rdiag = L11 + n * n;
-    P* xs = rdiag + n;
+    P* xs = inv ? smp + n * (n + 1) : rdiag + n;  // with Y: the right-hand side, then xs
+    if (inv) stage_dinv(smp, reinterpret_cast<const P*>(d.dinv), n);
     const int u = d.m - n;
     // w_s minus the partials of the supernode's backward tasks, summed in a fixed order with
     // eight loads in flight
@@ -310,9 +380,17 @@ __global__ void __launch_bounds__(kSolveThreads)
       for (; q < nq; q++) a[0] += pp[q * ps];
       xs[idx] = (P)(w[c * ldv + d.col0 + j] - (((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]))));
     }
-    load_l11<P>(d, L11, rdiag);
-    warp_trisolve<false>(L11, rdiag, xs, n, nrhs);
-    __syncthreads();
+    if (inv) {
+      cp_async_wait_all();
+      __syncthreads();
+      P* xo = xs + n * nrhs;
+      dinv_apply<false>(smp, xs, xo, xo + n * nrhs, n, nrhs);
+      xs = xo;
+    } else {
+      load_l11<P>(d, L11, rdiag);
+      warp_trisolve<false>(L11, rdiag, xs, n, nrhs);
+      __syncthreads();
+    }
     for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
       const int c = idx / n, j = idx - c * n;
       w[c * ldv + d.col0 + j] = xs[idx];
@@ -329,7 +407,9 @@ __global__ void __launch_bounds__(kSolveThreads)
 
 // ---- launchers ---------------------------------------------------------------------------------
 static inline size_t solve_smem(int W, int nrhs) {
-  return ((size_t)W * W + W + (size_t)W * nrhs) * sizeof(double);
+  const size_t sub = (size_t)W * W + W + (size_t)W * nrhs;
+  const size_t inv = W <= kDinvMaxWidth ? (size_t)W * (W + 1) + 2 * (size_t)W * nrhs + kSolveThreads : 0;
+  return std::max(sub, inv) * sizeof(double);
 }
 
 static inline int grid_for(int64_t total) {

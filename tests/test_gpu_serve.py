@@ -108,3 +108,35 @@ def test_admission_under_a_small_budget(torch):
     X, res = srv.wait(srv.submit(A, perm, B))
     assert res["status"] == P.CHOL_OK
     srv.close()
+
+
+def test_request_arriving_mid_group_is_admitted_at_once(torch):
+    """Continuous batching: a small request submitted while a long group occupies one slot
+    is admitted by the other slot at once -- it starts after the long group started and
+    finishes before that group ends -- and its solution is bit for bit the one it gets
+    when served alone (owner-ordered assembly)."""
+    import time
+
+    L, lperm = inputs.workload("st27x3_40")
+    LB = np.asfortranarray(L.to_scipy_full() @ inputs.rhs_block(21, L.n, 32))
+    S, sperm = inputs.workload("lap2d_24")
+    SB = np.asfortranarray(S.to_scipy_full() @ inputs.rhs_block(22, S.n, 2))
+    srv = P.Server(slots=2, max_batch=4, assembly=P.CHOL_ASSEMBLY_OWNER)
+    srv.wait(srv.submit(L, lperm, LB))          # analysis of the long pattern cached
+    srv.wait(srv.submit(S, sperm, SB))          # and of the small one
+    t_long = srv.submit(L, lperm, LB)
+    time.sleep(0.03)                            # the long group is on the GPU by now
+    t_short = srv.submit(S, sperm, SB)
+    Xs, rs = srv.wait(t_short)
+    Xl, rl = srv.wait(t_long)
+    srv.close()
+    assert rs["status"] == P.CHOL_OK and rl["status"] == P.CHOL_OK
+    assert rl["batch_size"] == 1 and rs["batch_size"] == 1
+    assert rl["t_start"] < rs["t_start"] < rl["t_done"], (rl, rs)
+    assert rs["t_done"] < rl["t_done"], (rl, rs)
+    assert oracle.residual(S.n, S.colptr, S.rowind, S.vals, SB, Xs) <= 1e-12
+    assert oracle.residual(L.n, L.colptr, L.rowind, L.vals, LB, Xl) <= 1e-12
+    alone = P.Server(slots=1, max_batch=1, assembly=P.CHOL_ASSEMBLY_OWNER)
+    Xa, ra = alone.wait(alone.submit(S, sperm, SB))
+    alone.close()
+    assert np.array_equal(Xs, Xa)
