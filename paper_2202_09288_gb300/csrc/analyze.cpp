@@ -369,11 +369,13 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
   S->fg_ent.clear();
   S->max_fwd_per_level = 0;
   S->stage_elems = 0;
+  S->lvl_maxw.assign(S->nlev, 0);
   for (int32_t l = 0; l < S->nlev; l++) {
     int64_t stage = 0;
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
       const int32_t s = S->lvl_sn[q];
       const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
+      S->lvl_maxw[l] = std::max(S->lvl_maxw[l], w);
       const int32_t u = S->sn_m[s] - w;
       const int32_t first_bwd = (int32_t)(S->tasks[kTaskBwd].size() / 4);
       const int32_t nbwd = (std::max(u, 1) + kSolveRows - 1) / kSolveRows;

@@ -529,9 +529,10 @@ int enqueue_solve_seq(chol_ctx* c, const chol_num* f, int k, const double* B, in
   const int W = S.width_cap;
   const bool f32 = f->precision == CHOL_MIXED;
   const double* scale = f32 ? f->d_scale : nullptr;
+  const bool inv = f->d_dinv != nullptr;
   const double vec = 8.0 * n * k;
   const SolveTrace tr{c, trace};
-  CK(cudaMemsetAsync(bf.sq, 0, solve_counters(S.nlev) * sizeof(int), st));
+  CK(cudaMemsetAsync(bf.sq, 0, solve_counters(S) * sizeof(int), st));
   tr.begin(kProfPerm);
   chol::launch_gather_perm(B, ldb, sym->dev.perm, scale, n, k, bf.y, st);
   tr.end(kProfPerm, 2 * vec + 4.0 * n);
@@ -539,20 +540,21 @@ int enqueue_solve_seq(chol_ctx* c, const chol_num* f, int k, const double* B, in
     int cnt;
     const int4* t = task_ptr(sym, chol::kTaskFwd, l, &cnt);
     tr.begin(kProfFwd);
-    chol::launch_fwd(t, cnt, bf.sq + 3 * l, f->d_sn, n, k, W, bf.y, bf.w, bf.fstage, f32, st);
+    chol::launch_fwd(t, cnt, bf.sq + 3 * l, f->d_sn, n, k, S.lvl_maxw[l], bf.y, bf.w, bf.fstage,
+                     inv, f32, st);
     if (bf.fstage)
       chol::launch_fwd_gather(sym->dev.fg_row + S.fg_lvl[l], sym->dev.fg_ptr + S.fg_lvl[l],
                               sym->dev.fg_ent, S.fg_lvl[l + 1] - S.fg_lvl[l], n, k, bf.fstage,
                               bf.y, st);
     tr.end(kProfFwd, S.lvl_panel_bytes[l] * (f32 ? 0.5 : 1.0));
   }
+  int* arrive = bf.sq + solve_arrive_offset(S);
   for (int32_t l = S.nlev - 1; l >= 0; l--) {
-    int nb, nd;
+    int nb;
     const int4* tb = task_ptr(sym, chol::kTaskBwd, l, &nb);
-    const int4* td = task_ptr(sym, chol::kTaskPotrf, l, &nd);
     tr.begin(kProfBwd);
-    chol::launch_bwd(tb, nb, bf.sq + 3 * l + 1, S.task_off[chol::kTaskBwd][l], td, nd, f->d_sn,
-                     n, k, W, bf.w, bf.part, f32, st);
+    chol::launch_bwd(tb, nb, bf.sq + 3 * l + 1, f->d_sn, n, k, W, S.lvl_maxw[l], bf.w, bf.part,
+                     arrive, inv, f32, st);
     tr.end(kProfBwd, S.lvl_panel_bytes[l] * (f32 ? 0.5 : 1.0));
   }
   tr.begin(kProfPerm);
@@ -604,7 +606,7 @@ int make_factor(chol_ctx* c, chol_sym* sym, const double* vals, int where, int p
       (rc = dev_alloc(c, (void**)&f->d_mat, sizeof(MatDev))) ||
       (rc = dev_alloc(c, (void**)&f->d_err, 4 * sizeof(unsigned long long))) ||
       (rc = dev_alloc(c, (void**)&f->d_ctr,
-                      (factor_counters(S.nlev) + solve_counters(S.nlev)) * sizeof(int))) ||
+                      (factor_counters(S.nlev) + solve_counters(S)) * sizeof(int))) ||
       (rc = dev_alloc(c, (void**)&f->d_vals, (size_t)S.nnz_a * 8)) ||
       (f32 && (rc = dev_alloc(c, (void**)&f->d_scale, (size_t)S.n * 8))) ||
       (assembly == CHOL_ASSEMBLY_OWNER &&
@@ -778,7 +780,7 @@ namespace chol {
 // kSolveRows x k).
 size_t solve_scratch_doubles(const chol_num* f, int64_t k) {
   const Sym& S = f->sym->S;
-  size_t d = (rt::solve_counters(S.nlev) * sizeof(int) + 255) / 256 * 256 / sizeof(double);
+  size_t d = (rt::solve_counters(S) * sizeof(int) + 255) / 256 * 256 / sizeof(double);
   d += 2 * (size_t)S.n * k + (size_t)f->sym->max_bwd_per_level * S.width_cap * k;
   if (f->assembly == CHOL_ASSEMBLY_OWNER) d += (size_t)S.max_fwd_per_level * kSolveRows * k;
   return d;
@@ -790,7 +792,7 @@ int enqueue_solve_ws(chol_ctx* c, const chol_num* f, int k, const double* B, int
                      double* X, int64_t ldx, double* ws) {
   const chol_sym* sym = f->sym;
   const Sym& S = sym->S;
-  const size_t qd = (rt::solve_counters(S.nlev) * sizeof(int) + 255) / 256 * 256 / sizeof(double);
+  const size_t qd = (rt::solve_counters(S) * sizeof(int) + 255) / 256 * 256 / sizeof(double);
   rt::SolveBufs bf;
   bf.sq = reinterpret_cast<int*>(ws);  // work-queue counters, then the vectors
   bf.y = ws + qd;

@@ -133,6 +133,7 @@ struct Sym {
   std::vector<int64_t> amap;       // nnz_a: panel offset of every stored entry of A
   int32_t nlev = 0;
   std::vector<int32_t> lvl_ptr, lvl_sn;
+  std::vector<int32_t> lvl_maxw;  // widest supernode of each level (launch sizes of the solves)
   // task lists: tasks[k] holds all tasks of kind k, level l occupies
   // [task_off[k][l], task_off[k][l+1])
   std::vector<int32_t> tasks[kNumTaskKinds];      // 4 ints per task

@@ -59,15 +59,20 @@ void launch_gather_perm(const double* B, int64_t ldb, const int32_t* perm, const
                         int64_t n, int nrhs, double* y, cudaStream_t st);
 void launch_scatter_perm(const double* w, const int32_t* perm, const double* scale, int64_t n,
                          int nrhs, double* X, int64_t ldx, cudaStream_t st);
+// W: the level's widest supernode (launch sizes); inv: the factor keeps the inverses of its
+// diagonal blocks
 void launch_fwd(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int64_t ldv,
-                int nrhs, int W, double* y, double* w, double* fstage, bool f32, cudaStream_t st);
+                int nrhs, int W, double* y, double* w, double* fstage, bool inv, bool f32,
+                cudaStream_t st);
 void launch_fwd_gather(const int32_t* fg_row, const int64_t* fg_ptr, const int32_t* fg_ent,
                        int64_t nrows, int64_t ldv, int nrhs, const double* fstage, double* y,
                        cudaStream_t st);
-// queues: two counters (backward partials, then diagonal solves)
-void launch_bwd(const int4* bwd_tasks, int nbwd, int* queues, int64_t bwd_base,
-                const int4* diag_tasks, int ndiag, const SnDev* sns, int64_t ldv, int nrhs,
-                int W, double* w, double* part, bool f32, cudaStream_t st);
+// queue: the level's work-queue counter; arrive: one zeroed counter per supernode (the
+// backward step's last-task detection); W: the stride of the partial slots (the width cap);
+// wl: the level's widest supernode (launch sizes)
+void launch_bwd(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int64_t ldv,
+                int nrhs, int W, int wl, double* w, double* part, int* arrive, bool inv,
+                bool f32, cudaStream_t st);
 int set_solve_kernel_attrs(int W, int max_nrhs);
 
 void launch_diag_scale(const int64_t* colptr, const int32_t* rowind, const double* vals,

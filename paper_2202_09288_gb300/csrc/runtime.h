@@ -168,7 +168,10 @@ TaskView sym_view(const chol_sym* sym);
 // (POTRF, TRSM, four Schur tile classes, owner assembly), 3 per level for a solve.
 constexpr int kFactorCountersPerLevel = 3 + chol::kNumTileClasses;
 inline size_t factor_counters(int32_t nlev) { return kFactorCountersPerLevel * (size_t)nlev + 8; }
-inline size_t solve_counters(int32_t nlev) { return 3 * (size_t)nlev + 8; }
+// Counters of a solve, zeroed at its start: 3 work-queue counters per level, then (from
+// solve_arrive_offset) one arrival counter per supernode for the backward step.
+inline size_t solve_arrive_offset(const Sym& S) { return 3 * (size_t)S.nlev + 8; }
+inline size_t solve_counters(const Sym& S) { return solve_arrive_offset(S) + (size_t)S.ns; }
 // oz / oz_rows: slice scratch of FP64 128-tiles on the bf16 tensor cores (null: those
 // tiles run as 64 x 64 DMMA tiles)
 int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
