@@ -379,7 +379,7 @@ int analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
       const int32_t u = S->sn_m[s] - w;
       const int32_t first_bwd = (int32_t)(S->tasks[kTaskBwd].size() / 4);
       const int32_t nbwd = (std::max(u, 1) + kSolveRows - 1) / kSolveRows;
-      push4(S->tasks[kTaskPotrf], s, first_bwd, nbwd, 0);
+      push4(S->tasks[kTaskPotrf], s, first_bwd, nbwd, -1);
       const double dn = w, du = u;
       S->lvl_flops[kTaskPotrf][l] += dn * (dn + 1) * (2 * dn + 1) / 6.0;
       S->lvl_flops[kTaskTrsm][l] += du * dn * dn;
@@ -589,7 +589,8 @@ double partition_tree(int32_t nv, const int32_t* parent, const double* work, int
 
 void build_schur_tasks(Sym* S, const TilePolicy& policy) {
   S->policy = policy;
-  const int kinds[] = {kTaskSchur64, kTaskSchur32, kTaskSchur16, kTaskSchur128, kTaskOzSlice};
+  const int kinds[] = {kTaskSchur64, kTaskSchur32, kTaskSchur16, kTaskSchur128, kTaskOzSlice,
+                       kTaskTrsmRest};
   for (int k : kinds) {
     S->tasks[k].clear();
     S->task_off[k].assign(S->nlev + 1, 0);
@@ -597,6 +598,9 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
   }
   S->lvl_ozrows.assign(S->nlev, 0);
   S->oz_rows = 0;
+  S->lvl_oyrows.assign(S->nlev, 0);
+  S->oy_rows = 0;
+  for (size_t q = 3; q < S->tasks[kTaskPotrf].size(); q += 4) S->tasks[kTaskPotrf][q] = -1;
   // pass 1: every supernode's tile class under the size thresholds
   std::vector<int8_t> cls0(S->ns, kTile16);
   for (int32_t l = 0; l < S->nlev; l++) {
@@ -651,9 +655,12 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
       }
     }
   }
-  // pass 2: the task lists
+  // pass 2: the task lists.  A 128-tile supernode (FP64: slices on the tensor cores) also
+  // gets its TRSM on the tensor cores, with the slices of its diagonal block's inverse at
+  // 64 rows of the level's inverse slices (recorded in its POTRF task); the other supernodes'
+  // TRSM tasks form kTaskTrsmRest.
   for (int32_t l = 0; l < S->nlev; l++) {
-    int64_t ozrow = 0;
+    int64_t ozrow = 0, oyrow = 0;
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
       const int32_t s = S->lvl_sn[q];
       const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
@@ -665,15 +672,22 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
       if (cls == kTile128) {
         for (int32_t i0 = 0; i0 < u; i0 += T)
           for (int32_t k0 = 0; k0 <= i0; k0 += T) push4(S->tasks[k], s, i0, k0, (int32_t)ozrow);
-        for (int32_t r0 = 0; r0 < u; r0 += 128) push4(S->tasks[kTaskOzSlice], s, r0, (int32_t)ozrow, 0);
+        for (int32_t r0 = 0; r0 < u; r0 += 128)
+          push4(S->tasks[kTaskOzSlice], s, r0, (int32_t)ozrow, (int32_t)oyrow);
+        S->tasks[kTaskPotrf][4 * (size_t)q + 3] = (int32_t)oyrow;
         ozrow += (u + 7) / 8 * 8;
+        oyrow += kOzInvRows;
       } else {
         for (int32_t i0 = 0; i0 < u; i0 += T)
           for (int32_t k0 = 0; k0 <= i0; k0 += T) push4(S->tasks[k], s, i0, k0, T);
+        for (int32_t r0 = 0; r0 < u; r0 += kTrsmRows) push4(S->tasks[kTaskTrsmRest], s, r0, 0, 0);
+        S->lvl_flops[kTaskTrsmRest][l] += (double)u * w * w;  // kTaskTrsm's count
       }
     }
     S->lvl_ozrows[l] = ozrow;
     if (ozrow > 0) S->oz_rows = std::max(S->oz_rows, ozrow + 128);
+    S->lvl_oyrows[l] = oyrow;
+    S->oy_rows = std::max(S->oy_rows, oyrow);
     for (int k : kinds) S->task_off[k][l + 1] = (int64_t)S->tasks[k].size() / 4;
   }
 }

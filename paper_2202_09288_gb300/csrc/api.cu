@@ -323,7 +323,10 @@ bool use_oz(const chol_ctx* c, const chol_sym* sym) {
 }
 
 int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
-                   bool f32, bool owner, int* ctr, void* oz, int64_t oz_rows) {
+                   bool f32, bool owner, int* ctr, void* oz, int64_t oz_rows, void* oy,
+                   int64_t oy_rows) {
+  // FP64 factors with the slice scratches: 128-tile supernodes take the tensor-core TRSM
+  const bool trsm_oz = oz && oy && !f32;
   cudaStream_t st = c->stream;
   CK(cudaMemsetAsync(ctr, 0, factor_counters(v.nlev) * sizeof(int), st));
   const float tau = (float)(c->opts.pivot_tau > 0 ? c->opts.pivot_tau : 1e-5);
@@ -334,14 +337,29 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
     const int4* t = v.level(chol::kTaskPotrf, l, &cnt);
     if (cnt > 0) {
       prof_begin(c, kp);
-      chol::launch_potrf(t, cnt, q, sns, mats, v.max_width, f32, tau, st);
+      chol::launch_potrf(t, cnt, q, sns, mats, v.max_width, f32, tau, trsm_oz ? oy : nullptr,
+                         oy_rows, st);
       prof_end(c, kp, v.flops[chol::kTaskPotrf][l], 0.0);
     }
-    t = v.level(chol::kTaskTrsm, l, &cnt);
+    t = v.level(trsm_oz ? chol::kTaskTrsmRest : chol::kTaskTrsm, l, &cnt);
     if (cnt > 0) {
       prof_begin(c, kt);
       chol::launch_trsm(t, cnt, q + 1, sns, v.max_width, f32, st);
-      prof_end(c, kt, v.flops[chol::kTaskTrsm][l], 0.0);
+      prof_end(c, kt, v.flops[trsm_oz ? chol::kTaskTrsmRest : chol::kTaskTrsm][l], 0.0);
+    }
+    // the 128-tile supernodes' TRSM: slices of A21 S^-1, then L21 = A21 Y^T on the tensor
+    // cores
+    if (trsm_oz) {
+      t = v.level(chol::kTaskOzSlice, l, &cnt);
+      if (cnt > 0) {
+        prof_begin(c, kProfOzSlice);
+        chol::launch_oz_slice(t, cnt, sns, oz, oz_rows, oy, oy_rows, st);
+        prof_end(c, kProfOzSlice, 0.0, 0.0);
+        prof_begin(c, kProfTrsmOz);
+        chol::launch_trsm_oz(t, cnt, sns, mats, oz, oz_rows, oy, oy_rows, st);
+        prof_end(c, kProfTrsmOz,
+                 v.flops[chol::kTaskTrsm][l] - v.flops[chol::kTaskTrsmRest][l], 0.0);
+      }
     }
     // 128-tiles on the tensor cores: FP64 by bf16 slices, FP32 by TF32 hi/lo parts; their
     // operands are prepared per level after TRSM
@@ -350,7 +368,7 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
       if (cnt > 0) {
         prof_begin(c, kProfOzSlice);
         if (f32) chol::launch_tf32_split(t, cnt, sns, v.max_width, oz, oz_rows, st);
-        else chol::launch_oz_slice(t, cnt, sns, oz, oz_rows, st);
+        else chol::launch_oz_slice(t, cnt, sns, oz, oz_rows, nullptr, 0, st);
         prof_end(c, kProfOzSlice, 0.0, 0.0);
       }
     }
@@ -385,7 +403,7 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
     const int cnt = (int)(o[v.nlev] - o[0]);
     if (cnt > 0) {
       prof_begin(c, kProfDinv);
-      chol::launch_diag_inverse(v.d[chol::kTaskPotrf] + o[0], cnt, sns, f32, st);
+      chol::launch_diag_inverse(v.d[chol::kTaskPotrf] + o[0], cnt, sns, f32, trsm_oz, st);
       prof_end(c, kProfDinv, 0.0, 0.0);
     }
   }
@@ -396,42 +414,54 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
 // Enqueues the numeric factorization of the values in f->d_vals.
 // Slice scratch of a factor's FP64 tensor-core Schur tiles, grown to the analysis' need
 // (a new tile policy can raise it) and zeroed when allocated.
-int ensure_oz(chol_num* f, void** oz, int64_t* rows) {
+int grow_scratch(chol_ctx* c, void** buf, int64_t* cap, int64_t rows, bool inverses) {
+  if (*cap >= rows) return CHOL_OK;
+  // the stream may still use the old scratch: free it only after the stream drains
+  if (*buf) {
+    CK(cudaStreamSynchronize(c->stream));
+    dev_free(c, *buf);
+    *buf = nullptr;
+    *cap = 0;
+  }
+  const size_t bytes = inverses ? chol::oy_scratch_bytes(rows) : chol::oz_scratch_bytes(rows);
+  int rc = dev_alloc(c, buf, bytes);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(*buf, 0, bytes, c->stream));
+  *cap = rows;
+  return CHOL_OK;
+}
+
+int ensure_oz(chol_num* f, void** oz, int64_t* rows, void** oy, int64_t* oy_rows) {
   *oz = nullptr;
   *rows = 0;
+  *oy = nullptr;
+  *oy_rows = 0;
   const Sym& S = f->sym->S;
   // FP64: bf16 slices (W <= 64, unless the DMMA tiles are asked for); FP32: TF32 parts
   const bool need = f->precision == CHOL_MIXED ? true : use_oz(f->ctx, f->sym);
   if (!need || S.oz_rows <= 0) return CHOL_OK;
-  if (f->oz_cap < S.oz_rows) {
-    chol_ctx* c = f->ctx;
-    // the stream may still use the old scratch: free it only after the stream drains
-    if (f->d_oz) {
-      CK(cudaStreamSynchronize(c->stream));
-      dev_free(c, f->d_oz);
-      f->d_oz = nullptr;
-      f->oz_cap = 0;
-    }
-    const size_t bytes = chol::oz_scratch_bytes(S.oz_rows);
-    int rc = dev_alloc(c, &f->d_oz, bytes);
-    if (rc) return rc;
-    CK(cudaMemsetAsync(f->d_oz, 0, bytes, c->stream));
-    f->oz_cap = S.oz_rows;
-  }
+  int rc = grow_scratch(f->ctx, &f->d_oz, &f->oz_cap, S.oz_rows, false);
+  if (rc) return rc;
   *oz = f->d_oz;
   *rows = f->oz_cap;
+  // FP64: the slices of the 128-tile supernodes' diagonal-block inverses (tensor-core TRSM)
+  if (f->precision != CHOL_MIXED && S.oy_rows > 0 && f->d_dinv) {
+    if ((rc = grow_scratch(f->ctx, &f->d_oy, &f->oy_cap, S.oy_rows, true))) return rc;
+    *oy = f->d_oy;
+    *oy_rows = f->oy_cap;
+  }
   return CHOL_OK;
 }
 
 int enqueue_factor(chol_num* f) {
   int rc = enqueue_assembly(f);
   if (rc) return rc;
-  void* oz;
-  int64_t oz_rows;
-  if ((rc = ensure_oz(f, &oz, &oz_rows))) return rc;
+  void *oz, *oy;
+  int64_t oz_rows, oy_rows;
+  if ((rc = ensure_oz(f, &oz, &oz_rows, &oy, &oy_rows))) return rc;
   return enqueue_levels(f->ctx, sym_view(f->sym), f->d_sn, f->d_mat,
                         f->precision == CHOL_MIXED, f->assembly == CHOL_ASSEMBLY_OWNER, f->d_ctr,
-                        oz, oz_rows);
+                        oz, oz_rows, oy, oy_rows);
 }
 
 // Device descriptors of f's supernodes (matrix slot `mat`) and of f itself.
@@ -576,7 +606,7 @@ void free_num_buffers(chol_num* f) {
   if (!c) return;
   void* ptrs[] = {f->L, f->d_sn, f->d_mat, f->d_err, f->d_ctr, f->d_vals, f->d_stage, f->d_scale,
                   f->d_y, f->d_w, f->d_bx, f->d_part, f->d_fstage, f->d_rr, f->d_rd,
-                  f->d_rb, f->d_norm, f->d_oz, f->d_gv, f->d_gz, f->d_gw, f->d_gpart,
+                  f->d_rb, f->d_norm, f->d_oz, f->d_oy, f->d_gv, f->d_gz, f->d_gw, f->d_gpart,
                   f->d_gh, f->d_dinv};
   for (void* p : ptrs) dev_free(c, p);
   c->nums.erase(f);
@@ -670,6 +700,8 @@ size_t factor_bytes(const chol_sym* sym, int precision, int assembly) {
   if (precision == CHOL_MIXED) b += (size_t)S.n * 8;
   if (assembly == CHOL_ASSEMBLY_OWNER) b += (size_t)S.stage_elems * 8;
   if (precision != CHOL_MIXED && S.oz_rows > 0) b += chol::oz_scratch_bytes(S.oz_rows);
+  if (precision != CHOL_MIXED && S.oy_rows > 0 && S.max_width <= chol::kDinvMaxWidth)
+    b += chol::oy_scratch_bytes(S.oy_rows);
   if (S.max_width <= chol::kDinvMaxWidth) b += (size_t)S.l_dinv * esz;
   return b;
 }

@@ -37,6 +37,8 @@ struct chol_batch {
   int* d_ctr = nullptr;  // work-queue counters of the batch's launches
   void* d_oz = nullptr;  // FP64 tensor-core Schur tiles: slice scratch of all members
   int64_t oz_rows = 0;
+  void* d_oy = nullptr;  // FP64 tensor-core TRSM: slices of the members' inverses
+  int64_t oy_rows = 0;
   int32_t nlev = 0;
   int max_width = 0;
   // captured factorization
@@ -59,8 +61,10 @@ void batch_release(chol_batch* b) {
   dev_free(b->ctx, b->d_mat);
   dev_free(b->ctx, b->d_ctr);
   dev_free(b->ctx, b->d_oz);
+  dev_free(b->ctx, b->d_oy);
   b->d_ctr = nullptr;
   b->d_oz = nullptr;
+  b->d_oy = nullptr;
   for (int k = 0; k < chol::kNumTaskKinds; k++) b->d_tasks[k] = nullptr;
   b->d_asm_src = nullptr;
   b->d_sn = nullptr;
@@ -88,12 +92,12 @@ int enqueue_batch(chol_batch* b) {
     if (rc) return rc;
   }
   return enqueue_levels(b->ctx, batch_view(b), b->d_sn, b->d_mat, b->f32, b->owner, b->d_ctr,
-                        b->d_oz, b->oz_rows);
+                        b->d_oz, b->oz_rows, b->d_oy, b->oy_rows);
 }
 
 const int kFactorKinds[] = {chol::kTaskPotrf,    chol::kTaskTrsm,     chol::kTaskSchur64,
                             chol::kTaskSchur32,  chol::kTaskSchur16, chol::kTaskSchur128,
-                            chol::kTaskOzSlice, chol::kTaskAsm};
+                            chol::kTaskOzSlice, chol::kTaskTrsmRest, chol::kTaskAsm};
 
 }  // namespace
 
@@ -148,29 +152,41 @@ int chol_batch_create(chol_ctx* c, int count, chol_num* const* nums, chol_batch*
   // FP64 tensor-core Schur tiles: each member's slice rows of a level follow the previous
   // members' in one batch scratch
   const bool oz = b->f32 || use_oz(c, nums[0]->sym);  // tensor-core 128-tiles need the scratch
-  std::vector<int64_t> ozbase(count);
+  // FP64: the inverses' slices of the tensor-core TRSM follow the same pattern (every member
+  // keeps its inverses when W <= kDinvMaxWidth, which the tensor-core tiles imply)
+  bool oy = !b->f32 && oz;
+  for (int i = 0; i < count; i++) oy = oy && nums[i]->d_dinv != nullptr;
+  std::vector<int64_t> ozbase(count), oybase(count);
   for (int32_t l = 0; l < b->nlev; l++) {
-    int64_t total = 0;
+    int64_t total = 0, ytotal = 0;
     for (int i = 0; i < count; i++) {
       const Sym& S = nums[i]->sym->S;
       ozbase[i] = total;
-      if (l < S.nlev) total += S.lvl_ozrows[l];
+      oybase[i] = ytotal;
+      if (l < S.nlev) {
+        total += S.lvl_ozrows[l];
+        ytotal += S.lvl_oyrows[l];
+      }
     }
     if (oz && total > 0) b->oz_rows = std::max(b->oz_rows, total + 128);
+    if (oy) b->oy_rows = std::max(b->oy_rows, ytotal);
     for (int k : kFactorKinds) {
       for (int i = 0; i < count; i++) {
         const Sym& S = nums[i]->sym->S;
         if (l >= S.nlev) continue;
         for (int64_t q = S.task_off[k][l]; q < S.task_off[k][l + 1]; q++) {
           const int32_t* t = &S.tasks[k][4 * q];
-          const int32_t zb = (int32_t)ozbase[i];
+          const int32_t zb = (int32_t)ozbase[i], yb = (int32_t)oybase[i];
           if (k == chol::kTaskAsm) {  // {t, cb, first, end}: target and source range move
             b->tasks[k].insert(b->tasks[k].end(),
                                {t[0] + base[i], t[1], t[2] + src_base[i], t[3] + src_base[i]});
           } else if (k == chol::kTaskSchur128) {  // {s, i0, k0, oz}
             b->tasks[k].insert(b->tasks[k].end(), {t[0] + base[i], t[1], t[2], t[3] + zb});
-          } else if (k == chol::kTaskOzSlice) {   // {s, r0, oz, -}
-            b->tasks[k].insert(b->tasks[k].end(), {t[0] + base[i], t[1], t[2] + zb, t[3]});
+          } else if (k == chol::kTaskOzSlice) {   // {s, r0, oz, y}
+            b->tasks[k].insert(b->tasks[k].end(), {t[0] + base[i], t[1], t[2] + zb, t[3] + yb});
+          } else if (k == chol::kTaskPotrf) {     // {s, first_bwd, nbwd, y or -1}
+            b->tasks[k].insert(b->tasks[k].end(),
+                               {t[0] + base[i], t[1], t[2], t[3] >= 0 ? t[3] + yb : -1});
           } else {
             b->tasks[k].insert(b->tasks[k].end(), {t[0] + base[i], t[1], t[2], t[3]});
           }
@@ -203,9 +219,13 @@ int chol_batch_create(chol_ctx* c, int count, chol_num* const* nums, chol_batch*
         !(rc = dev_alloc(c, (void**)&b->d_mat, mats.size() * sizeof(MatDev))) &&
         !(rc = dev_alloc(c, (void**)&b->d_ctr, factor_counters(b->nlev) * sizeof(int))) &&
         !(b->oz_rows > 0 &&
-          (rc = dev_alloc(c, &b->d_oz, chol::oz_scratch_bytes(b->oz_rows))))) {
-      if (b->d_oz && cudaMemsetAsync(b->d_oz, 0, chol::oz_scratch_bytes(b->oz_rows), c->stream) !=
-                         cudaSuccess)
+          (rc = dev_alloc(c, &b->d_oz, chol::oz_scratch_bytes(b->oz_rows)))) &&
+        !(b->oy_rows > 0 &&
+          (rc = dev_alloc(c, &b->d_oy, chol::oy_scratch_bytes(b->oy_rows))))) {
+      if ((b->d_oz && cudaMemsetAsync(b->d_oz, 0, chol::oz_scratch_bytes(b->oz_rows),
+                                      c->stream) != cudaSuccess) ||
+          (b->d_oy && cudaMemsetAsync(b->d_oy, 0, chol::oy_scratch_bytes(b->oy_rows),
+                                      c->stream) != cudaSuccess))
         rc = CHOL_E_CUDA;
       if ((ab && cudaMemcpyAsync(b->d_asm_src, b->asm_src.data(), ab, cudaMemcpyHostToDevice,
                                  c->stream) != cudaSuccess) ||
@@ -429,8 +449,13 @@ int chol_sym_set_tile_policy(chol_sym* s, const chol_tile_policy* p) {
   if (!s->ctx) return CHOL_OK;
   chol_ctx* c = s->ctx;
   if (cudaSetDevice(c->opts.device) != cudaSuccess) return CHOL_E_NODEVICE;
-  for (int cls = 0; cls <= chol::kNumTileClasses; cls++) {  // the Schur kinds, then slices
-    const int k = cls < chol::kNumTileClasses ? chol::schur_kind(cls) : chol::kTaskOzSlice;
+  // the lists the tile classes decide: the Schur kinds, the slices, the TRSM without the
+  // 128-tile supernodes, and POTRF (whose tasks record the inverses' slice rows)
+  const int kinds[] = {chol::schur_kind(0), chol::schur_kind(1), chol::schur_kind(2),
+                       chol::schur_kind(3), chol::kTaskOzSlice, chol::kTaskTrsmRest,
+                       chol::kTaskPotrf};
+  static_assert(chol::kNumTileClasses == 4, "one Schur kind per tile class");
+  for (int k : kinds) {
     dev_free(c, s->dev.tasks[k]);
     s->dev.tasks[k] = nullptr;
     const size_t bytes = s->S.tasks[k].size() * sizeof(int32_t);

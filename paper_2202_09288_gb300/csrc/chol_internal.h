@@ -29,6 +29,7 @@ constexpr int kMaxWidth = 128;   // hard limit on the width cap W (diagonal bloc
 // The representation error is below 2^-57 of the row maximum.
 constexpr int kOzSlices = 8;
 constexpr int kOzRowBytes = 128;  // one slice row: 64 bf16 (K <= 64), 128-byte swizzled
+constexpr int kOzInvRows = 64;    // slice rows of a diagonal-block inverse (n <= 64, zero-padded)
 enum SchurClass { kTile64 = 0, kTile32 = 1, kTile16 = 2, kTile128 = 3, kNumTileClasses = 4 };
 inline int tile_of_class(int c) {
   return c == kTile128 ? 128 : (c == kTile64 ? 64 : (c == kTile32 ? 32 : 16));
@@ -36,7 +37,8 @@ inline int tile_of_class(int c) {
 
 // Task kinds of the per-level schedule.  Every task is an int4 {s, a, b, c}.
 enum TaskKind {
-  kTaskPotrf = 0,   // {s, first_bwd, nbwd, -}: diagonal block of s; its backward tasks
+  kTaskPotrf = 0,   // {s, first_bwd, nbwd, y}: diagonal block of s; its backward tasks; y: the
+                    //   first row of its inverse's slices (128-tile supernodes) or -1
   kTaskTrsm = 1,    // {s, r0, -, -}: L21 rows r0 .. r0+kTrsmRows of s
   kTaskSchur64 = 2, // {s, i0, k0, -}: tile of U_s (rows i0.., cols k0.., offsets into L21)
   kTaskSchur32 = 3,
@@ -45,8 +47,10 @@ enum TaskKind {
   kTaskBwd = 6,     // {s, r0, -, -}: backward-solve partial block
   kTaskAsm = 7,     // {t, cb, first, end}: owner assembly group (see Sym::asm_src)
   kTaskSchur128 = 8,  // {s, i0, k0, oz}: 128 x 128 tile of U_s; oz = first slice row of s
-  kTaskOzSlice = 9,   // {s, r0, oz, -}: slices of L21 rows r0 .. r0+127 of s (FP64 only)
-  kNumTaskKinds = 10
+  kTaskOzSlice = 9,   // {s, r0, oz, y}: slices of rows r0 .. r0+127 of s's A21 or L21 (FP64
+                      //   only); the same rows' tensor-core TRSM with the inverse's slices at y
+  kTaskTrsmRest = 10, // {s, r0, -, -}: kTaskTrsm without the 128-tile supernodes
+  kNumTaskKinds = 11
 };
 inline int schur_kind(int cls) { return cls == kTile128 ? kTaskSchur128 : kTaskSchur64 + cls; }
 
@@ -149,6 +153,9 @@ struct Sym {
   // and the largest level's count plus one tile of slack (rows a tile may read past u)
   std::vector<int64_t> lvl_ozrows;
   int64_t oz_rows = 0;
+  // slice rows of the 128-tile supernodes' diagonal-block inverses (64 per supernode)
+  std::vector<int64_t> lvl_oyrows;
+  int64_t oy_rows = 0;
   std::vector<int64_t> sn_ustage;  // ns
   // sources of the owner-assembly groups: {s, kb, ke, 0}, columns [kb, ke) of U_s
   std::vector<int32_t> asm_src;

@@ -21,6 +21,7 @@
 #include "kernels.h"
 #include "launch_util.h"
 #include "device_common.cuh"
+#include "oz_common.cuh"
 
 namespace chol {
 
@@ -91,6 +92,11 @@ __device__ __forceinline__ void build_update_table(uint16_t* tab, int n) {
 }
 __host__ __device__ constexpr size_t update_table_bytes(int w) {
   return w > 2 ? (size_t)(w - 2) * (w - 1) / 2 * sizeof(uint16_t) : 0;
+}
+// FP64 POTRF's shared memory: the block (w^2 doubles), the update table, then (8-byte
+// aligned) the w reciprocals of the diagonal that the in-place inverse uses
+__host__ __device__ constexpr size_t potrf_rd_offset(int w) {
+  return ((size_t)w * w * sizeof(double) + update_table_bytes(w) + 7) / 8 * 8;
 }
 
 // Right-looking Cholesky of the n x n block A (shared memory, column-major A[c * n + r]; only
@@ -182,16 +188,88 @@ __device__ __forceinline__ void store_diag_block(T* __restrict__ L, const S* A, 
     for (int r = c + lane; r < n; r += 32) L[(int64_t)c * m + r] = (T)A[c * n + r];
 }
 
+// Y = L11^-1 in place in A (n x n, column-major, L11 in the lower triangle), by forward
+// substitution on all columns of the identity at once: with l'_ij = L_ij / L_jj and Z = I, step
+// j (one barrier) takes Z[i, c] -= l'_ij Z[j, c] for the rows i > j and columns c <= j (row j
+// is final by then); Y[i, c] = Z[i, c] / L_ii.  l' lives in the strict lower triangle and the
+// lower-triangular Z transposed in the upper triangle and the diagonal (Z[i, c] at
+// A[i * n + c]), so that a warp's threads update consecutive words; on return A holds Y
+// row-major (A[r * n + c] = Y[r, c], zeros above the diagonal).  rd: n doubles.
+__device__ void invert_lower_inplace(double* A, double* rd, int n) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rd[j] = 1.0 / A[j * n + j];
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int c = idx / n, r = idx - c * n;
+    if (r > c) A[idx] *= rd[c];          // l'_rc
+    else A[idx] = r == c ? 1.0 : 0.0;    // Z[c, r] = I
+  }
+  __syncthreads();
+  for (int j = 0; j + 1 < n; j++) {
+    const int cols = j + 1, rows = n - 1 - j;
+    for (int idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
+      const int ii = idx / cols, c = idx - ii * cols, i = j + 1 + ii;
+      A[i * n + c] -= A[j * n + i] * A[j * n + c];
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx / n, c = idx - r * n;
+    A[idx] = c <= r ? A[idx] * rd[r] : 0.0;
+  }
+  __syncthreads();
+}
+
+// The kOzInvRows slice rows of Y S (Y row-major in A, n x n; rows and columns past n are zero;
+// S = diag(2^t_k), t_k the exponent of L11[k,k]) at slice rows y0 .. y0+63 of the scratch oy
+// (planes oy_rows rows apart, then the rows' exponents, then the column shifts t_k): the
+// right-hand operand of the supernode's tensor-core TRSM, A21 Y^T = (A21 S^-1)(Y S)^T.  The
+// shift balances the operands: a column k of Y scales like 1/L_kk and the same column of A21
+// like L_kk (rows and columns of A may span many decades), while Y S is the inverse of the
+// unit-diagonal factor (exact: powers of two).  t: the n shifts; e: kOzInvRows ints.
+__device__ void slice_inverse(const double* A, int n, const int* t, uint8_t* oy,
+                              int64_t oy_rows, int64_t y0, int* e) {
+  const size_t stride = (size_t)oy_rows * kOzRowBytes;
+  int32_t* oexp = reinterpret_cast<int32_t*>(oy + kOzSlices * stride);
+  for (int r = threadIdx.x; r < kOzInvRows; r += blockDim.x) {
+    int f = 0;  // the largest exponent field of the row of Y S (fields shifted by t_k)
+    if (r < n)
+      for (int c = 0; c <= r; c++) {
+        const int fc = oz_exp_field(A[r * n + c]);
+        if (fc > 0) f = max(f, fc + t[c]);
+      }
+    e[r] = oz_row_exponent(f);
+    oexp[y0 + r] = e[r];
+    oexp[oy_rows + y0 + r] = r < n ? t[r] : 0;
+  }
+  __syncthreads();
+  for (int item = threadIdx.x; item < kOzInvRows * 8; item += blockDim.x) {
+    const int r = item >> 3, pc = item & 7;  // row, physical 16-byte chunk
+    const int c = pc ^ (int)((y0 + r) & 7);  // logical chunk: columns 8c .. 8c+7
+    long long R[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int k = 8 * c + j;
+      R[j] = r < n && k < n ? oz_fixed(A[r * n + k], e[r] - t[k]) : 0;  // Y[r,k] 2^t_k
+    }
+    oz_write_chunk(R, oy + (size_t)(y0 + r) * kOzRowBytes + pc * 16, stride);
+  }
+}
+
 // ---- POTRF of each diagonal block ---------------------------------------------------------
 // One CTA (kPotrfThreads threads) per supernode; the n x n block is factored in shared memory by
 // potrf_lookahead.  A non-positive pivot is an error (not SPD), recorded with its column.
+// With oy, a task whose y field is set (a 128-tile supernode of the FP64 factor) also forms
+// Y = L11^-1 (into d.dinv, row-major, for the solves) and Y's slices at rows y .. y+63 of oy,
+// the operand of its tensor-core TRSM.
 template <typename T>
 __global__ void __launch_bounds__(kPotrfThreads) k_potrf(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
                                                const SnDev* __restrict__ sns,
-                                               const MatDev* __restrict__ mats) {
+                                               const MatDev* __restrict__ mats,
+                                               uint8_t* __restrict__ oy, int64_t oy_rows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   __shared__ int s_next_task;
+  __shared__ int s_e[kOzInvRows], s_t[kOzInvRows];
   for (int tq = blockIdx.x; tq < ntasks;) {
     const int4 tk = tasks[tq];
     const SnDev d = sns[tk.x];
@@ -206,6 +284,22 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf(const int4* __restrict_
     if (bad < n && threadIdx.x == 0) record_error(mats[d.mat], d.col0 + bad);
     store_diag_block(L, A, n, m);
     __syncthreads();
+    if constexpr (sizeof(T) == 8) {
+      if (oy && tk.w >= 0 && d.dinv && n <= kOzInvRows) {
+        double* Ad = reinterpret_cast<double*>(A);
+        double* rd = reinterpret_cast<double*>(smem_raw + potrf_rd_offset(n));
+        // column shifts t_k: the exponent of L11[k,k] (|L_kk| in [2^t, 2^(t+1)))
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+          const int f = oz_exp_field(Ad[k * n + k]);
+          s_t[k] = f > 0 ? f - 1023 : 0;
+        }
+        invert_lower_inplace(Ad, rd, n);
+        double* Y = reinterpret_cast<double*>(d.dinv);
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Y[idx] = Ad[idx];
+        slice_inverse(Ad, n, s_t, oy, oy_rows, tk.w, s_e);
+        __syncthreads();
+      }
+    }
     // a CTA's first task is its block index; only a grid smaller than the task list makes
     // CTAs take further tasks from this launch's work queue
     if (gridDim.x >= ntasks) break;
@@ -732,7 +826,7 @@ void launch_assemble(const double* vals, const int64_t* amap, int64_t nnz, void*
   else k_assemble<double><<<blocks, 256, 0, st>>>(vals, amap, nnz, (double*)L);
 }
 
-static size_t potrf_smem(int w) { return (size_t)w * w * sizeof(double) + update_table_bytes(w); }
+static size_t potrf_smem(int w) { return potrf_rd_offset(w) + (size_t)w * sizeof(double); }
 
 constexpr int kDinvThreads = 256;
 template <typename P>
@@ -753,10 +847,12 @@ constexpr size_t dinv_smem() {
 // instruction holds its warp ~64 cycles, so a 64-step substitution chain costs ~10 us).
 template <typename P>
 __global__ void __launch_bounds__(kDinvThreads)
-    k_diag_inverse(const int4* __restrict__ tasks, const SnDev* __restrict__ sns) {
+    k_diag_inverse(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
+                   bool skip_sliced) {
   extern __shared__ __align__(16) double dsm[];
-  const SnDev d = sns[tasks[blockIdx.x].x];
-  if (!d.dinv) return;
+  const int4 tk = tasks[blockIdx.x];
+  const SnDev d = sns[tk.x];
+  if (!d.dinv || (skip_sliced && tk.w >= 0)) return;
   const int n = d.n;
   P* S = reinterpret_cast<P*>(dsm);
   P* rd = S + n * n;
@@ -787,12 +883,13 @@ __global__ void __launch_bounds__(kDinvThreads)
 }
 
 void launch_diag_inverse(const int4* tasks, int ntasks, const SnDev* sns, bool f32,
-                         cudaStream_t st) {
+                         bool skip_sliced, cudaStream_t st) {
   if (ntasks <= 0) return;
   if (f32)
-    k_diag_inverse<float><<<ntasks, kDinvThreads, dinv_smem<float>(), st>>>(tasks, sns);
+    k_diag_inverse<float><<<ntasks, kDinvThreads, dinv_smem<float>(), st>>>(tasks, sns, false);
   else
-    k_diag_inverse<double><<<ntasks, kDinvThreads, dinv_smem<double>(), st>>>(tasks, sns);
+    k_diag_inverse<double><<<ntasks, kDinvThreads, dinv_smem<double>(), st>>>(tasks, sns,
+                                                                             skip_sliced);
 }
 static size_t potrf_mixed_smem(int w) {  // the FP64 block of a redo overlays the FP32 one
   return (size_t)w * w * sizeof(double) + update_table_bytes(w);
@@ -800,7 +897,8 @@ static size_t potrf_mixed_smem(int w) {  // the FP64 block of a redo overlays th
 static size_t trsm_smem(int w) { return ((size_t)w * w + w + (size_t)w * 32) * sizeof(double); }
 
 void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
-                  const MatDev* mats, int max_width, bool f32, float tau, cudaStream_t st) {
+                  const MatDev* mats, int max_width, bool f32, float tau, void* oy,
+                  int64_t oy_rows, cudaStream_t st) {
   if (ntasks <= 0) return;
   if (f32) {
     const size_t sm = potrf_mixed_smem(max_width);
@@ -809,7 +907,7 @@ void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
   } else {
     const size_t sm = potrf_smem(max_width);
     k_potrf<double><<<task_grid(k_potrf<double>, kPotrfThreads, sm, ntasks), kPotrfThreads, sm, st>>>(
-        tasks, ntasks, queue, sns, mats);
+        tasks, ntasks, queue, sns, mats, static_cast<uint8_t*>(oy), oy_rows);
   }
 }
 

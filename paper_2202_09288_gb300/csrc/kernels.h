@@ -10,16 +10,20 @@ namespace chol {
 
 void launch_assemble(const double* vals, const int64_t* amap, int64_t nnz, void* L, bool f32,
                      cudaStream_t st);
-// Task launches are persistent: at most one wave of CTAs, each taking its next task from the
-// zero-initialized work-queue counter `queue` (one counter per launch).
+// Task launches run one CTA per task (launch_util.h); a grid smaller than the task list would
+// take further tasks from the zero-initialized work-queue counter `queue` (one per launch).
 // Widest supernode whose diagonal-block inverse the factor keeps (for the solves).
 constexpr int kDinvMaxWidth = 64;
 // Y = L11^-1 of every supernode of a POTRF task list whose descriptor has dinv set (the
-// blocks are final: after launch_potrf of the same level).
+// blocks are final: after launch_potrf of the same level); with skip_sliced, not those whose
+// task has its y field set (FP64 POTRF formed their Y already).
 void launch_diag_inverse(const int4* tasks, int ntasks, const SnDev* sns, bool f32,
-                         cudaStream_t st);
+                         bool skip_sliced, cudaStream_t st);
+// oy: with the FP64 factor's tensor-core TRSM, the zeroed scratch (oz_scratch_bytes(oy_rows))
+// that receives the slices of the 128-tile supernodes' Y = L11^-1 (tasks with y set); else null
 void launch_potrf(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
-                  const MatDev* mats, int max_width, bool f32, float tau, cudaStream_t st);
+                  const MatDev* mats, int max_width, bool f32, float tau, void* oy,
+                  int64_t oy_rows, cudaStream_t st);
 void launch_trsm(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int max_width,
                  bool f32, cudaStream_t st);
 void launch_schur(int cls, const int4* tasks, int ntasks, int* queue, const SnDev* sns,
@@ -47,12 +51,22 @@ int set_tc_kernel_attrs();
 // FP64 128 x 128 Schur tiles on the bf16 tensor cores by operand splitting, oz_kernels.cu:
 // per level, first the slices of every 128-tile supernode's L21 (kTaskOzSlice tasks), then
 // the tiles.  oz is a zeroed scratch of oz_scratch_bytes(oz_rows) bytes.
+// oy: null for the Schur tiles' L21; for the tensor-core TRSM's A21, the inverses' scratch
+// (the columns are scaled by the shifts POTRF stored there)
 void launch_oz_slice(const int4* tasks, int ntasks, const SnDev* sns, void* oz, int64_t oz_rows,
-                     cudaStream_t st);
+                     const void* oy, int64_t oy_rows, cudaStream_t st);
 void launch_schur_oz(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
                      const MatDev* mats, bool owner, const void* oz, int64_t oz_rows,
                      long long acc_wait, cudaStream_t st);
+// L21 = A21 Y^T of the 128-tile supernodes on the bf16 tensor cores (kTaskOzSlice tasks: 128
+// rows each): A21's slices from launch_oz_slice with oy on the panel before this launch, Y's
+// slices from launch_potrf (oy); writes L21 into the panels.
+void launch_trsm_oz(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
+                    const void* oz, int64_t oz_rows, const void* oy, int64_t oy_rows,
+                    cudaStream_t st);
 size_t oz_scratch_bytes(int64_t oz_rows);
+// the inverses' slice scratch: slice planes, row exponents, then one column shift per row
+size_t oy_scratch_bytes(int64_t oy_rows);
 int set_oz_kernel_attrs();
 
 void launch_gather_perm(const double* B, int64_t ldb, const int32_t* perm, const double* scale,

@@ -33,6 +33,7 @@
 #include "chol_internal.h"
 #include "device_common.cuh"
 #include "kernels.h"
+#include "oz_common.cuh"
 #include "launch_util.h"
 
 namespace chol {
@@ -130,26 +131,6 @@ __device__ __forceinline__ void oz_commit(uint32_t bar) {
 
 }  // namespace
 
-// bf16 bits of an integer of magnitude at most 256 (exact).
-__device__ __forceinline__ uint32_t oz_bf16_of_int(int v) {
-  if (v == 0) return 0u;
-  const uint32_t a = (uint32_t)(v < 0 ? -v : v);
-  const int e = 31 - __clz(a);  // a in [2^e, 2^(e+1))
-  return (v < 0 ? 0x8000u : 0u) | ((uint32_t)(127 + e) << 7) | ((a << (7 - e)) & 0x7Fu);
-}
-
-// x 2^(56 - e) as an integer (|x| < 2^e, so |result| < 2^56), truncated toward zero below
-// 2^0 (an error below 2^(e-56)); subnormal x give 0.
-__device__ __forceinline__ long long oz_fixed(double x, int e) {
-  const long long bits = __double_as_longlong(x);
-  const int exb = (int)((bits >> 52) & 0x7FF);
-  if (exb == 0) return 0;
-  const long long mant = (bits & ((1ll << 52) - 1)) | (1ll << 52);  // x = mant 2^(exb-1075)
-  const int sh = exb - 1019 - e;
-  const long long M = sh >= 0 ? mant << sh : (sh > -64 ? mant >> -sh : 0);
-  return bits < 0 ? -M : M;
-}
-
 constexpr int kOzSliceThreads = 256;
 constexpr int kOzSliceLd = kOzM + 1;  // padded column stride of the staged block
 
@@ -159,11 +140,14 @@ constexpr int kOzSliceLd = kOzM + 1;  // padded column stride of the staged bloc
 // entry becomes the 56-bit fixed-point integer x 2^(56-e_r), cut into 8 balanced digits
 // of 7 bits (round to nearest: |s_0| <= 128, |s_p| <= 64, exact); thread t writes the
 // 16-byte chunk t % 8 of row t / 8 of every slice (coalesced, pre-swizzled).
+// With oy (the tensor-core TRSM's operand A21 S^-1, sliced before that TRSM), column k is
+// scaled by 2^-t_k, the shift POTRF stored with the supernode's inverse slices in oy.
 __global__ void __launch_bounds__(kOzSliceThreads)
     k_oz_slice(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
-               uint8_t* __restrict__ oz, int64_t oz_rows) {
+               uint8_t* __restrict__ oz, int64_t oz_rows, const uint8_t* __restrict__ oy,
+               int64_t oy_rows) {
   extern __shared__ __align__(16) double xs[];  // [n][kOzSliceLd]
-  __shared__ int s_e[kOzM];
+  __shared__ int s_e[kOzM], s_t[kOzInvRows];
   const int4 tk = tasks[blockIdx.x];
   const SnDev d = sns[tk.x];
   const int n = d.n, m = d.m, u = m - n;
@@ -172,6 +156,14 @@ __global__ void __launch_bounds__(kOzSliceThreads)
   const double* L = reinterpret_cast<const double*>(d.L) + n + r0;  // L21[r0 + i, k] = L[k m + i]
   static_assert(kOzM == 128, "stage_row_block stages 128 rows");
   stage_row_block(xs, kOzSliceLd, L, m, n, u - r0);
+  if (threadIdx.x < kOzInvRows) {
+    // the shifts follow the inverse slices' row exponents in oy
+    const int32_t* shift =
+        oy ? reinterpret_cast<const int32_t*>(oy + kOzSlices * (size_t)oy_rows * kOzRowBytes) +
+                 oy_rows + tk.w
+           : nullptr;
+    s_t[threadIdx.x] = shift && threadIdx.x < n ? shift[threadIdx.x] : 0;
+  }
   cp_async_wait_all();
   __syncthreads();
   const int64_t row0 = tk.z + (int64_t)r0;
@@ -181,10 +173,12 @@ __global__ void __launch_bounds__(kOzSliceThreads)
     // the largest entry's exponent field by integer comparison (the FP64 unit is slow):
     // max |x| = f 2^e with f in [0.5, 1) has e = field - 1022 (0 for rows of zeros and
     // subnormals, whose slices are zero)
-    int emax = 0;
-    for (int k = 0; k < n; k++)
-      emax = max(emax, (int)((__double_as_longlong(xs[k * kOzSliceLd + i]) >> 52) & 0x7FF));
-    const int e = emax > 0 ? emax - 1022 : 0;
+    int emax = 0;  // of the row scaled by 2^-t_k (exponent fields shifted by -t_k)
+    for (int k = 0; k < n; k++) {
+      const int f = oz_exp_field(xs[k * kOzSliceLd + i]);
+      if (f > 0) emax = max(emax, f - s_t[k]);
+    }
+    const int e = oz_row_exponent(emax);
     s_e[i] = e;
     if (i < rows) reinterpret_cast<int32_t*>(oz + kOzSlices * stride)[row0 + i] = e;
   }
@@ -198,31 +192,9 @@ __global__ void __launch_bounds__(kOzSliceThreads)
 #pragma unroll
     for (int j = 0; j < 8; j++) {
       const int k = 8 * c + j;
-      R[j] = k < n ? oz_fixed(xs[k * kOzSliceLd + i], e) : 0;
+      R[j] = k < n ? oz_fixed(xs[k * kOzSliceLd + i], e + s_t[k]) : 0;  // x 2^-t_k
     }
-    uint8_t* dst = oz + (size_t)(row0 + i) * kOzRowBytes + pc * 16;
-#pragma unroll
-    for (int p = 0; p < kOzSlices; p++) {
-      const int w = 49 - 7 * p;  // weight of digit p: 2^w
-      uint32_t h[8];
-#pragma unroll
-      for (int j = 0; j < 8; j++) {
-        long long dgt;
-        if (p + 1 < kOzSlices) {
-          dgt = (R[j] + (1ll << (w - 1))) >> w;
-          R[j] -= dgt << w;
-        } else {
-          dgt = R[j];  // the last digit takes the exact remainder (|R| <= 2^6)
-        }
-        h[j] = oz_bf16_of_int((int)dgt);
-      }
-      uint4 v;
-      v.x = h[0] | (h[1] << 16);
-      v.y = h[2] | (h[3] << 16);
-      v.z = h[4] | (h[5] << 16);
-      v.w = h[6] | (h[7] << 16);
-      *reinterpret_cast<uint4*>(dst + p * stride) = v;
-    }
+    oz_write_chunk(R, oz + (size_t)(row0 + i) * kOzRowBytes + pc * 16, stride);
   }
 }
 
@@ -741,11 +713,153 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                  "r"(kOzTmemCols));
 }
 
+// ---- TRSM of the 128-tile supernodes on the tensor cores ----------------------------------
+// L21 = A21 L11^{-T} = A21 Y^T with Y = L11^{-1}, formed by POTRF, which also stored the
+// slices of Y S (S = diag(2^t_k), t_k the exponent of L11[k,k]) and the shifts t_k in oy; the
+// slices of A21 S^-1 come from the slicing kernel run on the panel just before.  L21 =
+// (A21 S^-1)(Y S)^T is a product of row-sliced operands of exactly the Schur tiles' form,
+// L21[i, j] = 2^(e_i + e_j) sum_{p+q<8} 2^(-7(p+q+2)) sum_k a_p[i,k] y_q[j,k], K = n <= 64, so
+// every diagonal's partial sums are integers below 2^22 (exact in FP32) and the combination is
+// the same integer one.  One CTA per task (128 rows of A21): one thread bulk-copies the task's
+// 8 A slices (128 KB) and Y's 8 slices (64 rows each, 64 KB), then issues, per K step and A
+// slice p, the MMAs of A_p against Y slices 0 .. 7-p in one go (N = (8-p) 64, at most 256 per
+// MMA): diagonal p + q lands at TMEM columns (p + q) 64, the 8 diagonals fill the 512 columns.
+// Eight warps then read the accumulators (warp w: TMEM lanes 32 (w & 3) .., columns
+// 32 (w >> 2) ..), combine them exactly, round once to FP64 and store L21 into the panel.
+// (Forming the slices inside this kernel as well was measured slower: one CTA per SM then
+// serializes the slicing, the copies and the tensor work, which separate launches overlap.)
+// Waits are bounded as in the Schur tiles; a timeout is recorded in err[3] and nothing stored.
+constexpr int kToThreads = 256;
+constexpr uint32_t kToBSlice = kOzInvRows * kOzRowBytes;  // 8 KB: one slice of Y's rows
+constexpr uint32_t kToBBytes = kOzSlices * kToBSlice;      // 64 KB
+constexpr size_t kToSmem = 1024 + kOzABytes + kToBBytes;   // + alignment slack
+constexpr uint32_t kToTmemCols = kOzSlices * kOzInvRows;   // 512
+
+__global__ void __launch_bounds__(kToThreads, 1)
+    k_trsm_oz(const int4* __restrict__ tasks, const SnDev* __restrict__ sns,
+              const MatDev* __restrict__ mats, const uint8_t* __restrict__ oz, int64_t oz_rows,
+              const uint8_t* __restrict__ oy, int64_t oy_rows) {
+  extern __shared__ __align__(1024) unsigned char to_sm[];
+  unsigned char* A =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(to_sm) + 1023) & ~uintptr_t(1023));
+  unsigned char* B = A + kOzABytes;
+  __shared__ __align__(8) uint64_t full, done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int4 tk = tasks[blockIdx.x];
+  const SnDev d = sns[tk.x];
+  unsigned long long* err = mats[d.mat].err;
+  // a launch of this factorization already gave up on a wait: skip (before any set-up)
+  if (*(volatile unsigned long long*)(err + 3) != 0) return;
+  const int n = d.n, m = d.m, u = m - n, r0 = tk.y;
+  const int rb = min(kOzM, u - r0);
+  const size_t sa = (size_t)oz_rows * kOzRowBytes, sb = (size_t)oy_rows * kOzRowBytes;
+  const int32_t* ea = reinterpret_cast<const int32_t*>(oz + kOzSlices * sa);
+  const int32_t* ey = reinterpret_cast<const int32_t*>(oy + kOzSlices * sb);
+  const int64_t arow = (int64_t)tk.z + r0, yrow = tk.w;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(kToTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    const uint32_t fb = smem_u32(&full);
+    oz_expect(fb, kOzABytes + kToBBytes);
+    for (int p = 0; p < kOzSlices; p++)
+      oz_bulk_load(smem_u32(A + p * kOzASlice), oz + p * sa + (size_t)arow * kOzRowBytes,
+                   kOzASlice, fb);
+    for (int p = 0; p < kOzSlices; p++)
+      oz_bulk_load(smem_u32(B + p * kToBSlice), oy + p * sb + (size_t)yrow * kOzRowBytes,
+                   kToBSlice, fb);
+    if (oz_wait(fb, 0)) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint64_t da = oz_desc(smem_u32(A)), db = oz_desc(smem_u32(B));
+      const int ks = (n + 15) >> 4;
+      // K step outer, A slice inner (consecutive MMAs start at different diagonals); the
+      // first K step of slice 0 writes every diagonal, everything after accumulates
+      for (int k = 0; k < ks; k++)
+        for (int p = 0; p < kOzSlices; p++)
+          for (int q0 = 0; q0 < kOzSlices - p; q0 += 4) {
+            const int nq = min(4, kOzSlices - p - q0);
+            oz_mma(tmem + (uint32_t)((p + q0) * kOzInvRows),
+                   da + (uint64_t)((p * kOzASlice) >> 4) + 2 * k,
+                   db + (uint64_t)((q0 * kToBSlice) >> 4) + 2 * k, oz_idesc(nq * kOzInvRows),
+                   (p > 0 || k > 0) ? 1u : 0u);
+          }
+      oz_commit(smem_u32(&done));
+    } else {
+      s_fail = 1;
+      oz_arrive(smem_u32(&done));
+      oz_wait(fb, 0);  // bounded: the copies in flight
+    }
+  }
+  if (!oz_wait(smem_u32(&done), 0)) s_fail = 1;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
+  if (!s_fail) {  // uniform: the warps' TMEM loads are collective
+    const int lq = warp & 3, ch = warp >> 2;
+    const int i = 32 * lq + lane;  // this thread's row of the task
+    const int eA = i < rb ? ea[arow + i] - 55 : 0;
+    double* out = reinterpret_cast<double*>(d.L) + n + r0 + i;
+    for (int c8 = 0; c8 < 4; c8++) {
+      const int col0 = 32 * ch + 8 * c8;
+      uint32_t v[kOzSlices][8];
+#pragma unroll
+      for (int dd = 0; dd < kOzSlices; dd++)
+        oz_tmem_load8(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(dd * kOzInvRows + col0), v[dd]);
+      oz_tmem_wait();
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int col = col0 + j;
+        if (i < rb && col < n) {
+          const unsigned long long lo =
+              oz_low(oz_fbits(v[4][j]), oz_fbits(v[5][j]), oz_fbits(v[6][j]), oz_fbits(v[7][j]));
+          const long long W =
+              oz_high(lo, oz_fbits(v[0][j]), oz_fbits(v[1][j]), oz_fbits(v[2][j]), oz_fbits(v[3][j]));
+          out[(int64_t)col * m] = oz_to_double<false>(W, eA + ey[yrow + col]);
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicAdd(err + 3, 1ull);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kToTmemCols));
+}
+
+void launch_trsm_oz(const int4* tasks, int ntasks, const SnDev* sns, const MatDev* mats,
+                    const void* oz, int64_t oz_rows, const void* oy, int64_t oy_rows,
+                    cudaStream_t st) {
+  if (ntasks <= 0) return;
+  k_trsm_oz<<<ntasks, kToThreads, kToSmem, st>>>(tasks, sns, mats,
+                                                 static_cast<const uint8_t*>(oz), oz_rows,
+                                                 static_cast<const uint8_t*>(oy), oy_rows);
+}
+
 void launch_oz_slice(const int4* tasks, int ntasks, const SnDev* sns, void* oz, int64_t oz_rows,
-                     cudaStream_t st) {
+                     const void* oy, int64_t oy_rows, cudaStream_t st) {
   if (ntasks <= 0) return;
   k_oz_slice<<<ntasks, kOzSliceThreads, (size_t)64 * kOzSliceLd * sizeof(double), st>>>(
-      tasks, sns, static_cast<uint8_t*>(oz), oz_rows);
+      tasks, sns, static_cast<uint8_t*>(oz), oz_rows, static_cast<const uint8_t*>(oy), oy_rows);
+}
+
+size_t oy_scratch_bytes(int64_t oy_rows) {
+  return oz_scratch_bytes(oy_rows) + (size_t)oy_rows * sizeof(int32_t);
 }
 
 void launch_schur_oz(const int4* tasks, int ntasks, int* queue, const SnDev* sns,
@@ -775,7 +889,9 @@ int set_oz_kernel_attrs() {
       cudaFuncSetAttribute(k_schur_oz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kOzSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_schur_oz<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kOzSmem) != cudaSuccess)
+                           (int)kOzSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_trsm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kToSmem) != cudaSuccess)
     return CHOL_E_CUDA;
   return CHOL_OK;
 }

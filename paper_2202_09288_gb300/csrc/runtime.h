@@ -21,14 +21,14 @@ enum ProfKindId {
   kProfAssemble, kProfPotrf, kProfTrsm, kProfSchur64, kProfSchur32, kProfSchur16,
   kProfAsmOwner, kProfFwd, kProfBwd, kProfPerm, kProfScale, kProfPotrfF32, kProfTrsmF32,
   kProfSchur64F32, kProfSchur32F32, kProfSchur16F32, kProfRefine, kProfGraph, kProfSchur128,
-  kProfSchur128Tc, kProfOzSlice, kProfSchur128Oz, kProfDinv, kNumProf
+  kProfSchur128Tc, kProfOzSlice, kProfSchur128Oz, kProfDinv, kProfTrsmOz, kNumProf
 };
 inline const char* const kProfNames[kNumProf] = {
     "assemble",    "potrf_f64",   "trsm_f64",    "schur64_f64",  "schur32_f64",
     "schur16_f64", "assemble_owner", "solve_fwd", "solve_bwd",   "solve_perm",
     "equilibrate", "potrf_f32",   "trsm_f32",    "schur64_f32",  "schur32_f32",
     "schur16_f32", "refine",      "batch_graph", "schur128_f64", "schur128_tc",
-    "oz_slice",    "schur128_oz", "diag_inverse"};
+    "oz_slice",    "schur128_oz", "diag_inverse", "trsm_oz"};
 
 // Tracing kind of a Schur tile class (oz: FP64 128-tiles on the bf16 tensor cores).
 inline int prof_schur_kind(int cls, bool f32, bool oz = false) {
@@ -116,6 +116,8 @@ struct chol_num {
   void* d_oz = nullptr;        // FP64 tensor-core Schur: operand slices (zeroed scratch)
   void* d_dinv = nullptr;      // inverses of the diagonal blocks (W <= 64; panel precision)
   int64_t oz_cap = 0;          // slice rows d_oz holds
+  void* d_oy = nullptr;        // FP64 tensor-core TRSM: slices of the diagonal-block inverses
+  int64_t oy_cap = 0;          // slice rows d_oy holds
   // solve workspace, grown on demand
   int64_t ws_nrhs = 0;
   double* d_y = nullptr;
@@ -174,8 +176,15 @@ inline size_t solve_arrive_offset(const Sym& S) { return 3 * (size_t)S.nlev + 8;
 inline size_t solve_counters(const Sym& S) { return solve_arrive_offset(S) + (size_t)S.ns; }
 // oz / oz_rows: slice scratch of FP64 128-tiles on the bf16 tensor cores (null: those
 // tiles run as 64 x 64 DMMA tiles)
+// oz: the slice scratch of the tensor-core Schur tiles (FP64 slices or TF32 parts); oy (FP64
+// only): the scratch of the diagonal-block inverses' slices, which also selects the
+// tensor-core TRSM of the 128-tile supernodes.
 int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
-                   bool f32, bool owner, int* ctr, void* oz = nullptr, int64_t oz_rows = 0);
+                   bool f32, bool owner, int* ctr, void* oz = nullptr, int64_t oz_rows = 0,
+                   void* oy = nullptr, int64_t oy_rows = 0);
+// Grows a zeroed slice scratch to at least `rows` rows (oz_scratch_bytes, or oy_scratch_bytes
+// for the inverses' slices), freeing the old one only after the stream drains.
+int grow_scratch(chol_ctx* c, void** buf, int64_t* cap, int64_t rows, bool inverses);
 // Whether FP64 factors of sym under c's options use the bf16 tensor-core Schur tiles.
 bool use_oz(const chol_ctx* c, const chol_sym* sym);
 void fill_descriptors(const chol_num* f, int mat, int32_t sn_base, std::vector<SnDev>* sn,
