@@ -599,6 +599,7 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
   S->lvl_ozrows.assign(S->nlev, 0);
   S->oz_rows = 0;
   S->lvl_oyrows.assign(S->nlev, 0);
+  S->lvl_trsmoz.assign(S->nlev, 0);
   S->oy_rows = 0;
   for (size_t q = 3; q < S->tasks[kTaskPotrf].size(); q += 4) S->tasks[kTaskPotrf][q] = -1;
   // pass 1: every supernode's tile class under the size thresholds
@@ -655,12 +656,15 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
       }
     }
   }
-  // pass 2: the task lists.  A 128-tile supernode (FP64: slices on the tensor cores) also
-  // gets its TRSM on the tensor cores, with the slices of its diagonal block's inverse at
-  // 64 rows of the level's inverse slices (recorded in its POTRF task); the other supernodes'
-  // TRSM tasks form kTaskTrsmRest.
+  // pass 2: the task lists.  A 128-tile supernode (FP64: slices on the tensor cores) on a level
+  // of at least kTrsmOzMinLevel supernodes also gets its TRSM on the tensor cores, with the
+  // slices of its diagonal block's inverse at 64 rows of the level's inverse slices (recorded
+  // in its POTRF task).  A level of one supernode keeps the FP64 TRSM: there the inverse, one
+  // CTA's n^3/6 FP64 multiply-adds, costs as much latency as the FP64 TRSM spread over the
+  // SMs (measured on GB300).  The other supernodes' TRSM tasks form kTaskTrsmRest.
   for (int32_t l = 0; l < S->nlev; l++) {
     int64_t ozrow = 0, oyrow = 0;
+    const bool wide = S->lvl_ptr[l + 1] - S->lvl_ptr[l] >= kTrsmOzMinLevel;
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
       const int32_t s = S->lvl_sn[q];
       const int32_t w = S->sn_start[s + 1] - S->sn_start[s];
@@ -669,17 +673,22 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
       const int cls = whole[s] ? whole_tile_class(u) : cls0[s];
       const int T = tile_of_class(cls), k = schur_kind(cls);
       S->lvl_flops[k][l] += (double)u * (u + 1.0) * w;
+      const bool tc = cls == kTile128 && wide;  // TRSM on the tensor cores
       if (cls == kTile128) {
         for (int32_t i0 = 0; i0 < u; i0 += T)
           for (int32_t k0 = 0; k0 <= i0; k0 += T) push4(S->tasks[k], s, i0, k0, (int32_t)ozrow);
         for (int32_t r0 = 0; r0 < u; r0 += 128)
-          push4(S->tasks[kTaskOzSlice], s, r0, (int32_t)ozrow, (int32_t)oyrow);
-        S->tasks[kTaskPotrf][4 * (size_t)q + 3] = (int32_t)oyrow;
+          push4(S->tasks[kTaskOzSlice], s, r0, (int32_t)ozrow, tc ? (int32_t)oyrow : -1);
         ozrow += (u + 7) / 8 * 8;
-        oyrow += kOzInvRows;
       } else {
         for (int32_t i0 = 0; i0 < u; i0 += T)
           for (int32_t k0 = 0; k0 <= i0; k0 += T) push4(S->tasks[k], s, i0, k0, T);
+      }
+      if (tc) {
+        S->tasks[kTaskPotrf][4 * (size_t)q + 3] = (int32_t)oyrow;
+        oyrow += kOzInvRows;
+        S->lvl_trsmoz[l]++;
+      } else {
         for (int32_t r0 = 0; r0 < u; r0 += kTrsmRows) push4(S->tasks[kTaskTrsmRest], s, r0, 0, 0);
         S->lvl_flops[kTaskTrsmRest][l] += (double)u * w * w;  // kTaskTrsm's count
       }

@@ -311,6 +311,7 @@ TaskView sym_view(const chol_sym* sym) {
     v.flops[k] = S.lvl_flops[k].data();
   }
   v.asm_src = sym->dev.asm_src;
+  v.trsmoz = S.lvl_trsmoz.data();
   v.nlev = S.nlev;
   v.max_width = (int)S.max_width;
   return v;
@@ -349,7 +350,7 @@ int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDe
     }
     // the 128-tile supernodes' TRSM: slices of A21 S^-1, then L21 = A21 Y^T on the tensor
     // cores
-    if (trsm_oz) {
+    if (trsm_oz && v.trsmoz[l] > 0) {
       t = v.level(chol::kTaskOzSlice, l, &cnt);
       if (cnt > 0) {
         prof_begin(c, kProfOzSlice);

@@ -39,6 +39,7 @@ struct chol_batch {
   int64_t oz_rows = 0;
   void* d_oy = nullptr;  // FP64 tensor-core TRSM: slices of the members' inverses
   int64_t oy_rows = 0;
+  std::vector<int32_t> trsmoz;  // per level: the members' tensor-core TRSM supernodes
   int32_t nlev = 0;
   int max_width = 0;
   // captured factorization
@@ -81,6 +82,7 @@ chol::rt::TaskView batch_view(const chol_batch* b) {
     v.flops[k] = b->flops[k].data();
   }
   v.asm_src = b->d_asm_src;
+  v.trsmoz = b->trsmoz.data();
   v.nlev = b->nlev;
   v.max_width = b->max_width;
   return v;
@@ -157,6 +159,7 @@ int chol_batch_create(chol_ctx* c, int count, chol_num* const* nums, chol_batch*
   bool oy = !b->f32 && oz;
   for (int i = 0; i < count; i++) oy = oy && nums[i]->d_dinv != nullptr;
   std::vector<int64_t> ozbase(count), oybase(count);
+  b->trsmoz.assign(b->nlev, 0);
   for (int32_t l = 0; l < b->nlev; l++) {
     int64_t total = 0, ytotal = 0;
     for (int i = 0; i < count; i++) {
@@ -166,6 +169,7 @@ int chol_batch_create(chol_ctx* c, int count, chol_num* const* nums, chol_batch*
       if (l < S.nlev) {
         total += S.lvl_ozrows[l];
         ytotal += S.lvl_oyrows[l];
+        b->trsmoz[l] += S.lvl_trsmoz[l];
       }
     }
     if (oz && total > 0) b->oz_rows = std::max(b->oz_rows, total + 128);
@@ -183,7 +187,8 @@ int chol_batch_create(chol_ctx* c, int count, chol_num* const* nums, chol_batch*
           } else if (k == chol::kTaskSchur128) {  // {s, i0, k0, oz}
             b->tasks[k].insert(b->tasks[k].end(), {t[0] + base[i], t[1], t[2], t[3] + zb});
           } else if (k == chol::kTaskOzSlice) {   // {s, r0, oz, y}
-            b->tasks[k].insert(b->tasks[k].end(), {t[0] + base[i], t[1], t[2] + zb, t[3] + yb});
+            b->tasks[k].insert(b->tasks[k].end(),
+                               {t[0] + base[i], t[1], t[2] + zb, t[3] >= 0 ? t[3] + yb : -1});
           } else if (k == chol::kTaskPotrf) {     // {s, first_bwd, nbwd, y or -1}
             b->tasks[k].insert(b->tasks[k].end(),
                                {t[0] + base[i], t[1], t[2], t[3] >= 0 ? t[3] + yb : -1});

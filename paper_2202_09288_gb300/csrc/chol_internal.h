@@ -30,6 +30,7 @@ constexpr int kMaxWidth = 128;   // hard limit on the width cap W (diagonal bloc
 constexpr int kOzSlices = 8;
 constexpr int kOzRowBytes = 128;  // one slice row: 64 bf16 (K <= 64), 128-byte swizzled
 constexpr int kOzInvRows = 64;    // slice rows of a diagonal-block inverse (n <= 64, zero-padded)
+constexpr int kTrsmOzMinLevel = 2;  // supernodes on a level for the tensor-core TRSM
 enum SchurClass { kTile64 = 0, kTile32 = 1, kTile16 = 2, kTile128 = 3, kNumTileClasses = 4 };
 inline int tile_of_class(int c) {
   return c == kTile128 ? 128 : (c == kTile64 ? 64 : (c == kTile32 ? 32 : 16));
@@ -49,6 +50,7 @@ enum TaskKind {
   kTaskSchur128 = 8,  // {s, i0, k0, oz}: 128 x 128 tile of U_s; oz = first slice row of s
   kTaskOzSlice = 9,   // {s, r0, oz, y}: slices of rows r0 .. r0+127 of s's A21 or L21 (FP64
                       //   only); the same rows' tensor-core TRSM with the inverse's slices at y
+                      //   (y = -1: s keeps the FP64 TRSM)
   kTaskTrsmRest = 10, // {s, r0, -, -}: kTaskTrsm without the 128-tile supernodes
   kNumTaskKinds = 11
 };
@@ -153,8 +155,10 @@ struct Sym {
   // and the largest level's count plus one tile of slack (rows a tile may read past u)
   std::vector<int64_t> lvl_ozrows;
   int64_t oz_rows = 0;
-  // slice rows of the 128-tile supernodes' diagonal-block inverses (64 per supernode)
+  // slice rows of the diagonal-block inverses of the supernodes whose TRSM runs on the tensor
+  // cores (64 per supernode), and those supernodes' count, per level
   std::vector<int64_t> lvl_oyrows;
+  std::vector<int32_t> lvl_trsmoz;
   int64_t oy_rows = 0;
   std::vector<int64_t> sn_ustage;  // ns
   // sources of the owner-assembly groups: {s, kb, ke, 0}, columns [kb, ke) of U_s

@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kOzSliceThreads)
   extern __shared__ __align__(16) double xs[];  // [n][kOzSliceLd]
   __shared__ int s_e[kOzM], s_t[kOzInvRows];
   const int4 tk = tasks[blockIdx.x];
+  if (oy && tk.w < 0) return;  // A21 slices only for the tensor-core TRSM's supernodes
   const SnDev d = sns[tk.x];
   const int n = d.n, m = d.m, u = m - n;
   const int r0 = tk.y;
@@ -748,6 +749,7 @@ __global__ void __launch_bounds__(kToThreads, 1)
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 tk = tasks[blockIdx.x];
+  if (tk.w < 0) return;  // the supernode keeps the FP64 TRSM
   const SnDev d = sns[tk.x];
   unsigned long long* err = mats[d.mat].err;
   // a launch of this factorization already gave up on a wait: skip (before any set-up)

@@ -153,6 +153,7 @@ struct TaskView {
   const int64_t* off[kNumTaskKinds] = {};
   const double* flops[kNumTaskKinds] = {};
   const int4* asm_src = nullptr;
+  const int32_t* trsmoz = nullptr;  // per level: supernodes whose TRSM runs on the tensor cores
   int32_t nlev = 0;
   int max_width = 0;
   const int4* level(int k, int32_t l, int* count) const {

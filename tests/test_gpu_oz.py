@@ -59,9 +59,14 @@ def test_oz_tiles_match_oracle(torch, name, assembly):
     ref = oracle.cholesky(A, perm)
     ctx, sym, num, prof = factor(A, perm, assembly=assembly)
     assert num.status()[0] == P.CHOL_OK
-    # the 128-tile supernodes' TRSM ran on the tensor cores too
-    assert prof["schur128_oz"]["launches"] > 0 and prof["trsm_oz"]["launches"] > 0
-    assert prof["oz_slice"]["launches"] == 2 * prof["trsm_oz"]["launches"]
+    # the 128-tile supernodes of levels with several supernodes take the tensor-core TRSM
+    # (A21's slices, then the product with the inverse's slices); every 128-tile level
+    # slices its L21 for the tiles
+    assert prof["schur128_oz"]["launches"] > 0
+    assert prof["oz_slice"]["launches"] == (prof["schur128_oz"]["launches"] +
+                                            prof["trsm_oz"]["launches"])
+    if name in ("st27x3_11", "diff3d7_14", "scaled_st27x3_9"):
+        assert prof["trsm_oz"]["launches"] > 0
     lp, li, lx = num.export()
     assert np.array_equal(li, ref.li)
     err = np.linalg.norm(lx - ref.lx) / np.linalg.norm(ref.lx)
