@@ -802,6 +802,134 @@ int refine_pass(chol_num* f, chol_num* g, int k, const double* B, int64_t ldb, d
   }
 }
 
+// Refinement of a group's requests together (the serving loop): the same steps as
+// refine_pass for every member (first solve, then residual, test, correction, update), but
+// per iteration the members' residual norms land in one device array read back with one
+// synchronization for the whole group, and every member's launches are enqueued before it.
+// Members whose residual stalls, or that need more than one pass of right-hand sides, are
+// finished by chol_refine afterwards (with its FP64 fallback for a mixed factor).  A member's
+// arithmetic is the same as alone, so its result does not depend on the group.
+int refine_group(chol_ctx* c, std::vector<GroupItem>& g) {
+  const size_t G = g.size();
+  constexpr int kSlots = 2 * 32 + 1;  // max |r| per column, max |x| per column, ||A||_inf
+  std::vector<uint8_t> state(G, 0);  // 0 out, 1 active, 2 done, 3 to chol_refine
+  for (size_t i = 0; i < G; i++) {
+    GroupItem& it = g[i];
+    memset(&it.info, 0, sizeof(it.info));
+    it.status = chol_factor_status(c, it.f, nullptr);
+    if (it.status) continue;
+    if (it.k <= 0 || it.f->sym->S.n == 0) continue;
+    if (it.k > 32 || it.f->fb) {
+      state[i] = 3;
+      continue;
+    }
+    if ((it.status = ensure_refine_ws(it.f, it.k)) || (it.status = ensure_solve_ws(it.f, it.k)))
+      continue;
+    state[i] = 1;
+  }
+  unsigned long long* d_g = nullptr;
+  int rc = dev_alloc(c, (void**)&d_g, G * kSlots * 8);
+  if (rc) return rc;
+  std::vector<unsigned long long> h(G * kSlots);
+  cudaStream_t st = c->stream;
+  // ||A||_inf of the members that have not computed it yet, then every first solve
+  CK(cudaMemsetAsync(d_g, 0, G * kSlots * 8, st));
+  bool any_anorm = false;
+  for (size_t i = 0; i < G; i++) {
+    if (state[i] != 1 || g[i].f->anorm >= 0.0) continue;
+    const chol_num* f = g[i].f;
+    chol::launch_anorm(f->sym->dev.csr_ptr, f->sym->dev.csr_src, f->d_vals, f->sym->S.n,
+                       d_g + i * kSlots + 64, st);
+    any_anorm = true;
+  }
+  if (any_anorm) {
+    CK(cudaMemcpyAsync(h.data(), d_g, G * kSlots * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < G; i++)
+      if (state[i] == 1 && g[i].f->anorm < 0.0) memcpy(&g[i].f->anorm, &h[i * kSlots + 64], 8);
+  }
+  for (size_t i = 0; i < G; i++) {
+    if (state[i] != 1) continue;
+    chol_num* f = g[i].f;
+    const int64_t n = f->sym->S.n;
+    CK(cudaMemcpy2DAsync(f->d_rb, n * 8, g[i].B, g[i].ldb * 8, n * 8, g[i].k,
+                         cudaMemcpyHostToDevice, st));
+    if ((g[i].status = enqueue_solve(f, g[i].k, f->d_rb, n, f->d_bx, n))) state[i] = 0;
+  }
+  std::vector<double> prev(G, INFINITY);
+  std::vector<int> stall(G, 0);
+  for (int iter = 0;; iter++) {
+    bool any = false;
+    CK(cudaMemsetAsync(d_g, 0, G * kSlots * 8, st));
+    for (size_t i = 0; i < G; i++) {
+      if (state[i] != 1) continue;
+      any = true;
+      chol_num* f = g[i].f;
+      const chol_sym* sym = f->sym;
+      const int64_t n = sym->S.n;
+      prof_begin(c, kProfRefine);
+      chol::launch_residual(sym->dev.csr_ptr, sym->dev.csr_col, sym->dev.csr_src, f->d_vals, n,
+                            g[i].k, f->d_bx, n, f->d_rb, n, f->d_rr, n, st);
+      chol::launch_absmax(f->d_rr, n, n, g[i].k, d_g + i * kSlots, st);
+      chol::launch_absmax(f->d_bx, n, n, g[i].k, d_g + i * kSlots + 32, st);
+      prof_end(c, kProfRefine, 2.0 * (double)sym->S.csr_ptr[n] * g[i].k,
+               (12.0 * (double)sym->S.csr_ptr[n] + 24.0 * n) * g[i].k);
+    }
+    if (!any) break;
+    CK(cudaMemcpyAsync(h.data(), d_g, G * kSlots * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < G; i++) {
+      if (state[i] != 1) continue;
+      GroupItem& it = g[i];
+      chol_num* f = it.f;
+      double worst = 0.0, rm = 0.0;
+      for (int j = 0; j < it.k; j++) {
+        double r, x;
+        memcpy(&r, &h[i * kSlots + j], 8);
+        memcpy(&x, &h[i * kSlots + 32 + j], 8);
+        worst = std::max(worst, (f->anorm > 0 && x > 0) ? r / (f->anorm * x) : r);
+        rm = std::max(rm, r);
+      }
+      it.info.residual = worst;
+      if (worst <= it.tol) {
+        state[i] = 2;
+        continue;
+      }
+      stall[i] = rm > 0.5 * prev[i] ? stall[i] + 1 : 0;
+      if (iter >= it.maxit || stall[i] >= 2) {
+        state[i] = 3;  // refinement with this factor stalls: chol_refine decides
+        continue;
+      }
+      prev[i] = rm;
+      const int64_t n = f->sym->S.n;
+      if ((it.status = enqueue_solve(f, it.k, f->d_rr, n, f->d_rd, n))) {
+        state[i] = 0;
+        continue;
+      }
+      prof_begin(c, kProfRefine);
+      chol::launch_axpy(f->d_bx, n, f->d_rd, n, n, it.k, st);
+      prof_end(c, kProfRefine, (double)n * it.k, 24.0 * n * it.k);
+      it.info.iterations++;
+    }
+  }
+  for (size_t i = 0; i < G; i++) {
+    GroupItem& it = g[i];
+    if (state[i] == 2) {
+      const int64_t n = it.f->sym->S.n;
+      CK(cudaMemcpy2DAsync(it.X, it.ldx * 8, it.f->d_bx, n * 8, n * 8, it.k,
+                           cudaMemcpyDeviceToHost, st));
+    } else if (state[i] == 3) {
+      const int64_t before = it.info.iterations;
+      it.status = chol_refine(c, it.f, it.k, it.B, it.ldb, it.X, it.ldx, CHOL_HOST, it.tol,
+                              it.maxit, &it.info);
+      it.info.iterations += before;
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  dev_free(c, d_g);
+  return CHOL_OK;
+}
+
 }  // namespace rt
 }  // namespace chol
 

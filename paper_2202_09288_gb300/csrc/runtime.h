@@ -180,6 +180,21 @@ inline size_t solve_counters(const Sym& S) { return solve_arrive_offset(S) + (si
 // oz: the slice scratch of the tensor-core Schur tiles (FP64 slices or TF32 parts); oy (FP64
 // only): the scratch of the diagonal-block inverses' slices, which also selects the
 // tensor-core TRSM of the 128-tile supernodes.
+// One request of a group refinement (refine_group): host right-hand sides B (n x k, ld ldb)
+// and solution X (ld ldx); info and status are outputs.
+struct GroupItem {
+  chol_num* f = nullptr;
+  int k = 0;
+  const double* B = nullptr;
+  int64_t ldb = 0;
+  double* X = nullptr;
+  int64_t ldx = 0;
+  double tol = 0.0;
+  int maxit = 10;
+  chol_refine_info info{};
+  int status = CHOL_OK;
+};
+int refine_group(chol_ctx* c, std::vector<GroupItem>& g);
 int enqueue_levels(chol_ctx* c, const TaskView& v, const SnDev* sns, const MatDev* mats,
                    bool f32, bool owner, int* ctr, void* oz = nullptr, int64_t oz_rows = 0,
                    void* oy = nullptr, int64_t oy_rows = 0);

@@ -321,7 +321,29 @@ void slot_loop(chol_server* srv, Slot* s) {
         for (size_t i = 0; i < group.size(); i++)
           if (nums[i] && nums[i]->precision == prec) status[i] = rc;
     }
-    // refine every request to its target and complete it
+    // refine the group's requests together (one synchronization per iteration for the whole
+    // group) and complete them
+    std::vector<GroupItem> items;
+    std::vector<size_t> slot_of(group.size(), SIZE_MAX);
+    for (size_t i = 0; i < group.size(); i++) {
+      if (status[i]) continue;
+      GroupItem it;
+      it.f = nums[i];
+      it.k = (int)group[i]->nrhs;
+      it.B = group[i]->B.data();
+      it.ldb = group[i]->n;
+      it.X = group[i]->X;
+      it.ldx = group[i]->ldx;
+      it.tol = group[i]->tol;
+      it.maxit = 10;
+      slot_of[i] = items.size();
+      items.push_back(it);
+    }
+    if (!items.empty()) {
+      const int rc = refine_group(s->ctx, items);
+      if (rc)
+        for (GroupItem& it : items) it.status = rc;
+    }
     for (size_t i = 0; i < group.size(); i++) {
       Request* r = group[i];
       chol_result res;
@@ -330,12 +352,11 @@ void slot_loop(chol_server* srv, Slot* s) {
       res.t_start = t_start;
       res.batch_size = (int)live.size();
       if (!status[i]) {
-        chol_refine_info info;
-        status[i] = chol_refine(s->ctx, nums[i], r->nrhs, r->B.data(), r->n, r->X, r->ldx,
-                                CHOL_HOST, r->tol, 10, &info);
-        res.iterations = info.iterations;
-        res.fell_back = info.fell_back;
-        res.residual = info.residual;
+        const GroupItem& it = items[slot_of[i]];
+        status[i] = it.status;
+        res.iterations = it.info.iterations;
+        res.fell_back = it.info.fell_back;
+        res.residual = it.info.residual;
       }
       if (nums[i]) chol_free_num(nums[i]);
       res.status = status[i];
