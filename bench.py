@@ -641,6 +641,16 @@ def main():
                 "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 "
                                "TFLOP/s nominal; 72.0 measured by an FFMA loop"}
 
+    # the step's solve against HBM: each pass reads every stored value of L once (the
+    # diagonal blocks as their inverses' lower triangles, the same count) plus the vectors
+    esz = 4 if mixed else 8
+    solve_bytes = 2.0 * esz * sym.info["nnz_l"] + 2.0 * 3 * 8 * n * nrhs
+    solve_roof = {"bound": "hbm", "achieved": solve_bytes / (sol_ms * 1e-3) / 1e9,
+                  "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                  "frac": solve_bytes / (sol_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                  "bytes": solve_bytes, "ms": sol_ms,
+                  "note": f"2 passes x {esz} B x nnz(L) + vectors; solve time from the timed "
+                          "region's CUDA events" + (" (refinement included)" if mixed else "")}
     value = replica_rate(world, F, ms_step * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
@@ -658,7 +668,7 @@ def main():
                        tile_policy=P.chol_sym_get_tile_policy(sym.handle),
                        granularity=P.chol_sym_granularity(sym.handle),
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
-        "factor_ms": fac_ms, "solve_ms": sol_ms,
+        "factor_ms": fac_ms, "solve_ms": sol_ms, "solve_roofline": solve_roof,
         "factor_gflops": F / (fac_ms * 1e-3) / 1e9,
         "fp64_peak_frac": (F / (fac_ms * 1e-3) / 1e12) / fp64_peak_tflops,
         "residual": resid,

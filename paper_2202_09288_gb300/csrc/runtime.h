@@ -167,8 +167,8 @@ int enqueue_factor(chol_num* f);
 // Releases the device memory of every batch of c (called by chol_destroy).
 void detach_batches(chol_ctx* c);
 TaskView sym_view(const chol_sym* sym);
-// Work-queue counters (one int per persistent launch): 7 per level for a factorization
-// (POTRF, TRSM, four Schur tile classes, owner assembly), 3 per level for a solve.
+// Work-queue counters (one int per task launch): 7 per level for a factorization (POTRF,
+// TRSM, four Schur tile classes, owner assembly), 3 per level for a solve.
 constexpr int kFactorCountersPerLevel = 3 + chol::kNumTileClasses;
 inline size_t factor_counters(int32_t nlev) { return kFactorCountersPerLevel * (size_t)nlev + 8; }
 // Counters of a solve, zeroed at its start: 3 work-queue counters per level, then (from
