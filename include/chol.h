@@ -313,6 +313,10 @@ typedef struct chol_tile_policy {
   int min_rows_tile128;
   int min_level_tiles128;
   int granularity;
+  /* FP64 factors with the tensor-core tiles: a level's 128-tile supernodes take the
+   * tensor-core TRSM (L21 = A21 L11^-T with the explicit inverse, slices on the bf16 tensor
+   * cores) when their off-diagonal rows add up to at least this many; >= 1 */
+  int min_rows_trsm_tc;
 } chol_tile_policy;
 int chol_sym_get_tile_policy(const chol_sym* sym, chol_tile_policy* policy);
 /* Rebuilds the Schur task lists of sym (and its device copy); factors made from sym use

@@ -56,7 +56,7 @@ class chol_tile_policy(C.Structure):
     _fields_ = [("min_rows_tile64", C.c_int), ("min_rows_tile32", C.c_int),
                 ("min_level_tiles64", C.c_int), ("min_rows_tile128", C.c_int),
                 ("min_level_tiles128", C.c_int),
-                ("granularity", C.c_int)]
+                ("granularity", C.c_int), ("min_rows_trsm_tc", C.c_int)]
 
 
 class chol_server_opts(C.Structure):

@@ -656,15 +656,20 @@ void build_schur_tasks(Sym* S, const TilePolicy& policy) {
       }
     }
   }
-  // pass 2: the task lists.  A 128-tile supernode (FP64: slices on the tensor cores) on a level
-  // of at least kTrsmOzMinLevel supernodes also gets its TRSM on the tensor cores, with the
-  // slices of its diagonal block's inverse at 64 rows of the level's inverse slices (recorded
-  // in its POTRF task).  A level of one supernode keeps the FP64 TRSM: there the inverse, one
-  // CTA's n^3/6 FP64 multiply-adds, costs as much latency as the FP64 TRSM spread over the
-  // SMs (measured on GB300).  The other supernodes' TRSM tasks form kTaskTrsmRest.
+  // pass 2: the task lists.  The 128-tile supernodes (FP64: slices on the tensor cores) of a
+  // level whose 128-tile rows add up to policy.min_rows_trsm_tc also get their TRSM on the
+  // tensor cores, with the slices of their diagonal blocks' inverses at 64 rows each of the
+  // level's inverse slices (recorded in the POTRF tasks).  On a narrower level the inverse
+  // and its slicing (~45 us of one SM per supernode on GB300, FP64 latency) cost more than
+  // the FP64 TRSM they replace.  The other supernodes' TRSM tasks form kTaskTrsmRest.
   for (int32_t l = 0; l < S->nlev; l++) {
-    int64_t ozrow = 0, oyrow = 0;
-    const bool wide = S->lvl_ptr[l + 1] - S->lvl_ptr[l] >= kTrsmOzMinLevel;
+    int64_t ozrow = 0, oyrow = 0, rows128 = 0;
+    for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
+      const int32_t s = S->lvl_sn[q];
+      const int32_t u = S->sn_m[s] - (S->sn_start[s + 1] - S->sn_start[s]);
+      if (u > 0 && (whole[s] ? whole_tile_class(u) : cls0[s]) == kTile128) rows128 += u;
+    }
+    const bool wide = rows128 >= policy.min_rows_trsm_tc;
     for (int32_t q = S->lvl_ptr[l]; q < S->lvl_ptr[l + 1]; q++) {
       const int32_t s = S->lvl_sn[q];
       const int32_t w = S->sn_start[s + 1] - S->sn_start[s];

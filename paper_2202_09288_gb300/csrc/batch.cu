@@ -335,6 +335,7 @@ int chol_sym_get_tile_policy(const chol_sym* s, chol_tile_policy* p) {
   p->min_rows_tile128 = s->S.policy.min_rows_tile128;
   p->min_level_tiles128 = s->S.policy.min_level_tiles128;
   p->granularity = s->S.policy.granularity;
+  p->min_rows_trsm_tc = s->S.policy.min_rows_trsm_tc;
   return CHOL_OK;
 }
 
@@ -441,7 +442,7 @@ int chol_sym_granularity(const chol_sym* s, int* rule, int32_t* D, int32_t* nspl
 int chol_sym_set_tile_policy(chol_sym* s, const chol_tile_policy* p) {
   if (!s || !p || p->min_rows_tile64 < 1 || p->min_rows_tile32 < 1 || p->min_level_tiles64 < 0 ||
       p->min_rows_tile128 < 1 || p->min_level_tiles128 < 0 || p->granularity < CHOL_GRAN_TILES ||
-      p->granularity > CHOL_GRAN_HYBRID)
+      p->granularity > CHOL_GRAN_HYBRID || p->min_rows_trsm_tc < 1)
     return CHOL_E_INVALID;
   chol::TilePolicy tp;
   tp.min_rows_tile64 = p->min_rows_tile64;
@@ -450,6 +451,7 @@ int chol_sym_set_tile_policy(chol_sym* s, const chol_tile_policy* p) {
   tp.min_rows_tile128 = p->min_rows_tile128;
   tp.min_level_tiles128 = p->min_level_tiles128;
   tp.granularity = p->granularity;
+  tp.min_rows_trsm_tc = p->min_rows_trsm_tc;
   chol::build_schur_tasks(&s->S, tp);
   if (!s->ctx) return CHOL_OK;
   chol_ctx* c = s->ctx;
@@ -513,18 +515,20 @@ int chol_autotune(chol_ctx* c, chol_num* num, int reps, chol_tile_policy* best, 
   chol_sym_get_tile_policy(num->sym, &cur);
   double cur_ms = 0.0;
   int rc = time_policy(c, num, cur, reps, &cur_ms);
-  // coordinate descent over the five thresholds (1 << 30 rows: no 128-wide tiles)
-  static const int kCand[5][5] = {{0, 152, 304, 608, 1216},
+  // coordinate descent over the six thresholds (1 << 30 rows: no 128-wide tiles, or no
+  // tensor-core TRSM)
+  static const int kCand[6][5] = {{0, 152, 304, 608, 1216},
                                   {32, 48, 64, 96, 128},
                                   {1, 9, 17, 25, 33},
                                   {128, 192, 256, 512, 1 << 30},
-                                  {0, 152, 304, 608, 1216}};
-  for (int pass = 0; pass < 5 && !rc; pass++) {
+                                  {0, 152, 304, 608, 1216},
+                                  {4096, 8192, 16384, 32768, 1 << 30}};
+  for (int pass = 0; pass < 6 && !rc; pass++) {
     const int* vals = kCand[pass];
     for (int q = 0; q < 5 && !rc; q++) {
       chol_tile_policy p = cur;
-      int* fields[5] = {&p.min_level_tiles64, &p.min_rows_tile64, &p.min_rows_tile32,
-                        &p.min_rows_tile128, &p.min_level_tiles128};
+      int* fields[6] = {&p.min_level_tiles64, &p.min_rows_tile64, &p.min_rows_tile32,
+                        &p.min_rows_tile128, &p.min_level_tiles128, &p.min_rows_trsm_tc};
       int* field = fields[pass];
       if (*field == vals[q]) continue;
       *field = vals[q];

@@ -30,7 +30,6 @@ constexpr int kMaxWidth = 128;   // hard limit on the width cap W (diagonal bloc
 constexpr int kOzSlices = 8;
 constexpr int kOzRowBytes = 128;  // one slice row: 64 bf16 (K <= 64), 128-byte swizzled
 constexpr int kOzInvRows = 64;    // slice rows of a diagonal-block inverse (n <= 64, zero-padded)
-constexpr int kTrsmOzMinLevel = 2;  // supernodes on a level for the tensor-core TRSM
 enum SchurClass { kTile64 = 0, kTile32 = 1, kTile16 = 2, kTile128 = 3, kNumTileClasses = 4 };
 inline int tile_of_class(int c) {
   return c == kTile128 ? 128 : (c == kTile64 ? 64 : (c == kTile32 ? 32 : 16));
@@ -111,6 +110,10 @@ struct TilePolicy {
   int min_rows_tile128 = 128;
   int min_level_tiles128 = 0;
   int granularity = kGranTiles;
+  // FP64: a level's 128-tile supernodes take the tensor-core TRSM when their off-diagonal rows
+  // add up to at least this many (below, the inverse's FP64 latency on one SM per supernode
+  // outweighs the FP64 TRSM it replaces)
+  int min_rows_trsm_tc = 16384;
 };
 
 // Host-side symbolic analysis result.

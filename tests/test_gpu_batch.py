@@ -115,7 +115,7 @@ POLICIES = [
      **NO128},                                                                    # all 16
     {"min_rows_tile64": 10 ** 6, "min_rows_tile32": 1, "min_level_tiles64": 0, **NO128},  # 32
     {"min_rows_tile64": 1, "min_rows_tile32": 1, "min_level_tiles64": 0,
-     "min_rows_tile128": 1, "min_level_tiles128": 0},                             # all 128
+     "min_rows_tile128": 1, "min_level_tiles128": 0, "min_rows_trsm_tc": 1},      # all 128
 ]
 
 
@@ -157,7 +157,8 @@ def test_autotuner(torch):
     num = P.Factor(ctx, sym, A.vals)
     policy, ms = num.autotune(reps=1)
     assert ms > 0 and set(policy) == {"min_rows_tile64", "min_rows_tile32", "min_level_tiles64",
-                                      "min_rows_tile128", "min_level_tiles128", "granularity"}
+                                      "min_rows_tile128", "min_level_tiles128", "granularity",
+                                      "min_rows_trsm_tc"}
     assert P.chol_sym_get_tile_policy(sym.handle) == policy
     check_member(ctx, num, A, perm, ref)
 

@@ -14,8 +14,9 @@ from conftest import column_error
 
 pytestmark = pytest.mark.gpu
 
+# every supernode in the 128-tile class, and every level's TRSM on the tensor cores
 ALL128 = {"min_rows_tile64": 1, "min_rows_tile32": 1, "min_level_tiles64": 0,
-          "min_rows_tile128": 1, "min_level_tiles128": 0}
+          "min_rows_tile128": 1, "min_level_tiles128": 0, "min_rows_trsm_tc": 1}
 
 
 @pytest.fixture(scope="module")
@@ -65,8 +66,7 @@ def test_oz_tiles_match_oracle(torch, name, assembly):
     assert prof["schur128_oz"]["launches"] > 0
     assert prof["oz_slice"]["launches"] == (prof["schur128_oz"]["launches"] +
                                             prof["trsm_oz"]["launches"])
-    if name in ("st27x3_11", "diff3d7_14", "scaled_st27x3_9"):
-        assert prof["trsm_oz"]["launches"] > 0
+    assert prof["trsm_oz"]["launches"] > 0
     lp, li, lx = num.export()
     assert np.array_equal(li, ref.li)
     err = np.linalg.norm(lx - ref.lx) / np.linalg.norm(ref.lx)
@@ -87,6 +87,8 @@ def test_oz_agrees_with_dmma(torch, name):
     _, _, oz, prof = factor(A, perm)
     _, _, dm, prof_dm = factor(A, perm, mode=P.CHOL_SCHUR_DMMA)
     assert prof_dm["schur128_oz"]["launches"] == 0 and prof_dm["schur128_f64"]["launches"] > 0
+    # the tensor-core TRSM against the FP64 one too
+    assert prof["trsm_oz"]["launches"] > 0 and prof_dm["trsm_oz"]["launches"] == 0
     lp, _, a = oz.export()
     b = dm.export()[2]
     assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 1e-14
