@@ -52,45 +52,76 @@ __global__ void k_assemble_scaled(const int64_t* __restrict__ colptr,
 }
 
 // R[:, c] = B[:, c] - A X[:, c] with the full symmetric A in CSR form (csr_src indexes the
-// stored lower values), FP64.
+// stored lower values), FP64: one thread per row, all NR (>= nrhs) right-hand sides at once,
+// so the row's entries are read once.
+template <int NR>
 __global__ void k_residual(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                            const int32_t* __restrict__ src, const double* __restrict__ vals,
                            int64_t n, int nrhs, const double* __restrict__ X, int64_t ldx,
                            const double* __restrict__ B, int64_t ldb, double* __restrict__ R,
                            int64_t ldr) {
-  const int64_t total = n * nrhs;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = q / n, i = q - c * n;
-    const double* x = X + c * ldx;
-    double s = 0.0;
-    for (int64_t e = ptr[i]; e < ptr[i + 1]; e++) s += vals[src[e]] * x[col[e]];
-    R[c * ldr + i] = B[c * ldb + i] - s;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s[NR];
+#pragma unroll
+    for (int c = 0; c < NR; c++) s[c] = 0.0;
+    for (int64_t e = ptr[i]; e < ptr[i + 1]; e++) {
+      const double v = vals[src[e]];
+      const int64_t j = col[e];
+#pragma unroll
+      for (int c = 0; c < NR; c++)
+        if (c < nrhs) s[c] += v * X[c * ldx + j];
+    }
+#pragma unroll
+    for (int c = 0; c < NR; c++)
+      if (c < nrhs) R[c * ldr + i] = B[c * ldb + i] - s[c];
   }
 }
 
-// out[c] = max_i |V[i, c]| (non-negative doubles order like their bit patterns).
-__global__ void k_absmax(const double* __restrict__ V, int64_t ld, int64_t n, int nrhs,
-                         unsigned long long* __restrict__ out) {
-  const int64_t total = n * nrhs;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = q / n, i = q - c * n;
-    const double v = fabs(V[c * ld + i]);
-    atomicMax(out + c, (unsigned long long)__double_as_longlong(v));
+// Largest value of a block's threads (non-negative doubles order like their bit patterns), one
+// atomic per block: v of every thread in, the result valid in thread 0.
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v) {
+  __shared__ unsigned long long w[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) w[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? w[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   }
+  __syncthreads();
+  return v;
+}
+
+// out[c] = max_i |V[i, c]|: column c = blockIdx.y, a grid-stride maximum per thread, then one
+// atomic per block.
+__global__ void k_absmax(const double* __restrict__ V, int64_t ld, int64_t n,
+                         unsigned long long* __restrict__ out) {
+  const int c = blockIdx.y;
+  unsigned long long m = 0ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned long long)__double_as_longlong(fabs(V[c * ld + i])));
+  m = block_max(m);
+  if (threadIdx.x == 0) atomicMax(out + c, m);
 }
 
 // ||A||_inf = max_i sum_e |a_ie| over the full CSR.
 __global__ void k_anorm(const int64_t* __restrict__ ptr, const int32_t* __restrict__ src,
                         const double* __restrict__ vals, int64_t n,
                         unsigned long long* __restrict__ out) {
+  unsigned long long m = 0ull;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int64_t e = ptr[i]; e < ptr[i + 1]; e++) s += fabs(vals[src[e]]);
-    atomicMax(out, (unsigned long long)__double_as_longlong(s));
+    m = max(m, (unsigned long long)__double_as_longlong(s));
   }
+  m = block_max(m);
+  if (threadIdx.x == 0) atomicMax(out, m);
 }
 
 // X[:, c] += D[:, c]
@@ -122,14 +153,26 @@ void launch_residual(const int64_t* ptr, const int32_t* col, const int32_t* src,
                      const double* vals, int64_t n, int nrhs, const double* X, int64_t ldx,
                      const double* B, int64_t ldb, double* R, int64_t ldr, cudaStream_t st) {
   if (n <= 0) return;
-  k_residual<<<grid_for(n * nrhs, 256), 256, 0, st>>>(ptr, col, src, vals, n, nrhs, X, ldx, B,
-                                                       ldb, R, ldr);
+  // right-hand sides per pass: the smallest of 1, 4, 8, 16, 32 >= nrhs
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int k = std::min(32, nrhs - c0);
+    const double* Xc = X + c0 * ldx;
+    const double* Bc = B + c0 * ldb;
+    double* Rc = R + c0 * ldr;
+    const int g = grid_for(n, 256);
+    if (k <= 1) k_residual<1><<<g, 256, 0, st>>>(ptr, col, src, vals, n, k, Xc, ldx, Bc, ldb, Rc, ldr);
+    else if (k <= 4) k_residual<4><<<g, 256, 0, st>>>(ptr, col, src, vals, n, k, Xc, ldx, Bc, ldb, Rc, ldr);
+    else if (k <= 8) k_residual<8><<<g, 256, 0, st>>>(ptr, col, src, vals, n, k, Xc, ldx, Bc, ldb, Rc, ldr);
+    else if (k <= 16) k_residual<16><<<g, 256, 0, st>>>(ptr, col, src, vals, n, k, Xc, ldx, Bc, ldb, Rc, ldr);
+    else k_residual<32><<<g, 256, 0, st>>>(ptr, col, src, vals, n, k, Xc, ldx, Bc, ldb, Rc, ldr);
+  }
 }
 
 void launch_absmax(const double* V, int64_t ld, int64_t n, int nrhs, unsigned long long* out,
                    cudaStream_t st) {
-  if (n <= 0) return;
-  k_absmax<<<grid_for(n * nrhs, 256), 256, 0, st>>>(V, ld, n, nrhs, out);
+  if (n <= 0 || nrhs <= 0) return;
+  const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 152 * 2), (unsigned)nrhs);
+  k_absmax<<<grid, 256, 0, st>>>(V, ld, n, out);
 }
 
 void launch_anorm(const int64_t* ptr, const int32_t* src, const double* vals, int64_t n,
