@@ -572,19 +572,19 @@ static inline int rhs_pass(int nrhs) {
   return nrhs <= 1 ? 1 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : 32;
 }
 
-// Launch sizes (bytes) for supernodes of width <= W in the given mode; global mode covers
-// both the layout with Y (widths <= kDinvMaxWidth) and the one by substitution.
-static inline size_t fwd_smem(int W, int nrhs, int mode) {
+// Launch sizes (bytes, elements of esz bytes: the panel precision) for supernodes of width
+// <= W in the given mode; global mode covers both the layout with Y (widths <= kDinvMaxWidth)
+// and the one by substitution.
+static inline size_t fwd_smem(int W, int nrhs, int mode, size_t esz = sizeof(double)) {
   const int wy = std::min(W, kDinvMaxWidth);
-  if (mode == kModeWide) return fwd_elems(wy, nrhs, true, mode) * sizeof(double);
-  return std::max(fwd_elems(wy, nrhs, true, mode), fwd_elems(W, nrhs, false, mode)) *
-         sizeof(double);
+  if (mode == kModeWide) return fwd_elems(wy, nrhs, true, mode) * esz;
+  return std::max(fwd_elems(wy, nrhs, true, mode), fwd_elems(W, nrhs, false, mode)) * esz;
 }
-static inline size_t bwd_smem(int W, int nrhs, int mode) {
+static inline size_t bwd_smem(int W, int nrhs, int mode, size_t esz = sizeof(double)) {
   const int wy = std::min(W, kDinvMaxWidth), nr = rhs_pass(nrhs);
-  if (mode != kModeGlobal) return bwd_elems(wy, nrhs, true, mode, nr) * sizeof(double);
+  if (mode != kModeGlobal) return bwd_elems(wy, nrhs, true, mode, nr) * esz;
   return std::max(bwd_elems(wy, nrhs, true, mode, nr), bwd_elems(W, nrhs, false, mode, nr)) *
-         sizeof(double);
+         esz;
 }
 
 // Mode of a level (factors that keep Y): wide when its tasks fit in one wave at one CTA per
@@ -619,7 +619,7 @@ template <typename P, int NR, int MODE>
 static void fwd_nr(const int4* tasks, int ntasks, int* queue, const SnDev* sns, int64_t ldv,
                    int nrhs, int W, double* y, double* w, double* fstage, cudaStream_t st) {
   constexpr int T = solve_threads<MODE>();
-  const size_t sm = fwd_smem(W, nrhs, MODE);
+  const size_t sm = fwd_smem(W, nrhs, MODE, sizeof(P));
   if (fstage)
     k_fwd<P, true, NR, MODE><<<task_grid(k_fwd<P, true, NR, MODE>, T, sm, ntasks), T, sm, st>>>(
         tasks, ntasks, queue, sns, ldv, nrhs, y, w, fstage);
@@ -670,7 +670,7 @@ static void bwd_nr(const int4* tasks, int ntasks, int* queue, const SnDev* sns, 
                    int nrhs, int W, int wl, double* w, double* part, int* arrive,
                    cudaStream_t st) {
   constexpr int T = solve_threads<MODE>();
-  const size_t sm = bwd_smem(wl, nrhs, MODE);
+  const size_t sm = bwd_smem(wl, nrhs, MODE, sizeof(P));
   k_bwd<P, NR, MODE><<<task_grid(k_bwd<P, NR, MODE>, T, sm, ntasks), T, sm, st>>>(
       tasks, ntasks, queue, sns, ldv, nrhs, W, w, part, arrive);
 }
