@@ -1,6 +1,5 @@
 """GPU parity of batched factorization (one launch per level and kernel kind across many
-matrices, persistent kernels, CUDA-graph replay), of Schur tile policies and of the
-autotuner.  Every member must match the oracle as when factored alone (Sec. 3, Fig. 1:
+matrices, CUDA-graph replay), of Schur tile policies and of the autotuner.  Every member must match the oracle as when factored alone (Sec. 3, Fig. 1:
 independent supernodes run together; here across matrices), and with owner-ordered
 assembly a member's factor must be bitwise identical alone and in the mix."""
 import numpy as np
