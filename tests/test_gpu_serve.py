@@ -140,3 +140,31 @@ def test_request_arriving_mid_group_is_admitted_at_once(torch):
     Xa, ra = alone.wait(alone.submit(S, sperm, SB))
     alone.close()
     assert np.array_equal(Xs, Xa)
+
+
+def test_group_refinement_with_a_stalling_member_and_many_rhs(torch):
+    """A group's requests refine together (one synchronization per iteration for the group).
+    One member's FP32 factor cannot reach the tolerance (floating diffusion, condition ~1e10:
+    its refinement stalls and falls back to the FP64 factor), one has 40 right-hand sides
+    (more than one pass), the others are ordinary: every result meets its tolerance and
+    equals, bit for bit, the same request served alone (owner-ordered assembly)."""
+    reqs = request_mix(4, 7)
+    F, fperm = inputs.workload("floatdiff_16")
+    reqs.append((F, fperm, np.asfortranarray(F.to_scipy_full() @ inputs.rhs_block(91, F.n, 2))))
+    A40, p40 = inputs.workload("lap2d_20")
+    reqs.append((A40, p40, np.asfortranarray(A40.to_scipy_full() @ inputs.rhs_block(92, A40.n, 40))))
+    alone = P.Server(slots=1, max_batch=1, assembly=P.CHOL_ASSEMBLY_OWNER)
+    ref = [alone.wait(alone.submit(A, perm, B, precision=P.CHOL_MIXED)) for A, perm, B in reqs]
+    alone.close()
+    mix = P.Server(slots=1, max_batch=8, assembly=P.CHOL_ASSEMBLY_OWNER)
+    tickets = [mix.submit(A, perm, B, precision=P.CHOL_MIXED) for A, perm, B in reqs]
+    got = [mix.wait(t) for t in tickets]
+    mix.close()
+    assert max(r["batch_size"] for _, r in got) > 1
+    for (A, perm, B), (X0, r0), (X, r) in zip(reqs, ref, got):
+        assert r["status"] == P.CHOL_OK and r0["status"] == P.CHOL_OK, (r, r0)
+        assert r["residual"] <= 1e-12
+        assert oracle.residual(A.n, A.colptr, A.rowind, A.vals, B, X) <= 1e-12
+        assert np.array_equal(X, X0)
+    assert got[-2][1]["fell_back"] and ref[-2][1]["fell_back"]
+    assert not got[0][1]["fell_back"]
