@@ -111,6 +111,8 @@ typedef struct chol_sym_stats {
   double flops_panel; /* sum of c^2 over the columns of the (padded) panels: the operations
                          the factorization performs, >= flops under relaxed amalgamation */
   int64_t nfundamental; /* fundamental supernodes (before amalgamation and the width cap) */
+  int64_t ntrsm_tc;     /* supernodes whose TRSM runs on the tensor cores in an FP64 factor with
+                           the tensor-core tiles (under the current tile policy) */
 } chol_sym_stats;
 
 /* Fills *opts with the defaults (device 0, own stream, W = 64, atomic assembly,

@@ -44,7 +44,8 @@ class chol_sym_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz_a", C.c_int64), ("nnz_l", C.c_int64),
                 ("l_storage", C.c_int64), ("nsuper", C.c_int64), ("nlevels", C.c_int64),
                 ("flops", C.c_double), ("max_width", C.c_int64), ("max_rows", C.c_int64),
-                ("flops_panel", C.c_double), ("nfundamental", C.c_int64)]
+                ("flops_panel", C.c_double), ("nfundamental", C.c_int64),
+                ("ntrsm_tc", C.c_int64)]
 
 
 class chol_refine_info(C.Structure):

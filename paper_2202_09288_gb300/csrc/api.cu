@@ -1107,6 +1107,8 @@ int chol_sym_info(const chol_sym* s, chol_sym_stats* st) {
   st->max_rows = S.max_rows;
   st->flops_panel = S.flops_panel;
   st->nfundamental = S.n_fundamental;
+  st->ntrsm_tc = 0;
+  for (int32_t c : S.lvl_trsmoz) st->ntrsm_tc += c;
   return CHOL_OK;
 }
 

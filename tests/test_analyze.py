@@ -270,3 +270,26 @@ def test_schur_tiles_cover_each_update_once(name, rule):
     for s, c in cover.items():
         low = c[np.tril_indices(len(c))]
         assert low.min() == 1 and low.max() == 1, s
+
+
+@pytest.mark.parametrize("name", ["st27x3_11", "diff3d7_14", "lap2d_64"])
+def test_tensor_core_trsm_levels(name):
+    """The tensor-core TRSM (FP64 factors) takes a level's 128-tile supernodes when their
+    off-diagonal rows add up to min_rows_trsm_tc: with the size thresholds alone deciding the
+    128-tile class (u >= 128, no level counts), the count of such supernodes follows from the
+    level sets."""
+    A, perm = inputs.workload(name)
+    sym = P.Symbolic(P.make_opts(width_cap=64), A, perm)
+    ex = sym.export()
+    lvl = ex["sn_level"]
+    rowptr, _ = P.chol_sym_rows(sym.handle)
+    w = np.diff(ex["sn_start"]).astype(np.int64)
+    u = np.diff(rowptr).astype(np.int64) - w
+    c128 = u >= 128
+    rows = np.bincount(lvl[c128], weights=u[c128], minlength=int(lvl.max()) + 1)
+    for thr in (1, 128, 300, 1000, 16384):
+        P.chol_sym_set_tile_policy(sym.handle, {**SIZE_ONLY, "min_rows_trsm_tc": thr})
+        expect = int(np.sum(c128 & (rows[lvl] >= thr)))
+        assert P.chol_sym_info(sym.handle)["ntrsm_tc"] == expect, thr
+    with pytest.raises(P.CholError):
+        P.chol_sym_set_tile_policy(sym.handle, {"min_rows_trsm_tc": 0})
