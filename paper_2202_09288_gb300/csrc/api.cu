@@ -830,6 +830,11 @@ int refine_group(chol_ctx* c, std::vector<GroupItem>& g) {
   unsigned long long* d_g = nullptr;
   int rc = dev_alloc(c, (void**)&d_g, G * kSlots * 8);
   if (rc) return rc;
+  struct Release {  // the norms' array goes back to the pool on every return path
+    chol_ctx* c;
+    void* p;
+    ~Release() { dev_free(c, p); }
+  } release{c, d_g};
   std::vector<unsigned long long> h(G * kSlots);
   cudaStream_t st = c->stream;
   // ||A||_inf of the members that have not computed it yet, then every first solve
@@ -926,7 +931,6 @@ int refine_group(chol_ctx* c, std::vector<GroupItem>& g) {
     }
   }
   CK(cudaStreamSynchronize(st));
-  dev_free(c, d_g);
   return CHOL_OK;
 }
 
