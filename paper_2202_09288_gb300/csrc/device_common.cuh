@@ -17,6 +17,16 @@ __device__ __forceinline__ int lower_bound_dev(const int32_t* a, int n, int key)
   return lo;
 }
 
+// Adds v to *p in global memory when the old value is not needed: a PTX reduction, which
+// returns nothing, so the issuing warp never waits for the round trip to L2 (an atomicAdd
+// can be compiled as an atomic that returns the old value into a register).
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v));
+}
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v));
+}
+
 __device__ __forceinline__ void record_error(const MatDev& md, int col) {
   atomicMin(md.err, (unsigned long long)col + 1ull);
 }
@@ -36,7 +46,7 @@ __device__ __forceinline__ int find_run(const MatDev& md, const SnDev& d, int po
 // i0 + ii and columns k0 + kk of the off-diagonal part of s): each entry U(i, k), i >= k,
 // is subtracted from the target panel t owning column rows[k] -- column rows[k] - col0(t),
 // row position of rows[i] inside t's row list (the relative map built once per pattern).
-//   OWNER == false: atomicAdd into the panel.
+//   OWNER == false: added into the panel (red_add).
 //   OWNER == true : the tile is written to the level staging buffer (U_s column-major,
 //                   ld u) and k_assemble_owner applies it later in a fixed order.
 template <typename T, int TILE, int THREADS, bool OWNER>
@@ -114,7 +124,7 @@ __device__ __forceinline__ void schur_tile_epilogue(const T* Cs, const SnDev& d,
         const int p = relpos[rr][ii];
         if (ii < ilim && i0 + ii >= k0 + kk && p >= 0) {
           const int c = rows[k0 + kk] - td.col0;
-          atomicAdd(&Lt[(int64_t)c * td.m + p], -Cs[kk * (TILE + 1) + ii]);
+          red_add(&Lt[(int64_t)c * td.m + p], -Cs[kk * (TILE + 1) + ii]);
         }
       }
     }

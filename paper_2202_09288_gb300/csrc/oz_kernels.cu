@@ -248,7 +248,7 @@ __device__ __forceinline__ long long oz_high(unsigned long long lo, uint32_t f0,
 
 // s W 2^E as a double (s = -1 when NEG), rounded to nearest (ties to even): the FP64 unit's
 // int64 -> double conversion, then an add to the exponent field and, for NEG, to the sign bit
-// (exact inside the normal range; ldexp for zero and outside it).  The FP64 unit is otherwise
+// (exact inside the normal range; a signed zero for W = 0, ldexp outside the range).  The FP64 unit is otherwise
 // idle in this kernel, and one conversion there costs the consumer warps far fewer issue slots
 // than normalizing and rounding the 64-bit integer with integer operations.
 template <bool NEG>
@@ -256,7 +256,8 @@ __device__ __forceinline__ double oz_to_double(long long W, int E) {
   const double d = __ll2double_rn(W);
   const uint32_t hi = (uint32_t)__double2hiint(d);
   const int be = (int)((hi >> 20) & 0x7ffu) + E;
-  if (hi != 0u && (unsigned)(be - 1) < 2046u)
+  if (hi == 0u) return NEG ? -0.0 : 0.0;  // W = 0: adds nothing (-0.0 leaves every sum as it is)
+  if ((unsigned)(be - 1) < 2046u)
     return __hiloint2double((int)(hi + (uint32_t)E * 1048576u + (NEG ? 0x80000000u : 0u)),
                             __double2loint(d));
   const double r = ldexp(d, E);
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             const int p = r < kOzMaxRuns ? M.rp[r][i] : M.relmap[M.rb[r] + gi];
             if (p >= 0) {
 #pragma unroll
-              for (int jj = 0; jj < 8; jj++) atomicAdd(M.cp[kb + jj] + p, val[jj]);
+              for (int jj = 0; jj < 8; jj++) red_add(M.cp[kb + jj] + p, val[jj]);
             }
           } else if (gi < u) {
             // the relative row changes only with the run, which is the same for every lane
@@ -694,7 +695,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 rprev = r;
                 p = r < kOzMaxRuns ? M.rp[r][i] : M.relmap[M.rb[r] + gi];
               }
-              if (p >= 0) atomicAdd(M.cp[kk] + p, val[jj]);
+              if (p >= 0) red_add(M.cp[kk] + p, val[jj]);
             }
           }
         }

@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(solve_threads<MODE>())
           if (OWNER)
             fstage[((int64_t)tq * kSolveRows + i) * nrhs + c0 + c] = (double)v[c];
           else
-            atomicAdd(&y[(int64_t)(c0 + c) * ldv + grow], -(double)v[c]);
+            red_add(&y[(int64_t)(c0 + c) * ldv + grow], -(double)v[c]);
         }
       }
       if (G > 1) __syncthreads();

@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
               rprev = r;
               p = r < kTfMaxRuns ? M.rp[r][i] : M.relmap[M.rb[r] + gi];
             }
-            if (p >= 0) atomicAdd(M.cp[kk] + p, -__uint_as_float(v[j]));
+            if (p >= 0) red_add(M.cp[kk] + p, -__uint_as_float(v[j]));
           }
         }
       }
