@@ -365,22 +365,31 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   if (warp == kOzLoadWarp) {
     // ---------------- loads: task claims, ring, bulk copies; one thread ----------------
     if (lane == 0) {
-      long long T = 0;                       // tasks whose A slices were issued
+      long long T = 0;                       // A slice loads issued
       long long qb = 0;                      // quarter B buffers issued (buffer = qb & 1)
       long long ord = 0;                     // ring entries published
       bool ok = true;
-      int tq = blockIdx.x;                   // a CTA's first task is its block index
+      // Tasks are claimed in runs of two while plenty remain (g0 per CTA at first, then from
+      // the queue), singles near the end: the tasks of a row strip are consecutive in the
+      // list, so the second task of a run usually has the first one's A rows, which stay in
+      // shared memory.
+      const int g0 = ntasks >= 4 * (int)gridDim.x ? 2 : 1;
+      int tq = g0 * (int)blockIdx.x;         // a CTA's first run follows its block index
+      int tend = min(tq + g0, ntasks);       // end of the claimed run
+      int arow = -1;                         // slice row of the A rows in shared memory
       for (;;) {
         int4 t = make_int4(0, 0, 0, 0);
         int nq = 0, ks = 0;
+        bool reuse = false;
         if (tq < ntasks) {
           t = tasks[tq];
           const SnDev& dd = sns[t.x];
           nq = min(4, (dd.m - dd.n - t.z + kOzQ - 1) / kOzQ);
           ks = (dd.n + 15) >> 4;
+          reuse = t.w + t.y == arow;
         }
         const int rs = (int)(ord % kOzRing);
-        ring[rs] = make_int2(tq < ntasks ? tq : ntasks, nq | (ks << 8));
+        ring[rs] = make_int2(tq < ntasks ? tq : ntasks, nq | (ks << 8) | ((int)reuse << 16));
         oz_arrive(smem_u32(&ring_full[rs]));
         ord++;
         if (tq >= ntasks) break;
@@ -404,21 +413,31 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           ok = false;
           break;
         }
-        // the A slices of this task, once the previous task's last quarter (the latest quarter
-        // before this task's first, qb - 2) is done: every K step reads every slice
-        if (T >= 1 && !oz_wait(smem_u32(&acc_full[(qb - 2) & 1]), (uint32_t)(((qb - 2) >> 1) & 1))) {
-          ok = false;
-          break;
+        // the A slices of this task (unless the previous task had the same rows), once the
+        // previous task's last quarter (the latest quarter before this task's first, qb - 2)
+        // is done: every K step reads every slice
+        if (!reuse) {
+          if (T >= 1 &&
+              !oz_wait(smem_u32(&acc_full[(qb - 2) & 1]), (uint32_t)(((qb - 2) >> 1) & 1))) {
+            ok = false;
+            break;
+          }
+          oz_expect(smem_u32(&a_full), kOzABytes);
+          for (int p = 0; p < kOzSlices; p++)
+            oz_bulk_load(smem_u32(A + p * kOzASlice),
+                         oz + p * stride + (size_t)(t.w + t.y) * kOzRowBytes, kOzASlice,
+                         smem_u32(&a_full));
+          T++;
+          arow = t.w + t.y;
         }
-        oz_expect(smem_u32(&a_full), kOzABytes);
-        for (int p = 0; p < kOzSlices; p++)
-          oz_bulk_load(smem_u32(A + p * kOzASlice),
-                       oz + p * stride + (size_t)(t.w + t.y) * kOzRowBytes, kOzASlice,
-                       smem_u32(&a_full));
-        T++;
         for (int j = 1; j < nq && ok; j++) ok = load_b(j);
         if (!ok) break;
-        tq = gridDim.x >= ntasks ? ntasks : (int)gridDim.x + atomicAdd(queue, 1);
+        if (++tq >= tend) {  // the run is done: claim the next one
+          const int g = tq < ntasks - 4 * (int)gridDim.x ? 2 : 1;
+          tq = g0 * (int)gridDim.x >= ntasks ? ntasks
+                                             : g0 * (int)gridDim.x + atomicAdd(queue, g);
+          tend = min(tq + g, ntasks);
+        }
       }
       if (!ok) {
         s_fail = 1;
@@ -443,7 +462,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const uint64_t db[2] = {oz_desc(smem_u32(Bq0)), oz_desc(smem_u32(Bq0 + kOzQBytes))};
       bool ok = true;
       long long q = 0;  // quarters issued (TMEM set and B buffer = q & 1)
-      long long T = 0;  // tasks issued
+      long long T = 0;  // A slice loads waited for
       for (long long ord = 0; ok; ord++) {
         const int rs = (int)(ord % kOzRing);
         if (!oz_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kOzRing) & 1))) {
@@ -452,7 +471,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         }
         const int2 e = ring[rs];
         if (e.x >= ntasks) break;
-        const int nq = e.y & 0xff, ks = e.y >> 8;
+        const int nq = e.y & 0xff, ks = (e.y >> 8) & 0xff;
+        const bool reuse = (e.y >> 16) & 1;  // the previous task's A slices
         for (int j = 0; j < nq; j++, q++) {
           const int b = (int)(q & 1);
           if (!oz_wait(smem_u32(&b_full[b]), (uint32_t)((q >> 1) & 1)) ||
@@ -461,7 +481,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             ok = false;
             break;
           }
-          if (j == 0 && !oz_wait(smem_u32(&a_full), (uint32_t)(T & 1))) {  // the task's A
+          if (j == 0 && !reuse && !oz_wait(smem_u32(&a_full), (uint32_t)(T & 1))) {  // the task's A
             ok = false;
             break;
           }
@@ -476,7 +496,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                      (p > 0 || k > 0) ? 1u : 0u);
           oz_commit(smem_u32(&acc_full[b]));
         }
-        T++;
+        if (!reuse) T++;
       }
       if (!ok) s_fail = 1;
       // bounded wait for the MMAs in flight (the last quarter's commit covers all earlier ones)
