@@ -13,14 +13,14 @@
 //               brought into shared memory by bulk copies issued by a load thread, which
 //               also claims the tasks; an MMA thread issues, for every slice pair p + q < 8,
 //               the bf16 MMAs of D_{p+q} += S_p S_q^T into the quarter's set of tensor-memory
-//               accumulators (one per diagonal p + q, 8 x 32 columns; two sets), slice by
-//               slice, so that a task's last quarter releases each A slice for the next task
-//               as soon as its MMAs are done.  Every partial sum of a diagonal is an integer
-//               below 2^22 (K <= 64), so FP32 accumulation is exact.  Consumer warps read a
-//               finished set (lane = tile row), release it, form U[i,k] = 2^(e_i+e_k)
+//               accumulators (one per diagonal p + q, 8 x 32 columns; two sets); tasks are
+//               claimed in runs of two, so that the second tile of a row strip reuses the
+//               A slices.  Every partial sum of a diagonal is an integer below 2^22
+//               (K <= 64), so FP32 accumulation is exact.  Consumer warps read a finished
+//               set (lane = tile row), release it, form U[i,k] = 2^(e_i+e_k)
 //               sum_d 2^(-7(d+2)) D_d[i,k] as an FP64 value (integer combination, one
-//               int64 -> double conversion) and scatter it into the ancestors with FP64
-//               atomics (or write the owner staging buffer) while the tensor cores compute
+//               int64 -> double conversion) and add it into the ancestors with FP64
+//               reductions (or write the owner staging buffer) while the tensor cores compute
 //               the next quarter; metadata warps prepare each task's targets one task ahead.
 // Every wait is bounded in time (kOzWaitCycles SM clock cycles, about a second): then the
 // kernel records a timeout in err[3],
@@ -300,11 +300,11 @@ __device__ __forceinline__ void oz_arrive(uint32_t bar) {
 // diagonals x 32 columns, slice by slice; the 16 consumer warps drain a finished set (and
 // release it) while the tensor cores compute the next quarter, then scatter; four metadata
 // warps build each task's exponents, column targets and relative rows one task ahead.
-// Barriers: a_full[p] (A slice p in), a_free[p] (the MMAs of a task's last quarter that read
-// A slice p are done: the slice may be reloaded for the next task while the later slices'
-// MMAs still run), b_full[2] (quarter B buffers in), acc_full[2] (a set's MMAs done: also
-// frees the B buffer they read), acc_empty[2] (a set drained), meta_full[2] / meta_empty[2]
-// (a metadata buffer built / released), ring_full[] (the task order).
+// Barriers: a_full (a task's 8 A slices in; a task with the previous task's A rows reuses
+// them), b_full[2] (quarter B buffers in), acc_full[2] (a set's MMAs done: also frees the B
+// buffer they read, and after a task's last quarter the A slices), acc_empty[2] (a set
+// drained), meta_full[2] / meta_empty[2] (a metadata buffer built / released), ring_full[]
+// (the task order).
 template <bool OWNER>
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_schur_oz(const int4* __restrict__ tasks, int ntasks, int* __restrict__ queue,
