@@ -376,23 +376,43 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int g0 = ntasks >= 4 * (int)gridDim.x ? 2 : 1;
       int tq = g0 * (int)blockIdx.x;         // a CTA's first run follows its block index
       int tend = min(tq + g0, ntasks);       // end of the claimed run
-      int arow = -1;                         // slice row of the A rows in shared memory
-      for (;;) {
-        int4 t = make_int4(0, 0, 0, 0);
-        int nq = 0, ks = 0;
-        bool reuse = false;
-        if (tq < ntasks) {
-          t = tasks[tq];
-          const SnDev& dd = sns[t.x];
-          nq = min(4, (dd.m - dd.n - t.z + kOzQ - 1) / kOzQ);
-          ks = (dd.n + 15) >> 4;
-          reuse = t.w + t.y == arow;
+      // The ring runs one task ahead of the copies: a task is published (and the next one
+      // claimed) before the current task's copies are issued, so that the metadata warps
+      // can build its targets while the current task is still being copied and computed.
+      int prow = -1;                         // slice row of the last published task's A rows
+      struct Job {
+        int4 t;
+        int nq, ks;
+        bool reuse;  // the A rows of the task before it (still in shared memory)
+      };
+      auto publish = [&](int ti) -> Job {
+        Job jb{make_int4(0, 0, 0, 0), 0, 0, false};
+        if (ti < ntasks) {
+          jb.t = tasks[ti];
+          const SnDev& dd = sns[jb.t.x];
+          jb.nq = min(4, (dd.m - dd.n - jb.t.z + kOzQ - 1) / kOzQ);
+          jb.ks = (dd.n + 15) >> 4;
+          jb.reuse = jb.t.w + jb.t.y == prow;
+          prow = jb.t.w + jb.t.y;
         }
         const int rs = (int)(ord % kOzRing);
-        ring[rs] = make_int2(tq < ntasks ? tq : ntasks, nq | (ks << 8) | ((int)reuse << 16));
+        ring[rs] = make_int2(ti < ntasks ? ti : ntasks, jb.nq | (jb.ks << 8) | ((int)jb.reuse << 16));
         oz_arrive(smem_u32(&ring_full[rs]));
         ord++;
-        if (tq >= ntasks) break;
+        return jb;
+      };
+      int cur = tq;
+      Job job = publish(cur);
+      while (cur < ntasks) {
+        if (++tq >= tend) {  // the run is done: claim the next one
+          const int g = tq < ntasks - 4 * (int)gridDim.x ? 2 : 1;
+          tq = g0 * (int)gridDim.x >= ntasks ? ntasks
+                                             : g0 * (int)gridDim.x + atomicAdd(queue, g);
+          tend = min(tq + g, ntasks);
+        }
+        const Job next = publish(tq);  // the next task (or the stop entry)
+        const int4 t = job.t;
+        const int nq = job.nq;
         // quarter j's B slices, once the MMAs of the quarter two back (same buffer) are done
         auto load_b = [&](int j) -> bool {
           const int b = (int)(qb & 1);
@@ -416,7 +436,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         // the A slices of this task (unless the previous task had the same rows), once the
         // previous task's last quarter (the latest quarter before this task's first, qb - 2)
         // is done: every K step reads every slice
-        if (!reuse) {
+        if (!job.reuse) {
           if (T >= 1 &&
               !oz_wait(smem_u32(&acc_full[(qb - 2) & 1]), (uint32_t)(((qb - 2) >> 1) & 1))) {
             ok = false;
@@ -428,16 +448,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                          oz + p * stride + (size_t)(t.w + t.y) * kOzRowBytes, kOzASlice,
                          smem_u32(&a_full));
           T++;
-          arow = t.w + t.y;
         }
         for (int j = 1; j < nq && ok; j++) ok = load_b(j);
         if (!ok) break;
-        if (++tq >= tend) {  // the run is done: claim the next one
-          const int g = tq < ntasks - 4 * (int)gridDim.x ? 2 : 1;
-          tq = g0 * (int)gridDim.x >= ntasks ? ntasks
-                                             : g0 * (int)gridDim.x + atomicAdd(queue, g);
-          tend = min(tq + g, ntasks);
-        }
+        job = next;
+        cur = tq;
       }
       if (!ok) {
         s_fail = 1;
