@@ -264,10 +264,11 @@ __device__ __forceinline__ double oz_to_double(long long W, int E) {
   return NEG ? -r : r;
 }
 
-constexpr int kOzMaxRuns = 16;  // column targets per task whose relative rows are cached
+constexpr int kOzMaxRuns = 8;  // column targets per task whose relative rows are cached
+constexpr int kOzMetaBufs = 3;  // metadata buffers: the metadata warps run up to two tasks ahead
 
-// Per-task metadata, double-buffered: the metadata warps build the next task's copy while
-// the consumers scatter with the current one.
+// Per-task metadata, in kOzMetaBufs buffers: the metadata warps build the next tasks' copies
+// while the consumers scatter with the current one.
 static_assert(2 * kOzN == 128, "the run count sums four 32-column words");
 struct OzMeta {
   double* cp[2 * kOzN];  // each column's target panel column (its relative rows are added)
@@ -303,7 +304,7 @@ __device__ __forceinline__ void oz_arrive(uint32_t bar) {
 // Barriers: a_full (a task's 8 A slices in; a task with the previous task's A rows reuses
 // them), b_full[2] (quarter B buffers in), acc_full[2] (a set's MMAs done: also frees the B
 // buffer they read, and after a task's last quarter the A slices), acc_empty[2] (a set
-// drained), meta_full[2] / meta_empty[2] (a metadata buffer built / released), ring_full[]
+// drained), meta_full[] / meta_empty[] (a metadata buffer built / released), ring_full[]
 // (the task order).
 template <bool OWNER>
 __global__ void __launch_bounds__(kOzThreads, 1)
@@ -318,8 +319,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __shared__ __align__(8) uint64_t ring_full[kOzRing];
   __shared__ int2 ring[kOzRing];  // {task, quarters | K steps << 8} (task = ntasks: stop)
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t meta_full[2], meta_empty[2];
-  __shared__ OzMeta meta[2];
+  __shared__ __align__(8) uint64_t meta_full[kOzMetaBufs], meta_empty[kOzMetaBufs];
+  __shared__ OzMeta meta[kOzMetaBufs];
   __shared__ __align__(8) uint64_t never;  // test hook: a barrier nothing completes
   __shared__ int s_mtq;  // the metadata warps' next task (or ntasks: stop)
   __shared__ int s_fail;
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     }
     for (int i = 0; i < kOzRing; i++)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ring_full[i])));
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < kOzMetaBufs; i++) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&meta_full[i])),
                    "r"(kOzMetaThreads));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&meta_empty[i])),
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     }
   } else if (warp >= kOzMetaBase / 32) {
     // ---------------- metadata warps: one thread per tile row / column ----------------
-    // For each task in ring order, into meta[ord & 1] once the consumers have released it:
+    // For each task in ring order, into meta[ord % kOzMetaBufs] once the consumers have released it:
     // the rows' and columns' slice exponents, every column's target supernode, the runs of
     // equal target (ballot per 32 columns), each column's run and column inside its target,
     // per run the relative-map base and target panel, and the relative rows of the first
@@ -527,13 +528,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     // group's decisions are uniform.
     const int mt = tid - kOzMetaBase, mwarp = mt >> 5;
     for (int ord = 0;; ord++) {
-      const int buf = ord & 1;
+      const int buf = ord % kOzMetaBufs;
       if (mt == 0) {
         const int rs = ord % kOzRing;
         int tq = ntasks;
         if (!oz_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kOzRing) & 1)) ||
-            (ring[rs].x < ntasks && ord >= 2 &&
-             !oz_wait(smem_u32(&meta_empty[buf]), (uint32_t)(((ord >> 1) - 1) & 1))))
+            (ring[rs].x < ntasks && ord >= kOzMetaBufs &&
+             !oz_wait(smem_u32(&meta_empty[buf]), (uint32_t)((ord / kOzMetaBufs - 1) & 1))))
           s_fail = 1;
         else
           tq = ring[rs].x;
@@ -619,14 +620,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int c16 = 16 * ((warp >> 2) & 1);   // this warp's 16 columns of a quarter
     long long q0 = 0;                         // global index of the task's first quarter
     for (int ord = 0;; ord++) {
-      const int rs = ord % kOzRing, buf = ord & 1;
+      const int rs = ord % kOzRing, buf = ord % kOzMetaBufs;
       if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kOzRing) & 1)))) {
         s_fail = 1;
         break;
       }
       if (ring[rs].x >= ntasks) break;
       const OzMeta& M = meta[buf];
-      if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&meta_full[buf]), (uint32_t)((ord >> 1) & 1)))) {
+      if (!__all_sync(0xffffffffu, oz_wait(smem_u32(&meta_full[buf]), (uint32_t)((ord / kOzMetaBufs) & 1)))) {
         s_fail = 1;
         break;
       }
