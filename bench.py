@@ -651,6 +651,14 @@ def main():
                   "bytes": solve_bytes, "ms": sol_ms,
                   "note": f"2 passes x {esz} B x nnz(L) + vectors; solve time from the timed "
                           "region's CUDA events" + (" (refinement included)" if mixed else "")}
+    if not mixed:
+        # the same solve against the FP64 unit: one FP64 FMA per stored value of L per pass
+        # and right-hand side, which on this part bounds the solve before HBM does
+        solve_flops = 2.0 * 2.0 * sym.info["nnz_l"] * nrhs
+        solve_roof["fp64"] = {"achieved": solve_flops / (sol_ms * 1e-3) / 1e12,
+                              "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                              "frac": solve_flops / (sol_ms * 1e-3) / 1e12 / fp64_peak_tflops,
+                              "flops": solve_flops}
     value = replica_rate(world, F, ms_step * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
