@@ -14,8 +14,8 @@
 //               also claims the tasks; an MMA thread issues, for every slice pair p + q < 8,
 //               the bf16 MMAs of D_{p+q} += S_p S_q^T into the quarter's set of tensor-memory
 //               accumulators (one per diagonal p + q, 8 x 32 columns; two sets); tasks are
-//               claimed in runs of two, so that the second tile of a row strip reuses the
-//               A slices.  Every partial sum of a diagonal is an integer below 2^22
+//               claimed in runs of up to four, so that the later tiles of a row strip reuse
+//               the A slices.  Every partial sum of a diagonal is an integer below 2^22
 //               (K <= 64), so FP32 accumulation is exact.  Consumer warps read a finished
 //               set (lane = tile row), release it, form U[i,k] = 2^(e_i+e_k)
 //               sum_d 2^(-7(d+2)) D_d[i,k] as an FP64 value (integer combination, one
@@ -370,11 +370,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       long long qb = 0;                      // quarter B buffers issued (buffer = qb & 1)
       long long ord = 0;                     // ring entries published
       bool ok = true;
-      // Tasks are claimed in runs of two while plenty remain (g0 per CTA at first, then from
-      // the queue), singles near the end: the tasks of a row strip are consecutive in the
-      // list, so the second task of a run usually has the first one's A rows, which stay in
-      // shared memory.
-      const int g0 = ntasks >= 4 * (int)gridDim.x ? 2 : 1;
+      // Tasks are claimed in runs (g0 per CTA at first, then from the queue): four while more
+      // than 16 per CTA remain, then two while more than 4 do, then singles: the tasks of a
+      // row strip are consecutive in the list, so the later tasks of a run usually have the
+      // first one's A rows, which stay in shared memory.
+      const int g0 = ntasks >= 8 * (int)gridDim.x ? 4 : (ntasks >= 4 * (int)gridDim.x ? 2 : 1);
       int tq = g0 * (int)blockIdx.x;         // a CTA's first run follows its block index
       int tend = min(tq + g0, ntasks);       // end of the claimed run
       // The ring runs one task ahead of the copies: a task is published (and the next one
@@ -406,7 +406,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       Job job = publish(cur);
       while (cur < ntasks) {
         if (++tq >= tend) {  // the run is done: claim the next one
-          const int g = tq < ntasks - 4 * (int)gridDim.x ? 2 : 1;
+          const int g = tq < ntasks - 16 * (int)gridDim.x ? 4
+                        : (tq < ntasks - 4 * (int)gridDim.x ? 2 : 1);
           tq = g0 * (int)gridDim.x >= ntasks ? ntasks
                                              : g0 * (int)gridDim.x + atomicAdd(queue, g);
           tend = min(tq + g, ntasks);
