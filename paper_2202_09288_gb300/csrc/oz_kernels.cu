@@ -21,7 +21,7 @@
 //               sum_d 2^(-7(d+2)) D_d[i,k] as an FP64 value (integer combination, one
 //               int64 -> double conversion) and add it into the ancestors with FP64
 //               reductions (or write the owner staging buffer) while the tensor cores compute
-//               the next quarter; metadata warps prepare each task's targets one task ahead.
+//               the next quarter; metadata warps prepare the coming tasks' targets ahead.
 // Every wait is bounded in time (kOzWaitCycles SM clock cycles, about a second): then the
 // kernel records a timeout in err[3],
 // waits (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
@@ -300,7 +300,7 @@ __device__ __forceinline__ void oz_arrive(uint32_t bar) {
 // an MMA thread (its own warp) issues each quarter's MMAs into one of two TMEM sets of 8
 // diagonals x 32 columns, slice by slice; the 16 consumer warps drain a finished set (and
 // release it) while the tensor cores compute the next quarter, then scatter; four metadata
-// warps build each task's exponents, column targets and relative rows one task ahead.
+// warps build each task's exponents, column targets and relative rows up to two tasks ahead.
 // Barriers: a_full (a task's 8 A slices in; a task with the previous task's A rows reuses
 // them), b_full[2] (quarter B buffers in), acc_full[2] (a set's MMAs done: also frees the B
 // buffer they read, and after a task's last quarter the A slices), acc_empty[2] (a set
