@@ -8,17 +8,18 @@
 //   k_tf32_split  the hi and lo parts of every L21 row of the level's 128-tile supernodes,
 //                 in planes (part, 32-column chunk) of 128-byte rows whose 16-byte pieces
 //                 are pre-swizzled for the tensor cores' 128-byte swizzle;
-//   k_schur_tf32  a persistent CTA per SM.  One producer thread (its own warp) streams each
-//                 task's operand chunks (A hi/lo, B hi/lo: 64 KB) into a 3-stage shared
-//                 memory ring with bulk copies and issues the MMAs (M = N = 128, three per
-//                 K step of 8) into one of four 128-column tensor-memory accumulators;
-//                 four metadata warps build each task's column targets and relative rows
-//                 ahead of use, into one of two buffers; 16 consumer warps read finished
-//                 accumulators (tcgen05.ld, one row per thread) and scatter them into the
-//                 ancestors with FP32 atomics (or write the owner staging buffer).  Loads,
-//                 MMAs, metadata and the scatter of different tasks overlap through
-//                 mbarriers: stage full/empty, accumulator full/empty, metadata full/empty,
-//                 and a ring that hands the task sequence to the consumers.
+//   k_schur_tf32  a persistent CTA per SM.  A load thread (its own warp) claims the tasks,
+//                 hands each to the other roles through a ring and streams its operand
+//                 chunks (A hi/lo, B hi/lo: 64 KB) into a 3-stage shared memory ring with
+//                 bulk copies; an MMA thread (its own warp) issues, chunk by chunk in ring
+//                 order, the MMAs (M = N = 128, three per K step of 8) into one of four
+//                 128-column tensor-memory accumulators; four metadata warps build each
+//                 task's column targets and relative rows ahead of use, into one of three
+//                 buffers; 16 consumer warps read finished accumulators (tcgen05.ld, one row
+//                 per thread) and add them into the ancestors with FP32 reductions (or write
+//                 the owner staging buffer).  Loads, MMAs, metadata and the scatter of
+//                 different tasks overlap through mbarriers: stage full/empty, accumulator
+//                 full/empty, metadata full/empty, and the ring of the task sequence.
 // Every wait is bounded in time (kTfWaitCycles SM clock cycles, about a second): then the
 // thread records a timeout in err[3]
 // and stops; its partners then time out as well, waits for copies and MMAs in flight are
@@ -45,9 +46,13 @@ constexpr size_t kTfSmem = 1024 + kTfStages * kTfStageBytes;
 constexpr int kTfSlots = 4;                        // accumulators of 128 TMEM columns
 constexpr int kTfConsumers = 512;                  // 16 warps: drain + scatter
 constexpr int kTfMetaThreads = 128;                // 4 warps: per-task column metadata
-constexpr int kTfThreads = kTfConsumers + 32 + kTfMetaThreads;  // + the producer warp
+constexpr int kTfMmaWarp = kTfConsumers / 32;       // issues the MMAs (one thread)
+constexpr int kTfLoadWarp = kTfMmaWarp + 1;         // claims tasks, issues the copies (one thread)
+constexpr int kTfMetaBase = kTfConsumers + 64;      // first metadata thread
+constexpr int kTfThreads = kTfMetaBase + kTfMetaThreads;
 constexpr int kTfRing = 16;
-constexpr int kTfMaxRuns = 16;
+constexpr int kTfMaxRuns = 8;   // column targets per task whose relative rows are cached
+constexpr int kTfMetaBufs = 3;  // metadata buffers: the metadata warps run up to two tasks ahead
 // Bound of every wait in SM clock cycles (~1 s at 2 GHz), counted with clock64(): a poll of
 // mbarrier.try_wait may suspend the thread for a hardware-defined time.
 constexpr long long kTfWaitCycles = 1ll << 31;
@@ -219,8 +224,8 @@ __global__ void __launch_bounds__(kTfThreads, 1)
   __shared__ __align__(8) uint64_t ring_full[kTfRing];
   __shared__ int ring[kTfRing];
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t meta_full[2], meta_empty[2];
-  __shared__ TfMeta meta[2];
+  __shared__ __align__(8) uint64_t meta_full[kTfMetaBufs], meta_empty[kTfMetaBufs];
+  __shared__ TfMeta meta[kTfMetaBufs];
   __shared__ int s_mtq;  // the metadata warps' next task (or ntasks: stop)
   __shared__ int s_fail;
   __shared__ __align__(8) uint64_t never;  // test hook: a barrier nothing completes
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
     }
     for (int i = 0; i < kTfRing; i++)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ring_full[i])));
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < kTfMetaBufs; i++) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&meta_full[i])),
                    "r"(kTfMetaThreads));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&meta_empty[i])),
@@ -264,118 +269,111 @@ __global__ void __launch_bounds__(kTfThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
 
-  if (warp == kTfConsumers / 32) {
-    // ---------------- producer: operand loads and MMAs, one thread ----------------
+  if (warp == kTfLoadWarp) {
+    // ---------------- loads: task claims, ring, bulk copies; one thread ----------------
     if (lane == 0) {
-      const uint32_t idesc = tf_idesc();
-      // chunks whose loads are issued but whose MMAs are not, oldest first: task index,
-      // chunk, chunks of the task, task ordinal (accumulator slot and ring entry)
-      int p_tq[kTfStages], p_c[kTfStages], p_nch[kTfStages], p_ord[kTfStages];
-      int head = 0, npend = 0;
       long long item = 0;  // chunk loads issued (stage = item % kTfStages)
-      long long done = 0;  // chunks whose MMAs are issued
-      int cur_tq = blockIdx.x, cur_c = 0, cur_nch = 0, ord = 0;
-      bool more = cur_tq < ntasks, ok = true;
-      ring[0] = more ? cur_tq : ntasks;
-      tf_arrive(smem_u32(&ring_full[0]));
-      if (more) cur_nch = (sns[tasks[cur_tq].x].n + kTfChunk - 1) / kTfChunk;
-      while (ok && (more || npend > 0)) {
-        // issue chunk loads up to the ring depth
-        while (more && npend < kTfStages) {
+      int ord = 0;         // ring entries published
+      bool ok = true;
+      int tq = blockIdx.x;  // a CTA's first task is its block index
+      for (;;) {
+        ring[ord % kTfRing] = tq < ntasks ? tq : ntasks;  // the task order, at claim time
+        tf_arrive(smem_u32(&ring_full[ord % kTfRing]));
+        ord++;
+        if (tq >= ntasks) break;
+        const int4 t = tasks[tq];
+        const int nch = (sns[t.x].n + kTfChunk - 1) / kTfChunk;
+        const uint8_t* arow = oz + (size_t)(t.w + t.y) * kOzRowBytes;
+        const uint8_t* brow = oz + (size_t)(t.w + t.z) * kOzRowBytes;
+        for (int c = 0; c < nch && ok; c++, item++) {
           const int s = (int)(item % kTfStages);
           if (item >= kTfStages &&  // the stage's previous MMAs must have read it
               !tf_wait(smem_u32(&st_empty[s]), (uint32_t)(((item / kTfStages) - 1) & 1))) {
             ok = false;
             break;
           }
-          const int4 t = tasks[cur_tq];
           unsigned char* sb = stage_base + (size_t)s * kTfStageBytes;
           const uint32_t bar = smem_u32(&st_full[s]);
-          const uint8_t* arow = oz + (size_t)(t.w + t.y) * kOzRowBytes;
-          const uint8_t* brow = oz + (size_t)(t.w + t.z) * kOzRowBytes;
           tf_expect(bar, kTfStageBytes);
-          tf_bulk_load(smem_u32(sb), arow + (size_t)cur_c * stride, kTfPlane, bar);
-          tf_bulk_load(smem_u32(sb + kTfPlane), arow + (size_t)(4 + cur_c) * stride, kTfPlane, bar);
-          tf_bulk_load(smem_u32(sb + 2 * kTfPlane), brow + (size_t)cur_c * stride, kTfPlane, bar);
-          tf_bulk_load(smem_u32(sb + 3 * kTfPlane), brow + (size_t)(4 + cur_c) * stride, kTfPlane,
+          tf_bulk_load(smem_u32(sb), arow + (size_t)c * stride, kTfPlane, bar);
+          tf_bulk_load(smem_u32(sb + kTfPlane), arow + (size_t)(4 + c) * stride, kTfPlane, bar);
+          tf_bulk_load(smem_u32(sb + 2 * kTfPlane), brow + (size_t)c * stride, kTfPlane, bar);
+          tf_bulk_load(smem_u32(sb + 3 * kTfPlane), brow + (size_t)(4 + c) * stride, kTfPlane,
                        bar);
-          const int slot = (head + npend) % kTfStages;
-          p_tq[slot] = cur_tq;
-          p_c[slot] = cur_c;
-          p_nch[slot] = cur_nch;
-          p_ord[slot] = ord;
-          npend++;
-          item++;
-          // next chunk, or next task (whose index the consumers learn through the ring)
-          if (++cur_c >= cur_nch) {
-            cur_tq = gridDim.x >= ntasks ? ntasks : (int)gridDim.x + atomicAdd(queue, 1);
-            ord++;
-            more = cur_tq < ntasks;
-            ring[ord % kTfRing] = more ? cur_tq : ntasks;
-            tf_arrive(smem_u32(&ring_full[ord % kTfRing]));
-            cur_c = 0;
-            if (more) cur_nch = (sns[tasks[cur_tq].x].n + kTfChunk - 1) / kTfChunk;
-          }
         }
-        if (!ok || npend == 0) break;
-        // MMAs of the oldest pending chunk
-        const int s = (int)(done % kTfStages);
-        if (!tf_wait(smem_u32(&st_full[s]), (uint32_t)((done / kTfStages) & 1))) {
-          ok = false;
-          break;
-        }
-        const int acc = p_ord[head] % kTfSlots;
-        if (p_c[head] == 0 && p_ord[head] >= kTfSlots &&  // wait for the drain of the slot
-            !tf_wait(smem_u32(&acc_empty[acc]), (uint32_t)(((p_ord[head] / kTfSlots) - 1) & 1))) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const int n = sns[tasks[p_tq[head]].x].n;
-        const int kw = min(kTfChunk, n - kTfChunk * p_c[head]);
-        const uint32_t sa = smem_u32(stage_base + (size_t)s * kTfStageBytes);
-        const uint64_t ahi = tf_desc(sa), alo = tf_desc(sa + kTfPlane);
-        const uint64_t bhi = tf_desc(sa + 2 * kTfPlane), blo = tf_desc(sa + 3 * kTfPlane);
-        const uint32_t dt = tmem + (uint32_t)(acc * kTfM);
-        for (int kk = 0; kk < (kw + 7) / 8; kk++) {  // K steps of 8 TF32 = 32 bytes
-          tf_mma(dt, ahi + 2 * kk, bhi + 2 * kk, idesc, (p_c[head] > 0 || kk > 0) ? 1u : 0u);
-          tf_mma(dt, ahi + 2 * kk, blo + 2 * kk, idesc, 1u);
-          tf_mma(dt, alo + 2 * kk, bhi + 2 * kk, idesc, 1u);
-        }
-        tf_commit(smem_u32(&st_empty[s]));  // the stage is free once these MMAs are done
-        if (p_c[head] + 1 == p_nch[head]) tf_commit(smem_u32(&acc_full[acc]));
-        head = (head + 1) % kTfStages;
-        npend--;
-        done++;
+        if (!ok) break;
+        tq = gridDim.x >= ntasks ? ntasks : (int)gridDim.x + atomicAdd(queue, 1);
       }
       if (!ok) {
         s_fail = 1;
-        // the consumers stop at their next ring wait on an end marker
-        ring[(ord + 1) % kTfRing] = ntasks;
-        tf_arrive(smem_u32(&ring_full[(ord + 1) % kTfRing]));
+        // the other roles stop at their next ring wait on an end marker
+        ring[ord % kTfRing] = ntasks;
+        tf_arrive(smem_u32(&ring_full[ord % kTfRing]));
       }
-      // bounded waits for the MMAs and copies still in flight
-      if (done > 0)
-        tf_wait(smem_u32(&st_empty[(done - 1) % kTfStages]), (uint32_t)(((done - 1) / kTfStages) & 1));
-      for (long long q = done; q < item; q++)
+      // bounded waits for the copies still in flight: the last one of each stage
+      for (long long q = item - kTfStages < 0 ? 0 : item - kTfStages; q < item; q++)
         tf_wait(smem_u32(&st_full[q % kTfStages]), (uint32_t)((q / kTfStages) & 1));
     }
-  } else if (warp > kTfConsumers / 32) {
+  } else if (warp == kTfMmaWarp) {
+    // ---------------- MMAs, one thread, in ring order ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tf_idesc();
+      long long done = 0;  // chunks whose MMAs are issued (stage = done % kTfStages)
+      bool ok = true;
+      for (int ord = 0; ok; ord++) {
+        if (!tf_wait(smem_u32(&ring_full[ord % kTfRing]), (uint32_t)((ord / kTfRing) & 1))) {
+          ok = false;
+          break;
+        }
+        const int tq = ring[ord % kTfRing];
+        if (tq >= ntasks) break;
+        const int n = sns[tasks[tq].x].n;
+        const int nch = (n + kTfChunk - 1) / kTfChunk;
+        const int acc = ord % kTfSlots;
+        for (int c = 0; c < nch; c++, done++) {
+          const int s = (int)(done % kTfStages);
+          if (!tf_wait(smem_u32(&st_full[s]), (uint32_t)((done / kTfStages) & 1)) ||
+              (c == 0 && ord >= kTfSlots &&  // wait for the drain of the slot
+               !tf_wait(smem_u32(&acc_empty[acc]), (uint32_t)(((ord / kTfSlots) - 1) & 1)))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const int kw = min(kTfChunk, n - kTfChunk * c);
+          const uint32_t sa = smem_u32(stage_base + (size_t)s * kTfStageBytes);
+          const uint64_t ahi = tf_desc(sa), alo = tf_desc(sa + kTfPlane);
+          const uint64_t bhi = tf_desc(sa + 2 * kTfPlane), blo = tf_desc(sa + 3 * kTfPlane);
+          const uint32_t dt = tmem + (uint32_t)(acc * kTfM);
+          for (int kk = 0; kk < (kw + 7) / 8; kk++) {  // K steps of 8 TF32 = 32 bytes
+            tf_mma(dt, ahi + 2 * kk, bhi + 2 * kk, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+            tf_mma(dt, ahi + 2 * kk, blo + 2 * kk, idesc, 1u);
+            tf_mma(dt, alo + 2 * kk, bhi + 2 * kk, idesc, 1u);
+          }
+          tf_commit(smem_u32(&st_empty[s]));  // the stage is free once these MMAs are done
+          if (c + 1 == nch) tf_commit(smem_u32(&acc_full[acc]));
+        }
+      }
+      if (!ok) s_fail = 1;
+      // bounded wait for the MMAs in flight (the last commit covers all earlier ones)
+      if (done > 0)
+        tf_wait(smem_u32(&st_empty[(done - 1) % kTfStages]), (uint32_t)(((done - 1) / kTfStages) & 1));
+    }
+  } else if (warp >= kTfMetaBase / 32) {
     // ---------------- metadata warps: one thread per tile column ----------------
-    // For each task in ring order, into meta[ord & 1] once the consumers have released it:
+    // For each task in ring order, into meta[ord % kTfMetaBufs] once the consumers have released it:
     // every column's target supernode, the runs of equal target (ballot per 32 columns), each
     // column's run and column inside its target, per run the relative-map base and target
     // panel, and the relative rows of the first kTfMaxRuns runs.  Thread 0 alone waits on
     // the ring and on the buffer, so that the group's decisions are uniform.
-    const int mt = tid - (kTfConsumers + 32), mwarp = mt >> 5;
+    const int mt = tid - kTfMetaBase, mwarp = mt >> 5;
     for (int ord = 0;; ord++) {
-      const int buf = ord & 1;
+      const int buf = ord % kTfMetaBufs;
       if (mt == 0) {
         const int rs = ord % kTfRing;
         int tq = ntasks;
         if (!tf_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kTfRing) & 1)) ||
-            (ring[rs] < ntasks && ord >= 2 &&
-             !tf_wait(smem_u32(&meta_empty[buf]), (uint32_t)(((ord >> 1) - 1) & 1))))
+            (ring[rs] < ntasks && ord >= kTfMetaBufs &&
+             !tf_wait(smem_u32(&meta_empty[buf]), (uint32_t)((ord / kTfMetaBufs - 1) & 1))))
           s_fail = 1;
         else
           tq = ring[rs];
@@ -450,7 +448,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
     // ---------------- consumers: accumulator drain and scatter ----------------
     // Each wait's outcome is made uniform over the warp (tcgen05.ld is warp-collective).
     for (int ord = 0;; ord++) {
-      const int rs = ord % kTfRing, buf = ord & 1;
+      const int rs = ord % kTfRing, buf = ord % kTfMetaBufs;
       if (!__all_sync(0xffffffffu, tf_wait(smem_u32(&ring_full[rs]), (uint32_t)((ord / kTfRing) & 1)))) {
         s_fail = 1;
         break;
@@ -458,7 +456,7 @@ __global__ void __launch_bounds__(kTfThreads, 1)
       if (ring[rs] >= ntasks) break;
       const TfMeta& M = meta[buf];
       const int acc = ord % kTfSlots;
-      if (!__all_sync(0xffffffffu, tf_wait(smem_u32(&meta_full[buf]), (uint32_t)((ord >> 1) & 1)) &&
+      if (!__all_sync(0xffffffffu, tf_wait(smem_u32(&meta_full[buf]), (uint32_t)((ord / kTfMetaBufs) & 1)) &&
                                        (acc_wait > 0  // test hook: a barrier never completed
                                             ? tf_wait(smem_u32(&never), 0u, acc_wait)
                                             : tf_wait(smem_u32(&acc_full[acc]),
