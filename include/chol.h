@@ -302,7 +302,7 @@ void chol_batch_free(chol_batch* batch);
  * would carry fewer than 50,000 flops each (OPT-D-COST); CHOL_GRAN_HYBRID takes
  * CHOL_GRAN_TILES when the average supernode size is above 50, or above 20 with density
  * nnz(A) / n^2 below 1e-4, and CHOL_GRAN_OPTD_COST otherwise.
- * Default {64, 17, 304, 128, 0, CHOL_GRAN_TILES}.  All thresholds >= 1 except the two
+ * Default {64, 17, 304, 128, 0, CHOL_GRAN_TILES, 8192}.  All thresholds >= 1 except the two
  * level thresholds (>= 0), granularity one of the four; anything else is CHOL_E_INVALID. */
 #define CHOL_GRAN_TILES 0
 #define CHOL_GRAN_OPTD 1

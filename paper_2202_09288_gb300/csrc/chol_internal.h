@@ -113,7 +113,7 @@ struct TilePolicy {
   // FP64: a level's 128-tile supernodes take the tensor-core TRSM when their off-diagonal rows
   // add up to at least this many (below, the inverse's FP64 latency on one SM per supernode
   // outweighs the FP64 TRSM it replaces)
-  int min_rows_trsm_tc = 16384;
+  int min_rows_trsm_tc = 8192;
 };
 
 // Host-side symbolic analysis result.
